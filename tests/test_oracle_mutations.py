@@ -1,0 +1,55 @@
+"""Plant plausible mistakes in the exact oracle (on the CPU) and check that
+the pins of test_oracle_pins.py catch each of them."""
+import inspect
+import types
+
+import numpy as np
+import pytest
+
+import oracle.exact as ex
+from oracle import direct
+from oracle.brute import brute
+from workloads import make_problem
+
+MUTATIONS = {
+    "sign_of_D_in_R": ("R = pibar + D.T @ W", "R = pibar - D.T @ W"),
+    "pi_instead_of_pibar": ("pibar = H.pibar(k).toarray()", "pibar = H.pi(k).toarray()"),
+    "transposed_B": ("B = W @ Ak @ W.T", "B = W @ Ak.T @ W.T + 1e-3 * np.eye(W.shape[0])"),
+    "g_restricted_by_pibar": ("gkm1 = R @ gk", "gkm1 = pibar @ gk"),
+    "dropped_detail_term": ("comps[k - 1] = P[k] @ (out[\"W\"][k].T @ out[\"w\"][k])",
+                            "comps[k - 1] = 0.0 * P[k][:, 0]"),
+    "wrong_D_rhs": ("D = -sla.cho_solve(cf, W @ Ak @ pibar.T)",
+                    "D = -sla.cho_solve(cf, W @ pibar.T)"),
+}
+
+
+def _mutated(name):
+    src = inspect.getsource(ex)
+    old, new = MUTATIONS[name]
+    assert old in src, name
+    mod = types.ModuleType("oracle.exact_mut")
+    mod.__dict__["__package__"] = "oracle"
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), mod.__dict__)
+    return mod.gamblet_exact
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name):
+    p = make_problem(8, 1e2, 1)
+    ud, _ = direct.solve(p.A, p.g)
+    b = brute(p.A, p.g, p.cells, p.q)
+    r = _mutated(name)(p.A, p.g, p.cells, p.q)
+    sum_ok = np.linalg.norm(r["u"] - ud) / np.linalg.norm(ud) < 1e-12
+    comps_ok = np.linalg.norm(r["comps"] - b["comps"]) / np.linalg.norm(b["comps"]) < 1e-11
+    A_ok = all(np.linalg.norm(r["A"][k] - b["Ak"][k]) / np.linalg.norm(b["Ak"][k]) < 1e-11
+               for k in range(1, p.q + 1))
+    assert not (sum_ok and comps_ok and A_ok)
+
+
+def test_unmutated_passes_same_checks():
+    p = make_problem(8, 1e2, 1)
+    ud, _ = direct.solve(p.A, p.g)
+    b = brute(p.A, p.g, p.cells, p.q)
+    r = ex.gamblet_exact(p.A, p.g, p.cells, p.q)
+    assert np.linalg.norm(r["u"] - ud) / np.linalg.norm(ud) < 1e-12
+    assert np.linalg.norm(r["comps"] - b["comps"]) / np.linalg.norm(b["comps"]) < 1e-11

@@ -1,0 +1,19 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+This package holds only input generation: the rough multiscale coefficient
+field, the random right-hand side, the Q1 finite-element stiffness matrix of
+-div(a grad u) = g with homogeneous Dirichlet conditions (the problem of
+Section 5.1, Eq. for the discrete system), and the level-q lattice cells that
+define the nested dyadic measurement hierarchy (Construction 4.2 with H = 1/2).
+None of the gamblet method's arithmetic lives here.
+"""
+from .rough import (  # noqa: F401
+    Problem,
+    K_REF,
+    assemble_q1,
+    example1_coefficient,
+    example1_rhs,
+    make_problem,
+    rough_log_coefficient,
+    interior_cells,
+)

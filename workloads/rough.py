@@ -1,0 +1,140 @@
+"""Synthetic rough-coefficient Poisson problems on the unit square.
+
+Recipe (stated once so both sides generate identical inputs):
+
+* Mesh: ``n`` x ``n`` square cells of side h = 1/n (n a power of two),
+  interior nodes (ix, iy) with 1 <= ix, iy <= n-1, numbered row-major
+  ``dof = (iy-1)*(n-1) + (ix-1)``.
+* Coefficient: piecewise constant per cell, log a = sum_{s=1..S} xi_s, where
+  xi_s is constant on the dyadic squares of side 2^-s and
+  xi_s ~ U[-1/2, 1/2] * ln(C) / S, so a has contrast at most C.
+  Draw order: ``rng = numpy.random.default_rng(seed)``; for s = 1..S draw
+  4^s uniforms laid out row-major over (sy, sx).
+* Right-hand side: g_i ~ N(0, 1) iid per interior node, drawn from the same
+  generator after the coefficient, row-major over (iy, ix).
+* Fine operator: Q1 (bilinear) elements, element matrix
+  a_c * K_REF with corners ordered counter-clockwise from (cx, cy); in 2-D
+  this matrix does not depend on h.  Boundary rows/columns are dropped
+  (homogeneous Dirichlet), giving the 9-point stencil matrix A.
+* Hierarchy: the level-q cell of node (ix, iy) is (ix, iy) in a 2^q x 2^q
+  lattice (q = log2 n); its level-k cell is (ix >> (q-k), iy >> (q-k)).
+  Level k < q lattices are full; at level q the cells with ix = 0 or
+  iy = 0 hold no node.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.sparse as sp
+
+# Bilinear element stiffness on a square, corners (0,0),(1,0),(1,1),(0,1).
+K_REF = np.array(
+    [[4.0, -1.0, -2.0, -1.0],
+     [-1.0, 4.0, -1.0, -2.0],
+     [-2.0, -1.0, 4.0, -1.0],
+     [-1.0, -2.0, -1.0, 4.0]]) / 6.0
+
+
+@dataclasses.dataclass
+class Problem:
+    n: int                 # cells per side
+    q: int                 # number of levels
+    log_a: np.ndarray      # (n, n) log coefficient, indexed [cy, cx]
+    A: sp.csr_matrix       # (n-1)^2 x (n-1)^2 fine stiffness (float64)
+    g: np.ndarray          # (n-1)^2 right-hand side
+    cells: np.ndarray      # (n-1)^2 x 2 int32 level-q lattice cells (x, y)
+
+    @property
+    def ndof(self) -> int:
+        return self.A.shape[0]
+
+
+def rough_log_coefficient(n: int, scales: int, contrast: float,
+                          rng: np.random.Generator) -> np.ndarray:
+    """log a on an n x n cell grid, sum of `scales` dyadic piecewise-constant
+    layers with amplitude ln(contrast)/scales each."""
+    q = int(round(np.log2(n)))
+    assert 1 << q == n, "n must be a power of two"
+    assert scales <= q
+    amp = np.log(contrast) / scales
+    log_a = np.zeros((n, n))
+    cy, cx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    for s in range(1, scales + 1):
+        u = rng.random(4 ** s).reshape(1 << s, 1 << s)  # [sy, sx]
+        xi = (u - 0.5) * amp
+        log_a += xi[cy >> (q - s), cx >> (q - s)]
+    return log_a
+
+
+def interior_cells(n: int) -> np.ndarray:
+    """Level-q lattice cells (x, y) of the interior nodes, dof order."""
+    iy, ix = np.meshgrid(np.arange(1, n), np.arange(1, n), indexing="ij")
+    return np.stack([ix.ravel(), iy.ravel()], axis=1).astype(np.int32)
+
+
+def assemble_q1(a: np.ndarray) -> sp.csr_matrix:
+    """Q1 stiffness matrix for a cellwise coefficient a[cy, cx] on an
+    n x n grid, interior nodes only, row-major dof numbering."""
+    n = a.shape[0]
+    m = n - 1
+    cy, cx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    cy = cy.ravel()
+    cx = cx.ravel()
+    av = a.ravel()
+    # corner nodes counter-clockwise
+    corners = [(cx, cy), (cx + 1, cy), (cx + 1, cy + 1), (cx, cy + 1)]
+    rows, cols, vals = [], [], []
+    for p in range(4):
+        xp, yp = corners[p]
+        inp = (xp >= 1) & (xp <= m) & (yp >= 1) & (yp <= m)
+        for r in range(4):
+            xr, yr = corners[r]
+            inr = (xr >= 1) & (xr <= m) & (yr >= 1) & (yr <= m)
+            keep = inp & inr
+            rows.append((yp[keep] - 1) * m + (xp[keep] - 1))
+            cols.append((yr[keep] - 1) * m + (xr[keep] - 1))
+            vals.append(av[keep] * K_REF[p, r])
+    A = sp.coo_matrix((np.concatenate(vals),
+                       (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(m * m, m * m)).tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    return A
+
+
+def make_problem(n: int, contrast: float, seed: int,
+                 scales: int | None = None) -> Problem:
+    """Rough-coefficient problem: coefficient then g from one generator."""
+    q = int(round(np.log2(n)))
+    scales = q if scales is None else scales
+    rng = np.random.default_rng(seed)
+    log_a = rough_log_coefficient(n, scales, contrast, rng)
+    g = rng.standard_normal((n - 1) * (n - 1))
+    A = assemble_q1(np.exp(log_a))
+    return Problem(n=n, q=q, log_a=log_a, A=A, g=g, cells=interior_cells(n))
+
+
+def example1_coefficient(q: int = 6) -> np.ndarray:
+    """Coefficient of the paper's Example 1 (Section 5.1) on the
+    (2^q+1) x (2^q+1) cell grid, indexed [j, i] for the cell
+    [i/(2^q+1), (i+1)/(2^q+1)) x [j/(2^q+1), (j+1)/(2^q+1))."""
+    n = (1 << q) + 1
+    j, i = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    x = i / n
+    y = j / n
+    a = np.ones((n, n))
+    for k in range(1, 7):
+        a *= (1 + 0.5 * np.cos(2 ** k * np.pi * (x + y))) * \
+             (1 + 0.5 * np.sin(2 ** k * np.pi * (y - 3 * x)))
+    return a
+
+
+def example1_rhs(q: int = 6) -> np.ndarray:
+    """Nodal values of g for Example 1 at interior nodes z = (i, j)/(2^q+1),
+    row-major over (j, i)."""
+    n = (1 << q) + 1
+    j, i = np.meshgrid(np.arange(1, n), np.arange(1, n), indexing="ij")
+    z1 = (i / n).ravel()
+    z2 = (j / n).ravel()
+    return np.cos(3 * z1 + z2) + np.sin(3 * z2) + np.sin(7 * z1 - 5 * z2)
