@@ -1,0 +1,195 @@
+/*
+ * gamblet.h - C ABI of the GB300 gamblet multiresolution solver.
+ *
+ * Problem (Sec. 5.1, discrete system (eqhuiuhiuhuiu)): given the fine
+ * stiffness matrix A = A^(q) of -div(a grad u) = g (symmetric positive
+ * definite, CSR) and a nested dyadic measurement hierarchy, compute the
+ * gamblet transform (Sec. 4, Algorithms 1 and 2 of Sec. 5) and the solution
+ * u of A u = g as the sum of its level components (Theorem thmgugyug2).
+ *
+ * Hierarchy (Sec. 4.1, Definition defindextree / Construction defmulires,
+ * H = 1/2): every fine unknown i carries a level-q lattice cell
+ * (x_i, y_i), 0 <= x_i, y_i < 2^q, all distinct.  The level-k subdomain of i
+ * is the cell (x_i >> (q-k), y_i >> (q-k)); I^(k) is the set of non-empty
+ * level-k cells, pi^(k-1,k) aggregates children into parents
+ * (Eq. eq:eigdeiud3dd).  Each level-(k-1) cell has m <= 4 children.  The
+ * detail basis W^(k) is Construction const2 (Sec. 4.6: normalised rows of
+ * U^(m), Lemma const0; children ordered row-major by (y & 1, x & 1)).
+ *
+ * Pointers: every array argument may be host memory (pageable or pinned) or
+ * device memory of the current CUDA device; the library tells them apart with
+ * cudaPointerGetAttributes and copies as needed.  The caller owns all input
+ * and output buffers; the handle owns every device buffer of the hierarchy.
+ *
+ * Errors: every function returns a gamblet_status.  No call aborts or
+ * throws; gamblet_last_error() returns a thread-local message describing the
+ * last failure.  A handle whose call failed with GAMBLET_ERR_CUDA should be
+ * destroyed.
+ *
+ * Streams: work is issued on opts.stream (a cudaStream_t, 0 = legacy
+ * default stream).  gamblet_setup and gamblet_solve return after their
+ * results are complete (they synchronise that stream once at the end).
+ */
+#ifndef GAMBLET_H
+#define GAMBLET_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GAMBLET_API __attribute__((visibility("default")))
+#else
+#define GAMBLET_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GAMBLET_OK = 0,
+  GAMBLET_ERR_INVALID_ARG = 1,     /* bad size, pointer, layout or option   */
+  GAMBLET_ERR_NOT_SPD = 2,         /* non-positive pivot in a Cholesky      */
+  GAMBLET_ERR_NOT_CONVERGED = 3,   /* iteration cap hit; result still written */
+  GAMBLET_ERR_CUDA = 4,            /* CUDA runtime error                    */
+  GAMBLET_ERR_OUT_OF_MEMORY = 5,   /* device allocation failed              */
+  GAMBLET_ERR_UNSUPPORTED = 6      /* valid input outside this build's limits */
+} gamblet_status;
+
+/* Square sparse matrix in CSR form with 0-based int32 indices. */
+typedef struct {
+  int32_t n;               /* rows = columns                                */
+  int64_t nnz;             /* number of stored entries                      */
+  const int32_t* rowptr;   /* n + 1 offsets                                 */
+  const int32_t* colind;   /* nnz column indices                            */
+  const double* val;       /* nnz values                                    */
+} gamblet_csr;
+
+typedef enum {
+  GAMBLET_FP64 = 0,   /* every stage in float64                              */
+  GAMBLET_MIXED = 1   /* patch factorisations, Galerkin products and level
+                         matrix-vector products in float32 with float32
+                         accumulation; dots, residuals, the coarsest solve and
+                         the outer refinement in float64                     */
+} gamblet_precision;
+
+typedef struct {
+  /* Localization radius rho (Sec. 4.10 / Definition defb), in level-(k-1)
+   * cells.  rho <= 0 selects the exact, non-localized transform of
+   * Algorithm 1 (dense levels; small problems only).                        */
+  double rho;
+  /* Neighbourhood rule for i^rho: 0 = Euclidean distance between closed
+   * squares <= rho (the paper's rule), 1 = Chebyshev box max(|dx|,|dy|)<=rho. */
+  int32_t nbr_rule;
+  int32_t precision;        /* gamblet_precision                           */
+  double level_tol;         /* relative residual target of each level CG   */
+  int32_t level_max_iter;   /* iteration cap of each level CG              */
+  double refine_tol;        /* outer float64 relative residual target      */
+  int32_t refine_max_iter;  /* cap on outer flexible-CG iterations; 0 = the
+                               one-pass transform of Algorithm 2 only      */
+  int32_t use_graph;        /* capture repeated launch sequences in CUDA graphs */
+  void* stream;             /* cudaStream_t                                */
+} gamblet_opts;
+
+typedef struct {
+  int32_t status;           /* gamblet_status of the call                   */
+  int32_t q;                /* number of levels                             */
+  int32_t outer_iters;      /* outer float64 iterations performed           */
+  int32_t level_iters[32];  /* level CG iterations summed over the call, [k] */
+  double rel_residual;      /* |g - A u|_2 / |g|_2 in float64 at exit       */
+  double setup_ms;          /* device time of the last gamblet_setup        */
+  double solve_ms;          /* device time of this call                     */
+} gamblet_info;
+
+typedef struct gamblet_ctx* gamblet_handle;
+
+/* Fill *opts with defaults: rho = 3, Euclidean rule, FP64, level_tol 1e-8,
+ * level_max_iter 1000, refine_tol 1e-13, refine_max_iter 50, graphs on,
+ * default stream. */
+GAMBLET_API void gamblet_default_opts(gamblet_opts* opts);
+
+/*
+ * Fine-to-coarse setup (Algorithm 1 lines 7-15 for rho <= 0, Algorithm 2
+ * lines 7-15 with Definition defb otherwise), with psi^(q) = phi (the
+ * initialisation described after Algorithm 1 in Sec. 5.2: A^(q) = A).
+ *   A      fine stiffness, symmetric positive definite; A->n = number of
+ *          fine unknowns (>= 1).  Entries may couple only cells within the
+ *          same or adjacent level-(q-1) cells' stencil reach (any sparse
+ *          pattern; the stored pattern must be symmetric).
+ *   q      number of levels, 2 <= q <= 15.
+ *   cells  n x 2 int32, row-major: cells[2 i] = x_i, cells[2 i + 1] = y_i.
+ *   opts   options (NULL = defaults).
+ *   out    receives the handle.
+ * Returns INVALID_ARG for malformed input (duplicate or out-of-range cells,
+ * bad CSR), NOT_SPD if a factorisation meets a non-positive pivot,
+ * UNSUPPORTED if a patch exceeds the on-chip capacity of this build.
+ */
+GAMBLET_API gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cells,
+                             const gamblet_opts* opts, gamblet_handle* out);
+
+/*
+ * Solve A u = g (Eqs. eqyguugy6t, eqsdjoejddi1, eqsdjoejddi2, Theorem
+ * thddwedmgugyug): restrict g through the levels, solve the independent
+ * level systems B^(k) w^(k) = W^(k) g^(k) by CG and A^(1) U^(1) = g^(1)
+ * directly, prolongate and sum.  With refine_max_iter > 0 this gamblet
+ * operator preconditions a float64 flexible CG on A^(q) (Sec. 5.4: use as a
+ * preconditioner) until |g - A u| <= refine_tol |g|.
+ *   g           n float64 right-hand side.
+ *   u           n float64 output.
+ *   components  NULL, or q x n float64 output: row 0 = u^(1), row k-1 =
+ *               u^(k) - u^(k-1) in fine coordinates (one-pass transform of
+ *               g; their sum is the one-pass solution).
+ *   info        NULL or receives iteration counts and residuals.
+ * Returns NOT_CONVERGED (u still written) if a cap was hit.
+ */
+GAMBLET_API gamblet_status gamblet_solve(gamblet_handle h, const double* g, double* u,
+                             double* components, gamblet_info* info);
+
+/*
+ * Adjoint gradient of J = 1/2 |u - u_obs|^2 with respect to theta_c =
+ * log a_c for a cellwise-constant coefficient (the paper has no adjoint; the
+ * discrete adjoint of A(theta) u = g):  A lambda = u - u_obs is solved with
+ * the same hierarchy as gamblet_solve, then
+ *   dJ/dtheta_c = -a_c sum_{p,r} lambda_{cell_nodes[4c+p]} K_ref[4p+r] u_{cell_nodes[4c+r]}
+ * over the cell's corners (entries -1 = Dirichlet corner, skipped).
+ *   ncell       number of cells.
+ *   cell_nodes  ncell x 4 int32 fine unknown of each corner, or -1.
+ *   cell_a      ncell float64 coefficient a_c.
+ *   K_ref       4 x 4 float64 reference element matrix (row-major).
+ *   u, u_obs    n float64: the current solution and the observation.
+ *   dJ          ncell float64 output.
+ *   J           NULL or receives J.
+ */
+GAMBLET_API gamblet_status gamblet_grad(gamblet_handle h, int32_t ncell, const int32_t* cell_nodes,
+                            const double* cell_a, const double* K_ref, const double* u,
+                            const double* u_obs, double* dJ, double* J, gamblet_info* info);
+
+/* Number of nodes n_k = |I^(k)| and detail rows |J^(k)| at level k. */
+GAMBLET_API gamblet_status gamblet_level_size(gamblet_handle h, int32_t k, int32_t* n_k, int32_t* nJ_k);
+
+/*
+ * Copy one level operator to caller memory as COO triplets in the oracle's
+ * index order (level q: the caller's unknown order; level k < q: cells
+ * sorted row-major by (y, x); J^(k): by parent, then t = 1..m-1).
+ *   which  0 = A^(k) (n_k x n_k), 1 = R^(k-1,k) (n_{k-1} x n_k, k >= 2),
+ *          2 = B^(k) (|J^(k)| x |J^(k)|, k >= 2).
+ *   capacity  size of rows/cols/vals; *nnz receives the count.  Call with
+ *          capacity 0 to query the count.  Entries that are structurally
+ *          present but zero may be included.
+ */
+GAMBLET_API gamblet_status gamblet_get_operator(gamblet_handle h, int32_t which, int32_t k, int64_t capacity,
+                                    int64_t* nnz, int32_t* rows, int32_t* cols, double* vals);
+
+/* Device bytes held by the handle. */
+GAMBLET_API int64_t gamblet_device_bytes(gamblet_handle h);
+
+/* Release every resource of the handle (NULL is ignored). */
+GAMBLET_API void gamblet_destroy(gamblet_handle h);
+
+GAMBLET_API const char* gamblet_status_string(int32_t status);
+GAMBLET_API const char* gamblet_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAMBLET_H */

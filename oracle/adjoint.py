@@ -12,22 +12,9 @@ from __future__ import annotations
 
 import numpy as np
 
+from workloads import cell_corner_dofs
+
 from . import direct
-
-
-def cell_corner_dofs(n):
-    """(n*n) x 4 fine dof index of each cell corner (counter-clockwise from
-    (cx, cy)), -1 on the Dirichlet boundary; cells in row-major (cy, cx)."""
-    m = n - 1
-    cy, cx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
-    cy = cy.ravel()
-    cx = cx.ravel()
-    out = np.full((n * n, 4), -1, dtype=np.int64)
-    for p, (xp, yp) in enumerate([(cx, cy), (cx + 1, cy),
-                                  (cx + 1, cy + 1), (cx, cy + 1)]):
-        ok = (xp >= 1) & (xp <= m) & (yp >= 1) & (yp <= m)
-        out[ok, p] = (yp[ok] - 1) * m + (xp[ok] - 1)
-    return out
 
 
 def contract(n, a, lam, u, K_ref):

@@ -1,0 +1,150 @@
+// galerkin.cu - Galerkin coarsening A^(k-1) = R^(k-1,k) A^(k) R^(k,k-1)
+// (Theorem thmhggfees5, Eq. eqhuhiuv; Algorithm 2, line 13).
+//
+// Everything is evaluated in the transformed basis: with Rhat = R Q^T and
+// Ahat = Q A^(k) Q^T (Q block-orthonormal), R A R^T = Rhat Ahat Rhat^T.
+// For a coarse cell i the row Rhat_i lives on the patch i + N_j; the product
+// t_i = Ahat Rhat_i^T lives on the window i + WIN_w (WIN = N + O_k), and
+//   A^(k-1)_{i, i+S_d} = Rhat_{i+S_d} . t_i   (WIN_w = S_d + N_j).
+// The index lists (j, o) per window position and (j, w) per output offset
+// are built once per level on the host from the offset sets.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace gb {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_galerkin(const T* __restrict__ Ahat,
+                                                  const T* __restrict__ Rhat,
+                                                  const uint32_t* __restrict__ pmask,
+                                                  GalerkinGeom g, T* __restrict__ Aout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* rrow = reinterpret_cast<T*>(smem_raw);
+  T* t = rrow + 4 * g.NB;
+  const int64_t nrow = g.nrow;
+  for (int64_t i = blockIdx.x; i < nrow; i += gridDim.x) {
+    if ((pmask[i] & 15u) == 0) {
+      for (int d = threadIdx.x; d < g.nout; d += blockDim.x) Aout[(int64_t)d * nrow + i] = T(0);
+      continue;
+    }
+    int xi, yi;
+    demorton((uint32_t)i, xi, yi);
+    for (int idx = threadIdx.x; idx < 4 * g.NB; idx += blockDim.x)
+      rrow[idx] = Rhat[(int64_t)idx * nrow + i];
+    __syncthreads();
+    // t_i = Ahat Rhat_i^T on the window
+    for (int w = threadIdx.x; w < g.nwin; w += blockDim.x) {
+      T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+      const int p = shift_cell(xi, yi, g.win[w].x, g.win[w].y, g.Lpar);
+      if (p >= 0) {
+        for (int e = g.l1_ptr[w]; e < g.l1_ptr[w + 1]; ++e) {
+          const int2 jo = g.l1_pairs[e];
+          const T* blk = Ahat + ((int64_t)jo.y * nrow + p) * 16;
+          const T r0 = rrow[4 * jo.x], r1 = rrow[4 * jo.x + 1];
+          const T r2 = rrow[4 * jo.x + 2], r3 = rrow[4 * jo.x + 3];
+          acc0 += blk[0] * r0 + blk[1] * r1 + blk[2] * r2 + blk[3] * r3;
+          acc1 += blk[4] * r0 + blk[5] * r1 + blk[6] * r2 + blk[7] * r3;
+          acc2 += blk[8] * r0 + blk[9] * r1 + blk[10] * r2 + blk[11] * r3;
+          acc3 += blk[12] * r0 + blk[13] * r1 + blk[14] * r2 + blk[15] * r3;
+        }
+      }
+      t[4 * w] = acc0;
+      t[4 * w + 1] = acc1;
+      t[4 * w + 2] = acc2;
+      t[4 * w + 3] = acc3;
+    }
+    __syncthreads();
+    // A_{i, i+S_d} = Rhat_{i+S_d} . t_i
+    for (int d = threadIdx.x; d < g.nout; d += blockDim.x) {
+      T acc = 0;
+      const int ip = shift_cell(xi, yi, g.out[d].x, g.out[d].y, g.Lpar);
+      if (ip >= 0 && (pmask[ip] & 15u)) {
+        for (int e = g.l2_ptr[d]; e < g.l2_ptr[d + 1]; ++e) {
+          const int2 jw = g.l2_pairs[e];
+          const T* tw = t + 4 * jw.y;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc += Rhat[(int64_t)(4 * jw.x + c) * nrow + ip] * tw[c];
+        }
+      }
+      Aout[(int64_t)d * nrow + i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_galerkin(const T* Ahat, const T* Rhat, const uint32_t* pmask_k, GalerkinGeom g,
+                     T* Aout, cudaStream_t s) {
+  if (g.nrow <= 0) return;
+  size_t smem = sizeof(T) * 4 * ((size_t)g.NB + (size_t)g.nwin);
+  cudaFuncSetAttribute(k_galerkin<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int64_t grid = g.nrow < 65535 * 16 ? g.nrow : 65535 * 16;
+  k_galerkin<T><<<(unsigned)grid, 256, smem, s>>>(Ahat, Rhat, pmask_k, g, Aout);
+}
+template void launch_galerkin<float>(const float*, const float*, const uint32_t*, GalerkinGeom,
+                                     float*, cudaStream_t);
+template void launch_galerkin<double>(const double*, const double*, const uint32_t*,
+                                      GalerkinGeom, double*, cudaStream_t);
+
+// Cell stencil of level k-1 -> transformed block stencil of level k-1.
+template <typename T>
+__global__ void k_cells_to_blocks(const T* __restrict__ Acell, int64_t ncell,
+                                  const int* __restrict__ map, int nO,
+                                  const int2* __restrict__ Ooff, int Lpar, int64_t npar,
+                                  const uint32_t* __restrict__ pmask, T* __restrict__ blk) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nO * npar) return;
+  const int o = (int)(t / npar);
+  const int64_t P = t - (int64_t)o * npar;
+  int x, y;
+  demorton((uint32_t)P, x, y);
+  const int PP = shift_cell(x, y, Ooff[o].x, Ooff[o].y, Lpar);
+  const int mr = (int)pmask[P] & 15;
+  const int mc = PP >= 0 ? (int)pmask[PP] & 15 : 0;
+  double M[16], Tm[16], Qr[16], Qc[16];
+  qmat<double>(mr, Qr);
+  qmat<double>(mc, Qc);
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const int d = map[o * 16 + c * 4 + cc];
+      M[c * 4 + cc] = (PP >= 0 && d >= 0) ? (double)Acell[(int64_t)d * ncell + 4 * P + c] : 0.0;
+    }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      double acc = 0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc += Qr[a * 4 + c] * M[c * 4 + cc];
+      Tm[a * 4 + cc] = acc;
+    }
+  T* out = blk + t * 16;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      double acc = 0;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) acc += Tm[a * 4 + cc] * Qc[b * 4 + cc];
+      out[a * 4 + b] = (T)acc;
+    }
+}
+
+template <typename T>
+void launch_cells_to_blocks(const T* Acell, int64_t ncell, const int* map, int nO,
+                            const int2* Ooff, int Lpar, int64_t npar, const uint32_t* pmask,
+                            T* blk, cudaStream_t s) {
+  int64_t n = (int64_t)nO * npar;
+  if (n <= 0) return;
+  k_cells_to_blocks<T><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(Acell, ncell, map, nO, Ooff,
+                                                                   Lpar, npar, pmask, blk);
+}
+template void launch_cells_to_blocks<float>(const float*, int64_t, const int*, int, const int2*,
+                                            int, int64_t, const uint32_t*, float*, cudaStream_t);
+template void launch_cells_to_blocks<double>(const double*, int64_t, const int*, int,
+                                             const int2*, int, int64_t, const uint32_t*, double*,
+                                             cudaStream_t);
+
+}  // namespace gb

@@ -1,0 +1,1332 @@
+// gamblet.cu - host orchestration behind the C ABI of include/gamblet.h.
+//
+// Setup (Algorithm 2 of Sec. 5.3 for rho > 0, Algorithm 1 of Sec. 5.2 for
+// rho <= 0), fine to coarse, k = q..2:
+//   import A^(q) -> transformed block stencil Ahat^(q) = Q A Q^T
+//   patch solves (Definition defb)            -> Rhat^(k-1,k)
+//   Galerkin product R A R^T (Eq. eqhuhiuv)   -> A^(k-1) -> Ahat^(k-1)
+// Solve: restriction chain, all level CGs batched in one launch sequence,
+// coarsest Cholesky, prolongation and summation; optionally as the
+// preconditioner of a float64 flexible CG on A^(q).
+//
+// Host work is limited to symbolic offset sets (a few thousand integers per
+// level), launch sequencing and one read-back per outer iteration / CG chunk.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/gamblet.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace gb {
+// declared in dense.cu / solve.cu
+void launch_dense_transform(const double* in, int64_t npar, const uint32_t* pmask, double* out,
+                            cudaStream_t s);
+}  // namespace gb
+
+using namespace gb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct GbError {
+  gamblet_status st;
+  std::string msg;
+};
+
+[[noreturn]] void fail(gamblet_status st, const std::string& msg) { throw GbError{st, msg}; }
+
+#define CK(x)                                                                           \
+  do {                                                                                  \
+    cudaError_t e_ = (x);                                                               \
+    if (e_ != cudaSuccess) {                                                            \
+      if (e_ == cudaErrorMemoryAllocation)                                              \
+        fail(GAMBLET_ERR_OUT_OF_MEMORY, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+      fail(GAMBLET_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_));          \
+    }                                                                                   \
+  } while (0)
+
+// ---------------------------------------------------------------- device memory
+struct Pool {
+  std::vector<void*> ptrs;
+  int64_t bytes = 0;
+  template <typename T>
+  T* alloc(int64_t n) {
+    if (n <= 0) n = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * (size_t)n);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(GAMBLET_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(sizeof(T) * n) + " bytes");
+    }
+    ptrs.push_back(p);
+    bytes += (int64_t)sizeof(T) * n;
+    return static_cast<T*>(p);
+  }
+  template <typename T>
+  T* zeros(int64_t n, cudaStream_t s) {
+    T* p = alloc<T>(n);
+    CK(cudaMemsetAsync(p, 0, sizeof(T) * (size_t)std::max<int64_t>(n, 1), s));
+    return p;
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v, cudaStream_t s) {
+    T* p = alloc<T>((int64_t)v.size());
+    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
+    return p;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+  ~Pool() { release(); }
+};
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy n elements from caller memory (host or device) into a device buffer.
+template <typename T>
+void to_device(Pool& pool, T*& dst, const T* src, int64_t n, cudaStream_t s) {
+  if (!dst) dst = pool.alloc<T>(n);
+  if (n > 0) CK(cudaMemcpyAsync(dst, src, sizeof(T) * (size_t)n, cudaMemcpyDefault, s));
+}
+
+// ---------------------------------------------------------------- offset sets
+using Off = std::pair<int, int>;  // (dx, dy)
+
+struct OffSet {
+  std::vector<int2> v;
+  std::map<Off, int> idx;
+  void add(int dx, int dy) {
+    Off k{dx, dy};
+    if (idx.count(k)) return;
+    idx[k] = (int)v.size();
+    v.push_back(make_int2(dx, dy));
+  }
+  int find(int dx, int dy) const {
+    auto it = idx.find(Off{dx, dy});
+    return it == idx.end() ? -1 : it->second;
+  }
+  int size() const { return (int)v.size(); }
+};
+
+// i^rho offsets of Sec. 4.10 in cell units, row-major (dy, dx).
+OffSet neighbour_offsets(double rho, int rule) {
+  OffSet N;
+  const int R = (int)std::floor(rho) + 1;
+  for (int dy = -R; dy <= R; ++dy)
+    for (int dx = -R; dx <= R; ++dx) {
+      bool ok;
+      if (rule == 0) {
+        const double ex = std::max(std::abs(dx) - 1, 0), ey = std::max(std::abs(dy) - 1, 0);
+        ok = ex * ex + ey * ey <= rho * rho * (1 + 1e-12);
+      } else {
+        ok = std::max(std::abs(dx), std::abs(dy)) <= rho + 1e-12;
+      }
+      if (ok) N.add(dx, dy);
+    }
+  return N;
+}
+
+// Symbolic data of one localized level k (patch, Galerkin, conversion).
+struct SymLevel {
+  OffSet O;                       // block offsets of Ahat^(k) (level k-1 cell units)
+  std::vector<int> pair_idx;      // NB x NB
+  OffSet WIN, S;                  // window and output cell offsets
+  std::vector<int> l1_ptr, l2_ptr;
+  std::vector<int2> l1_pairs, l2_pairs;
+  std::vector<int> map_next;      // conversion map to level k-1 blocks (or level-1 map)
+};
+
+// ---------------------------------------------------------------- handle
+struct LevelDev {
+  int k = 0;
+  int L = 0;          // 2^k
+  int64_t ncell = 0;  // 4^k
+  int64_t npar = 0;   // 4^(k-1)
+  std::vector<uint32_t> pmask_h;
+  uint32_t* pmask = nullptr;
+  int n_active = 0, nJ = 0;
+  // localized
+  int2* off = nullptr;
+  int noff = 0;
+  std::vector<int2> off_h;
+  void* Ahat = nullptr;      // T
+  double* Ahat64 = nullptr;  // level q float64 copy (mixed) or alias
+  void* Rhat = nullptr;      // T, rows 4^(k-1)
+  int* pair_idx = nullptr;
+  // exact (dense)
+  double* D = nullptr;       // transformed dense Ahat^(k)
+  double* Bc = nullptr;      // Cholesky factor of B^(k)
+  double* Rh = nullptr;      // dense Rhat (npar x ncell)
+  int32_t* det = nullptr;
+  int32_t* par = nullptr;
+  std::vector<int32_t> det_h, par_h;
+  // solve buffers (T)
+  void* ghat = nullptr;  // ncell
+  void* v = nullptr;     // ncell
+  void* w = nullptr;     // ncell
+  void* cr = nullptr;
+  void* cp = nullptr;
+  void* cAp = nullptr;
+  double* wc = nullptr;  // compact detail vector (exact path)
+};
+
+}  // namespace
+
+struct gamblet_ctx {
+  gamblet_opts opts;
+  cudaStream_t s = nullptr;
+  int q = 0;
+  int n = 0;           // fine unknowns
+  bool exact = false;
+  bool mixed = false;
+  int num_sms = 1;
+  Pool pool;
+  int32_t* morton_of = nullptr;   // n
+  int32_t* unknown_of = nullptr;  // 4^q
+  std::vector<int32_t> morton_of_h;
+  std::vector<LevelDev> lv;       // index k (0 unused)
+  OffSet N;                       // neighbour offsets
+  int jc = 0;
+  int2* nbr = nullptr;
+  // level 1
+  double* A1 = nullptr;      // plain 4 x 4 (copy, for getters)
+  double* A1L = nullptr;     // Cholesky factor
+  void* g1 = nullptr;        // T, 4
+  void* U1 = nullptr;        // T, 4
+  int* l1map = nullptr;
+  // CG batch
+  CgLevel* cg_lv = nullptr;
+  CgScalars* cg_sc = nullptr;
+  int* any_active = nullptr;
+  int* any_active_h = nullptr;  // pinned
+  int cg_blocks = 0;
+  int cg_nlev = 0;
+  // outer
+  double* u64 = nullptr;
+  double* r64 = nullptr;
+  double* z64 = nullptr;
+  double* p64 = nullptr;
+  double* q64 = nullptr;
+  double* g64 = nullptr;
+  void* rT = nullptr;
+  void* zT = nullptr;
+  double* dots = nullptr;
+  double* dots_h = nullptr;  // pinned
+  int* status = nullptr;
+  int* status_h = nullptr;   // pinned
+  double setup_ms = 0;
+  int level_iters_acc[32];
+  bool level_not_conv = false;
+};
+
+namespace {
+
+template <typename T>
+constexpr bool is_f32() {
+  return sizeof(T) == 4;
+}
+
+void check_status(gamblet_ctx* h, const char* where) {
+  CK(cudaMemcpyAsync(h->status_h, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (*h->status_h == DEV_NOT_SPD)
+    fail(GAMBLET_ERR_NOT_SPD, std::string("non-positive pivot in ") + where);
+}
+
+// ------------------------------------------------------------ symbolic build
+SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
+  SymLevel S;
+  S.O = O_k;
+  const int NB = N.size();
+  const int Lpar = 1 << (k - 1);  // level k-1 lattice side
+  S.pair_idx.assign((size_t)NB * NB, -1);
+  for (int a = 0; a < NB; ++a)
+    for (int b = 0; b < NB; ++b)
+      S.pair_idx[(size_t)a * NB + b] = O_k.find(N.v[b].x - N.v[a].x, N.v[b].y - N.v[a].y);
+  // window: positions p' = i + WIN_w reachable from the patch through O_k
+  for (int j = 0; j < NB; ++j)
+    for (const int2& o : O_k.v) {
+      const int wx = N.v[j].x - o.x, wy = N.v[j].y - o.y;  // row parent p' with p - p' = o
+      if (std::abs(wx) <= Lpar - 1 && std::abs(wy) <= Lpar - 1) S.WIN.add(wx, wy);
+    }
+  S.l1_ptr.assign(S.WIN.size() + 1, 0);
+  std::vector<std::vector<int2>> l1(S.WIN.size());
+  for (int j = 0; j < NB; ++j)
+    for (int o = 0; o < O_k.size(); ++o) {
+      const int w = S.WIN.find(N.v[j].x - O_k.v[o].x, N.v[j].y - O_k.v[o].y);
+      if (w >= 0) l1[w].push_back(make_int2(j, o));
+    }
+  for (int w = 0; w < S.WIN.size(); ++w) {
+    S.l1_ptr[w + 1] = S.l1_ptr[w] + (int)l1[w].size();
+    S.l1_pairs.insert(S.l1_pairs.end(), l1[w].begin(), l1[w].end());
+  }
+  // outputs d with WIN_w = d + N_j
+  for (int w = 0; w < S.WIN.size(); ++w)
+    for (int j = 0; j < NB; ++j) {
+      const int dx = S.WIN.v[w].x - N.v[j].x, dy = S.WIN.v[w].y - N.v[j].y;
+      if (std::abs(dx) <= Lpar - 1 && std::abs(dy) <= Lpar - 1) S.S.add(dx, dy);
+    }
+  std::vector<std::vector<int2>> l2(S.S.size());
+  for (int d = 0; d < S.S.size(); ++d)
+    for (int j = 0; j < NB; ++j) {
+      const int w = S.WIN.find(S.S.v[d].x + N.v[j].x, S.S.v[d].y + N.v[j].y);
+      if (w >= 0) l2[d].push_back(make_int2(j, w));
+    }
+  S.l2_ptr.assign(S.S.size() + 1, 0);
+  for (int d = 0; d < S.S.size(); ++d) {
+    S.l2_ptr[d + 1] = S.l2_ptr[d] + (int)l2[d].size();
+    S.l2_pairs.insert(S.l2_pairs.end(), l2[d].begin(), l2[d].end());
+  }
+  return S;
+}
+
+// Block offsets of level k-1 (level k-2 cell units) from the level k-1 cell
+// offsets S, and the conversion map [o][c*4+c'].
+OffSet blocks_from_cells(const OffSet& S, int km1, std::vector<int>& map) {
+  OffSet O;
+  const int Lp = 1 << (km1 - 1);
+  for (const int2& d : S.v)
+    for (int c = 0; c < 4; ++c)
+      for (int cc = 0; cc < 4; ++cc) {
+        const int ex = d.x - ((cc & 1) - (c & 1)), ey = d.y - ((cc >> 1) - (c >> 1));
+        if ((ex & 1) || (ey & 1)) continue;
+        const int Dx = ex / 2, Dy = ey / 2;
+        if (std::abs(Dx) <= Lp - 1 && std::abs(Dy) <= Lp - 1) O.add(Dx, Dy);
+      }
+  map.assign((size_t)O.size() * 16, -1);
+  for (int o = 0; o < O.size(); ++o)
+    for (int c = 0; c < 4; ++c)
+      for (int cc = 0; cc < 4; ++cc)
+        map[(size_t)o * 16 + c * 4 + cc] =
+            S.find(2 * O.v[o].x + (cc & 1) - (c & 1), 2 * O.v[o].y + (cc >> 1) - (c >> 1));
+  return O;
+}
+
+// ------------------------------------------------------------ hierarchy
+void build_hierarchy(gamblet_ctx* h, const int32_t* cells_user) {
+  const int q = h->q;
+  cudaStream_t s = h->s;
+  Pool& P = h->pool;
+  h->lv.assign(q + 1, LevelDev());
+  for (int k = 1; k <= q; ++k) {
+    LevelDev& L = h->lv[k];
+    L.k = k;
+    L.L = 1 << k;
+    L.ncell = (int64_t)1 << (2 * k);
+    L.npar = (int64_t)1 << (2 * (k - 1));
+    L.pmask = P.zeros<uint32_t>(L.npar, s);
+  }
+  int32_t* cells = nullptr;
+  to_device(P, cells, cells_user, 2 * (int64_t)h->n, s);
+  h->morton_of = P.alloc<int32_t>(h->n);
+  h->unknown_of = P.alloc<int32_t>(h->lv[q].ncell);
+  CK(cudaMemsetAsync(h->unknown_of, 0xff, sizeof(int32_t) * h->lv[q].ncell, s));
+  int* flag = P.zeros<int>(4, s);
+  launch_cells_to_morton(cells, h->n, q, h->morton_of, h->unknown_of, h->lv[q].pmask, flag, s);
+  for (int k = q; k >= 2; --k)
+    launch_coarsen_masks(h->lv[k].pmask, h->lv[k].npar, h->lv[k - 1].pmask, s);
+  CK(cudaGetLastError());
+  int flag_h[4];
+  CK(cudaMemcpyAsync(flag_h, flag, sizeof(flag_h), cudaMemcpyDeviceToHost, s));
+  for (int k = 1; k <= q; ++k) {
+    h->lv[k].pmask_h.resize(h->lv[k].npar);
+    CK(cudaMemcpyAsync(h->lv[k].pmask_h.data(), h->lv[k].pmask, sizeof(uint32_t) * h->lv[k].npar,
+                       cudaMemcpyDeviceToHost, s));
+  }
+  h->morton_of_h.resize(h->n);
+  CK(cudaMemcpyAsync(h->morton_of_h.data(), h->morton_of, sizeof(int32_t) * h->n,
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (flag_h[0] == 2) fail(GAMBLET_ERR_INVALID_ARG, "a cell lies outside [0, 2^q)");
+  if (flag_h[0] == 1) fail(GAMBLET_ERR_INVALID_ARG, "two unknowns share a level-q cell");
+  for (int k = 1; k <= q; ++k) {
+    LevelDev& L = h->lv[k];
+    int na = 0, nJ = 0;
+    for (uint32_t m : L.pmask_h) {
+      const int c = __builtin_popcount(m & 15u);
+      na += c;
+      nJ += c > 0 ? c - 1 : 0;
+    }
+    L.n_active = na;
+    L.nJ = nJ;
+  }
+}
+
+// Fine CSR -> transformed block stencil of level q (float64).
+void import_fine(gamblet_ctx* h, const gamblet_csr* A) {
+  cudaStream_t s = h->s;
+  Pool& P = h->pool;
+  const int n = h->n;
+  int32_t* rowptr = nullptr;
+  int32_t* colind = nullptr;
+  double* val = nullptr;
+  to_device(P, rowptr, A->rowptr, (int64_t)n + 1, s);
+  int32_t rp_last[2];
+  CK(cudaMemcpyAsync(rp_last, rowptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(rp_last + 1, rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (rp_last[0] != 0 || (int64_t)rp_last[1] != A->nnz)
+    fail(GAMBLET_ERR_INVALID_ARG, "rowptr[0] must be 0 and rowptr[n] must equal nnz");
+  to_device(P, colind, A->colind, A->nnz, s);
+  to_device(P, val, A->val, A->nnz, s);
+  int* ext = P.zeros<int>(4, s);
+  launch_csr_offset_extent(n, rowptr, colind, h->morton_of, ext, ext + 2, s);
+  CK(cudaGetLastError());
+  int ext_h[4];
+  CK(cudaMemcpyAsync(ext_h, ext, sizeof(ext_h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (ext_h[2]) fail(GAMBLET_ERR_INVALID_ARG, "CSR column index out of range or rowptr decreasing");
+  const int q = h->q;
+  LevelDev& L = h->lv[q];
+  const int Lpar = 1 << (q - 1);
+  const int rx = std::min(ext_h[0], Lpar - 1), ry = std::min(ext_h[1], Lpar - 1);
+  L.off_h.clear();
+  for (int dy = -ry; dy <= ry; ++dy)
+    for (int dx = -rx; dx <= rx; ++dx) L.off_h.push_back(make_int2(dx, dy));
+  L.noff = (int)L.off_h.size();
+  L.off = P.upload(L.off_h, s);
+  double* blk = P.zeros<double>((int64_t)L.noff * L.npar * 16, s);
+  launch_csr_to_blocks(n, rowptr, colind, val, h->morton_of, rx, ry, L.npar, blk, s);
+  launch_transform_blocks(blk, L.off, L.noff, L.npar, Lpar, L.pmask, s);
+  CK(cudaGetLastError());
+  L.Ahat64 = blk;
+}
+
+// ------------------------------------------------------------ localized setup
+template <typename T>
+void setup_local(gamblet_ctx* h) {
+  cudaStream_t s = h->s;
+  Pool& P = h->pool;
+  const int q = h->q;
+  const int NB = h->N.size();
+  if ((size_t)patch_smem_bytes<T>(NB) > 227 * 1024)
+    fail(GAMBLET_ERR_UNSUPPORTED, "patch of " + std::to_string(3 * NB) +
+                                      " unknowns exceeds on-chip capacity; lower rho");
+  // level q values in T
+  {
+    LevelDev& L = h->lv[q];
+    const int64_t nv = (int64_t)L.noff * L.npar * 16;
+    if (is_f32<T>()) {
+      float* a32 = P.alloc<float>(nv);
+      launch_convert_f64_f32(L.Ahat64, a32, nv, s);
+      L.Ahat = a32;
+    } else {
+      L.Ahat = L.Ahat64;
+    }
+  }
+  OffSet O = OffSet();
+  for (const int2& o : h->lv[q].off_h) O.add(o.x, o.y);
+  for (int k = q; k >= 2; --k) {
+    LevelDev& L = h->lv[k];
+    SymLevel S = build_sym(O, h->N, k);
+    const int Lpar = 1 << (k - 1);
+    L.pair_idx = P.upload(S.pair_idx, s);
+    // patch solves -> Rhat^(k-1,k)
+    T* Rhat = P.alloc<T>((int64_t)NB * 4 * L.npar);
+    PatchGeom pg{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar};
+    launch_patch_solve<T>((const T*)L.Ahat, L.pmask, pg, Rhat, h->status, h->num_sms, s);
+    CK(cudaGetLastError());
+    L.Rhat = Rhat;
+    // Galerkin product -> level k-1 cell stencil
+    GalerkinGeom gg;
+    gg.NB = NB;
+    gg.nbr = h->nbr;
+    gg.nwin = S.WIN.size();
+    gg.win = P.upload(S.WIN.v, s);
+    gg.l1_ptr = P.upload(S.l1_ptr, s);
+    gg.l1_pairs = P.upload(S.l1_pairs, s);
+    gg.nout = S.S.size();
+    gg.out = P.upload(S.S.v, s);
+    gg.l2_ptr = P.upload(S.l2_ptr, s);
+    gg.l2_pairs = P.upload(S.l2_pairs, s);
+    gg.Lpar = Lpar;
+    gg.nrow = L.npar;
+    if (sizeof(T) * 4 * ((size_t)NB + (size_t)gg.nwin) > 227 * 1024)
+      fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin window exceeds shared memory");
+    T* Acell = P.alloc<T>((int64_t)gg.nout * L.npar);
+    launch_galerkin<T>((const T*)L.Ahat, Rhat, L.pmask, gg, Acell, s);
+    CK(cudaGetLastError());
+    if (k - 1 >= 2) {
+      LevelDev& Ln = h->lv[k - 1];
+      std::vector<int> map;
+      OffSet On = blocks_from_cells(S.S, k - 1, map);
+      Ln.off_h = On.v;
+      Ln.noff = On.size();
+      Ln.off = P.upload(Ln.off_h, s);
+      int* dmap = P.upload(map, s);
+      T* blk = P.alloc<T>((int64_t)Ln.noff * Ln.npar * 16);
+      launch_cells_to_blocks<T>(Acell, L.npar, dmap, Ln.noff, Ln.off, 1 << (k - 2), Ln.npar,
+                                Ln.pmask, blk, s);
+      CK(cudaGetLastError());
+      Ln.Ahat = blk;
+      O = On;
+    } else {
+      std::vector<int> map1(16, -1);
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j)
+          map1[i * 4 + j] = S.S.find((j & 1) - (i & 1), (j >> 1) - (i >> 1));
+      h->l1map = P.upload(map1, s);
+      h->A1L = P.alloc<double>(16);
+      launch_level1_factor<T>(Acell, h->l1map, h->A1L, h->status, s);
+      CK(cudaGetLastError());
+      // keep the level-1 cell stencil for the getter
+      h->lv[1].Ahat = Acell;
+      h->lv[1].noff = S.S.size();
+      h->lv[1].off_h = S.S.v;
+    }
+  }
+}
+
+// ------------------------------------------------------------ exact setup
+void setup_exact(gamblet_ctx* h) {
+  cudaStream_t s = h->s;
+  Pool& P = h->pool;
+  const int q = h->q;
+  // dense level q
+  {
+    LevelDev& L = h->lv[q];
+    L.D = P.zeros<double>(L.ncell * L.ncell, s);
+    launch_dense_from_blocks(L.Ahat64, L.off, L.noff, 1 << (q - 1), L.npar, L.D, s);
+  }
+  for (int k = q; k >= 2; --k) {
+    LevelDev& L = h->lv[k];
+    L.det_h.clear();
+    L.par_h.clear();
+    std::vector<double> scale;
+    for (int64_t p = 0; p < L.npar; ++p) {
+      const int m = __builtin_popcount(L.pmask_h[p] & 15u);
+      for (int t = 0; t < m - 1; ++t) L.det_h.push_back((int32_t)(4 * p + t));
+      if (m > 0) {
+        L.par_h.push_back((int32_t)(4 * p + 3));
+        scale.push_back(-1.0 / std::sqrt((double)m));
+      }
+    }
+    const int nJ = (int)L.det_h.size(), nA = (int)L.par_h.size();
+    L.det = P.upload(L.det_h, s);
+    L.par = P.upload(L.par_h, s);
+    double* dscale = P.upload(scale, s);
+    L.Bc = P.alloc<double>((int64_t)nJ * nJ);
+    double* Y = P.alloc<double>((int64_t)nJ * nA);
+    launch_gather_rows_cols(L.D, (int)L.ncell, L.det, nJ, L.det, nJ, 1.0, nullptr, L.Bc, s);
+    launch_gather_rows_cols(L.D, (int)L.ncell, L.det, nJ, L.par, nA, 1.0, dscale, Y, s);
+    launch_dpotrf(L.Bc, nJ, h->status, s);
+    launch_dpotrs(L.Bc, nJ, Y, nA, s);
+    // parent index (not slot) for the Rhat scatter
+    std::vector<int32_t> pidx;
+    for (int32_t v : L.par_h) pidx.push_back(v >> 2);
+    int32_t* dpidx = P.upload(pidx, s);
+    L.Rh = P.zeros<double>(L.npar * L.ncell, s);
+    launch_dense_rhat(Y, L.det, nJ, dpidx, nA, L.pmask, L.npar, L.Rh, s);
+    double* T1 = P.alloc<double>(L.npar * L.ncell);
+    launch_dgemm((int)L.npar, (int)L.ncell, (int)L.ncell, 1.0, L.Rh, L.D, 0, 0.0, T1, s);
+    double* Ap = P.alloc<double>(L.npar * L.npar);
+    launch_dgemm((int)L.npar, (int)L.npar, (int)L.ncell, 1.0, T1, L.Rh, 1, 0.0, Ap, s);
+    CK(cudaGetLastError());
+    if (k - 1 >= 2) {
+      LevelDev& Ln = h->lv[k - 1];
+      Ln.D = P.alloc<double>(Ln.ncell * Ln.ncell);
+      launch_dense_transform(Ap, Ln.npar, Ln.pmask, Ln.D, s);
+    } else {
+      h->A1 = Ap;
+      h->A1L = P.alloc<double>(16);
+      launch_level1_factor_dense(Ap, h->A1L, h->status, s);
+    }
+    CK(cudaGetLastError());
+  }
+}
+
+// ------------------------------------------------------------ solve buffers
+template <typename T>
+void alloc_solve(gamblet_ctx* h) {
+  Pool& P = h->pool;
+  cudaStream_t s = h->s;
+  const int q = h->q;
+  for (int k = 1; k <= q; ++k) {
+    LevelDev& L = h->lv[k];
+    L.ghat = P.zeros<T>(L.ncell, s);
+    L.v = P.zeros<T>(L.ncell, s);
+    if (k >= 2) {
+      L.w = P.zeros<T>(L.ncell, s);
+      if (!h->exact) {
+        L.cr = P.zeros<T>(L.ncell, s);
+        L.cp = P.zeros<T>(L.ncell, s);
+        L.cAp = P.zeros<T>(L.ncell, s);
+      } else {
+        L.wc = P.zeros<double>(std::max(L.nJ, 1), s);
+      }
+    }
+  }
+  h->g1 = P.zeros<T>(4, s);
+  h->U1 = P.zeros<T>(4, s);
+  const int64_t nq = h->lv[q].ncell;
+  h->u64 = P.zeros<double>(nq, s);
+  h->r64 = P.zeros<double>(nq, s);
+  h->z64 = P.zeros<double>(nq, s);
+  h->p64 = P.zeros<double>(nq, s);
+  h->q64 = P.zeros<double>(nq, s);
+  h->g64 = P.zeros<double>(nq, s);
+  if (is_f32<T>()) {
+    h->rT = P.zeros<T>(nq, s);
+    h->zT = P.zeros<T>(nq, s);
+  }
+  h->dots = P.zeros<double>(8, s);
+  if (!h->exact) {
+    std::vector<CgLevel> cl;
+    int blocks = 0;
+    for (int k = 2; k <= q; ++k) {
+      LevelDev& L = h->lv[k];
+      CgLevel c;
+      c.Ahat = L.Ahat;
+      c.off = L.off;
+      c.noff = L.noff;
+      c.Lpar = 1 << (k - 1);
+      c.npar = L.npar;
+      c.pmask = L.pmask;
+      c.x = L.w;
+      c.r = L.cr;
+      c.p = L.cp;
+      c.Ap = L.cAp;
+      c.b = L.ghat;
+      c.block_begin = blocks;
+      blocks += (int)((L.npar + 255) / 256);
+      cl.push_back(c);
+    }
+    h->cg_nlev = (int)cl.size();
+    h->cg_blocks = blocks;
+    h->cg_lv = P.upload(cl, s);
+    h->cg_sc = P.zeros<CgScalars>(std::max(h->cg_nlev, 1), s);
+    h->any_active = P.zeros<int>(1, s);
+  }
+}
+
+// ------------------------------------------------------------ gamblet operator
+template <typename T>
+void run_level_cg(gamblet_ctx* h) {
+  cudaStream_t s = h->s;
+  if (h->cg_nlev == 0) return;
+  CK(cudaMemsetAsync(h->cg_sc, 0, sizeof(CgScalars) * h->cg_nlev, s));
+  launch_cg_init<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, s);
+  CK(cudaMemsetAsync(h->any_active, 0, sizeof(int), s));
+  launch_cg_start(h->cg_sc, h->cg_nlev, h->any_active, s);
+  const double tol2 = h->opts.level_tol * h->opts.level_tol;
+  const int maxit = std::max(h->opts.level_max_iter, 1);
+  const int chunk = 8;
+  for (int it = 0; it < maxit; it += chunk) {
+    CK(cudaMemsetAsync(h->any_active, 0, sizeof(int), s));
+    for (int c = 0; c < chunk; ++c)
+      launch_cg_iteration<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit,
+                             h->any_active, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->any_active_h, h->any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*h->any_active_h == 0) break;
+  }
+  std::vector<CgScalars> sc(h->cg_nlev);
+  CK(cudaMemcpyAsync(sc.data(), h->cg_sc, sizeof(CgScalars) * h->cg_nlev, cudaMemcpyDeviceToHost,
+                     s));
+  CK(cudaStreamSynchronize(s));
+  for (int l = 0; l < h->cg_nlev; ++l) {
+    h->level_iters_acc[l + 2] += sc[l].iters;
+    if (sc[l].rr > tol2 * sc[l].rr0) h->level_not_conv = true;
+  }
+}
+
+// in: transformed level-q vector (T); out: transformed (inverse_last = 0) or
+// plain (1) level-q vector (T).  in may alias lv[q].ghat.
+template <typename T>
+void apply_G(gamblet_ctx* h, const T* in, T* out, int inverse_last) {
+  cudaStream_t s = h->s;
+  const int q = h->q;
+  const int NB = h->N.size();
+  LevelDev& Lq = h->lv[q];
+  if ((const void*)in != Lq.ghat)
+    CK(cudaMemcpyAsync(Lq.ghat, in, sizeof(T) * Lq.ncell, cudaMemcpyDeviceToDevice, s));
+  // restriction chain
+  for (int k = q; k >= 2; --k) {
+    LevelDev& L = h->lv[k];
+    T* dst = (T*)(k - 1 >= 2 ? h->lv[k - 1].ghat : h->g1);
+    if (h->exact) {
+      launch_dgemm((int)L.npar, 1, (int)L.ncell, 1.0, L.Rh, (const double*)L.ghat, 0, 0.0,
+                   (double*)dst, s);
+      if (k - 1 >= 2) {
+        LevelDev& Ln = h->lv[k - 1];
+        launch_transform_vec<T>(dst, dst, Ln.npar, Ln.pmask, +1, s);
+      }
+    } else {
+      launch_restrict<T>((const T*)L.Rhat, NB, h->nbr, 1 << (k - 1), L.npar, (const T*)L.ghat, dst,
+                         k - 1 >= 2 ? h->lv[k - 1].pmask : nullptr, s);
+    }
+  }
+  CK(cudaGetLastError());
+  // level solves
+  if (h->exact) {
+    for (int k = 2; k <= q; ++k) {
+      LevelDev& L = h->lv[k];
+      launch_gather_det((const double*)L.ghat, L.det, L.nJ, L.wc, s);
+      launch_dpotrs(L.Bc, L.nJ, L.wc, 1, s);
+      CK(cudaMemsetAsync(L.w, 0, sizeof(double) * L.ncell, s));
+      launch_scatter_det(L.wc, L.det, L.nJ, (double*)L.w, s);
+    }
+  } else {
+    run_level_cg<T>(h);
+  }
+  launch_level1_solve<T>(h->A1L, (const T*)h->g1, (T*)h->U1, s);
+  CK(cudaGetLastError());
+  // prolongation and summation
+  for (int k = 2; k <= q; ++k) {
+    LevelDev& L = h->lv[k];
+    const T* vprev = (const T*)(k == 2 ? h->U1 : h->lv[k - 1].v);
+    T* dst = (k == q) ? out : (T*)L.v;
+    const int inv = (k == q) ? inverse_last : 1;
+    if (h->exact) {
+      CK(cudaMemcpyAsync(dst, L.w, sizeof(double) * L.ncell, cudaMemcpyDeviceToDevice, s));
+      launch_dgemm_t((int)L.ncell, 1, (int)L.npar, 1.0, L.Rh, 1, (const double*)vprev, 0, 1.0,
+                     (double*)dst, s);
+      if (inv) launch_transform_vec<T>(dst, dst, L.npar, L.pmask, -1, s);
+    } else {
+      launch_prolong<T>((const T*)L.Rhat, NB, h->nbr, 1 << (k - 1), L.npar, vprev, (const T*)L.w,
+                        L.pmask, inv, dst, s);
+    }
+  }
+  CK(cudaGetLastError());
+}
+
+// Components u^(l) - u^(l-1) in Morton order (plain), level by level.
+template <typename T>
+void components(gamblet_ctx* h, T* out_q /* ncell_q */, int lev, T* scratch_a, T* scratch_b) {
+  cudaStream_t s = h->s;
+  const int q = h->q;
+  const int NB = h->N.size();
+  // v at level `lev`
+  T* cur = scratch_a;
+  T* nxt = scratch_b;
+  if (lev == 1) {
+    CK(cudaMemcpyAsync(cur, h->U1, sizeof(T) * 4, cudaMemcpyDeviceToDevice, s));
+  } else {
+    LevelDev& L = h->lv[lev];
+    CK(cudaMemsetAsync(nxt, 0, sizeof(T) * L.npar, s));
+    if (h->exact) {
+      CK(cudaMemcpyAsync(cur, L.w, sizeof(double) * L.ncell, cudaMemcpyDeviceToDevice, s));
+      launch_transform_vec<T>(cur, cur, L.npar, L.pmask, -1, s);
+    } else {
+      launch_prolong<T>((const T*)L.Rhat, NB, h->nbr, 1 << (lev - 1), L.npar, nxt, (const T*)L.w,
+                        L.pmask, 1, cur, s);
+    }
+  }
+  for (int k = lev + 1; k <= q; ++k) {
+    LevelDev& L = h->lv[k];
+    if (h->exact) {
+      launch_dgemm_t((int)L.ncell, 1, (int)L.npar, 1.0, L.Rh, 1, (const double*)cur, 0, 0.0,
+                     (double*)nxt, s);
+      launch_transform_vec<T>(nxt, nxt, L.npar, L.pmask, -1, s);
+    } else {
+      launch_prolong<T>((const T*)L.Rhat, NB, h->nbr, 1 << (k - 1), L.npar, cur, nullptr, L.pmask,
+                        1, nxt, s);
+    }
+    std::swap(cur, nxt);
+  }
+  CK(cudaMemcpyAsync(out_q, cur, sizeof(T) * h->lv[q].ncell, cudaMemcpyDeviceToDevice, s));
+  CK(cudaGetLastError());
+}
+
+template <typename T>
+T* as_T(gamblet_ctx* h, double* v64, void* vT, int64_t n, bool to) {
+  if (!is_f32<T>()) return (T*)v64;
+  if (to) launch_convert_f64_f32(v64, (float*)vT, n, h->s);
+  return (T*)vT;
+}
+
+template <typename T>
+gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, double* comps_user,
+                          gamblet_info* info) {
+  cudaStream_t s = h->s;
+  Pool tmp;
+  const int q = h->q;
+  LevelDev& Lq = h->lv[q];
+  const int64_t nq = Lq.ncell;
+  for (int k = 0; k < 32; ++k) h->level_iters_acc[k] = 0;
+  h->level_not_conv = false;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  double* g_dev = nullptr;
+  to_device(tmp, g_dev, g_user, h->n, s);
+  // ghat = Q g (float64, Morton order)
+  launch_gather_morton(g_dev, h->unknown_of, nq, h->g64, s);
+  launch_transform_vec<double>(h->g64, h->g64, Lq.npar, Lq.pmask, +1, s);
+  CK(cudaMemsetAsync(h->dots, 0, sizeof(double) * 8, s));
+  launch_dots(nq, h->g64, h->g64, nullptr, nullptr, nullptr, nullptr, h->dots, s);
+  CK(cudaMemcpyAsync(h->dots_h, h->dots, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double gnorm = std::sqrt(h->dots_h[0]);
+  gamblet_status st = GAMBLET_OK;
+  int outer = 0;
+  double relres = 0;
+  // z = G ghat (one pass)
+  T* gT = as_T<T>(h, h->g64, h->rT, nq, true);
+  T* zT = as_T<T>(h, h->z64, h->zT, nq, false);
+  apply_G<T>(h, gT, zT, 0);
+  if (is_f32<T>()) launch_convert_f32_f64((const float*)zT, h->z64, nq, s);
+  T* comp_scratch = nullptr;
+  if (comps_user) {
+    // components of the one-pass transform
+    T* ca = tmp.alloc<T>(nq);
+    T* cb = tmp.alloc<T>(nq);
+    T* cq = tmp.alloc<T>(nq);
+    double* c64 = tmp.alloc<double>(nq);
+    double* cu = tmp.alloc<double>(h->n);
+    for (int lev = 1; lev <= q; ++lev) {
+      components<T>(h, cq, lev, ca, cb);
+      if (is_f32<T>()) launch_convert_f32_f64((const float*)cq, c64, nq, s);
+      else CK(cudaMemcpyAsync(c64, cq, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
+      launch_scatter_unknown(c64, h->morton_of, h->n, cu, s);
+      CK(cudaMemcpyAsync(comps_user + (int64_t)(lev - 1) * h->n, cu, sizeof(double) * h->n,
+                         cudaMemcpyDefault, s));
+    }
+    (void)comp_scratch;
+  }
+  CK(cudaMemcpyAsync(h->u64, h->z64, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
+  const int maxit = h->opts.refine_max_iter;
+  if (maxit > 0 && gnorm > 0) {
+    // flexible CG (one-term orthogonalisation) on Ahat^(q) u = ghat
+    const int Lpar = 1 << (q - 1);
+    double* d = h->dots;
+    // r = g - A u
+    launch_block_spmv64(Lq.Ahat64, Lq.off, Lq.noff, Lpar, Lq.npar, h->u64, h->q64, s);
+    CK(cudaMemcpyAsync(h->r64, h->g64, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(d, 0, sizeof(double) * 8, s));
+    // d[7] = 1 used as unit denominator: r += (-1) * (1/1) q
+    double one = 1.0;
+    CK(cudaMemcpyAsync(d + 7, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_axpy(nq, d + 7, d + 7, -1.0, h->q64, h->r64, s);
+    launch_dots(nq, h->r64, h->r64, nullptr, nullptr, nullptr, nullptr, d, s);
+    CK(cudaMemcpyAsync(h->dots_h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    relres = std::sqrt(h->dots_h[0]) / gnorm;
+    if (relres > h->opts.refine_tol) {
+      T* rT = as_T<T>(h, h->r64, h->rT, nq, true);
+      apply_G<T>(h, rT, zT, 0);
+      if (is_f32<T>()) launch_convert_f32_f64((const float*)zT, h->z64, nq, s);
+      CK(cudaMemcpyAsync(h->p64, h->z64, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
+      for (outer = 1; outer <= maxit; ++outer) {
+        launch_block_spmv64(Lq.Ahat64, Lq.off, Lq.noff, Lpar, Lq.npar, h->p64, h->q64, s);
+        CK(cudaMemsetAsync(d, 0, sizeof(double) * 4, s));
+        // d0 = p.q, d1 = p.r
+        launch_dots(nq, h->p64, h->q64, h->p64, h->r64, nullptr, nullptr, d, s);
+        launch_axpy(nq, d + 1, d + 0, +1.0, h->p64, h->u64, s);
+        launch_axpy(nq, d + 1, d + 0, -1.0, h->q64, h->r64, s);
+        launch_dots(nq, nullptr, nullptr, nullptr, nullptr, h->r64, h->r64, d, s);  // d2 = r.r
+        CK(cudaMemcpyAsync(h->dots_h, d, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        relres = std::sqrt(h->dots_h[2]) / gnorm;
+        if (!(relres == relres)) fail(GAMBLET_ERR_NOT_SPD, "outer iteration produced NaN");
+        if (relres <= h->opts.refine_tol) break;
+        rT = as_T<T>(h, h->r64, h->rT, nq, true);
+        apply_G<T>(h, rT, zT, 0);
+        if (is_f32<T>()) launch_convert_f32_f64((const float*)zT, h->z64, nq, s);
+        // d3 = z.q ; p = z - (d3 / d0) p
+        launch_dots(nq, h->z64, h->q64, nullptr, nullptr, nullptr, nullptr, d + 3, s);
+        launch_xpby(nq, h->z64, d + 3, d + 0, -1.0, h->p64, s);
+        CK(cudaGetLastError());
+      }
+      if (outer > maxit) {
+        outer = maxit;
+        st = GAMBLET_ERR_NOT_CONVERGED;
+      }
+    }
+    // true residual
+    launch_block_spmv64(Lq.Ahat64, Lq.off, Lq.noff, Lpar, Lq.npar, h->u64, h->q64, s);
+    CK(cudaMemcpyAsync(h->r64, h->g64, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(d + 7, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_axpy(nq, d + 7, d + 7, -1.0, h->q64, h->r64, s);
+    CK(cudaMemsetAsync(d, 0, sizeof(double), s));
+    launch_dots(nq, h->r64, h->r64, nullptr, nullptr, nullptr, nullptr, d, s);
+    CK(cudaMemcpyAsync(h->dots_h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    relres = std::sqrt(h->dots_h[0]) / gnorm;
+  }
+  // u = Q^T uhat, back to unknown order
+  launch_transform_vec<double>(h->u64, h->q64, Lq.npar, Lq.pmask, -1, s);
+  double* u_dev = nullptr;
+  if (is_device_ptr(u_user)) {
+    launch_scatter_unknown(h->q64, h->morton_of, h->n, u_user, s);
+  } else {
+    u_dev = tmp.alloc<double>(h->n);
+    launch_scatter_unknown(h->q64, h->morton_of, h->n, u_dev, s);
+    CK(cudaMemcpyAsync(u_user, u_dev, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaEventRecord(e1, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  check_status(h, "solve");
+  if (maxit == 0 && h->level_not_conv) st = GAMBLET_ERR_NOT_CONVERGED;
+  if (info) {
+    info->status = st;
+    info->q = q;
+    info->outer_iters = outer;
+    for (int k = 0; k < 32; ++k) info->level_iters[k] = h->level_iters_acc[k];
+    info->rel_residual = relres;
+    info->setup_ms = h->setup_ms;
+    info->solve_ms = ms;
+  }
+  return st;
+}
+
+gamblet_status set_error(const GbError& e) {
+  g_last_error = e.msg;
+  return e.st;
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+extern "C" {
+
+void gamblet_default_opts(gamblet_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->rho = 3.0;
+  o->nbr_rule = 0;
+  o->precision = GAMBLET_FP64;
+  o->level_tol = 1e-8;
+  o->level_max_iter = 1000;
+  o->refine_tol = 1e-13;
+  o->refine_max_iter = 50;
+  o->use_graph = 1;
+  o->stream = nullptr;
+}
+
+gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cells,
+                             const gamblet_opts* opts, gamblet_handle* out) {
+  if (!out) {
+    g_last_error = "out is NULL";
+    return GAMBLET_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  gamblet_ctx* h = nullptr;
+  try {
+    if (!A || !cells) fail(GAMBLET_ERR_INVALID_ARG, "A and cells must be non-NULL");
+    if (A->n < 1 || A->nnz < 1 || !A->rowptr || !A->colind || !A->val)
+      fail(GAMBLET_ERR_INVALID_ARG, "empty or incomplete CSR");
+    if (q < 2 || q > 15) fail(GAMBLET_ERR_INVALID_ARG, "q must be in [2, 15]");
+    if ((int64_t)A->n > ((int64_t)1 << (2 * q)))
+      fail(GAMBLET_ERR_INVALID_ARG, "more unknowns than level-q cells");
+    h = new gamblet_ctx();
+    if (opts) h->opts = *opts;
+    else gamblet_default_opts(&h->opts);
+    h->s = (cudaStream_t)h->opts.stream;
+    h->q = q;
+    h->n = A->n;
+    h->exact = !(h->opts.rho > 0);
+    h->mixed = h->opts.precision == GAMBLET_MIXED && !h->exact;
+    if (h->opts.precision != GAMBLET_FP64 && h->opts.precision != GAMBLET_MIXED)
+      fail(GAMBLET_ERR_INVALID_ARG, "unknown precision");
+    if (h->opts.nbr_rule != 0 && h->opts.nbr_rule != 1)
+      fail(GAMBLET_ERR_INVALID_ARG, "nbr_rule must be 0 or 1");
+    if (h->exact && q > 7)
+      fail(GAMBLET_ERR_UNSUPPORTED, "the exact (rho <= 0) transform is limited to q <= 7");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    for (int k = 0; k < 32; ++k) h->level_iters_acc[k] = 0;
+    CK(cudaMallocHost(&h->any_active_h, sizeof(int)));
+    CK(cudaMallocHost(&h->dots_h, sizeof(double) * 8));
+    CK(cudaMallocHost(&h->status_h, sizeof(int)));
+    h->status = h->pool.zeros<int>(1, h->s);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, h->s));
+    if (!h->exact) {
+      h->N = neighbour_offsets(h->opts.rho, h->opts.nbr_rule);
+      h->jc = h->N.find(0, 0);
+      h->nbr = h->pool.upload(h->N.v, h->s);
+    }
+    build_hierarchy(h, cells);
+    import_fine(h, A);
+    if (h->exact) {
+      setup_exact(h);
+      alloc_solve<double>(h);
+    } else if (h->mixed) {
+      setup_local<float>(h);
+      alloc_solve<float>(h);
+    } else {
+      setup_local<double>(h);
+      alloc_solve<double>(h);
+    }
+    CK(cudaEventRecord(e1, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    CK(cudaGetLastError());
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->setup_ms = ms;
+    check_status(h, "setup");
+    *out = h;
+    return GAMBLET_OK;
+  } catch (const GbError& e) {
+    if (h) gamblet_destroy(h);
+    return set_error(e);
+  } catch (const std::exception& e) {
+    if (h) gamblet_destroy(h);
+    g_last_error = e.what();
+    return GAMBLET_ERR_INVALID_ARG;
+  }
+}
+
+gamblet_status gamblet_solve(gamblet_handle h, const double* g, double* u, double* components,
+                             gamblet_info* info) {
+  try {
+    if (!h || !g || !u) fail(GAMBLET_ERR_INVALID_ARG, "handle, g and u must be non-NULL");
+    if (h->mixed) return solve_impl<float>(h, g, u, components, info);
+    return solve_impl<double>(h, g, u, components, info);
+  } catch (const GbError& e) {
+    if (info) info->status = e.st;
+    return set_error(e);
+  }
+}
+
+gamblet_status gamblet_grad(gamblet_handle h, int32_t ncell, const int32_t* cell_nodes,
+                            const double* cell_a, const double* K_ref, const double* u,
+                            const double* u_obs, double* dJ, double* J, gamblet_info* info) {
+  try {
+    if (!h || !cell_nodes || !cell_a || !K_ref || !u || !u_obs || !dJ)
+      fail(GAMBLET_ERR_INVALID_ARG, "NULL argument");
+    if (ncell < 1) fail(GAMBLET_ERR_INVALID_ARG, "ncell must be positive");
+    cudaStream_t s = h->s;
+    Pool tmp;
+    const int n = h->n;
+    double* ud = nullptr;
+    double* uo = nullptr;
+    to_device(tmp, ud, u, n, s);
+    to_device(tmp, uo, u_obs, n, s);
+    // residual u - u_obs and J
+    double* res = tmp.alloc<double>(n);
+    CK(cudaMemcpyAsync(res, ud, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    double* d = tmp.zeros<double>(2, s);
+    double one = 1.0;
+    CK(cudaMemcpyAsync(d + 1, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_axpy(n, d + 1, d + 1, -1.0, uo, res, s);
+    launch_dots(n, res, res, nullptr, nullptr, nullptr, nullptr, d, s);
+    double jh = 0;
+    CK(cudaMemcpyAsync(&jh, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (J) *J = 0.5 * jh;
+    // adjoint solve A lam = u - u_obs through the same hierarchy
+    double* lam = tmp.alloc<double>(n);
+    gamblet_status st = gamblet_solve(h, res, lam, nullptr, info);
+    if (st != GAMBLET_OK && st != GAMBLET_ERR_NOT_CONVERGED) return st;
+    int32_t* cn = nullptr;
+    double* ca = nullptr;
+    to_device(tmp, cn, cell_nodes, 4 * (int64_t)ncell, s);
+    to_device(tmp, ca, cell_a, ncell, s);
+    double kh[16];
+    CK(cudaMemcpy(kh, K_ref, sizeof(kh), cudaMemcpyDefault));
+    launch_set_kref(kh);
+    double* out = nullptr;
+    const bool dev_out = is_device_ptr(dJ);
+    out = dev_out ? dJ : tmp.alloc<double>(ncell);
+    launch_adjoint_contract(ncell, cn, ca, lam, ud, out, s);
+    CK(cudaGetLastError());
+    if (!dev_out)
+      CK(cudaMemcpyAsync(dJ, out, sizeof(double) * ncell, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return st;
+  } catch (const GbError& e) {
+    if (info) info->status = e.st;
+    return set_error(e);
+  }
+}
+
+gamblet_status gamblet_level_size(gamblet_handle h, int32_t k, int32_t* n_k, int32_t* nJ_k) {
+  if (!h || k < 1 || k > h->q) {
+    g_last_error = "bad handle or level";
+    return GAMBLET_ERR_INVALID_ARG;
+  }
+  if (n_k) *n_k = h->lv[k].n_active;
+  if (nJ_k) *nJ_k = k >= 2 ? h->lv[k].nJ : 0;
+  return GAMBLET_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- getters
+namespace {
+
+// canonical index of every Morton cell at level k (-1 if empty)
+std::vector<int32_t> canon_map(gamblet_ctx* h, int k) {
+  const LevelDev& L = h->lv[k];
+  std::vector<int32_t> cm(L.ncell, -1);
+  if (k == h->q) {
+    for (int i = 0; i < h->n; ++i) cm[h->morton_of_h[i]] = i;
+    return cm;
+  }
+  int idx = 0;
+  for (int y = 0; y < L.L; ++y)
+    for (int x = 0; x < L.L; ++x) {
+      const uint32_t s = morton((uint32_t)x, (uint32_t)y);
+      if ((L.pmask_h[s >> 2] >> (s & 3)) & 1u) cm[s] = idx++;
+    }
+  return cm;
+}
+
+// canonical index of each detail slot (4p + t) of level k, -1 otherwise.
+std::vector<int32_t> canon_detail(gamblet_ctx* h, int k) {
+  const LevelDev& L = h->lv[k];
+  std::vector<int32_t> cm_par = canon_map(h, k - 1);
+  std::vector<std::pair<int32_t, int32_t>> order;  // (canonical parent, p)
+  for (int64_t p = 0; p < L.npar; ++p)
+    if (cm_par[p] >= 0) order.push_back({cm_par[p], (int32_t)p});
+  std::sort(order.begin(), order.end());
+  std::vector<int32_t> cd(L.ncell, -1);
+  int idx = 0;
+  for (auto& pr : order) {
+    const int m = __builtin_popcount(L.pmask_h[pr.second] & 15u);
+    for (int t = 0; t < m - 1; ++t) cd[4 * (int64_t)pr.second + t] = idx++;
+  }
+  return cd;
+}
+
+template <typename T>
+std::vector<double> download(const void* p, int64_t n, cudaStream_t s) {
+  std::vector<T> tmp(n);
+  if (n > 0) CK(cudaMemcpyAsync(tmp.data(), p, sizeof(T) * n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return std::vector<double>(tmp.begin(), tmp.end());
+}
+
+struct Coo {
+  std::vector<int32_t> r, c;
+  std::vector<double> v;
+  void add(int32_t i, int32_t j, double x) {
+    r.push_back(i);
+    c.push_back(j);
+    v.push_back(x);
+  }
+};
+
+// Ahat^(k) (transformed, in blocks) of either path as a callback over blocks.
+void level_blocks(gamblet_ctx* h, int k,
+                  const std::function<void(int64_t p, int64_t pp, const double* blk)>& f);
+
+}  // namespace
+
+namespace {
+void level_blocks(gamblet_ctx* h, int k,
+                  const std::function<void(int64_t, int64_t, const double*)>& f) {
+  LevelDev& L = h->lv[k];
+  cudaStream_t s = h->s;
+  if (h->exact) {
+    std::vector<double> D = download<double>(L.D, L.ncell * L.ncell, s);
+    double blk[16];
+    for (int64_t p = 0; p < L.npar; ++p)
+      for (int64_t pp = 0; pp < L.npar; ++pp) {
+        bool nz = false;
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) {
+            blk[a * 4 + b] = D[(4 * p + a) * L.ncell + 4 * pp + b];
+            nz = nz || blk[a * 4 + b] != 0.0;
+          }
+        if (nz) f(p, pp, blk);
+      }
+    return;
+  }
+  const int64_t nv = (int64_t)L.noff * L.npar * 16;
+  std::vector<double> V = h->mixed ? download<float>(L.Ahat, nv, s) : download<double>(L.Ahat, nv, s);
+  const int Lpar = 1 << (k - 1);
+  for (int o = 0; o < L.noff; ++o)
+    for (int64_t p = 0; p < L.npar; ++p) {
+      int x, y;
+      demorton((uint32_t)p, x, y);
+      const int pp = shift_cell(x, y, L.off_h[o].x, L.off_h[o].y, Lpar);
+      if (pp < 0) continue;
+      f(p, pp, &V[((int64_t)o * L.npar + p) * 16]);
+    }
+}
+
+Coo get_A(gamblet_ctx* h, int k) {
+  Coo out;
+  cudaStream_t s = h->s;
+  if (k == 1) {
+    std::vector<int32_t> cm = canon_map(h, 1);
+    std::vector<double> M(16, 0.0);
+    if (h->exact) {
+      M = download<double>(h->A1, 16, s);
+    } else {
+      const LevelDev& L1 = h->lv[1];
+      std::vector<double> C = h->mixed ? download<float>(L1.Ahat, (int64_t)L1.noff * 4, s)
+                                       : download<double>(L1.Ahat, (int64_t)L1.noff * 4, s);
+      std::map<Off, int> sidx;
+      for (int d = 0; d < L1.noff; ++d) sidx[Off{L1.off_h[d].x, L1.off_h[d].y}] = d;
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+          auto it = sidx.find(Off{(j & 1) - (i & 1), (j >> 1) - (i >> 1)});
+          if (it != sidx.end()) M[i * 4 + j] = C[(int64_t)it->second * 4 + i];
+        }
+    }
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j)
+        if (cm[i] >= 0 && cm[j] >= 0 && M[i * 4 + j] != 0.0) out.add(cm[i], cm[j], M[i * 4 + j]);
+    return out;
+  }
+  std::vector<int32_t> cm = canon_map(h, k);
+  const LevelDev& L = h->lv[k];
+  level_blocks(h, k, [&](int64_t p, int64_t pp, const double* blk) {
+    double Qr[16], Qc[16];
+    qmat<double>((int)(L.pmask_h[p] & 15u), Qr);
+    qmat<double>((int)(L.pmask_h[pp] & 15u), Qc);
+    for (int c = 0; c < 4; ++c)
+      for (int cc = 0; cc < 4; ++cc) {
+        const int32_t i = cm[4 * p + c], j = cm[4 * pp + cc];
+        if (i < 0 || j < 0) continue;
+        double acc = 0;  // (Q^T blk Q)[c][cc]
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) acc += Qr[a * 4 + c] * blk[a * 4 + b] * Qc[b * 4 + cc];
+        out.add(i, j, acc);
+      }
+  });
+  return out;
+}
+
+Coo get_B(gamblet_ctx* h, int k) {
+  Coo out;
+  std::vector<int32_t> cd = canon_detail(h, k);
+  level_blocks(h, k, [&](int64_t p, int64_t pp, const double* blk) {
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const int32_t i = cd[4 * p + a], j = cd[4 * pp + b];
+        if (i >= 0 && j >= 0) out.add(i, j, blk[a * 4 + b]);
+      }
+  });
+  return out;
+}
+
+Coo get_R(gamblet_ctx* h, int k) {
+  Coo out;
+  cudaStream_t s = h->s;
+  const LevelDev& L = h->lv[k];
+  std::vector<int32_t> cmr = canon_map(h, k - 1), cmc = canon_map(h, k);
+  if (h->exact) {
+    std::vector<double> Rh = download<double>(L.Rh, L.npar * L.ncell, s);
+    for (int64_t i = 0; i < L.npar; ++i) {
+      if (cmr[i] < 0) continue;
+      for (int64_t p = 0; p < L.npar; ++p) {
+        double Q[16];
+        qmat<double>((int)(L.pmask_h[p] & 15u), Q);
+        for (int c = 0; c < 4; ++c) {
+          if (cmc[4 * p + c] < 0) continue;
+          double acc = 0;
+          for (int a = 0; a < 4; ++a) acc += Rh[i * L.ncell + 4 * p + a] * Q[a * 4 + c];
+          if (acc != 0.0) out.add(cmr[i], cmc[4 * p + c], acc);
+        }
+      }
+    }
+    return out;
+  }
+  const int NB = h->N.size();
+  const int64_t nv = (int64_t)NB * 4 * L.npar;
+  std::vector<double> R = h->mixed ? download<float>(L.Rhat, nv, s) : download<double>(L.Rhat, nv, s);
+  const int Lpar = 1 << (k - 1);
+  for (int64_t i = 0; i < L.npar; ++i) {
+    if (cmr[i] < 0) continue;
+    int x, y;
+    demorton((uint32_t)i, x, y);
+    for (int j = 0; j < NB; ++j) {
+      const int p = shift_cell(x, y, h->N.v[j].x, h->N.v[j].y, Lpar);
+      if (p < 0) continue;
+      double Q[16];
+      qmat<double>((int)(L.pmask_h[p] & 15u), Q);
+      for (int c = 0; c < 4; ++c) {
+        if (cmc[4 * (int64_t)p + c] < 0) continue;
+        double acc = 0;
+        for (int a = 0; a < 4; ++a) acc += R[(int64_t)(4 * j + a) * L.npar + i] * Q[a * 4 + c];
+        if (acc != 0.0) out.add(cmr[i], cmc[4 * (int64_t)p + c], acc);
+      }
+    }
+  }
+  return out;
+}
+
+}  // namespace
+
+extern "C" {
+
+gamblet_status gamblet_get_operator(gamblet_handle h, int32_t which, int32_t k, int64_t capacity,
+                                    int64_t* nnz, int32_t* rows, int32_t* cols, double* vals) {
+  try {
+    if (!h || !nnz) fail(GAMBLET_ERR_INVALID_ARG, "NULL handle or nnz");
+    if (k < 1 || k > h->q || (which != 0 && k < 2) || which < 0 || which > 2)
+      fail(GAMBLET_ERR_INVALID_ARG, "bad operator or level");
+    Coo c = which == 0 ? get_A(h, k) : which == 1 ? get_R(h, k) : get_B(h, k);
+    *nnz = (int64_t)c.v.size();
+    if (capacity == 0) return GAMBLET_OK;
+    if (capacity < *nnz || !rows || !cols || !vals)
+      fail(GAMBLET_ERR_INVALID_ARG, "capacity too small or NULL output");
+    std::memcpy(rows, c.r.data(), sizeof(int32_t) * c.r.size());
+    std::memcpy(cols, c.c.data(), sizeof(int32_t) * c.c.size());
+    std::memcpy(vals, c.v.data(), sizeof(double) * c.v.size());
+    return GAMBLET_OK;
+  } catch (const GbError& e) {
+    return set_error(e);
+  }
+}
+
+int64_t gamblet_device_bytes(gamblet_handle h) { return h ? h->pool.bytes : 0; }
+
+void gamblet_destroy(gamblet_handle h) {
+  if (!h) return;
+  if (h->s) cudaStreamSynchronize(h->s);
+  else cudaDeviceSynchronize();
+  h->pool.release();
+  if (h->any_active_h) cudaFreeHost(h->any_active_h);
+  if (h->dots_h) cudaFreeHost(h->dots_h);
+  if (h->status_h) cudaFreeHost(h->status_h);
+  delete h;
+}
+
+const char* gamblet_status_string(int32_t status) {
+  switch (status) {
+    case GAMBLET_OK: return "ok";
+    case GAMBLET_ERR_INVALID_ARG: return "invalid argument";
+    case GAMBLET_ERR_NOT_SPD: return "matrix not symmetric positive definite (non-positive pivot)";
+    case GAMBLET_ERR_NOT_CONVERGED: return "iteration cap reached before the tolerance";
+    case GAMBLET_ERR_CUDA: return "CUDA runtime error";
+    case GAMBLET_ERR_OUT_OF_MEMORY: return "device out of memory";
+    case GAMBLET_ERR_UNSUPPORTED: return "input outside this build's limits";
+    default: return "unknown status";
+  }
+}
+
+const char* gamblet_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

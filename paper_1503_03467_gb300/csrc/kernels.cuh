@@ -1,0 +1,189 @@
+// kernels.cuh - launch wrappers of the gamblet device kernels.
+//
+// All launches take the stream explicitly and return immediately; the host
+// orchestration in gamblet.cu checks cudaGetLastError after each phase.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gb {
+
+// ---------------------------------------------------------------- hierarchy
+// cells (n x 2, device) -> Morton index of every fine unknown, inverse map
+// (Morton -> unknown or -1), child masks of the level-q parents.  dup_flag
+// is set when two unknowns share a cell or a cell lies outside [0, 2^q).
+void launch_cells_to_morton(const int32_t* cells, int n, int q, int32_t* morton_of,
+                            int32_t* unknown_of, uint32_t* pmask_q, int* dup_flag,
+                            cudaStream_t s);
+// Child masks of level k-1 parents from the masks of level k parents:
+// parent p at level k is active iff pmask_k[p] != 0.
+void launch_coarsen_masks(const uint32_t* pmask_k, int64_t npar_k, uint32_t* pmask_km1,
+                          cudaStream_t s);
+
+// ---------------------------------------------------------------- fine operator
+// Largest |parent offset| in x and y over the stored entries (atomicMax).
+void launch_csr_offset_extent(int n, const int32_t* rowptr, const int32_t* colind,
+                              const int32_t* morton_of, int* ext, int* bad_flag,
+                              cudaStream_t s);
+// Scatter A^(q) into a block stencil (rows/cols in slot space, untransformed).
+// Offsets form the box [-rx, rx] x [-ry, ry], index (dy + ry) * (2 rx + 1) + dx + rx.
+void launch_csr_to_blocks(int n, const int32_t* rowptr, const int32_t* colind,
+                          const double* val, const int32_t* morton_of, int rx, int ry,
+                          int64_t npar, double* blk, cudaStream_t s);
+
+// ---------------------------------------------------------------- transforms
+// In place: blk(o, p) <- Q_{mask p} blk(o, p) Q_{mask p+off_o}^T.
+void launch_transform_blocks(double* blk, const int2* off, int noff, int64_t npar,
+                             int Lpar, const uint32_t* pmask, cudaStream_t s);
+// Copy a float64 block stencil to float32.
+void launch_convert_f64_f32(const double* in, float* out, int64_t n, cudaStream_t s);
+void launch_convert_f32_f64(const float* in, double* out, int64_t n, cudaStream_t s);
+
+// x_hat = Q x (dir = +1) or x = Q^T x_hat (dir = -1) on a level vector whose
+// parents have child masks pmask (4 * npar entries).
+template <typename T>
+void launch_transform_vec(const T* in, T* out, int64_t npar, const uint32_t* pmask, int dir,
+                          cudaStream_t s);
+
+// Gather unknown-ordered values to Morton order (inactive cells 0) and back.
+void launch_gather_morton(const double* in_unknown, const int32_t* unknown_of, int64_t ncell,
+                          double* out_morton, cudaStream_t s);
+void launch_scatter_unknown(const double* in_morton, const int32_t* morton_of, int n,
+                            double* out_unknown, cudaStream_t s);
+
+// ---------------------------------------------------------------- patches
+struct PatchGeom {
+  int NB;              // neighbour offsets N_j (level k-1 cell units)
+  int jc;              // index of (0, 0) in N
+  const int2* nbr;     // N_j
+  const int* pair_idx; // NB x NB: index in O_k of N_b - N_a, or -1
+  int Lpar;            // side of the level-(k-1) lattice
+  int64_t npatch;      // 4^(k-1)
+};
+// Localized patch solves of Definition defb for every coarse cell of level
+// k-1; writes Rhat rows (SoA [NB * 4][npatch]).  status receives DEV_NOT_SPD
+// on a non-positive pivot.
+template <typename T>
+void launch_patch_solve(const T* Ahat, const uint32_t* pmask_k, PatchGeom g, T* Rhat,
+                        int* status, int num_sms, cudaStream_t s);
+template <typename T>
+size_t patch_smem_bytes(int NB);
+
+// ---------------------------------------------------------------- Galerkin
+struct GalerkinGeom {
+  int NB;
+  const int2* nbr;       // N_j
+  int nwin;              // window positions WIN_w (relative to coarse cell i)
+  const int2* win;
+  const int* l1_ptr;     // nwin + 1
+  const int2* l1_pairs;  // (j, o): N_j - WIN_w = O_o
+  int nout;              // output cell offsets S_d
+  const int2* out;
+  const int* l2_ptr;     // nout + 1
+  const int2* l2_pairs;  // (j, w): WIN_w = S_d + N_j
+  int Lpar;              // side of the level-(k-1) lattice (= parent lattice of level k)
+  int64_t nrow;          // 4^(k-1)
+};
+// A'(d, i) = (Rhat Ahat Rhat^T)_{i, i + S_d} for every level-(k-1) cell i.
+template <typename T>
+void launch_galerkin(const T* Ahat, const T* Rhat, const uint32_t* pmask_k, GalerkinGeom g,
+                     T* Aout, cudaStream_t s);
+// Level-(k-1) cell stencil (S offsets, [d][i]) -> transformed block stencil
+// at level k-1 (offsets O, [o][P][16]) using masks of level k-1 parents.
+// map: nO x 16 index into S of 2*Delta + c' - c for (a = c, b = c'), or -1.
+template <typename T>
+void launch_cells_to_blocks(const T* Acell, int64_t ncell, const int* map, int nO,
+                            const int2* Ooff, int Lpar, int64_t npar, const uint32_t* pmask,
+                            T* blk, cudaStream_t s);
+// A^(1) (4 x 4) from the level-1 cell stencil (map[4 i + j] = index in S of
+// cell_j - cell_i, or -1), factored in place (lower Cholesky, float64).
+template <typename T>
+void launch_level1_factor(const T* Acell, const int* map, double* L1, int* status,
+                          cudaStream_t s);
+// U = A^(1)^-1 g from the factor.
+template <typename T>
+void launch_level1_solve(const double* L1, const T* g, T* U, cudaStream_t s);
+
+// ---------------------------------------------------------------- solve
+// g^(k-1)_i = sum_{j, c} Rhat[j, c, i] ghat^(k)[4 (i + N_j) + c]; if
+// pmask_km1 != nullptr the result is also transformed by Q^(k-1) in place.
+template <typename T>
+void launch_restrict(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t nrow,
+                     const T* ghat_k, T* g_km1, const uint32_t* pmask_km1, cudaStream_t s);
+// vhat^(k) = Rhat^T v^(k-1) + [w^(k); 0]; if inverse, v^(k) = Q^T vhat^(k).
+template <typename T>
+void launch_prolong(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t npar,
+                    const T* v_km1, const T* w_k, const uint32_t* pmask_k, int inverse,
+                    T* out, cudaStream_t s);
+
+// Batched level CG over several levels at once.
+struct CgLevel {
+  const void* Ahat;   // block stencil (T)
+  const int2* off;
+  int noff;
+  int Lpar;
+  int64_t npar;
+  const uint32_t* pmask;
+  void* x;            // solution (AoS4, slot 3 unused)
+  void* r;
+  void* p;
+  void* Ap;
+  const void* b;      // right-hand side (transformed vector; slots 0..2 used)
+  int block_begin;    // first CTA of this level in the batched grid
+};
+struct CgScalars {
+  double rr, rr_new, pAp, rr0, beta;
+  int active, iters;
+};
+template <typename T>
+void launch_cg_init(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
+                    cudaStream_t s);
+void launch_cg_start(CgScalars* sc, int nlev, int* any_active, cudaStream_t s);
+template <typename T>
+void launch_cg_iteration(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
+                         double tol2, int max_iter, int* any_active, cudaStream_t s);
+
+// Outer float64 operations on transformed level-q vectors.
+void launch_block_spmv64(const double* Ahat, const int2* off, int noff, int Lpar, int64_t npar,
+                         const double* x, double* y, cudaStream_t s);
+// dots[i] += a_i . b_i for up to 3 pairs (nullptr pairs skipped).
+void launch_dots(int64_t n, const double* a0, const double* b0, const double* a1,
+                 const double* b1, const double* a2, const double* b2, double* dots,
+                 cudaStream_t s);
+void launch_axpy(int64_t n, const double* alpha_num, const double* alpha_den, double sign,
+                 const double* x, double* y, cudaStream_t s);
+void launch_xpby(int64_t n, const double* x, const double* beta_num, const double* beta_den,
+                 double sign, double* p, cudaStream_t s);
+
+// Adjoint contraction: dJ_c = -a_c sum_{p,r} lam[n_p] K[p][r] u[n_r].
+void launch_adjoint_contract(int ncell, const int32_t* cell_nodes, const double* cell_a,
+                             const double* lam, const double* u, double* dJ,
+                             cudaStream_t s);
+void launch_set_kref(const double* K_ref_host);
+
+// ---------------------------------------------------------------- dense (exact path)
+void launch_dense_from_blocks(const double* blk, const int2* off, int noff, int Lpar,
+                              int64_t npar, double* D, cudaStream_t s);
+void launch_dense_transform(const double* in, int64_t npar, const uint32_t* pmask, double* out,
+                            cudaStream_t s);
+// C (m x n) = alpha * op(A) * op(B) + beta * C; op(A) is m x kk, op(B) kk x n.
+// Row-major, leading dimensions = column counts of the stored matrices.
+void launch_dgemm_t(int m, int n, int kk, double alpha, const double* A, int transA,
+                    const double* B, int transB, double beta, double* C, cudaStream_t s);
+void launch_dgemm(int m, int n, int kk, double alpha, const double* A, const double* B,
+                  int transB, double beta, double* C, cudaStream_t s);
+// In-place lower Cholesky of an n x n row-major matrix (single CTA).
+void launch_dpotrf(double* A, int n, int* status, cudaStream_t s);
+// Solve (L L^T) X = B for nrhs columns of B (n x nrhs row-major), in place.
+void launch_dpotrs(const double* L, int n, double* B, int nrhs, cudaStream_t s);
+// Gather helpers for the dense path.
+void launch_gather_rows_cols(const double* D, int ld, const int32_t* rows, int nr,
+                             const int32_t* cols, int nc, double alpha_scale,
+                             const double* col_scale, double* out, cudaStream_t s);
+void launch_dense_rhat(const double* Y, const int32_t* det, int nJ, const int32_t* par, int nA,
+                       const uint32_t* pmask, int64_t npar, double* Rh, cudaStream_t s);
+void launch_scatter_det(const double* wc, const int32_t* det, int nJ, double* w, cudaStream_t s);
+void launch_gather_det(const double* w, const int32_t* det, int nJ, double* wc, cudaStream_t s);
+void launch_level1_factor_dense(const double* A, double* L, int* status, cudaStream_t s);
+
+}  // namespace gb

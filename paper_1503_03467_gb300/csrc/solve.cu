@@ -1,0 +1,477 @@
+// solve.cu - the solve phase: restriction g^(k-1) = R g^(k) (Eq. eqyguugy6t),
+// the independent level systems B^(k) w^(k) = W g^(k) solved by CG
+// (Eq. eqsdjoejddi1, Sec. 4.9), the coarsest system A^(1) U^(1) = g^(1)
+// (Eq. eqsdjoejddi2), prolongation and summation of the components
+// (Theorem thddwedmgugyug), and the float64 outer operations.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace gb {
+
+// ---------------------------------------------------------------- restriction
+template <typename T>
+__global__ void k_restrict(const T* __restrict__ Rhat, int NB, const int2* __restrict__ nbr,
+                           int Lpar, int64_t nrow, const T* __restrict__ ghat, T* out,
+                           const uint32_t* __restrict__ pmask_km1) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  T acc = 0;
+  if (i < nrow) {
+    int x, y;
+    demorton((uint32_t)i, x, y);
+    for (int j = 0; j < NB; ++j) {
+      const int p = shift_cell(x, y, nbr[j].x, nbr[j].y, Lpar);
+      if (p < 0) continue;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc += Rhat[(int64_t)(4 * j + c) * nrow + i] * ghat[4 * p + c];
+    }
+  }
+  if (pmask_km1 == nullptr) {
+    if (i < nrow) out[i] = acc;
+    return;
+  }
+  // transform by Q^(k-1): lanes 4P..4P+3 hold the four children of parent P
+  const int lane = threadIdx.x & 31;
+  const int c = lane & 3;
+  const int base = lane & ~3;
+  T v0 = __shfl_sync(0xffffffffu, acc, base);
+  T v1 = __shfl_sync(0xffffffffu, acc, base + 1);
+  T v2 = __shfl_sync(0xffffffffu, acc, base + 2);
+  T v3 = __shfl_sync(0xffffffffu, acc, base + 3);
+  if (i < nrow) {
+    const int m = (int)pmask_km1[i >> 2] & 15;
+    out[i] = qv<T>(m, c, 0) * v0 + qv<T>(m, c, 1) * v1 + qv<T>(m, c, 2) * v2 +
+             qv<T>(m, c, 3) * v3;
+  }
+}
+
+template <typename T>
+void launch_restrict(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t nrow,
+                     const T* ghat_k, T* g_km1, const uint32_t* pmask_km1, cudaStream_t s) {
+  if (nrow <= 0) return;
+  k_restrict<T><<<(unsigned)((nrow + 127) / 128), 128, 0, s>>>(Rhat, NB, nbr, Lpar, nrow, ghat_k,
+                                                               g_km1, pmask_km1);
+}
+template void launch_restrict<float>(const float*, int, const int2*, int, int64_t, const float*,
+                                     float*, const uint32_t*, cudaStream_t);
+template void launch_restrict<double>(const double*, int, const int2*, int, int64_t,
+                                      const double*, double*, const uint32_t*, cudaStream_t);
+
+// ---------------------------------------------------------------- prolongation
+template <typename T>
+__global__ void k_prolong(const T* __restrict__ Rhat, int NB, const int2* __restrict__ nbr,
+                          int Lpar, int64_t npar, const T* __restrict__ v, const T* __restrict__ w,
+                          const uint32_t* __restrict__ pmask, int inverse, T* out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npar) return;
+  const int m = (int)pmask[p] & 15;
+  T h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+  if (m) {
+    int x, y;
+    demorton((uint32_t)p, x, y);
+    h3 = v[p] * (T(1) / sqrt(T(__popc(m))));
+    if (w) {
+      h0 = w[4 * p];
+      h1 = w[4 * p + 1];
+      h2 = w[4 * p + 2];
+    }
+    for (int j = 0; j < NB; ++j) {
+      const int i = shift_cell(x, y, -nbr[j].x, -nbr[j].y, Lpar);
+      if (i < 0) continue;
+      const T vi = v[i];
+      if (vi == T(0)) continue;
+      h0 += Rhat[(int64_t)(4 * j) * npar + i] * vi;
+      h1 += Rhat[(int64_t)(4 * j + 1) * npar + i] * vi;
+      h2 += Rhat[(int64_t)(4 * j + 2) * npar + i] * vi;
+    }
+  }
+  if (inverse) {
+    T Q[16];
+    qmat<T>(m, Q);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      out[4 * p + c] = Q[c] * h0 + Q[4 + c] * h1 + Q[8 + c] * h2 + Q[12 + c] * h3;
+  } else {
+    out[4 * p] = h0;
+    out[4 * p + 1] = h1;
+    out[4 * p + 2] = h2;
+    out[4 * p + 3] = h3;
+  }
+}
+
+template <typename T>
+void launch_prolong(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t npar,
+                    const T* v_km1, const T* w_k, const uint32_t* pmask_k, int inverse, T* out,
+                    cudaStream_t s) {
+  if (npar <= 0) return;
+  k_prolong<T><<<(unsigned)((npar + 127) / 128), 128, 0, s>>>(Rhat, NB, nbr, Lpar, npar, v_km1, w_k,
+                                                              pmask_k, inverse, out);
+}
+template void launch_prolong<float>(const float*, int, const int2*, int, int64_t, const float*,
+                                    const float*, const uint32_t*, int, float*, cudaStream_t);
+template void launch_prolong<double>(const double*, int, const int2*, int, int64_t,
+                                     const double*, const double*, const uint32_t*, int, double*,
+                                     cudaStream_t);
+
+// ---------------------------------------------------------------- batched level CG
+__device__ __forceinline__ int find_level(const CgLevel* lv, int nlev, int b) {
+  int l = 0;
+  while (l + 1 < nlev && lv[l + 1].block_begin <= b) ++l;
+  return l;
+}
+
+__device__ __forceinline__ void block_atomic_add(double v, double* dst) {
+  __shared__ double red[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0 && v != 0.0) atomicAdd(dst, v);
+  }
+}
+
+// r = b (detail slots), x = 0, p = r, rr = r.r
+template <typename T>
+__global__ void k_cg_init(const CgLevel* __restrict__ lv, int nlev, CgScalars* sc) {
+  const int l = find_level(lv, nlev, blockIdx.x);
+  const CgLevel L = lv[l];
+  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
+  double part = 0;
+  if (p < L.npar) {
+    const T* b = (const T*)L.b;
+    T* x = (T*)L.x;
+    T* r = (T*)L.r;
+    T* pp = (T*)L.p;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const T v = a < 3 ? b[4 * p + a] : T(0);
+      x[4 * p + a] = 0;
+      r[4 * p + a] = v;
+      pp[4 * p + a] = v;
+      part += (double)v * (double)v;
+    }
+  }
+  block_atomic_add(part, &sc[l].rr);
+}
+
+__global__ void k_cg_start(CgScalars* sc, int nlev, int* any_active) {
+  const int l = threadIdx.x;
+  if (l < nlev) {
+    sc[l].rr0 = sc[l].rr;
+    sc[l].active = sc[l].rr > 0.0;
+    sc[l].iters = 0;
+    sc[l].pAp = 0;
+    sc[l].rr_new = 0;
+    if (sc[l].active) atomicExch(any_active, 1);
+  }
+}
+
+template <typename T>
+void launch_cg_init(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
+                    cudaStream_t s) {
+  if (total_blocks <= 0) return;
+  k_cg_init<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc);
+}
+
+// Ap = B p over the 3x3 detail blocks; pAp += p.Ap
+template <typename T>
+__global__ void k_cg_spmv(const CgLevel* __restrict__ lv, int nlev, CgScalars* sc) {
+  const int l = find_level(lv, nlev, blockIdx.x);
+  if (!sc[l].active) return;
+  const CgLevel L = lv[l];
+  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
+  double part = 0;
+  if (p < L.npar) {
+    const T* A = (const T*)L.Ahat;
+    const T* pv = (const T*)L.p;
+    T y0 = 0, y1 = 0, y2 = 0;
+    int x, y;
+    demorton((uint32_t)p, x, y);
+    for (int o = 0; o < L.noff; ++o) {
+      const int q = shift_cell(x, y, L.off[o].x, L.off[o].y, L.Lpar);
+      if (q < 0) continue;
+      const T* blk = A + ((int64_t)o * L.npar + p) * 16;
+      const T x0 = pv[4 * q], x1 = pv[4 * q + 1], x2 = pv[4 * q + 2];
+      y0 += blk[0] * x0 + blk[1] * x1 + blk[2] * x2;
+      y1 += blk[4] * x0 + blk[5] * x1 + blk[6] * x2;
+      y2 += blk[8] * x0 + blk[9] * x1 + blk[10] * x2;
+    }
+    T* Ap = (T*)L.Ap;
+    Ap[4 * p] = y0;
+    Ap[4 * p + 1] = y1;
+    Ap[4 * p + 2] = y2;
+    Ap[4 * p + 3] = 0;
+    part = (double)pv[4 * p] * y0 + (double)pv[4 * p + 1] * y1 + (double)pv[4 * p + 2] * y2;
+  }
+  block_atomic_add(part, &sc[l].pAp);
+}
+
+// x += alpha p, r -= alpha Ap, rr_new += r.r
+template <typename T>
+__global__ void k_cg_axpy(const CgLevel* __restrict__ lv, int nlev, CgScalars* sc) {
+  const int l = find_level(lv, nlev, blockIdx.x);
+  if (!sc[l].active) return;
+  const CgLevel L = lv[l];
+  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
+  double part = 0;
+  if (p < L.npar) {
+    const double pAp = sc[l].pAp;
+    const T alpha = pAp > 0 ? (T)(sc[l].rr / pAp) : T(0);
+    T* x = (T*)L.x;
+    T* r = (T*)L.r;
+    const T* pv = (const T*)L.p;
+    const T* Ap = (const T*)L.Ap;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      x[4 * p + a] += alpha * pv[4 * p + a];
+      const T rv = r[4 * p + a] - alpha * Ap[4 * p + a];
+      r[4 * p + a] = rv;
+      part += (double)rv * (double)rv;
+    }
+  }
+  block_atomic_add(part, &sc[l].rr_new);
+}
+
+// beta, convergence, counters (one thread per level)
+__global__ void k_cg_scalars(CgScalars* sc, int nlev, double tol2, int max_iter,
+                             int* any_active) {
+  const int l = threadIdx.x;
+  if (l >= nlev || !sc[l].active) return;
+  CgScalars s = sc[l];
+  s.iters += 1;
+  const double beta = s.rr > 0 ? s.rr_new / s.rr : 0.0;
+  s.beta = beta;
+  s.rr = s.rr_new;
+  s.rr_new = 0;
+  s.pAp = 0;
+  if (s.rr <= tol2 * s.rr0 || s.iters >= max_iter || !(s.rr == s.rr)) s.active = 0;
+  else atomicExch(any_active, 1);
+  sc[l] = s;
+}
+
+// p = r + beta p
+template <typename T>
+__global__ void k_cg_dir(const CgLevel* __restrict__ lv, int nlev, CgScalars* sc) {
+  const int l = find_level(lv, nlev, blockIdx.x);
+  if (!sc[l].active) return;
+  const CgLevel L = lv[l];
+  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
+  if (p >= L.npar) return;
+  const T beta = (T)sc[l].beta;
+  T* pv = (T*)L.p;
+  const T* r = (const T*)L.r;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) pv[4 * p + a] = r[4 * p + a] + beta * pv[4 * p + a];
+}
+
+template <typename T>
+void launch_cg_iteration(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
+                         double tol2, int max_iter, int* any_active, cudaStream_t s) {
+  if (total_blocks <= 0) return;
+  k_cg_spmv<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc);
+  k_cg_axpy<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc);
+  k_cg_scalars<<<1, 32, 0, s>>>(sc, nlev, tol2, max_iter, any_active);
+  k_cg_dir<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc);
+}
+
+void launch_cg_start(CgScalars* sc, int nlev, int* any_active, cudaStream_t s) {
+  k_cg_start<<<1, 32, 0, s>>>(sc, nlev, any_active);
+}
+
+template void launch_cg_init<float>(const CgLevel*, int, int, CgScalars*, cudaStream_t);
+template void launch_cg_init<double>(const CgLevel*, int, int, CgScalars*, cudaStream_t);
+template void launch_cg_iteration<float>(const CgLevel*, int, int, CgScalars*, double, int, int*,
+                                         cudaStream_t);
+template void launch_cg_iteration<double>(const CgLevel*, int, int, CgScalars*, double, int, int*,
+                                          cudaStream_t);
+
+// ---------------------------------------------------------------- coarsest level
+// A^(1) (4 x 4, float64) from the level-1 cell stencil; Cholesky in place.
+template <typename T>
+__global__ void k_level1_factor(const T* __restrict__ Acell, const int* __restrict__ map,
+                                double* A1, int* status) {
+  if (threadIdx.x != 0) return;
+  double M[16];
+  for (int e = 0; e < 16; ++e) {
+    const int i = e / 4;
+    const int d = map[e];
+    M[e] = d >= 0 ? (double)Acell[(int64_t)d * 4 + i] : 0.0;
+  }
+  // inactive cells (zero row and column) become identity rows
+  for (int i = 0; i < 4; ++i) {
+    bool zero = true;
+    for (int j = 0; j < 4; ++j) zero = zero && M[i * 4 + j] == 0.0;
+    if (zero) M[i * 4 + i] = 1.0;
+  }
+  for (int j = 0; j < 4; ++j) {
+    double d = M[j * 4 + j];
+    for (int k = 0; k < j; ++k) d -= M[j * 4 + k] * M[j * 4 + k];
+    if (!(d > 0)) {
+      atomicExch(status, (int)DEV_NOT_SPD);
+      d = 1.0;
+    }
+    d = sqrt(d);
+    M[j * 4 + j] = d;
+    for (int i = j + 1; i < 4; ++i) {
+      double v = M[i * 4 + j];
+      for (int k = 0; k < j; ++k) v -= M[i * 4 + k] * M[j * 4 + k];
+      M[i * 4 + j] = v / d;
+    }
+  }
+  for (int e = 0; e < 16; ++e) A1[e] = M[e];
+}
+
+template <typename T>
+void launch_level1_factor(const T* Acell, const int* map, double* A1, int* status,
+                          cudaStream_t s) {
+  k_level1_factor<T><<<1, 32, 0, s>>>(Acell, map, A1, status);
+}
+template void launch_level1_factor<float>(const float*, const int*, double*, int*, cudaStream_t);
+template void launch_level1_factor<double>(const double*, const int*, double*, int*,
+                                           cudaStream_t);
+
+template <typename T>
+__global__ void k_level1_solve(const double* __restrict__ L, const T* __restrict__ g, T* U) {
+  if (threadIdx.x != 0) return;
+  double z[4];
+  for (int i = 0; i < 4; ++i) {
+    double v = (double)g[i];
+    for (int k = 0; k < i; ++k) v -= L[i * 4 + k] * z[k];
+    z[i] = v / L[i * 4 + i];
+  }
+  for (int i = 3; i >= 0; --i) {
+    double v = z[i];
+    for (int k = i + 1; k < 4; ++k) v -= L[k * 4 + i] * z[k];
+    z[i] = v / L[i * 4 + i];
+  }
+  for (int i = 0; i < 4; ++i) U[i] = (T)z[i];
+}
+
+template <typename T>
+void launch_level1_solve(const double* L, const T* g, T* U, cudaStream_t s) {
+  k_level1_solve<T><<<1, 32, 0, s>>>(L, g, U);
+}
+template void launch_level1_solve<float>(const double*, const float*, float*, cudaStream_t);
+template void launch_level1_solve<double>(const double*, const double*, double*, cudaStream_t);
+
+// ---------------------------------------------------------------- outer float64
+__global__ void k_block_spmv64(const double* __restrict__ A, const int2* __restrict__ off,
+                               int noff, int Lpar, int64_t npar, const double* __restrict__ xv,
+                               double* yv) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npar) return;
+  int x, y;
+  demorton((uint32_t)p, x, y);
+  double y0 = 0, y1 = 0, y2 = 0, y3 = 0;
+  for (int o = 0; o < noff; ++o) {
+    const int q = shift_cell(x, y, off[o].x, off[o].y, Lpar);
+    if (q < 0) continue;
+    const double* b = A + ((int64_t)o * npar + p) * 16;
+    const double x0 = xv[4 * q], x1 = xv[4 * q + 1], x2 = xv[4 * q + 2], x3 = xv[4 * q + 3];
+    y0 += b[0] * x0 + b[1] * x1 + b[2] * x2 + b[3] * x3;
+    y1 += b[4] * x0 + b[5] * x1 + b[6] * x2 + b[7] * x3;
+    y2 += b[8] * x0 + b[9] * x1 + b[10] * x2 + b[11] * x3;
+    y3 += b[12] * x0 + b[13] * x1 + b[14] * x2 + b[15] * x3;
+  }
+  yv[4 * p] = y0;
+  yv[4 * p + 1] = y1;
+  yv[4 * p + 2] = y2;
+  yv[4 * p + 3] = y3;
+}
+
+void launch_block_spmv64(const double* Ahat, const int2* off, int noff, int Lpar, int64_t npar,
+                         const double* x, double* y, cudaStream_t s) {
+  if (npar <= 0) return;
+  k_block_spmv64<<<(unsigned)((npar + 127) / 128), 128, 0, s>>>(Ahat, off, noff, Lpar, npar, x, y);
+}
+
+__global__ void k_dots(int64_t n, const double* __restrict__ a0, const double* __restrict__ b0,
+                       const double* __restrict__ a1, const double* __restrict__ b1,
+                       const double* __restrict__ a2, const double* __restrict__ b2,
+                       double* dots) {
+  double s0 = 0, s1 = 0, s2 = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (a0) s0 += a0[i] * b0[i];
+    if (a1) s1 += a1[i] * b1[i];
+    if (a2) s2 += a2[i] * b2[i];
+  }
+  if (a0) block_atomic_add(s0, &dots[0]);
+  if (a1) block_atomic_add(s1, &dots[1]);
+  if (a2) block_atomic_add(s2, &dots[2]);
+}
+
+void launch_dots(int64_t n, const double* a0, const double* b0, const double* a1,
+                 const double* b1, const double* a2, const double* b2, double* dots,
+                 cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_dots<<<(unsigned)blocks, 256, 0, s>>>(n, a0, b0, a1, b1, a2, b2, dots);
+}
+
+// y += sign * (num / den) * x
+__global__ void k_axpy(int64_t n, const double* __restrict__ num, const double* __restrict__ den,
+                       double sign, const double* __restrict__ x, double* y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double d = *den;
+  const double a = d != 0.0 ? sign * (*num) / d : 0.0;
+  y[i] += a * x[i];
+}
+void launch_axpy(int64_t n, const double* alpha_num, const double* alpha_den, double sign,
+                 const double* x, double* y, cudaStream_t s) {
+  if (n > 0)
+    k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, alpha_num, alpha_den, sign, x, y);
+}
+// p = x + sign * (num / den) * p
+__global__ void k_xpby(int64_t n, const double* __restrict__ x, const double* __restrict__ num,
+                       const double* __restrict__ den, double sign, double* p) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double d = *den;
+  const double b = d != 0.0 ? sign * (*num) / d : 0.0;
+  p[i] = x[i] + b * p[i];
+}
+void launch_xpby(int64_t n, const double* x, const double* beta_num, const double* beta_den,
+                 double sign, double* p, cudaStream_t s) {
+  if (n > 0)
+    k_xpby<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, beta_num, beta_den, sign, p);
+}
+
+// ---------------------------------------------------------------- adjoint contraction
+__constant__ double c_Kref[16];
+
+void launch_set_kref(const double* K_ref_host) {
+  cudaMemcpyToSymbol(c_Kref, K_ref_host, 16 * sizeof(double));
+}
+
+__global__ void k_adjoint_contract(int ncell, const int32_t* __restrict__ cn,
+                                   const double* __restrict__ a, const double* __restrict__ lam,
+                                   const double* __restrict__ u, double* dJ) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  double lv[4], uv[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int nd = cn[4 * c + p];
+    lv[p] = nd >= 0 ? lam[nd] : 0.0;
+    uv[p] = nd >= 0 ? u[nd] : 0.0;
+  }
+  double s = 0;
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) s += lv[p] * c_Kref[p * 4 + r] * uv[r];
+  dJ[c] = -a[c] * s;
+}
+
+void launch_adjoint_contract(int ncell, const int32_t* cell_nodes, const double* cell_a,
+                             const double* lam, const double* u, double* dJ, cudaStream_t s) {
+  if (ncell > 0)
+    k_adjoint_contract<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, cell_nodes, cell_a, lam, u, dJ);
+}
+
+}  // namespace gb

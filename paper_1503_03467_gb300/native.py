@@ -1,0 +1,202 @@
+"""ctypes binding of libgamblet.so (include/gamblet.h), argument marshalling
+only: every step of the method runs in the library's CUDA kernels.
+
+Array arguments may be torch tensors (CPU or CUDA) or NumPy arrays; they must
+be contiguous and of the dtype the C ABI names (int32 indices, float64
+values).  Failures raise GambletError carrying the library's status code and
+message.  Importing this module loads the library and raises if it has not
+been built: there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgamblet.so")
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_NOT_SPD = 2
+ERR_NOT_CONVERGED = 3
+ERR_CUDA = 4
+ERR_OUT_OF_MEMORY = 5
+ERR_UNSUPPORTED = 6
+FP64 = 0
+MIXED = 1
+
+
+class GambletError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p),
+                ("val", ctypes.c_void_p)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("nbr_rule", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("level_tol", ctypes.c_double),
+                ("level_max_iter", ctypes.c_int32), ("refine_tol", ctypes.c_double),
+                ("refine_max_iter", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("q", ctypes.c_int32),
+                ("outer_iters", ctypes.c_int32), ("level_iters", ctypes.c_int32 * 32),
+                ("rel_residual", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {"status": self.status, "q": self.q, "outer_iters": self.outer_iters,
+                "level_iters": list(self.level_iters)[: self.q + 1],
+                "rel_residual": self.rel_residual, "setup_ms": self.setup_ms,
+                "solve_ms": self.solve_ms}
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "gamblet_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "gamblet_setup": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.c_int32, ctypes.c_void_p,
+                                     ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "gamblet_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.POINTER(Info)]),
+    "gamblet_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Info)]),
+    "gamblet_level_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    "gamblet_get_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gamblet_device_bytes": (ctypes.c_int64, [ctypes.c_void_p]),
+    "gamblet_destroy": (None, [ctypes.c_void_p]),
+    "gamblet_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
+    "gamblet_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build it with `python -m paper_1503_03467_gb300.build` "
+            "(nvcc, sm_103a); there is no fallback implementation")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = load()
+
+
+def _ptr(x, dtype=None):
+    if x is None:
+        return None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if not x.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            if dtype is not None and x.dtype != {np.int32: torch.int32,
+                                                 np.float64: torch.float64}[dtype]:
+                raise TypeError(f"expected {dtype}, got {x.dtype}")
+            return ctypes.c_void_p(x.data_ptr())
+    except ImportError:  # pragma: no cover
+        pass
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if dtype is not None and x.dtype != dtype:
+            raise TypeError(f"expected {np.dtype(dtype)}, got {x.dtype}")
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _check(st: int) -> int:
+    if st not in (OK, ERR_NOT_CONVERGED):
+        raise GambletError(st, _lib.gamblet_last_error().decode())
+    return st
+
+
+def gamblet_default_opts() -> Opts:
+    o = Opts()
+    _lib.gamblet_default_opts(ctypes.byref(o))
+    return o
+
+
+def gamblet_setup(rowptr, colind, val, q: int, cells, opts: Opts | None = None) -> int:
+    n = int(rowptr.shape[0]) - 1
+    csr = Csr(n, int(colind.shape[0]), _ptr(rowptr, np.int32), _ptr(colind, np.int32),
+              _ptr(val, np.float64))
+    h = ctypes.c_void_p()
+    st = _lib.gamblet_setup(ctypes.byref(csr), int(q), _ptr(cells, np.int32),
+                            ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    _check(st)
+    return h.value
+
+
+def gamblet_solve(h: int, g, u, components=None, info: Info | None = None) -> int:
+    info = info if info is not None else Info()
+    st = _lib.gamblet_solve(ctypes.c_void_p(h), _ptr(g, np.float64), _ptr(u, np.float64),
+                            _ptr(components, np.float64), ctypes.byref(info))
+    return _check(st)
+
+
+def gamblet_grad(h: int, cell_nodes, cell_a, K_ref, u, u_obs, dJ,
+                 info: Info | None = None) -> float:
+    info = info if info is not None else Info()
+    J = ctypes.c_double()
+    ncell = int(cell_a.shape[0])
+    st = _lib.gamblet_grad(ctypes.c_void_p(h), ncell, _ptr(cell_nodes, np.int32),
+                           _ptr(cell_a, np.float64), _ptr(K_ref, np.float64),
+                           _ptr(u, np.float64), _ptr(u_obs, np.float64), _ptr(dJ, np.float64),
+                           ctypes.byref(J), ctypes.byref(info))
+    _check(st)
+    return J.value
+
+
+def gamblet_level_size(h: int, k: int) -> tuple[int, int]:
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.gamblet_level_size(ctypes.c_void_p(h), int(k), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def gamblet_get_operator(h: int, which: int, k: int):
+    """COO triplets (rows, cols, vals) of A^(k) (0), R^(k-1,k) (1), B^(k) (2)."""
+    nnz = ctypes.c_int64()
+    _check(_lib.gamblet_get_operator(ctypes.c_void_p(h), int(which), int(k), 0,
+                                     ctypes.byref(nnz), None, None, None))
+    r = np.zeros(nnz.value, dtype=np.int32)
+    c = np.zeros(nnz.value, dtype=np.int32)
+    v = np.zeros(nnz.value, dtype=np.float64)
+    _check(_lib.gamblet_get_operator(ctypes.c_void_p(h), int(which), int(k), nnz.value,
+                                     ctypes.byref(nnz), _ptr(r), _ptr(c), _ptr(v)))
+    return r, c, v
+
+
+def gamblet_device_bytes(h: int) -> int:
+    return int(_lib.gamblet_device_bytes(ctypes.c_void_p(h)))
+
+
+def gamblet_destroy(h: int) -> None:
+    _lib.gamblet_destroy(ctypes.c_void_p(h))
+
+
+def gamblet_status_string(st: int) -> str:
+    return _lib.gamblet_status_string(int(st)).decode()
+
+
+def gamblet_last_error() -> str:
+    return _lib.gamblet_last_error().decode()

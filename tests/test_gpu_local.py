@@ -1,0 +1,146 @@
+"""GPU parity of the localized transform (Algorithm 2 with Definition defb)
+against the CPU oracle, and of the refined solution against the direct solve."""
+import numpy as np
+import pytest
+
+from oracle import direct
+from oracle.local import gamblet_local_setup, gamblet_local_solve
+from workloads import make_problem
+
+from gpu_util import coo_to_dense, csr_arrays, drop_nodes, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(A, cells, q, rho, rule=0, precision=0, refine=0, level_tol=1e-14):
+    from paper_1503_03467_gb300 import native as nv
+    rp, ci, va = csr_arrays(A)
+    o = nv.gamblet_default_opts()
+    o.rho = rho
+    o.nbr_rule = rule
+    o.precision = precision
+    o.refine_max_iter = refine
+    o.level_tol = level_tol
+    o.level_max_iter = 5000
+    return nv.gamblet_setup(rp, ci, va, q, cells, o)
+
+
+def _ops(h, q):
+    from paper_1503_03467_gb300 import native as nv
+    out = {}
+    for k in range(1, q + 1):
+        nk, _ = nv.gamblet_level_size(h, k)
+        out[("A", k)] = coo_to_dense(*nv.gamblet_get_operator(h, 0, k), (nk, nk))
+        if k >= 2:
+            nkm1, _ = nv.gamblet_level_size(h, k - 1)
+            out[("R", k)] = coo_to_dense(*nv.gamblet_get_operator(h, 1, k), (nkm1, nk))
+    return out
+
+
+CASES = [(32, 1e4, 0, 3.0, 0), (64, 1e4, 1, 3.0, 0), (32, 1e2, 2, 2.0, 0),
+         (32, 1e3, 3, 3.0, 1), (64, 1e6, 5, 1.0, 0)]
+
+
+@pytest.mark.parametrize("n,C,seed,rho,rule", CASES)
+def test_local_operators_and_one_pass(n, C, seed, rho, rule):
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(n, C, seed)
+    ref = gamblet_local_setup(p.A, p.cells, p.q, rho, "euclid" if rule == 0 else "cheb")
+    one = gamblet_local_solve(ref, p.g)
+    h = _setup(p.A, p.cells, p.q, rho, rule)
+    try:
+        ops = _ops(h, p.q)
+        for k in range(2, p.q + 1):
+            assert rel(ops[("R", k)], ref["R"][k]) < 1e-10, ("R", k)
+            assert rel(ops[("A", k - 1)], ref["A"][k - 1]) < 1e-10, ("A", k - 1)
+        u = np.zeros(p.ndof)
+        st = nv.gamblet_solve(h, p.g, u)
+        assert st == nv.OK
+        assert rel(u, one["u"]) < 1e-9
+    finally:
+        nv.gamblet_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_refined_solution_matches_direct(precision):
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(64, 1e4, 7)
+    ud, _ = direct.solve(p.A, p.g)
+    h = _setup(p.A, p.cells, p.q, 3.0, precision=precision, refine=50, level_tol=1e-6)
+    try:
+        u = np.zeros(p.ndof)
+        info = nv.Info()
+        st = nv.gamblet_solve(h, p.g, u, None, info)
+        assert st == nv.OK
+        assert info.rel_residual < 1e-12
+        assert rel(u, ud) < 1e-9
+    finally:
+        nv.gamblet_destroy(h)
+
+
+def test_local_ragged_domain():
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(32, 1e3, 8)
+    x, y = p.cells[:, 0], p.cells[:, 1]
+    keep = ~((x >= 10) & (x <= 17) & (y >= 12) & (y <= 14)) & ~((x == 3) & (y == 29))
+    A, g, cells = drop_nodes(p, keep)
+    ref = gamblet_local_setup(A, cells, p.q, 3.0)
+    one = gamblet_local_solve(ref, g)
+    h = _setup(A, cells, p.q, 3.0)
+    try:
+        ops = _ops(h, p.q)
+        for k in range(2, p.q + 1):
+            assert rel(ops[("R", k)], ref["R"][k]) < 1e-10
+            assert rel(ops[("A", k - 1)], ref["A"][k - 1]) < 1e-10
+        u = np.zeros(A.shape[0])
+        assert nv.gamblet_solve(h, g, u) == nv.OK
+        assert rel(u, one["u"]) < 1e-9
+    finally:
+        nv.gamblet_destroy(h)
+
+
+def test_device_pointers_and_torch_tensors():
+    import torch
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(32, 1e4, 9)
+    rp, ci, va = csr_arrays(p.A)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.from_numpy(a).to(dev)
+    o = nv.gamblet_default_opts()
+    o.rho = 3.0
+    o.refine_max_iter = 30
+    o.level_tol = 1e-6
+    h = nv.gamblet_setup(t(rp), t(ci), t(va), p.q, t(np.ascontiguousarray(p.cells)), o)
+    try:
+        g = t(p.g)
+        u = torch.zeros_like(g)
+        assert nv.gamblet_solve(h, g, u) == nv.OK
+        ud, _ = direct.solve(p.A, p.g)
+        assert rel(u.cpu().numpy(), ud) < 1e-9
+    finally:
+        nv.gamblet_destroy(h)
+
+
+def test_invalid_inputs_are_rejected():
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(8, 10, 0)
+    rp, ci, va = csr_arrays(p.A)
+    cells = p.cells.copy()
+    cells[1] = cells[0]
+    with pytest.raises(nv.GambletError) as e:
+        nv.gamblet_setup(rp, ci, va, p.q, cells)
+    assert e.value.status == nv.ERR_INVALID_ARG
+    bad = p.cells.copy()
+    bad[0, 0] = 1 << p.q
+    with pytest.raises(nv.GambletError) as e:
+        nv.gamblet_setup(rp, ci, va, p.q, bad)
+    assert e.value.status == nv.ERR_INVALID_ARG
+    ci2 = ci.copy()
+    ci2[3] = 10 ** 6
+    with pytest.raises(nv.GambletError) as e:
+        nv.gamblet_setup(rp, ci2, va, p.q, p.cells)
+    assert e.value.status == nv.ERR_INVALID_ARG
+    # an indefinite operator meets a non-positive pivot
+    with pytest.raises(nv.GambletError) as e:
+        nv.gamblet_setup(rp, ci, -va, p.q, p.cells)
+    assert e.value.status == nv.ERR_NOT_SPD

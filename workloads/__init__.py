@@ -11,6 +11,7 @@ from .rough import (  # noqa: F401
     Problem,
     K_REF,
     assemble_q1,
+    cell_corner_dofs,
     example1_coefficient,
     example1_rhs,
     make_problem,

@@ -138,3 +138,18 @@ def example1_rhs(q: int = 6) -> np.ndarray:
     z1 = (i / n).ravel()
     z2 = (j / n).ravel()
     return np.cos(3 * z1 + z2) + np.sin(3 * z2) + np.sin(7 * z1 - 5 * z2)
+
+
+def cell_corner_dofs(n: int) -> np.ndarray:
+    """(n*n) x 4 int32 fine unknown of each cell corner (counter-clockwise
+    from (cx, cy), the K_REF order), -1 on the Dirichlet boundary; cells in
+    row-major (cy, cx) order, matching ``log_a.ravel()``."""
+    m = n - 1
+    cy, cx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    cy = cy.ravel()
+    cx = cx.ravel()
+    out = np.full((n * n, 4), -1, dtype=np.int32)
+    for p, (xp, yp) in enumerate([(cx, cy), (cx + 1, cy), (cx + 1, cy + 1), (cx, cy + 1)]):
+        ok = (xp >= 1) & (xp <= m) & (yp >= 1) & (yp <= m)
+        out[ok, p] = (yp[ok] - 1) * m + (xp[ok] - 1)
+    return out
