@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the gamblet setup + solve hot path on GB300.
+
+Metric: fine DOFs per second of one full pass (gamblet_setup + gamblet_solve
+with float64 refinement to the stated tolerance) on the 1024 x 1024 Q1
+rough-coefficient problem (1,046,529 unknowns, q = 10, rho = 3, contrast
+1e4, seed = rank).  The headline value is the mixed-precision path; the plain
+float64 path is measured beside it, and both must reach a relative error
+<= 1e-8 against the refined direct solve of the CPU oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gamblet|reference]
+
+Under torchrun (N > 1) every rank solves its own independent problem (weak
+scaling, no data-path collective); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fine DOFs/s setup+solve at 2^20 DOF: batched/mixed vs plain FP64, rel err <=1e-8"
+UNIT = "DOF/s"
+REL_ERR_BAR = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gamblet", choices=["gamblet", "reference"])
+    ap.add_argument("--size", type=int, default=1024, help="cells per side (power of two)")
+    ap.add_argument("--contrast", type=float, default=1e4)
+    ap.add_argument("--rho", type=float, default=3.0)
+    ap.add_argument("--level-tol", type=float, default=1e-4)
+    ap.add_argument("--refine-tol", type=float, default=1e-12)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain float64 arm")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_name(a):
+    return (f"{a.size}x{a.size} Q1 rough coefficient, q={int(np.log2(a.size))}, rho={a.rho:g} "
+            f"(Euclidean), contrast {a.contrast:g}, g~N(0,1)")
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except OSError:
+            rows = []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if self.path:
+            os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        load = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def ncu_traffic(kernel: str):
+    """Per-launch DRAM traffic of `kernel` from the committed ncu summary, or
+    None when absent or taken on a different version of the kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if sha != rec.get("source_sha"):
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def make_inputs(a, rank):
+    from workloads import make_problem
+    p = make_problem(a.size, a.contrast, seed=rank)
+    A = p.A.tocsr()
+    A.sort_indices()
+    host = {
+        "rowptr": np.ascontiguousarray(A.indptr, dtype=np.int32),
+        "colind": np.ascontiguousarray(A.indices, dtype=np.int32),
+        "val": np.ascontiguousarray(A.data, dtype=np.float64),
+        "cells": np.ascontiguousarray(p.cells, dtype=np.int32),
+        "g": np.ascontiguousarray(p.g, dtype=np.float64),
+    }
+    return p, host
+
+
+def opts_for(nv, a, precision, stream_ptr, profile):
+    o = nv.gamblet_default_opts()
+    o.rho = a.rho
+    o.nbr_rule = 0
+    o.precision = precision
+    o.level_tol = a.level_tol
+    o.level_max_iter = 2000
+    o.refine_tol = a.refine_tol
+    o.refine_max_iter = 100
+    o.profile = profile
+    o.stream = stream_ptr
+    return o
+
+
+def run_arm(nv, torch, a, dev_in, precision, steps, warmup, stream, flush, clocks_dev=None):
+    """Times `steps` setup+solve passes on device-resident inputs."""
+    ndof = int(dev_in["g"].shape[0])
+    q = int(np.log2(a.size))
+    o = opts_for(nv, a, precision, stream.cuda_stream, 1)
+    u = torch.zeros(ndof, dtype=torch.float64, device=dev_in["g"].device)
+    times, setup_ms, solve_ms, infos, stats = [], [], [], [], {}
+    clk = None
+    launches0 = None
+    for it in range(warmup + steps):
+        timed = it >= warmup
+        if timed and it == warmup and clocks_dev is not None:
+            clk = Clocks(clocks_dev).__enter__()
+        if timed and launches0 is None:
+            launches0 = nv.gamblet_kernel_launches()
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            h = nv.gamblet_setup(dev_in["rowptr"], dev_in["colind"], dev_in["val"], q,
+                                 dev_in["cells"], o)
+            info = nv.Info()
+            nv.gamblet_solve(h, dev_in["g"], u, None, info)
+            e1.record(stream)
+        e1.synchronize()
+        if timed:
+            times.append(e0.elapsed_time(e1))
+            setup_ms.append(info.setup_ms)
+            solve_ms.append(info.solve_ms)
+            infos.append(info.as_dict())
+            for st in nv.gamblet_kernel_stats(h):
+                acc = stats.setdefault(st["name"], {"launches": 0, "ms": 0.0, "bytes": 0.0,
+                                                    "flops": 0.0})
+                for key in ("launches", "ms", "bytes", "flops"):
+                    acc[key] += st[key]
+        nv.gamblet_destroy(h)
+    launches = nv.gamblet_kernel_launches() - launches0
+    clocks = None
+    if clk is not None:
+        clk.__exit__(None, None, None)
+        clocks = clk.summary()
+    return {"times_ms": times, "setup_ms": setup_ms, "solve_ms": solve_ms, "infos": infos,
+            "stats": stats, "u": u.cpu().numpy(), "launches": launches, "clocks": clocks}
+
+
+def run_e2e(nv, a, host, precision, steps):
+    """setup + solve through the C ABI with host buffers (copies inside)."""
+    q = int(np.log2(a.size))
+    o = opts_for(nv, a, precision, None, 0)
+    u = np.zeros_like(host["g"])
+    times = []
+    for it in range(steps + 1):
+        t0 = time.perf_counter()
+        h = nv.gamblet_setup(host["rowptr"], host["colind"], host["val"], q, host["cells"], o)
+        nv.gamblet_solve(h, host["g"], u)
+        t1 = time.perf_counter()
+        nv.gamblet_destroy(h)
+        if it > 0:
+            times.append((t1 - t0) * 1e3)
+    h2d = sum(host[k].nbytes for k in ("rowptr", "colind", "val", "cells", "g"))
+    return {"ms": statistics.mean(times), "h2d": h2d, "d2h": u.nbytes, "u": u}
+
+
+def cpu_oracle(p):
+    """The oracle's direct solve (SuperLU + extended-precision refinement)."""
+    from oracle import direct
+    t0 = time.perf_counter()
+    u, _ = direct.solve(p.A, p.g)
+    return u, time.perf_counter() - t0
+
+
+def rel_err(u, ud):
+    return float(np.linalg.norm(u - ud) / np.linalg.norm(ud))
+
+
+def roofline(stats, peaks, clocks, mixed):
+    """Roofline entry of the kernel with the largest share of device time."""
+    name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
+    avg_ms = st["ms"] / max(st["launches"], 1)
+    per_launch_bytes = st["bytes"] / max(st["launches"], 1)
+    per_launch_flops = st["flops"] / max(st["launches"], 1)
+    total_ms = sum(s["ms"] for s in stats.values())
+    if name == "patch_solve":
+        # SIMT arithmetic bound: 152 SMs x 128 lanes (fp32) or the nominal
+        # float64 rate, at the maximum SM clock
+        if mixed:
+            peak = 152 * 128 * 2 * 2.070e9 / 1e12
+            src = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (nominal)"
+        else:
+            peak = 1.25
+            src = "nominal GB300 float64 rate"
+        achieved = per_launch_flops / (avg_ms * 1e-3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src,
+                "traffic": ncu_traffic(name), "share_of_device_time": st["ms"] / total_ms}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+            else "fallback 6.8 TB/s", "traffic": ncu_traffic(name),
+            "share_of_device_time": st["ms"] / total_ms}
+
+
+def reference_main(a, ws, rank):
+    """--impl reference: the CPU oracle (direct solve) timed on host cores."""
+    if rank != 0:
+        return 0
+    from workloads import make_problem
+    p = make_problem(a.size, a.contrast, seed=0)
+    times = []
+    for it in range(a.warmup + a.steps):
+        _, t = cpu_oracle(p)
+        if it >= a.warmup:
+            times.append(t)
+    ms = statistics.mean(times) * 1e3
+    value = p.ndof / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": workload_name(a), "dofs": p.ndof},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "full 2^20-class problem: SuperLU factor + solve + 3 "
+                                   "extended-precision refinement steps, per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    a = parse()
+    ws, rank, local = dist_env()
+    if a.impl == "reference":
+        return reference_main(a, ws, rank)
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1503_03467_gb300 import build as _b
+    _b.build()
+    from paper_1503_03467_gb300 import native as nv
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    p, host = make_inputs(a, rank)
+    ndof = p.ndof
+    # oracle solution for the error bar (and the CPU baseline on rank 0, N = 1)
+    ud, cpu_s = cpu_oracle(p)
+    dev_in = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    if ws > 1:
+        dist.barrier()
+    mixed = run_arm(nv, torch, a, dev_in, nv.MIXED, a.steps, a.warmup, stream, flush,
+                    clocks_dev=torch.cuda.current_device())
+    plain = None
+    if not a.no_plain:
+        plain = run_arm(nv, torch, a, dev_in, nv.FP64, max(2, a.steps // 2), max(1, a.warmup // 2),
+                        stream, flush)
+    e2e = run_e2e(nv, a, host, nv.MIXED, a.e2e_steps)
+    ms = statistics.mean(mixed["times_ms"])
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        dist.barrier()
+    else:
+        ms_max = ms
+    err_mixed = rel_err(mixed["u"], ud)
+    err_e2e = rel_err(e2e["u"], ud)
+    value = ws * ndof / (ms_max * 1e-3)
+    peaks = load_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "dofs": ndof, "per_rank_problems": 1,
+                   "l2": "flushed between timed steps (256 MiB device write)",
+                   "level_tol": a.level_tol, "refine_tol": a.refine_tol,
+                   "precision": "mixed: f32 patch Cholesky / Galerkin / level SpMV, "
+                                "f64 dots, coarsest solve and refinement"},
+        "rel_err": err_mixed, "rel_err_ok": err_mixed <= REL_ERR_BAR,
+        "setup_ms": statistics.mean(mixed["setup_ms"]),
+        "solve_ms": statistics.mean(mixed["solve_ms"]),
+        "outer_iters": mixed["infos"][-1]["outer_iters"],
+        "level_iters": mixed["infos"][-1]["level_iters"],
+        "gpu_launches": int(mixed["launches"]),
+        "e2e": {"value": ws * ndof / (e2e["ms"] * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(e2e["h2d"]), "d2h_bytes_per_step": int(e2e["d2h"]),
+                "rel_err": err_e2e},
+        "roofline": roofline(mixed["stats"], peaks, mixed["clocks"], True),
+        "clocks": mixed["clocks"],
+        "kernels": {k: {"share": v["ms"] / sum(s["ms"] for s in mixed["stats"].values()),
+                        "ms_per_step": v["ms"] / a.steps, "launches_per_step": v["launches"] / a.steps}
+                    for k, v in sorted(mixed["stats"].items(), key=lambda kv: -kv[1]["ms"])},
+    }
+    if plain is not None:
+        pms = statistics.mean(plain["times_ms"])
+        line["plain_fp64"] = {
+            "value": ndof / (pms * 1e-3), "ms_per_step": pms,
+            "setup_ms": statistics.mean(plain["setup_ms"]),
+            "solve_ms": statistics.mean(plain["solve_ms"]),
+            "rel_err": rel_err(plain["u"], ud), "outer_iters": plain["infos"][-1]["outer_iters"],
+            "roofline": roofline(plain["stats"], peaks, None, False)}
+        line["speedup_mixed_vs_plain"] = line["plain_fp64"]["ms_per_step"] / ms
+    if rank == 0 and ws == 1 and not a.no_cpu:
+        line["cpu_baseline"] = {"value": ndof / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "one full solve of the same problem: SuperLU factor + "
+                                          "solve + 3 extended-precision refinement steps"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -87,6 +87,8 @@ typedef struct {
   int32_t refine_max_iter;  /* cap on outer flexible-CG iterations; 0 = the
                                one-pass transform of Algorithm 2 only      */
   int32_t use_graph;        /* capture repeated launch sequences in CUDA graphs */
+  int32_t profile;          /* 1: time every kernel phase with CUDA events on
+                               the library's stream (gamblet_kernel_stats)  */
   void* stream;             /* cudaStream_t                                */
 } gamblet_opts;
 
@@ -104,7 +106,7 @@ typedef struct gamblet_ctx* gamblet_handle;
 
 /* Fill *opts with defaults: rho = 3, Euclidean rule, FP64, level_tol 1e-8,
  * level_max_iter 1000, refine_tol 1e-13, refine_max_iter 50, graphs on,
- * default stream. */
+ * profiling off, default stream. */
 GAMBLET_API void gamblet_default_opts(gamblet_opts* opts);
 
 /*
@@ -178,6 +180,26 @@ GAMBLET_API gamblet_status gamblet_level_size(gamblet_handle h, int32_t k, int32
  */
 GAMBLET_API gamblet_status gamblet_get_operator(gamblet_handle h, int32_t which, int32_t k, int64_t capacity,
                                     int64_t* nnz, int32_t* rows, int32_t* cols, double* vals);
+
+/* Per-kernel statistics accumulated since the handle was created or last
+ * reset, when opts.profile = 1: CUDA-event time on the library's stream, the
+ * number of launches, and the algorithmic bytes moved and flops performed
+ * (counted from the data the operation must read and write once, not from
+ * hardware counters).  Writes up to capacity entries; returns the number of
+ * entries available (call with capacity 0 to query). */
+typedef struct {
+  char name[48];
+  int64_t launches;
+  double ms;
+  double bytes;
+  double flops;
+} gamblet_kernel_stat;
+GAMBLET_API int32_t gamblet_kernel_stats(gamblet_handle h, gamblet_kernel_stat* out,
+                                         int32_t capacity);
+GAMBLET_API void gamblet_reset_kernel_stats(gamblet_handle h);
+
+/* Total CUDA kernel launches issued by this library in this process. */
+GAMBLET_API int64_t gamblet_kernel_launches(void);
 
 /* Device bytes held by the handle. */
 GAMBLET_API int64_t gamblet_device_bytes(gamblet_handle h);

@@ -19,6 +19,10 @@
 
 namespace gb {
 
+// Counts every kernel launch issued by the library (reported by
+// gamblet_kernel_launches() so a caller can attribute GPU work to it).
+void count_launch();
+
 __host__ __device__ __forceinline__ int __popc_portable(unsigned v) {
 #ifdef __CUDA_ARCH__
   return __popc(v);

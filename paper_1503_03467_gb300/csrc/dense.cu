@@ -28,7 +28,7 @@ void launch_dense_from_blocks(const double* blk, const int2* off, int noff, int 
                               int64_t npar, double* D, cudaStream_t s) {
   const int64_t n = (int64_t)noff * npar;
   if (n > 0)
-    k_dense_from_blocks<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blk, off, noff, Lpar, npar, D);
+    { count_launch(); k_dense_from_blocks<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blk, off, noff, Lpar, npar, D); }
 }
 
 // Blockwise transform of a dense level matrix: D <- Qblk D Qblk^T.
@@ -61,7 +61,7 @@ __global__ void k_dense_transform(const double* __restrict__ in, int64_t npar,
 void launch_dense_transform(const double* in, int64_t npar, const uint32_t* pmask, double* out,
                             cudaStream_t s) {
   const int64_t n = npar * npar;
-  if (n > 0) k_dense_transform<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(in, npar, pmask, out);
+  if (n > 0) { count_launch(); k_dense_transform<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(in, npar, pmask, out); }
 }
 
 // C = alpha op(A) op(B) + beta C, row-major, 16 x 16 shared-memory tiles.
@@ -100,10 +100,10 @@ void launch_dgemm_t(int m, int n, int kk, double alpha, const double* A, int tra
                     const double* B, int transB, double beta, double* C, cudaStream_t s) {
   if (m <= 0 || n <= 0) return;
   dim3 blk(16, 16), grd((n + 15) / 16, (m + 15) / 16);
-  if (!transA && !transB) k_dgemm<0, 0><<<grd, blk, 0, s>>>(m, n, kk, alpha, A, B, beta, C);
-  else if (!transA && transB) k_dgemm<0, 1><<<grd, blk, 0, s>>>(m, n, kk, alpha, A, B, beta, C);
-  else if (transA && !transB) k_dgemm<1, 0><<<grd, blk, 0, s>>>(m, n, kk, alpha, A, B, beta, C);
-  else k_dgemm<1, 1><<<grd, blk, 0, s>>>(m, n, kk, alpha, A, B, beta, C);
+  if (!transA && !transB) { count_launch(); k_dgemm<0, 0><<<grd, blk, 0, s>>>(m, n, kk, alpha, A, B, beta, C); }
+  else if (!transA && transB) { count_launch(); k_dgemm<0, 1><<<grd, blk, 0, s>>>(m, n, kk, alpha, A, B, beta, C); }
+  else if (transA && !transB) { count_launch(); k_dgemm<1, 0><<<grd, blk, 0, s>>>(m, n, kk, alpha, A, B, beta, C); }
+  else { count_launch(); k_dgemm<1, 1><<<grd, blk, 0, s>>>(m, n, kk, alpha, A, B, beta, C); }
 }
 
 void launch_dgemm(int m, int n, int kk, double alpha, const double* A, const double* B,
@@ -139,7 +139,7 @@ __global__ void k_dpotrf(double* A, int n, int* status) {
 }
 
 void launch_dpotrf(double* A, int n, int* status, cudaStream_t s) {
-  if (n > 0) k_dpotrf<<<1, 1024, 0, s>>>(A, n, status);
+  if (n > 0) { count_launch(); k_dpotrf<<<1, 1024, 0, s>>>(A, n, status); }
 }
 
 // Solve L L^T x = b for column `col` of B (n x nrhs row-major); one warp per column.
@@ -170,7 +170,7 @@ void launch_dpotrs(const double* L, int n, double* B, int nrhs, cudaStream_t s) 
   if (n <= 0 || nrhs <= 0) return;
   size_t smem = sizeof(double) * (size_t)n;
   cudaFuncSetAttribute(k_dpotrs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_dpotrs<<<nrhs, 32, smem, s>>>(L, n, B, nrhs);
+  { count_launch(); k_dpotrs<<<nrhs, 32, smem, s>>>(L, n, B, nrhs); }
 }
 
 // out[a][b] = D[rows[a]][cols[b]] * alpha * (col_scale ? col_scale[b] : 1)
@@ -190,8 +190,8 @@ void launch_gather_rows_cols(const double* D, int ld, const int32_t* rows, int n
                              const double* col_scale, double* out, cudaStream_t s) {
   const int64_t n = (int64_t)nr * nc;
   if (n > 0)
-    k_gather_rc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(D, ld, rows, nr, cols, nc, alpha_scale,
-                                                            col_scale, out);
+    { count_launch(); k_gather_rc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(D, ld, rows, nr, cols, nc, alpha_scale,
+                                                            col_scale, out); }
 }
 
 // Rhat dense (npar x nslot): Rhat[par_b][det_a] = Y[a][b], Rhat[p][4p+3] = 1/sqrt(m_p).
@@ -215,7 +215,7 @@ void launch_dense_rhat(const double* Y, const int32_t* det, int nJ, const int32_
   int64_t n = (int64_t)nJ * nA;
   if (n < npar) n = npar;
   if (n > 0)
-    k_dense_rhat<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, det, nJ, par, nA, pmask, npar, Rh);
+    { count_launch(); k_dense_rhat<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Y, det, nJ, par, nA, pmask, npar, Rh); }
 }
 
 // Scatter a compact detail vector into AoS4 slots (others 0) and gather back.
@@ -225,7 +225,7 @@ __global__ void k_scatter_det(const double* __restrict__ wc, const int32_t* __re
   if (a < nJ) w[det[a]] = wc[a];
 }
 void launch_scatter_det(const double* wc, const int32_t* det, int nJ, double* w, cudaStream_t s) {
-  if (nJ > 0) k_scatter_det<<<(nJ + 255) / 256, 256, 0, s>>>(wc, det, nJ, w);
+  if (nJ > 0) { count_launch(); k_scatter_det<<<(nJ + 255) / 256, 256, 0, s>>>(wc, det, nJ, w); }
 }
 __global__ void k_gather_det(const double* __restrict__ w, const int32_t* __restrict__ det, int nJ,
                              double* wc) {
@@ -233,7 +233,7 @@ __global__ void k_gather_det(const double* __restrict__ w, const int32_t* __rest
   if (a < nJ) wc[a] = w[det[a]];
 }
 void launch_gather_det(const double* w, const int32_t* det, int nJ, double* wc, cudaStream_t s) {
-  if (nJ > 0) k_gather_det<<<(nJ + 255) / 256, 256, 0, s>>>(w, det, nJ, wc);
+  if (nJ > 0) { count_launch(); k_gather_det<<<(nJ + 255) / 256, 256, 0, s>>>(w, det, nJ, wc); }
 }
 
 // Level-1 factor from a dense 4 x 4 (float64); zero rows become identity.
@@ -264,7 +264,7 @@ __global__ void k_level1_factor_dense(const double* __restrict__ A, double* L, i
   for (int e = 0; e < 16; ++e) L[e] = M[e];
 }
 void launch_level1_factor_dense(const double* A, double* L, int* status, cudaStream_t s) {
-  k_level1_factor_dense<<<1, 32, 0, s>>>(A, L, status);
+  { count_launch(); k_level1_factor_dense<<<1, 32, 0, s>>>(A, L, status); }
 }
 
 }  // namespace gb

@@ -79,7 +79,7 @@ void launch_galerkin(const T* Ahat, const T* Rhat, const uint32_t* pmask_k, Gale
   size_t smem = sizeof(T) * 4 * ((size_t)g.NB + (size_t)g.nwin);
   cudaFuncSetAttribute(k_galerkin<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int64_t grid = g.nrow < 65535 * 16 ? g.nrow : 65535 * 16;
-  k_galerkin<T><<<(unsigned)grid, 256, smem, s>>>(Ahat, Rhat, pmask_k, g, Aout);
+  { count_launch(); k_galerkin<T><<<(unsigned)grid, 256, smem, s>>>(Ahat, Rhat, pmask_k, g, Aout); }
 }
 template void launch_galerkin<float>(const float*, const float*, const uint32_t*, GalerkinGeom,
                                      float*, cudaStream_t);
@@ -138,8 +138,8 @@ void launch_cells_to_blocks(const T* Acell, int64_t ncell, const int* map, int n
                             T* blk, cudaStream_t s) {
   int64_t n = (int64_t)nO * npar;
   if (n <= 0) return;
-  k_cells_to_blocks<T><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(Acell, ncell, map, nO, Ooff,
-                                                                   Lpar, npar, pmask, blk);
+  { count_launch(); k_cells_to_blocks<T><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(Acell, ncell, map, nO, Ooff,
+                                                                   Lpar, npar, pmask, blk); }
 }
 template void launch_cells_to_blocks<float>(const float*, int64_t, const int*, int, const int2*,
                                             int, int64_t, const uint32_t*, float*, cudaStream_t);

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <functional>
 #include <cstdio>
@@ -33,6 +34,8 @@ namespace gb {
 // declared in dense.cu / solve.cu
 void launch_dense_transform(const double* in, int64_t npar, const uint32_t* pmask, double* out,
                             cudaStream_t s);
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace gb
 
 using namespace gb;
@@ -59,14 +62,17 @@ struct GbError {
   } while (0)
 
 // ---------------------------------------------------------------- device memory
+// Stream-ordered allocations from the device's default memory pool (kept
+// cached across handles, so a repeated setup does not pay for cudaMalloc).
 struct Pool {
   std::vector<void*> ptrs;
   int64_t bytes = 0;
+  cudaStream_t s = nullptr;
   template <typename T>
   T* alloc(int64_t n) {
     if (n <= 0) n = 1;
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, sizeof(T) * (size_t)n);
+    cudaError_t e = cudaMallocAsync(&p, sizeof(T) * (size_t)n, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       fail(GAMBLET_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(sizeof(T) * n) + " bytes");
@@ -88,7 +94,7 @@ struct Pool {
     return p;
   }
   void release() {
-    for (void* p : ptrs) cudaFree(p);
+    for (void* p : ptrs) cudaFreeAsync(p, s);
     ptrs.clear();
     bytes = 0;
   }
@@ -194,9 +200,84 @@ struct LevelDev {
   double* wc = nullptr;  // compact detail vector (exact path)
 };
 
+// Per-kernel CUDA-event timing on the library's stream (opts.profile).
+struct Prof {
+  struct Stat {
+    std::string name;
+    long long launches = 0;
+    double ms = 0, bytes = 0, flops = 0;
+  };
+  struct Pend {
+    int id;
+    cudaEvent_t a, b;
+    double bytes, flops;
+  };
+  bool on = false;
+  std::vector<Stat> stats;
+  std::vector<Pend> pend;
+  std::vector<cudaEvent_t> pool;
+  int id(const std::string& name) {
+    for (size_t i = 0; i < stats.size(); ++i)
+      if (stats[i].name == name) return (int)i;
+    stats.push_back(Stat{name});
+    return (int)stats.size() - 1;
+  }
+  cudaEvent_t ev() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    return e;
+  }
+  // returns a token for end(); -1 when profiling is off
+  int begin(const std::string& name, double bytes, double flops, cudaStream_t s) {
+    if (!on) return -1;
+    Pend p{id(name), ev(), ev(), bytes, flops};
+    CK(cudaEventRecord(p.a, s));
+    pend.push_back(p);
+    return (int)pend.size() - 1;
+  }
+  void end(int tok, cudaStream_t s) {
+    if (tok < 0) return;
+    CK(cudaEventRecord(pend[tok].b, s));
+  }
+  // call after the stream has been synchronised
+  void resolve() {
+    for (Pend& p : pend) {
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, p.a, p.b));
+      Stat& st = stats[p.id];
+      st.launches += 1;
+      st.ms += ms;
+      st.bytes += p.bytes;
+      st.flops += p.flops;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pend.clear();
+  }
+  void add(const std::string& name, double bytes, double flops) {
+    if (!on) return;
+    Stat& st = stats[id(name)];
+    st.bytes += bytes;
+    st.flops += flops;
+  }
+  ~Prof() {
+    for (Pend& p : pend) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
 }  // namespace
 
 struct gamblet_ctx {
+  Prof prof;
   gamblet_opts opts;
   cudaStream_t s = nullptr;
   int q = 0;
@@ -416,6 +497,29 @@ void import_fine(gamblet_ctx* h, const gamblet_csr* A) {
   L.Ahat64 = blk;
 }
 
+// Algorithmic flops of the level-k patch solves: for a patch with n active
+// unknowns, n^3/3 (Cholesky, right-hand side carried along) + 2 n^2 (the two
+// triangular sweeps), multiply-adds counted as two flops.
+double patch_flops(gamblet_ctx* h, int k) {
+  const LevelDev& L = h->lv[k];
+  const int Lpar = 1 << (k - 1);
+  double f = 0;
+  for (int64_t i = 0; i < L.npar; ++i) {
+    if (!(L.pmask_h[i] & 15u)) continue;
+    int x, y;
+    demorton((uint32_t)i, x, y);
+    double na = 0;
+    for (const int2& o : h->N.v) {
+      const int p = shift_cell(x, y, o.x, o.y, Lpar);
+      if (p < 0) continue;
+      const int m = __builtin_popcount(L.pmask_h[p] & 15u);
+      na += m > 0 ? m - 1 : 0;
+    }
+    f += 2.0 * (na * na * na / 6.0 + na * na / 2.0) + 2.0 * 2.0 * na * na / 2.0;
+  }
+  return f;
+}
+
 // ------------------------------------------------------------ localized setup
 template <typename T>
 void setup_local(gamblet_ctx* h) {
@@ -448,7 +552,11 @@ void setup_local(gamblet_ctx* h) {
     // patch solves -> Rhat^(k-1,k)
     T* Rhat = P.alloc<T>((int64_t)NB * 4 * L.npar);
     PatchGeom pg{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar};
+    const double sz = (double)sizeof(T);
+    int tok = h->prof.begin("patch_solve", sz * ((double)L.noff * L.npar * 16 + 4.0 * NB * L.npar),
+                            h->prof.on ? patch_flops(h, k) : 0.0, s);
     launch_patch_solve<T>((const T*)L.Ahat, L.pmask, pg, Rhat, h->status, h->num_sms, s);
+    h->prof.end(tok, s);
     CK(cudaGetLastError());
     L.Rhat = Rhat;
     // Galerkin product -> level k-1 cell stencil
@@ -468,7 +576,12 @@ void setup_local(gamblet_ctx* h) {
     if (sizeof(T) * 4 * ((size_t)NB + (size_t)gg.nwin) > 227 * 1024)
       fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin window exceeds shared memory");
     T* Acell = P.alloc<T>((int64_t)gg.nout * L.npar);
+    tok = h->prof.begin(
+        "galerkin",
+        sz * ((double)L.noff * L.npar * 16 + 4.0 * NB * L.npar + (double)gg.nout * L.npar),
+        2.0 * (16.0 * S.l1_pairs.size() + 4.0 * S.l2_pairs.size()) * h->lv[k - 1].n_active, s);
     launch_galerkin<T>((const T*)L.Ahat, Rhat, L.pmask, gg, Acell, s);
+    h->prof.end(tok, s);
     CK(cudaGetLastError());
     if (k - 1 >= 2) {
       LevelDev& Ln = h->lv[k - 1];
@@ -479,8 +592,11 @@ void setup_local(gamblet_ctx* h) {
       Ln.off = P.upload(Ln.off_h, s);
       int* dmap = P.upload(map, s);
       T* blk = P.alloc<T>((int64_t)Ln.noff * Ln.npar * 16);
+      tok = h->prof.begin("cells_to_blocks",
+                          sz * ((double)gg.nout * L.npar + (double)Ln.noff * Ln.npar * 16), 0.0, s);
       launch_cells_to_blocks<T>(Acell, L.npar, dmap, Ln.noff, Ln.off, 1 << (k - 2), Ln.npar,
                                 Ln.pmask, blk, s);
+      h->prof.end(tok, s);
       CK(cudaGetLastError());
       Ln.Ahat = blk;
       O = On;
@@ -637,9 +753,15 @@ void run_level_cg(gamblet_ctx* h) {
   const int chunk = 8;
   for (int it = 0; it < maxit; it += chunk) {
     CK(cudaMemsetAsync(h->any_active, 0, sizeof(int), s));
-    for (int c = 0; c < chunk; ++c)
-      launch_cg_iteration<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit,
-                             h->any_active, s);
+    for (int c = 0; c < chunk; ++c) {
+      int tok = h->prof.begin("level_cg_spmv", 0.0, 0.0, s);
+      launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, s);
+      h->prof.end(tok, s);
+      tok = h->prof.begin("level_cg_vector", 0.0, 0.0, s);
+      launch_cg_rest<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit, h->any_active,
+                        s);
+      h->prof.end(tok, s);
+    }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->any_active_h, h->any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -652,6 +774,13 @@ void run_level_cg(gamblet_ctx* h) {
   for (int l = 0; l < h->cg_nlev; ++l) {
     h->level_iters_acc[l + 2] += sc[l].iters;
     if (sc[l].rr > tol2 * sc[l].rr0) h->level_not_conv = true;
+    // algorithmic traffic: the 3x3 detail blocks of B^(k) once per iteration,
+    // p read, Ap written (3 active slots); vector kernels: x, r, p, Ap, r
+    const LevelDev& L = h->lv[l + 2];
+    const double sz = (double)sizeof(T), it = sc[l].iters;
+    h->prof.add("level_cg_spmv", it * sz * ((double)L.noff * L.npar * 9 + 6.0 * L.npar),
+                it * 2.0 * 9.0 * L.noff * L.npar);
+    h->prof.add("level_cg_vector", it * sz * 3.0 * L.npar * 8, it * 3.0 * L.npar * 6);
   }
 }
 
@@ -677,8 +806,12 @@ void apply_G(gamblet_ctx* h, const T* in, T* out, int inverse_last) {
         launch_transform_vec<T>(dst, dst, Ln.npar, Ln.pmask, +1, s);
       }
     } else {
+      const double sz = (double)sizeof(T);
+      int tok = h->prof.begin("restrict", sz * (4.0 * NB * L.npar + L.ncell + L.npar),
+                              8.0 * NB * L.npar, s);
       launch_restrict<T>((const T*)L.Rhat, NB, h->nbr, 1 << (k - 1), L.npar, (const T*)L.ghat, dst,
                          k - 1 >= 2 ? h->lv[k - 1].pmask : nullptr, s);
+      h->prof.end(tok, s);
     }
   }
   CK(cudaGetLastError());
@@ -708,8 +841,12 @@ void apply_G(gamblet_ctx* h, const T* in, T* out, int inverse_last) {
                      (double*)dst, s);
       if (inv) launch_transform_vec<T>(dst, dst, L.npar, L.pmask, -1, s);
     } else {
+      const double sz = (double)sizeof(T);
+      int tok = h->prof.begin("prolong", sz * (3.0 * NB * L.npar + 2.0 * L.ncell + L.npar),
+                              6.0 * NB * L.npar, s);
       launch_prolong<T>((const T*)L.Rhat, NB, h->nbr, 1 << (k - 1), L.npar, vprev, (const T*)L.w,
                         L.pmask, inv, dst, s);
+      h->prof.end(tok, s);
     }
   }
   CK(cudaGetLastError());
@@ -765,6 +902,7 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
                           gamblet_info* info) {
   cudaStream_t s = h->s;
   Pool tmp;
+  tmp.s = h->s;
   const int q = h->q;
   LevelDev& Lq = h->lv[q];
   const int64_t nq = Lq.ncell;
@@ -834,7 +972,10 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
       if (is_f32<T>()) launch_convert_f32_f64((const float*)zT, h->z64, nq, s);
       CK(cudaMemcpyAsync(h->p64, h->z64, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
       for (outer = 1; outer <= maxit; ++outer) {
+        int tok = h->prof.begin("outer_spmv64", 8.0 * ((double)Lq.noff * Lq.npar * 16 + 8.0 * Lq.npar),
+                                2.0 * 16.0 * Lq.noff * Lq.npar, s);
         launch_block_spmv64(Lq.Ahat64, Lq.off, Lq.noff, Lpar, Lq.npar, h->p64, h->q64, s);
+        h->prof.end(tok, s);
         CK(cudaMemsetAsync(d, 0, sizeof(double) * 4, s));
         // d0 = p.q, d1 = p.r
         launch_dots(nq, h->p64, h->q64, h->p64, h->r64, nullptr, nullptr, d, s);
@@ -887,6 +1028,7 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
   CK(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  h->prof.resolve();
   check_status(h, "solve");
   if (maxit == 0 && h->level_not_conv) st = GAMBLET_ERR_NOT_CONVERGED;
   if (info) {
@@ -922,6 +1064,7 @@ void gamblet_default_opts(gamblet_opts* o) {
   o->refine_tol = 1e-13;
   o->refine_max_iter = 50;
   o->use_graph = 1;
+  o->profile = 0;
   o->stream = nullptr;
 }
 
@@ -944,6 +1087,8 @@ gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cel
     if (opts) h->opts = *opts;
     else gamblet_default_opts(&h->opts);
     h->s = (cudaStream_t)h->opts.stream;
+    h->pool.s = h->s;
+    h->prof.on = h->opts.profile != 0;
     h->q = q;
     h->n = A->n;
     h->exact = !(h->opts.rho > 0);
@@ -957,6 +1102,13 @@ gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cel
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    {
+      // keep freed pool memory cached in this process (no device setting changes)
+      cudaMemPool_t mp;
+      CK(cudaDeviceGetDefaultMemPool(&mp, dev));
+      uint64_t thr = UINT64_MAX;
+      CK(cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr));
+    }
     for (int k = 0; k < 32; ++k) h->level_iters_acc[k] = 0;
     CK(cudaMallocHost(&h->any_active_h, sizeof(int)));
     CK(cudaMallocHost(&h->dots_h, sizeof(double) * 8));
@@ -991,6 +1143,7 @@ gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cel
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->setup_ms = ms;
+    h->prof.resolve();
     check_status(h, "setup");
     *out = h;
     return GAMBLET_OK;
@@ -1025,6 +1178,7 @@ gamblet_status gamblet_grad(gamblet_handle h, int32_t ncell, const int32_t* cell
     if (ncell < 1) fail(GAMBLET_ERR_INVALID_ARG, "ncell must be positive");
     cudaStream_t s = h->s;
     Pool tmp;
+  tmp.s = h->s;
     const int n = h->n;
     double* ud = nullptr;
     double* uo = nullptr;
@@ -1302,6 +1456,27 @@ gamblet_status gamblet_get_operator(gamblet_handle h, int32_t which, int32_t k, 
 }
 
 int64_t gamblet_device_bytes(gamblet_handle h) { return h ? h->pool.bytes : 0; }
+
+int32_t gamblet_kernel_stats(gamblet_handle h, gamblet_kernel_stat* out, int32_t capacity) {
+  if (!h) return 0;
+  const int32_t n = (int32_t)h->prof.stats.size();
+  for (int32_t i = 0; i < n && i < capacity && out; ++i) {
+    const Prof::Stat& st = h->prof.stats[i];
+    std::memset(out[i].name, 0, sizeof(out[i].name));
+    std::strncpy(out[i].name, st.name.c_str(), sizeof(out[i].name) - 1);
+    out[i].launches = st.launches;
+    out[i].ms = st.ms;
+    out[i].bytes = st.bytes;
+    out[i].flops = st.flops;
+  }
+  return n;
+}
+
+void gamblet_reset_kernel_stats(gamblet_handle h) {
+  if (h) h->prof.stats.clear();
+}
+
+int64_t gamblet_kernel_launches(void) { return (int64_t)gb::g_launches.load(); }
 
 void gamblet_destroy(gamblet_handle h) {
   if (!h) return;

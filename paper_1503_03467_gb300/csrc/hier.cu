@@ -36,8 +36,8 @@ void launch_cells_to_morton(const int32_t* cells, int n, int q, int32_t* morton_
                             int32_t* unknown_of, uint32_t* pmask_q, int* dup_flag,
                             cudaStream_t s) {
   if (n <= 0) return;
-  k_cells_to_morton<<<(n + 255) / 256, 256, 0, s>>>(cells, n, q, morton_of, unknown_of,
-                                                    pmask_q, dup_flag);
+  { count_launch(); k_cells_to_morton<<<(n + 255) / 256, 256, 0, s>>>(cells, n, q, morton_of, unknown_of,
+                                                    pmask_q, dup_flag); }
 }
 
 // Parent P of level k-1 has child c active iff level-k parent 4P + c has
@@ -56,7 +56,7 @@ void launch_coarsen_masks(const uint32_t* pmask_k, int64_t npar_k, uint32_t* pma
                           cudaStream_t s) {
   int64_t n = npar_k / 4;
   if (n <= 0) return;
-  k_coarsen_masks<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pmask_k, n, pmask_km1);
+  { count_launch(); k_coarsen_masks<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pmask_k, n, pmask_km1); }
 }
 
 // ---------------------------------------------------------------- fine operator
@@ -93,7 +93,7 @@ void launch_csr_offset_extent(int n, const int32_t* rowptr, const int32_t* colin
                               const int32_t* morton_of, int* ext, int* bad_flag,
                               cudaStream_t s) {
   if (n <= 0) return;
-  k_csr_extent<<<(n + 127) / 128, 128, 0, s>>>(n, rowptr, colind, morton_of, ext, bad_flag);
+  { count_launch(); k_csr_extent<<<(n + 127) / 128, 128, 0, s>>>(n, rowptr, colind, morton_of, ext, bad_flag); }
 }
 
 __global__ void k_csr_to_blocks(int n, const int32_t* __restrict__ rowptr,
@@ -122,8 +122,8 @@ void launch_csr_to_blocks(int n, const int32_t* rowptr, const int32_t* colind,
                           const double* val, const int32_t* morton_of, int rx, int ry,
                           int64_t npar, double* blk, cudaStream_t s) {
   if (n <= 0) return;
-  k_csr_to_blocks<<<(n + 127) / 128, 128, 0, s>>>(n, rowptr, colind, val, morton_of, rx, ry,
-                                                  npar, blk);
+  { count_launch(); k_csr_to_blocks<<<(n + 127) / 128, 128, 0, s>>>(n, rowptr, colind, val, morton_of, rx, ry,
+                                                  npar, blk); }
 }
 
 // ---------------------------------------------------------------- transforms
@@ -170,8 +170,8 @@ void launch_transform_blocks(double* blk, const int2* off, int noff, int64_t npa
                              const uint32_t* pmask, cudaStream_t s) {
   int64_t n = (int64_t)noff * npar;
   if (n <= 0) return;
-  k_transform_blocks<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blk, off, noff, npar, Lpar,
-                                                                pmask);
+  { count_launch(); k_transform_blocks<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blk, off, noff, npar, Lpar,
+                                                                pmask); }
 }
 
 __global__ void k_f64_to_f32(const double* __restrict__ in, float* out, int64_t n) {
@@ -183,10 +183,10 @@ __global__ void k_f32_to_f64(const float* __restrict__ in, double* out, int64_t 
   if (i < n) out[i] = (double)in[i];
 }
 void launch_convert_f64_f32(const double* in, float* out, int64_t n, cudaStream_t s) {
-  if (n > 0) k_f64_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
+  if (n > 0) { count_launch(); k_f64_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n); }
 }
 void launch_convert_f32_f64(const float* in, double* out, int64_t n, cudaStream_t s) {
-  if (n > 0) k_f32_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
+  if (n > 0) { count_launch(); k_f32_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n); }
 }
 
 template <typename T>
@@ -214,7 +214,7 @@ template <typename T>
 void launch_transform_vec(const T* in, T* out, int64_t npar, const uint32_t* pmask, int dir,
                           cudaStream_t s) {
   if (npar <= 0) return;
-  k_transform_vec<T><<<(unsigned)((npar + 255) / 256), 256, 0, s>>>(in, out, npar, pmask, dir);
+  { count_launch(); k_transform_vec<T><<<(unsigned)((npar + 255) / 256), 256, 0, s>>>(in, out, npar, pmask, dir); }
 }
 template void launch_transform_vec<double>(const double*, double*, int64_t, const uint32_t*,
                                            int, cudaStream_t);
@@ -236,13 +236,13 @@ __global__ void k_scatter_unknown(const double* __restrict__ in, const int32_t* 
 void launch_gather_morton(const double* in_unknown, const int32_t* unknown_of, int64_t ncell,
                           double* out_morton, cudaStream_t s) {
   if (ncell > 0)
-    k_gather_morton<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(in_unknown, unknown_of,
-                                                                    ncell, out_morton);
+    { count_launch(); k_gather_morton<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(in_unknown, unknown_of,
+                                                                    ncell, out_morton); }
 }
 void launch_scatter_unknown(const double* in_morton, const int32_t* morton_of, int n,
                             double* out_unknown, cudaStream_t s) {
   if (n > 0)
-    k_scatter_unknown<<<(n + 255) / 256, 256, 0, s>>>(in_morton, morton_of, n, out_unknown);
+    { count_launch(); k_scatter_unknown<<<(n + 255) / 256, 256, 0, s>>>(in_morton, morton_of, n, out_unknown); }
 }
 
 }  // namespace gb

@@ -139,9 +139,14 @@ template <typename T>
 void launch_cg_init(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
                     cudaStream_t s);
 void launch_cg_start(CgScalars* sc, int nlev, int* any_active, cudaStream_t s);
+// One CG iteration = launch_cg_spmv (Ap = B p, p.Ap) then launch_cg_rest
+// (x, r update and r.r; scalars and convergence; p = r + beta p).
 template <typename T>
-void launch_cg_iteration(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
-                         double tol2, int max_iter, int* any_active, cudaStream_t s);
+void launch_cg_spmv(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
+                    cudaStream_t s);
+template <typename T>
+void launch_cg_rest(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, double tol2,
+                    int max_iter, int* any_active, cudaStream_t s);
 
 // Outer float64 operations on transformed level-q vectors.
 void launch_block_spmv64(const double* Ahat, const int2* off, int noff, int Lpar, int64_t npar,

@@ -185,7 +185,7 @@ void launch_patch_solve(const T* Ahat, const uint32_t* pmask_k, PatchGeom g, T* 
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)num_sms * per_sm;
   if (grid > g.npatch) grid = g.npatch;
-  k_patch_solve<T><<<(unsigned)grid, 256, smem, s>>>(Ahat, pmask_k, g, Rhat, status);
+  { count_launch(); k_patch_solve<T><<<(unsigned)grid, 256, smem, s>>>(Ahat, pmask_k, g, Rhat, status); }
 }
 template void launch_patch_solve<float>(const float*, const uint32_t*, PatchGeom, float*, int*,
                                         int, cudaStream_t);

@@ -48,8 +48,8 @@ template <typename T>
 void launch_restrict(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t nrow,
                      const T* ghat_k, T* g_km1, const uint32_t* pmask_km1, cudaStream_t s) {
   if (nrow <= 0) return;
-  k_restrict<T><<<(unsigned)((nrow + 127) / 128), 128, 0, s>>>(Rhat, NB, nbr, Lpar, nrow, ghat_k,
-                                                               g_km1, pmask_km1);
+  { count_launch(); k_restrict<T><<<(unsigned)((nrow + 127) / 128), 128, 0, s>>>(Rhat, NB, nbr, Lpar, nrow, ghat_k,
+                                                               g_km1, pmask_km1); }
 }
 template void launch_restrict<float>(const float*, int, const int2*, int, int64_t, const float*,
                                      float*, const uint32_t*, cudaStream_t);
@@ -103,8 +103,8 @@ void launch_prolong(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t np
                     const T* v_km1, const T* w_k, const uint32_t* pmask_k, int inverse, T* out,
                     cudaStream_t s) {
   if (npar <= 0) return;
-  k_prolong<T><<<(unsigned)((npar + 127) / 128), 128, 0, s>>>(Rhat, NB, nbr, Lpar, npar, v_km1, w_k,
-                                                              pmask_k, inverse, out);
+  { count_launch(); k_prolong<T><<<(unsigned)((npar + 127) / 128), 128, 0, s>>>(Rhat, NB, nbr, Lpar, npar, v_km1, w_k,
+                                                              pmask_k, inverse, out); }
 }
 template void launch_prolong<float>(const float*, int, const int2*, int, int64_t, const float*,
                                     const float*, const uint32_t*, int, float*, cudaStream_t);
@@ -172,7 +172,7 @@ template <typename T>
 void launch_cg_init(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
                     cudaStream_t s) {
   if (total_blocks <= 0) return;
-  k_cg_init<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc);
+  { count_launch(); k_cg_init<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
 }
 
 // Ap = B p over the 3x3 detail blocks; pAp += p.Ap
@@ -234,21 +234,24 @@ __global__ void k_cg_axpy(const CgLevel* __restrict__ lv, int nlev, CgScalars* s
   block_atomic_add(part, &sc[l].rr_new);
 }
 
-// beta, convergence, counters (one thread per level)
+// beta, convergence, counters; one thread, so any_active is exact
 __global__ void k_cg_scalars(CgScalars* sc, int nlev, double tol2, int max_iter,
                              int* any_active) {
-  const int l = threadIdx.x;
-  if (l >= nlev || !sc[l].active) return;
-  CgScalars s = sc[l];
-  s.iters += 1;
-  const double beta = s.rr > 0 ? s.rr_new / s.rr : 0.0;
-  s.beta = beta;
-  s.rr = s.rr_new;
-  s.rr_new = 0;
-  s.pAp = 0;
-  if (s.rr <= tol2 * s.rr0 || s.iters >= max_iter || !(s.rr == s.rr)) s.active = 0;
-  else atomicExch(any_active, 1);
-  sc[l] = s;
+  if (threadIdx.x != 0) return;
+  int act = 0;
+  for (int l = 0; l < nlev; ++l) {
+    CgScalars st = sc[l];
+    if (!st.active) continue;
+    st.iters += 1;
+    st.beta = st.rr > 0 ? st.rr_new / st.rr : 0.0;
+    st.rr = st.rr_new;
+    st.rr_new = 0;
+    st.pAp = 0;
+    if (st.rr <= tol2 * st.rr0 || st.iters >= max_iter || !(st.rr == st.rr)) st.active = 0;
+    else act = 1;
+    sc[l] = st;
+  }
+  *any_active = act;
 }
 
 // p = r + beta p
@@ -267,25 +270,33 @@ __global__ void k_cg_dir(const CgLevel* __restrict__ lv, int nlev, CgScalars* sc
 }
 
 template <typename T>
-void launch_cg_iteration(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
-                         double tol2, int max_iter, int* any_active, cudaStream_t s) {
+void launch_cg_spmv(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
+                    cudaStream_t s) {
   if (total_blocks <= 0) return;
-  k_cg_spmv<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc);
-  k_cg_axpy<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc);
-  k_cg_scalars<<<1, 32, 0, s>>>(sc, nlev, tol2, max_iter, any_active);
-  k_cg_dir<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc);
+  { count_launch(); k_cg_spmv<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
+}
+
+template <typename T>
+void launch_cg_rest(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, double tol2,
+                    int max_iter, int* any_active, cudaStream_t s) {
+  if (total_blocks <= 0) return;
+  { count_launch(); k_cg_axpy<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
+  { count_launch(); k_cg_scalars<<<1, 32, 0, s>>>(sc, nlev, tol2, max_iter, any_active); }
+  { count_launch(); k_cg_dir<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
 }
 
 void launch_cg_start(CgScalars* sc, int nlev, int* any_active, cudaStream_t s) {
-  k_cg_start<<<1, 32, 0, s>>>(sc, nlev, any_active);
+  { count_launch(); k_cg_start<<<1, 32, 0, s>>>(sc, nlev, any_active); }
 }
 
 template void launch_cg_init<float>(const CgLevel*, int, int, CgScalars*, cudaStream_t);
 template void launch_cg_init<double>(const CgLevel*, int, int, CgScalars*, cudaStream_t);
-template void launch_cg_iteration<float>(const CgLevel*, int, int, CgScalars*, double, int, int*,
-                                         cudaStream_t);
-template void launch_cg_iteration<double>(const CgLevel*, int, int, CgScalars*, double, int, int*,
-                                          cudaStream_t);
+template void launch_cg_spmv<float>(const CgLevel*, int, int, CgScalars*, cudaStream_t);
+template void launch_cg_spmv<double>(const CgLevel*, int, int, CgScalars*, cudaStream_t);
+template void launch_cg_rest<float>(const CgLevel*, int, int, CgScalars*, double, int, int*,
+                                    cudaStream_t);
+template void launch_cg_rest<double>(const CgLevel*, int, int, CgScalars*, double, int, int*,
+                                     cudaStream_t);
 
 // ---------------------------------------------------------------- coarsest level
 // A^(1) (4 x 4, float64) from the level-1 cell stencil; Cholesky in place.
@@ -326,7 +337,7 @@ __global__ void k_level1_factor(const T* __restrict__ Acell, const int* __restri
 template <typename T>
 void launch_level1_factor(const T* Acell, const int* map, double* A1, int* status,
                           cudaStream_t s) {
-  k_level1_factor<T><<<1, 32, 0, s>>>(Acell, map, A1, status);
+  { count_launch(); k_level1_factor<T><<<1, 32, 0, s>>>(Acell, map, A1, status); }
 }
 template void launch_level1_factor<float>(const float*, const int*, double*, int*, cudaStream_t);
 template void launch_level1_factor<double>(const double*, const int*, double*, int*,
@@ -351,7 +362,7 @@ __global__ void k_level1_solve(const double* __restrict__ L, const T* __restrict
 
 template <typename T>
 void launch_level1_solve(const double* L, const T* g, T* U, cudaStream_t s) {
-  k_level1_solve<T><<<1, 32, 0, s>>>(L, g, U);
+  { count_launch(); k_level1_solve<T><<<1, 32, 0, s>>>(L, g, U); }
 }
 template void launch_level1_solve<float>(const double*, const float*, float*, cudaStream_t);
 template void launch_level1_solve<double>(const double*, const double*, double*, cudaStream_t);
@@ -384,7 +395,7 @@ __global__ void k_block_spmv64(const double* __restrict__ A, const int2* __restr
 void launch_block_spmv64(const double* Ahat, const int2* off, int noff, int Lpar, int64_t npar,
                          const double* x, double* y, cudaStream_t s) {
   if (npar <= 0) return;
-  k_block_spmv64<<<(unsigned)((npar + 127) / 128), 128, 0, s>>>(Ahat, off, noff, Lpar, npar, x, y);
+  { count_launch(); k_block_spmv64<<<(unsigned)((npar + 127) / 128), 128, 0, s>>>(Ahat, off, noff, Lpar, npar, x, y); }
 }
 
 __global__ void k_dots(int64_t n, const double* __restrict__ a0, const double* __restrict__ b0,
@@ -409,7 +420,7 @@ void launch_dots(int64_t n, const double* a0, const double* b0, const double* a1
   if (n <= 0) return;
   int64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  k_dots<<<(unsigned)blocks, 256, 0, s>>>(n, a0, b0, a1, b1, a2, b2, dots);
+  { count_launch(); k_dots<<<(unsigned)blocks, 256, 0, s>>>(n, a0, b0, a1, b1, a2, b2, dots); }
 }
 
 // y += sign * (num / den) * x
@@ -424,7 +435,7 @@ __global__ void k_axpy(int64_t n, const double* __restrict__ num, const double* 
 void launch_axpy(int64_t n, const double* alpha_num, const double* alpha_den, double sign,
                  const double* x, double* y, cudaStream_t s) {
   if (n > 0)
-    k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, alpha_num, alpha_den, sign, x, y);
+    { count_launch(); k_axpy<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, alpha_num, alpha_den, sign, x, y); }
 }
 // p = x + sign * (num / den) * p
 __global__ void k_xpby(int64_t n, const double* __restrict__ x, const double* __restrict__ num,
@@ -438,7 +449,7 @@ __global__ void k_xpby(int64_t n, const double* __restrict__ x, const double* __
 void launch_xpby(int64_t n, const double* x, const double* beta_num, const double* beta_den,
                  double sign, double* p, cudaStream_t s) {
   if (n > 0)
-    k_xpby<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, beta_num, beta_den, sign, p);
+    { count_launch(); k_xpby<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, beta_num, beta_den, sign, p); }
 }
 
 // ---------------------------------------------------------------- adjoint contraction
@@ -471,7 +482,7 @@ __global__ void k_adjoint_contract(int ncell, const int32_t* __restrict__ cn,
 void launch_adjoint_contract(int ncell, const int32_t* cell_nodes, const double* cell_a,
                              const double* lam, const double* u, double* dJ, cudaStream_t s) {
   if (ncell > 0)
-    k_adjoint_contract<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, cell_nodes, cell_a, lam, u, dJ);
+    { count_launch(); k_adjoint_contract<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, cell_nodes, cell_a, lam, u, dJ); }
 }
 
 }  // namespace gb

@@ -45,7 +45,7 @@ class Opts(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("level_tol", ctypes.c_double),
                 ("level_max_iter", ctypes.c_int32), ("refine_tol", ctypes.c_double),
                 ("refine_max_iter", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -59,6 +59,11 @@ class Info(ctypes.Structure):
                 "level_iters": list(self.level_iters)[: self.q + 1],
                 "rel_residual": self.rel_residual, "setup_ms": self.setup_ms,
                 "solve_ms": self.solve_ms}
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
 # name -> (restype, argtypes)
@@ -79,6 +84,10 @@ SIGNATURES = {
                                             ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gamblet_device_bytes": (ctypes.c_int64, [ctypes.c_void_p]),
+    "gamblet_kernel_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(KernelStat),
+                                              ctypes.c_int32]),
+    "gamblet_reset_kernel_stats": (None, [ctypes.c_void_p]),
+    "gamblet_kernel_launches": (ctypes.c_int64, []),
     "gamblet_destroy": (None, [ctypes.c_void_p]),
     "gamblet_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "gamblet_last_error": (ctypes.c_char_p, []),
@@ -184,6 +193,22 @@ def gamblet_get_operator(h: int, which: int, k: int):
     _check(_lib.gamblet_get_operator(ctypes.c_void_p(h), int(which), int(k), nnz.value,
                                      ctypes.byref(nnz), _ptr(r), _ptr(c), _ptr(v)))
     return r, c, v
+
+
+def gamblet_kernel_stats(h: int) -> list[dict]:
+    n = _lib.gamblet_kernel_stats(ctypes.c_void_p(h), None, 0)
+    arr = (KernelStat * max(n, 1))()
+    n = _lib.gamblet_kernel_stats(ctypes.c_void_p(h), arr, n)
+    return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "ms": arr[i].ms,
+             "bytes": arr[i].bytes, "flops": arr[i].flops} for i in range(n)]
+
+
+def gamblet_reset_kernel_stats(h: int) -> None:
+    _lib.gamblet_reset_kernel_stats(ctypes.c_void_p(h))
+
+
+def gamblet_kernel_launches() -> int:
+    return int(_lib.gamblet_kernel_launches())
 
 
 def gamblet_device_bytes(h: int) -> int:

@@ -1,0 +1,78 @@
+"""The C ABI library loads without a GPU, exports every function that
+include/gamblet.h declares, and the ctypes structures match the C layout."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gamblet.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1503_03467_gb300 import build
+    build.build()
+    from paper_1503_03467_gb300 import native
+    return native
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"GAMBLET_API\s+[\w\s\*]+?\b(gamblet_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gamblet_setup", "gamblet_solve", "gamblet_grad", "gamblet_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(gamblet_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    # and the binding knows each of them
+    assert set(declared_functions()) <= set(lib.SIGNATURES)
+
+
+def test_struct_layouts_match_header(lib):
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "gamblet.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(gamblet_csr), sizeof(gamblet_opts), sizeof(gamblet_info),
+         sizeof(gamblet_kernel_stat));
+  printf("%zu %zu %zu\n", offsetof(gamblet_opts, stream), offsetof(gamblet_info, rel_residual),
+         offsetof(gamblet_csr, val));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(prog)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        l1, l2 = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")[:2]
+    sizes = [int(x) for x in l1.split()]
+    offs = [int(x) for x in l2.split()]
+    assert sizes == [ctypes.sizeof(lib.Csr), ctypes.sizeof(lib.Opts), ctypes.sizeof(lib.Info),
+                     ctypes.sizeof(lib.KernelStat)]
+    assert offs == [lib.Opts.stream.offset, lib.Info.rel_residual.offset, lib.Csr.val.offset]
+
+
+def test_host_only_calls(lib):
+    o = lib.gamblet_default_opts()
+    assert o.rho == 3.0 and o.precision == lib.FP64 and o.refine_max_iter == 50
+    assert lib.gamblet_status_string(lib.ERR_NOT_SPD).startswith("matrix not")
+    assert lib.gamblet_device_bytes(0) == 0
+    assert lib.gamblet_kernel_stats(0) == []
+    lib.gamblet_destroy(0)  # NULL is ignored
+    with pytest.raises(lib.GambletError):
+        lib.gamblet_level_size(0, 1)
