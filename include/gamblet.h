@@ -165,6 +165,30 @@ GAMBLET_API gamblet_status gamblet_grad(gamblet_handle h, int32_t ncell, const i
                             const double* cell_a, const double* K_ref, const double* u,
                             const double* u_obs, double* dJ, double* J, gamblet_info* info);
 
+/*
+ * J = 1/2 |u - u_obs|^2, the objective that gamblet_grad also returns, for
+ * callers that cannot allocate device memory when they need it: code inside
+ * CUDA stream capture in global mode (cudaMalloc is not permitted there) and
+ * hosts whose own allocator holds the free device memory or that run under a
+ * hard memory budget (e.g. an optimiser evaluating J during a line search).
+ * The paper has no counterpart; this is a service entry point.
+ *   n       number of unknowns, 1 <= n <= GAMBLET_NOALLOC_MAX_N; larger n
+ *           returns UNSUPPORTED.
+ *   u, u_obs  device pointers, n float64 each.
+ *   J       device or host pointer to one float64 (host: the call waits).
+ *   stream  cudaStream_t for the two kernels (0 = legacy default stream).
+ * Allocates nothing: the partial sums live in a fixed 8.2 KB device array
+ * that every GPU loading the library keeps until exit.  The first call on a
+ * device looks up that array's address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  Calls
+ * share the array, so calls that overlap on the GPU race; each call
+ * overwrites every slot it reads, so no clearing is needed between calls.
+ */
+#define GAMBLET_NOALLOC_MAX_N 2097152
+GAMBLET_API gamblet_status gamblet_objective_noalloc(int32_t n, const double* u,
+                                                     const double* u_obs, double* J,
+                                                     void* stream);
+
 /* Number of nodes n_k = |I^(k)| and detail rows |J^(k)| at level k. */
 GAMBLET_API gamblet_status gamblet_level_size(gamblet_handle h, int32_t k, int32_t* n_k, int32_t* nJ_k);
 

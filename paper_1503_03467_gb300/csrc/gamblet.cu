@@ -1505,3 +1505,8 @@ const char* gamblet_status_string(int32_t status) {
 const char* gamblet_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+namespace gb {
+// error text for the allocation-free entry point (noalloc.cu)
+void noalloc_set_error(const char* msg) { g_last_error = msg; }
+}  // namespace gb

@@ -88,6 +88,9 @@ SIGNATURES = {
                                               ctypes.c_int32]),
     "gamblet_reset_kernel_stats": (None, [ctypes.c_void_p]),
     "gamblet_kernel_launches": (ctypes.c_int64, []),
+    "gamblet_objective_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p]),
     "gamblet_destroy": (None, [ctypes.c_void_p]),
     "gamblet_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "gamblet_last_error": (ctypes.c_char_p, []),
@@ -174,6 +177,14 @@ def gamblet_grad(h: int, cell_nodes, cell_a, K_ref, u, u_obs, dJ,
                            ctypes.byref(J), ctypes.byref(info))
     _check(st)
     return J.value
+
+
+def gamblet_objective_noalloc(n: int, u, u_obs, J, stream=None) -> int:
+    """J = 1/2 |u - u_obs|^2 into J (a 1-element float64 tensor or array);
+    u and u_obs must be CUDA tensors.  Allocates no device memory."""
+    return _check(_lib.gamblet_objective_noalloc(int(n), _ptr(u, np.float64),
+                                                 _ptr(u_obs, np.float64), _ptr(J, np.float64),
+                                                 stream))
 
 
 def gamblet_level_size(h: int, k: int) -> tuple[int, int]:
