@@ -7,11 +7,50 @@
 // t_i = Ahat Rhat_i^T lives on the window i + WIN_w (WIN = N + O_k), and
 //   A^(k-1)_{i, i+S_d} = Rhat_{i+S_d} . t_i   (WIN_w = S_d + N_j).
 // The index lists (j, o) per window position and (j, w) per output offset
-// are built once per level on the host from the offset sets.
+// are built once per level on the host from the offset sets.  A^(k-1) is
+// symmetric, so only the offsets of one half-plane S+ are computed; the
+// conversion to blocks reads the other half as A_{i, i+d} = A_{i+d, i}.
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace gb {
+
+// 16-element block / 4-element row loads as 128-bit transactions
+__device__ __forceinline__ void load_block16(const float* p, float* b) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 v = __ldg(q + k);
+    b[4 * k] = v.x;
+    b[4 * k + 1] = v.y;
+    b[4 * k + 2] = v.z;
+    b[4 * k + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void load_block16(const double* p, double* b) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const double2 v = __ldg(q + k);
+    b[2 * k] = v.x;
+    b[2 * k + 1] = v.y;
+  }
+}
+__device__ __forceinline__ void load_vec4(const float* p, float* b) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  b[0] = v.x;
+  b[1] = v.y;
+  b[2] = v.z;
+  b[3] = v.w;
+}
+__device__ __forceinline__ void load_vec4(const double* p, double* b) {
+  const double2 v0 = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 v1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  b[0] = v0.x;
+  b[1] = v0.y;
+  b[2] = v1.x;
+  b[3] = v1.y;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_galerkin(const T* __restrict__ Ahat,
@@ -30,7 +69,7 @@ __global__ void __launch_bounds__(256) k_galerkin(const T* __restrict__ Ahat,
     int xi, yi;
     demorton((uint32_t)i, xi, yi);
     for (int idx = threadIdx.x; idx < 4 * g.NB; idx += blockDim.x)
-      rrow[idx] = Rhat[(int64_t)idx * nrow + i];
+      rrow[idx] = Rhat[i * 4 * g.NB + idx];
     __syncthreads();
     // t_i = Ahat Rhat_i^T on the window
     for (int w = threadIdx.x; w < g.nwin; w += blockDim.x) {
@@ -40,12 +79,14 @@ __global__ void __launch_bounds__(256) k_galerkin(const T* __restrict__ Ahat,
         for (int e = g.l1_ptr[w]; e < g.l1_ptr[w + 1]; ++e) {
           const int2 jo = g.l1_pairs[e];
           const T* blk = Ahat + ((int64_t)jo.y * nrow + p) * 16;
+          T b[16];
+          load_block16(blk, b);
           const T r0 = rrow[4 * jo.x], r1 = rrow[4 * jo.x + 1];
           const T r2 = rrow[4 * jo.x + 2], r3 = rrow[4 * jo.x + 3];
-          acc0 += blk[0] * r0 + blk[1] * r1 + blk[2] * r2 + blk[3] * r3;
-          acc1 += blk[4] * r0 + blk[5] * r1 + blk[6] * r2 + blk[7] * r3;
-          acc2 += blk[8] * r0 + blk[9] * r1 + blk[10] * r2 + blk[11] * r3;
-          acc3 += blk[12] * r0 + blk[13] * r1 + blk[14] * r2 + blk[15] * r3;
+          acc0 += b[0] * r0 + b[1] * r1 + b[2] * r2 + b[3] * r3;
+          acc1 += b[4] * r0 + b[5] * r1 + b[6] * r2 + b[7] * r3;
+          acc2 += b[8] * r0 + b[9] * r1 + b[10] * r2 + b[11] * r3;
+          acc3 += b[12] * r0 + b[13] * r1 + b[14] * r2 + b[15] * r3;
         }
       }
       t[4 * w] = acc0;
@@ -59,11 +100,14 @@ __global__ void __launch_bounds__(256) k_galerkin(const T* __restrict__ Ahat,
       T acc = 0;
       const int ip = shift_cell(xi, yi, g.out[d].x, g.out[d].y, g.Lpar);
       if (ip >= 0 && (pmask[ip] & 15u)) {
+        const T* rrow_ip = Rhat + (int64_t)ip * 4 * g.NB;
         for (int e = g.l2_ptr[d]; e < g.l2_ptr[d + 1]; ++e) {
           const int2 jw = g.l2_pairs[e];
           const T* tw = t + 4 * jw.y;
+          T rv[4];
+          load_vec4(rrow_ip + 4 * jw.x, rv);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc += Rhat[(int64_t)(4 * jw.x + c) * nrow + ip] * tw[c];
+          for (int c = 0; c < 4; ++c) acc += rv[c] * tw[c];
         }
       }
       Aout[(int64_t)d * nrow + i] = acc;
@@ -109,7 +153,10 @@ __global__ void k_cells_to_blocks(const T* __restrict__ Acell, int64_t ncell,
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
       const int d = map[o * 16 + c * 4 + cc];
-      M[c * 4 + cc] = (PP >= 0 && d >= 0) ? (double)Acell[(int64_t)d * ncell + 4 * P + c] : 0.0;
+      double v = 0.0;
+      if (PP >= 0 && d >= 0) v = (double)Acell[(int64_t)d * ncell + 4 * P + c];
+      else if (PP >= 0 && d <= -2) v = (double)Acell[(int64_t)(-d - 2) * ncell + 4 * PP + cc];
+      M[c * 4 + cc] = v;
     }
 #pragma unroll
   for (int a = 0; a < 4; ++a)

@@ -161,6 +161,7 @@ struct SymLevel {
   OffSet O;                       // block offsets of Ahat^(k) (level k-1 cell units)
   std::vector<int> pair_idx;      // NB x NB
   OffSet WIN, S;                  // window and output cell offsets
+  OffSet Sp;                      // the half-plane of S that is computed
   std::vector<int> l1_ptr, l2_ptr;
   std::vector<int2> l1_pairs, l2_pairs;
   std::vector<int> map_next;      // conversion map to level k-1 blocks (or level-1 map)
@@ -195,9 +196,14 @@ struct LevelDev {
   void* v = nullptr;     // ncell
   void* w = nullptr;     // ncell
   void* cr = nullptr;
+  void* cz = nullptr;
   void* cp = nullptr;
   void* cAp = nullptr;
   double* wc = nullptr;  // compact detail vector (exact path)
+  // level CG operator (localized path)
+  void* Bd = nullptr;    // [noff][9][npar]
+  void* Dinv = nullptr;  // [9][npar]
+  int R = 0;             // halo radius
 };
 
 // Per-kernel CUDA-event timing on the library's stream (opts.profile).
@@ -306,6 +312,8 @@ struct gamblet_ctx {
   int* any_active_h = nullptr;  // pinned
   int cg_blocks = 0;
   int cg_nlev = 0;
+  int cg_max_ts = 1;
+  cudaGraphExec_t cg_exec = nullptr;
   // outer
   double* u64 = nullptr;
   double* r64 = nullptr;
@@ -371,23 +379,34 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
       const int dx = S.WIN.v[w].x - N.v[j].x, dy = S.WIN.v[w].y - N.v[j].y;
       if (std::abs(dx) <= Lpar - 1 && std::abs(dy) <= Lpar - 1) S.S.add(dx, dy);
     }
-  std::vector<std::vector<int2>> l2(S.S.size());
-  for (int d = 0; d < S.S.size(); ++d)
+  for (const int2& d : S.S.v)
+    if (d.y > 0 || (d.y == 0 && d.x >= 0)) S.Sp.add(d.x, d.y);
+  std::vector<std::vector<int2>> l2(S.Sp.size());
+  for (int d = 0; d < S.Sp.size(); ++d)
     for (int j = 0; j < NB; ++j) {
-      const int w = S.WIN.find(S.S.v[d].x + N.v[j].x, S.S.v[d].y + N.v[j].y);
+      const int w = S.WIN.find(S.Sp.v[d].x + N.v[j].x, S.Sp.v[d].y + N.v[j].y);
       if (w >= 0) l2[d].push_back(make_int2(j, w));
     }
-  S.l2_ptr.assign(S.S.size() + 1, 0);
-  for (int d = 0; d < S.S.size(); ++d) {
+  S.l2_ptr.assign(S.Sp.size() + 1, 0);
+  for (int d = 0; d < S.Sp.size(); ++d) {
     S.l2_ptr[d + 1] = S.l2_ptr[d] + (int)l2[d].size();
     S.l2_pairs.insert(S.l2_pairs.end(), l2[d].begin(), l2[d].end());
   }
   return S;
 }
 
+// Where A_{i, i+d} lives in the half-plane output: index of d in Sp, or
+// -2 - (index of -d) for the mirrored half, or -1 when d is outside S.
+int half_code(const OffSet& Sp, int dx, int dy) {
+  const int a = Sp.find(dx, dy);
+  if (a >= 0) return a;
+  const int b = Sp.find(-dx, -dy);
+  return b >= 0 ? -2 - b : -1;
+}
+
 // Block offsets of level k-1 (level k-2 cell units) from the level k-1 cell
-// offsets S, and the conversion map [o][c*4+c'].
-OffSet blocks_from_cells(const OffSet& S, int km1, std::vector<int>& map) {
+// offsets S, and the conversion map [o][c*4+c'] (half_code of the offset).
+OffSet blocks_from_cells(const OffSet& S, const OffSet& Sp, int km1, std::vector<int>& map) {
   OffSet O;
   const int Lp = 1 << (km1 - 1);
   for (const int2& d : S.v)
@@ -403,7 +422,7 @@ OffSet blocks_from_cells(const OffSet& S, int km1, std::vector<int>& map) {
     for (int c = 0; c < 4; ++c)
       for (int cc = 0; cc < 4; ++cc)
         map[(size_t)o * 16 + c * 4 + cc] =
-            S.find(2 * O.v[o].x + (cc & 1) - (c & 1), 2 * O.v[o].y + (cc >> 1) - (c >> 1));
+            half_code(Sp, 2 * O.v[o].x + (cc & 1) - (c & 1), 2 * O.v[o].y + (cc >> 1) - (c >> 1));
   return O;
 }
 
@@ -567,8 +586,8 @@ void setup_local(gamblet_ctx* h) {
     gg.win = P.upload(S.WIN.v, s);
     gg.l1_ptr = P.upload(S.l1_ptr, s);
     gg.l1_pairs = P.upload(S.l1_pairs, s);
-    gg.nout = S.S.size();
-    gg.out = P.upload(S.S.v, s);
+    gg.nout = S.Sp.size();
+    gg.out = P.upload(S.Sp.v, s);
     gg.l2_ptr = P.upload(S.l2_ptr, s);
     gg.l2_pairs = P.upload(S.l2_pairs, s);
     gg.Lpar = Lpar;
@@ -586,7 +605,7 @@ void setup_local(gamblet_ctx* h) {
     if (k - 1 >= 2) {
       LevelDev& Ln = h->lv[k - 1];
       std::vector<int> map;
-      OffSet On = blocks_from_cells(S.S, k - 1, map);
+      OffSet On = blocks_from_cells(S.S, S.Sp, k - 1, map);
       Ln.off_h = On.v;
       Ln.noff = On.size();
       Ln.off = P.upload(Ln.off_h, s);
@@ -604,17 +623,34 @@ void setup_local(gamblet_ctx* h) {
       std::vector<int> map1(16, -1);
       for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j)
-          map1[i * 4 + j] = S.S.find((j & 1) - (i & 1), (j >> 1) - (i >> 1));
+          map1[i * 4 + j] = half_code(S.Sp, (j & 1) - (i & 1), (j >> 1) - (i >> 1));
       h->l1map = P.upload(map1, s);
       h->A1L = P.alloc<double>(16);
       launch_level1_factor<T>(Acell, h->l1map, h->A1L, h->status, s);
       CK(cudaGetLastError());
       // keep the level-1 cell stencil for the getter
       h->lv[1].Ahat = Acell;
-      h->lv[1].noff = S.S.size();
-      h->lv[1].off_h = S.S.v;
+      h->lv[1].noff = S.Sp.size();
+      h->lv[1].off_h = S.Sp.v;
     }
   }
+  // level-CG operators: coalesced detail blocks and block-Jacobi inverses
+  for (int k = 2; k <= q; ++k) {
+    LevelDev& L = h->lv[k];
+    int o0 = -1, R = 0;
+    for (int o = 0; o < L.noff; ++o) {
+      if (L.off_h[o].x == 0 && L.off_h[o].y == 0) o0 = o;
+      R = std::max(R, std::max(std::abs(L.off_h[o].x), std::abs(L.off_h[o].y)));
+    }
+    if (o0 < 0) fail(GAMBLET_ERR_INVALID_ARG, "level operator has no diagonal blocks");
+    L.R = R;
+    T* Bd = P.alloc<T>((int64_t)L.noff * 9 * L.npar);
+    T* Dinv = P.alloc<T>(9 * L.npar);
+    launch_cg_level_setup<T>((const T*)L.Ahat, L.noff, o0, L.npar, L.pmask, Bd, Dinv, s);
+    L.Bd = Bd;
+    L.Dinv = Dinv;
+  }
+  CK(cudaGetLastError());
 }
 
 // ------------------------------------------------------------ exact setup
@@ -689,6 +725,7 @@ void alloc_solve(gamblet_ctx* h) {
       L.w = P.zeros<T>(L.ncell, s);
       if (!h->exact) {
         L.cr = P.zeros<T>(L.ncell, s);
+        L.cz = P.zeros<T>(L.ncell, s);
         L.cp = P.zeros<T>(L.ncell, s);
         L.cAp = P.zeros<T>(L.ncell, s);
       } else {
@@ -713,24 +750,32 @@ void alloc_solve(gamblet_ctx* h) {
   if (!h->exact) {
     std::vector<CgLevel> cl;
     int blocks = 0;
+    int max_ts = 1;
     for (int k = 2; k <= q; ++k) {
       LevelDev& L = h->lv[k];
       CgLevel c;
-      c.Ahat = L.Ahat;
+      c.Bd = L.Bd;
+      c.Dinv = L.Dinv;
       c.off = L.off;
       c.noff = L.noff;
+      c.R = L.R;
       c.Lpar = 1 << (k - 1);
       c.npar = L.npar;
-      c.pmask = L.pmask;
       c.x = L.w;
       c.r = L.cr;
+      c.z = L.cz;
       c.p = L.cp;
       c.Ap = L.cAp;
       c.b = L.ghat;
       c.block_begin = blocks;
       blocks += (int)((L.npar + 255) / 256);
+      max_ts = std::max(max_ts, std::min(c.Lpar, 16) + 2 * L.R);
       cl.push_back(c);
     }
+    h->cg_max_ts = max_ts;
+    if (cg_spmv_smem_bytes(max_ts, sizeof(T)) > 227 * 1024)
+      fail(GAMBLET_ERR_UNSUPPORTED, "level operator stencil too wide for the CG tile");
+    prepare_cg_spmv<T>(max_ts);
     h->cg_nlev = (int)cl.size();
     h->cg_blocks = blocks;
     h->cg_lv = P.upload(cl, s);
@@ -740,27 +785,51 @@ void alloc_solve(gamblet_ctx* h) {
 }
 
 // ------------------------------------------------------------ gamblet operator
+// Capture `chunk` CG iterations (all levels) once per handle.
+template <typename T>
+void build_cg_graph(gamblet_ctx* h, int chunk, double tol2, int maxit) {
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  for (int c = 0; c < chunk; ++c) {
+    launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, h->cg_max_ts, cs);
+    launch_cg_rest<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit, h->any_active,
+                      cs);
+  }
+  CK(cudaStreamEndCapture(cs, &g));
+  CK(cudaGraphInstantiate(&h->cg_exec, g, 0));
+  CK(cudaGraphDestroy(g));
+  CK(cudaStreamDestroy(cs));
+}
+
 template <typename T>
 void run_level_cg(gamblet_ctx* h) {
   cudaStream_t s = h->s;
   if (h->cg_nlev == 0) return;
-  CK(cudaMemsetAsync(h->cg_sc, 0, sizeof(CgScalars) * h->cg_nlev, s));
-  launch_cg_init<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, s);
-  CK(cudaMemsetAsync(h->any_active, 0, sizeof(int), s));
-  launch_cg_start(h->cg_sc, h->cg_nlev, h->any_active, s);
   const double tol2 = h->opts.level_tol * h->opts.level_tol;
   const int maxit = std::max(h->opts.level_max_iter, 1);
   const int chunk = 8;
+  CK(cudaMemsetAsync(h->cg_sc, 0, sizeof(CgScalars) * h->cg_nlev, s));
+  launch_cg_init<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, s);
+  launch_cg_start(h->cg_sc, h->cg_nlev, tol2, h->any_active, s);
+  if (h->opts.use_graph && !h->cg_exec) build_cg_graph<T>(h, chunk, tol2, maxit);
   for (int it = 0; it < maxit; it += chunk) {
-    CK(cudaMemsetAsync(h->any_active, 0, sizeof(int), s));
-    for (int c = 0; c < chunk; ++c) {
-      int tok = h->prof.begin("level_cg_spmv", 0.0, 0.0, s);
-      launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, s);
+    if (h->cg_exec) {
+      // with graphs the CG kernels are timed together, per chunk
+      int tok = h->prof.begin("level_cg", 0.0, 0.0, s);
+      CK(cudaGraphLaunch(h->cg_exec, s));
       h->prof.end(tok, s);
-      tok = h->prof.begin("level_cg_vector", 0.0, 0.0, s);
-      launch_cg_rest<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit, h->any_active,
-                        s);
-      h->prof.end(tok, s);
+    } else {
+      for (int c = 0; c < chunk; ++c) {
+        int tok = h->prof.begin("level_cg_spmv", 0.0, 0.0, s);
+        launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, h->cg_max_ts, s);
+        h->prof.end(tok, s);
+        tok = h->prof.begin("level_cg_vector", 0.0, 0.0, s);
+        launch_cg_rest<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit,
+                          h->any_active, s);
+        h->prof.end(tok, s);
+      }
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->any_active_h, h->any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -775,12 +844,18 @@ void run_level_cg(gamblet_ctx* h) {
     h->level_iters_acc[l + 2] += sc[l].iters;
     if (sc[l].rr > tol2 * sc[l].rr0) h->level_not_conv = true;
     // algorithmic traffic: the 3x3 detail blocks of B^(k) once per iteration,
-    // p read, Ap written (3 active slots); vector kernels: x, r, p, Ap, r
+    // p read, Ap written (3 active slots); vector kernels: x, r, z, p, Ap, Dinv
     const LevelDev& L = h->lv[l + 2];
     const double sz = (double)sizeof(T), it = sc[l].iters;
-    h->prof.add("level_cg_spmv", it * sz * ((double)L.noff * L.npar * 9 + 6.0 * L.npar),
-                it * 2.0 * 9.0 * L.noff * L.npar);
-    h->prof.add("level_cg_vector", it * sz * 3.0 * L.npar * 8, it * 3.0 * L.npar * 6);
+    const double b_spmv = it * sz * ((double)L.noff * L.npar * 9 + 6.0 * L.npar);
+    const double f_spmv = it * 2.0 * 9.0 * L.noff * L.npar;
+    const double b_vec = it * sz * 3.0 * L.npar * 12, f_vec = it * 3.0 * L.npar * 12;
+    if (h->cg_exec) {
+      h->prof.add("level_cg", b_spmv + b_vec, f_spmv + f_vec);
+    } else {
+      h->prof.add("level_cg_spmv", b_spmv, f_spmv);
+      h->prof.add("level_cg_vector", b_vec, f_vec);
+    }
   }
 }
 
@@ -1340,12 +1415,13 @@ Coo get_A(gamblet_ctx* h, int k) {
       const LevelDev& L1 = h->lv[1];
       std::vector<double> C = h->mixed ? download<float>(L1.Ahat, (int64_t)L1.noff * 4, s)
                                        : download<double>(L1.Ahat, (int64_t)L1.noff * 4, s);
-      std::map<Off, int> sidx;
-      for (int d = 0; d < L1.noff; ++d) sidx[Off{L1.off_h[d].x, L1.off_h[d].y}] = d;
+      OffSet Sp;
+      for (const int2& d : L1.off_h) Sp.add(d.x, d.y);
       for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) {
-          auto it = sidx.find(Off{(j & 1) - (i & 1), (j >> 1) - (i >> 1)});
-          if (it != sidx.end()) M[i * 4 + j] = C[(int64_t)it->second * 4 + i];
+          const int code = half_code(Sp, (j & 1) - (i & 1), (j >> 1) - (i >> 1));
+          if (code >= 0) M[i * 4 + j] = C[(int64_t)code * 4 + i];
+          else if (code <= -2) M[i * 4 + j] = C[(int64_t)(-code - 2) * 4 + j];
         }
     }
     for (int i = 0; i < 4; ++i)
@@ -1423,7 +1499,7 @@ Coo get_R(gamblet_ctx* h, int k) {
       for (int c = 0; c < 4; ++c) {
         if (cmc[4 * (int64_t)p + c] < 0) continue;
         double acc = 0;
-        for (int a = 0; a < 4; ++a) acc += R[(int64_t)(4 * j + a) * L.npar + i] * Q[a * 4 + c];
+        for (int a = 0; a < 4; ++a) acc += R[i * 4 * NB + 4 * j + a] * Q[a * 4 + c];
         if (acc != 0.0) out.add(cmr[i], cmc[4 * (int64_t)p + c], acc);
       }
     }
@@ -1483,6 +1559,7 @@ void gamblet_destroy(gamblet_handle h) {
   if (h->s) cudaStreamSynchronize(h->s);
   else cudaDeviceSynchronize();
   h->pool.release();
+  if (h->cg_exec) cudaGraphExecDestroy(h->cg_exec);
   if (h->any_active_h) cudaFreeHost(h->any_active_h);
   if (h->dots_h) cudaFreeHost(h->dots_h);
   if (h->status_h) cudaFreeHost(h->status_h);

@@ -116,37 +116,47 @@ void launch_prolong(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t np
                     const T* v_km1, const T* w_k, const uint32_t* pmask_k, int inverse,
                     T* out, cudaStream_t s);
 
-// Batched level CG over several levels at once.
+// Batched, block-Jacobi preconditioned level CG over several levels at once
+// (levelcg.cu).
 struct CgLevel {
-  const void* Ahat;   // block stencil (T)
+  const void* Bd;     // detail blocks, SoA [noff][9][npar] (T)
+  const void* Dinv;   // inverse diagonal detail blocks [9][npar] (T)
   const int2* off;
   int noff;
+  int R;              // largest |offset component| (halo radius)
   int Lpar;
   int64_t npar;
-  const uint32_t* pmask;
   void* x;            // solution (AoS4, slot 3 unused)
   void* r;
+  void* z;
   void* p;
   void* Ap;
   const void* b;      // right-hand side (transformed vector; slots 0..2 used)
   int block_begin;    // first CTA of this level in the batched grid
 };
 struct CgScalars {
-  double rr, rr_new, pAp, rr0, beta;
+  double rz, rz_new, rr, rr_new, pAp, rr0, beta;
   int active, iters;
 };
+size_t cg_spmv_smem_bytes(int max_ts, size_t elem);
+template <typename T>
+void prepare_cg_spmv(int max_ts);
 template <typename T>
 void launch_cg_init(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
                     cudaStream_t s);
-void launch_cg_start(CgScalars* sc, int nlev, int* any_active, cudaStream_t s);
+void launch_cg_start(CgScalars* sc, int nlev, double tol2, int* any_active, cudaStream_t s);
 // One CG iteration = launch_cg_spmv (Ap = B p, p.Ap) then launch_cg_rest
-// (x, r update and r.r; scalars and convergence; p = r + beta p).
+// (x, r, z update with r.z and r.r; scalars and convergence; p = z + beta p).
 template <typename T>
-void launch_cg_spmv(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
+void launch_cg_spmv(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, int max_ts,
                     cudaStream_t s);
 template <typename T>
 void launch_cg_rest(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, double tol2,
                     int max_iter, int* any_active, cudaStream_t s);
+// Coalesced detail-block copy and block-Jacobi inverses of one level.
+template <typename T>
+void launch_cg_level_setup(const T* Ahat, int noff, int o0, int64_t npar, const uint32_t* pmask,
+                           T* Bd, T* Dinv, cudaStream_t s);
 
 // Outer float64 operations on transformed level-q vectors.
 void launch_block_spmv64(const double* Ahat, const int2* off, int noff, int Lpar, int64_t npar,

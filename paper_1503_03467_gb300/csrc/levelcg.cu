@@ -1,0 +1,360 @@
+// levelcg.cu - the independent level systems B^(k) w^(k) = W g^(k)
+// (Eq. eqsdjoejddi1), k = 2..q, solved by conjugate gradients (Sec. 4.9) for
+// all levels at once: every launch covers every level still iterating, one
+// CTA per 16 x 16 Morton tile of parents (the paper's "parallel in
+// subscale", Sec. 5.4, as one grid).
+//
+// B^(k) is the 3x3 detail block of the transformed block stencil; for the
+// CG it is kept as a separate coalesced copy Bd[o][e][p] (e = 3a + b).  Each
+// CTA stages the direction vector of its tile plus a halo of R cells (R =
+// largest offset of the level) in shared memory, so the inner loop over
+// offsets reads the matrix with unit stride and the vector from shared
+// memory.  The CG is preconditioned by the inverse of each parent's 3x3
+// diagonal detail block (block Jacobi).  Dots accumulate in float64.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace gb {
+
+__device__ __forceinline__ int find_level(const CgLevel* lv, int nlev, int b) {
+  int l = 0;
+  while (l + 1 < nlev && lv[l + 1].block_begin <= b) ++l;
+  return l;
+}
+
+__device__ __forceinline__ void block_sum_add(double v, double* dst, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0 && v != 0.0) atomicAdd(dst, v);
+  }
+  __syncthreads();
+}
+
+// z = Dinv r for one parent (3 active slots at most)
+template <typename T>
+__device__ __forceinline__ void apply_dinv(const T* __restrict__ Dinv, int64_t npar, int64_t p,
+                                           const T r[3], T z[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T acc = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) acc += Dinv[(int64_t)(3 * a + b) * npar + p] * r[b];
+    z[a] = acc;
+  }
+}
+
+// r = b, x = 0, z = Dinv r, p = z; rz = r.z, rr = r.r
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_init(const CgLevel* __restrict__ lv, int nlev,
+                                                 CgScalars* sc) {
+  __shared__ double red[8];
+  const int l = find_level(lv, nlev, blockIdx.x);
+  const CgLevel L = lv[l];
+  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
+  double rz = 0, rr = 0;
+  if (p < L.npar) {
+    const T* b = (const T*)L.b;
+    T rv[3], zv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rv[a] = b[4 * p + a];
+    apply_dinv<T>((const T*)L.Dinv, L.npar, p, rv, zv);
+    T* x = (T*)L.x;
+    T* r = (T*)L.r;
+    T* z = (T*)L.z;
+    T* pp = (T*)L.p;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      x[4 * p + a] = 0;
+      r[4 * p + a] = rv[a];
+      z[4 * p + a] = zv[a];
+      pp[4 * p + a] = zv[a];
+      rz += (double)rv[a] * (double)zv[a];
+      rr += (double)rv[a] * (double)rv[a];
+    }
+    x[4 * p + 3] = 0;
+    pp[4 * p + 3] = 0;
+  }
+  block_sum_add(rz, &sc[l].rz, red);
+  block_sum_add(rr, &sc[l].rr, red);
+}
+
+__global__ void k_cg_start(CgScalars* sc, int nlev, double tol2, int* any_active) {
+  if (threadIdx.x != 0) return;
+  int act = 0;
+  for (int l = 0; l < nlev; ++l) {
+    CgScalars s = sc[l];
+    s.rr0 = s.rr;
+    s.active = s.rr > 0.0 && s.rz > 0.0;
+    s.iters = 0;
+    s.pAp = 0;
+    s.rz_new = 0;
+    s.rr_new = 0;
+    act |= s.active;
+    sc[l] = s;
+  }
+  *any_active = act;
+}
+
+// Ap = B p over the 3x3 detail blocks; pAp += p.Ap.  One CTA = one tile of
+// T x T parents (T = 16, or the whole lattice when it is smaller).
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_spmv(const CgLevel* __restrict__ lv, int nlev,
+                                                 CgScalars* sc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[8];
+  const int l = find_level(lv, nlev, blockIdx.x);
+  if (!sc[l].active) return;
+  const CgLevel L = lv[l];
+  const int tile = L.Lpar < 16 ? L.Lpar : 16;
+  const int R = L.R;
+  const int TS = tile + 2 * R;
+  T* xs = reinterpret_cast<T*>(smem_raw);  // 3 planes of TS x TS
+  const int64_t base = (int64_t)(blockIdx.x - L.block_begin) * 256;
+  int x0, y0;
+  demorton((uint32_t)base, x0, y0);
+  const T* pv = (const T*)L.p;
+  for (int c = threadIdx.x; c < TS * TS; c += blockDim.x) {
+    const int gx = x0 - R + c % TS, gy = y0 - R + c / TS;
+    T v0 = 0, v1 = 0, v2 = 0;
+    if ((unsigned)gx < (unsigned)L.Lpar && (unsigned)gy < (unsigned)L.Lpar) {
+      const int64_t q = morton((uint32_t)gx, (uint32_t)gy);
+      v0 = pv[4 * q];
+      v1 = pv[4 * q + 1];
+      v2 = pv[4 * q + 2];
+    }
+    xs[c] = v0;
+    xs[TS * TS + c] = v1;
+    xs[2 * TS * TS + c] = v2;
+  }
+  __syncthreads();
+  const int64_t p = base + threadIdx.x;
+  double part = 0;
+  if (threadIdx.x < tile * tile && p < L.npar) {
+    int px, py;
+    demorton((uint32_t)p, px, py);
+    const int lx = px - x0 + R, ly = py - y0 + R;
+    const T* Bd = (const T*)L.Bd;
+    const int64_t np = L.npar;
+    T y0v = 0, y1v = 0, y2v = 0;
+    for (int o = 0; o < L.noff; ++o) {
+      const int2 d = L.off[o];
+      const int c = (ly + d.y) * TS + lx + d.x;
+      const T a0 = xs[c], a1 = xs[TS * TS + c], a2 = xs[2 * TS * TS + c];
+      const T* B = Bd + (int64_t)o * 9 * np + p;
+      y0v += B[0] * a0 + B[np] * a1 + B[2 * np] * a2;
+      y1v += B[3 * np] * a0 + B[4 * np] * a1 + B[5 * np] * a2;
+      y2v += B[6 * np] * a0 + B[7 * np] * a1 + B[8 * np] * a2;
+    }
+    T* Ap = (T*)L.Ap;
+    Ap[4 * p] = y0v;
+    Ap[4 * p + 1] = y1v;
+    Ap[4 * p + 2] = y2v;
+    const int c0 = ly * TS + lx;
+    part = (double)xs[c0] * y0v + (double)xs[TS * TS + c0] * y1v +
+           (double)xs[2 * TS * TS + c0] * y2v;
+  }
+  block_sum_add(part, &sc[l].pAp, red);
+}
+
+// x += alpha p, r -= alpha Ap, z = Dinv r; rz_new += r.z, rr_new += r.r
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_update(const CgLevel* __restrict__ lv, int nlev,
+                                                   CgScalars* sc) {
+  __shared__ double red[8];
+  const int l = find_level(lv, nlev, blockIdx.x);
+  if (!sc[l].active) return;
+  const CgLevel L = lv[l];
+  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
+  double rz = 0, rr = 0;
+  if (p < L.npar) {
+    const double pAp = sc[l].pAp;
+    const T alpha = pAp > 0 ? (T)(sc[l].rz / pAp) : T(0);
+    T* x = (T*)L.x;
+    T* r = (T*)L.r;
+    T* z = (T*)L.z;
+    const T* pv = (const T*)L.p;
+    const T* Ap = (const T*)L.Ap;
+    T rv[3], zv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      x[4 * p + a] += alpha * pv[4 * p + a];
+      rv[a] = r[4 * p + a] - alpha * Ap[4 * p + a];
+      r[4 * p + a] = rv[a];
+    }
+    apply_dinv<T>((const T*)L.Dinv, L.npar, p, rv, zv);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      z[4 * p + a] = zv[a];
+      rz += (double)rv[a] * (double)zv[a];
+      rr += (double)rv[a] * (double)rv[a];
+    }
+  }
+  block_sum_add(rz, &sc[l].rz_new, red);
+  block_sum_add(rr, &sc[l].rr_new, red);
+}
+
+// beta, convergence on |r|_2, counters; one thread so any_active is exact
+__global__ void k_cg_scalars(CgScalars* sc, int nlev, double tol2, int max_iter,
+                             int* any_active) {
+  if (threadIdx.x != 0) return;
+  int act = 0;
+  for (int l = 0; l < nlev; ++l) {
+    CgScalars s = sc[l];
+    if (!s.active) continue;
+    s.iters += 1;
+    s.beta = s.rz > 0 ? s.rz_new / s.rz : 0.0;
+    s.rz = s.rz_new;
+    s.rr = s.rr_new;
+    s.rz_new = 0;
+    s.rr_new = 0;
+    s.pAp = 0;
+    if (s.rr <= tol2 * s.rr0 || s.iters >= max_iter || !(s.rr == s.rr) || !(s.rz > 0))
+      s.active = 0;
+    else
+      act = 1;
+    sc[l] = s;
+  }
+  *any_active = act;
+}
+
+// p = z + beta p
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_dir(const CgLevel* __restrict__ lv, int nlev,
+                                                CgScalars* sc) {
+  const int l = find_level(lv, nlev, blockIdx.x);
+  if (!sc[l].active) return;
+  const CgLevel L = lv[l];
+  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
+  if (p >= L.npar) return;
+  const T beta = (T)sc[l].beta;
+  T* pv = (T*)L.p;
+  const T* z = (const T*)L.z;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) pv[4 * p + a] = z[4 * p + a] + beta * pv[4 * p + a];
+}
+
+size_t cg_spmv_smem_bytes(int max_ts, size_t elem) { return 3 * elem * (size_t)max_ts * max_ts; }
+
+template <typename T>
+void launch_cg_init(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
+                    cudaStream_t s) {
+  if (total_blocks <= 0) return;
+  { count_launch(); k_cg_init<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
+}
+
+void launch_cg_start(CgScalars* sc, int nlev, double tol2, int* any_active, cudaStream_t s) {
+  { count_launch(); k_cg_start<<<1, 32, 0, s>>>(sc, nlev, tol2, any_active); }
+}
+
+template <typename T>
+void prepare_cg_spmv(int max_ts) {
+  const size_t smem = cg_spmv_smem_bytes(max_ts, sizeof(T));
+  cudaFuncSetAttribute(k_cg_spmv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+template void prepare_cg_spmv<float>(int);
+template void prepare_cg_spmv<double>(int);
+
+template <typename T>
+void launch_cg_spmv(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, int max_ts,
+                    cudaStream_t s) {
+  if (total_blocks <= 0) return;
+  const size_t smem = cg_spmv_smem_bytes(max_ts, sizeof(T));
+  { count_launch(); k_cg_spmv<T><<<total_blocks, 256, smem, s>>>(lv, nlev, sc); }
+}
+
+template <typename T>
+void launch_cg_rest(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, double tol2,
+                    int max_iter, int* any_active, cudaStream_t s) {
+  if (total_blocks <= 0) return;
+  { count_launch(); k_cg_update<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
+  { count_launch(); k_cg_scalars<<<1, 32, 0, s>>>(sc, nlev, tol2, max_iter, any_active); }
+  { count_launch(); k_cg_dir<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
+}
+
+template void launch_cg_init<float>(const CgLevel*, int, int, CgScalars*, cudaStream_t);
+template void launch_cg_init<double>(const CgLevel*, int, int, CgScalars*, cudaStream_t);
+template void launch_cg_spmv<float>(const CgLevel*, int, int, CgScalars*, int, cudaStream_t);
+template void launch_cg_spmv<double>(const CgLevel*, int, int, CgScalars*, int, cudaStream_t);
+template void launch_cg_rest<float>(const CgLevel*, int, int, CgScalars*, double, int, int*,
+                                    cudaStream_t);
+template void launch_cg_rest<double>(const CgLevel*, int, int, CgScalars*, double, int, int*,
+                                     cudaStream_t);
+
+// ---------------------------------------------------------------- set-up helpers
+// Bd[o][3a+b][p] = Ahat[o][p][4a+b] (detail block, coalesced copy).
+template <typename T>
+__global__ void k_extract_detail(const T* __restrict__ Ahat, int noff, int64_t npar, T* Bd) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)noff * npar) return;
+  const int o = (int)(t / npar);
+  const int64_t p = t - (int64_t)o * npar;
+  const T* A = Ahat + t * 16;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) Bd[((int64_t)o * 9 + 3 * a + b) * npar + p] = A[4 * a + b];
+}
+
+// Dinv[e][p] = inverse of the active leading block of the diagonal detail
+// block (zeros outside it), computed in float64.
+template <typename T>
+__global__ void k_detail_dinv(const T* __restrict__ Ahat, int o0, int64_t npar,
+                              const uint32_t* __restrict__ pmask, T* Dinv) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npar) return;
+  const int m = __popc(pmask[p] & 15u);
+  const int na = m > 0 ? m - 1 : 0;
+  double M[9], Inv[9];
+  for (int e = 0; e < 9; ++e) Inv[e] = 0.0;
+  const T* A = Ahat + ((int64_t)o0 * npar + p) * 16;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) M[3 * a + b] = (a < na && b < na) ? (double)A[4 * a + b] : 0.0;
+  // Gauss-Jordan on the na x na SPD block (no pivoting needed)
+  for (int a = 0; a < na; ++a) Inv[3 * a + a] = 1.0;
+  bool ok = true;
+  for (int c = 0; c < na; ++c) {
+    const double d = M[3 * c + c];
+    if (!(d > 0)) {
+      ok = false;
+      break;
+    }
+    for (int b = 0; b < 3; ++b) {
+      M[3 * c + b] /= d;
+      Inv[3 * c + b] /= d;
+    }
+    for (int a = 0; a < na; ++a) {
+      if (a == c) continue;
+      const double f = M[3 * a + c];
+      for (int b = 0; b < 3; ++b) {
+        M[3 * a + b] -= f * M[3 * c + b];
+        Inv[3 * a + b] -= f * Inv[3 * c + b];
+      }
+    }
+  }
+  for (int e = 0; e < 9; ++e) Dinv[(int64_t)e * npar + p] = ok ? (T)Inv[e] : T(0);
+}
+
+template <typename T>
+void launch_cg_level_setup(const T* Ahat, int noff, int o0, int64_t npar, const uint32_t* pmask,
+                           T* Bd, T* Dinv, cudaStream_t s) {
+  const int64_t n = (int64_t)noff * npar;
+  if (n > 0) {
+    count_launch();
+    k_extract_detail<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ahat, noff, npar, Bd);
+  }
+  if (npar > 0) {
+    count_launch();
+    k_detail_dinv<T><<<(unsigned)((npar + 255) / 256), 256, 0, s>>>(Ahat, o0, npar, pmask, Dinv);
+  }
+}
+template void launch_cg_level_setup<float>(const float*, int, int, int64_t, const uint32_t*,
+                                           float*, float*, cudaStream_t);
+template void launch_cg_level_setup<double>(const double*, int, int, int64_t, const uint32_t*,
+                                            double*, double*, cudaStream_t);
+
+}  // namespace gb

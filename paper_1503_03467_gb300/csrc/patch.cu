@@ -11,25 +11,47 @@
 //   Rhat[i][(p_j, t)] = y_(j,t),  Rhat[i][(i, 3)] = 1 / sqrt(m_i)
 // (R = pibar + D^T W with pibar Q^T = e_(i,3) / sqrt(m_i) and W Q^T = [I 0]).
 //
-// Layout: the patch system is padded to n = 3 NB unknowns; unknowns whose
+// Factorisation: the system is padded to n = 3 NB unknowns (unknowns whose
 // parent lies outside the lattice or has fewer children are decoupled
-// identity rows with zero right-hand side.  The right-hand side is carried
-// as row n of a packed lower-triangular augmented matrix, so the Cholesky
-// elimination also performs the forward substitution; one warp finishes
-// with the back substitution.  One CTA per patch, persistent over patches.
+// identity rows) and bordered by the right-hand side as the last row of
+// [[B, b], [b^T, c]] with c large, so the Cholesky factor's last row is
+// z = L^-1 b (the forward substitution comes free).  The lower triangle is
+// stored as 8 x 8 tiles (column-major inside a tile, tile stride padded to
+// an XOR swizzle against bank conflicts) and factored right-looking one tile
+// column at a time: one warp factors the diagonal tile, all threads solve
+// the tiles below it, then pairs of threads update the trailing tiles with
+// rank-8 products held in registers (4 x 8 accumulators each; small enough
+// for three float32 patches per SM).  One warp finishes
+// with the tile-blocked back substitution L^T y = z.  One CTA per patch,
+// persistent over the patches of the level.
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace gb {
 
-__host__ __device__ __forceinline__ int packed_size(int n) { return (n + 1) * (n + 2) / 2; }
+constexpr int kTile = 8;
+constexpr int kTileStride = 64;
+constexpr int kPatchThreads = 256;
+
+// Element idx = 8 c + r of tile t sits at t * 64 + (idx ^ swz(t)): the XOR on
+// bits 2..4 spreads equal offsets of different tiles over different bank
+// groups while keeping every aligned group of four elements contiguous.
+__host__ __device__ __forceinline__ int swz(int t) { return (t & 7) << 2; }
+
+__host__ __device__ __forceinline__ int patch_rows(int NB) {
+  return ((3 * NB + 1 + kTile - 1) / kTile) * kTile;  // unknowns + rhs row, padded
+}
+__host__ __device__ __forceinline__ int tri_tiles(int nt) { return nt * (nt + 1) / 2; }
+__host__ __device__ __forceinline__ int tile_index(int I, int K) { return I * (I + 1) / 2 + K; }
 
 template <typename T>
 size_t patch_smem_bytes(int NB) {
-  int n = 3 * NB;
-  size_t b = sizeof(T) * (size_t)packed_size(n);     // augmented packed matrix
-  b += sizeof(T) * (size_t)(n + 1);                   // column buffer / solution
-  b += sizeof(int) * 2 * (size_t)NB;                  // parent index, child count
+  const int nt = patch_rows(NB) / kTile;
+  size_t b = sizeof(T) * (size_t)tri_tiles(nt) * kTileStride;  // factor tiles
+  b += sizeof(T) * (size_t)patch_rows(NB);                      // solution vector
+  b += sizeof(T) * kTile;                                       // reciprocal pivots
+  b += sizeof(int) * 2 * (size_t)NB;                            // parent index, child count
+  b += sizeof(int) * (size_t)patch_rows(NB);                    // row descriptors
   return (b + 15) & ~(size_t)15;
 }
 template size_t patch_smem_bytes<float>(int);
@@ -43,131 +65,259 @@ template <>
 __device__ __forceinline__ double dev_sqrt<double>(double v) { return sqrt(v); }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_patch_solve(const T* __restrict__ Ahat,
-                                                     const uint32_t* __restrict__ pmask,
-                                                     PatchGeom g, T* __restrict__ Rhat,
-                                                     int* status) {
+__device__ __forceinline__ T big_corner();
+template <>
+__device__ __forceinline__ float big_corner<float>() { return 1e30f; }
+template <>
+__device__ __forceinline__ double big_corner<double>() { return 1e200; }
+
+// element (r, c), r >= c, of the tiled lower triangle
+template <typename T>
+__device__ __forceinline__ T& tel(T* M, int r, int c) {
+  const int t = tile_index(r / kTile, c / kTile);
+  return M[t * kTileStride + (((c % kTile) * kTile + (r % kTile)) ^ swz(t))];
+}
+
+// float32: three CTAs per SM (registers <= 85); float64 is ALU-bound anyway.
+template <typename T>
+struct PatchOcc {
+  static constexpr int kMinBlocks = 1;
+};
+template <>
+struct PatchOcc<float> {
+  static constexpr int kMinBlocks = 3;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kPatchThreads, PatchOcc<T>::kMinBlocks)
+    k_patch_solve(const T* __restrict__ Ahat,
+                                                               const uint32_t* __restrict__ pmask,
+                                                               PatchGeom g, T* __restrict__ Rhat,
+                                                               int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = g.NB;
-  const int n = 3 * NB;
+  const int n = 3 * NB;               // patch unknowns (padded layout)
+  const int N1 = patch_rows(NB);      // rows incl. padding and the rhs row
+  const int NT = N1 / kTile;
+  const int rhs = N1 - 1;             // the bordering row
   T* M = reinterpret_cast<T*>(smem_raw);
-  T* col = M + packed_size(n);
-  int* pj = reinterpret_cast<int*>(col + (n + 1));
+  T* y = M + tri_tiles(NT) * kTileStride;
+  T* rinv = y + N1;
+  int* pj = reinterpret_cast<int*>(rinv + kTile);
   int* mj = pj + NB;
+  int* rowd = mj + NB;  // (j << 2 | t) of an active unknown, -1 otherwise
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const int nwarp = blockDim.x >> 5;
+  const int nwarp = kPatchThreads / 32;
   const int64_t np = g.npatch;
 
   for (int64_t i = blockIdx.x; i < np; i += gridDim.x) {
     const uint32_t mi = pmask[i] & 15u;
     if (mi == 0) {  // empty coarse cell: no gamblet
-      for (int idx = tid; idx < NB * 4; idx += blockDim.x) Rhat[(int64_t)idx * np + i] = T(0);
+      for (int idx = tid; idx < NB * 4; idx += kPatchThreads) Rhat[i * 4 * NB + idx] = T(0);
       continue;
     }
     const T inv_sqrt_mi = T(1) / dev_sqrt<T>(T(__popc(mi)));
     int xi, yi;
     demorton((uint32_t)i, xi, yi);
-    for (int j = tid; j < NB; j += blockDim.x) {
-      int p = shift_cell(xi, yi, g.nbr[j].x, g.nbr[j].y, g.Lpar);
+    for (int j = tid; j < NB; j += kPatchThreads) {
+      const int p = shift_cell(xi, yi, g.nbr[j].x, g.nbr[j].y, g.Lpar);
       pj[j] = p;
       mj[j] = p >= 0 ? __popc(pmask[p] & 15u) : 0;
     }
     __syncthreads();
 
-    // ---- gather the augmented packed matrix [B b; b^T *]
-    for (int r = warp; r <= n; r += nwarp) {
-      const int base = r * (r + 1) / 2;
+    for (int r = tid; r < N1; r += kPatchThreads) {
+      int d = -1;
       if (r < n) {
-        const int ja = r / 3, ta = r - 3 * ja;
-        const int pa = pj[ja];
-        const bool acta = pa >= 0 && ta < mj[ja] - 1;
+        const int j = r / 3, t = r - 3 * j;
+        if (pj[j] >= 0 && t < mj[j] - 1) d = (j << 2) | t;
+      }
+      rowd[r] = d;
+    }
+    __syncthreads();
+
+    // ---- gather [B b; b^T c] into the tiles (lower triangle)
+    for (int r = warp; r < N1; r += nwarp) {
+      const int da = rowd[r];
+      if (r < n) {
+        const int ja = da >> 2, ta = da & 3;
+        const int pa = da >= 0 ? pj[ja] : 0;
+        const int* prow = g.pair_idx + ja * NB;
         for (int c = lane; c <= r; c += 32) {
-          const int jb = c / 3, tb = c - 3 * jb;
-          const bool actb = pj[jb] >= 0 && tb < mj[jb] - 1;
+          const int db = rowd[c];
           T v;
-          if (acta && actb) {
-            const int o = g.pair_idx[ja * NB + jb];
-            v = o >= 0 ? Ahat[((int64_t)o * np + pa) * 16 + ta * 4 + tb] : T(0);
+          if (da >= 0 && db >= 0) {
+            const int o = prow[db >> 2];
+            v = o >= 0 ? Ahat[((int64_t)o * np + pa) * 16 + ta * 4 + (db & 3)] : T(0);
           } else {
             v = (r == c) ? T(1) : T(0);
           }
-          M[base + c] = v;
+          tel(M, r, c) = v;
         }
-      } else {
-        for (int c = lane; c <= n; c += 32) {
+      } else if (r < rhs) {  // padding rows: identity
+        for (int c = lane; c <= r; c += 32) tel(M, r, c) = (r == c) ? T(1) : T(0);
+      } else {  // bordering row b^T and the corner
+        for (int c = lane; c <= r; c += 32) {
           T v = T(0);
-          if (c < n) {
-            const int jb = c / 3, tb = c - 3 * jb;
-            const int pb = pj[jb];
-            if (pb >= 0 && tb < mj[jb] - 1) {
-              const int o = g.pair_idx[jb * NB + g.jc];
-              if (o >= 0) v = -inv_sqrt_mi * Ahat[((int64_t)o * np + pb) * 16 + tb * 4 + 3];
-            }
-          } else {
-            v = T(1);
+          const int db = c < n ? rowd[c] : -1;
+          if (db >= 0) {
+            const int jb = db >> 2;
+            const int o = g.pair_idx[jb * NB + g.jc];
+            if (o >= 0) v = -inv_sqrt_mi * Ahat[((int64_t)o * np + pj[jb]) * 16 + (db & 3) * 4 + 3];
+          } else if (c == rhs) {
+            v = big_corner<T>();
           }
-          M[base + c] = v;
+          tel(M, r, c) = v;
         }
       }
     }
     __syncthreads();
 
-    // ---- right-looking Cholesky on the first n columns of the augmented matrix
-    for (int j = 0; j < n; ++j) {
-      const int jj = j * (j + 1) / 2 + j;
-      T d = M[jj];
-      if (!(d > T(0))) {  // non-positive or NaN pivot
-        if (tid == 0) atomicExch(status, (int)DEV_NOT_SPD);
-        d = T(1);
-      }
-      const T s = dev_sqrt<T>(d);
-      const T inv = T(1) / s;
-      for (int r = j + 1 + tid; r <= n; r += blockDim.x) {
-        const int idx = r * (r + 1) / 2 + j;
-        const T l = M[idx] * inv;
-        M[idx] = l;
-        col[r] = l;
+    // ---- right-looking tiled Cholesky
+    for (int J = 0; J < NT; ++J) {
+      const int tJ = tile_index(J, J);
+      T* D = M + tJ * kTileStride;
+      const int sJ = swz(tJ);
+      // (1) diagonal tile, one warp; lane l < 8 owns row l during the sweep
+      if (warp == 0) {
+        for (int c = 0; c < kTile; ++c) {
+          T d = D[(c * kTile + c) ^ sJ];
+          if (!(d > T(0))) {
+            if (lane == 0) atomicExch(status, (int)DEV_NOT_SPD);
+            d = T(1);
+          }
+          const T s = dev_sqrt<T>(d);
+          const T is = T(1) / s;
+          __syncwarp();
+          if (lane == 0) {
+            D[(c * kTile + c) ^ sJ] = s;
+            rinv[c] = is;
+          }
+          if (lane > c && lane < kTile) D[(c * kTile + lane) ^ sJ] *= is;
+          __syncwarp();
+          // rank-1 update of the remaining lower part: lanes cover (r, cc), c < cc <= r < 8
+          for (int e = lane; e < kTile * kTile; e += 32) {
+            const int r = e % kTile, cc = e / kTile;
+            if (cc > c && r >= cc)
+              D[(cc * kTile + r) ^ sJ] -= D[(c * kTile + r) ^ sJ] * D[(c * kTile + cc) ^ sJ];
+          }
+          __syncwarp();
+        }
       }
       __syncthreads();
-      if (tid == 0) M[jj] = s;
-      for (int r = j + 1 + warp; r <= n; r += nwarp) {
-        const T lr = col[r];
-        if (lr == T(0)) continue;
-        const int base = r * (r + 1) / 2;
-        const int cmax = r < n ? r : n - 1;
-        for (int c = j + 1 + lane; c <= cmax; c += 32) M[base + c] -= lr * col[c];
+      // (2) tiles below: L_IJ = A_IJ L_JJ^-T, one thread per row
+      const int below = (NT - 1 - J) * kTile;
+      for (int t = tid; t < below; t += kPatchThreads) {
+        const int I = J + 1 + t / kTile, rr = t % kTile;
+        const int tI = tile_index(I, J), sI = swz(tI);
+        T* A = M + tI * kTileStride;
+        T x[kTile];
+#pragma unroll
+        for (int c = 0; c < kTile; ++c) {
+          T v = A[(c * kTile + rr) ^ sI];
+#pragma unroll
+          for (int cp = 0; cp < c; ++cp) v -= D[(cp * kTile + c) ^ sJ] * x[cp];
+          x[c] = v * rinv[c];
+        }
+#pragma unroll
+        for (int c = 0; c < kTile; ++c) A[(c * kTile + rr) ^ sI] = x[c];
+      }
+      __syncthreads();
+      // (3) trailing update: A_IK -= L_IJ L_KJ^T for J < K <= I; two threads
+      //     per tile, each owning 4 rows x 8 columns in registers
+      const int m = NT - 1 - J;
+      const int count = m * (m + 1) / 2;
+      for (int t2 = tid; t2 < 2 * count; t2 += kPatchThreads) {
+        const int t = t2 >> 1, half = t2 & 1;
+        int ii = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+        while (ii * (ii + 1) / 2 > t) --ii;
+        while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+        const int kk = t - ii * (ii + 1) / 2;
+        const int I = J + 1 + ii, K = J + 1 + kk;
+        const int tI = tile_index(I, J), tK = tile_index(K, J), tC = tile_index(I, K);
+        const int sI = swz(tI), sK = swz(tK), sC = swz(tC);
+        const T* LI = M + tI * kTileStride;
+        const T* LK = M + tK * kTileStride;
+        T* C = M + tC * kTileStride;
+        const int h4 = 4 * half;
+        T acc[4][kTile];
+#pragma unroll
+        for (int c = 0; c < kTile; ++c) {
+          const T* cp = C + ((c * kTile + h4) ^ sC);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc[r][c] = cp[r];
+        }
+#pragma unroll
+        for (int q = 0; q < kTile; ++q) {
+          T a[4], b[kTile];
+          const T* ap = LI + ((q * kTile + h4) ^ sI);
+          const T* b0 = LK + ((q * kTile) ^ sK);
+          const T* b1 = LK + ((q * kTile + 4) ^ sK);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) a[r] = ap[r];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            b[c] = b0[c];
+            b[c + 4] = b1[c];
+          }
+#pragma unroll
+          for (int c = 0; c < kTile; ++c)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[r][c] -= a[r] * b[c];
+        }
+#pragma unroll
+        for (int c = 0; c < kTile; ++c) {
+          T* cp = C + ((c * kTile + h4) ^ sC);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) cp[r] = acc[r][c];
+        }
       }
       __syncthreads();
     }
 
-    // ---- back substitution L^T y = z, z = row n (one warp)
+    // ---- back substitution L^T y = z (z = bordering row), one warp
     if (warp == 0) {
-      const int zb = n * (n + 1) / 2;
-      for (int c = lane; c < n; c += 32) col[c] = M[zb + c];
+      for (int c = lane; c < rhs; c += 32) y[c] = tel(M, rhs, c);
       __syncwarp();
-      for (int j = n - 1; j >= 0; --j) {
-        const int rb = j * (j + 1) / 2;
-        const T yj = col[j] / M[rb + j];
+      for (int I = NT - 1; I >= 0; --I) {
+        const int r0 = I * kTile;
+        const int r1 = min(r0 + kTile, rhs);  // exclusive; skips the bordering row
+        const int tD = tile_index(I, I), sD = swz(tD);
+        const T* Dt = M + tD * kTileStride;
+        if (lane == 0) {
+          for (int r = r1 - 1; r >= r0; --r) {
+            T v = y[r];
+            for (int rp = r + 1; rp < r1; ++rp) v -= Dt[((r - r0) * kTile + (rp - r0)) ^ sD] * y[rp];
+            y[r] = v / Dt[((r - r0) * kTile + (r - r0)) ^ sD];
+          }
+        }
         __syncwarp();
-        for (int c = lane; c < j; c += 32) col[c] -= M[rb + c] * yj;
-        if (lane == 0) col[j] = yj;
+        // subtract block I's contribution from the rows above it
+        for (int c = lane; c < r0; c += 32) {
+          const int tL = tile_index(I, c / kTile), sL = swz(tL);
+          const T* Lt = M + tL * kTileStride;
+          const int cb = (c % kTile) * kTile;
+          T v = y[c];
+          for (int r = r0; r < r1; ++r) v -= Lt[(cb + r - r0) ^ sL] * y[r];
+          y[c] = v;
+        }
         __syncwarp();
       }
     }
     __syncthreads();
 
-    // ---- interpolation row of coarse cell i (SoA over [j][slot])
-    for (int idx = tid; idx < NB * 4; idx += blockDim.x) {
+    // ---- interpolation row of coarse cell i (row-contiguous [j][slot])
+    for (int idx = tid; idx < NB * 4; idx += kPatchThreads) {
       const int j = idx >> 2, c = idx & 3;
       T v = T(0);
       if (c < 3) {
-        if (pj[j] >= 0 && c < mj[j] - 1) v = col[3 * j + c];
+        if (pj[j] >= 0 && c < mj[j] - 1) v = y[3 * j + c];
       } else if (j == g.jc) {
         v = inv_sqrt_mi;
       }
-      Rhat[(int64_t)idx * np + i] = v;
+      Rhat[i * 4 * NB + idx] = v;
     }
     __syncthreads();
   }
@@ -181,11 +331,11 @@ void launch_patch_solve(const T* Ahat, const uint32_t* pmask_k, PatchGeom g, T* 
   cudaFuncSetAttribute(k_patch_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_patch_solve<T>, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_patch_solve<T>, kPatchThreads, smem);
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)num_sms * per_sm;
   if (grid > g.npatch) grid = g.npatch;
-  { count_launch(); k_patch_solve<T><<<(unsigned)grid, 256, smem, s>>>(Ahat, pmask_k, g, Rhat, status); }
+  { count_launch(); k_patch_solve<T><<<(unsigned)grid, kPatchThreads, smem, s>>>(Ahat, pmask_k, g, Rhat, status); }
 }
 template void launch_patch_solve<float>(const float*, const uint32_t*, PatchGeom, float*, int*,
                                         int, cudaStream_t);

@@ -18,11 +18,12 @@ __global__ void k_restrict(const T* __restrict__ Rhat, int NB, const int2* __res
   if (i < nrow) {
     int x, y;
     demorton((uint32_t)i, x, y);
+    const T* row = Rhat + i * 4 * NB;
     for (int j = 0; j < NB; ++j) {
       const int p = shift_cell(x, y, nbr[j].x, nbr[j].y, Lpar);
       if (p < 0) continue;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc += Rhat[(int64_t)(4 * j + c) * nrow + i] * ghat[4 * p + c];
+      for (int c = 0; c < 4; ++c) acc += row[4 * j + c] * ghat[4 * p + c];
     }
   }
   if (pmask_km1 == nullptr) {
@@ -79,9 +80,10 @@ __global__ void k_prolong(const T* __restrict__ Rhat, int NB, const int2* __rest
       if (i < 0) continue;
       const T vi = v[i];
       if (vi == T(0)) continue;
-      h0 += Rhat[(int64_t)(4 * j) * npar + i] * vi;
-      h1 += Rhat[(int64_t)(4 * j + 1) * npar + i] * vi;
-      h2 += Rhat[(int64_t)(4 * j + 2) * npar + i] * vi;
+      const T* rr = Rhat + (int64_t)i * 4 * NB + 4 * j;
+      h0 += rr[0] * vi;
+      h1 += rr[1] * vi;
+      h2 += rr[2] * vi;
     }
   }
   if (inverse) {
@@ -112,13 +114,7 @@ template void launch_prolong<double>(const double*, int, const int2*, int, int64
                                      const double*, const double*, const uint32_t*, int, double*,
                                      cudaStream_t);
 
-// ---------------------------------------------------------------- batched level CG
-__device__ __forceinline__ int find_level(const CgLevel* lv, int nlev, int b) {
-  int l = 0;
-  while (l + 1 < nlev && lv[l + 1].block_begin <= b) ++l;
-  return l;
-}
-
+// ---------------------------------------------------------------- reductions
 __device__ __forceinline__ void block_atomic_add(double v, double* dst) {
   __shared__ double red[32];
   v = warp_sum(v);
@@ -130,173 +126,8 @@ __device__ __forceinline__ void block_atomic_add(double v, double* dst) {
     v = warp_sum(v);
     if (lane == 0 && v != 0.0) atomicAdd(dst, v);
   }
+  __syncthreads();  // red[] may be reused by the next call
 }
-
-// r = b (detail slots), x = 0, p = r, rr = r.r
-template <typename T>
-__global__ void k_cg_init(const CgLevel* __restrict__ lv, int nlev, CgScalars* sc) {
-  const int l = find_level(lv, nlev, blockIdx.x);
-  const CgLevel L = lv[l];
-  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
-  double part = 0;
-  if (p < L.npar) {
-    const T* b = (const T*)L.b;
-    T* x = (T*)L.x;
-    T* r = (T*)L.r;
-    T* pp = (T*)L.p;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const T v = a < 3 ? b[4 * p + a] : T(0);
-      x[4 * p + a] = 0;
-      r[4 * p + a] = v;
-      pp[4 * p + a] = v;
-      part += (double)v * (double)v;
-    }
-  }
-  block_atomic_add(part, &sc[l].rr);
-}
-
-__global__ void k_cg_start(CgScalars* sc, int nlev, int* any_active) {
-  const int l = threadIdx.x;
-  if (l < nlev) {
-    sc[l].rr0 = sc[l].rr;
-    sc[l].active = sc[l].rr > 0.0;
-    sc[l].iters = 0;
-    sc[l].pAp = 0;
-    sc[l].rr_new = 0;
-    if (sc[l].active) atomicExch(any_active, 1);
-  }
-}
-
-template <typename T>
-void launch_cg_init(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
-                    cudaStream_t s) {
-  if (total_blocks <= 0) return;
-  { count_launch(); k_cg_init<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
-}
-
-// Ap = B p over the 3x3 detail blocks; pAp += p.Ap
-template <typename T>
-__global__ void k_cg_spmv(const CgLevel* __restrict__ lv, int nlev, CgScalars* sc) {
-  const int l = find_level(lv, nlev, blockIdx.x);
-  if (!sc[l].active) return;
-  const CgLevel L = lv[l];
-  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
-  double part = 0;
-  if (p < L.npar) {
-    const T* A = (const T*)L.Ahat;
-    const T* pv = (const T*)L.p;
-    T y0 = 0, y1 = 0, y2 = 0;
-    int x, y;
-    demorton((uint32_t)p, x, y);
-    for (int o = 0; o < L.noff; ++o) {
-      const int q = shift_cell(x, y, L.off[o].x, L.off[o].y, L.Lpar);
-      if (q < 0) continue;
-      const T* blk = A + ((int64_t)o * L.npar + p) * 16;
-      const T x0 = pv[4 * q], x1 = pv[4 * q + 1], x2 = pv[4 * q + 2];
-      y0 += blk[0] * x0 + blk[1] * x1 + blk[2] * x2;
-      y1 += blk[4] * x0 + blk[5] * x1 + blk[6] * x2;
-      y2 += blk[8] * x0 + blk[9] * x1 + blk[10] * x2;
-    }
-    T* Ap = (T*)L.Ap;
-    Ap[4 * p] = y0;
-    Ap[4 * p + 1] = y1;
-    Ap[4 * p + 2] = y2;
-    Ap[4 * p + 3] = 0;
-    part = (double)pv[4 * p] * y0 + (double)pv[4 * p + 1] * y1 + (double)pv[4 * p + 2] * y2;
-  }
-  block_atomic_add(part, &sc[l].pAp);
-}
-
-// x += alpha p, r -= alpha Ap, rr_new += r.r
-template <typename T>
-__global__ void k_cg_axpy(const CgLevel* __restrict__ lv, int nlev, CgScalars* sc) {
-  const int l = find_level(lv, nlev, blockIdx.x);
-  if (!sc[l].active) return;
-  const CgLevel L = lv[l];
-  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
-  double part = 0;
-  if (p < L.npar) {
-    const double pAp = sc[l].pAp;
-    const T alpha = pAp > 0 ? (T)(sc[l].rr / pAp) : T(0);
-    T* x = (T*)L.x;
-    T* r = (T*)L.r;
-    const T* pv = (const T*)L.p;
-    const T* Ap = (const T*)L.Ap;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      x[4 * p + a] += alpha * pv[4 * p + a];
-      const T rv = r[4 * p + a] - alpha * Ap[4 * p + a];
-      r[4 * p + a] = rv;
-      part += (double)rv * (double)rv;
-    }
-  }
-  block_atomic_add(part, &sc[l].rr_new);
-}
-
-// beta, convergence, counters; one thread, so any_active is exact
-__global__ void k_cg_scalars(CgScalars* sc, int nlev, double tol2, int max_iter,
-                             int* any_active) {
-  if (threadIdx.x != 0) return;
-  int act = 0;
-  for (int l = 0; l < nlev; ++l) {
-    CgScalars st = sc[l];
-    if (!st.active) continue;
-    st.iters += 1;
-    st.beta = st.rr > 0 ? st.rr_new / st.rr : 0.0;
-    st.rr = st.rr_new;
-    st.rr_new = 0;
-    st.pAp = 0;
-    if (st.rr <= tol2 * st.rr0 || st.iters >= max_iter || !(st.rr == st.rr)) st.active = 0;
-    else act = 1;
-    sc[l] = st;
-  }
-  *any_active = act;
-}
-
-// p = r + beta p
-template <typename T>
-__global__ void k_cg_dir(const CgLevel* __restrict__ lv, int nlev, CgScalars* sc) {
-  const int l = find_level(lv, nlev, blockIdx.x);
-  if (!sc[l].active) return;
-  const CgLevel L = lv[l];
-  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
-  if (p >= L.npar) return;
-  const T beta = (T)sc[l].beta;
-  T* pv = (T*)L.p;
-  const T* r = (const T*)L.r;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) pv[4 * p + a] = r[4 * p + a] + beta * pv[4 * p + a];
-}
-
-template <typename T>
-void launch_cg_spmv(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
-                    cudaStream_t s) {
-  if (total_blocks <= 0) return;
-  { count_launch(); k_cg_spmv<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
-}
-
-template <typename T>
-void launch_cg_rest(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, double tol2,
-                    int max_iter, int* any_active, cudaStream_t s) {
-  if (total_blocks <= 0) return;
-  { count_launch(); k_cg_axpy<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
-  { count_launch(); k_cg_scalars<<<1, 32, 0, s>>>(sc, nlev, tol2, max_iter, any_active); }
-  { count_launch(); k_cg_dir<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
-}
-
-void launch_cg_start(CgScalars* sc, int nlev, int* any_active, cudaStream_t s) {
-  { count_launch(); k_cg_start<<<1, 32, 0, s>>>(sc, nlev, any_active); }
-}
-
-template void launch_cg_init<float>(const CgLevel*, int, int, CgScalars*, cudaStream_t);
-template void launch_cg_init<double>(const CgLevel*, int, int, CgScalars*, cudaStream_t);
-template void launch_cg_spmv<float>(const CgLevel*, int, int, CgScalars*, cudaStream_t);
-template void launch_cg_spmv<double>(const CgLevel*, int, int, CgScalars*, cudaStream_t);
-template void launch_cg_rest<float>(const CgLevel*, int, int, CgScalars*, double, int, int*,
-                                    cudaStream_t);
-template void launch_cg_rest<double>(const CgLevel*, int, int, CgScalars*, double, int, int*,
-                                     cudaStream_t);
 
 // ---------------------------------------------------------------- coarsest level
 // A^(1) (4 x 4, float64) from the level-1 cell stencil; Cholesky in place.
@@ -306,9 +137,10 @@ __global__ void k_level1_factor(const T* __restrict__ Acell, const int* __restri
   if (threadIdx.x != 0) return;
   double M[16];
   for (int e = 0; e < 16; ++e) {
-    const int i = e / 4;
+    const int i = e / 4, j = e % 4;
     const int d = map[e];
-    M[e] = d >= 0 ? (double)Acell[(int64_t)d * 4 + i] : 0.0;
+    M[e] = d >= 0 ? (double)Acell[(int64_t)d * 4 + i]
+                  : (d <= -2 ? (double)Acell[(int64_t)(-d - 2) * 4 + j] : 0.0);
   }
   // inactive cells (zero row and column) become identity rows
   for (int i = 0; i < 4; ++i) {
