@@ -258,14 +258,26 @@ def rel_err(u, ud):
     return float(np.linalg.norm(u - ud) / np.linalg.norm(ud))
 
 
+def families(stats):
+    """Per-level entries (name_kN) summed into kernel families."""
+    out = {}
+    for k, v in stats.items():
+        base = k.rsplit("_k", 1)[0] if "_k" in k and k.rsplit("_k", 1)[1].isdigit() else k
+        acc = out.setdefault(base, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+        for key in acc:
+            acc[key] += v[key]
+    return out
+
+
 def roofline(stats, peaks, clocks, mixed):
-    """Roofline entry of the kernel with the largest share of device time."""
+    """Roofline entry of the kernel family with the largest share of device time."""
+    stats = families(stats)
     name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
     avg_ms = st["ms"] / max(st["launches"], 1)
     per_launch_bytes = st["bytes"] / max(st["launches"], 1)
     per_launch_flops = st["flops"] / max(st["launches"], 1)
     total_ms = sum(s["ms"] for s in stats.values())
-    if name == "patch_solve":
+    if name in ("patch_pcg", "patch_cholesky"):
         # SIMT arithmetic bound: 152 SMs x 128 lanes (fp32) or the nominal
         # float64 rate, at the maximum SM clock
         if mixed:
@@ -379,9 +391,9 @@ def main():
                 "rel_err": err_e2e},
         "roofline": roofline(mixed["stats"], peaks, mixed["clocks"], True),
         "clocks": mixed["clocks"],
-        "kernels": {k: {"share": v["ms"] / sum(s["ms"] for s in mixed["stats"].values()),
+        "kernels": {k: {"share": v["ms"] / sum(s["ms"] for s in families(mixed["stats"]).values()),
                         "ms_per_step": v["ms"] / a.steps, "launches_per_step": v["launches"] / a.steps}
-                    for k, v in sorted(mixed["stats"].items(), key=lambda kv: -kv[1]["ms"])},
+                    for k, v in sorted(families(mixed["stats"]).items(), key=lambda kv: -kv[1]["ms"])},
     }
     if plain is not None:
         pms = statistics.mean(plain["times_ms"])

@@ -86,6 +86,11 @@ typedef struct {
   double refine_tol;        /* outer float64 relative residual target      */
   int32_t refine_max_iter;  /* cap on outer flexible-CG iterations; 0 = the
                                one-pass transform of Algorithm 2 only      */
+  /* Patch systems of Definition defb: > 0 = block-Jacobi preconditioned CG
+   * to this relative residual (Sec. 5.4 / Thm tmdiscreteaccuracy allow
+   * inexact patch solves); 0 = default (1e-6 mixed, 1e-12 float64);
+   * < 0 = dense Cholesky (exact to rounding).                              */
+  double patch_tol;
   int32_t use_graph;        /* capture repeated launch sequences in CUDA graphs */
   int32_t profile;          /* 1: time every kernel phase with CUDA events on
                                the library's stream (gamblet_kernel_stats)  */
@@ -100,6 +105,8 @@ typedef struct {
   double rel_residual;      /* |g - A u|_2 / |g|_2 in float64 at exit       */
   double setup_ms;          /* device time of the last gamblet_setup        */
   double solve_ms;          /* device time of this call                     */
+  int32_t patch_iters_max;  /* largest patch CG iteration count in setup (0 = Cholesky) */
+  double patch_iters_mean;  /* mean patch CG iterations per patch in setup  */
 } gamblet_info;
 
 typedef struct gamblet_ctx* gamblet_handle;
@@ -188,6 +195,26 @@ GAMBLET_API gamblet_status gamblet_grad(gamblet_handle h, int32_t ncell, const i
 GAMBLET_API gamblet_status gamblet_objective_noalloc(int32_t n, const double* u,
                                                      const double* u_obs, double* J,
                                                      void* stream);
+
+/*
+ * Values of the fine operator of Sec. 5.1 (Eq. eqhuiuhiuhuiu) for a
+ * coefficient constant on each cell: A = sum_c exp(log_a[c]) K_ref restricted
+ * to the cell's interior corners, written into an existing CSR pattern.
+ *   n, rowptr, colind, nnz  the pattern (device pointers); every pair of
+ *                 interior corners of a cell must be present in it.
+ *   ncell, cell_nodes  ncell x 4 int32 fine unknown of each corner, -1 on the
+ *                 Dirichlet boundary (device pointer).
+ *   log_a         ncell float64 (device pointer).
+ *   K_ref         4 x 4 float64 element matrix (host or device).
+ *   val           nnz float64 output (device pointer), overwritten.
+ *   cell_a        NULL or ncell float64 output (device): exp(log_a).
+ * Returns INVALID_ARG if a corner pair is missing from the pattern.
+ */
+GAMBLET_API gamblet_status gamblet_assemble_cells(int32_t n, const int32_t* rowptr,
+                                                  const int32_t* colind, int64_t nnz,
+                                                  int32_t ncell, const int32_t* cell_nodes,
+                                                  const double* log_a, const double* K_ref,
+                                                  double* val, double* cell_a, void* stream);
 
 /* Number of nodes n_k = |I^(k)| and detail rows |J^(k)| at level k. */
 GAMBLET_API gamblet_status gamblet_level_size(gamblet_handle h, int32_t k, int32_t* n_k, int32_t* nJ_k);

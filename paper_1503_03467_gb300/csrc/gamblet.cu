@@ -328,6 +328,11 @@ struct gamblet_ctx {
   int* status = nullptr;
   int* status_h = nullptr;   // pinned
   double setup_ms = 0;
+  double patch_tol = 0;         // resolved patch tolerance (< 0: Cholesky)
+  int* patch_stats = nullptr;   // device: max, sum, count over all levels
+  int patch_iters_max = 0;
+  double patch_iters_mean = 0;
+  std::vector<double> patch_flops_iter_k;  // per level: flops of one iteration of one patch
   int level_iters_acc[32];
   bool level_not_conv = false;
 };
@@ -546,9 +551,12 @@ void setup_local(gamblet_ctx* h) {
   Pool& P = h->pool;
   const int q = h->q;
   const int NB = h->N.size();
-  if ((size_t)patch_smem_bytes<T>(NB) > 227 * 1024)
+  if (h->patch_tol < 0 && patch_smem_bytes<T>(NB) > 227 * 1024)
     fail(GAMBLET_ERR_UNSUPPORTED, "patch of " + std::to_string(3 * NB) +
                                       " unknowns exceeds on-chip capacity; lower rho");
+  if (NB > 256) fail(GAMBLET_ERR_UNSUPPORTED, "patch neighbourhood too large; lower rho");
+  h->patch_stats = P.zeros<int>(4 * (q + 1), s);
+  h->patch_flops_iter_k.assign(q + 1, 0.0);
   // level q values in T
   {
     LevelDev& L = h->lv[q];
@@ -572,10 +580,47 @@ void setup_local(gamblet_ctx* h) {
     T* Rhat = P.alloc<T>((int64_t)NB * 4 * L.npar);
     PatchGeom pg{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar};
     const double sz = (double)sizeof(T);
-    int tok = h->prof.begin("patch_solve", sz * ((double)L.noff * L.npar * 16 + 4.0 * NB * L.npar),
-                            h->prof.on ? patch_flops(h, k) : 0.0, s);
-    launch_patch_solve<T>((const T*)L.Ahat, L.pmask, pg, Rhat, h->status, h->num_sms, s);
-    h->prof.end(tok, s);
+    const double pbytes = sz * ((double)L.noff * L.npar * 16 + 4.0 * NB * L.npar);
+    if (h->patch_tol < 0) {
+      int tok = h->prof.begin("patch_cholesky", pbytes, h->prof.on ? patch_flops(h, k) : 0.0, s);
+      launch_patch_solve<T>((const T*)L.Ahat, L.pmask, pg, Rhat, h->status, h->num_sms, s);
+      h->prof.end(tok, s);
+    } else {
+      // stored blocks: pairs (ja >= jb) coupled through O_k; per-row adjacency
+      std::vector<int4> half, adj;
+      std::vector<int> adj_ptr(NB + 1, 0), diag_h(NB, -1);
+      std::vector<std::vector<int4>> rows(NB);
+      for (int ja = 0; ja < NB; ++ja)
+        for (int jb = 0; jb <= ja; ++jb) {
+          const int o = S.pair_idx[(size_t)ja * NB + jb];
+          if (o < 0) continue;
+          const int hidx = (int)half.size();
+          half.push_back(make_int4(ja, jb, o, 0));
+          rows[ja].push_back(make_int4(hidx, jb, 0, 0));
+          if (jb != ja) rows[jb].push_back(make_int4(hidx, ja, 1, 0));
+          else diag_h[ja] = hidx;
+        }
+      for (int j = 0; j < NB; ++j) {
+        if (diag_h[j] < 0) fail(GAMBLET_ERR_INVALID_ARG, "patch block without diagonal");
+        adj_ptr[j + 1] = adj_ptr[j] + (int)rows[j].size();
+        adj.insert(adj.end(), rows[j].begin(), rows[j].end());
+      }
+      // long block rows (dense coarse levels) are split over 2 or 4 lanes
+      const double row_len = (double)adj.size() / NB;
+      int spp = row_len > 24 ? 4 : (row_len > 12 ? 2 : 1);
+      while (spp > 1 && NB * spp > 256) spp >>= 1;
+      PatchPcgGeom gp{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar, (int)half.size(),
+                      P.upload(half, s), P.upload(adj_ptr, s), P.upload(adj, s),
+                      P.upload(diag_h, s), spp};
+      if (patch_pcg_smem_bytes<T>(gp) > 227 * 1024)
+        fail(GAMBLET_ERR_UNSUPPORTED, "patch blocks exceed shared memory; lower rho");
+      // flops are added after setup from the measured iteration counts
+      int tok = h->prof.begin("patch_pcg_k" + std::to_string(k), pbytes, 0.0, s);
+      launch_patch_pcg<T>((const T*)L.Ahat, L.pmask, gp, Rhat, h->patch_tol, 200,
+                          h->patch_stats + 4 * k, h->num_sms, s);
+      h->prof.end(tok, s);
+      h->patch_flops_iter_k[k] = 18.0 * (2.0 * half.size() - NB) + 60.0 * NB;
+    }
     CK(cudaGetLastError());
     L.Rhat = Rhat;
     // Galerkin product -> level k-1 cell stencil
@@ -595,8 +640,8 @@ void setup_local(gamblet_ctx* h) {
     if (sizeof(T) * 4 * ((size_t)NB + (size_t)gg.nwin) > 227 * 1024)
       fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin window exceeds shared memory");
     T* Acell = P.alloc<T>((int64_t)gg.nout * L.npar);
-    tok = h->prof.begin(
-        "galerkin",
+    int tok = h->prof.begin(
+        "galerkin_k" + std::to_string(k),
         sz * ((double)L.noff * L.npar * 16 + 4.0 * NB * L.npar + (double)gg.nout * L.npar),
         2.0 * (16.0 * S.l1_pairs.size() + 4.0 * S.l2_pairs.size()) * h->lv[k - 1].n_active, s);
     launch_galerkin<T>((const T*)L.Ahat, Rhat, L.pmask, gg, Acell, s);
@@ -1114,6 +1159,8 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
     info->rel_residual = relres;
     info->setup_ms = h->setup_ms;
     info->solve_ms = ms;
+    info->patch_iters_max = h->patch_iters_max;
+    info->patch_iters_mean = h->patch_iters_mean;
   }
   return st;
 }
@@ -1138,6 +1185,7 @@ void gamblet_default_opts(gamblet_opts* o) {
   o->level_max_iter = 1000;
   o->refine_tol = 1e-13;
   o->refine_max_iter = 50;
+  o->patch_tol = 0.0;
   o->use_graph = 1;
   o->profile = 0;
   o->stream = nullptr;
@@ -1168,6 +1216,7 @@ gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cel
     h->n = A->n;
     h->exact = !(h->opts.rho > 0);
     h->mixed = h->opts.precision == GAMBLET_MIXED && !h->exact;
+    h->patch_tol = h->opts.patch_tol != 0 ? h->opts.patch_tol : (h->mixed ? 1e-6 : 1e-12);
     if (h->opts.precision != GAMBLET_FP64 && h->opts.precision != GAMBLET_MIXED)
       fail(GAMBLET_ERR_INVALID_ARG, "unknown precision");
     if (h->opts.nbr_rule != 0 && h->opts.nbr_rule != 1)
@@ -1218,6 +1267,23 @@ gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cel
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->setup_ms = ms;
+    if (h->patch_stats && h->patch_tol >= 0) {
+      std::vector<int> ps(4 * (q + 1));
+      CK(cudaMemcpy(ps.data(), h->patch_stats, sizeof(int) * ps.size(), cudaMemcpyDeviceToHost));
+      long long it_sum = 0, n_sum = 0;
+      h->patch_iters_max = 0;
+      for (int k = 2; k <= q; ++k) {
+        h->patch_iters_max = std::max(h->patch_iters_max, ps[4 * k]);
+        it_sum += ps[4 * k + 1];
+        n_sum += ps[4 * k + 2];
+        // algorithmic flops of the patch CG at level k: per iteration the
+        // block product (18 flops per used 3x3 block) plus block-Jacobi and
+        // vector work, times the iterations actually run
+        h->prof.add("patch_pcg_k" + std::to_string(k), 0.0,
+                    (double)ps[4 * k + 1] * h->patch_flops_iter_k[k]);
+      }
+      h->patch_iters_mean = n_sum > 0 ? (double)it_sum / n_sum : 0.0;
+    }
     h->prof.resolve();
     check_status(h, "setup");
     *out = h;
@@ -1293,6 +1359,38 @@ gamblet_status gamblet_grad(gamblet_handle h, int32_t ncell, const int32_t* cell
     return st;
   } catch (const GbError& e) {
     if (info) info->status = e.st;
+    return set_error(e);
+  }
+}
+
+gamblet_status gamblet_assemble_cells(int32_t n, const int32_t* rowptr, const int32_t* colind,
+                                      int64_t nnz, int32_t ncell, const int32_t* cell_nodes,
+                                      const double* log_a, const double* K_ref, double* val,
+                                      double* cell_a, void* stream) {
+  try {
+    if (n < 1 || nnz < 1 || ncell < 1 || !rowptr || !colind || !cell_nodes || !log_a || !K_ref ||
+        !val)
+      fail(GAMBLET_ERR_INVALID_ARG, "bad sizes or NULL pointer");
+    if (!is_device_ptr(rowptr) || !is_device_ptr(colind) || !is_device_ptr(cell_nodes) ||
+        !is_device_ptr(log_a) || !is_device_ptr(val))
+      fail(GAMBLET_ERR_INVALID_ARG, "pattern, cells, log_a and val must be device pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    double kh[16];
+    CK(cudaMemcpy(kh, K_ref, sizeof(kh), cudaMemcpyDefault));
+    launch_set_kref(kh);
+    Pool tmp;
+    tmp.s = s;
+    int* missing = tmp.zeros<int>(1, s);
+    CK(cudaMemsetAsync(val, 0, sizeof(double) * (size_t)nnz, s));
+    if (cell_a && !is_device_ptr(cell_a)) fail(GAMBLET_ERR_INVALID_ARG, "cell_a must be device memory");
+    launch_assemble_cells(n, rowptr, colind, ncell, cell_nodes, log_a, val, cell_a, missing, s);
+    CK(cudaGetLastError());
+    int mh = 0;
+    CK(cudaMemcpyAsync(&mh, missing, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (mh) fail(GAMBLET_ERR_INVALID_ARG, "a cell's corner pair is missing from the CSR pattern");
+    return GAMBLET_OK;
+  } catch (const GbError& e) {
     return set_error(e);
   }
 }

@@ -68,6 +68,28 @@ void launch_patch_solve(const T* Ahat, const uint32_t* pmask_k, PatchGeom g, T* 
                         int* status, int num_sms, cudaStream_t s);
 template <typename T>
 size_t patch_smem_bytes(int NB);
+// Same rows by block-Jacobi preconditioned CG to relative residual tol
+// (at most max_iter iterations), on the patch's nonzero 3x3 blocks;
+// iter_stats (device, 3 ints) accumulates the maximum and the sum of
+// iterations and the number of patches.
+struct PatchPcgGeom {
+  int NB, jc;
+  const int2* nbr;
+  const int* pair_idx;  // NB x NB
+  int Lpar;
+  int64_t npatch;
+  int nhalf;            // stored blocks (ja >= jb, offset in O_k)
+  const int4* half;     // (ja, jb, o, 0)
+  const int* adj_ptr;   // NB + 1
+  const int4* adj;      // (stored block, other neighbour, transposed, 0)
+  const int* diag_h;    // NB: stored block of (j, j)
+  int spp;              // threads per neighbour parent: 1, 2 or 4
+};
+template <typename T>
+void launch_patch_pcg(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g, T* Rhat, double tol,
+                      int max_iter, int* iter_stats, int num_sms, cudaStream_t s);
+template <typename T>
+size_t patch_pcg_smem_bytes(const PatchPcgGeom& g);
 
 // ---------------------------------------------------------------- Galerkin
 struct GalerkinGeom {
@@ -175,6 +197,11 @@ void launch_adjoint_contract(int ncell, const int32_t* cell_nodes, const double*
                              const double* lam, const double* u, double* dJ,
                              cudaStream_t s);
 void launch_set_kref(const double* K_ref_host);
+// CSR values of sum_c exp(log_a_c) K_ref (val must be zeroed; columns sorted
+// within each row); *missing is set if a corner pair is not in the pattern.
+void launch_assemble_cells(int n, const int32_t* rowptr, const int32_t* colind, int ncell,
+                           const int32_t* cell_nodes, const double* log_a, double* val,
+                           double* cell_a, int* missing, cudaStream_t s);
 
 // ---------------------------------------------------------------- dense (exact path)
 void launch_dense_from_blocks(const double* blk, const int2* off, int noff, int Lpar,

@@ -323,6 +323,284 @@ __global__ void __launch_bounds__(kPatchThreads, PatchOcc<T>::kMinBlocks)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Block-Jacobi preconditioned CG on the patch system (the iterative solve
+// Sec. 5.4 proposes for Alg. 2 line 11, to the accuracy Thm tmdiscreteaccuracy
+// allows).  The preconditioner inverts each neighbour parent's 3x3 diagonal
+// detail block; for rough coefficients this leaves a condition number of a
+// few units, so a handful of iterations reach the tolerance.
+//
+// The patch matrix is stored as its nonzero 3x3 blocks: one block per
+// neighbour pair (ja >= jb) whose offset N_jb - N_ja lies in O_k (host list
+// `half`), so the finest level, where A^(q) is a 9-point operator, keeps ~8x
+// fewer entries than the dense patch.  Thread j owns neighbour parent j: its
+// three unknowns, their residuals and its 3x3 block-Jacobi inverse live in
+// registers, so the preconditioner needs no communication; the block row of
+// j is walked through a compact adjacency list (stored block, other
+// neighbour, transposed flag) staged once per CTA in shared memory, split
+// over `spp` adjacent lanes when block rows are long (dense coarse levels).
+// Reductions run in the working precision (float32 in the mixed path, where
+// the patch factorisations accumulate in float32).
+template <typename T>
+size_t patch_pcg_smem_bytes(const PatchPcgGeom& pg) {
+  const int nadj = 2 * pg.nhalf - pg.NB;
+  size_t b = sizeof(T) * 9 * (size_t)pg.nhalf;           // stored blocks
+  b += sizeof(T) * 3 * (size_t)pg.NB;                     // shared direction vector
+  b += sizeof(int) * ((size_t)nadj + pg.NB + 1);          // adjacency (packed) + row pointers
+  b += sizeof(int) * 2 * (size_t)pg.NB;                   // parent index, active unknowns
+  b += sizeof(double) * 2 * 32 + 16;                      // reductions
+  return (b + 15) & ~(size_t)15;
+}
+template size_t patch_pcg_smem_bytes<float>(const PatchPcgGeom&);
+template size_t patch_pcg_smem_bytes<double>(const PatchPcgGeom&);
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// sum over the block of a and b (every thread gets both)
+template <typename T>
+__device__ __forceinline__ void block_sum2(T& a, T& b, T* red) {
+  a = warp_sum_t(a);
+  b = warp_sum_t(b);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    red[2 * warp] = a;
+    red[2 * warp + 1] = b;
+  }
+  __syncthreads();
+  a = 0;
+  b = 0;
+  for (int w = 0; w < nw; ++w) {
+    a += red[2 * w];
+    b += red[2 * w + 1];
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void load_detail_block(const T* __restrict__ blk16, T* out9, int na,
+                                                  int nb) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) out9[3 * a + b] = (a < na && b < nb) ? blk16[4 * a + b] : T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_patch_pcg(const T* __restrict__ Ahat,
+                                                   const uint32_t* __restrict__ pmask,
+                                                   PatchPcgGeom g, T* __restrict__ Rhat,
+                                                   double tol2, int max_iter, int* iter_stats) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int NB = g.NB;
+  const int nadj = 2 * g.nhalf - NB;
+  T* blk = reinterpret_cast<T*>(smem_raw);
+  T* sv = blk + 9 * g.nhalf;
+  int* sadj = reinterpret_cast<int*>(sv + 3 * NB);
+  int* sptr = sadj + nadj;
+  int* pj = sptr + NB + 1;
+  int* mj = pj + NB;
+  T* red = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(mj + NB) + 15) & ~(uintptr_t)15);
+  const int tid = threadIdx.x;
+  const int64_t np = g.npatch;
+  const int S = g.spp;  // threads per neighbour parent (lanes of one warp)
+  // patch structure, identical for every patch of the level
+  for (int e = tid; e < nadj; e += blockDim.x) {
+    const int4 ad = g.adj[e];  // (stored block, other neighbour, transposed, -)
+    sadj[e] = (ad.x << 9) | (ad.y << 1) | ad.z;
+  }
+  for (int j = tid; j <= NB; j += blockDim.x) sptr[j] = g.adj_ptr[j];
+  __syncthreads();
+  const int j = tid / S, sub = tid - (tid / S) * S;
+  const bool own = j < NB;
+  const bool lead = own && sub == 0;  // writes and reductions
+  const int e0 = own ? sptr[j] : 0, e1 = own ? sptr[j + 1] : 0;
+  int it_max = 0, it_sum = 0, done = 0;
+
+  for (int64_t i = blockIdx.x; i < np; i += gridDim.x) {
+    const uint32_t mi = pmask[i] & 15u;
+    if (mi == 0) {
+      for (int idx = tid; idx < NB * 4; idx += blockDim.x) Rhat[i * 4 * NB + idx] = T(0);
+      continue;
+    }
+    const T inv_sqrt_mi = T(1) / dev_sqrt<T>(T(__popc(mi)));
+    int xi, yi;
+    demorton((uint32_t)i, xi, yi);
+    int na = 0, pjj = -1;
+    if (own) {
+      pjj = shift_cell(xi, yi, g.nbr[j].x, g.nbr[j].y, g.Lpar);
+      const int m = pjj >= 0 ? __popc(pmask[pjj] & 15u) : 0;
+      na = m > 1 ? m - 1 : 0;  // active detail unknowns of neighbour j
+      if (lead) {
+        pj[j] = pjj;
+        mj[j] = na;
+      }
+    }
+    __syncthreads();
+    // ---- gather the stored blocks (identity on inactive diagonal entries)
+    for (int h = tid; h < g.nhalf; h += blockDim.x) {
+      const int4 e = g.half[h];  // (ja, jb, o, -)
+      const int nra = mj[e.x], nrb = mj[e.y];
+      T out9[9];
+      if (nra > 0 && nrb > 0) {
+        load_detail_block<T>(Ahat + ((int64_t)e.z * np + pj[e.x]) * 16, out9, nra, nrb);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) out9[q] = T(0);
+      }
+      if (e.x == e.y)
+        for (int a = nra; a < 3; ++a) out9[4 * a] = T(1);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) blk[9 * h + q] = out9[q];
+    }
+    // ---- right-hand side of neighbour j
+    T rv[3] = {T(0), T(0), T(0)};
+    if (own && na > 0) {
+      const int o = g.pair_idx[j * NB + g.jc];
+      if (o >= 0) {
+        const T* bl = Ahat + ((int64_t)o * np + pjj) * 16;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) rv[t] = t < na ? -inv_sqrt_mi * bl[4 * t + 3] : T(0);
+      }
+    }
+    __syncthreads();
+    // ---- block-Jacobi inverse of j's diagonal block (Gauss-Jordan, registers)
+    T Di[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Di[q] = (q % 4 == 0) ? T(1) : T(0);
+    if (own) {
+      T Mm[9];
+      const T* D = blk + 9 * g.diag_h[j];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Mm[q] = D[q];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T d = Mm[4 * c] > T(0) ? Mm[4 * c] : T(1);
+        const T id = T(1) / d;
+#pragma unroll
+        for (int b2 = 0; b2 < 3; ++b2) {
+          Mm[3 * c + b2] *= id;
+          Di[3 * c + b2] *= id;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (a == c) continue;
+          const T f = Mm[3 * a + c];
+#pragma unroll
+          for (int b2 = 0; b2 < 3; ++b2) {
+            Mm[3 * a + b2] -= f * Mm[3 * c + b2];
+            Di[3 * a + b2] -= f * Di[3 * c + b2];
+          }
+        }
+      }
+    }
+    // ---- PCG
+    T xv[3] = {T(0), T(0), T(0)}, zv[3], pv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) zv[a] = Di[3 * a] * rv[0] + Di[3 * a + 1] * rv[1] + Di[3 * a + 2] * rv[2];
+    T rz = lead ? rv[0] * zv[0] + rv[1] * zv[1] + rv[2] * zv[2] : T(0);
+    T rr0 = lead ? rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2] : T(0);
+    block_sum2<T>(rz, rr0, red);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) pv[a] = zv[a];
+    int it = 0;
+    if (rr0 > T(0)) {
+      for (it = 1; it <= max_iter; ++it) {
+        if (lead) {
+          sv[3 * j] = pv[0];
+          sv[3 * j + 1] = pv[1];
+          sv[3 * j + 2] = pv[2];
+        }
+        __syncthreads();
+        T q0 = 0, q1 = 0, q2 = 0;
+        for (int e = e0 + sub; e < e1; e += S) {
+          const int ad = sadj[e];
+          const T* B = blk + 9 * (ad >> 9);
+          const T* ps = sv + 3 * ((ad >> 1) & 255);
+          const T p0 = ps[0], p1 = ps[1], p2 = ps[2];
+          if (ad & 1) {
+            q0 += B[0] * p0 + B[3] * p1 + B[6] * p2;
+            q1 += B[1] * p0 + B[4] * p1 + B[7] * p2;
+            q2 += B[2] * p0 + B[5] * p1 + B[8] * p2;
+          } else {
+            q0 += B[0] * p0 + B[1] * p1 + B[2] * p2;
+            q1 += B[3] * p0 + B[4] * p1 + B[5] * p2;
+            q2 += B[6] * p0 + B[7] * p1 + B[8] * p2;
+          }
+        }
+        for (int o = 1; o < S; o <<= 1) {  // combine the S partial products
+          q0 += __shfl_xor_sync(0xffffffffu, q0, o);
+          q1 += __shfl_xor_sync(0xffffffffu, q1, o);
+          q2 += __shfl_xor_sync(0xffffffffu, q2, o);
+        }
+        T pq = lead ? pv[0] * q0 + pv[1] * q1 + pv[2] * q2 : T(0), unused = 0;
+        block_sum2<T>(pq, unused, red);
+        const T alpha = pq > T(0) ? rz / pq : T(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) xv[a] += alpha * pv[a];
+        rv[0] -= alpha * q0;
+        rv[1] -= alpha * q1;
+        rv[2] -= alpha * q2;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          zv[a] = Di[3 * a] * rv[0] + Di[3 * a + 1] * rv[1] + Di[3 * a + 2] * rv[2];
+        T rz_new = lead ? rv[0] * zv[0] + rv[1] * zv[1] + rv[2] * zv[2] : T(0);
+        T rr = lead ? rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2] : T(0);
+        block_sum2<T>(rz_new, rr, red);
+        if ((double)rr <= tol2 * (double)rr0 || !(rz_new > T(0))) break;
+        const T beta = rz_new / rz;
+        rz = rz_new;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) pv[a] = zv[a] + beta * pv[a];
+      }
+      if (it > max_iter) it = max_iter;
+    }
+    it_max = max(it_max, it);
+    it_sum += it;
+    ++done;
+    // ---- interpolation row: detail coefficients of neighbour j and the average slot
+    if (lead) {
+      T* row = Rhat + i * 4 * NB + 4 * j;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) row[t] = t < na ? xv[t] : T(0);
+      row[3] = (j == g.jc) ? inv_sqrt_mi : T(0);
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && iter_stats) {
+    atomicMax(&iter_stats[0], it_max);
+    atomicAdd(&iter_stats[1], it_sum);
+    atomicAdd(&iter_stats[2], done);
+  }
+}
+
+template <typename T>
+void launch_patch_pcg(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g, T* Rhat, double tol,
+                      int max_iter, int* iter_stats, int num_sms, cudaStream_t s) {
+  if (g.npatch <= 0) return;
+  const size_t smem = patch_pcg_smem_bytes<T>(g);
+  cudaFuncSetAttribute(k_patch_pcg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int threads = ((g.NB * g.spp + 31) / 32) * 32;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_patch_pcg<T>, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)num_sms * per_sm;
+  if (grid > g.npatch) grid = g.npatch;
+  {
+    count_launch();
+    k_patch_pcg<T><<<(unsigned)grid, threads, smem, s>>>(Ahat, pmask_k, g, Rhat, tol * tol, max_iter,
+                                                          iter_stats);
+  }
+}
+template void launch_patch_pcg<float>(const float*, const uint32_t*, PatchPcgGeom, float*, double,
+                                      int, int*, int, cudaStream_t);
+template void launch_patch_pcg<double>(const double*, const uint32_t*, PatchPcgGeom, double*,
+                                       double, int, int*, int, cudaStream_t);
+
 template <typename T>
 void launch_patch_solve(const T* Ahat, const uint32_t* pmask_k, PatchGeom g, T* Rhat,
                         int* status, int num_sms, cudaStream_t s) {

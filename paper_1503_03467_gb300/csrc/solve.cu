@@ -311,6 +311,56 @@ __global__ void k_adjoint_contract(int ncell, const int32_t* __restrict__ cn,
   dJ[c] = -a[c] * s;
 }
 
+// A values from the cell coefficients: each cell adds exp(log_a) K_ref on
+// its interior corner pairs; the CSR position is found by binary search.
+__global__ void k_assemble_cells(int n, const int32_t* __restrict__ rowptr,
+                                 const int32_t* __restrict__ colind, int ncell,
+                                 const int32_t* __restrict__ cn, const double* __restrict__ log_a,
+                                 double* val, double* cell_a, int* missing) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const double a = exp(log_a[c]);
+  if (cell_a) cell_a[c] = a;
+  int nd[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) nd[p] = cn[4 * c + p];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    if (nd[p] < 0 || nd[p] >= n) continue;
+    const int b = rowptr[nd[p]], e = rowptr[nd[p] + 1];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (nd[r] < 0 || nd[r] >= n) continue;
+      int lo = b, hi = e - 1, pos = -1;
+      while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int cm = colind[mid];
+        if (cm == nd[r]) {
+          pos = mid;
+          break;
+        }
+        if (cm < nd[r]) lo = mid + 1;
+        else hi = mid - 1;
+      }
+      if (pos < 0) {
+        atomicExch(missing, 1);
+        continue;
+      }
+      atomicAdd(&val[pos], a * c_Kref[p * 4 + r]);
+    }
+  }
+}
+
+void launch_assemble_cells(int n, const int32_t* rowptr, const int32_t* colind, int ncell,
+                           const int32_t* cell_nodes, const double* log_a, double* val,
+                           double* cell_a, int* missing, cudaStream_t s) {
+  if (ncell > 0) {
+    count_launch();
+    k_assemble_cells<<<(ncell + 255) / 256, 256, 0, s>>>(n, rowptr, colind, ncell, cell_nodes,
+                                                         log_a, val, cell_a, missing);
+  }
+}
+
 void launch_adjoint_contract(int ncell, const int32_t* cell_nodes, const double* cell_a,
                              const double* lam, const double* u, double* dJ, cudaStream_t s) {
   if (ncell > 0)

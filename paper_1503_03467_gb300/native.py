@@ -44,7 +44,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_double), ("nbr_rule", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("level_tol", ctypes.c_double),
                 ("level_max_iter", ctypes.c_int32), ("refine_tol", ctypes.c_double),
-                ("refine_max_iter", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("refine_max_iter", ctypes.c_int32), ("patch_tol", ctypes.c_double),
+                ("use_graph", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
@@ -52,13 +53,15 @@ class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("q", ctypes.c_int32),
                 ("outer_iters", ctypes.c_int32), ("level_iters", ctypes.c_int32 * 32),
                 ("rel_residual", ctypes.c_double), ("setup_ms", ctypes.c_double),
-                ("solve_ms", ctypes.c_double)]
+                ("solve_ms", ctypes.c_double), ("patch_iters_max", ctypes.c_int32),
+                ("patch_iters_mean", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {"status": self.status, "q": self.q, "outer_iters": self.outer_iters,
                 "level_iters": list(self.level_iters)[: self.q + 1],
                 "rel_residual": self.rel_residual, "setup_ms": self.setup_ms,
-                "solve_ms": self.solve_ms}
+                "solve_ms": self.solve_ms, "patch_iters_max": self.patch_iters_max,
+                "patch_iters_mean": self.patch_iters_mean}
 
 
 class KernelStat(ctypes.Structure):
@@ -77,6 +80,10 @@ SIGNATURES = {
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Info)]),
+    "gamblet_assemble_cells": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p]),
     "gamblet_level_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32)]),
@@ -185,6 +192,17 @@ def gamblet_objective_noalloc(n: int, u, u_obs, J, stream=None) -> int:
     return _check(_lib.gamblet_objective_noalloc(int(n), _ptr(u, np.float64),
                                                  _ptr(u_obs, np.float64), _ptr(J, np.float64),
                                                  stream))
+
+
+def gamblet_assemble_cells(rowptr, colind, cell_nodes, log_a, K_ref, val, cell_a=None,
+                           stream=None) -> int:
+    """CSR values of sum_c exp(log_a_c) K_ref into `val` (CUDA tensors);
+    optionally exp(log_a) into `cell_a`."""
+    n = int(rowptr.shape[0]) - 1
+    return _check(_lib.gamblet_assemble_cells(
+        n, _ptr(rowptr, np.int32), _ptr(colind, np.int32), int(colind.shape[0]),
+        int(log_a.shape[0]), _ptr(cell_nodes, np.int32), _ptr(log_a, np.float64),
+        _ptr(K_ref, np.float64), _ptr(val, np.float64), _ptr(cell_a, np.float64), stream))
 
 
 def gamblet_level_size(h: int, k: int) -> tuple[int, int]:

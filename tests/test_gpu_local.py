@@ -12,7 +12,7 @@ from gpu_util import coo_to_dense, csr_arrays, drop_nodes, rel
 pytestmark = pytest.mark.gpu
 
 
-def _setup(A, cells, q, rho, rule=0, precision=0, refine=0, level_tol=1e-14):
+def _setup(A, cells, q, rho, rule=0, precision=0, refine=0, level_tol=1e-14, patch_tol=0.0):
     from paper_1503_03467_gb300 import native as nv
     rp, ci, va = csr_arrays(A)
     o = nv.gamblet_default_opts()
@@ -22,6 +22,7 @@ def _setup(A, cells, q, rho, rule=0, precision=0, refine=0, level_tol=1e-14):
     o.refine_max_iter = refine
     o.level_tol = level_tol
     o.level_max_iter = 5000
+    o.patch_tol = patch_tol
     return nv.gamblet_setup(rp, ci, va, q, cells, o)
 
 
@@ -37,17 +38,19 @@ def _ops(h, q):
     return out
 
 
-CASES = [(32, 1e4, 0, 3.0, 0), (64, 1e4, 1, 3.0, 0), (32, 1e2, 2, 2.0, 0),
-         (32, 1e3, 3, 3.0, 1), (64, 1e6, 5, 1.0, 0)]
+# (n, contrast, seed, rho, rule, patch solver: 0 = block-Jacobi CG, -1 = Cholesky)
+CASES = [(32, 1e4, 0, 3.0, 0, 0.0), (64, 1e4, 1, 3.0, 0, 0.0), (32, 1e2, 2, 2.0, 0, 0.0),
+         (32, 1e3, 3, 3.0, 1, 0.0), (64, 1e6, 5, 1.0, 0, 0.0), (32, 1e4, 0, 3.0, 0, -1.0),
+         (64, 1e4, 1, 2.0, 1, -1.0)]
 
 
-@pytest.mark.parametrize("n,C,seed,rho,rule", CASES)
-def test_local_operators_and_one_pass(n, C, seed, rho, rule):
+@pytest.mark.parametrize("n,C,seed,rho,rule,patch_tol", CASES)
+def test_local_operators_and_one_pass(n, C, seed, rho, rule, patch_tol):
     from paper_1503_03467_gb300 import native as nv
     p = make_problem(n, C, seed)
     ref = gamblet_local_setup(p.A, p.cells, p.q, rho, "euclid" if rule == 0 else "cheb")
     one = gamblet_local_solve(ref, p.g)
-    h = _setup(p.A, p.cells, p.q, rho, rule)
+    h = _setup(p.A, p.cells, p.q, rho, rule, patch_tol=patch_tol)
     try:
         ops = _ops(h, p.q)
         for k in range(2, p.q + 1):
