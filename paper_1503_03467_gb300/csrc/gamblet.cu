@@ -183,6 +183,7 @@ struct LevelDev {
   void* Ahat = nullptr;      // T
   double* Ahat64 = nullptr;  // level q float64 copy (mixed) or alias
   void* Rhat = nullptr;      // T, rows 4^(k-1)
+  void* RT = nullptr;        // T, Rhat regrouped by parent (prolongation)
   int* pair_idx = nullptr;
   // exact (dense)
   double* D = nullptr;       // transformed dense Ahat^(k)
@@ -623,6 +624,9 @@ void setup_local(gamblet_ctx* h) {
     }
     CK(cudaGetLastError());
     L.Rhat = Rhat;
+    T* RT = P.alloc<T>((int64_t)NB * 4 * L.npar);
+    launch_transpose_rhat<T>(Rhat, NB, h->nbr, Lpar, L.npar, RT, s);
+    L.RT = RT;
     // Galerkin product -> level k-1 cell stencil
     GalerkinGeom gg;
     gg.NB = NB;
@@ -637,14 +641,40 @@ void setup_local(gamblet_ctx* h) {
     gg.l2_pairs = P.upload(S.l2_pairs, s);
     gg.Lpar = Lpar;
     gg.nrow = L.npar;
-    if (sizeof(T) * 4 * ((size_t)NB + (size_t)gg.nwin) > 227 * 1024)
+    // tiled Galerkin: dense offset lookup tables over the boxes of N, WIN, S+
+    auto box_table = [](const std::vector<int2>& v, int& R) {
+      R = 0;
+      for (const int2& d : v) R = std::max(R, std::max(std::abs(d.x), std::abs(d.y)));
+      const int D = 2 * R + 1;
+      std::vector<int> tab((size_t)D * D, -1);
+      for (int e = 0; e < (int)v.size(); ++e) tab[(size_t)(v[e].y + R) * D + v[e].x + R] = e;
+      return tab;
+    };
+    GalerkinTileGeom tg;
+    tg.NB = NB;
+    tg.nbr = h->nbr;
+    tg.noff = L.noff;
+    tg.off = L.off;
+    std::vector<int> nmap = box_table(h->N.v, tg.RN);
+    std::vector<int> wmap = box_table(S.WIN.v, tg.RW);
+    std::vector<int> smap = box_table(S.Sp.v, tg.RS);
+    tg.nmap = P.upload(nmap, s);
+    tg.wmap = P.upload(wmap, s);
+    tg.smap = P.upload(smap, s);
+    tg.nwin = S.WIN.size();
+    tg.nout = S.Sp.size();
+    tg.Lpar = Lpar;
+    tg.nrow = L.npar;
+    int tr = 4;
+    while (tr > 1 && (tr > Lpar || galerkin_tiled_smem(tg, tr, sizeof(T)) > 110 * 1024)) tr >>= 1;
+    if (galerkin_tiled_smem(tg, tr, sizeof(T)) > 227 * 1024)
       fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin window exceeds shared memory");
     T* Acell = P.alloc<T>((int64_t)gg.nout * L.npar);
     int tok = h->prof.begin(
         "galerkin_k" + std::to_string(k),
         sz * ((double)L.noff * L.npar * 16 + 4.0 * NB * L.npar + (double)gg.nout * L.npar),
         2.0 * (16.0 * S.l1_pairs.size() + 4.0 * S.l2_pairs.size()) * h->lv[k - 1].n_active, s);
-    launch_galerkin<T>((const T*)L.Ahat, Rhat, L.pmask, gg, Acell, s);
+    launch_galerkin_tiled<T>((const T*)L.Ahat, Rhat, L.pmask, tg, tr, Acell, s);
     h->prof.end(tok, s);
     CK(cudaGetLastError());
     if (k - 1 >= 2) {
@@ -964,7 +994,7 @@ void apply_G(gamblet_ctx* h, const T* in, T* out, int inverse_last) {
       const double sz = (double)sizeof(T);
       int tok = h->prof.begin("prolong", sz * (3.0 * NB * L.npar + 2.0 * L.ncell + L.npar),
                               6.0 * NB * L.npar, s);
-      launch_prolong<T>((const T*)L.Rhat, NB, h->nbr, 1 << (k - 1), L.npar, vprev, (const T*)L.w,
+      launch_prolong<T>((const T*)L.RT, NB, h->nbr, 1 << (k - 1), L.npar, vprev, (const T*)L.w,
                         L.pmask, inv, dst, s);
       h->prof.end(tok, s);
     }
@@ -990,7 +1020,7 @@ void components(gamblet_ctx* h, T* out_q /* ncell_q */, int lev, T* scratch_a, T
       CK(cudaMemcpyAsync(cur, L.w, sizeof(double) * L.ncell, cudaMemcpyDeviceToDevice, s));
       launch_transform_vec<T>(cur, cur, L.npar, L.pmask, -1, s);
     } else {
-      launch_prolong<T>((const T*)L.Rhat, NB, h->nbr, 1 << (lev - 1), L.npar, nxt, (const T*)L.w,
+      launch_prolong<T>((const T*)L.RT, NB, h->nbr, 1 << (lev - 1), L.npar, nxt, (const T*)L.w,
                         L.pmask, 1, cur, s);
     }
   }
@@ -1001,7 +1031,7 @@ void components(gamblet_ctx* h, T* out_q /* ncell_q */, int lev, T* scratch_a, T
                      (double*)nxt, s);
       launch_transform_vec<T>(nxt, nxt, L.npar, L.pmask, -1, s);
     } else {
-      launch_prolong<T>((const T*)L.Rhat, NB, h->nbr, 1 << (k - 1), L.npar, cur, nullptr, L.pmask,
+      launch_prolong<T>((const T*)L.RT, NB, h->nbr, 1 << (k - 1), L.npar, cur, nullptr, L.pmask,
                         1, nxt, s);
     }
     std::swap(cur, nxt);

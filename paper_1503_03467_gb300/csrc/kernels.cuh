@@ -110,6 +110,27 @@ struct GalerkinGeom {
 template <typename T>
 void launch_galerkin(const T* Ahat, const T* Rhat, const uint32_t* pmask_k, GalerkinGeom g,
                      T* Aout, cudaStream_t s);
+// Tiled variant (one CTA per tr x tr tile of coarse rows; tr in {1, 2, 4},
+// tr <= Lpar); offsets located through dense lookup tables over the boxes
+// [-R, R]^2 of N (nmap), the window (wmap) and the half-plane output (smap).
+struct GalerkinTileGeom {
+  int NB;
+  const int2* nbr;
+  int noff;
+  const int2* off;   // O_k
+  int RN;
+  const int* nmap;   // N index or -1
+  int nwin, RW;
+  const int* wmap;   // WIN index or -1
+  int nout, RS;
+  const int* smap;   // S+ index or -1
+  int Lpar;
+  int64_t nrow;
+};
+template <typename T>
+void launch_galerkin_tiled(const T* Ahat, const T* Rhat, const uint32_t* pmask_k,
+                           GalerkinTileGeom g, int tr, T* Aout, cudaStream_t s);
+size_t galerkin_tiled_smem(const GalerkinTileGeom& g, int tr, size_t elem);
 // Level-(k-1) cell stencil (S offsets, [d][i]) -> transformed block stencil
 // at level k-1 (offsets O, [o][P][16]) using masks of level k-1 parents.
 // map: nO x 16 index into S of 2*Delta + c' - c for (a = c, b = c'), or -1.
@@ -132,9 +153,14 @@ void launch_level1_solve(const double* L1, const T* g, T* U, cudaStream_t s);
 template <typename T>
 void launch_restrict(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t nrow,
                      const T* ghat_k, T* g_km1, const uint32_t* pmask_km1, cudaStream_t s);
-// vhat^(k) = Rhat^T v^(k-1) + [w^(k); 0]; if inverse, v^(k) = Q^T vhat^(k).
+// RT[p][j] = Rhat[p - N_j][j] (interpolation rows regrouped by parent).
 template <typename T>
-void launch_prolong(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t npar,
+void launch_transpose_rhat(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t npar, T* RT,
+                           cudaStream_t s);
+// vhat^(k) = Rhat^T v^(k-1) + [w^(k); 0] from the regrouped rows RT; if
+// inverse, v^(k) = Q^T vhat^(k).
+template <typename T>
+void launch_prolong(const T* RT, int NB, const int2* nbr, int Lpar, int64_t npar,
                     const T* v_km1, const T* w_k, const uint32_t* pmask_k, int inverse,
                     T* out, cudaStream_t s);
 

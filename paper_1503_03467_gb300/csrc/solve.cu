@@ -9,39 +9,46 @@
 namespace gb {
 
 // ---------------------------------------------------------------- restriction
+// One warp per coarse row i (lanes over the neighbours j, so the row of R-hat
+// is read with unit stride); the four warps of a CTA hold the four children
+// of one level-(k-2) parent, whose transform Q^(k-1) is applied through
+// shared memory before the write.
 template <typename T>
-__global__ void k_restrict(const T* __restrict__ Rhat, int NB, const int2* __restrict__ nbr,
-                           int Lpar, int64_t nrow, const T* __restrict__ ghat, T* out,
-                           const uint32_t* __restrict__ pmask_km1) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) k_restrict(const T* __restrict__ Rhat, int NB,
+                                                  const int2* __restrict__ nbr, int Lpar,
+                                                  int64_t nrow, const T* __restrict__ ghat, T* out,
+                                                  const uint32_t* __restrict__ pmask_km1) {
+  __shared__ T vals[4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * 4 + w;
   T acc = 0;
   if (i < nrow) {
     int x, y;
     demorton((uint32_t)i, x, y);
     const T* row = Rhat + i * 4 * NB;
-    for (int j = 0; j < NB; ++j) {
+    for (int j = lane; j < NB; j += 32) {
       const int p = shift_cell(x, y, nbr[j].x, nbr[j].y, Lpar);
       if (p < 0) continue;
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc += row[4 * j + c] * ghat[4 * p + c];
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (pmask_km1 == nullptr) {
-    if (i < nrow) out[i] = acc;
+    if (lane == 0 && i < nrow) out[i] = acc;
     return;
   }
-  // transform by Q^(k-1): lanes 4P..4P+3 hold the four children of parent P
-  const int lane = threadIdx.x & 31;
-  const int c = lane & 3;
-  const int base = lane & ~3;
-  T v0 = __shfl_sync(0xffffffffu, acc, base);
-  T v1 = __shfl_sync(0xffffffffu, acc, base + 1);
-  T v2 = __shfl_sync(0xffffffffu, acc, base + 2);
-  T v3 = __shfl_sync(0xffffffffu, acc, base + 3);
-  if (i < nrow) {
-    const int m = (int)pmask_km1[i >> 2] & 15;
-    out[i] = qv<T>(m, c, 0) * v0 + qv<T>(m, c, 1) * v1 + qv<T>(m, c, 2) * v2 +
-             qv<T>(m, c, 3) * v3;
+  if (lane == 0) vals[w] = acc;
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    const int64_t base = (int64_t)blockIdx.x * 4;
+    if (base + threadIdx.x < nrow) {
+      const int m = (int)pmask_km1[base >> 2] & 15;
+      const int a = threadIdx.x;
+      out[base + a] = qv<T>(m, a, 0) * vals[0] + qv<T>(m, a, 1) * vals[1] +
+                      qv<T>(m, a, 2) * vals[2] + qv<T>(m, a, 3) * vals[3];
+    }
   }
 }
 
@@ -49,8 +56,7 @@ template <typename T>
 void launch_restrict(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t nrow,
                      const T* ghat_k, T* g_km1, const uint32_t* pmask_km1, cudaStream_t s) {
   if (nrow <= 0) return;
-  { count_launch(); k_restrict<T><<<(unsigned)((nrow + 127) / 128), 128, 0, s>>>(Rhat, NB, nbr, Lpar, nrow, ghat_k,
-                                                               g_km1, pmask_km1); }
+  { count_launch(); k_restrict<T><<<(unsigned)((nrow + 3) / 4), 128, 0, s>>>(Rhat, NB, nbr, Lpar, nrow, ghat_k, g_km1, pmask_km1); }
 }
 template void launch_restrict<float>(const float*, int, const int2*, int, int64_t, const float*,
                                      float*, const uint32_t*, cudaStream_t);
@@ -58,32 +64,76 @@ template void launch_restrict<double>(const double*, int, const int2*, int, int6
                                       const double*, double*, const uint32_t*, cudaStream_t);
 
 // ---------------------------------------------------------------- prolongation
+// RT[p][j][a] = Rhat[p - N_j][j][a]: the interpolation rows regrouped by the
+// parent they reach, so the prolongation reads them with unit stride.
 template <typename T>
-__global__ void k_prolong(const T* __restrict__ Rhat, int NB, const int2* __restrict__ nbr,
-                          int Lpar, int64_t npar, const T* __restrict__ v, const T* __restrict__ w,
-                          const uint32_t* __restrict__ pmask, int inverse, T* out) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void k_transpose_rhat(const T* __restrict__ Rhat, int NB, const int2* __restrict__ nbr,
+                                 int Lpar, int64_t npar, T* RT) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= npar * NB) return;
+  const int64_t p = t / NB;
+  const int j = (int)(t - p * NB);
+  int x, y;
+  demorton((uint32_t)p, x, y);
+  const int i = shift_cell(x, y, -nbr[j].x, -nbr[j].y, Lpar);
+  T* dst = RT + t * 4;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dst[a] = i >= 0 ? Rhat[(int64_t)i * 4 * NB + 4 * j + a] : T(0);
+  dst[3] = T(0);
+}
+
+template <typename T>
+void launch_transpose_rhat(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t npar, T* RT,
+                           cudaStream_t s) {
+  const int64_t n = npar * NB;
+  if (n > 0) { count_launch(); k_transpose_rhat<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Rhat, NB, nbr, Lpar, npar, RT); }
+}
+template void launch_transpose_rhat<float>(const float*, int, const int2*, int, int64_t, float*,
+                                           cudaStream_t);
+template void launch_transpose_rhat<double>(const double*, int, const int2*, int, int64_t,
+                                            double*, cudaStream_t);
+
+// One warp per parent p: vhat = [w; v_p / sqrt(m)] + sum_j RT[p][j] v[p - N_j],
+// then (inverse) v = Q^T vhat.
+template <typename T>
+__global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ RT, int NB,
+                                                 const int2* __restrict__ nbr, int Lpar,
+                                                 int64_t npar, const T* __restrict__ v,
+                                                 const T* __restrict__ w,
+                                                 const uint32_t* __restrict__ pmask, int inverse,
+                                                 T* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (p >= npar) return;
   const int m = (int)pmask[p] & 15;
-  T h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+  T h0 = 0, h1 = 0, h2 = 0;
   if (m) {
     int x, y;
     demorton((uint32_t)p, x, y);
-    h3 = v[p] * (T(1) / sqrt(T(__popc(m))));
-    if (w) {
-      h0 = w[4 * p];
-      h1 = w[4 * p + 1];
-      h2 = w[4 * p + 2];
-    }
-    for (int j = 0; j < NB; ++j) {
+    const T* row = RT + p * 4 * NB;
+    for (int j = lane; j < NB; j += 32) {
       const int i = shift_cell(x, y, -nbr[j].x, -nbr[j].y, Lpar);
       if (i < 0) continue;
       const T vi = v[i];
-      if (vi == T(0)) continue;
-      const T* rr = Rhat + (int64_t)i * 4 * NB + 4 * j;
-      h0 += rr[0] * vi;
-      h1 += rr[1] * vi;
-      h2 += rr[2] * vi;
+      h0 += row[4 * j] * vi;
+      h1 += row[4 * j + 1] * vi;
+      h2 += row[4 * j + 2] * vi;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    h0 += __shfl_xor_sync(0xffffffffu, h0, o);
+    h1 += __shfl_xor_sync(0xffffffffu, h1, o);
+    h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+  }
+  if (lane != 0) return;
+  T h3 = 0;
+  if (m) {
+    h3 = v[p] * (T(1) / sqrt(T(__popc(m))));
+    if (w) {
+      h0 += w[4 * p];
+      h1 += w[4 * p + 1];
+      h2 += w[4 * p + 2];
     }
   }
   if (inverse) {
@@ -101,12 +151,11 @@ __global__ void k_prolong(const T* __restrict__ Rhat, int NB, const int2* __rest
 }
 
 template <typename T>
-void launch_prolong(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t npar,
+void launch_prolong(const T* RT, int NB, const int2* nbr, int Lpar, int64_t npar,
                     const T* v_km1, const T* w_k, const uint32_t* pmask_k, int inverse, T* out,
                     cudaStream_t s) {
   if (npar <= 0) return;
-  { count_launch(); k_prolong<T><<<(unsigned)((npar + 127) / 128), 128, 0, s>>>(Rhat, NB, nbr, Lpar, npar, v_km1, w_k,
-                                                              pmask_k, inverse, out); }
+  { count_launch(); k_prolong<T><<<(unsigned)((npar * 32 + 127) / 128), 128, 0, s>>>(RT, NB, nbr, Lpar, npar, v_km1, w_k, pmask_k, inverse, out); }
 }
 template void launch_prolong<float>(const float*, int, const int2*, int, int64_t, const float*,
                                     const float*, const uint32_t*, int, float*, cudaStream_t);
