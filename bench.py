@@ -45,10 +45,11 @@ def parse():
     ap.add_argument("--contrast", type=float, default=1e4)
     ap.add_argument("--rho", type=float, default=3.0)
     ap.add_argument("--level-tol", type=float, default=0.1)
-    ap.add_argument("--refine-tol", type=float, default=1e-12)
+    ap.add_argument("--refine-tol", type=float, default=1e-10)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain float64 arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient timing")
     return ap.parse_args()
 
 
@@ -246,6 +247,52 @@ def run_e2e(nv, a, host, precision, steps):
     return {"ms": statistics.mean(times), "h2d": h2d, "d2h": u.nbytes, "u": u}
 
 
+def adjoint_timing(nv, torch, dev, steps=3):
+    """Gradient of J = 1/2 |u - u_obs|^2 with respect to log a on the 256 x 256
+    problem (q = 8, contrast 1e3, u_obs from the field of seed 7): forward
+    (assembly + setup + solve) and backward (adjoint solve + contraction)
+    through the autograd wrapper, timed with CUDA events, checked against the
+    CPU oracle's direct-solve adjoint."""
+    from oracle import adjoint, direct
+    from paper_1503_03467_gb300.solver import Q1Mesh, gamblet_solve
+    from workloads import cell_corner_dofs, make_problem
+    from workloads.rough import K_REF
+    n = 256
+    p = make_problem(n, 1e3, 0)
+    obs = make_problem(n, 1e3, 7)
+    u_obs_np, _ = direct.solve(obs.A, p.g)
+    A = p.A.tocsr()
+    mesh = Q1Mesh(A.indptr, A.indices, p.cells, cell_corner_dofs(n), K_REF, p.q, dev)
+    o = nv.gamblet_default_opts()
+    o.precision = nv.MIXED
+    o.level_tol = 0.1
+    o.refine_tol = 1e-12
+    o.refine_max_iter = 100
+    g = torch.tensor(p.g, device=dev)
+    u_obs = torch.tensor(u_obs_np, device=dev)
+    fwd, bwd = [], []
+    for it in range(steps + 1):
+        log_a = torch.tensor(p.log_a.ravel(), dtype=torch.float64, device=dev, requires_grad=True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record()
+        u = gamblet_solve(log_a, g, mesh, o)
+        J = 0.5 * ((u - u_obs) ** 2).sum()
+        e1.record()
+        J.backward()
+        e2.record()
+        e2.synchronize()
+        if it > 0:
+            fwd.append(e0.elapsed_time(e1))
+            bwd.append(e1.elapsed_time(e2))
+    _, grad_ref, _ = adjoint.gradient(p.A, p.g, u_obs_np, n, np.exp(p.log_a), K_REF)
+    gr = log_a.grad.cpu().numpy()
+    err = float(np.linalg.norm(gr - grad_ref) / np.linalg.norm(grad_ref))
+    f, b = statistics.mean(fwd), statistics.mean(bwd)
+    return {"workload": "256x256 Q1, q=8, contrast 1e3, 65,536 cells", "forward_ms": f,
+            "grad_ms": b, "grad_over_forward": b / f, "rel_err_vs_oracle_adjoint": err}
+
+
 def cpu_oracle(p):
     """The oracle's direct solve (SuperLU + extended-precision refinement)."""
     from oracle import direct
@@ -270,16 +317,20 @@ def families(stats):
 
 
 def roofline(stats, peaks, clocks, mixed):
-    """Roofline entry of the kernel family with the largest share of device time."""
-    stats = families(stats)
+    """Roofline entry of the single kernel (kernel family and level) with the
+    largest share of device time; per-launch figures are its own averages."""
     name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
-    avg_ms = st["ms"] / max(st["launches"], 1)
-    per_launch_bytes = st["bytes"] / max(st["launches"], 1)
-    per_launch_flops = st["flops"] / max(st["launches"], 1)
+    family = name.rsplit("_k", 1)[0] if "_k" in name and name.rsplit("_k", 1)[1].isdigit() else name
+    launches = max(st["launches"], 1)
+    avg_ms = st["ms"] / launches
+    per_launch_bytes = st["bytes"] / launches
+    per_launch_flops = st["flops"] / launches
     total_ms = sum(s["ms"] for s in stats.values())
-    if name in ("patch_pcg", "patch_cholesky"):
-        # SIMT arithmetic bound: 152 SMs x 128 lanes (fp32) or the nominal
-        # float64 rate, at the maximum SM clock
+    common = {"kernel": name, "launches": st["launches"], "avg_launch_ms": avg_ms,
+              "share_of_device_time": st["ms"] / total_ms, "traffic": ncu_traffic(name)}
+    if family in ("patch_pcg", "patch_cholesky"):
+        # SIMT arithmetic: 152 SMs x 128 lanes (fp32) or the nominal float64
+        # rate, at the maximum SM clock
         if mixed:
             peak = 152 * 128 * 2 * 2.070e9 / 1e12
             src = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (nominal)"
@@ -287,16 +338,15 @@ def roofline(stats, peaks, clocks, mixed):
             peak = 1.25
             src = "nominal GB300 float64 rate"
         achieved = per_launch_flops / (avg_ms * 1e-3) / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src,
-                "traffic": ncu_traffic(name), "share_of_device_time": st["ms"] / total_ms}
+        return {**common, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "peak_source": src,
+                "algorithmic": f"{per_launch_flops:.4g} flop per launch"}
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    return {**common, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
-            else "fallback 6.8 TB/s", "traffic": ncu_traffic(name),
-            "share_of_device_time": st["ms"] / total_ms}
+            else "fallback 6.8 TB/s", "algorithmic": f"{per_launch_bytes:.4g} byte per launch"}
 
 
 def reference_main(a, ws, rank):
@@ -404,6 +454,8 @@ def main():
             "rel_err": rel_err(plain["u"], ud), "outer_iters": plain["infos"][-1]["outer_iters"],
             "roofline": roofline(plain["stats"], peaks, None, False)}
         line["speedup_mixed_vs_plain"] = line["plain_fp64"]["ms_per_step"] / ms
+    if not a.no_adjoint:
+        line["adjoint"] = adjoint_timing(nv, torch, dev)
     if rank == 0 and ws == 1 and not a.no_cpu:
         line["cpu_baseline"] = {"value": ndof / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "one full solve of the same problem: SuperLU factor + "

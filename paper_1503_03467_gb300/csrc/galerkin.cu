@@ -196,187 +196,3 @@ template void launch_cells_to_blocks<double>(const double*, int64_t, const int*,
 
 }  // namespace gb
 
-namespace gb {
-
-// ---------------------------------------------------------------------------
-// Tiled Galerkin product: one CTA per TR x TR tile of coarse rows i.  Every
-// block Ahat[o][p'] and every interpolation row Rhat_{i'} the tile touches is
-// read from L2 once and applied to all rows of the tile, with the products
-// accumulated in registers:
-//   phase 1  thread per window parent p':  t_i[p' - i] = sum_o Ahat[o][p'] Rhat_i[j],
-//            N_j = p' + O_o - i, for every tile row i;
-//   phase 2  thread per output neighbour i': A_{i, i'} = sum_j Rhat_{i'}[j] . t_i[i' + N_j - i]
-//            for every tile row i with i' - i in the half-plane S+.
-// Offsets are located through small dense lookup tables held in shared memory.
-template <typename T, int TR>
-__global__ void __launch_bounds__(256) k_galerkin_tiled(const T* __restrict__ Ahat,
-                                                        const T* __restrict__ Rhat,
-                                                        const uint32_t* __restrict__ pmask,
-                                                        GalerkinTileGeom g, T* __restrict__ Aout) {
-  constexpr int NR = TR * TR;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int NB = g.NB;
-  T* rr = reinterpret_cast<T*>(smem_raw);           // NR x 4 NB
-  T* t = rr + NR * 4 * NB;                          // NR x nwin x 4
-  int* nmap = reinterpret_cast<int*>(t + (size_t)NR * g.nwin * 4);
-  const int DN = 2 * g.RN + 1, DW = 2 * g.RW + 1, DS = 2 * g.RS + 1;
-  int* wmap = nmap + DN * DN;
-  int* smap = wmap + DW * DW;
-  for (int e = threadIdx.x; e < DN * DN; e += blockDim.x) nmap[e] = g.nmap[e];
-  for (int e = threadIdx.x; e < DW * DW; e += blockDim.x) wmap[e] = g.wmap[e];
-  for (int e = threadIdx.x; e < DS * DS; e += blockDim.x) smap[e] = g.smap[e];
-  int bx, by;
-  demorton((uint32_t)blockIdx.x, bx, by);
-  const int x0 = bx * TR, y0 = by * TR;
-  int64_t irow[NR];
-  bool ract[NR];
-#pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    const int rx = x0 + r % TR, ry = y0 + r / TR;
-    irow[r] = morton((uint32_t)rx, (uint32_t)ry);
-    ract[r] = (pmask[irow[r]] & 15u) != 0;
-  }
-  for (int e = threadIdx.x; e < NR * 4 * NB; e += blockDim.x) {
-    const int r = e / (4 * NB), q = e - r * 4 * NB;
-    rr[e] = ract[r] ? Rhat[irow[r] * 4 * NB + q] : T(0);
-  }
-  // window parents outside the lattice are never written below; their Rhat
-  // partners are zero, so they must read as zero too
-  for (int e = threadIdx.x; e < NR * g.nwin * 4; e += blockDim.x) t[e] = T(0);
-  __syncthreads();
-
-  // ---- phase 1: t_i = Ahat Rhat_i^T on the window of every tile row
-  const int BW = TR + 2 * g.RW;
-  for (int c = threadIdx.x; c < BW * BW; c += blockDim.x) {
-    const int px = x0 - g.RW + c % BW, py = y0 - g.RW + c / BW;
-    if ((unsigned)px >= (unsigned)g.Lpar || (unsigned)py >= (unsigned)g.Lpar) continue;
-    int wr[NR];
-    bool any = false;
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const int wx = px - (x0 + r % TR), wy = py - (y0 + r / TR);
-      int w = -1;
-      if (ract[r] && abs(wx) <= g.RW && abs(wy) <= g.RW) w = wmap[(wy + g.RW) * DW + wx + g.RW];
-      wr[r] = w;
-      any |= w >= 0;
-    }
-    if (!any) continue;
-    const int64_t pp = morton((uint32_t)px, (uint32_t)py);
-    T acc[NR][4];
-#pragma unroll
-    for (int r = 0; r < NR; ++r)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[r][b] = T(0);
-    for (int o = 0; o < g.noff; ++o) {
-      const int2 d = g.off[o];
-      int jr[NR];
-      bool use = false;
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        const int nx = px + d.x - (x0 + r % TR), ny = py + d.y - (y0 + r / TR);
-        int j = -1;
-        if (wr[r] >= 0 && abs(nx) <= g.RN && abs(ny) <= g.RN) j = nmap[(ny + g.RN) * DN + nx + g.RN];
-        jr[r] = j;
-        use |= j >= 0;
-      }
-      if (!use) continue;
-      T blk[16];
-      load_block16(Ahat + ((int64_t)o * g.nrow + pp) * 16, blk);
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (jr[r] < 0) continue;
-        const T* rv = rr + r * 4 * NB + 4 * jr[r];
-        const T r0 = rv[0], r1 = rv[1], r2 = rv[2], r3 = rv[3];
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          acc[r][b] += blk[4 * b] * r0 + blk[4 * b + 1] * r1 + blk[4 * b + 2] * r2 + blk[4 * b + 3] * r3;
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      if (wr[r] < 0) continue;
-      T* tw = t + ((size_t)r * g.nwin + wr[r]) * 4;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) tw[b] = acc[r][b];
-    }
-  }
-  __syncthreads();
-
-  // ---- phase 2: A_{i, i'} = Rhat_{i'} . t_i for i' - i in S+
-  const int BS = TR + 2 * g.RS;
-  for (int c = threadIdx.x; c < BS * BS; c += blockDim.x) {
-    const int ix = x0 - g.RS + c % BS, iy = y0 - g.RS + c / BS;
-    if ((unsigned)ix >= (unsigned)g.Lpar || (unsigned)iy >= (unsigned)g.Lpar) continue;
-    const int64_t ip = morton((uint32_t)ix, (uint32_t)iy);
-    if (!(pmask[ip] & 15u)) continue;
-    int sr[NR], dxr[NR], dyr[NR];
-    bool any = false;
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      dxr[r] = ix - (x0 + r % TR);
-      dyr[r] = iy - (y0 + r / TR);
-      int si = -1;
-      if (ract[r] && abs(dxr[r]) <= g.RS && abs(dyr[r]) <= g.RS)
-        si = smap[(dyr[r] + g.RS) * DS + dxr[r] + g.RS];
-      sr[r] = si;
-      any |= si >= 0;
-    }
-    if (!any) continue;
-    T acc2[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) acc2[r] = T(0);
-    const T* rowp = Rhat + ip * 4 * NB;
-    for (int j = 0; j < NB; ++j) {
-      T rv[4];
-      load_vec4(rowp + 4 * j, rv);
-      const int2 nj = g.nbr[j];
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        if (sr[r] < 0) continue;
-        const int wx = dxr[r] + nj.x, wy = dyr[r] + nj.y;
-        if (abs(wx) > g.RW || abs(wy) > g.RW) continue;
-        const int w = wmap[(wy + g.RW) * DW + wx + g.RW];
-        if (w < 0) continue;
-        const T* tw = t + ((size_t)r * g.nwin + w) * 4;
-        acc2[r] += rv[0] * tw[0] + rv[1] * tw[1] + rv[2] * tw[2] + rv[3] * tw[3];
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < NR; ++r)
-      if (sr[r] >= 0) Aout[(int64_t)sr[r] * g.nrow + irow[r]] = acc2[r];
-  }
-}
-
-size_t galerkin_tiled_smem(const GalerkinTileGeom& g, int tr, size_t elem) {
-  const int nr = tr * tr;
-  size_t b = elem * ((size_t)nr * 4 * g.NB + (size_t)nr * g.nwin * 4);
-  b += sizeof(int) * ((size_t)(2 * g.RN + 1) * (2 * g.RN + 1) + (size_t)(2 * g.RW + 1) * (2 * g.RW + 1) +
-                      (size_t)(2 * g.RS + 1) * (2 * g.RS + 1));
-  return (b + 15) & ~(size_t)15;
-}
-
-template <typename T, int TR>
-static void launch_tiled(const T* Ahat, const T* Rhat, const uint32_t* pmask, GalerkinTileGeom g,
-                         T* Aout, cudaStream_t s) {
-  const size_t smem = galerkin_tiled_smem(g, TR, sizeof(T));
-  cudaFuncSetAttribute(k_galerkin_tiled<T, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
-  const int64_t tiles = (int64_t)(g.Lpar / TR) * (g.Lpar / TR);
-  { count_launch(); k_galerkin_tiled<T, TR><<<(unsigned)tiles, 256, smem, s>>>(Ahat, Rhat, pmask, g, Aout); }
-}
-
-template <typename T>
-void launch_galerkin_tiled(const T* Ahat, const T* Rhat, const uint32_t* pmask_k,
-                           GalerkinTileGeom g, int tr, T* Aout, cudaStream_t s) {
-  if (g.nrow <= 0) return;
-  cudaMemsetAsync(Aout, 0, sizeof(T) * (size_t)g.nout * (size_t)g.nrow, s);
-  if (tr >= 4) launch_tiled<T, 4>(Ahat, Rhat, pmask_k, g, Aout, s);
-  else if (tr == 2) launch_tiled<T, 2>(Ahat, Rhat, pmask_k, g, Aout, s);
-  else launch_tiled<T, 1>(Ahat, Rhat, pmask_k, g, Aout, s);
-}
-template void launch_galerkin_tiled<float>(const float*, const float*, const uint32_t*,
-                                           GalerkinTileGeom, int, float*, cudaStream_t);
-template void launch_galerkin_tiled<double>(const double*, const double*, const uint32_t*,
-                                            GalerkinTileGeom, int, double*, cudaStream_t);
-
-}  // namespace gb

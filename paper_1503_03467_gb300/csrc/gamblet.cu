@@ -21,6 +21,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <set>
 #include <string>
 #include <utility>
@@ -281,10 +282,13 @@ struct Prof {
   }
 };
 
+struct Plan;  // symbolic plan of a geometry (defined with the setup code)
+
 }  // namespace
 
 struct gamblet_ctx {
   Prof prof;
+  std::shared_ptr<const Plan> plan;
   gamblet_opts opts;
   cudaStream_t s = nullptr;
   int q = 0;
@@ -312,6 +316,7 @@ struct gamblet_ctx {
   int* any_active = nullptr;
   int* any_active_h = nullptr;  // pinned
   int cg_blocks = 0;
+  int cg_spmv_blocks = 0;
   int cg_nlev = 0;
   int cg_max_ts = 1;
   cudaGraphExec_t cg_exec = nullptr;
@@ -522,6 +527,89 @@ void import_fine(gamblet_ctx* h, const gamblet_csr* A) {
   L.Ahat64 = blk;
 }
 
+// ------------------------------------------------------------ symbolic plan
+// Everything the localized setup derives from the geometry alone (q, rho,
+// neighbour rule and the fine operator's block offsets): offset sets, the
+// patch block lists and the Galerkin pair lists of every level.  It does not
+// depend on coefficient values, so it is built once per geometry and kept in
+// a process-wide cache (like an FFT plan).
+struct PlanLevel {
+  SymLevel S;
+  std::vector<int4> half, adj;   // patch CG: stored blocks and per-row adjacency
+  std::vector<int> adj_ptr, diag_h;
+  int spp = 1;
+  double flops_iter = 0;
+  std::vector<int> map_next;          // block conversion map (or the level-1 map)
+  OffSet O_next;
+};
+struct Plan {
+  std::vector<PlanLevel> lv;  // index k
+};
+
+int half_code(const OffSet& Sp, int dx, int dy);
+OffSet blocks_from_cells(const OffSet& S, const OffSet& Sp, int km1, std::vector<int>& map);
+
+std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N) {
+  auto plan = std::make_shared<Plan>();
+  plan->lv.resize(q + 1);
+  const int NB = N.size();
+  OffSet O = Oq;
+  for (int k = q; k >= 2; --k) {
+    PlanLevel& pl = plan->lv[k];
+    pl.S = build_sym(O, N, k);
+    // patch blocks: pairs (ja >= jb) coupled through O_k
+    std::vector<std::vector<int4>> rows(NB);
+    pl.adj_ptr.assign(NB + 1, 0);
+    pl.diag_h.assign(NB, -1);
+    for (int ja = 0; ja < NB; ++ja)
+      for (int jb = 0; jb <= ja; ++jb) {
+        const int o = pl.S.pair_idx[(size_t)ja * NB + jb];
+        if (o < 0) continue;
+        const int hidx = (int)pl.half.size();
+        pl.half.push_back(make_int4(ja, jb, o, 0));
+        rows[ja].push_back(make_int4(hidx, jb, 0, 0));
+        if (jb != ja) rows[jb].push_back(make_int4(hidx, ja, 1, 0));
+        else pl.diag_h[ja] = hidx;
+      }
+    for (int j = 0; j < NB; ++j) {
+      if (pl.diag_h[j] < 0) fail(GAMBLET_ERR_INVALID_ARG, "patch block without diagonal");
+      pl.adj_ptr[j + 1] = pl.adj_ptr[j] + (int)rows[j].size();
+      pl.adj.insert(pl.adj.end(), rows[j].begin(), rows[j].end());
+    }
+    const double row_len = (double)pl.adj.size() / NB;
+    pl.spp = row_len > 24 ? 4 : (row_len > 12 ? 2 : 1);
+    while (pl.spp > 1 && NB * pl.spp > 256) pl.spp >>= 1;
+    pl.flops_iter = 18.0 * (2.0 * pl.half.size() - NB) + 60.0 * NB;
+    if (k - 1 >= 2) {
+      pl.O_next = blocks_from_cells(pl.S.S, pl.S.Sp, k - 1, pl.map_next);
+      O = pl.O_next;
+    } else {
+      pl.map_next.assign(16, -1);
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j)
+          pl.map_next[i * 4 + j] = half_code(pl.S.Sp, (j & 1) - (i & 1), (j >> 1) - (i >> 1));
+    }
+  }
+  return plan;
+}
+
+std::shared_ptr<const Plan> cached_plan(int q, double rho, int rule, const OffSet& Oq,
+                                        const OffSet& N) {
+  static std::mutex mu;
+  static std::map<std::string, std::shared_ptr<const Plan>> cache;
+  std::string key = std::to_string(q) + "/" + std::to_string(rho) + "/" + std::to_string(rule);
+  for (const int2& o : Oq.v) key += "/" + std::to_string(o.x) + "," + std::to_string(o.y);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  auto plan = build_plan(q, Oq, N);
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = plan;
+  return plan;
+}
+
 // Algorithmic flops of the level-k patch solves: for a patch with n active
 // unknowns, n^3/3 (Cholesky, right-hand side carried along) + 2 n^2 (the two
 // triangular sweeps), multiply-adds counted as two flops.
@@ -570,49 +658,29 @@ void setup_local(gamblet_ctx* h) {
       L.Ahat = L.Ahat64;
     }
   }
-  OffSet O = OffSet();
-  for (const int2& o : h->lv[q].off_h) O.add(o.x, o.y);
+  OffSet Oq;
+  for (const int2& o : h->lv[q].off_h) Oq.add(o.x, o.y);
+  std::shared_ptr<const Plan> plan = cached_plan(q, h->opts.rho, h->opts.nbr_rule, Oq, h->N);
+  h->plan = plan;
   for (int k = q; k >= 2; --k) {
     LevelDev& L = h->lv[k];
-    SymLevel S = build_sym(O, h->N, k);
+    const PlanLevel& pl = plan->lv[k];
+    const SymLevel& S = pl.S;
     const int Lpar = 1 << (k - 1);
     L.pair_idx = P.upload(S.pair_idx, s);
     // patch solves -> Rhat^(k-1,k)
     T* Rhat = P.alloc<T>((int64_t)NB * 4 * L.npar);
-    PatchGeom pg{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar};
     const double sz = (double)sizeof(T);
     const double pbytes = sz * ((double)L.noff * L.npar * 16 + 4.0 * NB * L.npar);
     if (h->patch_tol < 0) {
+      PatchGeom pg{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar};
       int tok = h->prof.begin("patch_cholesky", pbytes, h->prof.on ? patch_flops(h, k) : 0.0, s);
       launch_patch_solve<T>((const T*)L.Ahat, L.pmask, pg, Rhat, h->status, h->num_sms, s);
       h->prof.end(tok, s);
     } else {
-      // stored blocks: pairs (ja >= jb) coupled through O_k; per-row adjacency
-      std::vector<int4> half, adj;
-      std::vector<int> adj_ptr(NB + 1, 0), diag_h(NB, -1);
-      std::vector<std::vector<int4>> rows(NB);
-      for (int ja = 0; ja < NB; ++ja)
-        for (int jb = 0; jb <= ja; ++jb) {
-          const int o = S.pair_idx[(size_t)ja * NB + jb];
-          if (o < 0) continue;
-          const int hidx = (int)half.size();
-          half.push_back(make_int4(ja, jb, o, 0));
-          rows[ja].push_back(make_int4(hidx, jb, 0, 0));
-          if (jb != ja) rows[jb].push_back(make_int4(hidx, ja, 1, 0));
-          else diag_h[ja] = hidx;
-        }
-      for (int j = 0; j < NB; ++j) {
-        if (diag_h[j] < 0) fail(GAMBLET_ERR_INVALID_ARG, "patch block without diagonal");
-        adj_ptr[j + 1] = adj_ptr[j] + (int)rows[j].size();
-        adj.insert(adj.end(), rows[j].begin(), rows[j].end());
-      }
-      // long block rows (dense coarse levels) are split over 2 or 4 lanes
-      const double row_len = (double)adj.size() / NB;
-      int spp = row_len > 24 ? 4 : (row_len > 12 ? 2 : 1);
-      while (spp > 1 && NB * spp > 256) spp >>= 1;
-      PatchPcgGeom gp{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar, (int)half.size(),
-                      P.upload(half, s), P.upload(adj_ptr, s), P.upload(adj, s),
-                      P.upload(diag_h, s), spp};
+      PatchPcgGeom gp{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar, (int)pl.half.size(),
+                      P.upload(pl.half, s), P.upload(pl.adj_ptr, s), P.upload(pl.adj, s),
+                      P.upload(pl.diag_h, s), pl.spp};
       if (patch_pcg_smem_bytes<T>(gp) > 227 * 1024)
         fail(GAMBLET_ERR_UNSUPPORTED, "patch blocks exceed shared memory; lower rho");
       // flops are added after setup from the measured iteration counts
@@ -620,14 +688,14 @@ void setup_local(gamblet_ctx* h) {
       launch_patch_pcg<T>((const T*)L.Ahat, L.pmask, gp, Rhat, h->patch_tol, 200,
                           h->patch_stats + 4 * k, h->num_sms, s);
       h->prof.end(tok, s);
-      h->patch_flops_iter_k[k] = 18.0 * (2.0 * half.size() - NB) + 60.0 * NB;
+      h->patch_flops_iter_k[k] = pl.flops_iter;
     }
     CK(cudaGetLastError());
     L.Rhat = Rhat;
     T* RT = P.alloc<T>((int64_t)NB * 4 * L.npar);
     launch_transpose_rhat<T>(Rhat, NB, h->nbr, Lpar, L.npar, RT, s);
     L.RT = RT;
-    // Galerkin product -> level k-1 cell stencil
+    // Galerkin product -> level k-1 cell stencil (one CTA per coarse row)
     GalerkinGeom gg;
     gg.NB = NB;
     gg.nbr = h->nbr;
@@ -641,50 +709,22 @@ void setup_local(gamblet_ctx* h) {
     gg.l2_pairs = P.upload(S.l2_pairs, s);
     gg.Lpar = Lpar;
     gg.nrow = L.npar;
-    // tiled Galerkin: dense offset lookup tables over the boxes of N, WIN, S+
-    auto box_table = [](const std::vector<int2>& v, int& R) {
-      R = 0;
-      for (const int2& d : v) R = std::max(R, std::max(std::abs(d.x), std::abs(d.y)));
-      const int D = 2 * R + 1;
-      std::vector<int> tab((size_t)D * D, -1);
-      for (int e = 0; e < (int)v.size(); ++e) tab[(size_t)(v[e].y + R) * D + v[e].x + R] = e;
-      return tab;
-    };
-    GalerkinTileGeom tg;
-    tg.NB = NB;
-    tg.nbr = h->nbr;
-    tg.noff = L.noff;
-    tg.off = L.off;
-    std::vector<int> nmap = box_table(h->N.v, tg.RN);
-    std::vector<int> wmap = box_table(S.WIN.v, tg.RW);
-    std::vector<int> smap = box_table(S.Sp.v, tg.RS);
-    tg.nmap = P.upload(nmap, s);
-    tg.wmap = P.upload(wmap, s);
-    tg.smap = P.upload(smap, s);
-    tg.nwin = S.WIN.size();
-    tg.nout = S.Sp.size();
-    tg.Lpar = Lpar;
-    tg.nrow = L.npar;
-    int tr = 4;
-    while (tr > 1 && (tr > Lpar || galerkin_tiled_smem(tg, tr, sizeof(T)) > 110 * 1024)) tr >>= 1;
-    if (galerkin_tiled_smem(tg, tr, sizeof(T)) > 227 * 1024)
+    if (sizeof(T) * 4 * ((size_t)NB + (size_t)gg.nwin) > 227 * 1024)
       fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin window exceeds shared memory");
     T* Acell = P.alloc<T>((int64_t)gg.nout * L.npar);
     int tok = h->prof.begin(
         "galerkin_k" + std::to_string(k),
         sz * ((double)L.noff * L.npar * 16 + 4.0 * NB * L.npar + (double)gg.nout * L.npar),
         2.0 * (16.0 * S.l1_pairs.size() + 4.0 * S.l2_pairs.size()) * h->lv[k - 1].n_active, s);
-    launch_galerkin_tiled<T>((const T*)L.Ahat, Rhat, L.pmask, tg, tr, Acell, s);
+    launch_galerkin<T>((const T*)L.Ahat, Rhat, L.pmask, gg, Acell, s);
     h->prof.end(tok, s);
     CK(cudaGetLastError());
     if (k - 1 >= 2) {
       LevelDev& Ln = h->lv[k - 1];
-      std::vector<int> map;
-      OffSet On = blocks_from_cells(S.S, S.Sp, k - 1, map);
-      Ln.off_h = On.v;
-      Ln.noff = On.size();
+      Ln.off_h = pl.O_next.v;
+      Ln.noff = pl.O_next.size();
       Ln.off = P.upload(Ln.off_h, s);
-      int* dmap = P.upload(map, s);
+      int* dmap = P.upload(pl.map_next, s);
       T* blk = P.alloc<T>((int64_t)Ln.noff * Ln.npar * 16);
       tok = h->prof.begin("cells_to_blocks",
                           sz * ((double)gg.nout * L.npar + (double)Ln.noff * Ln.npar * 16), 0.0, s);
@@ -693,13 +733,8 @@ void setup_local(gamblet_ctx* h) {
       h->prof.end(tok, s);
       CK(cudaGetLastError());
       Ln.Ahat = blk;
-      O = On;
     } else {
-      std::vector<int> map1(16, -1);
-      for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j)
-          map1[i * 4 + j] = half_code(S.Sp, (j & 1) - (i & 1), (j >> 1) - (i >> 1));
-      h->l1map = P.upload(map1, s);
+      h->l1map = P.upload(pl.map_next, s);
       h->A1L = P.alloc<double>(16);
       launch_level1_factor<T>(Acell, h->l1map, h->A1L, h->status, s);
       CK(cudaGetLastError());
@@ -825,7 +860,7 @@ void alloc_solve(gamblet_ctx* h) {
   if (!h->exact) {
     std::vector<CgLevel> cl;
     int blocks = 0;
-    int max_ts = 1;
+    int max_ts = 1, sblocks = 0;
     for (int k = 2; k <= q; ++k) {
       LevelDev& L = h->lv[k];
       CgLevel c;
@@ -844,9 +879,15 @@ void alloc_solve(gamblet_ctx* h) {
       c.b = L.ghat;
       c.block_begin = blocks;
       blocks += (int)((L.npar + 255) / 256);
-      max_ts = std::max(max_ts, std::min(c.Lpar, 16) + 2 * L.R);
+      // wide stencils: four threads per parent over 8 x 8 tiles (more loads in flight)
+      c.spp = L.noff > 32 ? 4 : 1;
+      const int tmax = c.spp == 4 ? 8 : 16;
+      c.spmv_begin = sblocks;
+      sblocks += (int)((L.npar + tmax * tmax - 1) / (tmax * tmax));
+      max_ts = std::max(max_ts, std::min(c.Lpar, tmax) + 2 * L.R);
       cl.push_back(c);
     }
+    h->cg_spmv_blocks = sblocks;
     h->cg_max_ts = max_ts;
     if (cg_spmv_smem_bytes(max_ts, sizeof(T)) > 227 * 1024)
       fail(GAMBLET_ERR_UNSUPPORTED, "level operator stencil too wide for the CG tile");
@@ -868,7 +909,7 @@ void build_cg_graph(gamblet_ctx* h, int chunk, double tol2, int maxit) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   for (int c = 0; c < chunk; ++c) {
-    launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, h->cg_max_ts, cs);
+    launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_spmv_blocks, h->cg_sc, h->cg_max_ts, cs);
     launch_cg_rest<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit, h->any_active,
                       cs);
   }
@@ -898,7 +939,7 @@ void run_level_cg(gamblet_ctx* h) {
     } else {
       for (int c = 0; c < chunk; ++c) {
         int tok = h->prof.begin("level_cg_spmv", 0.0, 0.0, s);
-        launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, h->cg_max_ts, s);
+        launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_spmv_blocks, h->cg_sc, h->cg_max_ts, s);
         h->prof.end(tok, s);
         tok = h->prof.begin("level_cg_vector", 0.0, 0.0, s);
         launch_cg_rest<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit,

@@ -110,27 +110,6 @@ struct GalerkinGeom {
 template <typename T>
 void launch_galerkin(const T* Ahat, const T* Rhat, const uint32_t* pmask_k, GalerkinGeom g,
                      T* Aout, cudaStream_t s);
-// Tiled variant (one CTA per tr x tr tile of coarse rows; tr in {1, 2, 4},
-// tr <= Lpar); offsets located through dense lookup tables over the boxes
-// [-R, R]^2 of N (nmap), the window (wmap) and the half-plane output (smap).
-struct GalerkinTileGeom {
-  int NB;
-  const int2* nbr;
-  int noff;
-  const int2* off;   // O_k
-  int RN;
-  const int* nmap;   // N index or -1
-  int nwin, RW;
-  const int* wmap;   // WIN index or -1
-  int nout, RS;
-  const int* smap;   // S+ index or -1
-  int Lpar;
-  int64_t nrow;
-};
-template <typename T>
-void launch_galerkin_tiled(const T* Ahat, const T* Rhat, const uint32_t* pmask_k,
-                           GalerkinTileGeom g, int tr, T* Aout, cudaStream_t s);
-size_t galerkin_tiled_smem(const GalerkinTileGeom& g, int tr, size_t elem);
 // Level-(k-1) cell stencil (S offsets, [d][i]) -> transformed block stencil
 // at level k-1 (offsets O, [o][P][16]) using masks of level k-1 parents.
 // map: nO x 16 index into S of 2*Delta + c' - c for (a = c, b = c'), or -1.
@@ -180,7 +159,9 @@ struct CgLevel {
   void* p;
   void* Ap;
   const void* b;      // right-hand side (transformed vector; slots 0..2 used)
-  int block_begin;    // first CTA of this level in the batched grid
+  int block_begin;    // first CTA of this level in the vector-kernel grid
+  int spmv_begin;     // first CTA of this level in the SpMV grid
+  int spp;            // SpMV threads per parent (1: 16 x 16 tiles, 4: 8 x 8 tiles)
 };
 struct CgScalars {
   double rz, rz_new, rr, rr_new, pAp, rr0, beta;
@@ -197,7 +178,7 @@ void launch_cg_start(CgScalars* sc, int nlev, double tol2, int* any_active, cuda
 // (x, r, z update with r.z and r.r; scalars and convergence; p = z + beta p).
 template <typename T>
 void launch_cg_spmv(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, int max_ts,
-                    cudaStream_t s);
+                    cudaStream_t s);  // total_blocks: SpMV grid size
 template <typename T>
 void launch_cg_rest(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, double tol2,
                     int max_iter, int* any_active, cudaStream_t s);

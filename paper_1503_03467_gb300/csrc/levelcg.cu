@@ -21,6 +21,11 @@ __device__ __forceinline__ int find_level(const CgLevel* lv, int nlev, int b) {
   while (l + 1 < nlev && lv[l + 1].block_begin <= b) ++l;
   return l;
 }
+__device__ __forceinline__ int find_level_spmv(const CgLevel* lv, int nlev, int b) {
+  int l = 0;
+  while (l + 1 < nlev && lv[l + 1].spmv_begin <= b) ++l;
+  return l;
+}
 
 __device__ __forceinline__ void block_sum_add(double v, double* dst, double* red) {
   v = warp_sum(v);
@@ -101,20 +106,23 @@ __global__ void k_cg_start(CgScalars* sc, int nlev, double tol2, int* any_active
 }
 
 // Ap = B p over the 3x3 detail blocks; pAp += p.Ap.  One CTA = one tile of
-// T x T parents (T = 16, or the whole lattice when it is smaller).
+// T x T parents (T = 16, or 8 with four threads per parent splitting the
+// offsets when the stencil is wide; or the whole lattice when smaller).
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg_spmv(const CgLevel* __restrict__ lv, int nlev,
                                                  CgScalars* sc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[8];
-  const int l = find_level(lv, nlev, blockIdx.x);
+  const int l = find_level_spmv(lv, nlev, blockIdx.x);
   if (!sc[l].active) return;
   const CgLevel L = lv[l];
-  const int tile = L.Lpar < 16 ? L.Lpar : 16;
+  const int spp = L.spp;
+  const int tmax = spp == 4 ? 8 : 16;
+  const int tile = L.Lpar < tmax ? L.Lpar : tmax;
   const int R = L.R;
   const int TS = tile + 2 * R;
   T* xs = reinterpret_cast<T*>(smem_raw);  // 3 planes of TS x TS
-  const int64_t base = (int64_t)(blockIdx.x - L.block_begin) * 256;
+  const int64_t base = (int64_t)(blockIdx.x - L.spmv_begin) * (tmax * tmax);
   int x0, y0;
   demorton((uint32_t)base, x0, y0);
   const T* pv = (const T*)L.p;
@@ -132,16 +140,19 @@ __global__ void __launch_bounds__(256) k_cg_spmv(const CgLevel* __restrict__ lv,
     xs[2 * TS * TS + c] = v2;
   }
   __syncthreads();
-  const int64_t p = base + threadIdx.x;
-  double part = 0;
-  if (threadIdx.x < tile * tile && p < L.npar) {
+  const int pl = threadIdx.x / spp, sub = threadIdx.x - (threadIdx.x / spp) * spp;
+  const int64_t p = base + pl;
+  const bool own = pl < tile * tile && p < L.npar;
+  T y0v = 0, y1v = 0, y2v = 0;
+  int lx = 0, ly = 0;
+  if (own) {
     int px, py;
     demorton((uint32_t)p, px, py);
-    const int lx = px - x0 + R, ly = py - y0 + R;
+    lx = px - x0 + R;
+    ly = py - y0 + R;
     const T* Bd = (const T*)L.Bd;
     const int64_t np = L.npar;
-    T y0v = 0, y1v = 0, y2v = 0;
-    for (int o = 0; o < L.noff; ++o) {
+    for (int o = sub; o < L.noff; o += spp) {
       const int2 d = L.off[o];
       const int c = (ly + d.y) * TS + lx + d.x;
       const T a0 = xs[c], a1 = xs[TS * TS + c], a2 = xs[2 * TS * TS + c];
@@ -150,6 +161,14 @@ __global__ void __launch_bounds__(256) k_cg_spmv(const CgLevel* __restrict__ lv,
       y1v += B[3 * np] * a0 + B[4 * np] * a1 + B[5 * np] * a2;
       y2v += B[6 * np] * a0 + B[7 * np] * a1 + B[8 * np] * a2;
     }
+  }
+  for (int o = 1; o < spp; o <<= 1) {
+    y0v += __shfl_xor_sync(0xffffffffu, y0v, o);
+    y1v += __shfl_xor_sync(0xffffffffu, y1v, o);
+    y2v += __shfl_xor_sync(0xffffffffu, y2v, o);
+  }
+  double part = 0;
+  if (own && sub == 0) {
     T* Ap = (T*)L.Ap;
     Ap[4 * p] = y0v;
     Ap[4 * p + 1] = y1v;
