@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain float64 arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient timing")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the many-problem (48 x {128,256,512}^2) timing")
+    ap.add_argument("--batch-problems", type=int, default=48)
+    ap.add_argument("--batch-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -177,6 +181,7 @@ def opts_for(nv, a, precision, stream_ptr, profile):
     o.level_max_iter = 2000
     o.refine_tol = a.refine_tol
     o.refine_max_iter = 100
+    o.patch_tol = getattr(a, "patch_tol", 0.0)
     o.profile = profile
     o.stream = stream_ptr
     return o
@@ -291,6 +296,103 @@ def adjoint_timing(nv, torch, dev, steps=3):
     f, b = statistics.mean(fwd), statistics.mean(bwd)
     return {"workload": "256x256 Q1, q=8, contrast 1e3, 65,536 cells", "forward_ms": f,
             "grad_ms": b, "grad_over_forward": b / f, "rel_err_vs_oracle_adjoint": err}
+
+
+def batched_timing(nv, torch, dev, a, stream, flush):
+    """Many independent problems (seeds 1..P, sides drawn from {128, 256, 512},
+    contrast log-uniform in [1e2, 1e6]) set up and solved as one hierarchy by
+    gamblet_setup_batched, against the same problems one by one through
+    gamblet_setup.  Accuracy: relative residual of every problem (float64,
+    torch sparse product, validation only) and the oracle's direct solve for
+    the first problem of each side."""
+    from workloads import make_batch
+    probs = make_batch(a.batch_problems, first_seed=1)
+    items, gs = [], []
+    for p in probs:
+        A = p.A.tocsr()
+        A.sort_indices()
+        items.append((torch.from_numpy(A.indptr.astype(np.int32)).to(dev),
+                      torch.from_numpy(A.indices.astype(np.int32)).to(dev),
+                      torch.from_numpy(A.data.astype(np.float64)).to(dev), p.q,
+                      torch.from_numpy(np.ascontiguousarray(p.cells, dtype=np.int32)).to(dev)))
+        gs.append(torch.from_numpy(p.g).to(dev))
+    g = torch.cat(gs)
+    ndof = int(g.shape[0])
+    u = torch.zeros_like(g)
+    o = opts_for(nv, a, nv.MIXED, stream.cuda_stream, 0)
+    times, setup, solve, outer = [], [], [], []
+    off = None
+    for it in range(1 + a.batch_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            h, off = nv.gamblet_setup_batched(items, o)
+            info = nv.Info()
+            nv.gamblet_solve(h, g, u, None, info)
+            e1.record(stream)
+        e1.synchronize()
+        nv.gamblet_destroy(h)
+        if it > 0:
+            times.append(e0.elapsed_time(e1))
+            setup.append(info.setup_ms)
+            solve.append(info.solve_ms)
+            outer.append(info.outer_iters)
+    ms = statistics.mean(times)
+    # accuracy per problem
+    res = []
+    for p, (rp, ci, va, q, _), gp in zip(range(len(probs)), items, gs):
+        A = torch.sparse_csr_tensor(rp.long(), ci.long(), va, size=(gp.shape[0],) * 2)
+        up = u[int(off[p]):int(off[p + 1])]
+        res.append(float(torch.linalg.norm(gp - A @ up) / torch.linalg.norm(gp)))
+    ub = u.cpu().numpy()
+    err = {}
+    for p, pr in enumerate(probs):
+        if pr.n in err:
+            continue
+        ud, _ = cpu_oracle(pr)
+        err[pr.n] = rel_err(ub[int(off[p]):int(off[p + 1])], ud)
+    # the same problems one at a time (plans of each size warmed first)
+    seq = []
+    seen = set()
+    for p, it in enumerate(items):
+        if probs[p].n not in seen:
+            seen.add(probs[p].n)
+            with torch.cuda.stream(stream):
+                h = nv.gamblet_setup(it[0], it[1], it[2], it[3], it[4], o)
+                nv.gamblet_solve(h, gs[p], torch.zeros_like(gs[p]))
+            nv.gamblet_destroy(h)
+    for p, it in enumerate(items):
+        up = torch.zeros_like(gs[p])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            h = nv.gamblet_setup(it[0], it[1], it[2], it[3], it[4], o)
+            nv.gamblet_solve(h, gs[p], up)
+            e1.record(stream)
+        e1.synchronize()
+        nv.gamblet_destroy(h)
+        seq.append(e0.elapsed_time(e1))
+    seq_total = sum(seq)
+    sides = [pr.n for pr in probs]
+    return {
+        "workload": f"{len(probs)} problems, seeds 1..{len(probs)}, sides "
+                    f"128/256/512 x {sides.count(128)}/{sides.count(256)}/{sides.count(512)}, "
+                    "contrast log-uniform [1e2, 1e6], rho 3, mixed precision",
+        "dofs": ndof, "value": ndof / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+        "setup_ms": statistics.mean(setup), "solve_ms": statistics.mean(solve),
+        "outer_iters": max(outer), "max_rel_residual": max(res),
+        "rel_err_vs_oracle": {str(k): v for k, v in sorted(err.items())},
+        "batched_problem_latency_ms": ms,
+        "one_by_one": {"value": ndof / (seq_total * 1e-3), "ms_total": seq_total,
+                       "p50_ms": float(np.percentile(seq, 50)),
+                       "p99_ms": float(np.percentile(seq, 99))},
+        "speedup_vs_one_by_one": seq_total / ms,
+    }
 
 
 def cpu_oracle(p):
@@ -456,6 +558,8 @@ def main():
         line["speedup_mixed_vs_plain"] = line["plain_fp64"]["ms_per_step"] / ms
     if not a.no_adjoint:
         line["adjoint"] = adjoint_timing(nv, torch, dev)
+    if not a.no_batched:
+        line["batched"] = batched_timing(nv, torch, dev, a, stream, flush)
     if rank == 0 and ws == 1 and not a.no_cpu:
         line["cpu_baseline"] = {"value": ndof / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "one full solve of the same problem: SuperLU factor + "

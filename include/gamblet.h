@@ -88,12 +88,20 @@ typedef struct {
                                one-pass transform of Algorithm 2 only      */
   /* Patch systems of Definition defb: > 0 = block-Jacobi preconditioned CG
    * to this relative residual (Sec. 5.4 / Thm tmdiscreteaccuracy allow
-   * inexact patch solves); 0 = default (1e-6 mixed, 1e-12 float64);
-   * < 0 = dense Cholesky (exact to rounding).                              */
+   * inexact patch solves); 0 = default (1e-3 mixed, 1e-12 float64);
+   * < 0 = dense Cholesky (exact to rounding).  An inexact patch solve only
+   * changes R (any full-rank R keeps R A R^T SPD), so the mixed default
+   * trades a slightly weaker preconditioner for fewer patch iterations;
+   * the outer float64 iteration restores the accuracy.                    */
   double patch_tol;
   int32_t use_graph;        /* capture repeated launch sequences in CUDA graphs */
   int32_t profile;          /* 1: time every kernel phase with CUDA events on
                                the library's stream (gamblet_kernel_stats)  */
+  int32_t autotune;         /* 1: pick launch shapes (patch-CG lanes per
+                               neighbour parent, level-CG SpMV tile) by
+                               timing candidates on a sample of each large
+                               level, once per geometry and precision in a
+                               process; 0: fixed rules                     */
   void* stream;             /* cudaStream_t                                */
 } gamblet_opts;
 
@@ -113,7 +121,7 @@ typedef struct gamblet_ctx* gamblet_handle;
 
 /* Fill *opts with defaults: rho = 3, Euclidean rule, FP64, level_tol 1e-8,
  * level_max_iter 1000, refine_tol 1e-13, refine_max_iter 50, graphs on,
- * profiling off, default stream. */
+ * profiling off, autotuning on, default stream. */
 GAMBLET_API void gamblet_default_opts(gamblet_opts* opts);
 
 /*
@@ -134,6 +142,39 @@ GAMBLET_API void gamblet_default_opts(gamblet_opts* opts);
  */
 GAMBLET_API gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cells,
                              const gamblet_opts* opts, gamblet_handle* out);
+
+/*
+ * Setup of nprob independent problems (each its own fine stiffness,
+ * lattice and coefficient field, Sec. 5 per problem) as ONE hierarchy, so
+ * that every level's patch solves, Galerkin products and level CGs of all
+ * problems run in one launch per level.  The problems are placed, largest
+ * first, in disjoint aligned subtrees of one 2^Q x 2^Q lattice (Q the
+ * smallest with 4^Q >= sum_p 4^q[p]); the combined fine operator is block
+ * diagonal.  On the levels where a problem still spans several cells, its
+ * gamblets, R rows and level operators equal those of its own hierarchy
+ * (patches that reach into a neighbouring subtree see zero coupling there);
+ * above its own level 1 the measurement cells hold several problems, which
+ * is again a nested hierarchy of the combined operator (Sec. 4.1), so the
+ * solve is exact for every problem.
+ *   nprob    number of problems (>= 1).
+ *   A, q     arrays of nprob: fine stiffness and level count (1..15) of
+ *            each problem, as for gamblet_setup (host or device arrays).
+ *   cells    array of nprob pointers: n_p x 2 int32 cells of problem p in
+ *            its own 2^q[p] lattice.
+ *   opts     options (NULL = defaults); rho must be > 0.
+ *   out      receives the handle; gamblet_solve on it takes g and u of
+ *            sum_p n_p entries, problem after problem.
+ *   offsets  NULL or host array of nprob + 1: problem p owns entries
+ *            [offsets[p], offsets[p + 1]) of those vectors.
+ * info->setup_ms includes packing the problems.  Returns INVALID_ARG for
+ * malformed input (a column index or cell outside its problem), UNSUPPORTED
+ * when the packed lattice would exceed 2^15 cells per side or the combined
+ * CSR int32 indexing.
+ */
+GAMBLET_API gamblet_status gamblet_setup_batched(int32_t nprob, const gamblet_csr* A,
+                                                 const int32_t* q, const int32_t* const* cells,
+                                                 const gamblet_opts* opts, gamblet_handle* out,
+                                                 int32_t* offsets);
 
 /*
  * Solve A u = g (Eqs. eqyguugy6t, eqsdjoejddi1, eqsdjoejddi2, Theorem

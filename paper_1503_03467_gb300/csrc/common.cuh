@@ -6,8 +6,15 @@
 //    the odd ones.  The four children of a level-(k-1) cell p are then the
 //    contiguous entries 4p + c, with slot c = (y & 1) * 2 + (x & 1) - the
 //    row-major (y, x) sibling order of the detail basis W^(k) (Sec. 4.6).
+//  * A level stores the Morton prefix of its lattice that holds cells:
+//    npar_k parents (level-(k-1) cells) and ncell_k = 4 npar_k cells, with
+//    npar_(k-1) = ceil(npar_k / 4).  A single square problem fills the
+//    lattice (npar_k = 4^(k-1)); independent problems packed into aligned
+//    subtrees of one lattice fill a prefix of it.  Cells beyond the prefix
+//    do not exist: every neighbour lookup (shift_cell) rejects them.
 //  * Each parent p carries a 4-bit mask of its non-empty children (holes
-//    occur only where the fine grid has no node).  Its orthonormal 4x4
+//    occur where the fine grid has no node, and in the last parents of a
+//    prefix).  Its orthonormal 4x4
 //    transform Q_p (rows: detail t = 0..m-2, unused rows, and row 3 =
 //    1/sqrt(m) on the children) is the Helmert matrix Ubar^(m) of Lemma
 //    const0 (Construction const2) embedded on the active slots; it is
@@ -61,11 +68,15 @@ __host__ __device__ __forceinline__ void demorton(uint32_t m, int& x, int& y) {
   x = (int)compact_bits(m);
   y = (int)compact_bits(m >> 1);
 }
-// Morton index of (x + dx, y + dy) on a side-L lattice, or -1 outside.
-__host__ __device__ __forceinline__ int shift_cell(int x, int y, int dx, int dy, int L) {
+// Morton index of (x + dx, y + dy) on a side-L lattice whose stored cells
+// are the Morton prefix [0, n) (n = L * L for a full square), or -1 when the
+// shifted cell is outside the lattice or beyond the prefix.
+__host__ __device__ __forceinline__ int shift_cell(int x, int y, int dx, int dy, int L,
+                                                   int64_t n) {
   int nx = x + dx, ny = y + dy;
   if ((unsigned)nx >= (unsigned)L || (unsigned)ny >= (unsigned)L) return -1;
-  return (int)morton((uint32_t)nx, (uint32_t)ny);
+  const uint32_t m = morton((uint32_t)nx, (uint32_t)ny);
+  return (int64_t)m < n ? (int)m : -1;
 }
 
 // Entry (a, c) of the per-parent transform Q for child mask m: with

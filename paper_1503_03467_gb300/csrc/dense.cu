@@ -17,7 +17,7 @@ __global__ void k_dense_from_blocks(const double* __restrict__ blk, const int2* 
   const int64_t p = t - (int64_t)o * npar;
   int x, y;
   demorton((uint32_t)p, x, y);
-  const int pp = shift_cell(x, y, off[o].x, off[o].y, Lpar);
+  const int pp = shift_cell(x, y, off[o].x, off[o].y, Lpar, npar);
   if (pp < 0) return;
   const int64_t ld = 4 * npar;
   for (int a = 0; a < 4; ++a)

@@ -15,27 +15,7 @@
 
 namespace gb {
 
-// 16-element block / 4-element row loads as 128-bit transactions
-__device__ __forceinline__ void load_block16(const float* p, float* b) {
-  const float4* q = reinterpret_cast<const float4*>(p);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float4 v = __ldg(q + k);
-    b[4 * k] = v.x;
-    b[4 * k + 1] = v.y;
-    b[4 * k + 2] = v.z;
-    b[4 * k + 3] = v.w;
-  }
-}
-__device__ __forceinline__ void load_block16(const double* p, double* b) {
-  const double2* q = reinterpret_cast<const double2*>(p);
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const double2 v = __ldg(q + k);
-    b[2 * k] = v.x;
-    b[2 * k + 1] = v.y;
-  }
-}
+// 4-element row loads as 128-bit transactions
 __device__ __forceinline__ void load_vec4(const float* p, float* b) {
   const float4 v = __ldg(reinterpret_cast<const float4*>(p));
   b[0] = v.x;
@@ -52,6 +32,13 @@ __device__ __forceinline__ void load_vec4(const double* p, double* b) {
   b[3] = v1.y;
 }
 
+// One CTA per coarse row i.  Phase 1: a half-warp per window position w;
+// its 16 lanes hold the 16 entries of a 4x4 block, so every block of Ahat is
+// one coalesced 64-byte (float) read, multiplied by the matching entry of
+// Rhat_i from shared memory and reduced over the block's columns by two
+// shuffles.  Phase 2: a warp per output offset d; its lanes walk the (j, w)
+// pairs of d, reading the row Rhat_{i+S_d} with unit stride, and the dot
+// product ends in a warp reduction.
 template <typename T>
 __global__ void __launch_bounds__(256) k_galerkin(const T* __restrict__ Ahat,
                                                   const T* __restrict__ Rhat,
@@ -61,6 +48,10 @@ __global__ void __launch_bounds__(256) k_galerkin(const T* __restrict__ Ahat,
   T* rrow = reinterpret_cast<T*>(smem_raw);
   T* t = rrow + 4 * g.NB;
   const int64_t nrow = g.nrow;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int half = threadIdx.x >> 4, nhalf = blockDim.x >> 4;
+  const int e = threadIdx.x & 15, cb = e & 3;  // block entry (a = e >> 2, column cb)
+  const unsigned hmask = 0xffffu << (16 * (half & 1));
   for (int64_t i = blockIdx.x; i < nrow; i += gridDim.x) {
     if ((pmask[i] & 15u) == 0) {
       for (int d = threadIdx.x; d < g.nout; d += blockDim.x) Aout[(int64_t)d * nrow + i] = T(0);
@@ -72,45 +63,39 @@ __global__ void __launch_bounds__(256) k_galerkin(const T* __restrict__ Ahat,
       rrow[idx] = Rhat[i * 4 * g.NB + idx];
     __syncthreads();
     // t_i = Ahat Rhat_i^T on the window
-    for (int w = threadIdx.x; w < g.nwin; w += blockDim.x) {
-      T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
-      const int p = shift_cell(xi, yi, g.win[w].x, g.win[w].y, g.Lpar);
+    for (int w = half; w < g.nwin; w += nhalf) {
+      const int p = shift_cell(xi, yi, g.win[w].x, g.win[w].y, g.Lpar, nrow);
+      T acc = 0;
       if (p >= 0) {
-        for (int e = g.l1_ptr[w]; e < g.l1_ptr[w + 1]; ++e) {
-          const int2 jo = g.l1_pairs[e];
-          const T* blk = Ahat + ((int64_t)jo.y * nrow + p) * 16;
-          T b[16];
-          load_block16(blk, b);
-          const T r0 = rrow[4 * jo.x], r1 = rrow[4 * jo.x + 1];
-          const T r2 = rrow[4 * jo.x + 2], r3 = rrow[4 * jo.x + 3];
-          acc0 += b[0] * r0 + b[1] * r1 + b[2] * r2 + b[3] * r3;
-          acc1 += b[4] * r0 + b[5] * r1 + b[6] * r2 + b[7] * r3;
-          acc2 += b[8] * r0 + b[9] * r1 + b[10] * r2 + b[11] * r3;
-          acc3 += b[12] * r0 + b[13] * r1 + b[14] * r2 + b[15] * r3;
+        const int e0 = g.l1_ptr[w], e1 = g.l1_ptr[w + 1];
+        for (int q = e0; q < e1; ++q) {
+          const int2 jo = g.l1_pairs[q];
+          acc += __ldg(Ahat + ((int64_t)jo.y * nrow + p) * 16 + e) * rrow[4 * jo.x + cb];
         }
       }
-      t[4 * w] = acc0;
-      t[4 * w + 1] = acc1;
-      t[4 * w + 2] = acc2;
-      t[4 * w + 3] = acc3;
+      acc += __shfl_xor_sync(hmask, acc, 1);
+      acc += __shfl_xor_sync(hmask, acc, 2);
+      if (cb == 0) t[4 * w + (e >> 2)] = acc;
     }
     __syncthreads();
     // A_{i, i+S_d} = Rhat_{i+S_d} . t_i
-    for (int d = threadIdx.x; d < g.nout; d += blockDim.x) {
+    for (int d = warp; d < g.nout; d += nwarp) {
+      const int ip = shift_cell(xi, yi, g.out[d].x, g.out[d].y, g.Lpar, nrow);
       T acc = 0;
-      const int ip = shift_cell(xi, yi, g.out[d].x, g.out[d].y, g.Lpar);
       if (ip >= 0 && (pmask[ip] & 15u)) {
-        const T* rrow_ip = Rhat + (int64_t)ip * 4 * g.NB;
-        for (int e = g.l2_ptr[d]; e < g.l2_ptr[d + 1]; ++e) {
-          const int2 jw = g.l2_pairs[e];
-          const T* tw = t + 4 * jw.y;
+        const T* rr = Rhat + (int64_t)ip * 4 * g.NB;
+        const int e1 = g.l2_ptr[d + 1];
+        for (int q = g.l2_ptr[d] + lane; q < e1; q += 32) {
+          const int2 jw = g.l2_pairs[q];
           T rv[4];
-          load_vec4(rrow_ip + 4 * jw.x, rv);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc += rv[c] * tw[c];
+          load_vec4(rr + 4 * jw.x, rv);
+          const T* tw = t + 4 * jw.y;
+          acc += rv[0] * tw[0] + rv[1] * tw[1] + rv[2] * tw[2] + rv[3] * tw[3];
         }
       }
-      Aout[(int64_t)d * nrow + i] = acc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) Aout[(int64_t)d * nrow + i] = acc;
     }
     __syncthreads();
   }
@@ -142,27 +127,33 @@ __global__ void k_cells_to_blocks(const T* __restrict__ Acell, int64_t ncell,
   const int64_t P = t - (int64_t)o * npar;
   int x, y;
   demorton((uint32_t)P, x, y);
-  const int PP = shift_cell(x, y, Ooff[o].x, Ooff[o].y, Lpar);
+  const int PP = shift_cell(x, y, Ooff[o].x, Ooff[o].y, Lpar, npar);
   const int mr = (int)pmask[P] & 15;
   const int mc = PP >= 0 ? (int)pmask[PP] & 15 : 0;
-  double M[16], Tm[16], Qr[16], Qc[16];
-  qmat<double>(mr, Qr);
-  qmat<double>(mc, Qc);
+  // the transform runs in the working precision: float64 arithmetic would
+  // make this memory-bound kernel wait on the float64 pipe in the mixed path
+  T M[16], Tm[16], Qr[16], Qc[16];
+  qmat<T>(mr, Qr);
+  qmat<T>(mc, Qc);
 #pragma unroll
   for (int c = 0; c < 4; ++c)
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
       const int d = map[o * 16 + c * 4 + cc];
-      double v = 0.0;
-      if (PP >= 0 && d >= 0) v = (double)Acell[(int64_t)d * ncell + 4 * P + c];
-      else if (PP >= 0 && d <= -2) v = (double)Acell[(int64_t)(-d - 2) * ncell + 4 * PP + cc];
+      T v = T(0);
+      // only existing cells are read (the last parent of a prefix may have
+      // children beyond the ncell rows of Acell)
+      if (PP >= 0 && ((mr >> c) & 1) && ((mc >> cc) & 1)) {
+        if (d >= 0) v = Acell[(int64_t)d * ncell + 4 * P + c];
+        else if (d <= -2) v = Acell[(int64_t)(-d - 2) * ncell + 4 * PP + cc];
+      }
       M[c * 4 + cc] = v;
     }
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
-      double acc = 0;
+      T acc = 0;
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc += Qr[a * 4 + c] * M[c * 4 + cc];
       Tm[a * 4 + cc] = acc;
@@ -172,10 +163,10 @@ __global__ void k_cells_to_blocks(const T* __restrict__ Acell, int64_t ncell,
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      double acc = 0;
+      T acc = 0;
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) acc += Tm[a * 4 + cc] * Qc[b * 4 + cc];
-      out[a * 4 + b] = (T)acc;
+      out[a * 4 + b] = acc;
     }
 }
 

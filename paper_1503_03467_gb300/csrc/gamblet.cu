@@ -120,6 +120,17 @@ void to_device(Pool& pool, T*& dst, const T* src, int64_t n, cudaStream_t s) {
   if (n > 0) CK(cudaMemcpyAsync(dst, src, sizeof(T) * (size_t)n, cudaMemcpyDefault, s));
 }
 
+// Caller memory as a device pointer: device memory is read in place (the
+// calls that use this finish with a stream synchronisation), host memory is
+// copied into a pool buffer.
+template <typename T>
+const T* as_device(Pool& pool, const T* src, int64_t n, cudaStream_t s) {
+  if (is_device_ptr(src)) return src;
+  T* dst = nullptr;
+  to_device(pool, dst, src, n, s);
+  return dst;
+}
+
 // ---------------------------------------------------------------- offset sets
 using Off = std::pair<int, int>;  // (dx, dy)
 
@@ -172,8 +183,8 @@ struct SymLevel {
 struct LevelDev {
   int k = 0;
   int L = 0;          // 2^k
-  int64_t ncell = 0;  // 4^k
-  int64_t npar = 0;   // 4^(k-1)
+  int64_t ncell = 0;  // stored cells, 4 npar (4^k for a full square)
+  int64_t npar = 0;   // stored level-(k-1) cells (4^(k-1) for a full square)
   std::vector<uint32_t> pmask_h;
   uint32_t* pmask = nullptr;
   int n_active = 0, nJ = 0;
@@ -183,7 +194,7 @@ struct LevelDev {
   std::vector<int2> off_h;
   void* Ahat = nullptr;      // T
   double* Ahat64 = nullptr;  // level q float64 copy (mixed) or alias
-  void* Rhat = nullptr;      // T, rows 4^(k-1)
+  void* Rhat = nullptr;      // T, npar rows
   void* RT = nullptr;        // T, Rhat regrouped by parent (prolongation)
   int* pair_idx = nullptr;
   // exact (dense)
@@ -293,6 +304,7 @@ struct gamblet_ctx {
   cudaStream_t s = nullptr;
   int q = 0;
   int n = 0;           // fine unknowns
+  int nprob = 1;       // independent problems packed in the hierarchy
   bool exact = false;
   bool mixed = false;
   int num_sms = 1;
@@ -438,30 +450,41 @@ OffSet blocks_from_cells(const OffSet& S, const OffSet& Sp, int km1, std::vector
 }
 
 // ------------------------------------------------------------ hierarchy
+// Level sizes follow the stored Morton prefix: npar_q = ceil((largest cell
+// code + 1) / 4), npar_(k-1) = ceil(npar_k / 4), and level 1 always has the
+// single root parent.  One square problem gives npar_k = 4^(k-1).
 void build_hierarchy(gamblet_ctx* h, const int32_t* cells_user) {
   const int q = h->q;
   cudaStream_t s = h->s;
   Pool& P = h->pool;
+  const int32_t* cells = as_device(P, cells_user, 2 * (int64_t)h->n, s);
+  h->morton_of = P.alloc<int32_t>(h->n);
+  int* flag = P.zeros<int>(4, s);
+  launch_cells_to_morton(cells, h->n, q, h->morton_of, flag, s);
+  CK(cudaGetLastError());
+  int flag_h[4];
+  CK(cudaMemcpyAsync(flag_h, flag, sizeof(flag_h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (flag_h[0] == 2) fail(GAMBLET_ERR_INVALID_ARG, "a cell lies outside [0, 2^q)");
   h->lv.assign(q + 1, LevelDev());
-  for (int k = 1; k <= q; ++k) {
+  // the dense exact transform keeps the full square
+  int64_t npar = h->exact ? ((int64_t)1 << (2 * (q - 1))) : ((int64_t)flag_h[1] + 1 + 3) / 4;
+  for (int k = q; k >= 1; --k) {
     LevelDev& L = h->lv[k];
     L.k = k;
     L.L = 1 << k;
-    L.ncell = (int64_t)1 << (2 * k);
-    L.npar = (int64_t)1 << (2 * (k - 1));
+    L.npar = k == 1 ? 1 : npar;
+    L.ncell = 4 * L.npar;
     L.pmask = P.zeros<uint32_t>(L.npar, s);
+    npar = (npar + 3) / 4;
   }
-  int32_t* cells = nullptr;
-  to_device(P, cells, cells_user, 2 * (int64_t)h->n, s);
-  h->morton_of = P.alloc<int32_t>(h->n);
   h->unknown_of = P.alloc<int32_t>(h->lv[q].ncell);
   CK(cudaMemsetAsync(h->unknown_of, 0xff, sizeof(int32_t) * h->lv[q].ncell, s));
-  int* flag = P.zeros<int>(4, s);
-  launch_cells_to_morton(cells, h->n, q, h->morton_of, h->unknown_of, h->lv[q].pmask, flag, s);
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  launch_scatter_cells(h->morton_of, h->n, h->unknown_of, h->lv[q].pmask, flag, s);
   for (int k = q; k >= 2; --k)
-    launch_coarsen_masks(h->lv[k].pmask, h->lv[k].npar, h->lv[k - 1].pmask, s);
+    launch_coarsen_masks(h->lv[k].pmask, h->lv[k].npar, h->lv[k - 1].pmask, h->lv[k - 1].npar, s);
   CK(cudaGetLastError());
-  int flag_h[4];
   CK(cudaMemcpyAsync(flag_h, flag, sizeof(flag_h), cudaMemcpyDeviceToHost, s));
   for (int k = 1; k <= q; ++k) {
     h->lv[k].pmask_h.resize(h->lv[k].npar);
@@ -472,7 +495,6 @@ void build_hierarchy(gamblet_ctx* h, const int32_t* cells_user) {
   CK(cudaMemcpyAsync(h->morton_of_h.data(), h->morton_of, sizeof(int32_t) * h->n,
                      cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (flag_h[0] == 2) fail(GAMBLET_ERR_INVALID_ARG, "a cell lies outside [0, 2^q)");
   if (flag_h[0] == 1) fail(GAMBLET_ERR_INVALID_ARG, "two unknowns share a level-q cell");
   for (int k = 1; k <= q; ++k) {
     LevelDev& L = h->lv[k];
@@ -492,18 +514,15 @@ void import_fine(gamblet_ctx* h, const gamblet_csr* A) {
   cudaStream_t s = h->s;
   Pool& P = h->pool;
   const int n = h->n;
-  int32_t* rowptr = nullptr;
-  int32_t* colind = nullptr;
-  double* val = nullptr;
-  to_device(P, rowptr, A->rowptr, (int64_t)n + 1, s);
+  const int32_t* rowptr = as_device(P, A->rowptr, (int64_t)n + 1, s);
   int32_t rp_last[2];
   CK(cudaMemcpyAsync(rp_last, rowptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(rp_last + 1, rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (rp_last[0] != 0 || (int64_t)rp_last[1] != A->nnz)
     fail(GAMBLET_ERR_INVALID_ARG, "rowptr[0] must be 0 and rowptr[n] must equal nnz");
-  to_device(P, colind, A->colind, A->nnz, s);
-  to_device(P, val, A->val, A->nnz, s);
+  const int32_t* colind = as_device(P, A->colind, A->nnz, s);
+  const double* val = as_device(P, A->val, A->nnz, s);
   int* ext = P.zeros<int>(4, s);
   launch_csr_offset_extent(n, rowptr, colind, h->morton_of, ext, ext + 2, s);
   CK(cudaGetLastError());
@@ -544,13 +563,16 @@ struct PlanLevel {
 };
 struct Plan {
   std::vector<PlanLevel> lv;  // index k
+  std::string key;            // geometry key of the process-wide cache
 };
 
 int half_code(const OffSet& Sp, int dx, int dy);
 OffSet blocks_from_cells(const OffSet& S, const OffSet& Sp, int km1, std::vector<int>& map);
 
-std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N) {
+std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
+                                       const std::string& key) {
   auto plan = std::make_shared<Plan>();
+  plan->key = key;
   plan->lv.resize(q + 1);
   const int NB = N.size();
   OffSet O = Oq;
@@ -604,10 +626,57 @@ std::shared_ptr<const Plan> cached_plan(int q, double rho, int rule, const OffSe
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
   }
-  auto plan = build_plan(q, Oq, N);
+  auto plan = build_plan(q, Oq, N, key);
   std::lock_guard<std::mutex> lock(mu);
   cache[key] = plan;
   return plan;
+}
+
+// ------------------------------------------------------------ autotuner
+// Launch shapes chosen by timing the candidates on the device, once per
+// geometry key, level and working precision in a process, then reused by
+// every later setup of that geometry (the results depend on the shape only
+// through summation order).  Levels smaller than kTuneMinParents keep the
+// fixed rule: their kernels are too short for the choice to matter.
+constexpr int64_t kTuneMinParents = 16384;
+constexpr int64_t kTuneSample = 4096;  // a 64 x 64 Morton block of coarse cells
+
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+
+bool tune_lookup(const std::string& key, int* v) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  *v = it->second;
+  return true;
+}
+void tune_store(const std::string& key, int v) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = v;
+}
+
+// Best of two timed runs after one warm-up run, CUDA events on stream s.
+template <typename F>
+float time_on_stream(cudaStream_t s, F&& launch) {
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  launch();
+  float best = 1e30f;
+  for (int r = 0; r < 2; ++r) {
+    CK(cudaEventRecord(a, s));
+    launch();
+    CK(cudaEventRecord(b, s));
+    CK(cudaEventSynchronize(b));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  CK(cudaGetLastError());
+  return best;
 }
 
 // Algorithmic flops of the level-k patch solves: for a patch with n active
@@ -623,7 +692,7 @@ double patch_flops(gamblet_ctx* h, int k) {
     demorton((uint32_t)i, x, y);
     double na = 0;
     for (const int2& o : h->N.v) {
-      const int p = shift_cell(x, y, o.x, o.y, Lpar);
+      const int p = shift_cell(x, y, o.x, o.y, Lpar, L.npar);
       if (p < 0) continue;
       const int m = __builtin_popcount(L.pmask_h[p] & 15u);
       na += m > 0 ? m - 1 : 0;
@@ -631,6 +700,38 @@ double patch_flops(gamblet_ctx* h, int k) {
     f += 2.0 * (na * na * na / 6.0 + na * na / 2.0) + 2.0 * 2.0 * na * na / 2.0;
   }
   return f;
+}
+
+// Lanes per neighbour parent of the patch CG at level k: candidates 1, 2, 4
+// timed on a Morton block of kTuneSample coarse cells in the middle of the
+// level (its Rhat rows are overwritten by the full launch that follows).
+template <typename T>
+int tuned_patch_spp(gamblet_ctx* h, int k, const PatchPcgGeom& gp, T* Rhat) {
+  if (!h->opts.autotune || gp.npatch < kTuneMinParents) return gp.spp;
+  const std::string key = h->plan->key + "/patch_pcg/" + std::to_string(k) + "/" +
+                          std::to_string(sizeof(T)) + "/" + std::to_string(h->patch_tol);
+  int best_spp = gp.spp;
+  if (tune_lookup(key, &best_spp)) return best_spp;
+  cudaStream_t s = h->s;
+  int* stats = h->pool.zeros<int>(4, s);
+  PatchPcgGeom gt = gp;
+  gt.i_begin = (gp.npatch / 2 / kTuneSample) * kTuneSample;
+  gt.i_end = std::min(gt.i_begin + kTuneSample, gp.npatch);
+  float best = 1e30f;
+  for (int spp : {1, 2, 4}) {
+    if (gp.NB * spp > 256) continue;
+    gt.spp = spp;
+    const float ms = time_on_stream(s, [&] {
+      launch_patch_pcg<T>((const T*)h->lv[k].Ahat, h->lv[k].pmask, gt, Rhat, h->patch_tol, 200,
+                          stats, h->num_sms, s);
+    });
+    if (ms < best) {
+      best = ms;
+      best_spp = spp;
+    }
+  }
+  tune_store(key, best_spp);
+  return best_spp;
 }
 
 // ------------------------------------------------------------ localized setup
@@ -680,9 +781,10 @@ void setup_local(gamblet_ctx* h) {
     } else {
       PatchPcgGeom gp{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar, (int)pl.half.size(),
                       P.upload(pl.half, s), P.upload(pl.adj_ptr, s), P.upload(pl.adj, s),
-                      P.upload(pl.diag_h, s), pl.spp};
+                      P.upload(pl.diag_h, s), pl.spp, 0, L.npar};
       if (patch_pcg_smem_bytes<T>(gp) > 227 * 1024)
         fail(GAMBLET_ERR_UNSUPPORTED, "patch blocks exceed shared memory; lower rho");
+      gp.spp = tuned_patch_spp<T>(h, k, gp, Rhat);
       // flops are added after setup from the measured iteration counts
       int tok = h->prof.begin("patch_pcg_k" + std::to_string(k), pbytes, 0.0, s);
       launch_patch_pcg<T>((const T*)L.Ahat, L.pmask, gp, Rhat, h->patch_tol, 200,
@@ -736,7 +838,7 @@ void setup_local(gamblet_ctx* h) {
     } else {
       h->l1map = P.upload(pl.map_next, s);
       h->A1L = P.alloc<double>(16);
-      launch_level1_factor<T>(Acell, h->l1map, h->A1L, h->status, s);
+      launch_level1_factor<T>(Acell, (int)L.npar, h->l1map, h->A1L, h->status, s);
       CK(cudaGetLastError());
       // keep the level-1 cell stencil for the getter
       h->lv[1].Ahat = Acell;
@@ -821,6 +923,44 @@ void setup_exact(gamblet_ctx* h) {
   }
 }
 
+// Threads per parent of the level-CG SpMV at level k: 1 (16 x 16 tiles) or
+// 4 (8 x 8 tiles), timed on the whole level with the CG direction vector
+// (still zero here; the kernel has no data-dependent branches).
+template <typename T>
+int tuned_cg_spp(gamblet_ctx* h, int k, const CgLevel& c) {
+  if (!h->opts.autotune || c.npar < kTuneMinParents) return c.spp;
+  const std::string key = h->plan->key + "/cg_spmv/" + std::to_string(k) + "/" +
+                          std::to_string(sizeof(T));
+  int best_spp = c.spp;
+  if (tune_lookup(key, &best_spp)) return best_spp;
+  cudaStream_t s = h->s;
+  CgScalars sc{};
+  sc.active = 1;
+  CgScalars* sc_d = h->pool.upload(std::vector<CgScalars>{sc}, s);
+  float best = 1e30f;
+  for (int spp : {1, 4}) {
+    CgLevel c1 = c;
+    c1.spp = spp;
+    c1.block_begin = 0;
+    c1.spmv_begin = 0;
+    const int tmax = spp == 4 ? 8 : 16;
+    const int ts = std::min(c1.Lpar, tmax) + 2 * c1.R;
+    if (cg_spmv_smem_bytes(ts, sizeof(T)) > 227 * 1024) continue;
+    prepare_cg_spmv<T>(ts);
+    CgLevel* lv_d = h->pool.upload(std::vector<CgLevel>{c1}, s);
+    const int blocks = (int)((c1.npar + tmax * tmax - 1) / (tmax * tmax));
+    const float ms = time_on_stream(s, [&] {
+      launch_cg_spmv<T>(lv_d, 1, blocks, sc_d, ts, s);
+    });
+    if (ms < best) {
+      best = ms;
+      best_spp = spp;
+    }
+  }
+  tune_store(key, best_spp);
+  return best_spp;
+}
+
 // ------------------------------------------------------------ solve buffers
 template <typename T>
 void alloc_solve(gamblet_ctx* h) {
@@ -879,8 +1019,10 @@ void alloc_solve(gamblet_ctx* h) {
       c.b = L.ghat;
       c.block_begin = blocks;
       blocks += (int)((L.npar + 255) / 256);
-      // wide stencils: four threads per parent over 8 x 8 tiles (more loads in flight)
+      // wide stencils: four threads per parent over 8 x 8 tiles (more loads in
+      // flight); the autotuner may overrule the rule on large levels
       c.spp = L.noff > 32 ? 4 : 1;
+      c.spp = tuned_cg_spp<T>(h, k, c);
       const int tmax = c.spp == 4 ? 8 : 16;
       c.spmv_begin = sblocks;
       sblocks += (int)((L.npar + tmax * tmax - 1) / (tmax * tmax));
@@ -1243,32 +1385,12 @@ gamblet_status set_error(const GbError& e) {
 
 }  // namespace
 
-// ================================================================= C ABI
-extern "C" {
+namespace {
 
-void gamblet_default_opts(gamblet_opts* o) {
-  if (!o) return;
-  std::memset(o, 0, sizeof(*o));
-  o->rho = 3.0;
-  o->nbr_rule = 0;
-  o->precision = GAMBLET_FP64;
-  o->level_tol = 1e-8;
-  o->level_max_iter = 1000;
-  o->refine_tol = 1e-13;
-  o->refine_max_iter = 50;
-  o->patch_tol = 0.0;
-  o->use_graph = 1;
-  o->profile = 0;
-  o->stream = nullptr;
-}
-
-gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cells,
-                             const gamblet_opts* opts, gamblet_handle* out) {
-  if (!out) {
-    g_last_error = "out is NULL";
-    return GAMBLET_ERR_INVALID_ARG;
-  }
-  *out = nullptr;
+// gamblet_setup without the status conversion: throws GbError, frees the
+// handle on failure.
+gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
+                        const gamblet_opts* opts) {
   gamblet_ctx* h = nullptr;
   try {
     if (!A || !cells) fail(GAMBLET_ERR_INVALID_ARG, "A and cells must be non-NULL");
@@ -1287,7 +1409,7 @@ gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cel
     h->n = A->n;
     h->exact = !(h->opts.rho > 0);
     h->mixed = h->opts.precision == GAMBLET_MIXED && !h->exact;
-    h->patch_tol = h->opts.patch_tol != 0 ? h->opts.patch_tol : (h->mixed ? 1e-6 : 1e-12);
+    h->patch_tol = h->opts.patch_tol != 0 ? h->opts.patch_tol : (h->mixed ? 1e-3 : 1e-12);
     if (h->opts.precision != GAMBLET_FP64 && h->opts.precision != GAMBLET_MIXED)
       fail(GAMBLET_ERR_INVALID_ARG, "unknown precision");
     if (h->opts.nbr_rule != 0 && h->opts.nbr_rule != 1)
@@ -1357,13 +1479,165 @@ gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cel
     }
     h->prof.resolve();
     check_status(h, "setup");
-    *out = h;
+    return h;
+  } catch (...) {
+    if (h) gamblet_destroy(h);
+    throw;
+  }
+}
+
+
+// Independent problems packed into one hierarchy.  Problem p (q_p levels,
+// cells in its own 2^q_p lattice) is given the aligned subtree that starts
+// at Morton index base_p of a 2^Q lattice, largest problems first, so the
+// subtrees are disjoint and their union is a Morton prefix; the fine
+// operator is block diagonal and unknowns are numbered problem by problem.
+gamblet_ctx* setup_batched_impl(int32_t nprob, const gamblet_csr* A, const int32_t* q,
+                                const int32_t* const* cells, const gamblet_opts* opts,
+                                int32_t* offsets) {
+  if (nprob < 1 || !A || !q || !cells) fail(GAMBLET_ERR_INVALID_ARG, "nprob >= 1 and non-NULL A, q, cells required");
+  int qmax = 0;
+  for (int p = 0; p < nprob; ++p) {
+    if (q[p] < 1 || q[p] > 15) fail(GAMBLET_ERR_INVALID_ARG, "q[p] must be in [1, 15]");
+    if (!cells[p] || A[p].n < 1 || A[p].nnz < 1 || !A[p].rowptr || !A[p].colind || !A[p].val)
+      fail(GAMBLET_ERR_INVALID_ARG, "empty or incomplete CSR of problem " + std::to_string(p));
+    if ((int64_t)A[p].n > ((int64_t)1 << (2 * q[p])))
+      fail(GAMBLET_ERR_INVALID_ARG, "more unknowns than level-q cells in problem " + std::to_string(p));
+    qmax = std::max(qmax, (int)q[p]);
+  }
+  std::vector<int> order(nprob);
+  for (int p = 0; p < nprob; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return q[a] > q[b]; });
+  std::vector<int64_t> base(nprob);
+  int64_t total = 0;
+  for (int p : order) {
+    base[p] = total;  // a multiple of 4^q_p: every earlier subtree is at least as large
+    total += (int64_t)1 << (2 * q[p]);
+  }
+  int Q = std::max(qmax, 2);
+  while (((int64_t)1 << (2 * Q)) < total) ++Q;
+  if (Q > 15) fail(GAMBLET_ERR_UNSUPPORTED, "the problems do not fit a 2^15 x 2^15 lattice");
+  std::vector<BatchSeg> seg(nprob);
+  int64_t N = 0, NNZ = 0;
+  for (int p = 0; p < nprob; ++p) {
+    int x0, y0;
+    demorton((uint32_t)base[p], x0, y0);
+    seg[p] = BatchSeg{N, NNZ, A[p].n, q[p], x0, y0};
+    N += A[p].n;
+    NNZ += A[p].nnz;
+  }
+  if (N >= ((int64_t)1 << 31) || NNZ >= ((int64_t)1 << 31))
+    fail(GAMBLET_ERR_UNSUPPORTED, "combined CSR exceeds int32 indexing");
+  gamblet_opts o;
+  if (opts) o = *opts;
+  else gamblet_default_opts(&o);
+  cudaStream_t s = (cudaStream_t)o.stream;
+  Pool tmp;
+  tmp.s = s;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  int32_t* R = tmp.alloc<int32_t>(N + 1);
+  int32_t* C = tmp.alloc<int32_t>(NNZ);
+  double* V = tmp.alloc<double>(NNZ);
+  int32_t* X = tmp.alloc<int32_t>(2 * N);
+  std::vector<int32_t> ends(2 * (size_t)nprob);
+  for (int p = 0; p < nprob; ++p) {
+    const BatchSeg& b = seg[p];
+    CK(cudaMemcpyAsync(R + b.row0, A[p].rowptr, sizeof(int32_t) * b.n, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(&ends[2 * p], A[p].rowptr, sizeof(int32_t), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(&ends[2 * p + 1], A[p].rowptr + b.n, sizeof(int32_t), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(C + b.nnz0, A[p].colind, sizeof(int32_t) * A[p].nnz, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(V + b.nnz0, A[p].val, sizeof(double) * A[p].nnz, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(X + 2 * b.row0, cells[p], sizeof(int32_t) * 2 * b.n, cudaMemcpyDefault, s));
+  }
+  const int32_t nnz_total = (int32_t)NNZ;
+  CK(cudaMemcpyAsync(R + N, &nnz_total, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  BatchSeg* seg_d = tmp.upload(seg, s);
+  int* flag = tmp.zeros<int>(1, s);
+  launch_batch_fixup(nprob, seg_d, N, NNZ, R, C, X, flag, s);
+  CK(cudaGetLastError());
+  int flag_h = 0;
+  CK(cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int p = 0; p < nprob; ++p)
+    if (ends[2 * p] != 0 || (int64_t)ends[2 * p + 1] != A[p].nnz)
+      fail(GAMBLET_ERR_INVALID_ARG, "problem " + std::to_string(p) +
+                                        ": rowptr[0] must be 0 and rowptr[n] must equal nnz");
+  if (flag_h == 1) fail(GAMBLET_ERR_INVALID_ARG, "a column index lies outside its problem");
+  if (flag_h == 2) fail(GAMBLET_ERR_INVALID_ARG, "a cell lies outside its problem's 2^q lattice");
+  const gamblet_csr Ac{(int32_t)N, NNZ, R, C, V};
+  gamblet_ctx* h = setup_impl(&Ac, Q, X, &o);
+  CK(cudaEventRecord(e1, s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->setup_ms = ms;  // packing included
+  h->nprob = nprob;
+  if (offsets) {
+    for (int p = 0; p < nprob; ++p) offsets[p] = (int32_t)seg[p].row0;
+    offsets[nprob] = (int32_t)N;
+  }
+  return h;
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+extern "C" {
+
+void gamblet_default_opts(gamblet_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->rho = 3.0;
+  o->nbr_rule = 0;
+  o->precision = GAMBLET_FP64;
+  o->level_tol = 1e-8;
+  o->level_max_iter = 1000;
+  o->refine_tol = 1e-13;
+  o->refine_max_iter = 50;
+  o->patch_tol = 0.0;
+  o->use_graph = 1;
+  o->profile = 0;
+  o->autotune = 1;
+  o->stream = nullptr;
+}
+
+gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cells,
+                             const gamblet_opts* opts, gamblet_handle* out) {
+  if (!out) {
+    g_last_error = "out is NULL";
+    return GAMBLET_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    *out = setup_impl(A, q, cells, opts);
     return GAMBLET_OK;
   } catch (const GbError& e) {
-    if (h) gamblet_destroy(h);
     return set_error(e);
   } catch (const std::exception& e) {
-    if (h) gamblet_destroy(h);
+    g_last_error = e.what();
+    return GAMBLET_ERR_INVALID_ARG;
+  }
+}
+
+gamblet_status gamblet_setup_batched(int32_t nprob, const gamblet_csr* A, const int32_t* q,
+                                     const int32_t* const* cells, const gamblet_opts* opts,
+                                     gamblet_handle* out, int32_t* offsets) {
+  if (!out) {
+    g_last_error = "out is NULL";
+    return GAMBLET_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    *out = setup_batched_impl(nprob, A, q, cells, opts, offsets);
+    return GAMBLET_OK;
+  } catch (const GbError& e) {
+    return set_error(e);
+  } catch (const std::exception& e) {
     g_last_error = e.what();
     return GAMBLET_ERR_INVALID_ARG;
   }
@@ -1493,6 +1767,7 @@ std::vector<int32_t> canon_map(gamblet_ctx* h, int k) {
   for (int y = 0; y < L.L; ++y)
     for (int x = 0; x < L.L; ++x) {
       const uint32_t s = morton((uint32_t)x, (uint32_t)y);
+      if ((int64_t)(s >> 2) >= L.npar) continue;  // beyond the stored prefix
       if ((L.pmask_h[s >> 2] >> (s & 3)) & 1u) cm[s] = idx++;
     }
   return cm;
@@ -1566,7 +1841,7 @@ void level_blocks(gamblet_ctx* h, int k,
     for (int64_t p = 0; p < L.npar; ++p) {
       int x, y;
       demorton((uint32_t)p, x, y);
-      const int pp = shift_cell(x, y, L.off_h[o].x, L.off_h[o].y, Lpar);
+      const int pp = shift_cell(x, y, L.off_h[o].x, L.off_h[o].y, Lpar, L.npar);
       if (pp < 0) continue;
       f(p, pp, &V[((int64_t)o * L.npar + p) * 16]);
     }
@@ -1581,16 +1856,18 @@ Coo get_A(gamblet_ctx* h, int k) {
     if (h->exact) {
       M = download<double>(h->A1, 16, s);
     } else {
+      // the level-1 cell stencil has one column per existing level-1 cell
       const LevelDev& L1 = h->lv[1];
-      std::vector<double> C = h->mixed ? download<float>(L1.Ahat, (int64_t)L1.noff * 4, s)
-                                       : download<double>(L1.Ahat, (int64_t)L1.noff * 4, s);
+      const int64_t nr = h->lv[2].npar;
+      std::vector<double> C = h->mixed ? download<float>(L1.Ahat, (int64_t)L1.noff * nr, s)
+                                       : download<double>(L1.Ahat, (int64_t)L1.noff * nr, s);
       OffSet Sp;
       for (const int2& d : L1.off_h) Sp.add(d.x, d.y);
-      for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) {
+      for (int i = 0; i < nr; ++i)
+        for (int j = 0; j < nr; ++j) {
           const int code = half_code(Sp, (j & 1) - (i & 1), (j >> 1) - (i >> 1));
-          if (code >= 0) M[i * 4 + j] = C[(int64_t)code * 4 + i];
-          else if (code <= -2) M[i * 4 + j] = C[(int64_t)(-code - 2) * 4 + j];
+          if (code >= 0) M[i * 4 + j] = C[(int64_t)code * nr + i];
+          else if (code <= -2) M[i * 4 + j] = C[(int64_t)(-code - 2) * nr + j];
         }
     }
     for (int i = 0; i < 4; ++i)
@@ -1661,7 +1938,7 @@ Coo get_R(gamblet_ctx* h, int k) {
     int x, y;
     demorton((uint32_t)i, x, y);
     for (int j = 0; j < NB; ++j) {
-      const int p = shift_cell(x, y, h->N.v[j].x, h->N.v[j].y, Lpar);
+      const int p = shift_cell(x, y, h->N.v[j].x, h->N.v[j].y, Lpar, L.npar);
       if (p < 0) continue;
       double Q[16];
       qmat<double>((int)(L.pmask_h[p] & 15u), Q);

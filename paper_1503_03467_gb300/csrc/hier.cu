@@ -13,50 +13,122 @@
 namespace gb {
 
 // ---------------------------------------------------------------- hierarchy
+// Morton code of every unknown's level-q cell; flag[0] = 2 for a cell
+// outside the lattice, flag[1] = largest code (sizes the stored prefix).
 __global__ void k_cells_to_morton(const int32_t* __restrict__ cells, int n, int q,
-                                  int32_t* morton_of, int32_t* unknown_of,
-                                  uint32_t* pmask_q, int* dup_flag) {
+                                  int32_t* morton_of, int* flag) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int x = cells[2 * i], y = cells[2 * i + 1];
   int L = 1 << q;
   if ((unsigned)x >= (unsigned)L || (unsigned)y >= (unsigned)L) {
-    atomicExch(dup_flag, 2);
+    atomicExch(flag, 2);
     morton_of[i] = 0;
     return;
   }
   uint32_t s = morton((uint32_t)x, (uint32_t)y);
   morton_of[i] = (int32_t)s;
+  atomicMax(flag + 1, (int)s);
+}
+
+// unknown_of (cell -> unknown) and the level-q child masks; flag[0] = 1 when
+// two unknowns share a cell.
+__global__ void k_scatter_cells(const int32_t* __restrict__ morton_of, int n,
+                                int32_t* unknown_of, uint32_t* pmask_q, int* flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t s = (uint32_t)morton_of[i];
   int old = atomicExch(&unknown_of[s], i);
-  if (old != -1) atomicExch(dup_flag, 1);
+  if (old != -1) atomicExch(flag, 1);
   atomicOr(&pmask_q[s >> 2], 1u << (s & 3));
 }
 
-void launch_cells_to_morton(const int32_t* cells, int n, int q, int32_t* morton_of,
-                            int32_t* unknown_of, uint32_t* pmask_q, int* dup_flag,
+void launch_cells_to_morton(const int32_t* cells, int n, int q, int32_t* morton_of, int* flag,
                             cudaStream_t s) {
   if (n <= 0) return;
-  { count_launch(); k_cells_to_morton<<<(n + 255) / 256, 256, 0, s>>>(cells, n, q, morton_of, unknown_of,
-                                                    pmask_q, dup_flag); }
+  { count_launch(); k_cells_to_morton<<<(n + 255) / 256, 256, 0, s>>>(cells, n, q, morton_of, flag); }
+}
+void launch_scatter_cells(const int32_t* morton_of, int n, int32_t* unknown_of,
+                          uint32_t* pmask_q, int* flag, cudaStream_t s) {
+  if (n <= 0) return;
+  { count_launch(); k_scatter_cells<<<(n + 255) / 256, 256, 0, s>>>(morton_of, n, unknown_of, pmask_q, flag); }
 }
 
-// Parent P of level k-1 has child c active iff level-k parent 4P + c has
-// any active child.
-__global__ void k_coarsen_masks(const uint32_t* __restrict__ pmask_k, int64_t npar_km1,
-                                uint32_t* pmask_km1) {
+// Parent P of level k-1 has child c active iff level-k parent 4P + c exists
+// (4P + c < npar_k) and has any active child.
+__global__ void k_coarsen_masks(const uint32_t* __restrict__ pmask_k, int64_t npar_k,
+                                int64_t npar_km1, uint32_t* pmask_km1) {
   int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (P >= npar_km1) return;
   uint32_t m = 0;
   for (int c = 0; c < 4; ++c)
-    if (pmask_k[4 * P + c]) m |= 1u << c;
+    if (4 * P + c < npar_k && pmask_k[4 * P + c]) m |= 1u << c;
   pmask_km1[P] = m;
 }
 
 void launch_coarsen_masks(const uint32_t* pmask_k, int64_t npar_k, uint32_t* pmask_km1,
-                          cudaStream_t s) {
-  int64_t n = npar_k / 4;
-  if (n <= 0) return;
-  { count_launch(); k_coarsen_masks<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pmask_k, n, pmask_km1); }
+                          int64_t npar_km1, cudaStream_t s) {
+  if (npar_km1 <= 0) return;
+  { count_launch(); k_coarsen_masks<<<(unsigned)((npar_km1 + 255) / 256), 256, 0, s>>>(pmask_k, npar_k, npar_km1, pmask_km1); }
+}
+
+// ---------------------------------------------------------------- batched problems
+// Problem owning combined row i (or entry t): the last segment starting at
+// or before it (segments are in row order).
+__device__ __forceinline__ int find_seg_row(const BatchSeg* seg, int nprob, int64_t i) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (seg[mid].row0 <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int find_seg_nnz(const BatchSeg* seg, int nprob, int64_t t) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (seg[mid].nnz0 <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_batch_rows(int nprob, const BatchSeg* __restrict__ seg, int64_t n,
+                             int32_t* rowptr, int32_t* cells, int* flag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const BatchSeg b = seg[find_seg_row(seg, nprob, i)];
+  rowptr[i] += (int32_t)b.nnz0;
+  const int x = cells[2 * i], y = cells[2 * i + 1], L = 1 << b.q;
+  if ((unsigned)x >= (unsigned)L || (unsigned)y >= (unsigned)L) {
+    atomicExch(flag, 2);
+    cells[2 * i] = b.x0;  // any cell of the problem; the setup fails on the flag
+    cells[2 * i + 1] = b.y0;
+    return;
+  }
+  cells[2 * i] = x + b.x0;
+  cells[2 * i + 1] = y + b.y0;
+}
+
+__global__ void k_batch_cols(int nprob, const BatchSeg* __restrict__ seg, int64_t nnz,
+                             int32_t* colind, int* flag) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nnz) return;
+  const BatchSeg b = seg[find_seg_nnz(seg, nprob, t)];
+  const int c = colind[t];
+  if ((unsigned)c >= (unsigned)b.n) {
+    atomicExch(flag, 1);
+    colind[t] = (int32_t)b.row0;
+    return;
+  }
+  colind[t] = c + (int32_t)b.row0;
+}
+
+void launch_batch_fixup(int nprob, const BatchSeg* seg, int64_t n, int64_t nnz, int32_t* rowptr,
+                        int32_t* colind, int32_t* cells, int* flag, cudaStream_t s) {
+  if (n > 0) { count_launch(); k_batch_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nprob, seg, n, rowptr, cells, flag); }
+  if (nnz > 0) { count_launch(); k_batch_cols<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(nprob, seg, nnz, colind, flag); }
 }
 
 // ---------------------------------------------------------------- fine operator
@@ -136,7 +208,7 @@ __global__ void k_transform_blocks(double* blk, const int2* __restrict__ off, in
   double* B = blk + t * 16;
   int x, y;
   demorton((uint32_t)p, x, y);
-  int pp = shift_cell(x, y, off[o].x, off[o].y, Lpar);
+  int pp = shift_cell(x, y, off[o].x, off[o].y, Lpar, npar);
   int mr = (int)pmask[p] & 15;
   int mc = pp >= 0 ? (int)pmask[pp] & 15 : 0;
   double M[16], Tm[16], Qr[16], Qc[16];

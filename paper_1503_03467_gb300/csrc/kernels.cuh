@@ -9,16 +9,31 @@
 namespace gb {
 
 // ---------------------------------------------------------------- hierarchy
-// cells (n x 2, device) -> Morton index of every fine unknown, inverse map
-// (Morton -> unknown or -1), child masks of the level-q parents.  dup_flag
-// is set when two unknowns share a cell or a cell lies outside [0, 2^q).
-void launch_cells_to_morton(const int32_t* cells, int n, int q, int32_t* morton_of,
-                            int32_t* unknown_of, uint32_t* pmask_q, int* dup_flag,
+// cells (n x 2, device) -> Morton index of every fine unknown; flag[0] = 2
+// when a cell lies outside [0, 2^q), flag[1] = largest Morton index.
+void launch_cells_to_morton(const int32_t* cells, int n, int q, int32_t* morton_of, int* flag,
                             cudaStream_t s);
-// Child masks of level k-1 parents from the masks of level k parents:
-// parent p at level k is active iff pmask_k[p] != 0.
+// Inverse map (Morton -> unknown or -1) and child masks of the level-q
+// parents; flag[0] = 1 when two unknowns share a cell.
+void launch_scatter_cells(const int32_t* morton_of, int n, int32_t* unknown_of,
+                          uint32_t* pmask_q, int* flag, cudaStream_t s);
+// One problem of a batched setup: its unknowns start at row0 and its
+// stored entries at nnz0 of the combined CSR; its 2^q lattice is the
+// subtree with lower-left cell (x0, y0) of the combined lattice.
+struct BatchSeg {
+  int64_t row0, nnz0;
+  int32_t n, q;
+  int32_t x0, y0;
+};
+// In place on the concatenated arrays: rowptr += nnz0, colind += row0,
+// cells += (x0, y0) per problem; flag = 1 for a column index outside its
+// problem, 2 for a cell outside its problem's lattice.
+void launch_batch_fixup(int nprob, const BatchSeg* seg, int64_t n, int64_t nnz, int32_t* rowptr,
+                        int32_t* colind, int32_t* cells, int* flag, cudaStream_t s);
+// Child masks of the npar_km1 level-(k-1) parents from the masks of the
+// npar_k level-k parents: parent p at level k is active iff pmask_k[p] != 0.
 void launch_coarsen_masks(const uint32_t* pmask_k, int64_t npar_k, uint32_t* pmask_km1,
-                          cudaStream_t s);
+                          int64_t npar_km1, cudaStream_t s);
 
 // ---------------------------------------------------------------- fine operator
 // Largest |parent offset| in x and y over the stored entries (atomicMax).
@@ -58,7 +73,7 @@ struct PatchGeom {
   const int2* nbr;     // N_j
   const int* pair_idx; // NB x NB: index in O_k of N_b - N_a, or -1
   int Lpar;            // side of the level-(k-1) lattice
-  int64_t npatch;      // 4^(k-1)
+  int64_t npatch;      // stored level-(k-1) cells (4^(k-1) for a full square)
 };
 // Localized patch solves of Definition defb for every coarse cell of level
 // k-1; writes Rhat rows (SoA [NB * 4][npatch]).  status receives DEV_NOT_SPD
@@ -84,6 +99,7 @@ struct PatchPcgGeom {
   const int4* adj;      // (stored block, other neighbour, transposed, 0)
   const int* diag_h;    // NB: stored block of (j, j)
   int spp;              // threads per neighbour parent: 1, 2 or 4
+  int64_t i_begin, i_end;  // coarse cells solved: [i_begin, i_end) (all: 0, npatch)
 };
 template <typename T>
 void launch_patch_pcg(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g, T* Rhat, double tol,
@@ -117,10 +133,11 @@ template <typename T>
 void launch_cells_to_blocks(const T* Acell, int64_t ncell, const int* map, int nO,
                             const int2* Ooff, int Lpar, int64_t npar, const uint32_t* pmask,
                             T* blk, cudaStream_t s);
-// A^(1) (4 x 4) from the level-1 cell stencil (map[4 i + j] = index in S of
-// cell_j - cell_i, or -1), factored in place (lower Cholesky, float64).
+// A^(1) (4 x 4) from the level-1 cell stencil of the nrow <= 4 existing
+// level-1 cells (map[4 i + j] = index in S of cell_j - cell_i, or -1),
+// factored in place (lower Cholesky, float64; absent cells get unit rows).
 template <typename T>
-void launch_level1_factor(const T* Acell, const int* map, double* L1, int* status,
+void launch_level1_factor(const T* Acell, int nrow, const int* map, double* L1, int* status,
                           cudaStream_t s);
 // U = A^(1)^-1 g from the factor.
 template <typename T>

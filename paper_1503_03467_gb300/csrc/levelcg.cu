@@ -131,9 +131,11 @@ __global__ void __launch_bounds__(256) k_cg_spmv(const CgLevel* __restrict__ lv,
     T v0 = 0, v1 = 0, v2 = 0;
     if ((unsigned)gx < (unsigned)L.Lpar && (unsigned)gy < (unsigned)L.Lpar) {
       const int64_t q = morton((uint32_t)gx, (uint32_t)gy);
-      v0 = pv[4 * q];
-      v1 = pv[4 * q + 1];
-      v2 = pv[4 * q + 2];
+      if (q < L.npar) {
+        v0 = pv[4 * q];
+        v1 = pv[4 * q + 1];
+        v2 = pv[4 * q + 2];
+      }
     }
     xs[c] = v0;
     xs[TS * TS + c] = v1;

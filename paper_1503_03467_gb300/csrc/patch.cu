@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kPatchThreads, PatchOcc<T>::kMinBlocks)
     int xi, yi;
     demorton((uint32_t)i, xi, yi);
     for (int j = tid; j < NB; j += kPatchThreads) {
-      const int p = shift_cell(xi, yi, g.nbr[j].x, g.nbr[j].y, g.Lpar);
+      const int p = shift_cell(xi, yi, g.nbr[j].x, g.nbr[j].y, g.Lpar, g.npatch);
       pj[j] = p;
       mj[j] = p >= 0 ? __popc(pmask[p] & 15u) : 0;
     }
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(256) k_patch_pcg(const T* __restrict__ Ahat,
   const int e0 = own ? sptr[j] : 0, e1 = own ? sptr[j + 1] : 0;
   int it_max = 0, it_sum = 0, done = 0;
 
-  for (int64_t i = blockIdx.x; i < np; i += gridDim.x) {
+  for (int64_t i = g.i_begin + blockIdx.x; i < g.i_end; i += gridDim.x) {
     const uint32_t mi = pmask[i] & 15u;
     if (mi == 0) {
       for (int idx = tid; idx < NB * 4; idx += blockDim.x) Rhat[i * 4 * NB + idx] = T(0);
@@ -432,7 +432,7 @@ __global__ void __launch_bounds__(256) k_patch_pcg(const T* __restrict__ Ahat,
     demorton((uint32_t)i, xi, yi);
     int na = 0, pjj = -1;
     if (own) {
-      pjj = shift_cell(xi, yi, g.nbr[j].x, g.nbr[j].y, g.Lpar);
+      pjj = shift_cell(xi, yi, g.nbr[j].x, g.nbr[j].y, g.Lpar, g.npatch);
       const int m = pjj >= 0 ? __popc(pmask[pjj] & 15u) : 0;
       na = m > 1 ? m - 1 : 0;  // active detail unknowns of neighbour j
       if (lead) {
@@ -581,7 +581,8 @@ __global__ void __launch_bounds__(256) k_patch_pcg(const T* __restrict__ Ahat,
 template <typename T>
 void launch_patch_pcg(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g, T* Rhat, double tol,
                       int max_iter, int* iter_stats, int num_sms, cudaStream_t s) {
-  if (g.npatch <= 0) return;
+  const int64_t nsolve = g.i_end - g.i_begin;
+  if (nsolve <= 0) return;
   const size_t smem = patch_pcg_smem_bytes<T>(g);
   cudaFuncSetAttribute(k_patch_pcg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int threads = ((g.NB * g.spp + 31) / 32) * 32;
@@ -589,7 +590,7 @@ void launch_patch_pcg(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g, T*
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_patch_pcg<T>, threads, smem);
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)num_sms * per_sm;
-  if (grid > g.npatch) grid = g.npatch;
+  if (grid > nsolve) grid = nsolve;
   {
     count_launch();
     k_patch_pcg<T><<<(unsigned)grid, threads, smem, s>>>(Ahat, pmask_k, g, Rhat, tol * tol, max_iter,

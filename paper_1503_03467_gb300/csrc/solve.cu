@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(128) k_restrict(const T* __restrict__ Rhat, in
     demorton((uint32_t)i, x, y);
     const T* row = Rhat + i * 4 * NB;
     for (int j = lane; j < NB; j += 32) {
-      const int p = shift_cell(x, y, nbr[j].x, nbr[j].y, Lpar);
+      const int p = shift_cell(x, y, nbr[j].x, nbr[j].y, Lpar, nrow);
       if (p < 0) continue;
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc += row[4 * j + c] * ghat[4 * p + c];
@@ -42,13 +42,14 @@ __global__ void __launch_bounds__(128) k_restrict(const T* __restrict__ Rhat, in
   if (lane == 0) vals[w] = acc;
   __syncthreads();
   if (threadIdx.x < 4) {
+    // all four slots of the parent are written: in the last parent of a
+    // prefix the rows >= nrow are absent children (zero), but the slots of
+    // the transformed vector are not
     const int64_t base = (int64_t)blockIdx.x * 4;
-    if (base + threadIdx.x < nrow) {
-      const int m = (int)pmask_km1[base >> 2] & 15;
-      const int a = threadIdx.x;
-      out[base + a] = qv<T>(m, a, 0) * vals[0] + qv<T>(m, a, 1) * vals[1] +
-                      qv<T>(m, a, 2) * vals[2] + qv<T>(m, a, 3) * vals[3];
-    }
+    const int m = (int)pmask_km1[base >> 2] & 15;
+    const int a = threadIdx.x;
+    out[base + a] = qv<T>(m, a, 0) * vals[0] + qv<T>(m, a, 1) * vals[1] +
+                    qv<T>(m, a, 2) * vals[2] + qv<T>(m, a, 3) * vals[3];
   }
 }
 
@@ -75,7 +76,7 @@ __global__ void k_transpose_rhat(const T* __restrict__ Rhat, int NB, const int2*
   const int j = (int)(t - p * NB);
   int x, y;
   demorton((uint32_t)p, x, y);
-  const int i = shift_cell(x, y, -nbr[j].x, -nbr[j].y, Lpar);
+  const int i = shift_cell(x, y, -nbr[j].x, -nbr[j].y, Lpar, npar);
   T* dst = RT + t * 4;
 #pragma unroll
   for (int a = 0; a < 3; ++a) dst[a] = i >= 0 ? Rhat[(int64_t)i * 4 * NB + 4 * j + a] : T(0);
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ RT, int N
     demorton((uint32_t)p, x, y);
     const T* row = RT + p * 4 * NB;
     for (int j = lane; j < NB; j += 32) {
-      const int i = shift_cell(x, y, -nbr[j].x, -nbr[j].y, Lpar);
+      const int i = shift_cell(x, y, -nbr[j].x, -nbr[j].y, Lpar, npar);
       if (i < 0) continue;
       const T vi = v[i];
       h0 += row[4 * j] * vi;
@@ -180,16 +181,21 @@ __device__ __forceinline__ void block_atomic_add(double v, double* dst) {
 
 // ---------------------------------------------------------------- coarsest level
 // A^(1) (4 x 4, float64) from the level-1 cell stencil; Cholesky in place.
+// Acell holds the nrow <= 4 level-1 cells that exist ([d][i], stride nrow).
 template <typename T>
-__global__ void k_level1_factor(const T* __restrict__ Acell, const int* __restrict__ map,
-                                double* A1, int* status) {
+__global__ void k_level1_factor(const T* __restrict__ Acell, int nrow,
+                                const int* __restrict__ map, double* A1, int* status) {
   if (threadIdx.x != 0) return;
   double M[16];
   for (int e = 0; e < 16; ++e) {
     const int i = e / 4, j = e % 4;
     const int d = map[e];
-    M[e] = d >= 0 ? (double)Acell[(int64_t)d * 4 + i]
-                  : (d <= -2 ? (double)Acell[(int64_t)(-d - 2) * 4 + j] : 0.0);
+    double v = 0.0;
+    if (i < nrow && j < nrow) {
+      if (d >= 0) v = (double)Acell[(int64_t)d * nrow + i];
+      else if (d <= -2) v = (double)Acell[(int64_t)(-d - 2) * nrow + j];
+    }
+    M[e] = v;
   }
   // inactive cells (zero row and column) become identity rows
   for (int i = 0; i < 4; ++i) {
@@ -216,12 +222,13 @@ __global__ void k_level1_factor(const T* __restrict__ Acell, const int* __restri
 }
 
 template <typename T>
-void launch_level1_factor(const T* Acell, const int* map, double* A1, int* status,
+void launch_level1_factor(const T* Acell, int nrow, const int* map, double* A1, int* status,
                           cudaStream_t s) {
-  { count_launch(); k_level1_factor<T><<<1, 32, 0, s>>>(Acell, map, A1, status); }
+  { count_launch(); k_level1_factor<T><<<1, 32, 0, s>>>(Acell, nrow, map, A1, status); }
 }
-template void launch_level1_factor<float>(const float*, const int*, double*, int*, cudaStream_t);
-template void launch_level1_factor<double>(const double*, const int*, double*, int*,
+template void launch_level1_factor<float>(const float*, int, const int*, double*, int*,
+                                          cudaStream_t);
+template void launch_level1_factor<double>(const double*, int, const int*, double*, int*,
                                            cudaStream_t);
 
 template <typename T>
@@ -258,7 +265,7 @@ __global__ void k_block_spmv64(const double* __restrict__ A, const int2* __restr
   demorton((uint32_t)p, x, y);
   double y0 = 0, y1 = 0, y2 = 0, y3 = 0;
   for (int o = 0; o < noff; ++o) {
-    const int q = shift_cell(x, y, off[o].x, off[o].y, Lpar);
+    const int q = shift_cell(x, y, off[o].x, off[o].y, Lpar, npar);
     if (q < 0) continue;
     const double* b = A + ((int64_t)o * npar + p) * 16;
     const double x0 = xv[4 * q], x1 = xv[4 * q + 1], x2 = xv[4 * q + 2], x3 = xv[4 * q + 3];

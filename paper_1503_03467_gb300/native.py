@@ -46,7 +46,8 @@ class Opts(ctypes.Structure):
                 ("level_max_iter", ctypes.c_int32), ("refine_tol", ctypes.c_double),
                 ("refine_max_iter", ctypes.c_int32), ("patch_tol", ctypes.c_double),
                 ("use_graph", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("profile", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -74,6 +75,11 @@ SIGNATURES = {
     "gamblet_default_opts": (None, [ctypes.POINTER(Opts)]),
     "gamblet_setup": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.c_int32, ctypes.c_void_p,
                                      ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "gamblet_setup_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Csr),
+                                             ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.POINTER(ctypes.c_int32)]),
     "gamblet_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.POINTER(Info)]),
     "gamblet_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
@@ -164,6 +170,29 @@ def gamblet_setup(rowptr, colind, val, q: int, cells, opts: Opts | None = None) 
                             ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
     _check(st)
     return h.value
+
+
+def gamblet_setup_batched(problems, opts: Opts | None = None):
+    """problems: sequence of (rowptr, colind, val, q, cells) as for
+    gamblet_setup.  Returns (handle, offsets): problem p owns entries
+    offsets[p]:offsets[p + 1] of the vectors passed to gamblet_solve."""
+    problems = list(problems)
+    nprob = len(problems)
+    csrs = (Csr * nprob)()
+    qs = (ctypes.c_int32 * nprob)()
+    cells = (ctypes.c_void_p * nprob)()
+    for p, (rowptr, colind, val, q, cl) in enumerate(problems):
+        csrs[p] = Csr(int(rowptr.shape[0]) - 1, int(colind.shape[0]), _ptr(rowptr, np.int32),
+                      _ptr(colind, np.int32), _ptr(val, np.float64))
+        qs[p] = int(q)
+        cells[p] = _ptr(cl, np.int32)
+    offsets = (ctypes.c_int32 * (nprob + 1))()
+    h = ctypes.c_void_p()
+    st = _lib.gamblet_setup_batched(nprob, csrs, qs, cells,
+                                    ctypes.byref(opts) if opts is not None else None,
+                                    ctypes.byref(h), offsets)
+    _check(st)
+    return h.value, np.array(offsets[:], dtype=np.int64)
 
 
 def gamblet_solve(h: int, g, u, components=None, info: Info | None = None) -> int:

@@ -28,3 +28,35 @@ def drop_nodes(p, keep):
     idx = np.nonzero(keep)[0]
     A = sp.csr_matrix(p.A)[idx][:, idx]
     return sp.csr_matrix(A), p.g[idx].copy(), np.ascontiguousarray(p.cells[idx])
+
+
+def demorton(m):
+    """(x, y) of a Morton index: x from the even bits, y from the odd bits."""
+    x = y = 0
+    for b in range(16):
+        x |= ((m >> (2 * b)) & 1) << b
+        y |= ((m >> (2 * b + 1)) & 1) << b
+    return x, y
+
+
+def pack_problems(probs):
+    """The placement gamblet_setup_batched documents: largest problems first
+    (stable), each in the aligned subtree starting at the running Morton
+    offset of a 2^Q lattice; unknowns numbered problem after problem.
+    Returns (A, g, cells, Q, offsets) of the combined block-diagonal system."""
+    order = sorted(range(len(probs)), key=lambda p: -probs[p].q)
+    base, total = {}, 0
+    for p in order:
+        base[p] = total
+        total += 4 ** probs[p].q
+    Q = max(max(pr.q for pr in probs), 2)
+    while 4 ** Q < total:
+        Q += 1
+    cells = []
+    for p, pr in enumerate(probs):
+        x0, y0 = demorton(base[p])
+        cells.append(pr.cells + np.array([x0, y0], dtype=np.int32))
+    offsets = np.concatenate([[0], np.cumsum([pr.ndof for pr in probs])]).astype(np.int64)
+    A = sp.block_diag([pr.A for pr in probs], format="csr")
+    g = np.concatenate([pr.g for pr in probs])
+    return A, g, np.ascontiguousarray(np.concatenate(cells), dtype=np.int32), Q, offsets

@@ -49,8 +49,8 @@ def test_struct_layouts_match_header(lib):
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(gamblet_csr), sizeof(gamblet_opts), sizeof(gamblet_info),
          sizeof(gamblet_kernel_stat));
-  printf("%zu %zu %zu\n", offsetof(gamblet_opts, stream), offsetof(gamblet_info, rel_residual),
-         offsetof(gamblet_csr, val));
+  printf("%zu %zu %zu %zu\n", offsetof(gamblet_opts, stream), offsetof(gamblet_info, rel_residual),
+         offsetof(gamblet_csr, val), offsetof(gamblet_opts, autotune));
   return 0;
 }
 """
@@ -64,12 +64,14 @@ int main(void) {
     offs = [int(x) for x in l2.split()]
     assert sizes == [ctypes.sizeof(lib.Csr), ctypes.sizeof(lib.Opts), ctypes.sizeof(lib.Info),
                      ctypes.sizeof(lib.KernelStat)]
-    assert offs == [lib.Opts.stream.offset, lib.Info.rel_residual.offset, lib.Csr.val.offset]
+    assert offs == [lib.Opts.stream.offset, lib.Info.rel_residual.offset, lib.Csr.val.offset,
+                    lib.Opts.autotune.offset]
 
 
 def test_host_only_calls(lib):
     o = lib.gamblet_default_opts()
     assert o.rho == 3.0 and o.precision == lib.FP64 and o.refine_max_iter == 50
+    assert o.autotune == 1
     assert lib.gamblet_status_string(lib.ERR_NOT_SPD).startswith("matrix not")
     assert lib.gamblet_device_bytes(0) == 0
     assert lib.gamblet_kernel_stats(0) == []

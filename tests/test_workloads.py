@@ -79,3 +79,22 @@ def test_rough_coefficient_bounds_and_determinism():
     assert p.cells.shape == (961, 2)
     assert interior_cells(4).tolist() == [[1, 1], [2, 1], [3, 1], [1, 2], [2, 2],
                                           [3, 2], [1, 3], [2, 3], [3, 3]]
+
+
+def test_batch_workload_draw_protocol():
+    from workloads import make_batch, make_batch_problem
+    # the documented draw order: side index, log10 contrast, then the fields
+    rng = np.random.default_rng(5)
+    n = (8, 16, 32)[int(rng.integers(3))]
+    C = 10.0 ** rng.uniform(2.0, 6.0)
+    la = rough_log_coefficient(n, int(np.log2(n)), C, rng)
+    g = rng.standard_normal((n - 1) ** 2)
+    p = make_batch_problem(5, sides=(8, 16, 32))
+    assert p.n == n and p.contrast == C
+    assert np.array_equal(p.log_a, la) and np.array_equal(p.g, g)
+    assert p.log_a.max() - p.log_a.min() <= np.log(C) + 1e-12
+    probs = make_batch(12, first_seed=1, sides=(8, 16, 32))
+    assert [q.n for q in probs] == [make_batch_problem(s, sides=(8, 16, 32)).n
+                                    for s in range(1, 13)]
+    assert all(1e2 <= q.contrast <= 1e6 for q in probs)
+    assert all(q.A.shape == ((q.n - 1) ** 2,) * 2 for q in probs)

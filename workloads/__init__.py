@@ -15,6 +15,9 @@ from .rough import (  # noqa: F401
     example1_coefficient,
     example1_rhs,
     make_problem,
+    make_batch,
+    make_batch_problem,
+    BATCH_SIDES,
     rough_log_coefficient,
     interior_cells,
 )

@@ -20,6 +20,8 @@ Recipe (stated once so both sides generate identical inputs):
   lattice (q = log2 n); its level-k cell is (ix >> (q-k), iy >> (q-k)).
   Level k < q lattices are full; at level q the cells with ix = 0 or
   iy = 0 hold no node.
+* Many-instance workload: problem p draws, from default_rng(seed_p), its
+  side from BATCH_SIDES, then log10 C ~ U[2, 6], then coefficient and g.
 """
 from __future__ import annotations
 
@@ -44,6 +46,7 @@ class Problem:
     A: sp.csr_matrix       # (n-1)^2 x (n-1)^2 fine stiffness (float64)
     g: np.ndarray          # (n-1)^2 right-hand side
     cells: np.ndarray      # (n-1)^2 x 2 int32 level-q lattice cells (x, y)
+    contrast: float = 0.0  # C of the coefficient draw
 
     @property
     def ndof(self) -> int:
@@ -112,7 +115,36 @@ def make_problem(n: int, contrast: float, seed: int,
     log_a = rough_log_coefficient(n, scales, contrast, rng)
     g = rng.standard_normal((n - 1) * (n - 1))
     A = assemble_q1(np.exp(log_a))
-    return Problem(n=n, q=q, log_a=log_a, A=A, g=g, cells=interior_cells(n))
+    return Problem(n=n, q=q, log_a=log_a, A=A, g=g, cells=interior_cells(n),
+                   contrast=float(contrast))
+
+
+# Grid sides of the many-instance workload and the range of log10(contrast).
+BATCH_SIDES = (128, 256, 512)
+BATCH_LOG10_CONTRAST = (2.0, 6.0)
+
+
+def make_batch_problem(seed: int, sides=BATCH_SIDES,
+                       log10_contrast=BATCH_LOG10_CONTRAST) -> Problem:
+    """One problem of the many-instance workload.  Draw order from
+    ``default_rng(seed)``: the side index (uniform over ``sides``), then
+    log10 C ~ U[log10_contrast], then the coefficient (S = q scales) and g
+    exactly as in make_problem."""
+    rng = np.random.default_rng(seed)
+    n = int(sides[int(rng.integers(len(sides)))])
+    contrast = float(10.0 ** rng.uniform(*log10_contrast))
+    q = int(round(np.log2(n)))
+    log_a = rough_log_coefficient(n, q, contrast, rng)
+    g = rng.standard_normal((n - 1) * (n - 1))
+    A = assemble_q1(np.exp(log_a))
+    return Problem(n=n, q=q, log_a=log_a, A=A, g=g, cells=interior_cells(n),
+                   contrast=contrast)
+
+
+def make_batch(nprob: int = 48, first_seed: int = 1, sides=BATCH_SIDES,
+               log10_contrast=BATCH_LOG10_CONTRAST) -> list:
+    """Problems with seeds first_seed .. first_seed + nprob - 1."""
+    return [make_batch_problem(first_seed + p, sides, log10_contrast) for p in range(nprob)]
 
 
 def example1_coefficient(q: int = 6) -> np.ndarray:
