@@ -54,6 +54,8 @@ def parse():
                     help="skip the many-problem (48 x {128,256,512}^2) timing")
     ap.add_argument("--batch-problems", type=int, default=48)
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--no-localization", action="store_true",
+                    help="skip the one-pass localization error per patch radius")
     return ap.parse_args()
 
 
@@ -395,6 +397,33 @@ def batched_timing(nv, torch, dev, a, stream, flush):
     }
 
 
+def localization_errors(nv, a, dev_in, ud, radii=(1.0, 2.0, 3.0, 4.0)):
+    """One-pass (no outer iteration) relative error against the direct
+    solution for each patch radius rho: the localization error of the
+    transform of Definition defb.  Tight patch and level tolerances
+    (1e-6, float32 storage) so that localization dominates."""
+    import torch
+    q = int(np.log2(a.size))
+    out = {}
+    for rho in radii:
+        o = nv.gamblet_default_opts()
+        o.rho = rho
+        o.precision = nv.MIXED
+        o.level_tol = 1e-6
+        o.level_max_iter = 5000
+        o.patch_tol = 1e-6
+        o.refine_max_iter = 0
+        h = nv.gamblet_setup(dev_in["rowptr"], dev_in["colind"], dev_in["val"], q,
+                             dev_in["cells"], o)
+        try:
+            u = torch.zeros_like(dev_in["g"])
+            nv.gamblet_solve(h, dev_in["g"], u)
+            out[str(int(rho))] = rel_err(u.cpu().numpy(), ud)
+        finally:
+            nv.gamblet_destroy(h)
+    return out
+
+
 def cpu_oracle(p):
     """The oracle's direct solve (SuperLU + extended-precision refinement)."""
     from oracle import direct
@@ -560,6 +589,8 @@ def main():
         line["adjoint"] = adjoint_timing(nv, torch, dev)
     if not a.no_batched:
         line["batched"] = batched_timing(nv, torch, dev, a, stream, flush)
+    if not a.no_localization:
+        line["localization_error_one_pass"] = localization_errors(nv, a, dev_in, ud)
     if rank == 0 and ws == 1 and not a.no_cpu:
         line["cpu_baseline"] = {"value": ndof / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "one full solve of the same problem: SuperLU factor + "

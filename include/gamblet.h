@@ -195,6 +195,19 @@ GAMBLET_API gamblet_status gamblet_solve(gamblet_handle h, const double* g, doub
                              double* components, gamblet_info* info);
 
 /*
+ * Truncated one-pass solve (Sec. 5.4, subsequent solves): u^(k) = u^(1) +
+ * sum_{l=2..k} (u^(l) - u^(l-1)), the Galerkin approximation of u in the
+ * span of the level-k gamblets psi^(k) (Theorem thddwedmgugyug, Eq.
+ * eqhuhiuv), in fine coordinates.  The restriction runs to level 1, the
+ * level systems 2..k are solved, and the levels above k only interpolate
+ * (v^(l) = R^(l,l-1) v^(l-1)); no outer refinement.  k = q gives the
+ * one-pass solution (gamblet_solve with refine_max_iter = 0).
+ *   k   1 <= k <= q.   g, u, info as for gamblet_solve.
+ */
+GAMBLET_API gamblet_status gamblet_solve_truncated(gamblet_handle h, int32_t k, const double* g,
+                                                   double* u, gamblet_info* info);
+
+/*
  * Adjoint gradient of J = 1/2 |u - u_obs|^2 with respect to theta_c =
  * log a_c for a cellwise-constant coefficient (the paper has no adjoint; the
  * discrete adjoint of A(theta) u = g):  A lambda = u - u_obs is solved with
@@ -256,6 +269,14 @@ GAMBLET_API gamblet_status gamblet_assemble_cells(int32_t n, const int32_t* rowp
                                                   int32_t ncell, const int32_t* cell_nodes,
                                                   const double* log_a, const double* K_ref,
                                                   double* val, double* cell_a, void* stream);
+
+/* Launch shapes the setup used at level k (2 <= k <= q, localized
+ * transform), chosen by the autotuner or by the fixed rules:
+ *   shapes[0]  patch-CG threads per neighbour parent (1, 2, 4; 0 = Cholesky)
+ *   shapes[1]  patch-CG block gather (0 thread per block, 1 half-warp per block)
+ *   shapes[2]  Galerkin kernel (0 thread per position, 1 warp-cooperative)
+ *   shapes[3]  level-CG SpMV threads per parent (1: 16 x 16 tiles, 4: 8 x 8) */
+GAMBLET_API gamblet_status gamblet_launch_shapes(gamblet_handle h, int32_t k, int32_t* shapes);
 
 /* Number of nodes n_k = |I^(k)| and detail rows |J^(k)| at level k. */
 GAMBLET_API gamblet_status gamblet_level_size(gamblet_handle h, int32_t k, int32_t* n_k, int32_t* nJ_k);

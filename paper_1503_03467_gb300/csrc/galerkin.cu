@@ -32,6 +32,73 @@ __device__ __forceinline__ void load_vec4(const double* p, double* b) {
   b[3] = v1.y;
 }
 
+// One CTA per coarse row i, one thread per window position (phase 1: the
+// thread reads whole 4x4 blocks, 64 bytes, and keeps four accumulators) and
+// one thread per output offset (phase 2).  Fewer instructions per block
+// product than k_galerkin_warp; better when the block lists per window
+// position are short (the finest level's 9-point stencil).
+template <typename T>
+__global__ void __launch_bounds__(256) k_galerkin_rows(const T* __restrict__ Ahat,
+                                                       const T* __restrict__ Rhat,
+                                                       const uint32_t* __restrict__ pmask,
+                                                       GalerkinGeom g, T* __restrict__ Aout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* rrow = reinterpret_cast<T*>(smem_raw);
+  T* t = rrow + 4 * g.NB;
+  const int64_t nrow = g.nrow;
+  for (int64_t i = g.i_begin + blockIdx.x; i < g.i_end; i += gridDim.x) {
+    if ((pmask[i] & 15u) == 0) {
+      for (int d = threadIdx.x; d < g.nout; d += blockDim.x) Aout[(int64_t)d * nrow + i] = T(0);
+      continue;
+    }
+    int xi, yi;
+    demorton((uint32_t)i, xi, yi);
+    for (int idx = threadIdx.x; idx < 4 * g.NB; idx += blockDim.x)
+      rrow[idx] = Rhat[i * 4 * g.NB + idx];
+    __syncthreads();
+    for (int w = threadIdx.x; w < g.nwin; w += blockDim.x) {
+      T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+      const int p = shift_cell(xi, yi, g.win[w].x, g.win[w].y, g.Lpar, nrow);
+      if (p >= 0) {
+        for (int e = g.l1_ptr[w]; e < g.l1_ptr[w + 1]; ++e) {
+          const int2 jo = g.l1_pairs[e];
+          const T* blk = Ahat + ((int64_t)jo.y * nrow + p) * 16;
+          T b[16];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) load_vec4(blk + 4 * r, b + 4 * r);
+          const T r0 = rrow[4 * jo.x], r1 = rrow[4 * jo.x + 1];
+          const T r2 = rrow[4 * jo.x + 2], r3 = rrow[4 * jo.x + 3];
+          acc0 += b[0] * r0 + b[1] * r1 + b[2] * r2 + b[3] * r3;
+          acc1 += b[4] * r0 + b[5] * r1 + b[6] * r2 + b[7] * r3;
+          acc2 += b[8] * r0 + b[9] * r1 + b[10] * r2 + b[11] * r3;
+          acc3 += b[12] * r0 + b[13] * r1 + b[14] * r2 + b[15] * r3;
+        }
+      }
+      t[4 * w] = acc0;
+      t[4 * w + 1] = acc1;
+      t[4 * w + 2] = acc2;
+      t[4 * w + 3] = acc3;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < g.nout; d += blockDim.x) {
+      T acc = 0;
+      const int ip = shift_cell(xi, yi, g.out[d].x, g.out[d].y, g.Lpar, nrow);
+      if (ip >= 0 && (pmask[ip] & 15u)) {
+        const T* rr = Rhat + (int64_t)ip * 4 * g.NB;
+        for (int e = g.l2_ptr[d]; e < g.l2_ptr[d + 1]; ++e) {
+          const int2 jw = g.l2_pairs[e];
+          const T* tw = t + 4 * jw.y;
+          T rv[4];
+          load_vec4(rr + 4 * jw.x, rv);
+          acc += rv[0] * tw[0] + rv[1] * tw[1] + rv[2] * tw[2] + rv[3] * tw[3];
+        }
+      }
+      Aout[(int64_t)d * nrow + i] = acc;
+    }
+    __syncthreads();
+  }
+}
+
 // One CTA per coarse row i.  Phase 1: a half-warp per window position w;
 // its 16 lanes hold the 16 entries of a 4x4 block, so every block of Ahat is
 // one coalesced 64-byte (float) read, multiplied by the matching entry of
@@ -40,7 +107,7 @@ __device__ __forceinline__ void load_vec4(const double* p, double* b) {
 // pairs of d, reading the row Rhat_{i+S_d} with unit stride, and the dot
 // product ends in a warp reduction.
 template <typename T>
-__global__ void __launch_bounds__(256) k_galerkin(const T* __restrict__ Ahat,
+__global__ void __launch_bounds__(256) k_galerkin_warp(const T* __restrict__ Ahat,
                                                   const T* __restrict__ Rhat,
                                                   const uint32_t* __restrict__ pmask,
                                                   GalerkinGeom g, T* __restrict__ Aout) {
@@ -52,7 +119,7 @@ __global__ void __launch_bounds__(256) k_galerkin(const T* __restrict__ Ahat,
   const int half = threadIdx.x >> 4, nhalf = blockDim.x >> 4;
   const int e = threadIdx.x & 15, cb = e & 3;  // block entry (a = e >> 2, column cb)
   const unsigned hmask = 0xffffu << (16 * (half & 1));
-  for (int64_t i = blockIdx.x; i < nrow; i += gridDim.x) {
+  for (int64_t i = g.i_begin + blockIdx.x; i < g.i_end; i += gridDim.x) {
     if ((pmask[i] & 15u) == 0) {
       for (int d = threadIdx.x; d < g.nout; d += blockDim.x) Aout[(int64_t)d * nrow + i] = T(0);
       continue;
@@ -104,11 +171,18 @@ __global__ void __launch_bounds__(256) k_galerkin(const T* __restrict__ Ahat,
 template <typename T>
 void launch_galerkin(const T* Ahat, const T* Rhat, const uint32_t* pmask_k, GalerkinGeom g,
                      T* Aout, cudaStream_t s) {
-  if (g.nrow <= 0) return;
+  const int64_t nrows = g.i_end - g.i_begin;
+  if (nrows <= 0) return;
   size_t smem = sizeof(T) * 4 * ((size_t)g.NB + (size_t)g.nwin);
-  cudaFuncSetAttribute(k_galerkin<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int64_t grid = g.nrow < 65535 * 16 ? g.nrow : 65535 * 16;
-  { count_launch(); k_galerkin<T><<<(unsigned)grid, 256, smem, s>>>(Ahat, Rhat, pmask_k, g, Aout); }
+  int64_t grid = nrows < 65535 * 16 ? nrows : 65535 * 16;
+  count_launch();
+  if (g.variant == 1) {
+    cudaFuncSetAttribute(k_galerkin_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_galerkin_warp<T><<<(unsigned)grid, 256, smem, s>>>(Ahat, Rhat, pmask_k, g, Aout);
+  } else {
+    cudaFuncSetAttribute(k_galerkin_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_galerkin_rows<T><<<(unsigned)grid, 256, smem, s>>>(Ahat, Rhat, pmask_k, g, Aout);
+  }
 }
 template void launch_galerkin<float>(const float*, const float*, const uint32_t*, GalerkinGeom,
                                      float*, cudaStream_t);

@@ -197,6 +197,7 @@ struct LevelDev {
   void* Rhat = nullptr;      // T, npar rows
   void* RT = nullptr;        // T, Rhat regrouped by parent (prolongation)
   int* pair_idx = nullptr;
+  int shape[4] = {0, 0, 0, 0};  // launch shapes used: patch spp, patch gather, Galerkin variant, CG spp
   // exact (dense)
   double* D = nullptr;       // transformed dense Ahat^(k)
   double* Bc = nullptr;      // Cholesky factor of B^(k)
@@ -305,6 +306,7 @@ struct gamblet_ctx {
   int q = 0;
   int n = 0;           // fine unknowns
   int nprob = 1;       // independent problems packed in the hierarchy
+  int kmax = 0;        // finest level whose detail component a solve adds (q = all)
   bool exact = false;
   bool mixed = false;
   int num_sms = 1;
@@ -702,36 +704,72 @@ double patch_flops(gamblet_ctx* h, int k) {
   return f;
 }
 
-// Lanes per neighbour parent of the patch CG at level k: candidates 1, 2, 4
-// timed on a Morton block of kTuneSample coarse cells in the middle of the
-// level (its Rhat rows are overwritten by the full launch that follows).
+// Patch-CG launch shape at level k: lanes per neighbour parent (1, 2, 4)
+// and block gather (thread per block or half-warp per block), timed on a
+// Morton block of kTuneSample coarse cells in the middle of the level (its
+// Rhat rows are overwritten by the full launch that follows).
 template <typename T>
-int tuned_patch_spp(gamblet_ctx* h, int k, const PatchPcgGeom& gp, T* Rhat) {
-  if (!h->opts.autotune || gp.npatch < kTuneMinParents) return gp.spp;
+void tune_patch_shape(gamblet_ctx* h, int k, PatchPcgGeom& gp, T* Rhat) {
+  if (!h->opts.autotune || gp.npatch < kTuneMinParents) return;
   const std::string key = h->plan->key + "/patch_pcg/" + std::to_string(k) + "/" +
                           std::to_string(sizeof(T)) + "/" + std::to_string(h->patch_tol);
-  int best_spp = gp.spp;
-  if (tune_lookup(key, &best_spp)) return best_spp;
-  cudaStream_t s = h->s;
-  int* stats = h->pool.zeros<int>(4, s);
-  PatchPcgGeom gt = gp;
-  gt.i_begin = (gp.npatch / 2 / kTuneSample) * kTuneSample;
-  gt.i_end = std::min(gt.i_begin + kTuneSample, gp.npatch);
-  float best = 1e30f;
-  for (int spp : {1, 2, 4}) {
-    if (gp.NB * spp > 256) continue;
-    gt.spp = spp;
-    const float ms = time_on_stream(s, [&] {
-      launch_patch_pcg<T>((const T*)h->lv[k].Ahat, h->lv[k].pmask, gt, Rhat, h->patch_tol, 200,
-                          stats, h->num_sms, s);
-    });
-    if (ms < best) {
-      best = ms;
-      best_spp = spp;
-    }
+  int code = 0;
+  if (!tune_lookup(key, &code)) {
+    cudaStream_t s = h->s;
+    int* stats = h->pool.zeros<int>(4, s);
+    PatchPcgGeom gt = gp;
+    gt.i_begin = (gp.npatch / 2 / kTuneSample) * kTuneSample;
+    gt.i_end = std::min(gt.i_begin + kTuneSample, gp.npatch);
+    float best = 1e30f;
+    code = gp.spp * 2 + gp.gather;
+    for (int spp : {1, 2, 4})
+      for (int gather : {0, 1}) {
+        if (gp.NB * spp > 256) continue;
+        gt.spp = spp;
+        gt.gather = gather;
+        const float ms = time_on_stream(s, [&] {
+          launch_patch_pcg<T>((const T*)h->lv[k].Ahat, h->lv[k].pmask, gt, Rhat, h->patch_tol,
+                              200, stats, h->num_sms, s);
+        });
+        if (ms < best) {
+          best = ms;
+          code = spp * 2 + gather;
+        }
+      }
+    tune_store(key, code);
   }
-  tune_store(key, best_spp);
-  return best_spp;
+  gp.spp = code / 2;
+  gp.gather = code % 2;
+}
+
+// Galerkin kernel of level k (k_galerkin_rows or k_galerkin_warp), timed on
+// kTuneSample rows in the middle of the level (rewritten by the full launch).
+template <typename T>
+void tune_galerkin_variant(gamblet_ctx* h, int k, GalerkinGeom& gg, const T* Ahat,
+                           const T* Rhat, T* Acell) {
+  if (!h->opts.autotune || gg.nrow < kTuneMinParents) return;
+  const std::string key = h->plan->key + "/galerkin/" + std::to_string(k) + "/" +
+                          std::to_string(sizeof(T));
+  int v = gg.variant;
+  if (!tune_lookup(key, &v)) {
+    cudaStream_t s = h->s;
+    GalerkinGeom gt = gg;
+    gt.i_begin = (gg.nrow / 2 / kTuneSample) * kTuneSample;
+    gt.i_end = std::min(gt.i_begin + kTuneSample, gg.nrow);
+    float best = 1e30f;
+    for (int cand : {0, 1}) {
+      gt.variant = cand;
+      const float ms = time_on_stream(s, [&] {
+        launch_galerkin<T>(Ahat, Rhat, h->lv[k].pmask, gt, Acell, s);
+      });
+      if (ms < best) {
+        best = ms;
+        v = cand;
+      }
+    }
+    tune_store(key, v);
+  }
+  gg.variant = v;
 }
 
 // ------------------------------------------------------------ localized setup
@@ -781,10 +819,12 @@ void setup_local(gamblet_ctx* h) {
     } else {
       PatchPcgGeom gp{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar, (int)pl.half.size(),
                       P.upload(pl.half, s), P.upload(pl.adj_ptr, s), P.upload(pl.adj, s),
-                      P.upload(pl.diag_h, s), pl.spp, 0, L.npar};
+                      P.upload(pl.diag_h, s), pl.spp, 0, L.npar, 0};
       if (patch_pcg_smem_bytes<T>(gp) > 227 * 1024)
         fail(GAMBLET_ERR_UNSUPPORTED, "patch blocks exceed shared memory; lower rho");
-      gp.spp = tuned_patch_spp<T>(h, k, gp, Rhat);
+      tune_patch_shape<T>(h, k, gp, Rhat);
+      L.shape[0] = gp.spp;
+      L.shape[1] = gp.gather;
       // flops are added after setup from the measured iteration counts
       int tok = h->prof.begin("patch_pcg_k" + std::to_string(k), pbytes, 0.0, s);
       launch_patch_pcg<T>((const T*)L.Ahat, L.pmask, gp, Rhat, h->patch_tol, 200,
@@ -811,9 +851,16 @@ void setup_local(gamblet_ctx* h) {
     gg.l2_pairs = P.upload(S.l2_pairs, s);
     gg.Lpar = Lpar;
     gg.nrow = L.npar;
+    gg.i_begin = 0;
+    gg.i_end = L.npar;
+    // wide stencils (long block lists per window position) favour the
+    // warp-cooperative kernel; the autotuner decides on large levels
+    gg.variant = L.noff > 32 ? 1 : 0;
     if (sizeof(T) * 4 * ((size_t)NB + (size_t)gg.nwin) > 227 * 1024)
       fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin window exceeds shared memory");
     T* Acell = P.alloc<T>((int64_t)gg.nout * L.npar);
+    tune_galerkin_variant<T>(h, k, gg, (const T*)L.Ahat, Rhat, Acell);
+    L.shape[2] = gg.variant;
     int tok = h->prof.begin(
         "galerkin_k" + std::to_string(k),
         sz * ((double)L.noff * L.npar * 16 + 4.0 * NB * L.npar + (double)gg.nout * L.npar),
@@ -1023,6 +1070,7 @@ void alloc_solve(gamblet_ctx* h) {
       // flight); the autotuner may overrule the rule on large levels
       c.spp = L.noff > 32 ? 4 : 1;
       c.spp = tuned_cg_spp<T>(h, k, c);
+      L.shape[3] = c.spp;
       const int tmax = c.spp == 4 ? 8 : 16;
       c.spmv_begin = sblocks;
       sblocks += (int)((L.npar + tmax * tmax - 1) / (tmax * tmax));
@@ -1070,7 +1118,8 @@ void run_level_cg(gamblet_ctx* h) {
   const int chunk = 8;
   CK(cudaMemsetAsync(h->cg_sc, 0, sizeof(CgScalars) * h->cg_nlev, s));
   launch_cg_init<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, s);
-  launch_cg_start(h->cg_sc, h->cg_nlev, tol2, h->any_active, s);
+  // CG level l solves level k = l + 2; a truncated solve stops at h->kmax
+  launch_cg_start(h->cg_sc, h->cg_nlev, std::max(h->kmax - 1, 0), tol2, h->any_active, s);
   if (h->opts.use_graph && !h->cg_exec) build_cg_graph<T>(h, chunk, tol2, maxit);
   for (int it = 0; it < maxit; it += chunk) {
     if (h->cg_exec) {
@@ -1100,7 +1149,8 @@ void run_level_cg(gamblet_ctx* h) {
   CK(cudaStreamSynchronize(s));
   for (int l = 0; l < h->cg_nlev; ++l) {
     h->level_iters_acc[l + 2] += sc[l].iters;
-    if (sc[l].rr > tol2 * sc[l].rr0) h->level_not_conv = true;
+    // levels above a truncation are not solved and cannot fail to converge
+    if (l + 2 <= h->kmax && sc[l].rr > tol2 * sc[l].rr0) h->level_not_conv = true;
     // algorithmic traffic: the 3x3 detail blocks of B^(k) once per iteration,
     // p read, Ap written (3 active slots); vector kernels: x, r, z, p, Ap, Dinv
     const LevelDev& L = h->lv[l + 2];
@@ -1150,7 +1200,7 @@ void apply_G(gamblet_ctx* h, const T* in, T* out, int inverse_last) {
   CK(cudaGetLastError());
   // level solves
   if (h->exact) {
-    for (int k = 2; k <= q; ++k) {
+    for (int k = 2; k <= std::min(q, h->kmax); ++k) {
       LevelDev& L = h->lv[k];
       launch_gather_det((const double*)L.ghat, L.det, L.nJ, L.wc, s);
       launch_dpotrs(L.Bc, L.nJ, L.wc, 1, s);
@@ -1168,8 +1218,10 @@ void apply_G(gamblet_ctx* h, const T* in, T* out, int inverse_last) {
     const T* vprev = (const T*)(k == 2 ? h->U1 : h->lv[k - 1].v);
     T* dst = (k == q) ? out : (T*)L.v;
     const int inv = (k == q) ? inverse_last : 1;
+    const bool detail = k <= h->kmax;  // levels above a truncation only interpolate
     if (h->exact) {
-      CK(cudaMemcpyAsync(dst, L.w, sizeof(double) * L.ncell, cudaMemcpyDeviceToDevice, s));
+      if (detail) CK(cudaMemcpyAsync(dst, L.w, sizeof(double) * L.ncell, cudaMemcpyDeviceToDevice, s));
+      else CK(cudaMemsetAsync(dst, 0, sizeof(double) * L.ncell, s));
       launch_dgemm_t((int)L.ncell, 1, (int)L.npar, 1.0, L.Rh, 1, (const double*)vprev, 0, 1.0,
                      (double*)dst, s);
       if (inv) launch_transform_vec<T>(dst, dst, L.npar, L.pmask, -1, s);
@@ -1177,8 +1229,8 @@ void apply_G(gamblet_ctx* h, const T* in, T* out, int inverse_last) {
       const double sz = (double)sizeof(T);
       int tok = h->prof.begin("prolong", sz * (3.0 * NB * L.npar + 2.0 * L.ncell + L.npar),
                               6.0 * NB * L.npar, s);
-      launch_prolong<T>((const T*)L.RT, NB, h->nbr, 1 << (k - 1), L.npar, vprev, (const T*)L.w,
-                        L.pmask, inv, dst, s);
+      launch_prolong<T>((const T*)L.RT, NB, h->nbr, 1 << (k - 1), L.npar, vprev,
+                        detail ? (const T*)L.w : nullptr, L.pmask, inv, dst, s);
       h->prof.end(tok, s);
     }
   }
@@ -1406,6 +1458,7 @@ gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
     h->pool.s = h->s;
     h->prof.on = h->opts.profile != 0;
     h->q = q;
+    h->kmax = q;
     h->n = A->n;
     h->exact = !(h->opts.rho > 0);
     h->mixed = h->opts.precision == GAMBLET_MIXED && !h->exact;
@@ -1643,6 +1696,29 @@ gamblet_status gamblet_setup_batched(int32_t nprob, const gamblet_csr* A, const 
   }
 }
 
+gamblet_status gamblet_solve_truncated(gamblet_handle h, int32_t k, const double* g, double* u,
+                                       gamblet_info* info) {
+  try {
+    if (!h || !g || !u) fail(GAMBLET_ERR_INVALID_ARG, "handle, g and u must be non-NULL");
+    if (k < 1 || k > h->q) fail(GAMBLET_ERR_INVALID_ARG, "k must be in [1, q]");
+    struct Restore {  // one-pass, truncated; the handle's options are put back
+      gamblet_ctx* h;
+      int maxit;
+      ~Restore() {
+        h->kmax = h->q;
+        h->opts.refine_max_iter = maxit;
+      }
+    } restore{h, h->opts.refine_max_iter};
+    h->kmax = k;
+    h->opts.refine_max_iter = 0;
+    if (h->mixed) return solve_impl<float>(h, g, u, nullptr, info);
+    return solve_impl<double>(h, g, u, nullptr, info);
+  } catch (const GbError& e) {
+    if (info) info->status = e.st;
+    return set_error(e);
+  }
+}
+
 gamblet_status gamblet_solve(gamblet_handle h, const double* g, double* u, double* components,
                              gamblet_info* info) {
   try {
@@ -1738,6 +1814,15 @@ gamblet_status gamblet_assemble_cells(int32_t n, const int32_t* rowptr, const in
   } catch (const GbError& e) {
     return set_error(e);
   }
+}
+
+gamblet_status gamblet_launch_shapes(gamblet_handle h, int32_t k, int32_t* shapes) {
+  if (!h || !shapes || k < 2 || k > h->q || h->exact) {
+    g_last_error = "bad handle, level or output (localized transform only)";
+    return GAMBLET_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < 4; ++i) shapes[i] = h->lv[k].shape[i];
+  return GAMBLET_OK;
 }
 
 gamblet_status gamblet_level_size(gamblet_handle h, int32_t k, int32_t* n_k, int32_t* nJ_k) {

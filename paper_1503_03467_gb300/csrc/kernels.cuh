@@ -100,6 +100,7 @@ struct PatchPcgGeom {
   const int* diag_h;    // NB: stored block of (j, j)
   int spp;              // threads per neighbour parent: 1, 2 or 4
   int64_t i_begin, i_end;  // coarse cells solved: [i_begin, i_end) (all: 0, npatch)
+  int gather;           // block gather: 0 = thread per block, 1 = half-warp per block
 };
 template <typename T>
 void launch_patch_pcg(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g, T* Rhat, double tol,
@@ -120,7 +121,9 @@ struct GalerkinGeom {
   const int* l2_ptr;     // nout + 1
   const int2* l2_pairs;  // (j, w): WIN_w = S_d + N_j
   int Lpar;              // side of the level-(k-1) lattice (= parent lattice of level k)
-  int64_t nrow;          // 4^(k-1)
+  int64_t nrow;          // stored level-(k-1) cells (4^(k-1) for a full square)
+  int64_t i_begin, i_end;  // rows computed: [i_begin, i_end) (all: 0, nrow)
+  int variant;           // 0: thread per window position / output, 1: warp-cooperative
 };
 // A'(d, i) = (Rhat Ahat Rhat^T)_{i, i + S_d} for every level-(k-1) cell i.
 template <typename T>
@@ -190,7 +193,9 @@ void prepare_cg_spmv(int max_ts);
 template <typename T>
 void launch_cg_init(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc,
                     cudaStream_t s);
-void launch_cg_start(CgScalars* sc, int nlev, double tol2, int* any_active, cudaStream_t s);
+// Activates the levels l < nlev_on whose right-hand side is nonzero.
+void launch_cg_start(CgScalars* sc, int nlev, int nlev_on, double tol2, int* any_active,
+                     cudaStream_t s);
 // One CG iteration = launch_cg_spmv (Ap = B p, p.Ap) then launch_cg_rest
 // (x, r, z update with r.z and r.r; scalars and convergence; p = z + beta p).
 template <typename T>

@@ -88,13 +88,14 @@ __global__ void __launch_bounds__(256) k_cg_init(const CgLevel* __restrict__ lv,
   block_sum_add(rr, &sc[l].rr, red);
 }
 
-__global__ void k_cg_start(CgScalars* sc, int nlev, double tol2, int* any_active) {
+// Levels l >= nlev_on stay inactive (truncated solves stop below them).
+__global__ void k_cg_start(CgScalars* sc, int nlev, int nlev_on, double tol2, int* any_active) {
   if (threadIdx.x != 0) return;
   int act = 0;
   for (int l = 0; l < nlev; ++l) {
     CgScalars s = sc[l];
     s.rr0 = s.rr;
-    s.active = s.rr > 0.0 && s.rz > 0.0;
+    s.active = l < nlev_on && s.rr > 0.0 && s.rz > 0.0;
     s.iters = 0;
     s.pAp = 0;
     s.rz_new = 0;
@@ -268,8 +269,9 @@ void launch_cg_init(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc
   { count_launch(); k_cg_init<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
 }
 
-void launch_cg_start(CgScalars* sc, int nlev, double tol2, int* any_active, cudaStream_t s) {
-  { count_launch(); k_cg_start<<<1, 32, 0, s>>>(sc, nlev, tol2, any_active); }
+void launch_cg_start(CgScalars* sc, int nlev, int nlev_on, double tol2, int* any_active,
+                     cudaStream_t s) {
+  { count_launch(); k_cg_start<<<1, 32, 0, s>>>(sc, nlev, nlev_on, tol2, any_active); }
 }
 
 template <typename T>

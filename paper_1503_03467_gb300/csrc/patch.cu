@@ -381,16 +381,7 @@ __device__ __forceinline__ void block_sum2(T& a, T& b, T* red) {
   __syncthreads();
 }
 
-template <typename T>
-__device__ __forceinline__ void load_detail_block(const T* __restrict__ blk16, T* out9, int na,
-                                                  int nb) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) out9[3 * a + b] = (a < na && b < nb) ? blk16[4 * a + b] : T(0);
-}
-
-template <typename T>
+template <typename T, bool kHalfWarpGather>
 __global__ void __launch_bounds__(256) k_patch_pcg(const T* __restrict__ Ahat,
                                                    const uint32_t* __restrict__ pmask,
                                                    PatchPcgGeom g, T* __restrict__ Rhat,
@@ -441,21 +432,38 @@ __global__ void __launch_bounds__(256) k_patch_pcg(const T* __restrict__ Ahat,
       }
     }
     __syncthreads();
-    // ---- gather the stored blocks (identity on inactive diagonal entries)
-    for (int h = tid; h < g.nhalf; h += blockDim.x) {
-      const int4 e = g.half[h];  // (ja, jb, o, -)
-      const int nra = mj[e.x], nrb = mj[e.y];
-      T out9[9];
-      if (nra > 0 && nrb > 0) {
-        load_detail_block<T>(Ahat + ((int64_t)e.z * np + pj[e.x]) * 16, out9, nra, nrb);
-      } else {
+    // ---- gather the stored blocks (identity on inactive diagonal entries).
+    // kHalfWarpGather: a half-warp per block, lane (a, b) reads entry (a, b)
+    // of the 4x4 block, so each block is one coalesced read of its three
+    // detail rows; otherwise a thread per block with nine scalar reads (more
+    // reads in flight per thread, more L1 wavefronts).
+    if (!kHalfWarpGather) {
+      for (int h = tid; h < g.nhalf; h += blockDim.x) {
+        const int4 e = g.half[h];  // (ja, jb, o, -)
+        const int nra = mj[e.x], nrb = mj[e.y];
+        const T* src = Ahat + ((int64_t)e.z * np + (nra > 0 ? pj[e.x] : 0)) * 16;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) out9[q] = T(0);
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            T v = (a < nra && b < nrb) ? __ldg(src + 4 * a + b) : T(0);
+            if (e.x == e.y && a == b && a >= nra) v = T(1);
+            blk[9 * h + 3 * a + b] = v;
+          }
       }
-      if (e.x == e.y)
-        for (int a = nra; a < 3; ++a) out9[4 * a] = T(1);
-#pragma unroll
-      for (int q = 0; q < 9; ++q) blk[9 * h + q] = out9[q];
+    } else {
+      const int hw = tid >> 4, nhw = blockDim.x >> 4;
+      const int a = (tid >> 2) & 3, b = tid & 3;
+      for (int h = hw; h < g.nhalf; h += nhw) {
+        const int4 e = g.half[h];  // (ja, jb, o, -)
+        const int nra = mj[e.x], nrb = mj[e.y];
+        if (a < 3 && b < 3) {
+          T v = T(0);
+          if (a < nra && b < nrb) v = __ldg(Ahat + ((int64_t)e.z * np + pj[e.x]) * 16 + 4 * a + b);
+          else if (e.x == e.y && a == b) v = T(1);
+          blk[9 * h + 3 * a + b] = v;
+        }
+      }
     }
     // ---- right-hand side of neighbour j
     T rv[3] = {T(0), T(0), T(0)};
@@ -584,17 +592,18 @@ void launch_patch_pcg(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g, T*
   const int64_t nsolve = g.i_end - g.i_begin;
   if (nsolve <= 0) return;
   const size_t smem = patch_pcg_smem_bytes<T>(g);
-  cudaFuncSetAttribute(k_patch_pcg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = g.gather ? k_patch_pcg<T, true> : k_patch_pcg<T, false>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int threads = ((g.NB * g.spp + 31) / 32) * 32;
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_patch_pcg<T>, threads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)num_sms * per_sm;
   if (grid > nsolve) grid = nsolve;
   {
     count_launch();
-    k_patch_pcg<T><<<(unsigned)grid, threads, smem, s>>>(Ahat, pmask_k, g, Rhat, tol * tol, max_iter,
-                                                          iter_stats);
+    kern<<<(unsigned)grid, threads, smem, s>>>(Ahat, pmask_k, g, Rhat, tol * tol, max_iter,
+                                               iter_stats);
   }
 }
 template void launch_patch_pcg<float>(const float*, const uint32_t*, PatchPcgGeom, float*, double,

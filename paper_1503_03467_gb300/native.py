@@ -82,6 +82,8 @@ SIGNATURES = {
                                              ctypes.POINTER(ctypes.c_int32)]),
     "gamblet_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.POINTER(Info)]),
+    "gamblet_solve_truncated": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.POINTER(Info)]),
     "gamblet_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p,
@@ -90,6 +92,8 @@ SIGNATURES = {
                                               ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p]),
+    "gamblet_launch_shapes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_int32)]),
     "gamblet_level_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
                                           ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32)]),
@@ -195,10 +199,24 @@ def gamblet_setup_batched(problems, opts: Opts | None = None):
     return h.value, np.array(offsets[:], dtype=np.int64)
 
 
+def gamblet_launch_shapes(h: int, k: int) -> dict:
+    out = (ctypes.c_int32 * 4)()
+    _check(_lib.gamblet_launch_shapes(ctypes.c_void_p(h), int(k), out))
+    return {"patch_spp": out[0], "patch_gather": out[1], "galerkin_variant": out[2],
+            "cg_spp": out[3]}
+
+
 def gamblet_solve(h: int, g, u, components=None, info: Info | None = None) -> int:
     info = info if info is not None else Info()
     st = _lib.gamblet_solve(ctypes.c_void_p(h), _ptr(g, np.float64), _ptr(u, np.float64),
                             _ptr(components, np.float64), ctypes.byref(info))
+    return _check(st)
+
+
+def gamblet_solve_truncated(h: int, k: int, g, u, info: Info | None = None) -> int:
+    info = info if info is not None else Info()
+    st = _lib.gamblet_solve_truncated(ctypes.c_void_p(h), int(k), _ptr(g, np.float64),
+                                      _ptr(u, np.float64), ctypes.byref(info))
     return _check(st)
 
 

@@ -147,3 +147,60 @@ def test_invalid_inputs_are_rejected():
     with pytest.raises(nv.GambletError) as e:
         nv.gamblet_setup(rp, ci, -va, p.q, p.cells)
     assert e.value.status == nv.ERR_NOT_SPD
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-3)])
+def test_truncated_solve_sums_leading_components(precision, tol):
+    """u^(k) of a truncated solve = the oracle's components of levels 1..k
+    (Sec. 5.4); k = q is the one-pass solution."""
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(64, 1e4, 12)
+    ref = gamblet_local_setup(p.A, p.cells, p.q, 3.0)
+    one = gamblet_local_solve(ref, p.g, return_components=True)
+    h = _setup(p.A, p.cells, p.q, 3.0, precision=precision, level_tol=1e-14 if precision == 0 else 1e-7,
+               patch_tol=0.0 if precision == 0 else 1e-7)
+    try:
+        for k in (1, 2, 4, p.q):
+            u = np.zeros(p.ndof)
+            assert nv.gamblet_solve_truncated(h, k, p.g, u) == nv.OK
+            assert rel(u, one["comps"][:k].sum(axis=0)) < tol, k
+        with pytest.raises(nv.GambletError):
+            nv.gamblet_solve_truncated(h, p.q + 1, p.g, np.zeros(p.ndof))
+        # the handle keeps its full depth: a plain solve adds every level
+        u = np.zeros(p.ndof)
+        assert nv.gamblet_solve(h, p.g, u) == nv.OK
+        assert rel(u, one["u"]) < tol
+    finally:
+        nv.gamblet_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuned_shapes_are_valid_and_change_nothing_but_rounding(precision):
+    """The autotuner picks among launch shapes that compute the same rows
+    (only the summation order differs); 256 x 256 has levels large enough
+    to be tuned."""
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(256, 1e4, 13)
+    rp, ci, va = csr_arrays(p.A)
+    us = []
+    for tune in (1, 0, 1):  # the second tuned setup reads the process-wide cache
+        o = nv.gamblet_default_opts()
+        o.precision = precision
+        o.level_tol = 0.1
+        o.refine_tol = 1e-12
+        o.refine_max_iter = 100
+        o.autotune = tune
+        h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
+        try:
+            for k in range(2, p.q + 1):
+                sh = nv.gamblet_launch_shapes(h, k)
+                assert sh["patch_spp"] in (1, 2, 4) and sh["patch_gather"] in (0, 1)
+                assert sh["galerkin_variant"] in (0, 1) and sh["cg_spp"] in (1, 4)
+            u = np.zeros(p.ndof)
+            info = nv.Info()
+            assert nv.gamblet_solve(h, p.g, u, None, info) == nv.OK
+            assert info.rel_residual <= 1e-12
+            us.append(u)
+        finally:
+            nv.gamblet_destroy(h)
+    assert rel(us[0], us[1]) < 1e-9 and rel(us[2], us[1]) < 1e-9
