@@ -102,6 +102,11 @@ typedef struct {
                                timing candidates on a sample of each large
                                level, once per geometry and precision in a
                                process; 0: fixed rules                     */
+  int32_t galerkin_variant; /* -1: automatic; 0, 1, 2: use that Galerkin
+                               kernel on every level (see
+                               gamblet_launch_shapes)                      */
+  int32_t patch_gather;     /* -1: automatic; 0, 1: use that patch-CG block
+                               gather on every level                       */
   void* stream;             /* cudaStream_t                                */
 } gamblet_opts;
 
@@ -121,7 +126,8 @@ typedef struct gamblet_ctx* gamblet_handle;
 
 /* Fill *opts with defaults: rho = 3, Euclidean rule, FP64, level_tol 1e-8,
  * level_max_iter 1000, refine_tol 1e-13, refine_max_iter 50, graphs on,
- * profiling off, autotuning on, default stream. */
+ * profiling off, autotuning on (no forced kernel variants), default
+ * stream. */
 GAMBLET_API void gamblet_default_opts(gamblet_opts* opts);
 
 /*
@@ -274,7 +280,8 @@ GAMBLET_API gamblet_status gamblet_assemble_cells(int32_t n, const int32_t* rowp
  * transform), chosen by the autotuner or by the fixed rules:
  *   shapes[0]  patch-CG threads per neighbour parent (1, 2, 4; 0 = Cholesky)
  *   shapes[1]  patch-CG block gather (0 thread per block, 1 half-warp per block)
- *   shapes[2]  Galerkin kernel (0 thread per position, 1 warp-cooperative)
+ *   shapes[2]  Galerkin kernel (0 thread per position, 1 warp-cooperative,
+ *              2 warp per row)
  *   shapes[3]  level-CG SpMV threads per parent (1: 16 x 16 tiles, 4: 8 x 8) */
 GAMBLET_API gamblet_status gamblet_launch_shapes(gamblet_handle h, int32_t k, int32_t* shapes);
 

@@ -4,6 +4,8 @@ timing and profiling runs:
   python -m paper_1503_03467_gb300 [--size 512] [--precision mixed|fp64]
                                    [--rho 3] [--contrast 1e4] [--seed 0]
                                    [--repeat 1] [--profile] [--capture-last]
+                                   [--no-autotune] [--galerkin-variant -1|0|1|2]
+                                   [--patch-gather -1|0|1]
 
 Prints, for the last of `repeat` setup + solve passes, the setup and solve
 device times, the outer iterations and the final relative residual
@@ -34,6 +36,8 @@ def main(argv=None):
     ap.add_argument("--profile", action="store_true")
     ap.add_argument("--capture-last", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--galerkin-variant", type=int, default=-1)
+    ap.add_argument("--patch-gather", type=int, default=-1)
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from workloads import make_problem
@@ -51,6 +55,8 @@ def main(argv=None):
     o.refine_max_iter = 100
     o.profile = 1 if a.profile else 0
     o.autotune = 0 if a.no_autotune else 1
+    o.galerkin_variant = a.galerkin_variant
+    o.patch_gather = a.patch_gather
     rowptr = np.ascontiguousarray(A.indptr, dtype=np.int32)
     colind = np.ascontiguousarray(A.indices, dtype=np.int32)
     val = np.ascontiguousarray(A.data)

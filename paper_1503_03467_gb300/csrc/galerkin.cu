@@ -99,6 +99,80 @@ __global__ void __launch_bounds__(256) k_galerkin_rows(const T* __restrict__ Aha
   }
 }
 
+// One warp per coarse row, the work split as in k_galerkin_rows (lanes over
+// window positions, then over output offsets) but synchronised per warp
+// only: each warp keeps its own Rhat row and window in shared memory, so the
+// rows of a CTA proceed independently and no warp idles at a CTA barrier
+// while another finishes a phase.  Suited to short rows (the finest level).
+template <typename T>
+__global__ void __launch_bounds__(256) k_galerkin_warprow(const T* __restrict__ Ahat,
+                                                          const T* __restrict__ Rhat,
+                                                          const uint32_t* __restrict__ pmask,
+                                                          GalerkinGeom g, T* __restrict__ Aout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int per = 4 * (g.NB + g.nwin);  // T per warp
+  T* rrow = reinterpret_cast<T*>(smem_raw) + (size_t)warp * per;
+  T* t = rrow + 4 * g.NB;
+  const int64_t nrow = g.nrow;
+  for (int64_t i = g.i_begin + (int64_t)blockIdx.x * nwarp + warp; i < g.i_end;
+       i += (int64_t)gridDim.x * nwarp) {
+    if ((pmask[i] & 15u) == 0) {
+      for (int d = lane; d < g.nout; d += 32) Aout[(int64_t)d * nrow + i] = T(0);
+      continue;
+    }
+    int xi, yi;
+    demorton((uint32_t)i, xi, yi);
+    for (int j = lane; j < g.NB; j += 32) {
+      T v[4];
+      load_vec4(Rhat + (i * g.NB + j) * 4, v);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rrow[4 * j + c] = v[c];
+    }
+    __syncwarp();
+    for (int w = lane; w < g.nwin; w += 32) {
+      T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+      const int p = shift_cell(xi, yi, g.win[w].x, g.win[w].y, g.Lpar, nrow);
+      if (p >= 0) {
+        for (int e = g.l1_ptr[w]; e < g.l1_ptr[w + 1]; ++e) {
+          const int2 jo = g.l1_pairs[e];
+          const T* blk = Ahat + ((int64_t)jo.y * nrow + p) * 16;
+          T b[16];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) load_vec4(blk + 4 * r, b + 4 * r);
+          const T r0 = rrow[4 * jo.x], r1 = rrow[4 * jo.x + 1];
+          const T r2 = rrow[4 * jo.x + 2], r3 = rrow[4 * jo.x + 3];
+          acc0 += b[0] * r0 + b[1] * r1 + b[2] * r2 + b[3] * r3;
+          acc1 += b[4] * r0 + b[5] * r1 + b[6] * r2 + b[7] * r3;
+          acc2 += b[8] * r0 + b[9] * r1 + b[10] * r2 + b[11] * r3;
+          acc3 += b[12] * r0 + b[13] * r1 + b[14] * r2 + b[15] * r3;
+        }
+      }
+      t[4 * w] = acc0;
+      t[4 * w + 1] = acc1;
+      t[4 * w + 2] = acc2;
+      t[4 * w + 3] = acc3;
+    }
+    __syncwarp();
+    for (int d = lane; d < g.nout; d += 32) {
+      T acc = 0;
+      const int ip = shift_cell(xi, yi, g.out[d].x, g.out[d].y, g.Lpar, nrow);
+      if (ip >= 0 && (pmask[ip] & 15u)) {
+        const T* rr = Rhat + (int64_t)ip * 4 * g.NB;
+        for (int e = g.l2_ptr[d]; e < g.l2_ptr[d + 1]; ++e) {
+          const int2 jw = g.l2_pairs[e];
+          const T* tw = t + 4 * jw.y;
+          T rv[4];
+          load_vec4(rr + 4 * jw.x, rv);
+          acc += rv[0] * tw[0] + rv[1] * tw[1] + rv[2] * tw[2] + rv[3] * tw[3];
+        }
+      }
+      Aout[(int64_t)d * nrow + i] = acc;
+    }
+    __syncwarp();  // rrow and t are rewritten by the warp's next row
+  }
+}
+
 // One CTA per coarse row i.  Phase 1: a half-warp per window position w;
 // its 16 lanes hold the 16 entries of a 4x4 block, so every block of Ahat is
 // one coalesced 64-byte (float) read, multiplied by the matching entry of
@@ -176,7 +250,14 @@ void launch_galerkin(const T* Ahat, const T* Rhat, const uint32_t* pmask_k, Gale
   size_t smem = sizeof(T) * 4 * ((size_t)g.NB + (size_t)g.nwin);
   int64_t grid = nrows < 65535 * 16 ? nrows : 65535 * 16;
   count_launch();
-  if (g.variant == 1) {
+  if (g.variant == 2) {
+    const size_t smem8 = 8 * smem;  // eight warps, one row each
+    cudaFuncSetAttribute(k_galerkin_warprow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem8);
+    const int64_t g8 = (nrows + 7) / 8;
+    k_galerkin_warprow<T><<<(unsigned)(g8 < 65535 * 16 ? g8 : 65535 * 16), 256, smem8, s>>>(
+        Ahat, Rhat, pmask_k, g, Aout);
+  } else if (g.variant == 1) {
     cudaFuncSetAttribute(k_galerkin_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_galerkin_warp<T><<<(unsigned)grid, 256, smem, s>>>(Ahat, Rhat, pmask_k, g, Aout);
   } else {

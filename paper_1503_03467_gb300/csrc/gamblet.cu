@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <functional>
@@ -571,6 +572,77 @@ struct Plan {
 int half_code(const OffSet& Sp, int dx, int dy);
 OffSet blocks_from_cells(const OffSet& S, const OffSet& Sp, int km1, std::vector<int>& map);
 
+// Shared-memory slots of the stored patch blocks, chosen so that the lanes
+// of a warp that read blocks in the same CG step hit distinct banks.  Thread
+// (j, sub) of the patch CG walks entries sub, sub + S, ... of row j's
+// adjacency list (S = pl.spp lanes per neighbour parent), so the blocks read
+// together are those of one (warp, step) group.  A block's words sit at
+// 9 * slot + q, and 9 is invertible modulo 32, so blocks whose slots differ
+// modulo 32 never share a bank.  Each block is greedily given a residue
+// (colour) unused in its two groups (the row of ja and, transposed, of jb);
+// when all 32 are taken the least used one is reused.  Slots are colour +
+// 32 * rank; unused slots are padding (ja = -1).  Only the layout changes,
+// not the arithmetic.
+void assign_bank_slots(PlanLevel& pl, int NB) {
+  const int nb = (int)pl.half.size();
+  const int S = pl.spp;
+  std::vector<std::vector<int>> groups_of(nb);
+  std::map<std::pair<int, int>, int> gid;
+  for (int j = 0; j < NB; ++j)
+    for (int e = pl.adj_ptr[j]; e < pl.adj_ptr[j + 1]; ++e) {
+      const int kpos = e - pl.adj_ptr[j];
+      const int thread = j * S + kpos % S;
+      const std::pair<int, int> key{thread / 32, kpos / S};
+      auto it = gid.find(key);
+      const int g = it == gid.end() ? (gid[key] = (int)gid.size()) : it->second;
+      groups_of[pl.adj[e].x].push_back(g);
+    }
+  std::vector<uint32_t> used(gid.size(), 0u);           // colours taken per group
+  std::vector<std::array<int, 32>> use_count(gid.size());
+  for (auto& a : use_count) a.fill(0);
+  std::vector<int> colour(nb, 0), count(32, 0);
+  for (int b = 0; b < nb; ++b) {
+    uint32_t taken = 0;
+    for (int g : groups_of[b]) taken |= used[g];
+    int c = -1;
+    for (int t = 0; t < 32; ++t) {
+      const int cand = (b + t) & 31;  // rotate the start to balance the classes
+      if (!((taken >> cand) & 1u)) {
+        c = cand;
+        break;
+      }
+    }
+    if (c < 0) {  // every residue taken: the least used in these groups
+      int best = 1 << 30;
+      for (int cand = 0; cand < 32; ++cand) {
+        int u = 0;
+        for (int g : groups_of[b]) u += use_count[g][cand];
+        if (u < best) {
+          best = u;
+          c = cand;
+        }
+      }
+    }
+    colour[b] = c;
+    for (int g : groups_of[b]) {
+      used[g] |= 1u << c;
+      ++use_count[g][c];
+    }
+  }
+  std::vector<int> rank(nb);
+  for (int b = 0; b < nb; ++b) rank[b] = count[colour[b]]++;
+  const int per = *std::max_element(count.begin(), count.end());
+  std::vector<int> slot(nb);
+  std::vector<int4> half(32 * (size_t)per, make_int4(-1, -1, 0, 0));
+  for (int b = 0; b < nb; ++b) {
+    slot[b] = colour[b] + 32 * rank[b];
+    half[slot[b]] = pl.half[b];
+  }
+  pl.half.swap(half);
+  for (int4& a : pl.adj) a.x = slot[a.x];
+  for (int& d : pl.diag_h) d = slot[d];
+}
+
 std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
                                        const std::string& key) {
   auto plan = std::make_shared<Plan>();
@@ -604,6 +676,7 @@ std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
     pl.spp = row_len > 24 ? 4 : (row_len > 12 ? 2 : 1);
     while (pl.spp > 1 && NB * pl.spp > 256) pl.spp >>= 1;
     pl.flops_iter = 18.0 * (2.0 * pl.half.size() - NB) + 60.0 * NB;
+    assign_bank_slots(pl, NB);
     if (k - 1 >= 2) {
       pl.O_next = blocks_from_cells(pl.S.S, pl.S.Sp, k - 1, pl.map_next);
       O = pl.O_next;
@@ -642,6 +715,9 @@ std::shared_ptr<const Plan> cached_plan(int q, double rho, int rule, const OffSe
 // fixed rule: their kernels are too short for the choice to matter.
 constexpr int64_t kTuneMinParents = 16384;
 constexpr int64_t kTuneSample = 4096;  // a 64 x 64 Morton block of coarse cells
+// Galerkin rows are cheap and one variant packs eight rows per CTA: a larger
+// sample keeps every candidate's grid larger than the GPU
+constexpr int64_t kTuneSampleRows = 16384;
 
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
@@ -742,8 +818,9 @@ void tune_patch_shape(gamblet_ctx* h, int k, PatchPcgGeom& gp, T* Rhat) {
   gp.gather = code % 2;
 }
 
-// Galerkin kernel of level k (k_galerkin_rows or k_galerkin_warp), timed on
-// kTuneSample rows in the middle of the level (rewritten by the full launch).
+// Galerkin kernel of level k (k_galerkin_rows, k_galerkin_warp or
+// k_galerkin_warprow), timed on kTuneSampleRows rows in the middle of the
+// level (rewritten by the full launch).
 template <typename T>
 void tune_galerkin_variant(gamblet_ctx* h, int k, GalerkinGeom& gg, const T* Ahat,
                            const T* Rhat, T* Acell) {
@@ -754,10 +831,11 @@ void tune_galerkin_variant(gamblet_ctx* h, int k, GalerkinGeom& gg, const T* Aha
   if (!tune_lookup(key, &v)) {
     cudaStream_t s = h->s;
     GalerkinGeom gt = gg;
-    gt.i_begin = (gg.nrow / 2 / kTuneSample) * kTuneSample;
-    gt.i_end = std::min(gt.i_begin + kTuneSample, gg.nrow);
+    gt.i_begin = (gg.nrow / 2 / kTuneSampleRows) * kTuneSampleRows;
+    gt.i_end = std::min(gt.i_begin + kTuneSampleRows, gg.nrow);
     float best = 1e30f;
-    for (int cand : {0, 1}) {
+    for (int cand : {0, 1, 2}) {
+      if (cand == 2 && 8 * sizeof(T) * 4 * ((size_t)gg.NB + gg.nwin) > 227 * 1024) continue;
       gt.variant = cand;
       const float ms = time_on_stream(s, [&] {
         launch_galerkin<T>(Ahat, Rhat, h->lv[k].pmask, gt, Acell, s);
@@ -818,11 +896,12 @@ void setup_local(gamblet_ctx* h) {
       h->prof.end(tok, s);
     } else {
       PatchPcgGeom gp{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar, (int)pl.half.size(),
-                      P.upload(pl.half, s), P.upload(pl.adj_ptr, s), P.upload(pl.adj, s),
-                      P.upload(pl.diag_h, s), pl.spp, 0, L.npar, 0};
+                      P.upload(pl.half, s), (int)pl.adj.size(), P.upload(pl.adj_ptr, s),
+                      P.upload(pl.adj, s), P.upload(pl.diag_h, s), pl.spp, 0, L.npar, 0};
       if (patch_pcg_smem_bytes<T>(gp) > 227 * 1024)
         fail(GAMBLET_ERR_UNSUPPORTED, "patch blocks exceed shared memory; lower rho");
       tune_patch_shape<T>(h, k, gp, Rhat);
+      if (h->opts.patch_gather == 0 || h->opts.patch_gather == 1) gp.gather = h->opts.patch_gather;
       L.shape[0] = gp.spp;
       L.shape[1] = gp.gather;
       // flops are added after setup from the measured iteration counts
@@ -854,12 +933,20 @@ void setup_local(gamblet_ctx* h) {
     gg.i_begin = 0;
     gg.i_end = L.npar;
     // wide stencils (long block lists per window position) favour the
-    // warp-cooperative kernel; the autotuner decides on large levels
-    gg.variant = L.noff > 32 ? 1 : 0;
+    // warp-cooperative kernel, short ones a warp per row; the autotuner
+    // decides on large levels
+    gg.variant = L.noff > 32 ? 1 : 2;
+    if (gg.variant == 2 && 8 * sizeof(T) * 4 * ((size_t)NB + gg.nwin) > 227 * 1024) gg.variant = 0;
     if (sizeof(T) * 4 * ((size_t)NB + (size_t)gg.nwin) > 227 * 1024)
       fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin window exceeds shared memory");
     T* Acell = P.alloc<T>((int64_t)gg.nout * L.npar);
-    tune_galerkin_variant<T>(h, k, gg, (const T*)L.Ahat, Rhat, Acell);
+    if (h->opts.galerkin_variant >= 0 && h->opts.galerkin_variant <= 2) {
+      gg.variant = h->opts.galerkin_variant;
+      if (gg.variant == 2 && 8 * sizeof(T) * 4 * ((size_t)NB + gg.nwin) > 227 * 1024)
+        fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin warp-per-row window exceeds shared memory");
+    } else {
+      tune_galerkin_variant<T>(h, k, gg, (const T*)L.Ahat, Rhat, Acell);
+    }
     L.shape[2] = gg.variant;
     int tok = h->prof.begin(
         "galerkin_k" + std::to_string(k),
@@ -1467,6 +1554,10 @@ gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
       fail(GAMBLET_ERR_INVALID_ARG, "unknown precision");
     if (h->opts.nbr_rule != 0 && h->opts.nbr_rule != 1)
       fail(GAMBLET_ERR_INVALID_ARG, "nbr_rule must be 0 or 1");
+    if (h->opts.galerkin_variant < -1 || h->opts.galerkin_variant > 2)
+      fail(GAMBLET_ERR_INVALID_ARG, "galerkin_variant must be -1, 0, 1 or 2");
+    if (h->opts.patch_gather < -1 || h->opts.patch_gather > 1)
+      fail(GAMBLET_ERR_INVALID_ARG, "patch_gather must be -1, 0 or 1");
     if (h->exact && q > 7)
       fail(GAMBLET_ERR_UNSUPPORTED, "the exact (rho <= 0) transform is limited to q <= 7");
     int dev = 0;
@@ -1656,6 +1747,8 @@ void gamblet_default_opts(gamblet_opts* o) {
   o->use_graph = 1;
   o->profile = 0;
   o->autotune = 1;
+  o->galerkin_variant = -1;
+  o->patch_gather = -1;
   o->stream = nullptr;
 }
 

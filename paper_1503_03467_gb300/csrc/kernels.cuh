@@ -93,8 +93,9 @@ struct PatchPcgGeom {
   const int* pair_idx;  // NB x NB
   int Lpar;
   int64_t npatch;
-  int nhalf;            // stored blocks (ja >= jb, offset in O_k)
-  const int4* half;     // (ja, jb, o, 0)
+  int nhalf;            // block slots in shared memory (stored blocks plus padding)
+  const int4* half;     // per slot (ja, jb, o, 0) of a stored block ja >= jb, or ja = -1
+  int nadj;             // adjacency entries (2 x stored blocks - NB)
   const int* adj_ptr;   // NB + 1
   const int4* adj;      // (stored block, other neighbour, transposed, 0)
   const int* diag_h;    // NB: stored block of (j, j)
@@ -123,7 +124,8 @@ struct GalerkinGeom {
   int Lpar;              // side of the level-(k-1) lattice (= parent lattice of level k)
   int64_t nrow;          // stored level-(k-1) cells (4^(k-1) for a full square)
   int64_t i_begin, i_end;  // rows computed: [i_begin, i_end) (all: 0, nrow)
-  int variant;           // 0: thread per window position / output, 1: warp-cooperative
+  int variant;           // 0: thread per window position / output, 1: warp-cooperative,
+                         // 2: warp per row
 };
 // A'(d, i) = (Rhat Ahat Rhat^T)_{i, i + S_d} for every level-(k-1) cell i.
 template <typename T>

@@ -343,8 +343,8 @@ __global__ void __launch_bounds__(kPatchThreads, PatchOcc<T>::kMinBlocks)
 // the patch factorisations accumulate in float32).
 template <typename T>
 size_t patch_pcg_smem_bytes(const PatchPcgGeom& pg) {
-  const int nadj = 2 * pg.nhalf - pg.NB;
-  size_t b = sizeof(T) * 9 * (size_t)pg.nhalf;           // stored blocks
+  const int nadj = pg.nadj;
+  size_t b = sizeof(T) * 9 * (size_t)pg.nhalf;           // stored blocks (slots)
   b += sizeof(T) * 3 * (size_t)pg.NB;                     // shared direction vector
   b += sizeof(int) * ((size_t)nadj + pg.NB + 1);          // adjacency (packed) + row pointers
   b += sizeof(int) * 2 * (size_t)pg.NB;                   // parent index, active unknowns
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(256) k_patch_pcg(const T* __restrict__ Ahat,
                                                    double tol2, int max_iter, int* iter_stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = g.NB;
-  const int nadj = 2 * g.nhalf - NB;
+  const int nadj = g.nadj;
   T* blk = reinterpret_cast<T*>(smem_raw);
   T* sv = blk + 9 * g.nhalf;
   int* sadj = reinterpret_cast<int*>(sv + 3 * NB);
@@ -439,7 +439,8 @@ __global__ void __launch_bounds__(256) k_patch_pcg(const T* __restrict__ Ahat,
     // reads in flight per thread, more L1 wavefronts).
     if (!kHalfWarpGather) {
       for (int h = tid; h < g.nhalf; h += blockDim.x) {
-        const int4 e = g.half[h];  // (ja, jb, o, -)
+        const int4 e = g.half[h];  // (ja, jb, o, -); ja < 0 marks a padding slot
+        if (e.x < 0) continue;
         const int nra = mj[e.x], nrb = mj[e.y];
         const T* src = Ahat + ((int64_t)e.z * np + (nra > 0 ? pj[e.x] : 0)) * 16;
 #pragma unroll
@@ -455,7 +456,8 @@ __global__ void __launch_bounds__(256) k_patch_pcg(const T* __restrict__ Ahat,
       const int hw = tid >> 4, nhw = blockDim.x >> 4;
       const int a = (tid >> 2) & 3, b = tid & 3;
       for (int h = hw; h < g.nhalf; h += nhw) {
-        const int4 e = g.half[h];  // (ja, jb, o, -)
+        const int4 e = g.half[h];  // (ja, jb, o, -); ja < 0 marks a padding slot
+        if (e.x < 0) continue;
         const int nra = mj[e.x], nrb = mj[e.y];
         if (a < 3 && b < 3) {
           T v = T(0);

@@ -8,6 +8,24 @@
 
 namespace gb {
 
+// 4-element loads as 128-bit transactions (rows of Rhat / RT and level
+// vectors are 16-byte aligned: 4 T per neighbour or cell)
+__device__ __forceinline__ void ld4(const float* p, float* b) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  b[0] = v.x;
+  b[1] = v.y;
+  b[2] = v.z;
+  b[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* b) {
+  const double2 v0 = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 v1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  b[0] = v0.x;
+  b[1] = v0.y;
+  b[2] = v1.x;
+  b[3] = v1.y;
+}
+
 // ---------------------------------------------------------------- restriction
 // One warp per coarse row i (lanes over the neighbours j, so the row of R-hat
 // is read with unit stride); the four warps of a CTA hold the four children
@@ -26,11 +44,22 @@ __global__ void __launch_bounds__(128) k_restrict(const T* __restrict__ Rhat, in
     int x, y;
     demorton((uint32_t)i, x, y);
     const T* row = Rhat + i * 4 * NB;
-    for (int j = lane; j < NB; j += 32) {
-      const int p = shift_cell(x, y, nbr[j].x, nbr[j].y, Lpar, nrow);
-      if (p < 0) continue;
+    // two neighbours per lane per pass, loads issued before use
+    for (int j0 = lane; j0 < NB; j0 += 64) {
+      const int j1 = j0 + 32;
+      const int p0 = shift_cell(x, y, nbr[j0].x, nbr[j0].y, Lpar, nrow);
+      const int p1 = j1 < NB ? shift_cell(x, y, nbr[j1].x, nbr[j1].y, Lpar, nrow) : -1;
+      T r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0}, g0[4] = {0, 0, 0, 0}, g1[4] = {0, 0, 0, 0};
+      if (p0 >= 0) {
+        ld4(row + 4 * j0, r0);
+        ld4(ghat + 4 * (int64_t)p0, g0);
+      }
+      if (p1 >= 0) {
+        ld4(row + 4 * j1, r1);
+        ld4(ghat + 4 * (int64_t)p1, g1);
+      }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc += row[4 * j + c] * ghat[4 * p + c];
+      for (int c = 0; c < 4; ++c) acc += r0[c] * g0[c] + r1[c] * g1[c];
     }
   }
 #pragma unroll
@@ -112,13 +141,24 @@ __global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ RT, int N
     int x, y;
     demorton((uint32_t)p, x, y);
     const T* row = RT + p * 4 * NB;
-    for (int j = lane; j < NB; j += 32) {
-      const int i = shift_cell(x, y, -nbr[j].x, -nbr[j].y, Lpar, npar);
-      if (i < 0) continue;
-      const T vi = v[i];
-      h0 += row[4 * j] * vi;
-      h1 += row[4 * j + 1] * vi;
-      h2 += row[4 * j + 2] * vi;
+    // two neighbours per lane per pass, loads issued before use
+    for (int j0 = lane; j0 < NB; j0 += 64) {
+      const int j1 = j0 + 32;
+      const int i0 = shift_cell(x, y, -nbr[j0].x, -nbr[j0].y, Lpar, npar);
+      const int i1 = j1 < NB ? shift_cell(x, y, -nbr[j1].x, -nbr[j1].y, Lpar, npar) : -1;
+      T r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0};
+      T v0 = 0, v1 = 0;
+      if (i0 >= 0) {
+        ld4(row + 4 * j0, r0);
+        v0 = v[i0];
+      }
+      if (i1 >= 0) {
+        ld4(row + 4 * j1, r1);
+        v1 = v[i1];
+      }
+      h0 += r0[0] * v0 + r1[0] * v1;
+      h1 += r0[1] * v0 + r1[1] * v1;
+      h2 += r0[2] * v0 + r1[2] * v1;
     }
   }
 #pragma unroll
@@ -256,34 +296,42 @@ template void launch_level1_solve<float>(const double*, const float*, float*, cu
 template void launch_level1_solve<double>(const double*, const double*, double*, cudaStream_t);
 
 // ---------------------------------------------------------------- outer float64
-__global__ void k_block_spmv64(const double* __restrict__ A, const int2* __restrict__ off,
-                               int noff, int Lpar, int64_t npar, const double* __restrict__ xv,
-                               double* yv) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// y = Ahat x on the float64 block stencil.  Four lanes per parent, lane a
+// owning block row a: for each offset the 8 parents of a warp read 8
+// consecutive 128-byte blocks (one coalesced 1 KB stream), the neighbour's
+// four x values are a broadcast, and row a is written by its own lane.
+__global__ void __launch_bounds__(256) k_block_spmv64(const double* __restrict__ A,
+                                                      const int2* __restrict__ off, int noff,
+                                                      int Lpar, int64_t npar,
+                                                      const double* __restrict__ xv, double* yv) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = t >> 2;
+  const int a = (int)(t & 3);
   if (p >= npar) return;
   int x, y;
   demorton((uint32_t)p, x, y);
-  double y0 = 0, y1 = 0, y2 = 0, y3 = 0;
+  double acc = 0;
+  const double2 zero = make_double2(0.0, 0.0);
+#pragma unroll 3
   for (int o = 0; o < noff; ++o) {
+    // predicated rather than branched, so unrolled iterations keep their
+    // loads in flight together
     const int q = shift_cell(x, y, off[o].x, off[o].y, Lpar, npar);
-    if (q < 0) continue;
-    const double* b = A + ((int64_t)o * npar + p) * 16;
-    const double x0 = xv[4 * q], x1 = xv[4 * q + 1], x2 = xv[4 * q + 2], x3 = xv[4 * q + 3];
-    y0 += b[0] * x0 + b[1] * x1 + b[2] * x2 + b[3] * x3;
-    y1 += b[4] * x0 + b[5] * x1 + b[6] * x2 + b[7] * x3;
-    y2 += b[8] * x0 + b[9] * x1 + b[10] * x2 + b[11] * x3;
-    y3 += b[12] * x0 + b[13] * x1 + b[14] * x2 + b[15] * x3;
+    const bool ok = q >= 0;
+    const double2* row = reinterpret_cast<const double2*>(A + ((int64_t)o * npar + p) * 16 + 4 * a);
+    const double2* xq = reinterpret_cast<const double2*>(xv + 4 * (int64_t)(ok ? q : 0));
+    const double2 r0 = ok ? __ldg(row) : zero, r1 = ok ? __ldg(row + 1) : zero;
+    const double2 x0 = ok ? __ldg(xq) : zero, x1 = ok ? __ldg(xq + 1) : zero;
+    acc += r0.x * x0.x + r0.y * x0.y + r1.x * x1.x + r1.y * x1.y;
   }
-  yv[4 * p] = y0;
-  yv[4 * p + 1] = y1;
-  yv[4 * p + 2] = y2;
-  yv[4 * p + 3] = y3;
+  yv[4 * p + a] = acc;
 }
 
 void launch_block_spmv64(const double* Ahat, const int2* off, int noff, int Lpar, int64_t npar,
                          const double* x, double* y, cudaStream_t s) {
   if (npar <= 0) return;
-  { count_launch(); k_block_spmv64<<<(unsigned)((npar + 127) / 128), 128, 0, s>>>(Ahat, off, noff, Lpar, npar, x, y); }
+  const int64_t n = 4 * npar;
+  { count_launch(); k_block_spmv64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ahat, off, noff, Lpar, npar, x, y); }
 }
 
 __global__ void k_dots(int64_t n, const double* __restrict__ a0, const double* __restrict__ b0,

@@ -47,6 +47,7 @@ class Opts(ctypes.Structure):
                 ("refine_max_iter", ctypes.c_int32), ("patch_tol", ctypes.c_double),
                 ("use_graph", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("galerkin_variant", ctypes.c_int32), ("patch_gather", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 

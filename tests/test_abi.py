@@ -71,7 +71,7 @@ int main(void) {
 def test_host_only_calls(lib):
     o = lib.gamblet_default_opts()
     assert o.rho == 3.0 and o.precision == lib.FP64 and o.refine_max_iter == 50
-    assert o.autotune == 1
+    assert o.autotune == 1 and o.galerkin_variant == -1 and o.patch_gather == -1
     assert lib.gamblet_status_string(lib.ERR_NOT_SPD).startswith("matrix not")
     assert lib.gamblet_device_bytes(0) == 0
     assert lib.gamblet_kernel_stats(0) == []

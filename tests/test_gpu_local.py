@@ -195,7 +195,7 @@ def test_autotuned_shapes_are_valid_and_change_nothing_but_rounding(precision):
             for k in range(2, p.q + 1):
                 sh = nv.gamblet_launch_shapes(h, k)
                 assert sh["patch_spp"] in (1, 2, 4) and sh["patch_gather"] in (0, 1)
-                assert sh["galerkin_variant"] in (0, 1) and sh["cg_spp"] in (1, 4)
+                assert sh["galerkin_variant"] in (0, 1, 2) and sh["cg_spp"] in (1, 4)
             u = np.zeros(p.ndof)
             info = nv.Info()
             assert nv.gamblet_solve(h, p.g, u, None, info) == nv.OK
@@ -204,3 +204,31 @@ def test_autotuned_shapes_are_valid_and_change_nothing_but_rounding(precision):
         finally:
             nv.gamblet_destroy(h)
     assert rel(us[0], us[1]) < 1e-9 and rel(us[2], us[1]) < 1e-9
+
+
+@pytest.mark.parametrize("variant,gather", [(0, 0), (1, 1), (2, 0), (2, 1)])
+def test_every_galerkin_kernel_and_gather_matches_oracle(variant, gather):
+    """Each Galerkin kernel and patch-CG gather, forced on every level,
+    reproduces the oracle's localized operators (the autotuner only picks
+    among them)."""
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(64, 1e3, 14)
+    ref = gamblet_local_setup(p.A, p.cells, p.q, 3.0)
+    rp, ci, va = csr_arrays(p.A)
+    o = nv.gamblet_default_opts()
+    o.level_tol = 1e-14
+    o.level_max_iter = 5000
+    o.refine_max_iter = 0
+    o.galerkin_variant = variant
+    o.patch_gather = gather
+    h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
+    try:
+        for k in range(2, p.q + 1):
+            assert nv.gamblet_launch_shapes(h, k)["galerkin_variant"] == variant
+            assert nv.gamblet_launch_shapes(h, k)["patch_gather"] == gather
+        ops = _ops(h, p.q)
+        for k in range(2, p.q + 1):
+            assert rel(ops[("R", k)], ref["R"][k]) < 1e-10, ("R", k)
+            assert rel(ops[("A", k - 1)], ref["A"][k - 1]) < 1e-10, ("A", k - 1)
+    finally:
+        nv.gamblet_destroy(h)
