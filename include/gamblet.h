@@ -102,7 +102,7 @@ typedef struct {
                                timing candidates on a sample of each large
                                level, once per geometry and precision in a
                                process; 0: fixed rules                     */
-  int32_t galerkin_variant; /* -1: automatic; 0, 1, 2: use that Galerkin
+  int32_t galerkin_variant; /* -1: automatic; 0..3: use that Galerkin
                                kernel on every level (see
                                gamblet_launch_shapes)                      */
   int32_t patch_gather;     /* -1: automatic; 0, 1: use that patch-CG block
@@ -281,8 +281,9 @@ GAMBLET_API gamblet_status gamblet_assemble_cells(int32_t n, const int32_t* rowp
  *   shapes[0]  patch-CG threads per neighbour parent (1, 2, 4; 0 = Cholesky)
  *   shapes[1]  patch-CG block gather (0 thread per block, 1 half-warp per block)
  *   shapes[2]  Galerkin kernel (0 thread per position, 1 warp-cooperative,
- *              2 warp per row)
- *   shapes[3]  level-CG SpMV threads per parent (1: 16 x 16 tiles, 4: 8 x 8) */
+ *              2 warp per row, 3 2 x 2 row tiles)
+ *   shapes[3]  level-CG SpMV threads per parent (1: 16 x 16 tiles, 4: 8 x 8,
+ *              16: 4 x 4) */
 GAMBLET_API gamblet_status gamblet_launch_shapes(gamblet_handle h, int32_t k, int32_t* shapes);
 
 /* Number of nodes n_k = |I^(k)| and detail rows |J^(k)| at level k. */

@@ -99,6 +99,118 @@ __global__ void __launch_bounds__(256) k_galerkin_rows(const T* __restrict__ Aha
   }
 }
 
+// Four coarse rows per CTA: the 2 x 2 cells i0..i0+3 of one level-(k-2)
+// parent (row r at (r & 1, r >> 1) from the tile origin).  Phase 1: a thread
+// per position u of the tile's window box loads each block Ahat[o][origin+u]
+// once and applies it to every row whose patch reaches it (host list t1:
+// the neighbour index j of each row), accumulating t_r(u) for the four rows.
+// Phase 2: a warp per output target cell c loads the row Rhat_c once (lanes
+// over j) and forms the dot products with t_r(c + N_j) of every row r for
+// which c - r is an output offset (host list t2).  Compared with a row per
+// CTA this reads each block and each Rhat row up to four times less often.
+size_t galerkin_tile_smem_bytes(const GalerkinGeom& g, size_t elem) {
+  return elem * (16 * (size_t)g.NB + 16 * (size_t)g.tile_W * g.tile_W);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Ahat,
+                                                       const T* __restrict__ Rhat,
+                                                       const uint32_t* __restrict__ pmask,
+                                                       GalerkinGeom g, T* __restrict__ Aout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int NB = g.NB, W = g.tile_W, WW = W * W, wmin = g.tile_wmin;
+  T* rr = reinterpret_cast<T*>(smem_raw);  // [4][NB][4]
+  T* tt = rr + 16 * NB;                    // [4][WW][4]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int64_t nrow = g.nrow;
+  const int64_t t0 = g.i_begin >> 2, t1 = (g.i_end + 3) >> 2;
+  for (int64_t tile = t0 + blockIdx.x; tile < t1; tile += gridDim.x) {
+    const int64_t i0 = tile << 2;
+    int x0, y0;
+    demorton((uint32_t)i0, x0, y0);
+    bool live[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      live[r] = i0 + r >= g.i_begin && i0 + r < g.i_end && (pmask[i0 + r] & 15u);
+    for (int idx = threadIdx.x; idx < 4 * NB; idx += blockDim.x) {
+      const int r = idx / NB, j = idx - r * NB;
+      T v[4] = {T(0), T(0), T(0), T(0)};
+      if (live[r]) load_vec4(Rhat + ((i0 + r) * NB + j) * 4, v);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) rr[(r * NB + j) * 4 + c] = v[c];
+    }
+    __syncthreads();
+    // phase 1: t_r(u) = sum over stored blocks of the window
+    for (int u = threadIdx.x; u < WW; u += blockDim.x) {
+      const int uy = u / W, ux = u - uy * W;
+      const int p = shift_cell(x0, y0, ux + wmin, uy + wmin, g.Lpar, nrow);
+      T acc[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
+      if (p >= 0) {
+        const int e1 = g.t1_ptr[u + 1];
+        for (int e = g.t1_ptr[u]; e < e1; ++e) {
+          const int2 ent = g.t1[e];
+          const T* blk = Ahat + ((int64_t)ent.x * nrow + p) * 16;
+          T b[16];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) load_vec4(blk + 4 * q, b + 4 * q);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int j = ((unsigned)ent.y >> (8 * r)) & 0xffu;
+            if (j == 0xff) continue;
+            const T* rv = rr + (r * NB + j) * 4;
+            const T v0 = rv[0], v1 = rv[1], v2 = rv[2], v3 = rv[3];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+              acc[r][a] += b[4 * a] * v0 + b[4 * a + 1] * v1 + b[4 * a + 2] * v2 + b[4 * a + 3] * v3;
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tt[((size_t)r * WW + u) * 4 + c] = acc[r][c];
+    }
+    __syncthreads();
+    // phase 2: outputs A_{i0+r, c} for every target cell c
+    for (int e = warp; e < g.nt2; e += nwarp) {
+      const int4 tg = g.t2[e];
+      int d[4] = {(int)(short)(tg.z & 0xffff), tg.z >> 16, (int)(short)(tg.w & 0xffff), tg.w >> 16};
+      const int ip = shift_cell(x0, y0, tg.x, tg.y, g.Lpar, nrow);
+      const bool have = ip >= 0 && (pmask[ip] & 15u);
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+      if (have) {
+        const T* rc = Rhat + (int64_t)ip * 4 * NB;
+        for (int j = lane; j < NB; j += 32) {
+          const int ux = tg.x + g.nbr[j].x - wmin, uy = tg.y + g.nbr[j].y - wmin;
+          if ((unsigned)ux >= (unsigned)W || (unsigned)uy >= (unsigned)W) continue;
+          const int u = uy * W + ux;
+          T rv[4];
+          load_vec4(rc + 4 * j, rv);
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            if (d[r] < 0) continue;
+            const T* tv = tt + ((size_t)r * WW + u) * 4;
+            acc[r] += rv[0] * tv[0] + rv[1] * tv[1] + rv[2] * tv[2] + rv[3] * tv[3];
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        T v = acc[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && d[r] >= 0 && i0 + r >= g.i_begin && i0 + r < g.i_end)
+          Aout[(int64_t)d[r] * nrow + i0 + r] = live[r] ? v : T(0);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // One warp per coarse row, the work split as in k_galerkin_rows (lanes over
 // window positions, then over output offsets) but synchronised per warp
 // only: each warp keeps its own Rhat row and window in shared memory, so the
@@ -250,7 +362,13 @@ void launch_galerkin(const T* Ahat, const T* Rhat, const uint32_t* pmask_k, Gale
   size_t smem = sizeof(T) * 4 * ((size_t)g.NB + (size_t)g.nwin);
   int64_t grid = nrows < 65535 * 16 ? nrows : 65535 * 16;
   count_launch();
-  if (g.variant == 2) {
+  if (g.variant == 3) {
+    const size_t st = galerkin_tile_smem_bytes(g, sizeof(T));
+    cudaFuncSetAttribute(k_galerkin_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st);
+    const int64_t nt = ((g.i_end + 3) >> 2) - (g.i_begin >> 2);
+    k_galerkin_tile<T><<<(unsigned)(nt < 65535 * 16 ? nt : 65535 * 16), 256, st, s>>>(
+        Ahat, Rhat, pmask_k, g, Aout);
+  } else if (g.variant == 2) {
     const size_t smem8 = 8 * smem;  // eight warps, one row each
     cudaFuncSetAttribute(k_galerkin_warprow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem8);

@@ -178,6 +178,14 @@ struct SymLevel {
   std::vector<int> l1_ptr, l2_ptr;
   std::vector<int2> l1_pairs, l2_pairs;
   std::vector<int> map_next;      // conversion map to level k-1 blocks (or level-1 map)
+  // 2 x 2 row tiles (k_galerkin_tile): window positions u of the tile as a
+  // box [wmin, wmin + W)^2 relative to the tile origin; per u the offsets o
+  // with, for each of the four rows, the neighbour index j (0xff = none);
+  // output targets c with the index d in Sp of c - row, per row (-1 = none)
+  int tile_wmin = 0, tile_W = 0;
+  std::vector<int> t1_ptr;
+  std::vector<int2> t1;           // (o, j of rows 0..3 packed in bytes)
+  std::vector<int4> t2;           // (c.x, c.y, d0 | d1 << 16, d2 | d3 << 16)
 };
 
 // ---------------------------------------------------------------- handle
@@ -417,6 +425,47 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
   for (int d = 0; d < S.Sp.size(); ++d) {
     S.l2_ptr[d + 1] = S.l2_ptr[d] + (int)l2[d].size();
     S.l2_pairs.insert(S.l2_pairs.end(), l2[d].begin(), l2[d].end());
+  }
+  // 2 x 2 tiles: row r sits at (r & 1, r >> 1) from the tile origin
+  int wmin = 0, wmax = 0;
+  for (const int2& w : S.WIN.v) {
+    wmin = std::min(wmin, std::min(w.x, w.y));
+    wmax = std::max(wmax, std::max(w.x, w.y));
+  }
+  const int W = wmax - wmin + 2;
+  S.tile_wmin = wmin;
+  S.tile_W = W;
+  S.t1_ptr.assign((size_t)W * W + 1, 0);
+  for (int uy = 0; uy < W; ++uy)
+    for (int ux = 0; ux < W; ++ux) {
+      const int u = uy * W + ux;
+      for (int o = 0; o < O_k.size(); ++o) {
+        uint32_t packed = 0;
+        bool any = false;
+        for (int r = 0; r < 4; ++r) {
+          // t_i(w) gathers A_hat[o][i + w] R_hat_i[j] with N_j = w + O_o
+          const int wx = ux + wmin - (r & 1), wy = uy + wmin - (r >> 1);
+          int j = S.WIN.find(wx, wy) >= 0 ? N.find(wx + O_k.v[o].x, wy + O_k.v[o].y) : -1;
+          if (j > 254) fail(GAMBLET_ERR_UNSUPPORTED, "neighbourhood too large for tiled Galerkin");
+          if (j >= 0) any = true;
+          packed |= (uint32_t)(j >= 0 ? j : 0xff) << (8 * r);
+        }
+        if (any) S.t1.push_back(make_int2(o, (int)packed));
+      }
+      S.t1_ptr[u + 1] = (int)S.t1.size();
+    }
+  std::set<std::pair<int, int>> targets;
+  for (int r = 0; r < 4; ++r)
+    for (const int2& d : S.Sp.v) targets.insert({d.y + (r >> 1), d.x + (r & 1)});
+  for (const auto& c : targets) {
+    const int cx = c.second, cy = c.first;
+    int dr[4];
+    for (int r = 0; r < 4; ++r) dr[r] = S.Sp.find(cx - (r & 1), cy - (r >> 1));
+    if (S.Sp.size() > 32767) fail(GAMBLET_ERR_UNSUPPORTED, "output stencil too large for tiled Galerkin");
+    auto pack = [](int lo, int hi) {
+      return (int)(((uint32_t)lo & 0xffffu) | ((uint32_t)hi << 16));
+    };
+    S.t2.push_back(make_int4(cx, cy, pack(dr[0], dr[1]), pack(dr[2], dr[3])));
   }
   return S;
 }
@@ -834,8 +883,9 @@ void tune_galerkin_variant(gamblet_ctx* h, int k, GalerkinGeom& gg, const T* Aha
     gt.i_begin = (gg.nrow / 2 / kTuneSampleRows) * kTuneSampleRows;
     gt.i_end = std::min(gt.i_begin + kTuneSampleRows, gg.nrow);
     float best = 1e30f;
-    for (int cand : {0, 1, 2}) {
+    for (int cand : {0, 1, 2, 3}) {
       if (cand == 2 && 8 * sizeof(T) * 4 * ((size_t)gg.NB + gg.nwin) > 227 * 1024) continue;
+      if (cand == 3 && galerkin_tile_smem_bytes(gg, sizeof(T)) > 227 * 1024) continue;
       gt.variant = cand;
       const float ms = time_on_stream(s, [&] {
         launch_galerkin<T>(Ahat, Rhat, h->lv[k].pmask, gt, Acell, s);
@@ -932,18 +982,25 @@ void setup_local(gamblet_ctx* h) {
     gg.nrow = L.npar;
     gg.i_begin = 0;
     gg.i_end = L.npar;
-    // wide stencils (long block lists per window position) favour the
-    // warp-cooperative kernel, short ones a warp per row; the autotuner
+    gg.tile_wmin = S.tile_wmin;
+    gg.tile_W = S.tile_W;
+    gg.t1_ptr = P.upload(S.t1_ptr, s);
+    gg.t1 = P.upload(S.t1, s);
+    gg.nt2 = (int)S.t2.size();
+    gg.t2 = P.upload(S.t2, s);
+    // 2 x 2 row tiles while their window boxes stay small enough for
+    // several CTAs per SM, else the warp-cooperative kernel; the autotuner
     // decides on large levels
-    gg.variant = L.noff > 32 ? 1 : 2;
-    if (gg.variant == 2 && 8 * sizeof(T) * 4 * ((size_t)NB + gg.nwin) > 227 * 1024) gg.variant = 0;
+    gg.variant = galerkin_tile_smem_bytes(gg, sizeof(T)) <= 100 * 1024 ? 3 : 1;
     if (sizeof(T) * 4 * ((size_t)NB + (size_t)gg.nwin) > 227 * 1024)
       fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin window exceeds shared memory");
     T* Acell = P.alloc<T>((int64_t)gg.nout * L.npar);
-    if (h->opts.galerkin_variant >= 0 && h->opts.galerkin_variant <= 2) {
+    if (h->opts.galerkin_variant >= 0 && h->opts.galerkin_variant <= 3) {
       gg.variant = h->opts.galerkin_variant;
       if (gg.variant == 2 && 8 * sizeof(T) * 4 * ((size_t)NB + gg.nwin) > 227 * 1024)
         fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin warp-per-row window exceeds shared memory");
+      if (gg.variant == 3 && galerkin_tile_smem_bytes(gg, sizeof(T)) > 227 * 1024)
+        fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin tile window exceeds shared memory");
     } else {
       tune_galerkin_variant<T>(h, k, gg, (const T*)L.Ahat, Rhat, Acell);
     }
@@ -1072,12 +1129,12 @@ int tuned_cg_spp(gamblet_ctx* h, int k, const CgLevel& c) {
   sc.active = 1;
   CgScalars* sc_d = h->pool.upload(std::vector<CgScalars>{sc}, s);
   float best = 1e30f;
-  for (int spp : {1, 4}) {
+  for (int spp : {1, 4, 16}) {
     CgLevel c1 = c;
     c1.spp = spp;
     c1.block_begin = 0;
     c1.spmv_begin = 0;
-    const int tmax = spp == 4 ? 8 : 16;
+    const int tmax = cg_tile_side(spp);
     const int ts = std::min(c1.Lpar, tmax) + 2 * c1.R;
     if (cg_spmv_smem_bytes(ts, sizeof(T)) > 227 * 1024) continue;
     prepare_cg_spmv<T>(ts);
@@ -1153,12 +1210,13 @@ void alloc_solve(gamblet_ctx* h) {
       c.b = L.ghat;
       c.block_begin = blocks;
       blocks += (int)((L.npar + 255) / 256);
-      // wide stencils: four threads per parent over 8 x 8 tiles (more loads in
-      // flight); the autotuner may overrule the rule on large levels
-      c.spp = L.noff > 32 ? 4 : 1;
+      // wide stencils: four threads per parent over 8 x 8 tiles, or sixteen
+      // over 4 x 4 tiles for the widest (more CTAs and more loads in flight
+      // per byte); the autotuner may overrule the rule on large levels
+      c.spp = L.noff > 128 ? 16 : (L.noff > 32 ? 4 : 1);
       c.spp = tuned_cg_spp<T>(h, k, c);
       L.shape[3] = c.spp;
-      const int tmax = c.spp == 4 ? 8 : 16;
+      const int tmax = cg_tile_side(c.spp);
       c.spmv_begin = sblocks;
       sblocks += (int)((L.npar + tmax * tmax - 1) / (tmax * tmax));
       max_ts = std::max(max_ts, std::min(c.Lpar, tmax) + 2 * L.R);
@@ -1554,8 +1612,8 @@ gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
       fail(GAMBLET_ERR_INVALID_ARG, "unknown precision");
     if (h->opts.nbr_rule != 0 && h->opts.nbr_rule != 1)
       fail(GAMBLET_ERR_INVALID_ARG, "nbr_rule must be 0 or 1");
-    if (h->opts.galerkin_variant < -1 || h->opts.galerkin_variant > 2)
-      fail(GAMBLET_ERR_INVALID_ARG, "galerkin_variant must be -1, 0, 1 or 2");
+    if (h->opts.galerkin_variant < -1 || h->opts.galerkin_variant > 3)
+      fail(GAMBLET_ERR_INVALID_ARG, "galerkin_variant must be -1, 0, 1, 2 or 3");
     if (h->opts.patch_gather < -1 || h->opts.patch_gather > 1)
       fail(GAMBLET_ERR_INVALID_ARG, "patch_gather must be -1, 0 or 1");
     if (h->exact && q > 7)

@@ -125,8 +125,15 @@ struct GalerkinGeom {
   int64_t nrow;          // stored level-(k-1) cells (4^(k-1) for a full square)
   int64_t i_begin, i_end;  // rows computed: [i_begin, i_end) (all: 0, nrow)
   int variant;           // 0: thread per window position / output, 1: warp-cooperative,
-                         // 2: warp per row
+                         // 2: warp per row, 3: 2 x 2 row tiles
+  int tile_wmin, tile_W; // tiles: window box [wmin, wmin + W)^2 from the tile origin
+  const int* t1_ptr;     // W * W + 1
+  const int2* t1;        // (o, j per row packed in bytes, 0xff = none)
+  int nt2;
+  const int4* t2;        // (c.x, c.y, d0 | d1 << 16, d2 | d3 << 16), d = -1: none
 };
+// Shared memory of k_galerkin_tile: four Rhat rows and four window boxes.
+size_t galerkin_tile_smem_bytes(const GalerkinGeom& g, size_t elem);
 // A'(d, i) = (Rhat Ahat Rhat^T)_{i, i + S_d} for every level-(k-1) cell i.
 template <typename T>
 void launch_galerkin(const T* Ahat, const T* Rhat, const uint32_t* pmask_k, GalerkinGeom g,
@@ -190,6 +197,10 @@ struct CgScalars {
   int active, iters;
 };
 size_t cg_spmv_smem_bytes(int max_ts, size_t elem);
+// Side of the square parent tile of one level-CG SpMV CTA (256 threads):
+// 16 with one thread per parent, 8 with four, 4 with sixteen (wide stencils:
+// more CTAs per level and more lanes splitting the offsets).
+__host__ __device__ inline int cg_tile_side(int spp) { return spp >= 16 ? 4 : (spp >= 4 ? 8 : 16); }
 template <typename T>
 void prepare_cg_spmv(int max_ts);
 template <typename T>

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) k_cg_spmv(const CgLevel* __restrict__ lv,
   if (!sc[l].active) return;
   const CgLevel L = lv[l];
   const int spp = L.spp;
-  const int tmax = spp == 4 ? 8 : 16;
+  const int tmax = cg_tile_side(spp);
   const int tile = L.Lpar < tmax ? L.Lpar : tmax;
   const int R = L.R;
   const int TS = tile + 2 * R;
@@ -155,14 +155,26 @@ __global__ void __launch_bounds__(256) k_cg_spmv(const CgLevel* __restrict__ lv,
     ly = py - y0 + R;
     const T* Bd = (const T*)L.Bd;
     const int64_t np = L.npar;
-    for (int o = sub; o < L.noff; o += spp) {
+    // two offsets per pass: their 18 matrix loads are in flight together
+    for (int o = sub; o < L.noff; o += 2 * spp) {
+      const int o2 = o + spp;
+      const bool two = o2 < L.noff;
       const int2 d = L.off[o];
-      const int c = (ly + d.y) * TS + lx + d.x;
-      const T a0 = xs[c], a1 = xs[TS * TS + c], a2 = xs[2 * TS * TS + c];
+      const int2 d2 = L.off[two ? o2 : o];
       const T* B = Bd + (int64_t)o * 9 * np + p;
-      y0v += B[0] * a0 + B[np] * a1 + B[2 * np] * a2;
-      y1v += B[3 * np] * a0 + B[4 * np] * a1 + B[5 * np] * a2;
-      y2v += B[6 * np] * a0 + B[7 * np] * a1 + B[8 * np] * a2;
+      const T* B2 = Bd + (int64_t)(two ? o2 : o) * 9 * np + p;
+      T b[9], b2[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) b[e] = B[e * np];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) b2[e] = two ? B2[e * np] : T(0);
+      const int c = (ly + d.y) * TS + lx + d.x;
+      const int c2 = (ly + d2.y) * TS + lx + d2.x;
+      const T a0 = xs[c], a1 = xs[TS * TS + c], a2 = xs[2 * TS * TS + c];
+      const T e0 = xs[c2], e1 = xs[TS * TS + c2], e2 = xs[2 * TS * TS + c2];
+      y0v += b[0] * a0 + b[1] * a1 + b[2] * a2 + b2[0] * e0 + b2[1] * e1 + b2[2] * e2;
+      y1v += b[3] * a0 + b[4] * a1 + b[5] * a2 + b2[3] * e0 + b2[4] * e1 + b2[5] * e2;
+      y2v += b[6] * a0 + b[7] * a1 + b[8] * a2 + b2[6] * e0 + b2[7] * e1 + b2[8] * e2;
     }
   }
   for (int o = 1; o < spp; o <<= 1) {

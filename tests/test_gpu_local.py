@@ -195,7 +195,7 @@ def test_autotuned_shapes_are_valid_and_change_nothing_but_rounding(precision):
             for k in range(2, p.q + 1):
                 sh = nv.gamblet_launch_shapes(h, k)
                 assert sh["patch_spp"] in (1, 2, 4) and sh["patch_gather"] in (0, 1)
-                assert sh["galerkin_variant"] in (0, 1, 2) and sh["cg_spp"] in (1, 4)
+                assert sh["galerkin_variant"] in (0, 1, 2, 3) and sh["cg_spp"] in (1, 4, 16)
             u = np.zeros(p.ndof)
             info = nv.Info()
             assert nv.gamblet_solve(h, p.g, u, None, info) == nv.OK
@@ -206,7 +206,7 @@ def test_autotuned_shapes_are_valid_and_change_nothing_but_rounding(precision):
     assert rel(us[0], us[1]) < 1e-9 and rel(us[2], us[1]) < 1e-9
 
 
-@pytest.mark.parametrize("variant,gather", [(0, 0), (1, 1), (2, 0), (2, 1)])
+@pytest.mark.parametrize("variant,gather", [(0, 0), (1, 1), (2, 0), (2, 1), (3, 0)])
 def test_every_galerkin_kernel_and_gather_matches_oracle(variant, gather):
     """Each Galerkin kernel and patch-CG gather, forced on every level,
     reproduces the oracle's localized operators (the autotuner only picks
@@ -232,3 +232,63 @@ def test_every_galerkin_kernel_and_gather_matches_oracle(variant, gather):
             assert rel(ops[("A", k - 1)], ref["A"][k - 1]) < 1e-10, ("A", k - 1)
     finally:
         nv.gamblet_destroy(h)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_galerkin_kernels_on_ragged_and_prefix_domains(variant):
+    """Every Galerkin kernel on a domain with holes and on one whose cells
+    fill only a Morton prefix (rows of a tile or window missing)."""
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(32, 1e3, 15)
+    x, y = p.cells[:, 0], p.cells[:, 1]
+    masks = [~((x >= 10) & (x <= 17) & (y >= 12) & (y <= 14)) & ~((x == 3) & (y == 29)),
+             ~((x >= 16) & (y >= 16)) & ~((x >= 9) & (x <= 11) & (y <= 4))]
+    for keep in masks:
+        A, g, cells = drop_nodes(p, keep)
+        ref = gamblet_local_setup(A, cells, p.q, 3.0)
+        rp, ci, va = csr_arrays(A)
+        o = nv.gamblet_default_opts()
+        o.level_tol = 1e-14
+        o.level_max_iter = 5000
+        o.refine_max_iter = 0
+        o.galerkin_variant = variant
+        h = nv.gamblet_setup(rp, ci, va, p.q, cells, o)
+        try:
+            ops = _ops(h, p.q)
+            for k in range(2, p.q + 1):
+                assert rel(ops[("R", k)], ref["R"][k]) < 1e-10, ("R", k)
+                assert rel(ops[("A", k - 1)], ref["A"][k - 1]) < 1e-10, ("A", k - 1)
+        finally:
+            nv.gamblet_destroy(h)
+
+
+@pytest.mark.parametrize("variant", [-1, 1, 3])
+def test_rho4_operators_match_oracle(variant):
+    """rho = 4 (89 neighbour parents, wider windows and stencils) in the
+    mixed path, with the automatic and the forced Galerkin kernels; float32
+    operators against the float64 oracle.  The float64 path stages the
+    patch blocks of rho = 4 beyond shared memory and refuses cleanly."""
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(64, 1e3, 16)
+    ref = gamblet_local_setup(p.A, p.cells, p.q, 4.0)
+    rp, ci, va = csr_arrays(p.A)
+    o = nv.gamblet_default_opts()
+    o.rho = 4.0
+    o.precision = nv.MIXED
+    o.patch_tol = 1e-7
+    o.level_tol = 1e-7
+    o.level_max_iter = 5000
+    o.refine_max_iter = 0
+    o.galerkin_variant = variant
+    h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
+    try:
+        ops = _ops(h, p.q)
+        for k in range(2, p.q + 1):
+            assert rel(ops[("R", k)], ref["R"][k]) < 1e-4, ("R", k)
+            assert rel(ops[("A", k - 1)], ref["A"][k - 1]) < 1e-4, ("A", k - 1)
+    finally:
+        nv.gamblet_destroy(h)
+    o.precision = nv.FP64
+    with pytest.raises(nv.GambletError) as e:
+        nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
+    assert e.value.status == nv.ERR_UNSUPPORTED
