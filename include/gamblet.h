@@ -105,8 +105,8 @@ typedef struct {
   int32_t galerkin_variant; /* -1: automatic; 0..3: use that Galerkin
                                kernel on every level (see
                                gamblet_launch_shapes)                      */
-  int32_t patch_gather;     /* -1: automatic; 0, 1: use that patch-CG block
-                               gather on every level                       */
+  int32_t patch_gather;     /* -1: automatic; 0, 1, 2: use that patch-CG
+                               block gather on every level                 */
   void* stream;             /* cudaStream_t                                */
 } gamblet_opts;
 
@@ -279,7 +279,8 @@ GAMBLET_API gamblet_status gamblet_assemble_cells(int32_t n, const int32_t* rowp
 /* Launch shapes the setup used at level k (2 <= k <= q, localized
  * transform), chosen by the autotuner or by the fixed rules:
  *   shapes[0]  patch-CG threads per neighbour parent (1, 2, 4; 0 = Cholesky)
- *   shapes[1]  patch-CG block gather (0 thread per block, 1 half-warp per block)
+ *   shapes[1]  patch-CG block gather (0 thread per block, 1 half-warp per block,
+ *              2 four lanes per block)
  *   shapes[2]  Galerkin kernel (0 thread per position, 1 warp-cooperative,
  *              2 warp per row, 3 2 x 2 row tiles)
  *   shapes[3]  level-CG SpMV threads per parent (1: 16 x 16 tiles, 4: 8 x 8,

@@ -5,7 +5,7 @@ timing and profiling runs:
                                    [--rho 3] [--contrast 1e4] [--seed 0]
                                    [--repeat 1] [--profile] [--capture-last]
                                    [--no-autotune] [--galerkin-variant -1|0|1|2]
-                                   [--patch-gather -1|0|1]
+                                   [--patch-gather -1|0|1|2]
 
 Prints, for the last of `repeat` setup + solve passes, the setup and solve
 device times, the outer iterations and the final relative residual

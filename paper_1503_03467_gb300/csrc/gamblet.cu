@@ -830,7 +830,7 @@ double patch_flops(gamblet_ctx* h, int k) {
 }
 
 // Patch-CG launch shape at level k: lanes per neighbour parent (1, 2, 4)
-// and block gather (thread per block or half-warp per block), timed on a
+// and block gather (thread, half-warp or four lanes per block), timed on a
 // Morton block of kTuneSample coarse cells in the middle of the level (its
 // Rhat rows are overwritten by the full launch that follows).
 template <typename T>
@@ -846,9 +846,9 @@ void tune_patch_shape(gamblet_ctx* h, int k, PatchPcgGeom& gp, T* Rhat) {
     gt.i_begin = (gp.npatch / 2 / kTuneSample) * kTuneSample;
     gt.i_end = std::min(gt.i_begin + kTuneSample, gp.npatch);
     float best = 1e30f;
-    code = gp.spp * 2 + gp.gather;
+    code = gp.spp * 4 + gp.gather;
     for (int spp : {1, 2, 4})
-      for (int gather : {0, 1}) {
+      for (int gather : {0, 1, 2}) {
         if (gp.NB * spp > 256) continue;
         gt.spp = spp;
         gt.gather = gather;
@@ -858,13 +858,13 @@ void tune_patch_shape(gamblet_ctx* h, int k, PatchPcgGeom& gp, T* Rhat) {
         });
         if (ms < best) {
           best = ms;
-          code = spp * 2 + gather;
+          code = spp * 4 + gather;
         }
       }
     tune_store(key, code);
   }
-  gp.spp = code / 2;
-  gp.gather = code % 2;
+  gp.spp = code / 4;
+  gp.gather = code % 4;
 }
 
 // Galerkin kernel of level k (k_galerkin_rows, k_galerkin_warp or
@@ -947,11 +947,11 @@ void setup_local(gamblet_ctx* h) {
     } else {
       PatchPcgGeom gp{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar, (int)pl.half.size(),
                       P.upload(pl.half, s), (int)pl.adj.size(), P.upload(pl.adj_ptr, s),
-                      P.upload(pl.adj, s), P.upload(pl.diag_h, s), pl.spp, 0, L.npar, 0};
+                      P.upload(pl.adj, s), P.upload(pl.diag_h, s), pl.spp, 0, L.npar, 2};
       if (patch_pcg_smem_bytes<T>(gp) > 227 * 1024)
         fail(GAMBLET_ERR_UNSUPPORTED, "patch blocks exceed shared memory; lower rho");
       tune_patch_shape<T>(h, k, gp, Rhat);
-      if (h->opts.patch_gather == 0 || h->opts.patch_gather == 1) gp.gather = h->opts.patch_gather;
+      if (h->opts.patch_gather >= 0 && h->opts.patch_gather <= 2) gp.gather = h->opts.patch_gather;
       L.shape[0] = gp.spp;
       L.shape[1] = gp.gather;
       // flops are added after setup from the measured iteration counts
@@ -1614,8 +1614,8 @@ gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
       fail(GAMBLET_ERR_INVALID_ARG, "nbr_rule must be 0 or 1");
     if (h->opts.galerkin_variant < -1 || h->opts.galerkin_variant > 3)
       fail(GAMBLET_ERR_INVALID_ARG, "galerkin_variant must be -1, 0, 1, 2 or 3");
-    if (h->opts.patch_gather < -1 || h->opts.patch_gather > 1)
-      fail(GAMBLET_ERR_INVALID_ARG, "patch_gather must be -1, 0 or 1");
+    if (h->opts.patch_gather < -1 || h->opts.patch_gather > 2)
+      fail(GAMBLET_ERR_INVALID_ARG, "patch_gather must be -1, 0, 1 or 2");
     if (h->exact && q > 7)
       fail(GAMBLET_ERR_UNSUPPORTED, "the exact (rho <= 0) transform is limited to q <= 7");
     int dev = 0;

@@ -101,7 +101,8 @@ struct PatchPcgGeom {
   const int* diag_h;    // NB: stored block of (j, j)
   int spp;              // threads per neighbour parent: 1, 2 or 4
   int64_t i_begin, i_end;  // coarse cells solved: [i_begin, i_end) (all: 0, npatch)
-  int gather;           // block gather: 0 = thread per block, 1 = half-warp per block
+  int gather;           // block gather: 0 thread per block, 1 half-warp per block,
+                        // 2 four lanes (one row each) per block
 };
 template <typename T>
 void launch_patch_pcg(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g, T* Rhat, double tol,

@@ -354,6 +354,23 @@ size_t patch_pcg_smem_bytes(const PatchPcgGeom& pg) {
 template size_t patch_pcg_smem_bytes<float>(const PatchPcgGeom&);
 template size_t patch_pcg_smem_bytes<double>(const PatchPcgGeom&);
 
+// One 4-entry row of a 4x4 block (16-byte aligned) as vector loads.
+__device__ __forceinline__ void load_row4(const float* p, float* r) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  r[0] = v.x;
+  r[1] = v.y;
+  r[2] = v.z;
+  r[3] = v.w;
+}
+__device__ __forceinline__ void load_row4(const double* p, double* r) {
+  const double2 v0 = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 v1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  r[0] = v0.x;
+  r[1] = v0.y;
+  r[2] = v1.x;
+  r[3] = v1.y;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum_t(T v) {
 #pragma unroll
@@ -381,7 +398,7 @@ __device__ __forceinline__ void block_sum2(T& a, T& b, T* red) {
   __syncthreads();
 }
 
-template <typename T, bool kHalfWarpGather>
+template <typename T, int kGather>
 __global__ void __launch_bounds__(256) k_patch_pcg(const T* __restrict__ Ahat,
                                                    const uint32_t* __restrict__ pmask,
                                                    PatchPcgGeom g, T* __restrict__ Rhat,
@@ -433,11 +450,43 @@ __global__ void __launch_bounds__(256) k_patch_pcg(const T* __restrict__ Ahat,
     }
     __syncthreads();
     // ---- gather the stored blocks (identity on inactive diagonal entries).
-    // kHalfWarpGather: a half-warp per block, lane (a, b) reads entry (a, b)
-    // of the 4x4 block, so each block is one coalesced read of its three
-    // detail rows; otherwise a thread per block with nine scalar reads (more
-    // reads in flight per thread, more L1 wavefronts).
-    if (!kHalfWarpGather) {
+    // kGather 0: a thread per block with nine scalar reads (many reads in
+    // flight per thread, one L1 wavefront per scattered sector); 1: a
+    // half-warp per block, lane (a, b) reading entry (a, b), one coalesced
+    // read per block; 2: four lanes per block, one 16-byte row each, four
+    // blocks in flight per group.
+    if (kGather == 2) {
+      // four lanes per block, lane a loading row a as one 16-byte vector;
+      // each group of four lanes keeps four blocks in flight
+      const int grp = tid >> 2, ngrp = blockDim.x >> 2, a = tid & 3;
+      for (int h0 = grp; h0 < g.nhalf; h0 += 4 * ngrp) {
+        T row[4][4];
+        int4 ent[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int h = h0 + u * ngrp;
+          ent[u] = h < g.nhalf ? g.half[h] : make_int4(-1, -1, 0, 0);
+          const int nra = ent[u].x >= 0 ? mj[ent[u].x] : 0;
+          const int nrb = ent[u].x >= 0 ? mj[ent[u].y] : 0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) row[u][b] = T(0);
+          if (a < nra && nrb > 0)
+            load_row4(Ahat + ((int64_t)ent[u].z * np + pj[ent[u].x]) * 16 + 4 * a, row[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int h = h0 + u * ngrp;
+          if (h >= g.nhalf || ent[u].x < 0 || a >= 3) continue;
+          const int nra = mj[ent[u].x], nrb = mj[ent[u].y];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            T v = (a < nra && b < nrb) ? row[u][b] : T(0);
+            if (ent[u].x == ent[u].y && a == b && a >= nra) v = T(1);
+            blk[9 * h + 3 * a + b] = v;
+          }
+        }
+      }
+    } else if (kGather == 0) {
       for (int h = tid; h < g.nhalf; h += blockDim.x) {
         const int4 e = g.half[h];  // (ja, jb, o, -); ja < 0 marks a padding slot
         if (e.x < 0) continue;
@@ -594,7 +643,7 @@ void launch_patch_pcg(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g, T*
   const int64_t nsolve = g.i_end - g.i_begin;
   if (nsolve <= 0) return;
   const size_t smem = patch_pcg_smem_bytes<T>(g);
-  auto kern = g.gather ? k_patch_pcg<T, true> : k_patch_pcg<T, false>;
+  auto kern = g.gather == 2 ? k_patch_pcg<T, 2> : (g.gather == 1 ? k_patch_pcg<T, 1> : k_patch_pcg<T, 0>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int threads = ((g.NB * g.spp + 31) / 32) * 32;
   int per_sm = 1;
