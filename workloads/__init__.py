@@ -11,6 +11,8 @@ from .rough import (  # noqa: F401
     Problem,
     K_REF,
     assemble_q1,
+    assemble_q1_mass,
+    M_REF,
     cell_corner_dofs,
     example1_coefficient,
     example1_rhs,

@@ -76,9 +76,11 @@ def interior_cells(n: int) -> np.ndarray:
     return np.stack([ix.ravel(), iy.ravel()], axis=1).astype(np.int32)
 
 
-def assemble_q1(a: np.ndarray) -> sp.csr_matrix:
+def assemble_q1(a: np.ndarray, element: np.ndarray = None) -> sp.csr_matrix:
     """Q1 stiffness matrix for a cellwise coefficient a[cy, cx] on an
-    n x n grid, interior nodes only, row-major dof numbering."""
+    n x n grid, interior nodes only, row-major dof numbering (element
+    matrix a_c * K_REF, or a_c * element when given)."""
+    E = K_REF if element is None else element
     n = a.shape[0]
     m = n - 1
     cy, cx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
@@ -97,13 +99,28 @@ def assemble_q1(a: np.ndarray) -> sp.csr_matrix:
             keep = inp & inr
             rows.append((yp[keep] - 1) * m + (xp[keep] - 1))
             cols.append((yr[keep] - 1) * m + (xr[keep] - 1))
-            vals.append(av[keep] * K_REF[p, r])
+            vals.append(av[keep] * E[p, r])
     A = sp.coo_matrix((np.concatenate(vals),
                        (np.concatenate(rows), np.concatenate(cols))),
                       shape=(m * m, m * m)).tocsr()
     A.sum_duplicates()
     A.sort_indices()
     return A
+
+
+# Bilinear element mass matrix on a square of side h, divided by h^2,
+# corners counter-clockwise from (0, 0) as in K_REF.
+M_REF = np.array(
+    [[4.0, 2.0, 1.0, 2.0],
+     [2.0, 4.0, 2.0, 1.0],
+     [1.0, 2.0, 4.0, 2.0],
+     [2.0, 1.0, 2.0, 4.0]]) / 36.0
+
+
+def assemble_q1_mass(n: int) -> sp.csr_matrix:
+    """Q1 mass matrix M_ij = integral of phi_i phi_j on an n x n grid of the
+    unit square (h = 1/n), interior nodes only, row-major dof numbering."""
+    return assemble_q1(np.ones((n, n)), element=M_REF / (n * n))
 
 
 def make_problem(n: int, contrast: float, seed: int,
