@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-localization", action="store_true",
                     help="skip the one-pass localization error per patch radius")
+    ap.add_argument("--no-mass", action="store_true",
+                    help="skip the mass-matrix initialisation timings")
     return ap.parse_args()
 
 
@@ -425,6 +427,59 @@ def localization_errors(nv, a, dev_in, ud, radii=(1.0, 2.0, 3.0)):
     return out
 
 
+def mass_init_timing(nv, torch, dev, a, stream):
+    """Setup with the mass-matrix initialisation (Algorithm 2 lines 2a-5,
+    rho_q = 2) and refined solve: the paper's Example 1 (q = 6, float64,
+    error against the oracle's direct solve of the initialised system) and
+    the 1024 x 1024 rough problem (mixed, relative residual of A^(q) U = g)."""
+    import scipy.sparse.linalg as spla
+    from oracle.massinit import mass_initialised_operator
+    from workloads import assemble_q1_mass, make_example1, make_problem
+    out = {}
+    for name, p, prec in (("example1_q6", make_example1(6), nv.FP64),
+                          (f"rough_{a.size}x{a.size}", make_problem(a.size, a.contrast, 0), nv.MIXED)):
+        M = assemble_q1_mass(p.n)
+        dev_arrays = []
+        for X in (p.A, M):
+            X = X.tocsr()
+            X.sort_indices()
+            dev_arrays.append(tuple(torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in
+                                    (X.indptr.astype(np.int32), X.indices.astype(np.int32),
+                                     X.data.astype(np.float64))))
+        cells = torch.from_numpy(np.ascontiguousarray(p.cells, dtype=np.int32)).to(dev)
+        g = torch.from_numpy(p.g).to(dev)
+        o = opts_for(nv, a, prec, stream.cuda_stream, 0)
+        o.refine_tol = 1e-12 if prec == nv.FP64 else a.refine_tol
+        times = []
+        for it in range(3):
+            u = torch.zeros_like(g)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                h = nv.gamblet_setup_mass(dev_arrays[0], dev_arrays[1], p.q, cells, 2.0, o)
+                info = nv.Info()
+                nv.gamblet_solve(h, g, u, None, info)
+                e1.record(stream)
+            e1.synchronize()
+            nv.gamblet_destroy(h)
+            if it > 0:
+                times.append(e0.elapsed_time(e1))
+        ms = statistics.mean(times)
+        rec = {"dofs": p.ndof, "rho": a.rho, "rho_q": 2.0, "ms_per_step": ms,
+               "value": p.ndof / (ms * 1e-3), "unit": UNIT, "setup_ms": info.setup_ms,
+               "solve_ms": info.solve_ms, "outer_iters": info.outer_iters,
+               "rel_residual": info.rel_residual,
+               "precision": "f64" if prec == nv.FP64 else "f32+f64"}
+        if p.ndof <= 20000:
+            Aq, Minv = mass_initialised_operator(p.A, M, p.cells, p.q, 2.0)
+            u_ref = Minv @ spla.spsolve(Aq.tocsc(), p.g)
+            rec["rel_err_vs_oracle"] = rel_err(u.cpu().numpy(), u_ref)
+        out[name] = rec
+    return out
+
+
 def cpu_oracle(p):
     """The oracle's direct solve (SuperLU + extended-precision refinement)."""
     from oracle import direct
@@ -592,6 +647,8 @@ def main():
         line["batched"] = batched_timing(nv, torch, dev, a, stream, flush)
     if not a.no_localization:
         line["localization_error_one_pass"] = localization_errors(nv, a, dev_in, ud)
+    if not a.no_mass:
+        line["mass_init"] = mass_init_timing(nv, torch, dev, a, stream)
     if rank == 0 and ws == 1 and not a.no_cpu:
         line["cpu_baseline"] = {"value": ndof / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "one full solve of the same problem: SuperLU factor + "

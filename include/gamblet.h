@@ -150,6 +150,27 @@ GAMBLET_API gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const 
                              const gamblet_opts* opts, gamblet_handle* out);
 
 /*
+ * Setup with the level-q initialisation by the mass matrix (Algorithm 1,
+ * lines 1-5; Algorithm 2, lines 2a-5 with Definition deflocinvm): the
+ * level-q gamblets psi^(q)_i = sum_j (M^-1,loc)_{j,i} phi_j, where column i
+ * of M^-1,loc solves the mass system restricted to the nodes whose cells lie
+ * within distance rho_q of node i's cell (same rule as opts->nbr_rule) with
+ * right-hand side e_i.  The hierarchy is built on
+ * A^(q),loc = (M^-1,loc)^T A M^-1,loc (symmetrised), with g^(q) = g (the
+ * nodal values of the right-hand side, Algorithm 1 line 4).  gamblet_solve
+ * on the handle solves A^(q),loc U = g and returns the nodal coefficients
+ * u = M^-1,loc U (with an unbounded rho_q: the solution of A u = M g).
+ *   A, M    fine stiffness and mass matrices (same size, symmetric positive
+ *           definite; cell offsets between coupled unknowns at most 5).
+ *   rho_q   patch radius of M^-1,loc in level-q cell units (> 0).
+ *   Other arguments as for gamblet_setup.  gamblet_grad is not available on
+ *   the handle (UNSUPPORTED).  info->setup_ms includes the initialisation.
+ */
+GAMBLET_API gamblet_status gamblet_setup_mass(const gamblet_csr* A, const gamblet_csr* M,
+                                              int32_t q, const int32_t* cells, double rho_q,
+                                              const gamblet_opts* opts, gamblet_handle* out);
+
+/*
  * Setup of nprob independent problems (each its own fine stiffness,
  * lattice and coefficient field, Sec. 5 per problem) as ONE hierarchy, so
  * that every level's patch solves, Galerkin products and level CGs of all

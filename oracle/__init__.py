@@ -19,4 +19,7 @@ be checked against the paper by eye:
   without the level recursion (Sec. 4.2 Theorem thmgugyug0), tiny grids.
 * ``adjoint``   - gradient of J = 1/2 |u - u_obs|^2 with respect to the
   cell log-coefficients through a direct adjoint solve.
+* ``massinit``  - the level-q initialisation by the mass matrix
+  (Algorithm 1 lines 1-5, Algorithm 2 lines 2a-5 with Definition
+  deflocinvm).
 """

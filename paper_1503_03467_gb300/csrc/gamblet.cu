@@ -316,6 +316,12 @@ struct gamblet_ctx {
   int n = 0;           // fine unknowns
   int nprob = 1;       // independent problems packed in the hierarchy
   int kmax = 0;        // finest level whose detail component a solve adds (q = all)
+  // level-q initialisation by the mass matrix: nodal coefficients are
+  // u_phi = M^-1,loc U (Minv[i][j] on the patch offsets nbrq)
+  bool mass = false;
+  double* Minv = nullptr;
+  int2* nbrq = nullptr;
+  int NBq = 0;
   bool exact = false;
   bool mixed = false;
   int num_sms = 1;
@@ -1473,6 +1479,12 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
       if (is_f32<T>()) launch_convert_f32_f64((const float*)cq, c64, nq, s);
       else CK(cudaMemcpyAsync(c64, cq, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
       launch_scatter_unknown(c64, h->morton_of, h->n, cu, s);
+      if (h->mass) {
+        double* cm = tmp.alloc<double>(h->n);
+        launch_mass_apply(h->n, h->NBq, h->nbrq, h->Minv, cu, h->morton_of, h->unknown_of,
+                          1 << q, Lq.ncell, cm, s);
+        cu = cm;
+      }
       CK(cudaMemcpyAsync(comps_user + (int64_t)(lev - 1) * h->n, cu, sizeof(double) * h->n,
                          cudaMemcpyDefault, s));
     }
@@ -1541,16 +1553,20 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
     CK(cudaStreamSynchronize(s));
     relres = std::sqrt(h->dots_h[0]) / gnorm;
   }
-  // u = Q^T uhat, back to unknown order
+  // u = Q^T uhat, back to unknown order (and, after a mass initialisation,
+  // from the coefficients U of psi^(q) to nodal coefficients M^-1,loc U)
   launch_transform_vec<double>(h->u64, h->q64, Lq.npar, Lq.pmask, -1, s);
-  double* u_dev = nullptr;
-  if (is_device_ptr(u_user)) {
-    launch_scatter_unknown(h->q64, h->morton_of, h->n, u_user, s);
+  double* u_out = is_device_ptr(u_user) ? u_user : tmp.alloc<double>(h->n);
+  if (h->mass) {
+    double* U = tmp.alloc<double>(h->n);
+    launch_scatter_unknown(h->q64, h->morton_of, h->n, U, s);
+    launch_mass_apply(h->n, h->NBq, h->nbrq, h->Minv, U, h->morton_of, h->unknown_of, 1 << q,
+                      Lq.ncell, u_out, s);
   } else {
-    u_dev = tmp.alloc<double>(h->n);
-    launch_scatter_unknown(h->q64, h->morton_of, h->n, u_dev, s);
-    CK(cudaMemcpyAsync(u_user, u_dev, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
+    launch_scatter_unknown(h->q64, h->morton_of, h->n, u_out, s);
   }
+  if (u_out != u_user)
+    CK(cudaMemcpyAsync(u_user, u_out, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
   CK(cudaEventRecord(e1, s));
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
@@ -1786,6 +1802,159 @@ gamblet_ctx* setup_batched_impl(int32_t nprob, const gamblet_csr* A, const int32
   return h;
 }
 
+// Level-q initialisation by the mass matrix (Algorithm 2, lines 2a-5 with
+// Definition deflocinvm): M^-1,loc on patches of radius rho_q around every
+// node, A^(q),loc = (M^-1,loc)^T A M^-1,loc as a CSR, then the ordinary
+// setup on it.  The handle keeps M^-1,loc for the solve's output map.
+gamblet_ctx* setup_mass_impl(const gamblet_csr* A, const gamblet_csr* M, int32_t q,
+                             const int32_t* cells, double rho_q, const gamblet_opts* opts) {
+  if (!A || !M || !cells) fail(GAMBLET_ERR_INVALID_ARG, "A, M and cells must be non-NULL");
+  if (A->n < 1 || M->n != A->n || M->nnz < 1 || !M->rowptr || !M->colind || !M->val ||
+      A->nnz < 1 || !A->rowptr || !A->colind || !A->val)
+    fail(GAMBLET_ERR_INVALID_ARG, "A and M must be complete CSRs of the same size");
+  if (q < 2 || q > 15) fail(GAMBLET_ERR_INVALID_ARG, "q must be in [2, 15]");
+  if (!(rho_q > 0)) fail(GAMBLET_ERR_INVALID_ARG, "rho_q must be positive");
+  if ((int64_t)A->n > ((int64_t)1 << (2 * q)))
+    fail(GAMBLET_ERR_INVALID_ARG, "more unknowns than level-q cells");
+  gamblet_opts o;
+  if (opts) o = *opts;
+  else gamblet_default_opts(&o);
+  if (o.nbr_rule != 0 && o.nbr_rule != 1) fail(GAMBLET_ERR_INVALID_ARG, "nbr_rule must be 0 or 1");
+  cudaStream_t s = (cudaStream_t)o.stream;
+  const int n = A->n;
+  Pool tmp;
+  tmp.s = s;
+  int dev = 0, num_sms = 1;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  // cells -> Morton codes and the cell -> node map of the level-q lattice
+  const int32_t* cells_d = as_device(tmp, cells, 2 * (int64_t)n, s);
+  int32_t* morton_of = tmp.alloc<int32_t>(n);
+  int* flag = tmp.zeros<int>(4, s);
+  launch_cells_to_morton(cells_d, n, q, morton_of, flag, s);
+  int flag_h[4];
+  CK(cudaMemcpyAsync(flag_h, flag, sizeof(flag_h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (flag_h[0] == 2) fail(GAMBLET_ERR_INVALID_ARG, "a cell lies outside [0, 2^q)");
+  const int64_t ncell = 4 * (((int64_t)flag_h[1] + 1 + 3) / 4);
+  int32_t* unknown_of = tmp.alloc<int32_t>(ncell);
+  CK(cudaMemsetAsync(unknown_of, 0xff, sizeof(int32_t) * ncell, s));
+  uint32_t* pm = tmp.zeros<uint32_t>(ncell / 4, s);
+  CK(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  launch_scatter_cells(morton_of, n, unknown_of, pm, flag, s);
+  // per-node stencils of A and M
+  auto stencil = [&](const gamblet_csr* X, int& rx, int& ry) {
+    const int32_t* rp = as_device(tmp, X->rowptr, (int64_t)n + 1, s);
+    const int32_t* ci = as_device(tmp, X->colind, X->nnz, s);
+    const double* va = as_device(tmp, X->val, X->nnz, s);
+    int* ext = tmp.zeros<int>(4, s);
+    launch_csr_node_extent(n, rp, ci, morton_of, ext, ext + 2, s);
+    int ext_h[4];
+    CK(cudaMemcpyAsync(ext_h, ext, sizeof(ext_h), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ext_h[2]) fail(GAMBLET_ERR_INVALID_ARG, "CSR column index out of range or rowptr decreasing");
+    rx = ext_h[0];
+    ry = ext_h[1];
+    if ((2 * rx + 1) * (2 * ry + 1) > 121)
+      fail(GAMBLET_ERR_UNSUPPORTED, "mass initialisation needs a compact fine stencil (|offset| <= 5)");
+    double* st = tmp.zeros<double>((int64_t)n * (2 * rx + 1) * (2 * ry + 1), s);
+    launch_csr_to_stencil(n, rp, ci, va, morton_of, rx, ry, st, s);
+    return st;
+  };
+  int arx, ary, mrx, mry;
+  double* Ast = stencil(A, arx, ary);
+  double* Mst = stencil(M, mrx, mry);
+  // patch offsets N_q (the same closed-square rule at the fine level)
+  const OffSet Nq = neighbour_offsets(rho_q, o.nbr_rule);
+  const int NBq = Nq.size(), jcq = Nq.find(0, 0);
+  if (mass_patch_smem_bytes(NBq) > 227 * 1024)
+    fail(GAMBLET_ERR_UNSUPPORTED, "mass patch exceeds shared memory; lower rho_q");
+  int2* nbrq_t = tmp.upload(Nq.v, s);
+  double* Minv = tmp.alloc<double>((int64_t)n * NBq);
+  int* status = tmp.zeros<int>(1, s);
+  launch_mass_patch_inverse(n, NBq, jcq, nbrq_t, Mst, mrx, mry, morton_of, unknown_of, 1 << q,
+                            ncell, Minv, status, num_sms, s);
+  // symbolic lists of (M^-1,loc)^T A M^-1,loc
+  OffSet Aoff, W, D;
+  for (int dy = -ary; dy <= ary; ++dy)
+    for (int dx = -arx; dx <= arx; ++dx) Aoff.add(dx, dy);
+  for (const int2& nj : Nq.v)
+    for (const int2& a : Aoff.v) W.add(nj.x - a.x, nj.y - a.y);
+  std::vector<int> l1_ptr(W.size() + 1, 0), l2_ptr;
+  std::vector<int2> l1, l2;
+  for (int w = 0; w < W.size(); ++w) {
+    for (int a = 0; a < Aoff.size(); ++a) {
+      const int j = Nq.find(W.v[w].x + Aoff.v[a].x, W.v[w].y + Aoff.v[a].y);
+      if (j >= 0) l1.push_back(make_int2(a, j));
+    }
+    l1_ptr[w + 1] = (int)l1.size();
+  }
+  for (const int2& w : W.v)
+    for (const int2& nj : Nq.v) D.add(w.x - nj.x, w.y - nj.y);
+  l2_ptr.assign(D.size() + 1, 0);
+  for (int d = 0; d < D.size(); ++d) {
+    for (int j = 0; j < NBq; ++j) {
+      const int w = W.find(D.v[d].x + Nq.v[j].x, D.v[d].y + Nq.v[j].y);
+      if (w >= 0) l2.push_back(make_int2(j, w));
+    }
+    l2_ptr[d + 1] = (int)l2.size();
+  }
+  std::vector<int> mirror(D.size());
+  for (int d = 0; d < D.size(); ++d) mirror[d] = D.find(-D.v[d].x, -D.v[d].y);
+  MassTripleGeom tg{NBq, Aoff.size(), W.size(), tmp.upload(W.v, s), tmp.upload(l1_ptr, s),
+                    tmp.upload(l1, s), D.size(), tmp.upload(D.v, s), tmp.upload(l2_ptr, s),
+                    tmp.upload(l2, s)};
+  double* X = tmp.alloc<double>((int64_t)n * D.size());
+  launch_mass_triple(n, tg, Ast, Minv, morton_of, unknown_of, 1 << q, ncell, X, s);
+  // CSR of A^(q),loc (symmetrised)
+  int2* Doff = tmp.upload(D.v, s);
+  int32_t* cnt = tmp.alloc<int32_t>(n);
+  launch_stencil_counts(n, Doff, D.size(), morton_of, unknown_of, 1 << q, ncell, cnt, s);
+  std::vector<int32_t> rowptr_h((size_t)n + 1, 0);
+  CK(cudaMemcpyAsync(rowptr_h.data() + 1, cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  int status_h = 0;
+  CK(cudaMemcpyAsync(&status_h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  if (status_h == DEV_NOT_SPD) fail(GAMBLET_ERR_NOT_SPD, "non-positive pivot in a mass patch");
+  for (int i = 0; i < n; ++i) {
+    if ((int64_t)rowptr_h[i] + rowptr_h[i + 1] >= ((int64_t)1 << 31))
+      fail(GAMBLET_ERR_UNSUPPORTED, "initialised operator exceeds int32 CSR indexing");
+    rowptr_h[i + 1] += rowptr_h[i];
+  }
+  const int64_t nnz = rowptr_h[n];
+  int32_t* rp = tmp.upload(rowptr_h, s);
+  int32_t* ci = tmp.alloc<int32_t>(nnz);
+  double* va = tmp.alloc<double>(nnz);
+  launch_stencil_to_csr(n, Doff, tmp.upload(mirror, s), D.size(), X, morton_of, unknown_of,
+                        1 << q, ncell, rp, ci, va, s);
+  CK(cudaGetLastError());
+  const gamblet_csr Aq{n, nnz, rp, ci, va};
+  gamblet_ctx* h = setup_impl(&Aq, q, cells_d, &o);
+  try {
+    h->mass = true;
+    h->NBq = NBq;
+    h->nbrq = h->pool.upload(Nq.v, s);
+    h->Minv = h->pool.alloc<double>((int64_t)n * NBq);
+    CK(cudaMemcpyAsync(h->Minv, Minv, sizeof(double) * n * NBq, cudaMemcpyDeviceToDevice, s));
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    h->setup_ms = ms;  // the mass initialisation included
+  } catch (...) {
+    gamblet_destroy(h);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return h;
+}
+
 }  // namespace
 
 // ================================================================= C ABI
@@ -1819,6 +1988,25 @@ gamblet_status gamblet_setup(const gamblet_csr* A, int32_t q, const int32_t* cel
   *out = nullptr;
   try {
     *out = setup_impl(A, q, cells, opts);
+    return GAMBLET_OK;
+  } catch (const GbError& e) {
+    return set_error(e);
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return GAMBLET_ERR_INVALID_ARG;
+  }
+}
+
+gamblet_status gamblet_setup_mass(const gamblet_csr* A, const gamblet_csr* M, int32_t q,
+                                  const int32_t* cells, double rho_q, const gamblet_opts* opts,
+                                  gamblet_handle* out) {
+  if (!out) {
+    g_last_error = "out is NULL";
+    return GAMBLET_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    *out = setup_mass_impl(A, M, q, cells, rho_q, opts);
     return GAMBLET_OK;
   } catch (const GbError& e) {
     return set_error(e);
@@ -1889,6 +2077,8 @@ gamblet_status gamblet_grad(gamblet_handle h, int32_t ncell, const int32_t* cell
     if (!h || !cell_nodes || !cell_a || !K_ref || !u || !u_obs || !dJ)
       fail(GAMBLET_ERR_INVALID_ARG, "NULL argument");
     if (ncell < 1) fail(GAMBLET_ERR_INVALID_ARG, "ncell must be positive");
+    if (h->mass)
+      fail(GAMBLET_ERR_UNSUPPORTED, "the adjoint covers the phi initialisation (A^(q) = A) only");
     cudaStream_t s = h->s;
     Pool tmp;
   tmp.s = h->s;

@@ -17,6 +17,51 @@ void launch_cells_to_morton(const int32_t* cells, int n, int q, int32_t* morton_
 // parents; flag[0] = 1 when two unknowns share a cell.
 void launch_scatter_cells(const int32_t* morton_of, int n, int32_t* unknown_of,
                           uint32_t* pmask_q, int* flag, cudaStream_t s);
+// ---------------------------------------------------------------- mass initialisation
+// Largest |cell offset| (x, y) between the rows and columns of a fine CSR.
+void launch_csr_node_extent(int n, const int32_t* rowptr, const int32_t* colind,
+                            const int32_t* morton_of, int* ext, int* bad, cudaStream_t s);
+// Fine CSR -> per-node stencil St[i][s] over the (2 rx + 1) x (2 ry + 1)
+// cell offsets (row-major in (dy, dx)); St must be zeroed.
+void launch_csr_to_stencil(int n, const int32_t* rowptr, const int32_t* colind, const double* val,
+                           const int32_t* morton_of, int rx, int ry, double* St, cudaStream_t s);
+// Minv[i][j]: column i of the localized mass inverse (Definition deflocinvm)
+// on the patch nodes c_i + N_j; status receives DEV_NOT_SPD on a
+// non-positive pivot.
+void launch_mass_patch_inverse(int n, int NB, int jc, const int2* nbr, const double* Mst, int mrx,
+                               int mry, const int32_t* morton_of, const int32_t* unknown_of,
+                               int L, int64_t ncell, double* Minv, int* status, int num_sms,
+                               cudaStream_t s);
+size_t mass_patch_smem_bytes(int NB);
+// Node-level lists of the product (M^-1,loc)^T A M^-1,loc (as the Galerkin
+// lists, with scalar entries): window offsets W and pairs (s, j) with
+// W_w + A_s = N_j; output offsets D and pairs (j, w) with W_w = D_d + N_j.
+struct MassTripleGeom {
+  int NB, nast;
+  int nwin;
+  const int2* win;
+  const int* l1_ptr;
+  const int2* l1;
+  int nout;
+  const int2* out;
+  const int* l2_ptr;
+  const int2* l2;
+};
+void launch_mass_triple(int n, MassTripleGeom g, const double* Ast, const double* Minv,
+                        const int32_t* morton_of, const int32_t* unknown_of, int L, int64_t ncell,
+                        double* out, cudaStream_t s);
+void launch_stencil_counts(int n, const int2* off, int noff, const int32_t* morton_of,
+                           const int32_t* unknown_of, int L, int64_t ncell, int32_t* count,
+                           cudaStream_t s);
+void launch_stencil_to_csr(int n, const int2* off, const int* mirror, int noff, const double* X,
+                           const int32_t* morton_of, const int32_t* unknown_of, int L,
+                           int64_t ncell, const int32_t* rowptr, int32_t* colind, double* val,
+                           cudaStream_t s);
+// u[j] = (M^-1,loc U)_j.
+void launch_mass_apply(int n, int NB, const int2* nbr, const double* Minv, const double* U,
+                       const int32_t* morton_of, const int32_t* unknown_of, int L, int64_t ncell,
+                       double* u, cudaStream_t s);
+
 // One problem of a batched setup: its unknowns start at row0 and its
 // stored entries at nnz0 of the combined CSR; its 2^q lattice is the
 // subtree with lower-left cell (x0, y0) of the combined lattice.

@@ -76,6 +76,9 @@ SIGNATURES = {
     "gamblet_default_opts": (None, [ctypes.POINTER(Opts)]),
     "gamblet_setup": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.c_int32, ctypes.c_void_p,
                                      ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "gamblet_setup_mass": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.POINTER(Csr), ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(Opts),
+                                          ctypes.POINTER(ctypes.c_void_p)]),
     "gamblet_setup_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Csr),
                                              ctypes.POINTER(ctypes.c_int32),
                                              ctypes.POINTER(ctypes.c_void_p),
@@ -173,6 +176,21 @@ def gamblet_setup(rowptr, colind, val, q: int, cells, opts: Opts | None = None) 
     h = ctypes.c_void_p()
     st = _lib.gamblet_setup(ctypes.byref(csr), int(q), _ptr(cells, np.int32),
                             ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    _check(st)
+    return h.value
+
+
+def gamblet_setup_mass(A_csr, M_csr, q: int, cells, rho_q: float, opts: Opts | None = None) -> int:
+    """A_csr, M_csr: (rowptr, colind, val) of the stiffness and mass matrices."""
+    def csr(t):
+        rowptr, colind, val = t
+        return Csr(int(rowptr.shape[0]) - 1, int(colind.shape[0]), _ptr(rowptr, np.int32),
+                   _ptr(colind, np.int32), _ptr(val, np.float64))
+    a, m = csr(A_csr), csr(M_csr)
+    h = ctypes.c_void_p()
+    st = _lib.gamblet_setup_mass(ctypes.byref(a), ctypes.byref(m), int(q), _ptr(cells, np.int32),
+                                 float(rho_q), ctypes.byref(opts) if opts is not None else None,
+                                 ctypes.byref(h))
     _check(st)
     return h.value
 

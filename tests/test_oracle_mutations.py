@@ -53,3 +53,38 @@ def test_unmutated_passes_same_checks():
     r = ex.gamblet_exact(p.A, p.g, p.cells, p.q)
     assert np.linalg.norm(r["u"] - ud) / np.linalg.norm(ud) < 1e-12
     assert np.linalg.norm(r["comps"] - b["comps"]) / np.linalg.norm(b["comps"]) < 1e-11
+
+
+MASS_MUTATIONS = {
+    "missing_right_factor": ("Aq = sp.csr_matrix(Minv.T @ sp.csr_matrix(A) @ Minv)",
+                             "Aq = sp.csr_matrix(Minv.T @ sp.csr_matrix(A))"),
+    "rhs_not_unit": ("e = (idx == i).astype(np.float64)", "e = np.ones(len(idx))"),
+    "output_not_mapped": ("return setup[\"Minv\"] @ U, U", "return U, U"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MASS_MUTATIONS))
+def test_mass_pins_catch_mutation(name):
+    """The direct solve of A u = M g (exact inverse) or the patch exactness of
+    the localized inverse catches each planted mistake."""
+    import scipy.sparse.linalg as spla
+    import oracle.massinit as mi
+    from workloads import assemble_q1_mass
+    src = inspect.getsource(mi)
+    old, new = MASS_MUTATIONS[name]
+    assert old in src, name
+    mod = types.ModuleType("oracle.massinit_mut")
+    mod.__dict__["__package__"] = "oracle"
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), mod.__dict__)
+    p = make_problem(8, 1e2, 2)
+    M = assemble_q1_mass(8)
+    u_ref = spla.spsolve(p.A.tocsc(), M @ p.g)
+    setup = mod.gamblet_mass_setup(p.A, M, p.cells, p.q, np.inf, np.inf)
+    u, _ = mod.gamblet_mass_solve(setup, p.g)
+    exact_ok = np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref) < 1e-12
+    Mi = mod.localized_mass_inverse(M, p.cells, p.q, 1.0)
+    P = (M @ Mi).toarray()
+    patch_ok = all(np.allclose(P[Mi[:, i].nonzero()[0], i],
+                               (Mi[:, i].nonzero()[0] == i).astype(float), atol=1e-12)
+                   for i in range(0, M.shape[0], 7))
+    assert not (exact_ok and patch_ok)

@@ -98,3 +98,13 @@ def test_batch_workload_draw_protocol():
                                     for s in range(1, 13)]
     assert all(1e2 <= q.contrast <= 1e6 for q in probs)
     assert all(q.A.shape == ((q.n - 1) ** 2,) * 2 for q in probs)
+
+
+def test_example1_problem_layout():
+    from workloads import assemble_q1_mass, make_example1
+    p = make_example1(4)
+    assert p.n == 17 and p.q == 4 and p.A.shape == (256, 256)
+    assert p.cells.min() == 0 and p.cells.max() == 15          # 2^q x 2^q lattice, all cells used
+    assert len({(int(x), int(y)) for x, y in p.cells}) == 256
+    assert assemble_q1_mass(17).shape == (256, 256)
+    assert p.g.shape == (256,)

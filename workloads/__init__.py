@@ -16,6 +16,7 @@ from .rough import (  # noqa: F401
     cell_corner_dofs,
     example1_coefficient,
     example1_rhs,
+    make_example1,
     make_problem,
     make_batch,
     make_batch_problem,

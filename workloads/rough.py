@@ -189,6 +189,19 @@ def example1_rhs(q: int = 6) -> np.ndarray:
     return np.cos(3 * z1 + z2) + np.sin(3 * z2) + np.sin(7 * z1 - 5 * z2)
 
 
+def make_example1(q: int = 6) -> Problem:
+    """The paper's Example 1 (Section 5.1): (2^q + 1) x (2^q + 1) cells, the
+    product coefficient of example1_coefficient, g from example1_rhs; the
+    2^q x 2^q interior nodes sit in the cells (ix - 1, iy - 1) of the level-q
+    lattice.  The mass matrix of the same grid is assemble_q1_mass(2^q + 1)."""
+    n = (1 << q) + 1
+    a = example1_coefficient(q)
+    A = assemble_q1(a)
+    return Problem(n=n, q=q, log_a=np.log(a), A=A, g=example1_rhs(q),
+                   cells=np.ascontiguousarray(interior_cells(n) - 1, dtype=np.int32),
+                   contrast=float(a.max() / a.min()))
+
+
 def cell_corner_dofs(n: int) -> np.ndarray:
     """(n*n) x 4 int32 fine unknown of each cell corner (counter-clockwise
     from (cx, cy), the K_REF order), -1 on the Dirichlet boundary; cells in
