@@ -302,7 +302,26 @@ def adjoint_timing(nv, torch, dev, steps=3):
             "grad_ms": b, "grad_over_forward": b / f, "rel_err_vs_oracle_adjoint": err}
 
 
-def batched_timing(nv, torch, dev, a, stream, flush):
+def rank_share(items, ws, rank):
+    """The items of one rank: round-robin, so sizes mix evenly; every item
+    belongs to exactly one rank."""
+    return list(items)[rank::ws]
+
+
+def reduce_over_ranks(torch, dev, ms, count):
+    """(max of ms, sum of count) over the ranks of the default process group
+    (one all-reduce each, on a tensor of `dev`); identity without one."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), int(count)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    c = torch.tensor([float(count)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
+def batched_timing(nv, torch, dev, a, stream, flush, ws=1, rank=0):
     """Many independent problems (seeds 1..P, sides drawn from {128, 256, 512},
     contrast log-uniform in [1e2, 1e6]) set up and solved as one hierarchy by
     gamblet_setup_batched, against the same problems one by one through
@@ -310,7 +329,9 @@ def batched_timing(nv, torch, dev, a, stream, flush):
     torch sparse product, validation only) and the oracle's direct solve for
     the first problem of each side."""
     from workloads import make_batch
-    probs = make_batch(a.batch_problems, first_seed=1)
+    # with several ranks the problems are partitioned round-robin (no
+    # collective on the data path); each rank sets up its share as one batch
+    probs = rank_share(make_batch(a.batch_problems, first_seed=1), ws, rank)
     items, gs = [], []
     for p in probs:
         A = p.A.tocsr()
@@ -345,6 +366,7 @@ def batched_timing(nv, torch, dev, a, stream, flush):
             solve.append(info.solve_ms)
             outer.append(info.outer_iters)
     ms = statistics.mean(times)
+    ms, total_dofs = reduce_over_ranks(torch, dev, ms, ndof)
     # accuracy per problem
     res = []
     for p, (rp, ci, va, q, _), gp in zip(range(len(probs)), items, gs):
@@ -384,10 +406,11 @@ def batched_timing(nv, torch, dev, a, stream, flush):
     seq_total = sum(seq)
     sides = [pr.n for pr in probs]
     return {
-        "workload": f"{len(probs)} problems, seeds 1..{len(probs)}, sides "
-                    f"128/256/512 x {sides.count(128)}/{sides.count(256)}/{sides.count(512)}, "
-                    "contrast log-uniform [1e2, 1e6], rho 3, mixed precision",
-        "dofs": ndof, "value": ndof / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+        "workload": f"{a.batch_problems} problems, seeds 1..{a.batch_problems}, sides 128/256/512 "
+                    f"(this rank: {len(probs)} problems, {sides.count(128)}/{sides.count(256)}/"
+                    f"{sides.count(512)}), contrast log-uniform [1e2, 1e6], rho 3, mixed precision",
+        "dofs": total_dofs, "value": total_dofs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+        "ranks": ws, "partition": "problems round-robin over ranks, max time over ranks",
         "setup_ms": statistics.mean(setup), "solve_ms": statistics.mean(solve),
         "outer_iters": max(outer), "max_rel_residual": max(res),
         "rel_err_vs_oracle": {str(k): v for k, v in sorted(err.items())},
@@ -597,13 +620,9 @@ def main():
                         stream, flush)
     e2e = run_e2e(nv, a, host, nv.MIXED, a.e2e_steps)
     ms = statistics.mean(mixed["times_ms"])
+    ms_max, _ = reduce_over_ranks(torch, dev, ms, ndof)
     if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
         dist.barrier()
-    else:
-        ms_max = ms
     err_mixed = rel_err(mixed["u"], ud)
     err_e2e = rel_err(e2e["u"], ud)
     value = ws * ndof / (ms_max * 1e-3)
@@ -644,7 +663,7 @@ def main():
     if not a.no_adjoint:
         line["adjoint"] = adjoint_timing(nv, torch, dev)
     if not a.no_batched:
-        line["batched"] = batched_timing(nv, torch, dev, a, stream, flush)
+        line["batched"] = batched_timing(nv, torch, dev, a, stream, flush, ws, rank)
     if not a.no_localization:
         line["localization_error_one_pass"] = localization_errors(nv, a, dev_in, ud)
     if not a.no_mass:
