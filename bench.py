@@ -503,6 +503,23 @@ def mass_init_timing(nv, torch, dev, a, stream):
     return out
 
 
+def level_conditions(nv, a, dev_in, steps=60):
+    """cond(B^(k)) estimates (Lanczos, float64 level operators) per level:
+    the paper bounds them uniformly in k (Theorem thmodhehiudhehd)."""
+    q = int(np.log2(a.size))
+    o = opts_for(nv, a, nv.FP64, None, 0)
+    o.refine_max_iter = 0
+    h = nv.gamblet_setup(dev_in["rowptr"], dev_in["colind"], dev_in["val"], q, dev_in["cells"], o)
+    try:
+        out = {}
+        for k in range(2, q + 1):
+            lo, hi = nv.gamblet_level_condition(h, k, steps)
+            out[str(k)] = {"lmin": lo, "lmax": hi, "cond": hi / lo}
+        return out
+    finally:
+        nv.gamblet_destroy(h)
+
+
 def cpu_oracle(p):
     """The oracle's direct solve (SuperLU + extended-precision refinement)."""
     from oracle import direct
@@ -668,6 +685,8 @@ def main():
         line["localization_error_one_pass"] = localization_errors(nv, a, dev_in, ud)
     if not a.no_mass:
         line["mass_init"] = mass_init_timing(nv, torch, dev, a, stream)
+    if not a.no_localization:
+        line["level_condition"] = level_conditions(nv, a, dev_in)
     if rank == 0 and ws == 1 and not a.no_cpu:
         line["cpu_baseline"] = {"value": ndof / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "one full solve of the same problem: SuperLU factor + "

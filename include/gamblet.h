@@ -235,6 +235,32 @@ GAMBLET_API gamblet_status gamblet_solve_truncated(gamblet_handle h, int32_t k, 
                                                    double* u, gamblet_info* info);
 
 /*
+ * Diagnostics: estimates of the extreme eigenvalues of B^(k) = W A^(k) W^T
+ * (the level systems whose condition numbers the paper bounds uniformly in
+ * k, Theorem thmodhehiudhehd) by the Lanczos process on the stored detail
+ * blocks, steps iterations (capped at |J^(k)|) from a fixed pseudo-random
+ * start, extremes of the Lanczos matrix by Sturm bisection.  Localized
+ * transform only.  cond(B^(k)) ~ lmax / lmin.
+ */
+GAMBLET_API gamblet_status gamblet_level_condition(gamblet_handle h, int32_t k, int32_t steps,
+                                                   double* lmin, double* lmax);
+
+/*
+ * Compression in the normalised gamblet basis (Sec. 5.1, Example 1: the
+ * representation of u in psi^(1)_i / ||psi^(1)_i||_a and chi^(k)_j /
+ * ||chi^(k)_j||_a is sparse).  Runs the one-pass transform of g, forms the
+ * normalised coefficients c^(1)_i = U_i sqrt(A^(1)_ii) and c^(k)_j =
+ * w^(k)_j sqrt(B^(k)_jj), keeps those with |c| >= eps * max |c| and rebuilds
+ * u from them (zeroed coefficients dropped from the level recursion).
+ *   eps     relative threshold (>= 0; 0 keeps everything: the one-pass u).
+ *   u       n float64 output (nodal coefficients after a mass setup).
+ *   kept, total  NULL or receive the kept and the total coefficient counts.
+ * Localized transform only (UNSUPPORTED for rho <= 0).
+ */
+GAMBLET_API gamblet_status gamblet_compress(gamblet_handle h, const double* g, double eps,
+                                            double* u, int64_t* kept, int64_t* total);
+
+/*
  * Adjoint gradient of J = 1/2 |u - u_obs|^2 with respect to theta_c =
  * log a_c for a cellwise-constant coefficient (the paper has no adjoint; the
  * discrete adjoint of A(theta) u = g):  A lambda = u - u_obs is solved with

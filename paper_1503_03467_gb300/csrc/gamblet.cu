@@ -227,6 +227,7 @@ struct LevelDev {
   void* Bd = nullptr;    // [noff][9][npar]
   void* Dinv = nullptr;  // [9][npar]
   int R = 0;             // halo radius
+  int o0 = -1;           // index of the zero offset in O_k (diagonal blocks)
 };
 
 // Per-kernel CUDA-event timing on the library's stream (opts.profile).
@@ -1052,6 +1053,7 @@ void setup_local(gamblet_ctx* h) {
       R = std::max(R, std::max(std::abs(L.off_h[o].x), std::abs(L.off_h[o].y)));
     }
     if (o0 < 0) fail(GAMBLET_ERR_INVALID_ARG, "level operator has no diagonal blocks");
+    L.o0 = o0;
     L.R = R;
     T* Bd = P.alloc<T>((int64_t)L.noff * 9 * L.npar);
     T* Dinv = P.alloc<T>(9 * L.npar);
@@ -1321,7 +1323,12 @@ void run_level_cg(gamblet_ctx* h) {
 // in: transformed level-q vector (T); out: transformed (inverse_last = 0) or
 // plain (1) level-q vector (T).  in may alias lv[q].ghat.
 template <typename T>
-void apply_G(gamblet_ctx* h, const T* in, T* out, int inverse_last) {
+void apply_G_up(gamblet_ctx* h, T* out, int inverse_last);
+
+// Restriction, level solves and the coarsest solve of the gamblet operator:
+// leaves w^(k) in lv[k].w and U^(1) in h->U1.
+template <typename T>
+void apply_G_down(gamblet_ctx* h, const T* in) {
   cudaStream_t s = h->s;
   const int q = h->q;
   const int NB = h->N.size();
@@ -1363,7 +1370,14 @@ void apply_G(gamblet_ctx* h, const T* in, T* out, int inverse_last) {
   }
   launch_level1_solve<T>(h->A1L, (const T*)h->g1, (T*)h->U1, s);
   CK(cudaGetLastError());
-  // prolongation and summation
+}
+
+// Prolongation and summation from U^(1) and the w^(k) in place.
+template <typename T>
+void apply_G_up(gamblet_ctx* h, T* out, int inverse_last) {
+  cudaStream_t s = h->s;
+  const int q = h->q;
+  const int NB = h->exact ? 0 : h->N.size();
   for (int k = 2; k <= q; ++k) {
     LevelDev& L = h->lv[k];
     const T* vprev = (const T*)(k == 2 ? h->U1 : h->lv[k - 1].v);
@@ -1386,6 +1400,12 @@ void apply_G(gamblet_ctx* h, const T* in, T* out, int inverse_last) {
     }
   }
   CK(cudaGetLastError());
+}
+
+template <typename T>
+void apply_G(gamblet_ctx* h, const T* in, T* out, int inverse_last) {
+  apply_G_down<T>(h, in);
+  apply_G_up<T>(h, out, inverse_last);
 }
 
 // Components u^(l) - u^(l-1) in Morton order (plain), level by level.
@@ -1955,6 +1975,165 @@ gamblet_ctx* setup_mass_impl(const gamblet_csr* A, const gamblet_csr* M, int32_t
   return h;
 }
 
+// Compression in the normalised basis psi^(1)/||psi^(1)||_a, chi^(k)/||chi^(k)||_a
+// (Sec. 5.1): one-pass transform of g, threshold eps * max |c|, rebuild.
+template <typename T>
+void compress_impl(gamblet_ctx* h, const double* g_user, double eps, double* u_user,
+                   int64_t* kept_out, int64_t* total_out) {
+  cudaStream_t s = h->s;
+  Pool tmp;
+  tmp.s = s;
+  const int q = h->q;
+  LevelDev& Lq = h->lv[q];
+  const int64_t nq = Lq.ncell;
+  double* g_dev = nullptr;
+  to_device(tmp, g_dev, g_user, h->n, s);
+  launch_gather_morton(g_dev, h->unknown_of, nq, h->g64, s);
+  launch_transform_vec<double>(h->g64, h->g64, Lq.npar, Lq.pmask, +1, s);
+  T* gT = as_T<T>(h, h->g64, h->rT, nq, true);
+  apply_G_down<T>(h, gT);
+  // level 1: c_i = U_i sqrt(A^(1)_ii), A^(1)_ii from the Cholesky factor
+  T U1[4];
+  double L1[16];
+  CK(cudaMemcpyAsync(U1, h->U1, sizeof(T) * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(L1, h->A1L, sizeof(double) * 16, cudaMemcpyDeviceToHost, s));
+  unsigned long long* dv = tmp.zeros<unsigned long long>(2, s);  // max bits, kept
+  for (int k = 2; k <= q; ++k) {
+    LevelDev& L = h->lv[k];
+    launch_coef_max<T>((const T*)L.w, (const T*)L.Bd, L.o0, L.npar, L.pmask, dv, s);
+  }
+  unsigned long long dh[2];
+  CK(cudaMemcpyAsync(dh, dv, sizeof(dh), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  const uint32_t m1 = h->lv[1].pmask_h[0] & 15u;
+  double c1[4], cmax = 0;
+  std::memcpy(&cmax, &dh[0], sizeof(double));
+  int64_t total = 0;
+  for (int i = 0; i < 4; ++i) {
+    double a = 0;
+    for (int j = 0; j <= i; ++j) a += L1[i * 4 + j] * L1[i * 4 + j];
+    c1[i] = ((m1 >> i) & 1u) ? std::fabs((double)U1[i]) * std::sqrt(a) : 0.0;
+    if ((m1 >> i) & 1u) ++total;
+    cmax = std::max(cmax, c1[i]);
+  }
+  for (int k = 2; k <= q; ++k) total += h->lv[k].nJ;
+  const double thr = eps * cmax;
+  int64_t kept = 0;
+  for (int i = 0; i < 4; ++i) {
+    if (!((m1 >> i) & 1u)) continue;
+    if (c1[i] >= thr) ++kept;
+    else U1[i] = T(0);
+  }
+  CK(cudaMemcpyAsync(h->U1, U1, sizeof(T) * 4, cudaMemcpyHostToDevice, s));
+  for (int k = 2; k <= q; ++k) {
+    LevelDev& L = h->lv[k];
+    launch_coef_threshold<T>((T*)L.w, (const T*)L.Bd, L.o0, L.npar, L.pmask, thr, dv + 1, s);
+  }
+  T* zT = as_T<T>(h, h->z64, h->zT, nq, false);
+  apply_G_up<T>(h, zT, 1);
+  if (is_f32<T>()) launch_convert_f32_f64((const float*)zT, h->q64, nq, s);
+  else CK(cudaMemcpyAsync(h->q64, zT, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
+  double* u_out = is_device_ptr(u_user) ? u_user : tmp.alloc<double>(h->n);
+  if (h->mass) {
+    double* U = tmp.alloc<double>(h->n);
+    launch_scatter_unknown(h->q64, h->morton_of, h->n, U, s);
+    launch_mass_apply(h->n, h->NBq, h->nbrq, h->Minv, U, h->morton_of, h->unknown_of, 1 << q,
+                      Lq.ncell, u_out, s);
+  } else {
+    launch_scatter_unknown(h->q64, h->morton_of, h->n, u_out, s);
+  }
+  if (u_out != u_user)
+    CK(cudaMemcpyAsync(u_user, u_out, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(dh, dv, sizeof(dh), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  kept += (int64_t)dh[1];
+  if (kept_out) *kept_out = kept;
+  if (total_out) *total_out = total;
+}
+
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with
+// diagonal d and off-diagonal e (e[i] couples i and i + 1): the negative
+// pivots of the LDL^T factorisation of T - x I (Sylvester's law of inertia).
+int tridiag_count_below(const std::vector<double>& d, const std::vector<double>& e, double x) {
+  int c = 0;
+  double piv = 1.0;
+  for (size_t i = 0; i < d.size(); ++i) {
+    const double off = i > 0 ? e[i - 1] * e[i - 1] : 0.0;
+    piv = (d[i] - x) - (i > 0 ? off / piv : 0.0);
+    if (piv == 0.0) piv = -1e-300;  // x hits a pivot exactly: treat it as just below
+    if (piv < 0) ++c;
+  }
+  return c;
+}
+
+// Extreme eigenvalues of B^(k) by the Lanczos process (steps iterations from
+// a fixed pseudo-random start on the detail slots), then bisection on the
+// Sturm counts of the Lanczos tridiagonal matrix.
+template <typename T>
+void level_condition_impl(gamblet_ctx* h, int k, int steps, double* lmin, double* lmax) {
+  cudaStream_t s = h->s;
+  LevelDev& L = h->lv[k];
+  Pool tmp;
+  tmp.s = s;
+  const int64_t n = L.ncell;
+  double* v = tmp.zeros<double>(n, s);
+  double* vp = tmp.zeros<double>(n, s);
+  double* w = tmp.zeros<double>(n, s);
+  double* d = tmp.zeros<double>(8, s);
+  const int Lpar = 1 << (k - 1);
+  auto dot = [&](const double* a, const double* b) {
+    CK(cudaMemsetAsync(d, 0, sizeof(double) * 8, s));
+    launch_dots(n, a, b, nullptr, nullptr, nullptr, nullptr, d, s);
+    double r = 0;
+    CK(cudaMemcpyAsync(&r, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return r;
+  };
+  launch_detail_start(L.npar, L.pmask, v, s);
+  const double nv0 = std::sqrt(dot(v, v));
+  if (!(nv0 > 0)) fail(GAMBLET_ERR_INVALID_ARG, "level has no detail unknowns");
+  launch_lanczos_step(n, 1.0 / nv0, v, nullptr, 0.0, nullptr, 0.0, v, s);  // normalise
+  std::vector<double> al, be;
+  double beta = 0;
+  const int m = std::max(1, std::min<int>(steps, L.nJ));
+  for (int j = 0; j < m; ++j) {
+    launch_detail_spmv<T>((const T*)L.Bd, L.off, L.noff, Lpar, L.npar, v, w, s);
+    const double alpha = dot(w, v);
+    // w <- w - alpha v - beta v_prev
+    launch_lanczos_step(n, 1.0, w, v, -alpha, vp, -beta, w, s);
+    al.push_back(alpha);
+    const double b = std::sqrt(dot(w, w));
+    if (j + 1 == m || !(b > 1e-12 * std::fabs(alpha))) break;
+    be.push_back(b);
+    // v_prev <- v, v <- w / b
+    CK(cudaMemcpyAsync(vp, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    launch_lanczos_step(n, 1.0 / b, w, nullptr, 0.0, nullptr, 0.0, v, s);
+    beta = b;
+  }
+  CK(cudaGetLastError());
+  // Gershgorin interval, then bisection for the smallest and largest
+  double lo = 1e300, hi = -1e300;
+  for (size_t i = 0; i < al.size(); ++i) {
+    const double r = (i > 0 ? std::fabs(be[i - 1]) : 0.0) + (i < be.size() ? std::fabs(be[i]) : 0.0);
+    lo = std::min(lo, al[i] - r);
+    hi = std::max(hi, al[i] + r);
+  }
+  const int mm = (int)al.size();
+  auto bisect = [&](int target) {  // smallest x with count_below(x) >= target
+    double a = lo, b = hi;
+    for (int it = 0; it < 200; ++it) {
+      const double c = 0.5 * (a + b);
+      if (tridiag_count_below(al, be, c) >= target) b = c;
+      else a = c;
+    }
+    return 0.5 * (a + b);
+  };
+  *lmin = bisect(1);
+  *lmax = bisect(mm);
+}
+
 }  // namespace
 
 // ================================================================= C ABI
@@ -2054,6 +2233,34 @@ gamblet_status gamblet_solve_truncated(gamblet_handle h, int32_t k, const double
     return solve_impl<double>(h, g, u, nullptr, info);
   } catch (const GbError& e) {
     if (info) info->status = e.st;
+    return set_error(e);
+  }
+}
+
+gamblet_status gamblet_level_condition(gamblet_handle h, int32_t k, int32_t steps,
+                                       double* lmin, double* lmax) {
+  try {
+    if (!h || !lmin || !lmax || k < 2 || k > h->q || steps < 1)
+      fail(GAMBLET_ERR_INVALID_ARG, "bad handle, level, steps or output");
+    if (h->exact) fail(GAMBLET_ERR_UNSUPPORTED, "diagnostics run on the localized transform");
+    if (h->mixed) level_condition_impl<float>(h, k, steps, lmin, lmax);
+    else level_condition_impl<double>(h, k, steps, lmin, lmax);
+    return GAMBLET_OK;
+  } catch (const GbError& e) {
+    return set_error(e);
+  }
+}
+
+gamblet_status gamblet_compress(gamblet_handle h, const double* g, double eps, double* u,
+                                int64_t* kept, int64_t* total) {
+  try {
+    if (!h || !g || !u) fail(GAMBLET_ERR_INVALID_ARG, "handle, g and u must be non-NULL");
+    if (!(eps >= 0)) fail(GAMBLET_ERR_INVALID_ARG, "eps must be >= 0");
+    if (h->exact) fail(GAMBLET_ERR_UNSUPPORTED, "compression runs on the localized transform");
+    if (h->mixed) compress_impl<float>(h, g, eps, u, kept, total);
+    else compress_impl<double>(h, g, eps, u, kept, total);
+    return GAMBLET_OK;
+  } catch (const GbError& e) {
     return set_error(e);
   }
 }

@@ -17,6 +17,28 @@ void launch_cells_to_morton(const int32_t* cells, int n, int q, int32_t* morton_
 // parents; flag[0] = 1 when two unknowns share a cell.
 void launch_scatter_cells(const int32_t* morton_of, int n, int32_t* unknown_of,
                           uint32_t* pmask_q, int* flag, cudaStream_t s);
+// ---------------------------------------------------------------- diagnostics
+// y = B^(k) x on the detail slots of transformed level-k vectors (float64).
+template <typename T>
+void launch_detail_spmv(const T* Bd, const int2* off, int noff, int Lpar, int64_t npar,
+                        const double* x, double* y, cudaStream_t s);
+// deterministic pseudo-random start vector on the active detail slots
+void launch_detail_start(int64_t npar, const uint32_t* pmask, double* v, cudaStream_t s);
+// out = a x + b y + c z (y, z may be NULL)
+void launch_lanczos_step(int64_t n, double a, const double* x, const double* y, double b,
+                         const double* z, double c, double* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- compression
+// max over the level's detail coefficients of |w_j| sqrt(B_jj), as the bit
+// pattern of a non-negative double (atomicMax into *cmax).
+template <typename T>
+void launch_coef_max(const T* w, const T* Bd, int o0, int64_t npar, const uint32_t* pmask,
+                     unsigned long long* cmax, cudaStream_t s);
+// zero the w_j with |w_j| sqrt(B_jj) < thr; *kept += the others.
+template <typename T>
+void launch_coef_threshold(T* w, const T* Bd, int o0, int64_t npar, const uint32_t* pmask,
+                           double thr, unsigned long long* kept, cudaStream_t s);
+
 // ---------------------------------------------------------------- mass initialisation
 // Largest |cell offset| (x, y) between the rows and columns of a fine CSR.
 void launch_csr_node_extent(int n, const int32_t* rowptr, const int32_t* colind,

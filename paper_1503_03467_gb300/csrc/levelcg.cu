@@ -392,4 +392,60 @@ template void launch_cg_level_setup<float>(const float*, int, int, int64_t, cons
 template void launch_cg_level_setup<double>(const double*, int, int, int64_t, const uint32_t*,
                                             double*, double*, cudaStream_t);
 
+// ---------------------------------------------------------------- diagnostics
+// y = B^(k) x on the detail slots (thread per parent, float64 vectors): the
+// plain operator of the level system, for the Lanczos estimate of its
+// extreme eigenvalues.
+template <typename T>
+__global__ void k_detail_spmv(const T* __restrict__ Bd, const int2* __restrict__ off, int noff,
+                              int Lpar, int64_t npar, const double* __restrict__ x, double* y) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npar) return;
+  int px, py;
+  demorton((uint32_t)p, px, py);
+  double y0 = 0, y1 = 0, y2 = 0;
+  for (int o = 0; o < noff; ++o) {
+    const int qn = shift_cell(px, py, off[o].x, off[o].y, Lpar, npar);
+    if (qn < 0) continue;
+    const double a0 = x[4 * (int64_t)qn], a1 = x[4 * (int64_t)qn + 1], a2 = x[4 * (int64_t)qn + 2];
+    const T* B = Bd + (int64_t)o * 9 * npar + p;
+    y0 += (double)B[0] * a0 + (double)B[npar] * a1 + (double)B[2 * npar] * a2;
+    y1 += (double)B[3 * npar] * a0 + (double)B[4 * npar] * a1 + (double)B[5 * npar] * a2;
+    y2 += (double)B[6 * npar] * a0 + (double)B[7 * npar] * a1 + (double)B[8 * npar] * a2;
+  }
+  y[4 * p] = y0;
+  y[4 * p + 1] = y1;
+  y[4 * p + 2] = y2;
+  y[4 * p + 3] = 0.0;
+}
+
+// Deterministic start vector on the active detail slots, zero elsewhere: the
+// SplitMix64 output function (Steele, Lea and Flood, 2014) of the slot
+// index, mapped to [-1, 1).
+__global__ void k_detail_start(int64_t npar, const uint32_t* __restrict__ pmask, double* v) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npar) return;
+  const int na = __popc(pmask[p] & 15u) - 1;
+  for (int a = 0; a < 4; ++a) {
+    uint64_t z = (uint64_t)(4 * p + a) + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[4 * p + a] = a < na ? (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0 : 0.0;
+  }
+}
+
+template <typename T>
+void launch_detail_spmv(const T* Bd, const int2* off, int noff, int Lpar, int64_t npar,
+                        const double* x, double* y, cudaStream_t s) {
+  if (npar > 0) { count_launch(); k_detail_spmv<T><<<(unsigned)((npar + 127) / 128), 128, 0, s>>>(Bd, off, noff, Lpar, npar, x, y); }
+}
+void launch_detail_start(int64_t npar, const uint32_t* pmask, double* v, cudaStream_t s) {
+  if (npar > 0) { count_launch(); k_detail_start<<<(unsigned)((npar + 255) / 256), 256, 0, s>>>(npar, pmask, v); }
+}
+template void launch_detail_spmv<float>(const float*, const int2*, int, int, int64_t,
+                                        const double*, double*, cudaStream_t);
+template void launch_detail_spmv<double>(const double*, const int2*, int, int, int64_t,
+                                         const double*, double*, cudaStream_t);
+
 }  // namespace gb

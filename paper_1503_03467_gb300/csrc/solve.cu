@@ -471,4 +471,78 @@ void launch_adjoint_contract(int ncell, const int32_t* cell_nodes, const double*
     { count_launch(); k_adjoint_contract<<<(ncell + 255) / 256, 256, 0, s>>>(ncell, cell_nodes, cell_a, lam, u, dJ); }
 }
 
+// ---------------------------------------------------------------- compression
+// Normalised detail coefficients c = w^(k)_j sqrt(B^(k)_jj) (||chi_j||_a),
+// B_jj being entry (a, a) of the diagonal detail block Bd[o0][4a][p].
+template <typename T>
+__device__ __forceinline__ double coef_norm(const T* __restrict__ w, const T* __restrict__ Bd,
+                                            int o0, int64_t npar, int64_t p, int a) {
+  const double b = (double)Bd[((int64_t)o0 * 9 + 4 * a) * npar + p];
+  return fabs((double)w[4 * p + a]) * sqrt(b > 0 ? b : 0.0);
+}
+
+template <typename T>
+__global__ void k_coef_max(const T* __restrict__ w, const T* __restrict__ Bd, int o0,
+                           int64_t npar, const uint32_t* __restrict__ pmask,
+                           unsigned long long* cmax) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double m = 0;
+  if (p < npar) {
+    const int na = __popc(pmask[p] & 15u) - 1;
+    for (int a = 0; a < na; ++a) m = fmax(m, coef_norm(w, Bd, o0, npar, p, a));
+  }
+  // non-negative doubles order as their bit patterns
+  if (m > 0) atomicMax(cmax, (unsigned long long)__double_as_longlong(m));
+}
+
+template <typename T>
+__global__ void k_coef_threshold(T* w, const T* __restrict__ Bd, int o0, int64_t npar,
+                                 const uint32_t* __restrict__ pmask, double thr,
+                                 unsigned long long* kept) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npar) return;
+  const int na = __popc(pmask[p] & 15u) - 1;
+  int k = 0;
+  for (int a = 0; a < na; ++a) {
+    if (coef_norm(w, Bd, o0, npar, p, a) >= thr) ++k;
+    else w[4 * p + a] = T(0);
+  }
+  if (k) atomicAdd(kept, (unsigned long long)k);
+}
+
+template <typename T>
+void launch_coef_max(const T* w, const T* Bd, int o0, int64_t npar, const uint32_t* pmask,
+                     unsigned long long* cmax, cudaStream_t s) {
+  if (npar > 0) { count_launch(); k_coef_max<T><<<(unsigned)((npar + 255) / 256), 256, 0, s>>>(w, Bd, o0, npar, pmask, cmax); }
+}
+template <typename T>
+void launch_coef_threshold(T* w, const T* Bd, int o0, int64_t npar, const uint32_t* pmask,
+                           double thr, unsigned long long* kept, cudaStream_t s) {
+  if (npar > 0) { count_launch(); k_coef_threshold<T><<<(unsigned)((npar + 255) / 256), 256, 0, s>>>(w, Bd, o0, npar, pmask, thr, kept); }
+}
+template void launch_coef_max<float>(const float*, const float*, int, int64_t, const uint32_t*,
+                                     unsigned long long*, cudaStream_t);
+template void launch_coef_max<double>(const double*, const double*, int, int64_t,
+                                      const uint32_t*, unsigned long long*, cudaStream_t);
+template void launch_coef_threshold<float>(float*, const float*, int, int64_t, const uint32_t*,
+                                           double, unsigned long long*, cudaStream_t);
+template void launch_coef_threshold<double>(double*, const double*, int, int64_t,
+                                            const uint32_t*, double, unsigned long long*,
+                                            cudaStream_t);
+
+// out = a x + b y + c z (y, z may be NULL); out may alias x.
+__global__ void k_lanczos_step(int64_t n, double a, const double* x, const double* y, double b,
+                               const double* z, double c, double* out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = a * x[i];
+  if (y) v += b * y[i];
+  if (z) v += c * z[i];
+  out[i] = v;
+}
+void launch_lanczos_step(int64_t n, double a, const double* x, const double* y, double b,
+                         const double* z, double c, double* out, cudaStream_t s) {
+  if (n > 0) { count_launch(); k_lanczos_step<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, x, y, b, z, c, out); }
+}
+
 }  // namespace gb

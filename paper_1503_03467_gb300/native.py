@@ -86,6 +86,12 @@ SIGNATURES = {
                                              ctypes.POINTER(ctypes.c_int32)]),
     "gamblet_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.POINTER(Info)]),
+    "gamblet_level_condition": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double)]),
+    "gamblet_compress": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64)]),
     "gamblet_solve_truncated": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.POINTER(Info)]),
     "gamblet_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
@@ -230,6 +236,23 @@ def gamblet_solve(h: int, g, u, components=None, info: Info | None = None) -> in
     st = _lib.gamblet_solve(ctypes.c_void_p(h), _ptr(g, np.float64), _ptr(u, np.float64),
                             _ptr(components, np.float64), ctypes.byref(info))
     return _check(st)
+
+
+def gamblet_level_condition(h: int, k: int, steps: int = 60):
+    """(lmin, lmax) estimates of B^(k)'s extreme eigenvalues (Lanczos)."""
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.gamblet_level_condition(ctypes.c_void_p(h), int(k), int(steps), ctypes.byref(lo),
+                                        ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def gamblet_compress(h: int, g, eps: float, u):
+    """u <- g's solution rebuilt from its normalised coefficients >= eps *
+    max; returns (kept, total)."""
+    kept, total = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.gamblet_compress(ctypes.c_void_p(h), _ptr(g, np.float64), float(eps),
+                                 _ptr(u, np.float64), ctypes.byref(kept), ctypes.byref(total)))
+    return kept.value, total.value
 
 
 def gamblet_solve_truncated(h: int, k: int, g, u, info: Info | None = None) -> int:
