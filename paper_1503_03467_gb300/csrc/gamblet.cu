@@ -350,6 +350,8 @@ struct gamblet_ctx {
   int cg_nlev = 0;
   int cg_max_ts = 1;
   cudaGraphExec_t cg_exec = nullptr;
+  bool cg_while = false;           // cg_exec is a device-side while loop
+  int* cg_loop_count = nullptr;    // passes of that loop
   // outer
   double* u64 = nullptr;
   double* r64 = nullptr;
@@ -1240,23 +1242,57 @@ void alloc_solve(gamblet_ctx* h) {
     h->cg_lv = P.upload(cl, s);
     h->cg_sc = P.zeros<CgScalars>(std::max(h->cg_nlev, 1), s);
     h->any_active = P.zeros<int>(1, s);
+    h->cg_loop_count = P.zeros<int>(1, s);
   }
 }
 
 // ------------------------------------------------------------ gamblet operator
-// Capture `chunk` CG iterations (all levels) once per handle.
+// The batched level CG as one graph: a device-side while loop (conditional
+// node) whose body is one CG iteration of every level; the scalar kernel of
+// the body sets the loop condition from the levels' convergence, so the
+// whole CG runs without host synchronisation.  Falls back to chunks of
+// `chunk` captured iterations with a host check between chunks when the
+// driver offers no conditional nodes.
 template <typename T>
 void build_cg_graph(gamblet_ctx* h, int chunk, double tol2, int maxit) {
   cudaStream_t cs;
   CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t g;
-  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  for (int c = 0; c < chunk; ++c) {
-    launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_spmv_blocks, h->cg_sc, h->cg_max_ts, cs);
-    launch_cg_rest<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit, h->any_active,
-                      cs);
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle cond = 0;
+  bool while_ok = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) ==
+                  cudaSuccess;
+  cudaGraphNode_t node;
+  cudaGraphNodeParams cp{};
+  if (while_ok) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    while_ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
   }
-  CK(cudaStreamEndCapture(cs, &g));
+  cudaGetLastError();
+  if (while_ok) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_spmv_blocks, h->cg_sc, h->cg_max_ts, cs);
+    launch_cg_rest<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit, h->any_active, cs,
+                      cond, 1, h->cg_loop_count, maxit + 2);
+    cudaGraph_t captured;
+    CK(cudaStreamEndCapture(cs, &captured));
+    h->cg_while = true;
+  } else {
+    CK(cudaGraphDestroy(g));
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int c = 0; c < chunk; ++c) {
+      launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_spmv_blocks, h->cg_sc, h->cg_max_ts, cs);
+      launch_cg_rest<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit, h->any_active,
+                        cs);
+    }
+    CK(cudaStreamEndCapture(cs, &g));
+    h->cg_while = false;
+  }
   CK(cudaGraphInstantiate(&h->cg_exec, g, 0));
   CK(cudaGraphDestroy(g));
   CK(cudaStreamDestroy(cs));
@@ -1270,31 +1306,40 @@ void run_level_cg(gamblet_ctx* h) {
   const int maxit = std::max(h->opts.level_max_iter, 1);
   const int chunk = 8;
   CK(cudaMemsetAsync(h->cg_sc, 0, sizeof(CgScalars) * h->cg_nlev, s));
+  CK(cudaMemsetAsync(h->cg_loop_count, 0, sizeof(int), s));
   launch_cg_init<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, s);
   // CG level l solves level k = l + 2; a truncated solve stops at h->kmax
   launch_cg_start(h->cg_sc, h->cg_nlev, std::max(h->kmax - 1, 0), tol2, h->any_active, s);
   if (h->opts.use_graph && !h->cg_exec) build_cg_graph<T>(h, chunk, tol2, maxit);
-  for (int it = 0; it < maxit; it += chunk) {
-    if (h->cg_exec) {
-      // with graphs the CG kernels are timed together, per chunk
-      int tok = h->prof.begin("level_cg", 0.0, 0.0, s);
-      CK(cudaGraphLaunch(h->cg_exec, s));
-      h->prof.end(tok, s);
-    } else {
-      for (int c = 0; c < chunk; ++c) {
-        int tok = h->prof.begin("level_cg_spmv", 0.0, 0.0, s);
-        launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_spmv_blocks, h->cg_sc, h->cg_max_ts, s);
-        h->prof.end(tok, s);
-        tok = h->prof.begin("level_cg_vector", 0.0, 0.0, s);
-        launch_cg_rest<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit,
-                          h->any_active, s);
-        h->prof.end(tok, s);
-      }
-    }
+  if (h->cg_exec && h->cg_while) {
+    // the whole CG in one launch (timed as one "level_cg" entry)
+    int tok = h->prof.begin("level_cg", 0.0, 0.0, s);
+    CK(cudaGraphLaunch(h->cg_exec, s));
+    h->prof.end(tok, s);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(h->any_active_h, h->any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (*h->any_active_h == 0) break;
+  } else {
+    for (int it = 0; it < maxit; it += chunk) {
+      if (h->cg_exec) {
+        // with graphs the CG kernels are timed together, per chunk
+        int tok = h->prof.begin("level_cg", 0.0, 0.0, s);
+        CK(cudaGraphLaunch(h->cg_exec, s));
+        h->prof.end(tok, s);
+      } else {
+        for (int c = 0; c < chunk; ++c) {
+          int tok = h->prof.begin("level_cg_spmv", 0.0, 0.0, s);
+          launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_spmv_blocks, h->cg_sc, h->cg_max_ts, s);
+          h->prof.end(tok, s);
+          tok = h->prof.begin("level_cg_vector", 0.0, 0.0, s);
+          launch_cg_rest<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, tol2, maxit,
+                            h->any_active, s);
+          h->prof.end(tok, s);
+        }
+      }
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(h->any_active_h, h->any_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (*h->any_active_h == 0) break;
+    }
   }
   std::vector<CgScalars> sc(h->cg_nlev);
   CK(cudaMemcpyAsync(sc.data(), h->cg_sc, sizeof(CgScalars) * h->cg_nlev, cudaMemcpyDeviceToHost,

@@ -282,9 +282,14 @@ void launch_cg_start(CgScalars* sc, int nlev, int nlev_on, double tol2, int* any
 template <typename T>
 void launch_cg_spmv(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, int max_ts,
                     cudaStream_t s);  // total_blocks: SpMV grid size
+// Inside a device-side while loop (use_cond = 1) the scalar kernel sets the
+// loop condition `cond`: continue while a level iterates and fewer than
+// loop_limit passes ran (*loop_count counts them).
 template <typename T>
 void launch_cg_rest(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, double tol2,
-                    int max_iter, int* any_active, cudaStream_t s);
+                    int max_iter, int* any_active, cudaStream_t s,
+                    cudaGraphConditionalHandle cond = 0, int use_cond = 0,
+                    int* loop_count = nullptr, int loop_limit = 0);
 // Coalesced detail-block copy and block-Jacobi inverses of one level.
 template <typename T>
 void launch_cg_level_setup(const T* Ahat, int noff, int o0, int64_t npar, const uint32_t* pmask,

@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(256) k_cg_update(const CgLevel* __restrict__ l
 
 // beta, convergence on |r|_2, counters; one thread so any_active is exact
 __global__ void k_cg_scalars(CgScalars* sc, int nlev, double tol2, int max_iter,
-                             int* any_active) {
+                             int* any_active, cudaGraphConditionalHandle cond, int use_cond,
+                             int* loop_count, int loop_limit) {
   if (threadIdx.x != 0) return;
   int act = 0;
   for (int l = 0; l < nlev; ++l) {
@@ -254,6 +255,12 @@ __global__ void k_cg_scalars(CgScalars* sc, int nlev, double tol2, int max_iter,
     sc[l] = s;
   }
   *any_active = act;
+  if (use_cond) {
+    // body of a device-side while loop: continue while a level iterates;
+    // the per-level caps end it, the pass counter bounds it regardless
+    const int c = ++(*loop_count);
+    cudaGraphSetConditional(cond, (act && c < loop_limit) ? 1u : 0u);
+  }
 }
 
 // p = z + beta p
@@ -304,10 +311,12 @@ void launch_cg_spmv(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc
 
 template <typename T>
 void launch_cg_rest(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, double tol2,
-                    int max_iter, int* any_active, cudaStream_t s) {
+                    int max_iter, int* any_active, cudaStream_t s,
+                    cudaGraphConditionalHandle cond, int use_cond, int* loop_count,
+                    int loop_limit) {
   if (total_blocks <= 0) return;
   { count_launch(); k_cg_update<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
-  { count_launch(); k_cg_scalars<<<1, 32, 0, s>>>(sc, nlev, tol2, max_iter, any_active); }
+  { count_launch(); k_cg_scalars<<<1, 32, 0, s>>>(sc, nlev, tol2, max_iter, any_active, cond, use_cond, loop_count, loop_limit); }
   { count_launch(); k_cg_dir<T><<<total_blocks, 256, 0, s>>>(lv, nlev, sc); }
 }
 
@@ -316,9 +325,9 @@ template void launch_cg_init<double>(const CgLevel*, int, int, CgScalars*, cudaS
 template void launch_cg_spmv<float>(const CgLevel*, int, int, CgScalars*, int, cudaStream_t);
 template void launch_cg_spmv<double>(const CgLevel*, int, int, CgScalars*, int, cudaStream_t);
 template void launch_cg_rest<float>(const CgLevel*, int, int, CgScalars*, double, int, int*,
-                                    cudaStream_t);
+                                    cudaStream_t, cudaGraphConditionalHandle, int, int*, int);
 template void launch_cg_rest<double>(const CgLevel*, int, int, CgScalars*, double, int, int*,
-                                     cudaStream_t);
+                                     cudaStream_t, cudaGraphConditionalHandle, int, int*, int);
 
 // ---------------------------------------------------------------- set-up helpers
 // Bd[o][3a+b][p] = Ahat[o][p][4a+b] (detail block, coalesced copy).
