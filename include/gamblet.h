@@ -222,6 +222,25 @@ GAMBLET_API gamblet_status gamblet_solve(gamblet_handle h, const double* g, doub
                              double* components, gamblet_info* info);
 
 /*
+ * Several right-hand sides with one hierarchy (Sec. 5.4, subsequent
+ * solves).  Right-hand sides go through the gamblet operator in groups of
+ * up to four: the restriction, the level CG, the prolongation and the
+ * float64 outer product read each matrix (Rhat, the level blocks, RT,
+ * Ahat^(q)) once for the whole group (a sparse matrix times a block of
+ * vectors); each right-hand side keeps its own outer flexible CG and stops
+ * when it reaches refine_tol.
+ *   nrhs  number of right-hand sides (>= 1).
+ *   G     nrhs x n float64, row-major: right-hand side r at G + r * n.
+ *   U     nrhs x n float64 output, same layout.
+ *   info  NULL or receives the largest outer iteration count and the
+ *         worst final relative residual.
+ * Returns NOT_CONVERGED (U still written) if a right-hand side hit the cap.
+ * Localized transform only.
+ */
+GAMBLET_API gamblet_status gamblet_solve_many(gamblet_handle h, int32_t nrhs, const double* G,
+                                              double* U, gamblet_info* info);
+
+/*
  * Truncated one-pass solve (Sec. 5.4, subsequent solves): u^(k) = u^(1) +
  * sum_{l=2..k} (u^(l) - u^(l-1)), the Galerkin approximation of u in the
  * span of the level-k gamblets psi^(k) (Theorem thddwedmgugyug, Eq.

@@ -1867,6 +1867,284 @@ gamblet_ctx* setup_batched_impl(int32_t nprob, const gamblet_csr* A, const int32
   return h;
 }
 
+// ------------------------------------------------------------ several right-hand sides
+// Buffers of one group of nb <= kMaxRhs right-hand sides: per level the
+// transformed right-hand sides, level solutions, CG vectors and prolongated
+// vectors, each [nb][ncell_k]; the CG level table and scalars of the group.
+template <typename T>
+struct RhsGroup {
+  int nb = 0;
+  std::vector<T*> ghat, w, v, cr, cz, cp, cAp;  // index k
+  T* g1 = nullptr;
+  T* U1 = nullptr;
+  CgLevel* lv = nullptr;
+  CgScalars* sc = nullptr;
+  int* any = nullptr;
+};
+
+template <typename T>
+RhsGroup<T> make_group(gamblet_ctx* h, Pool& P, int nb) {
+  cudaStream_t s = h->s;
+  const int q = h->q;
+  RhsGroup<T> G;
+  G.nb = nb;
+  G.ghat.assign(q + 1, nullptr);
+  G.w = G.v = G.cr = G.cz = G.cp = G.cAp = G.ghat;
+  for (int k = 2; k <= q; ++k) {
+    const int64_t n = h->lv[k].ncell * nb;
+    G.ghat[k] = P.zeros<T>(n, s);
+    G.w[k] = P.zeros<T>(n, s);
+    G.v[k] = P.zeros<T>(n, s);
+    G.cr[k] = P.zeros<T>(n, s);
+    G.cz[k] = P.zeros<T>(n, s);
+    G.cp[k] = P.zeros<T>(n, s);
+    G.cAp[k] = P.zeros<T>(n, s);
+  }
+  G.g1 = P.zeros<T>(4 * nb, s);
+  G.U1 = P.zeros<T>(4 * nb, s);
+  std::vector<CgLevel> cl(h->cg_nlev);
+  CK(cudaMemcpyAsync(cl.data(), h->cg_lv, sizeof(CgLevel) * h->cg_nlev, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int l = 0; l < h->cg_nlev; ++l) {
+    const int k = l + 2;
+    cl[l].x = G.w[k];
+    cl[l].r = G.cr[k];
+    cl[l].z = G.cz[k];
+    cl[l].p = G.cp[k];
+    cl[l].Ap = G.cAp[k];
+    cl[l].b = G.ghat[k];
+    cl[l].rstride = h->lv[k].ncell;
+  }
+  G.lv = P.upload(cl, s);
+  G.sc = P.zeros<CgScalars>(std::max(h->cg_nlev, 1) * nb, s);
+  G.any = P.zeros<int>(1, s);
+  return G;
+}
+
+// The gamblet operator on nb transformed level-q vectors (in, out: [nb][ncell_q]).
+template <typename T>
+void apply_G_many(gamblet_ctx* h, RhsGroup<T>& G, const T* in, T* out, int inverse_last) {
+  cudaStream_t s = h->s;
+  const int q = h->q;
+  const int NB = h->N.size();
+  const int nb = G.nb;
+  const int64_t nq = h->lv[q].ncell;
+  CK(cudaMemcpyAsync(G.ghat[q], in, sizeof(T) * nq * nb, cudaMemcpyDeviceToDevice, s));
+  for (int k = q; k >= 2; --k) {
+    LevelDev& L = h->lv[k];
+    const bool lower = k - 1 >= 2;
+    int tok = h->prof.begin("restrict", 0.0, 0.0, s);
+    launch_restrict_m<T>((const T*)L.Rhat, NB, h->nbr, 1 << (k - 1), L.npar, G.ghat[k], L.ncell,
+                         lower ? G.ghat[k - 1] : G.g1, lower ? h->lv[k - 1].ncell : 4,
+                         lower ? h->lv[k - 1].pmask : nullptr, nb, s);
+    h->prof.end(tok, s);
+  }
+  if (h->cg_nlev > 0) {
+    const double tol2 = h->opts.level_tol * h->opts.level_tol;
+    const int maxit = std::max(h->opts.level_max_iter, 1);
+    CK(cudaMemsetAsync(G.sc, 0, sizeof(CgScalars) * h->cg_nlev * nb, s));
+    launch_cgm_init<T>(G.lv, h->cg_nlev, h->cg_blocks, G.sc, nb, s);
+    launch_cgm_start(G.sc, h->cg_nlev * nb, tol2, G.any, s);
+    for (int it = 0; it < maxit; it += 8) {
+      int tok = h->prof.begin("level_cg", 0.0, 0.0, s);
+      for (int c = 0; c < 8; ++c)
+        launch_cgm_iteration<T>(G.lv, h->cg_nlev, h->cg_spmv_blocks, h->cg_blocks, G.sc, nb,
+                                h->cg_max_ts, tol2, maxit, G.any, s);
+      h->prof.end(tok, s);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(h->any_active_h, G.any, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (*h->any_active_h == 0) break;
+    }
+  }
+  for (int r = 0; r < nb; ++r) launch_level1_solve<T>(h->A1L, G.g1 + 4 * r, G.U1 + 4 * r, s);
+  for (int k = 2; k <= q; ++k) {
+    LevelDev& L = h->lv[k];
+    const T* vprev = k == 2 ? G.U1 : G.v[k - 1];
+    const int64_t vstride = k == 2 ? 4 : h->lv[k - 1].ncell;
+    T* dst = k == q ? out : G.v[k];
+    int tok = h->prof.begin("prolong", 0.0, 0.0, s);
+    launch_prolong_m<T>((const T*)L.RT, NB, h->nbr, 1 << (k - 1), L.npar, vprev, vstride, G.w[k],
+                        L.ncell, L.pmask, k == q ? inverse_last : 1, dst, L.ncell, nb, s);
+    h->prof.end(tok, s);
+  }
+  CK(cudaGetLastError());
+}
+
+// nb right-hand sides (rows of G_user) solved together: the one-pass
+// transform preconditions a float64 flexible CG per right-hand side, all
+// sharing each pass's matrix reads.
+template <typename T>
+void solve_group(gamblet_ctx* h, int nb, const double* G_user, double* U_user, double* worst_res,
+                 int* max_outer, bool* not_conv) {
+  cudaStream_t s = h->s;
+  Pool tmp;
+  tmp.s = s;
+  const int q = h->q;
+  LevelDev& Lq = h->lv[q];
+  const int64_t nq = Lq.ncell, n = h->n;
+  RhsGroup<T> Gp = make_group<T>(h, tmp, nb);
+  double* g64 = tmp.zeros<double>(nq * nb, s);
+  double* u64 = tmp.zeros<double>(nq * nb, s);
+  double* r64 = tmp.zeros<double>(nq * nb, s);
+  double* z64 = tmp.zeros<double>(nq * nb, s);
+  double* p64 = tmp.zeros<double>(nq * nb, s);
+  double* q64 = tmp.zeros<double>(nq * nb, s);
+  T* rT = is_f32<T>() ? (T*)tmp.zeros<float>(nq * nb, s) : nullptr;
+  T* zT = is_f32<T>() ? (T*)tmp.zeros<float>(nq * nb, s) : nullptr;
+  double* d = tmp.zeros<double>(8 * nb, s);
+  double* gin = nullptr;
+  to_device(tmp, gin, G_user, n * nb, s);
+  for (int r = 0; r < nb; ++r) {
+    launch_gather_morton(gin + r * n, h->unknown_of, nq, g64 + r * nq, s);
+    launch_transform_vec<double>(g64 + r * nq, g64 + r * nq, Lq.npar, Lq.pmask, +1, s);
+    launch_dots(nq, g64 + r * nq, g64 + r * nq, nullptr, nullptr, nullptr, nullptr, d + 8 * r, s);
+  }
+  std::vector<double> dh(8 * nb);
+  CK(cudaMemcpyAsync(dh.data(), d, sizeof(double) * 8 * nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> gnorm(nb);
+  for (int r = 0; r < nb; ++r) gnorm[r] = std::sqrt(dh[8 * r]);
+  // z = G r for the whole group (float path through float copies)
+  auto precondition = [&](double* src, double* dst) {
+    if (is_f32<T>()) {
+      launch_convert_f64_f32(src, (float*)rT, nq * nb, s);
+      apply_G_many<T>(h, Gp, rT, zT, 0);
+      launch_convert_f32_f64((const float*)zT, dst, nq * nb, s);
+    } else {
+      apply_G_many<T>(h, Gp, (const T*)src, (T*)dst, 0);
+    }
+  };
+  precondition(g64, z64);
+  CK(cudaMemcpyAsync(u64, z64, sizeof(double) * nq * nb, cudaMemcpyDeviceToDevice, s));
+  const int maxit = h->opts.refine_max_iter;
+  const int Lpar = 1 << (q - 1);
+  std::vector<double> rel(nb, 0.0);
+  std::vector<int> active(nb, 0), outer(nb, 0);
+  double one = 1.0;
+  double* onep = tmp.upload(std::vector<double>(nb, 1.0), s);
+  auto residual = [&]() {  // r = g - A u, rel = |r| / |g|
+    launch_block_spmv64_m(Lq.Ahat64, Lq.off, Lq.noff, Lpar, Lq.npar, u64, q64, nq, nb, s);
+    CK(cudaMemcpyAsync(r64, g64, sizeof(double) * nq * nb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(d, 0, sizeof(double) * 8 * nb, s));
+    for (int r = 0; r < nb; ++r) {
+      launch_axpy(nq, onep + r, onep + r, -1.0, q64 + r * nq, r64 + r * nq, s);
+      launch_dots(nq, r64 + r * nq, r64 + r * nq, nullptr, nullptr, nullptr, nullptr, d + 8 * r, s);
+    }
+    CK(cudaMemcpyAsync(dh.data(), d, sizeof(double) * 8 * nb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int r = 0; r < nb; ++r) rel[r] = gnorm[r] > 0 ? std::sqrt(dh[8 * r]) / gnorm[r] : 0.0;
+  };
+  (void)one;
+  if (maxit > 0) {
+    residual();
+    int nact = 0;
+    for (int r = 0; r < nb; ++r) nact += active[r] = rel[r] > h->opts.refine_tol;
+    if (nact) {
+      precondition(r64, z64);
+      CK(cudaMemcpyAsync(p64, z64, sizeof(double) * nq * nb, cudaMemcpyDeviceToDevice, s));
+      for (int it = 1; it <= maxit && nact; ++it) {
+        int tok = h->prof.begin("outer_spmv64", 0.0, 0.0, s);
+        launch_block_spmv64_m(Lq.Ahat64, Lq.off, Lq.noff, Lpar, Lq.npar, p64, q64, nq, nb, s);
+        h->prof.end(tok, s);
+        CK(cudaMemsetAsync(d, 0, sizeof(double) * 8 * nb, s));
+        for (int r = 0; r < nb; ++r) {
+          if (!active[r]) continue;
+          double* dr = d + 8 * r;
+          const int64_t o = r * nq;
+          launch_dots(nq, p64 + o, q64 + o, p64 + o, r64 + o, nullptr, nullptr, dr, s);
+          launch_axpy(nq, dr + 1, dr + 0, +1.0, p64 + o, u64 + o, s);
+          launch_axpy(nq, dr + 1, dr + 0, -1.0, q64 + o, r64 + o, s);
+          launch_dots(nq, nullptr, nullptr, nullptr, nullptr, r64 + o, r64 + o, dr, s);
+        }
+        CK(cudaMemcpyAsync(dh.data(), d, sizeof(double) * 8 * nb, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        nact = 0;
+        for (int r = 0; r < nb; ++r) {
+          if (!active[r]) continue;
+          outer[r] = it;
+          rel[r] = gnorm[r] > 0 ? std::sqrt(dh[8 * r + 2]) / gnorm[r] : 0.0;
+          if (!(rel[r] == rel[r])) fail(GAMBLET_ERR_NOT_SPD, "outer iteration produced NaN");
+          if (rel[r] <= h->opts.refine_tol) active[r] = 0;
+          nact += active[r];
+        }
+        if (!nact) break;
+        precondition(r64, z64);
+        for (int r = 0; r < nb; ++r) {
+          if (!active[r]) continue;
+          double* dr = d + 8 * r;
+          const int64_t o = r * nq;
+          launch_dots(nq, z64 + o, q64 + o, nullptr, nullptr, nullptr, nullptr, dr + 3, s);
+          launch_xpby(nq, z64 + o, dr + 3, dr + 0, -1.0, p64 + o, s);
+        }
+        CK(cudaGetLastError());
+      }
+      for (int r = 0; r < nb; ++r)
+        if (active[r]) *not_conv = true;
+    }
+    residual();
+  }
+  for (int r = 0; r < nb; ++r) {
+    *worst_res = std::max(*worst_res, rel[r]);
+    *max_outer = std::max(*max_outer, outer[r]);
+  }
+  // back to unknown order (nodal coefficients after a mass initialisation)
+  const bool dev_out = is_device_ptr(U_user);
+  double* uo = dev_out ? U_user : tmp.alloc<double>(n * nb);
+  for (int r = 0; r < nb; ++r) {
+    launch_transform_vec<double>(u64 + r * nq, q64 + r * nq, Lq.npar, Lq.pmask, -1, s);
+    if (h->mass) {
+      double* Ut = tmp.alloc<double>(n);
+      launch_scatter_unknown(q64 + r * nq, h->morton_of, n, Ut, s);
+      launch_mass_apply(n, h->NBq, h->nbrq, h->Minv, Ut, h->morton_of, h->unknown_of, 1 << q,
+                        Lq.ncell, uo + r * n, s);
+    } else {
+      launch_scatter_unknown(q64 + r * nq, h->morton_of, n, uo + r * n, s);
+    }
+  }
+  if (!dev_out)
+    CK(cudaMemcpyAsync(U_user, uo, sizeof(double) * n * nb, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+}
+
+template <typename T>
+gamblet_status solve_many_impl(gamblet_ctx* h, int nrhs, const double* G, double* U,
+                               gamblet_info* info) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, h->s));
+  double worst = 0;
+  int outer = 0;
+  bool not_conv = false;
+  for (int r0 = 0; r0 < nrhs; r0 += kMaxRhs) {
+    const int nb = std::min(kMaxRhs, nrhs - r0);
+    solve_group<T>(h, nb, G + (int64_t)r0 * h->n, U + (int64_t)r0 * h->n, &worst, &outer,
+                   &not_conv);
+  }
+  CK(cudaEventRecord(e1, h->s));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->prof.resolve();
+  check_status(h, "solve");
+  const gamblet_status st = not_conv ? GAMBLET_ERR_NOT_CONVERGED : GAMBLET_OK;
+  if (info) {
+    info->status = st;
+    info->q = h->q;
+    info->outer_iters = outer;
+    info->rel_residual = worst;
+    info->setup_ms = h->setup_ms;
+    info->solve_ms = ms;
+    info->patch_iters_max = h->patch_iters_max;
+    info->patch_iters_mean = h->patch_iters_mean;
+  }
+  return st;
+}
+
 // Level-q initialisation by the mass matrix (Algorithm 2, lines 2a-5 with
 // Definition deflocinvm): M^-1,loc on patches of radius rho_q around every
 // node, A^(q),loc = (M^-1,loc)^T A M^-1,loc as a CSR, then the ordinary
@@ -2256,6 +2534,20 @@ gamblet_status gamblet_setup_batched(int32_t nprob, const gamblet_csr* A, const 
   } catch (const std::exception& e) {
     g_last_error = e.what();
     return GAMBLET_ERR_INVALID_ARG;
+  }
+}
+
+gamblet_status gamblet_solve_many(gamblet_handle h, int32_t nrhs, const double* G, double* U,
+                                  gamblet_info* info) {
+  try {
+    if (!h || !G || !U || nrhs < 1)
+      fail(GAMBLET_ERR_INVALID_ARG, "handle, G and U must be non-NULL and nrhs >= 1");
+    if (h->exact) fail(GAMBLET_ERR_UNSUPPORTED, "several right-hand sides use the localized transform");
+    if (h->mixed) return solve_many_impl<float>(h, nrhs, G, U, info);
+    return solve_many_impl<double>(h, nrhs, G, U, info);
+  } catch (const GbError& e) {
+    if (info) info->status = e.st;
+    return set_error(e);
   }
 }
 

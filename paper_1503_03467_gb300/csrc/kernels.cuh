@@ -258,7 +258,8 @@ struct CgLevel {
   const void* b;      // right-hand side (transformed vector; slots 0..2 used)
   int block_begin;    // first CTA of this level in the vector-kernel grid
   int spmv_begin;     // first CTA of this level in the SpMV grid
-  int spp;            // SpMV threads per parent (1: 16 x 16 tiles, 4: 8 x 8 tiles)
+  int spp;            // SpMV threads per parent (1: 16 x 16 tiles, 4: 8 x 8, 16: 4 x 4)
+  int64_t rstride;    // several right-hand sides: distance between their vectors
 };
 struct CgScalars {
   double rz, rz_new, rr, rr_new, pAp, rr0, beta;
@@ -342,5 +343,33 @@ void launch_dense_rhat(const double* Y, const int32_t* det, int nJ, const int32_
 void launch_scatter_det(const double* wc, const int32_t* det, int nJ, double* w, cudaStream_t s);
 void launch_gather_det(const double* w, const int32_t* det, int nJ, double* wc, cudaStream_t s);
 void launch_level1_factor_dense(const double* A, double* L, int* status, cudaStream_t s);
+
+// ---------------------------------------------------------------- several right-hand sides
+// Up to kMaxRhs vectors per pass; each is a separate vector, the one of
+// right-hand side r at base + r * stride.  The matrix data (Rhat, RT, the
+// level blocks, Ahat^(q)) is read once for all of them.
+constexpr int kMaxRhs = 4;
+template <typename T>
+void launch_restrict_m(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t nrow,
+                       const T* ghat_k, int64_t gstride, T* g_km1, int64_t ostride,
+                       const uint32_t* pmask_km1, int nrhs, cudaStream_t s);
+template <typename T>
+void launch_prolong_m(const T* RT, int NB, const int2* nbr, int Lpar, int64_t npar,
+                      const T* v_km1, int64_t vstride, const T* w_k, int64_t wstride,
+                      const uint32_t* pmask_k, int inverse, T* out, int64_t ostride, int nrhs,
+                      cudaStream_t s);
+void launch_block_spmv64_m(const double* Ahat, const int2* off, int noff, int Lpar, int64_t npar,
+                           const double* x, double* y, int64_t stride, int nrhs, cudaStream_t s);
+// The batched level CG over (level, right-hand side): scalars sc[l * nrhs + r],
+// vectors of right-hand side r at CgLevel pointer + r * rstride.
+template <typename T>
+void launch_cgm_init(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, int nrhs,
+                     cudaStream_t s);
+void launch_cgm_start(CgScalars* sc, int n, double tol2, int* any_active, cudaStream_t s);
+template <typename T>
+void launch_cgm_iteration(const CgLevel* lv, int nlev, int spmv_blocks, int total_blocks,
+                          CgScalars* sc, int nrhs, int max_ts, double tol2, int max_iter,
+                          int* any_active, cudaStream_t s);
+size_t cgm_spmv_smem_bytes(int max_ts, size_t elem, int nrhs);
 
 }  // namespace gb

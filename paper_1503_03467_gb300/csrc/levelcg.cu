@@ -457,4 +457,269 @@ template void launch_detail_spmv<float>(const float*, const int2*, int, int, int
 template void launch_detail_spmv<double>(const double*, const int2*, int, int, int64_t,
                                          const double*, double*, cudaStream_t);
 
+// ---------------------------------------------------------------- several right-hand sides
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgm_init(const CgLevel* __restrict__ lv, int nlev,
+                                                  CgScalars* sc, int nrhs) {
+  __shared__ double red[8];
+  const int l = find_level(lv, nlev, blockIdx.x);
+  const int rh = blockIdx.y;
+  const CgLevel L = lv[l];
+  const int64_t off = rh * L.rstride;
+  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
+  double rz = 0, rr = 0;
+  if (p < L.npar) {
+    const T* b = (const T*)L.b + off;
+    T rv[3], zv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rv[a] = b[4 * p + a];
+    apply_dinv<T>((const T*)L.Dinv, L.npar, p, rv, zv);
+    T* x = (T*)L.x + off;
+    T* r = (T*)L.r + off;
+    T* z = (T*)L.z + off;
+    T* pp = (T*)L.p + off;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      x[4 * p + a] = 0;
+      r[4 * p + a] = rv[a];
+      z[4 * p + a] = zv[a];
+      pp[4 * p + a] = zv[a];
+      rz += (double)rv[a] * (double)zv[a];
+      rr += (double)rv[a] * (double)rv[a];
+    }
+    x[4 * p + 3] = 0;
+    pp[4 * p + 3] = 0;
+  }
+  block_sum_add(rz, &sc[l * nrhs + rh].rz, red);
+  block_sum_add(rr, &sc[l * nrhs + rh].rr, red);
+}
+
+__global__ void k_cgm_start(CgScalars* sc, int n, double tol2, int* any_active) {
+  if (threadIdx.x != 0) return;
+  int act = 0;
+  for (int i = 0; i < n; ++i) {
+    CgScalars s = sc[i];
+    s.rr0 = s.rr;
+    s.active = s.rr > 0.0 && s.rz > 0.0;
+    s.iters = 0;
+    s.pAp = 0;
+    s.rz_new = 0;
+    s.rr_new = 0;
+    act |= s.active;
+    sc[i] = s;
+  }
+  *any_active = act;
+}
+
+// Ap = B p for every active right-hand side of the tile's level: the halo
+// of each right-hand side is staged in shared memory and each 3x3 block is
+// read once for all of them.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgm_spmv(const CgLevel* __restrict__ lv, int nlev,
+                                                  CgScalars* sc, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[8];
+  const int l = find_level_spmv(lv, nlev, blockIdx.x);
+  int act = 0;
+  for (int r = 0; r < nrhs; ++r) act |= sc[l * nrhs + r].active << r;
+  if (!act) return;
+  const CgLevel L = lv[l];
+  const int spp = L.spp;
+  const int tmax = cg_tile_side(spp);
+  const int tile = L.Lpar < tmax ? L.Lpar : tmax;
+  const int R = L.R;
+  const int TS = tile + 2 * R;
+  const int plane = TS * TS;
+  T* xs = reinterpret_cast<T*>(smem_raw);  // [nrhs][3][TS * TS]
+  const int64_t base = (int64_t)(blockIdx.x - L.spmv_begin) * (tmax * tmax);
+  int x0, y0;
+  demorton((uint32_t)base, x0, y0);
+  for (int c = threadIdx.x; c < plane; c += blockDim.x) {
+    const int gx = x0 - R + c % TS, gy = y0 - R + c / TS;
+    int64_t q = -1;
+    if ((unsigned)gx < (unsigned)L.Lpar && (unsigned)gy < (unsigned)L.Lpar) {
+      q = morton((uint32_t)gx, (uint32_t)gy);
+      if (q >= L.npar) q = -1;
+    }
+    for (int r = 0; r < nrhs; ++r) {
+      const T* pv = (const T*)L.p + r * L.rstride;
+      const bool on = q >= 0 && ((act >> r) & 1);
+      xs[(r * 3) * plane + c] = on ? pv[4 * q] : T(0);
+      xs[(r * 3 + 1) * plane + c] = on ? pv[4 * q + 1] : T(0);
+      xs[(r * 3 + 2) * plane + c] = on ? pv[4 * q + 2] : T(0);
+    }
+  }
+  __syncthreads();
+  const int pl = threadIdx.x / spp, sub = threadIdx.x - (threadIdx.x / spp) * spp;
+  const int64_t p = base + pl;
+  const bool own = pl < tile * tile && p < L.npar;
+  T yv[kMaxRhs][3];
+#pragma unroll
+  for (int r = 0; r < kMaxRhs; ++r) yv[r][0] = yv[r][1] = yv[r][2] = T(0);
+  int lx = 0, ly = 0;
+  if (own) {
+    int px, py;
+    demorton((uint32_t)p, px, py);
+    lx = px - x0 + R;
+    ly = py - y0 + R;
+    const T* Bd = (const T*)L.Bd;
+    const int64_t np = L.npar;
+    for (int o = sub; o < L.noff; o += spp) {
+      const int2 d = L.off[o];
+      const int c = (ly + d.y) * TS + lx + d.x;
+      const T* B = Bd + (int64_t)o * 9 * np + p;
+      T b[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) b[e] = B[e * np];
+#pragma unroll
+      for (int r = 0; r < kMaxRhs; ++r) {
+        if (r < nrhs) {
+          const T a0 = xs[(r * 3) * plane + c], a1 = xs[(r * 3 + 1) * plane + c],
+                  a2 = xs[(r * 3 + 2) * plane + c];
+          yv[r][0] += b[0] * a0 + b[1] * a1 + b[2] * a2;
+          yv[r][1] += b[3] * a0 + b[4] * a1 + b[5] * a2;
+          yv[r][2] += b[6] * a0 + b[7] * a1 + b[8] * a2;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kMaxRhs; ++r)
+    for (int o = 1; o < spp; o <<= 1)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) yv[r][a] += __shfl_xor_sync(0xffffffffu, yv[r][a], o);
+#pragma unroll
+  for (int r = 0; r < kMaxRhs; ++r) {
+    if (r >= nrhs) break;
+    double part = 0;
+    if (own && sub == 0 && ((act >> r) & 1)) {
+      T* Ap = (T*)L.Ap + r * L.rstride;
+      Ap[4 * p] = yv[r][0];
+      Ap[4 * p + 1] = yv[r][1];
+      Ap[4 * p + 2] = yv[r][2];
+      const int c0 = ly * TS + lx;
+      part = (double)xs[(r * 3) * plane + c0] * yv[r][0] +
+             (double)xs[(r * 3 + 1) * plane + c0] * yv[r][1] +
+             (double)xs[(r * 3 + 2) * plane + c0] * yv[r][2];
+    }
+    block_sum_add(part, &sc[l * nrhs + r].pAp, red);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgm_update(const CgLevel* __restrict__ lv, int nlev,
+                                                    CgScalars* sc, int nrhs) {
+  __shared__ double red[8];
+  const int l = find_level(lv, nlev, blockIdx.x);
+  const int rh = blockIdx.y;
+  CgScalars* S = &sc[l * nrhs + rh];
+  if (!S->active) return;
+  const CgLevel L = lv[l];
+  const int64_t off = rh * L.rstride;
+  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
+  double rz = 0, rr = 0;
+  if (p < L.npar) {
+    const double pAp = S->pAp;
+    const T alpha = pAp > 0 ? (T)(S->rz / pAp) : T(0);
+    T* x = (T*)L.x + off;
+    T* r = (T*)L.r + off;
+    T* z = (T*)L.z + off;
+    const T* pv = (const T*)L.p + off;
+    const T* Ap = (const T*)L.Ap + off;
+    T rv[3], zv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      x[4 * p + a] += alpha * pv[4 * p + a];
+      rv[a] = r[4 * p + a] - alpha * Ap[4 * p + a];
+      r[4 * p + a] = rv[a];
+    }
+    apply_dinv<T>((const T*)L.Dinv, L.npar, p, rv, zv);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      z[4 * p + a] = zv[a];
+      rz += (double)rv[a] * (double)zv[a];
+      rr += (double)rv[a] * (double)rv[a];
+    }
+  }
+  block_sum_add(rz, &S->rz_new, red);
+  block_sum_add(rr, &S->rr_new, red);
+}
+
+__global__ void k_cgm_scalars(CgScalars* sc, int n, double tol2, int max_iter, int* any_active) {
+  if (threadIdx.x != 0) return;
+  int act = 0;
+  for (int i = 0; i < n; ++i) {
+    CgScalars s = sc[i];
+    if (!s.active) continue;
+    s.iters += 1;
+    s.beta = s.rz > 0 ? s.rz_new / s.rz : 0.0;
+    s.rz = s.rz_new;
+    s.rr = s.rr_new;
+    s.rz_new = 0;
+    s.rr_new = 0;
+    s.pAp = 0;
+    if (s.rr <= tol2 * s.rr0 || s.iters >= max_iter || !(s.rr == s.rr) || !(s.rz > 0))
+      s.active = 0;
+    else
+      act = 1;
+    sc[i] = s;
+  }
+  *any_active = act;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_cgm_dir(const CgLevel* __restrict__ lv, int nlev,
+                                                 CgScalars* sc, int nrhs) {
+  const int l = find_level(lv, nlev, blockIdx.x);
+  const int rh = blockIdx.y;
+  const CgScalars* S = &sc[l * nrhs + rh];
+  if (!S->active) return;
+  const CgLevel L = lv[l];
+  const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
+  if (p >= L.npar) return;
+  const T beta = (T)S->beta;
+  T* pv = (T*)L.p + rh * L.rstride;
+  const T* z = (const T*)L.z + rh * L.rstride;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) pv[4 * p + a] = z[4 * p + a] + beta * pv[4 * p + a];
+}
+
+size_t cgm_spmv_smem_bytes(int max_ts, size_t elem, int nrhs) {
+  return 3 * elem * (size_t)max_ts * max_ts * (size_t)nrhs;
+}
+
+template <typename T>
+void launch_cgm_init(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc, int nrhs,
+                     cudaStream_t s) {
+  if (total_blocks <= 0) return;
+  count_launch();
+  k_cgm_init<T><<<dim3(total_blocks, nrhs), 256, 0, s>>>(lv, nlev, sc, nrhs);
+}
+void launch_cgm_start(CgScalars* sc, int n, double tol2, int* any_active, cudaStream_t s) {
+  count_launch();
+  k_cgm_start<<<1, 32, 0, s>>>(sc, n, tol2, any_active);
+}
+template <typename T>
+void launch_cgm_iteration(const CgLevel* lv, int nlev, int spmv_blocks, int total_blocks,
+                          CgScalars* sc, int nrhs, int max_ts, double tol2, int max_iter,
+                          int* any_active, cudaStream_t s) {
+  if (total_blocks <= 0) return;
+  const size_t smem = cgm_spmv_smem_bytes(max_ts, sizeof(T), nrhs);
+  cudaFuncSetAttribute(k_cgm_spmv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  count_launch();
+  k_cgm_spmv<T><<<spmv_blocks, 256, smem, s>>>(lv, nlev, sc, nrhs);
+  count_launch();
+  k_cgm_update<T><<<dim3(total_blocks, nrhs), 256, 0, s>>>(lv, nlev, sc, nrhs);
+  count_launch();
+  k_cgm_scalars<<<1, 32, 0, s>>>(sc, nlev * nrhs, tol2, max_iter, any_active);
+  count_launch();
+  k_cgm_dir<T><<<dim3(total_blocks, nrhs), 256, 0, s>>>(lv, nlev, sc, nrhs);
+}
+template void launch_cgm_init<float>(const CgLevel*, int, int, CgScalars*, int, cudaStream_t);
+template void launch_cgm_init<double>(const CgLevel*, int, int, CgScalars*, int, cudaStream_t);
+template void launch_cgm_iteration<float>(const CgLevel*, int, int, int, CgScalars*, int, int,
+                                          double, int, int*, cudaStream_t);
+template void launch_cgm_iteration<double>(const CgLevel*, int, int, int, CgScalars*, int, int,
+                                           double, int, int*, cudaStream_t);
+
 }  // namespace gb

@@ -545,4 +545,208 @@ void launch_lanczos_step(int64_t n, double a, const double* x, const double* y, 
   if (n > 0) { count_launch(); k_lanczos_step<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, x, y, b, z, c, out); }
 }
 
+// ---------------------------------------------------------------- several right-hand sides
+// Restriction of nrhs vectors: the row of Rhat is read once per lane and
+// applied to the neighbours' slots of every right-hand side.
+template <typename T>
+__global__ void __launch_bounds__(128) k_restrict_m(const T* __restrict__ Rhat, int NB,
+                                                    const int2* __restrict__ nbr, int Lpar,
+                                                    int64_t nrow, const T* __restrict__ ghat,
+                                                    int64_t gstride, T* out, int64_t ostride,
+                                                    const uint32_t* __restrict__ pmask_km1,
+                                                    int nrhs) {
+  __shared__ T vals[kMaxRhs][4];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * 4 + w;
+  T acc[kMaxRhs];
+#pragma unroll
+  for (int r = 0; r < kMaxRhs; ++r) acc[r] = T(0);
+  if (i < nrow) {
+    int x, y;
+    demorton((uint32_t)i, x, y);
+    const T* row = Rhat + i * 4 * NB;
+    for (int j = lane; j < NB; j += 32) {
+      const int p = shift_cell(x, y, nbr[j].x, nbr[j].y, Lpar, nrow);
+      if (p < 0) continue;
+      T rv[4];
+      ld4(row + 4 * j, rv);
+#pragma unroll
+      for (int r = 0; r < kMaxRhs; ++r) {
+        if (r < nrhs) {
+          T gv[4];
+          ld4(ghat + r * gstride + 4 * (int64_t)p, gv);
+          acc[r] += rv[0] * gv[0] + rv[1] * gv[1] + rv[2] * gv[2] + rv[3] * gv[3];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kMaxRhs; ++r)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+  if (pmask_km1 == nullptr) {
+    if (lane == 0 && i < nrow)
+      for (int r = 0; r < nrhs; ++r) out[r * ostride + i] = acc[r];
+    return;
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int r = 0; r < kMaxRhs; ++r) vals[r][w] = acc[r];
+  __syncthreads();
+  if (threadIdx.x < 4 * nrhs) {
+    const int r = threadIdx.x >> 2, a = threadIdx.x & 3;
+    const int64_t base = (int64_t)blockIdx.x * 4;
+    const int m = (int)pmask_km1[base >> 2] & 15;
+    out[r * ostride + base + a] = qv<T>(m, a, 0) * vals[r][0] + qv<T>(m, a, 1) * vals[r][1] +
+                                  qv<T>(m, a, 2) * vals[r][2] + qv<T>(m, a, 3) * vals[r][3];
+  }
+}
+
+template <typename T>
+void launch_restrict_m(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t nrow,
+                       const T* ghat_k, int64_t gstride, T* g_km1, int64_t ostride,
+                       const uint32_t* pmask_km1, int nrhs, cudaStream_t s) {
+  if (nrow <= 0) return;
+  count_launch();
+  k_restrict_m<T><<<(unsigned)((nrow + 3) / 4), 128, 0, s>>>(Rhat, NB, nbr, Lpar, nrow, ghat_k,
+                                                             gstride, g_km1, ostride, pmask_km1,
+                                                             nrhs);
+}
+template void launch_restrict_m<float>(const float*, int, const int2*, int, int64_t, const float*,
+                                       int64_t, float*, int64_t, const uint32_t*, int,
+                                       cudaStream_t);
+template void launch_restrict_m<double>(const double*, int, const int2*, int, int64_t,
+                                        const double*, int64_t, double*, int64_t, const uint32_t*,
+                                        int, cudaStream_t);
+
+// Prolongation of nrhs vectors with the rows of RT read once.
+template <typename T>
+__global__ void __launch_bounds__(128) k_prolong_m(const T* __restrict__ RT, int NB,
+                                                   const int2* __restrict__ nbr, int Lpar,
+                                                   int64_t npar, const T* __restrict__ v,
+                                                   int64_t vstride, const T* __restrict__ w,
+                                                   int64_t wstride,
+                                                   const uint32_t* __restrict__ pmask, int inverse,
+                                                   T* out, int64_t ostride, int nrhs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (p >= npar) return;
+  const int m = (int)pmask[p] & 15;
+  T h[kMaxRhs][3];
+#pragma unroll
+  for (int r = 0; r < kMaxRhs; ++r) h[r][0] = h[r][1] = h[r][2] = T(0);
+  if (m) {
+    int x, y;
+    demorton((uint32_t)p, x, y);
+    const T* row = RT + p * 4 * NB;
+    for (int j = lane; j < NB; j += 32) {
+      const int i = shift_cell(x, y, -nbr[j].x, -nbr[j].y, Lpar, npar);
+      if (i < 0) continue;
+      T rv[4];
+      ld4(row + 4 * j, rv);
+#pragma unroll
+      for (int r = 0; r < kMaxRhs; ++r) {
+        if (r < nrhs) {
+          const T vi = v[r * vstride + i];
+          h[r][0] += rv[0] * vi;
+          h[r][1] += rv[1] * vi;
+          h[r][2] += rv[2] * vi;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kMaxRhs; ++r)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) h[r][a] += __shfl_xor_sync(0xffffffffu, h[r][a], o);
+  if (lane >= nrhs) return;
+  // lane r writes right-hand side r
+  T hh[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int r = 0; r < kMaxRhs; ++r)
+    if (r == lane) {
+      hh[0] = h[r][0];
+      hh[1] = h[r][1];
+      hh[2] = h[r][2];
+    }
+  const int r = lane;
+  if (m) {
+    hh[3] = v[r * vstride + p] * (T(1) / sqrt(T(__popc(m))));
+    if (w) {
+      hh[0] += w[r * wstride + 4 * p];
+      hh[1] += w[r * wstride + 4 * p + 1];
+      hh[2] += w[r * wstride + 4 * p + 2];
+    }
+  }
+  T* o = out + r * ostride + 4 * p;
+  if (inverse) {
+    T Q[16];
+    qmat<T>(m, Q);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      o[c] = Q[c] * hh[0] + Q[4 + c] * hh[1] + Q[8 + c] * hh[2] + Q[12 + c] * hh[3];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o[c] = hh[c];
+  }
+}
+
+template <typename T>
+void launch_prolong_m(const T* RT, int NB, const int2* nbr, int Lpar, int64_t npar,
+                      const T* v_km1, int64_t vstride, const T* w_k, int64_t wstride,
+                      const uint32_t* pmask_k, int inverse, T* out, int64_t ostride, int nrhs,
+                      cudaStream_t s) {
+  if (npar <= 0) return;
+  count_launch();
+  k_prolong_m<T><<<(unsigned)((npar * 32 + 127) / 128), 128, 0, s>>>(
+      RT, NB, nbr, Lpar, npar, v_km1, vstride, w_k, wstride, pmask_k, inverse, out, ostride, nrhs);
+}
+template void launch_prolong_m<float>(const float*, int, const int2*, int, int64_t, const float*,
+                                      int64_t, const float*, int64_t, const uint32_t*, int,
+                                      float*, int64_t, int, cudaStream_t);
+template void launch_prolong_m<double>(const double*, int, const int2*, int, int64_t,
+                                       const double*, int64_t, const double*, int64_t,
+                                       const uint32_t*, int, double*, int64_t, int, cudaStream_t);
+
+// y_r = Ahat x_r for nrhs vectors, each 128-byte block row read once.
+__global__ void __launch_bounds__(256) k_block_spmv64_m(const double* __restrict__ A,
+                                                        const int2* __restrict__ off, int noff,
+                                                        int Lpar, int64_t npar,
+                                                        const double* __restrict__ xv, double* yv,
+                                                        int64_t stride, int nrhs) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = t >> 2;
+  const int a = (int)(t & 3);
+  if (p >= npar) return;
+  int x, y;
+  demorton((uint32_t)p, x, y);
+  double acc[kMaxRhs] = {0, 0, 0, 0};
+  for (int o = 0; o < noff; ++o) {
+    const int q = shift_cell(x, y, off[o].x, off[o].y, Lpar, npar);
+    if (q < 0) continue;
+    const double2* row = reinterpret_cast<const double2*>(A + ((int64_t)o * npar + p) * 16 + 4 * a);
+    const double2 r0 = __ldg(row), r1 = __ldg(row + 1);
+#pragma unroll
+    for (int r = 0; r < kMaxRhs; ++r) {
+      if (r < nrhs) {
+        const double2* xq = reinterpret_cast<const double2*>(xv + r * stride + 4 * (int64_t)q);
+        const double2 x0 = __ldg(xq), x1 = __ldg(xq + 1);
+        acc[r] += r0.x * x0.x + r0.y * x0.y + r1.x * x1.x + r1.y * x1.y;
+      }
+    }
+  }
+  for (int r = 0; r < nrhs; ++r) yv[r * stride + 4 * p + a] = acc[r];
+}
+
+void launch_block_spmv64_m(const double* Ahat, const int2* off, int noff, int Lpar, int64_t npar,
+                           const double* x, double* y, int64_t stride, int nrhs, cudaStream_t s) {
+  if (npar <= 0) return;
+  const int64_t n = 4 * npar;
+  count_launch();
+  k_block_spmv64_m<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ahat, off, noff, Lpar, npar, x, y,
+                                                                stride, nrhs);
+}
+
 }  // namespace gb

@@ -92,6 +92,8 @@ SIGNATURES = {
     "gamblet_compress": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int64)]),
+    "gamblet_solve_many": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.POINTER(Info)]),
     "gamblet_solve_truncated": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.POINTER(Info)]),
     "gamblet_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
@@ -253,6 +255,15 @@ def gamblet_compress(h: int, g, eps: float, u):
     _check(_lib.gamblet_compress(ctypes.c_void_p(h), _ptr(g, np.float64), float(eps),
                                  _ptr(u, np.float64), ctypes.byref(kept), ctypes.byref(total)))
     return kept.value, total.value
+
+
+def gamblet_solve_many(h: int, G, U, info: Info | None = None) -> int:
+    """G, U: (nrhs, n) float64 arrays or tensors (row r = right-hand side r)."""
+    info = info if info is not None else Info()
+    nrhs = int(G.shape[0])
+    st = _lib.gamblet_solve_many(ctypes.c_void_p(h), nrhs, _ptr(G, np.float64), _ptr(U, np.float64),
+                                 ctypes.byref(info))
+    return _check(st)
 
 
 def gamblet_solve_truncated(h: int, k: int, g, u, info: Info | None = None) -> int:

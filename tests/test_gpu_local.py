@@ -292,3 +292,38 @@ def test_rho4_operators_match_oracle(variant):
     with pytest.raises(nv.GambletError) as e:
         nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
     assert e.value.status == nv.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_several_right_hand_sides(precision):
+    """gamblet_solve_many (groups of four sharing the matrix reads) against
+    the direct solves and, for the one-pass transform, against gamblet_solve
+    one right-hand side at a time."""
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(64, 1e4, 17)
+    rng = np.random.default_rng(17)
+    G = np.ascontiguousarray(rng.standard_normal((5, p.ndof)))
+    G[3] = 0.0  # a zero right-hand side inside a group
+    for refine in (0, 60):
+        h = _setup(p.A, p.cells, p.q, 3.0, precision=precision, refine=refine,
+                   level_tol=1e-12 if refine == 0 and precision == 0 else 0.1)
+        try:
+            U = np.zeros_like(G)
+            info = nv.Info()
+            assert nv.gamblet_solve_many(h, G, U, info) == nv.OK
+            for r in range(G.shape[0]):
+                if refine == 0:
+                    u1 = np.zeros(p.ndof)
+                    nv.gamblet_solve(h, G[r], u1)
+                    tol = 1e-11 if precision == 0 else 1e-4
+                    assert np.linalg.norm(U[r] - u1) <= tol * max(np.linalg.norm(u1), 1e-300), r
+                else:
+                    if r == 3:
+                        assert not U[r].any()
+                        continue
+                    ud, _ = direct.solve(p.A, G[r])
+                    assert rel(U[r], ud) < 1e-9, r
+            if refine:
+                assert info.rel_residual < 1e-12
+        finally:
+            nv.gamblet_destroy(h)
