@@ -520,6 +520,46 @@ def level_conditions(nv, a, dev_in, steps=60):
         nv.gamblet_destroy(h)
 
 
+def multi_rhs_timing(nv, torch, a, dev_in, stream, nrhs=4, steps=3):
+    """Solve phase only: nrhs right-hand sides through gamblet_solve_many
+    (matrices read once per group) against nrhs calls of gamblet_solve, on
+    one mixed-precision hierarchy of the bench problem."""
+    q = int(np.log2(a.size))
+    o = opts_for(nv, a, nv.MIXED, stream.cuda_stream, 0)
+    h = nv.gamblet_setup(dev_in["rowptr"], dev_in["colind"], dev_in["val"], q, dev_in["cells"], o)
+    try:
+        n = int(dev_in["g"].shape[0])
+        gen = torch.Generator(device="cpu").manual_seed(11)
+        G = torch.randn(nrhs, n, generator=gen, dtype=torch.float64).to(dev_in["g"].device)
+        U = torch.zeros_like(G)
+        u1 = torch.zeros(n, dtype=torch.float64, device=G.device)
+
+        def timed(fn):
+            ts = []
+            for it in range(steps + 1):
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+                e1.synchronize()
+                if it > 0:
+                    ts.append(e0.elapsed_time(e1))
+            return statistics.mean(ts)
+
+        info = nv.Info()
+        many_ms = timed(lambda: nv.gamblet_solve_many(h, G, U, info))
+        worst = info.rel_residual
+        single_ms = timed(lambda: [nv.gamblet_solve(h, G[r], u1) for r in range(nrhs)])
+        return {"nrhs": nrhs, "dofs": n, "solve_many_ms": many_ms, "single_solves_ms": single_ms,
+                "speedup": single_ms / many_ms, "value": nrhs * n / (many_ms * 1e-3),
+                "unit": "DOF/s (solve phase, all right-hand sides)", "worst_rel_residual": worst}
+    finally:
+        nv.gamblet_destroy(h)
+
+
 def cpu_oracle(p):
     """The oracle's direct solve (SuperLU + extended-precision refinement)."""
     from oracle import direct
@@ -687,6 +727,8 @@ def main():
         line["mass_init"] = mass_init_timing(nv, torch, dev, a, stream)
     if not a.no_localization:
         line["level_condition"] = level_conditions(nv, a, dev_in)
+    if not a.no_mass:
+        line["multi_rhs"] = multi_rhs_timing(nv, torch, a, dev_in, stream)
     if rank == 0 and ws == 1 and not a.no_cpu:
         line["cpu_baseline"] = {"value": ndof / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "one full solve of the same problem: SuperLU factor + "
