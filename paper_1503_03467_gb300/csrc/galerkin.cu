@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) k_galerkin_rows(const T* __restrict__ Aha
 // which c - r is an output offset (host list t2).  Compared with a row per
 // CTA this reads each block and each Rhat row up to four times less often.
 size_t galerkin_tile_smem_bytes(const GalerkinGeom& g, size_t elem) {
-  return elem * (16 * (size_t)g.NB + 16 * (size_t)g.tile_W * g.tile_W);
+  return elem * (16 * (size_t)g.NB + 16 * (size_t)g.tile_W * g.tile_W) + sizeof(int2) * g.NB;
 }
 
 template <typename T>
@@ -121,9 +121,11 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
   const int NB = g.NB, W = g.tile_W, WW = W * W, wmin = g.tile_wmin;
   T* rr = reinterpret_cast<T*>(smem_raw);  // [4][NB][4]
   T* tt = rr + 16 * NB;                    // [4][WW][4]
+  int2* snbr = reinterpret_cast<int2*>(tt + 16 * WW);  // N_j
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int64_t nrow = g.nrow;
   const int64_t t0 = g.i_begin >> 2, t1 = (g.i_end + 3) >> 2;
+  for (int j = threadIdx.x; j < NB; j += blockDim.x) snbr[j] = g.nbr[j];
   for (int64_t tile = t0 + blockIdx.x; tile < t1; tile += gridDim.x) {
     const int64_t i0 = tile << 2;
     int x0, y0;
@@ -175,36 +177,47 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
         for (int c = 0; c < 4; ++c) tt[((size_t)r * WW + u) * 4 + c] = acc[r][c];
     }
     __syncthreads();
-    // phase 2: outputs A_{i0+r, c} for every target cell c
-    for (int e = warp; e < g.nt2; e += nwarp) {
-      const int4 tg = g.t2[e];
-      int d[4] = {(int)(short)(tg.z & 0xffff), tg.z >> 16, (int)(short)(tg.w & 0xffff), tg.w >> 16};
-      const int ip = shift_cell(x0, y0, tg.x, tg.y, g.Lpar, nrow);
-      const bool have = ip >= 0 && (pmask[ip] & 15u);
-      T acc[4] = {T(0), T(0), T(0), T(0)};
-      if (have) {
-        const T* rc = Rhat + (int64_t)ip * 4 * NB;
-        for (int j = lane; j < NB; j += 32) {
-          const int ux = tg.x + g.nbr[j].x - wmin, uy = tg.y + g.nbr[j].y - wmin;
-          if ((unsigned)ux >= (unsigned)W || (unsigned)uy >= (unsigned)W) continue;
-          const int u = uy * W + ux;
-          T rv[4];
-          load_vec4(rc + 4 * j, rv);
+    // phase 2: outputs A_{i0+r, c} for every target cell c.  Eight lanes per
+    // target (four targets per warp) stride over the neighbours j, so the
+    // partial sums combine in three shuffle steps.
+    {
+      const int sub = lane & 7, grp = lane >> 3;
+      for (int e0 = 4 * warp; e0 < g.nt2; e0 += 4 * nwarp) {
+        const int e = e0 + grp;
+        const bool ok = e < g.nt2;
+        const int4 tg = ok ? g.t2[e] : make_int4(0, 0, -1, -1);
+        const int d[4] = {(int)(short)(tg.z & 0xffff), tg.z >> 16, (int)(short)(tg.w & 0xffff),
+                          tg.w >> 16};
+        const int ip = ok ? shift_cell(x0, y0, tg.x, tg.y, g.Lpar, nrow) : -1;
+        const bool have = ip >= 0 && (pmask[ip] & 15u);
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        if (have) {
+          const T* rc = Rhat + (int64_t)ip * 4 * NB;
+          const int bx = tg.x - wmin, by = tg.y - wmin;
+          for (int j = sub; j < NB; j += 8) {
+            const int2 nb = snbr[j];
+            const int ux = bx + nb.x, uy = by + nb.y;
+            if ((unsigned)ux >= (unsigned)W || (unsigned)uy >= (unsigned)W) continue;
+            const int u = uy * W + ux;
+            T rv[4];
+            load_vec4(rc + 4 * j, rv);
 #pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            if (d[r] < 0) continue;
-            const T* tv = tt + ((size_t)r * WW + u) * 4;
-            acc[r] += rv[0] * tv[0] + rv[1] * tv[1] + rv[2] * tv[2] + rv[3] * tv[3];
+            for (int r = 0; r < 4; ++r) {
+              if (d[r] < 0) continue;
+              const T* tv = tt + ((size_t)r * WW + u) * 4;
+              acc[r] += rv[0] * tv[0] + rv[1] * tv[1] + rv[2] * tv[2] + rv[3] * tv[3];
+            }
           }
         }
-      }
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        T v = acc[r];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0 && d[r] >= 0 && i0 + r >= g.i_begin && i0 + r < g.i_end)
-          Aout[(int64_t)d[r] * nrow + i0 + r] = live[r] ? v : T(0);
+        for (int r = 0; r < 4; ++r) {
+          T v = acc[r];
+          v += __shfl_xor_sync(0xffffffffu, v, 4);
+          v += __shfl_xor_sync(0xffffffffu, v, 2);
+          v += __shfl_xor_sync(0xffffffffu, v, 1);
+          if (sub == 0 && ok && d[r] >= 0 && i0 + r >= g.i_begin && i0 + r < g.i_end)
+            Aout[(int64_t)d[r] * nrow + i0 + r] = live[r] ? v : T(0);
+        }
       }
     }
     __syncthreads();
