@@ -32,6 +32,32 @@ __device__ __forceinline__ void load_vec4(const double* p, double* b) {
   b[3] = v1.y;
 }
 
+// 4-element shared-memory rows as single 16-byte (float) or two 16-byte
+// (double) accesses: lanes that touch consecutive rows then hit distinct
+// banks, where four scalar accesses at a 16-byte stride collide four ways.
+__device__ __forceinline__ void sld4(const float* p, float* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+__device__ __forceinline__ void sld4(const double* p, double* v) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+__device__ __forceinline__ void sst4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void sst4(double* p, const double* v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
 // One CTA per coarse row i, one thread per window position (phase 1: the
 // thread reads whole 4x4 blocks, 64 bytes, and keeps four accumulators) and
 // one thread per output offset (phase 2).  Fewer instructions per block
@@ -138,8 +164,7 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
       const int r = idx / NB, j = idx - r * NB;
       T v[4] = {T(0), T(0), T(0), T(0)};
       if (live[r]) load_vec4(Rhat + ((i0 + r) * NB + j) * 4, v);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) rr[(r * NB + j) * 4 + c] = v[c];
+      sst4(rr + (r * NB + j) * 4, v);
     }
     __syncthreads();
     // phase 1: t_r(u) = sum over stored blocks of the window
@@ -163,18 +188,17 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
           for (int r = 0; r < 4; ++r) {
             const int j = ((unsigned)ent.y >> (8 * r)) & 0xffu;
             if (j == 0xff) continue;
-            const T* rv = rr + (r * NB + j) * 4;
-            const T v0 = rv[0], v1 = rv[1], v2 = rv[2], v3 = rv[3];
+            T rv[4];
+            sld4(rr + (r * NB + j) * 4, rv);
 #pragma unroll
             for (int a = 0; a < 4; ++a)
-              acc[r][a] += b[4 * a] * v0 + b[4 * a + 1] * v1 + b[4 * a + 2] * v2 + b[4 * a + 3] * v3;
+              acc[r][a] += b[4 * a] * rv[0] + b[4 * a + 1] * rv[1] + b[4 * a + 2] * rv[2] +
+                           b[4 * a + 3] * rv[3];
           }
         }
       }
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) tt[((size_t)r * WW + u) * 4 + c] = acc[r][c];
+      for (int r = 0; r < 4; ++r) sst4(tt + ((size_t)r * WW + u) * 4, acc[r]);
     }
     __syncthreads();
     // phase 2: outputs A_{i0+r, c} for every target cell c.  Eight lanes per
@@ -204,7 +228,8 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
               if (d[r] < 0) continue;
-              const T* tv = tt + ((size_t)r * WW + u) * 4;
+              T tv[4];
+              sld4(tt + ((size_t)r * WW + u) * 4, tv);
               acc[r] += rv[0] * tv[0] + rv[1] * tv[1] + rv[2] * tv[2] + rv[3] * tv[3];
             }
           }

@@ -352,6 +352,10 @@ struct gamblet_ctx {
   cudaGraphExec_t cg_exec = nullptr;
   bool cg_while = false;           // cg_exec is a device-side while loop
   int* cg_loop_count = nullptr;    // passes of that loop
+  int* cg_stats = nullptr;         // device: level-CG iterations per level, [32] not converged
+  // per level and CG iteration: algorithmic traffic and flops of the SpMV and
+  // of the vector kernels
+  std::vector<double> cg_bytes_spmv, cg_flops_spmv, cg_bytes_vec, cg_flops_vec;
   // outer
   double* u64 = nullptr;
   double* r64 = nullptr;
@@ -1243,6 +1247,7 @@ void alloc_solve(gamblet_ctx* h) {
     h->cg_sc = P.zeros<CgScalars>(std::max(h->cg_nlev, 1), s);
     h->any_active = P.zeros<int>(1, s);
     h->cg_loop_count = P.zeros<int>(1, s);
+    h->cg_stats = P.zeros<int>(33, s);
   }
 }
 
@@ -1341,28 +1346,50 @@ void run_level_cg(gamblet_ctx* h) {
       if (*h->any_active_h == 0) break;
     }
   }
-  std::vector<CgScalars> sc(h->cg_nlev);
-  CK(cudaMemcpyAsync(sc.data(), h->cg_sc, sizeof(CgScalars) * h->cg_nlev, cudaMemcpyDeviceToHost,
-                     s));
-  CK(cudaStreamSynchronize(s));
-  for (int l = 0; l < h->cg_nlev; ++l) {
-    h->level_iters_acc[l + 2] += sc[l].iters;
-    // levels above a truncation are not solved and cannot fail to converge
-    if (l + 2 <= h->kmax && sc[l].rr > tol2 * sc[l].rr0) h->level_not_conv = true;
-    // algorithmic traffic: the 3x3 detail blocks of B^(k) once per iteration,
-    // p read, Ap written (3 active slots); vector kernels: x, r, z, p, Ap, Dinv
-    const LevelDev& L = h->lv[l + 2];
-    const double sz = (double)sizeof(T), it = sc[l].iters;
-    const double b_spmv = it * sz * ((double)L.noff * L.npar * 9 + 6.0 * L.npar);
-    const double f_spmv = it * 2.0 * 9.0 * L.noff * L.npar;
-    const double b_vec = it * sz * 3.0 * L.npar * 12, f_vec = it * 3.0 * L.npar * 12;
-    if (h->cg_exec) {
-      h->prof.add("level_cg", b_spmv + b_vec, f_spmv + f_vec);
-    } else {
-      h->prof.add("level_cg_spmv", b_spmv, f_spmv);
-      h->prof.add("level_cg_vector", b_vec, f_vec);
+  // iteration counts and convergence stay on the device until the solve ends
+  // (levels above a truncation are not solved and cannot fail to converge)
+  launch_cg_collect(h->cg_sc, h->cg_nlev, h->kmax, tol2, h->cg_stats, s);
+  CK(cudaGetLastError());
+  if (h->cg_bytes_spmv.empty()) {
+    h->cg_bytes_spmv.assign(h->cg_nlev, 0.0);
+    h->cg_flops_spmv.assign(h->cg_nlev, 0.0);
+    h->cg_bytes_vec.assign(h->cg_nlev, 0.0);
+    h->cg_flops_vec.assign(h->cg_nlev, 0.0);
+    for (int l = 0; l < h->cg_nlev; ++l) {
+      // algorithmic traffic: the 3x3 detail blocks of B^(k) once per iteration,
+      // p read, Ap written (3 active slots); vector kernels: x, r, z, p, Ap, Dinv
+      const LevelDev& L = h->lv[l + 2];
+      const double sz = (double)sizeof(T);
+      h->cg_bytes_spmv[l] = sz * ((double)L.noff * L.npar * 9 + 6.0 * L.npar);
+      h->cg_flops_spmv[l] = 2.0 * 9.0 * L.noff * L.npar;
+      h->cg_bytes_vec[l] = sz * 3.0 * L.npar * 12;
+      h->cg_flops_vec[l] = 3.0 * L.npar * 12;
     }
   }
+}
+
+// Level-CG counts accumulated on the device since the last call: added to
+// the handle's totals and to the kernel profile (synchronises the stream).
+void flush_level_stats(gamblet_ctx* h) {
+  if (!h->cg_stats || h->cg_nlev == 0) return;
+  int st[33];
+  CK(cudaMemcpyAsync(st, h->cg_stats, sizeof(st), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaMemsetAsync(h->cg_stats, 0, sizeof(st), h->s));
+  CK(cudaStreamSynchronize(h->s));
+  for (int l = 0; l < h->cg_nlev && l + 2 < 32; ++l) {
+    h->level_iters_acc[l + 2] += st[l + 2];
+    if (!h->cg_bytes_spmv.empty() && st[l + 2] > 0) {
+      const double it = st[l + 2];
+      if (h->cg_exec) {
+        h->prof.add("level_cg", it * (h->cg_bytes_spmv[l] + h->cg_bytes_vec[l]),
+                    it * (h->cg_flops_spmv[l] + h->cg_flops_vec[l]));
+      } else {
+        h->prof.add("level_cg_spmv", it * h->cg_bytes_spmv[l], it * h->cg_flops_spmv[l]);
+        h->prof.add("level_cg_vector", it * h->cg_bytes_vec[l], it * h->cg_flops_vec[l]);
+      }
+    }
+  }
+  if (st[32]) h->level_not_conv = true;
 }
 
 // in: transformed level-q vector (T); out: transformed (inverse_last = 0) or
@@ -1507,6 +1534,7 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
   const int q = h->q;
   LevelDev& Lq = h->lv[q];
   const int64_t nq = Lq.ncell;
+  flush_level_stats(h);  // counts of earlier calls (compression, diagnostics) are not this solve's
   for (int k = 0; k < 32; ++k) h->level_iters_acc[k] = 0;
   h->level_not_conv = false;
   cudaEvent_t e0, e1;
@@ -1639,6 +1667,7 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
   CK(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  flush_level_stats(h);
   h->prof.resolve();
   check_status(h, "solve");
   if (maxit == 0 && h->level_not_conv) st = GAMBLET_ERR_NOT_CONVERGED;

@@ -293,6 +293,24 @@ void launch_cg_start(CgScalars* sc, int nlev, int nlev_on, double tol2, int* any
   { count_launch(); k_cg_start<<<1, 32, 0, s>>>(sc, nlev, nlev_on, tol2, any_active); }
 }
 
+// Iteration counts of one level-CG call added to stats[k] (level k = l + 2)
+// and stats[32] set when a solved level (k <= kmax) missed the tolerance, so
+// that the host reads them once per solve instead of after every call.
+__global__ void k_cg_collect(const CgScalars* __restrict__ sc, int nlev, int kmax, double tol2,
+                             int* stats) {
+  const int l = threadIdx.x;
+  if (l >= nlev || l + 2 > 31) return;
+  stats[l + 2] += sc[l].iters;
+  if (l + 2 <= kmax && sc[l].rr > tol2 * sc[l].rr0) stats[32] = 1;
+}
+
+void launch_cg_collect(const CgScalars* sc, int nlev, int kmax, double tol2, int* stats,
+                       cudaStream_t s) {
+  if (nlev <= 0) return;
+  count_launch();
+  k_cg_collect<<<1, 32, 0, s>>>(sc, nlev, kmax, tol2, stats);
+}
+
 template <typename T>
 void prepare_cg_spmv(int max_ts) {
   const size_t smem = cg_spmv_smem_bytes(max_ts, sizeof(T));
