@@ -198,14 +198,14 @@ struct LevelDev {
   uint32_t* pmask = nullptr;
   int n_active = 0, nJ = 0;
   // localized
-  int2* off = nullptr;
+  const int2* off = nullptr;
   int noff = 0;
   std::vector<int2> off_h;
   void* Ahat = nullptr;      // T
   double* Ahat64 = nullptr;  // level q float64 copy (mixed) or alias
   void* Rhat = nullptr;      // T, npar rows
   void* RT = nullptr;        // T, Rhat regrouped by parent (prolongation)
-  int* pair_idx = nullptr;
+  const int* pair_idx = nullptr;
   int shape[4] = {0, 0, 0, 0};  // launch shapes used: patch spp, patch gather, Galerkin variant, CG spp
   // exact (dense)
   double* D = nullptr;       // transformed dense Ahat^(k)
@@ -339,7 +339,7 @@ struct gamblet_ctx {
   double* A1L = nullptr;     // Cholesky factor
   void* g1 = nullptr;        // T, 4
   void* U1 = nullptr;        // T, 4
-  int* l1map = nullptr;
+  const int* l1map = nullptr;
   // CG batch
   CgLevel* cg_lv = nullptr;
   CgScalars* cg_sc = nullptr;
@@ -556,9 +556,6 @@ void build_hierarchy(gamblet_ctx* h, const int32_t* cells_user) {
     CK(cudaMemcpyAsync(h->lv[k].pmask_h.data(), h->lv[k].pmask, sizeof(uint32_t) * h->lv[k].npar,
                        cudaMemcpyDeviceToHost, s));
   }
-  h->morton_of_h.resize(h->n);
-  CK(cudaMemcpyAsync(h->morton_of_h.data(), h->morton_of, sizeof(int32_t) * h->n,
-                     cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (flag_h[0] == 1) fail(GAMBLET_ERR_INVALID_ARG, "two unknowns share a level-q cell");
   for (int k = 1; k <= q; ++k) {
@@ -625,11 +622,24 @@ struct PlanLevel {
   double flops_iter = 0;
   std::vector<int> map_next;          // block conversion map (or the level-1 map)
   OffSet O_next;
+  // byte offsets of this level's tables in Plan::packed
+  enum { kPairIdx, kHalf, kAdjPtr, kAdj, kDiagH, kWin, kL1Ptr, kL1Pairs, kOut, kL2Ptr, kL2Pairs,
+         kT1Ptr, kT1, kT2, kOffNext, kMapNext, kNumTables };
+  size_t table_off[kNumTables] = {};
 };
 struct Plan {
   std::vector<PlanLevel> lv;  // index k
   std::string key;            // geometry key of the process-wide cache
+  // every table of every level in one 16-byte aligned buffer, so that a setup
+  // moves the whole plan to the device with one copy
+  std::vector<char> packed;
 };
+
+// Device address of table t of level k in a device copy of Plan::packed.
+template <typename E>
+const E* plan_table(const char* dev, const PlanLevel& pl, int t) {
+  return reinterpret_cast<const E*>(dev + pl.table_off[t]);
+}
 
 int half_code(const OffSet& Sp, int dx, int dy);
 OffSet blocks_from_cells(const OffSet& S, const OffSet& Sp, int km1, std::vector<int>& map);
@@ -748,6 +758,34 @@ std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
         for (int j = 0; j < 4; ++j)
           pl.map_next[i * 4 + j] = half_code(pl.S.Sp, (j & 1) - (i & 1), (j >> 1) - (i >> 1));
     }
+  }
+  std::vector<char>& buf = plan->packed;
+  auto put = [&buf](const void* src, size_t bytes) {
+    const size_t off = buf.size();
+    buf.resize(off + std::max<size_t>((bytes + 15) & ~(size_t)15, 16), 0);
+    if (bytes) std::memcpy(buf.data() + off, src, bytes);
+    return off;
+  };
+  auto put_v = [&put](const auto& v) { return put(v.data(), v.size() * sizeof(v[0])); };
+  for (int k = q; k >= 2; --k) {
+    PlanLevel& pl = plan->lv[k];
+    const SymLevel& S = pl.S;
+    pl.table_off[PlanLevel::kPairIdx] = put_v(S.pair_idx);
+    pl.table_off[PlanLevel::kHalf] = put_v(pl.half);
+    pl.table_off[PlanLevel::kAdjPtr] = put_v(pl.adj_ptr);
+    pl.table_off[PlanLevel::kAdj] = put_v(pl.adj);
+    pl.table_off[PlanLevel::kDiagH] = put_v(pl.diag_h);
+    pl.table_off[PlanLevel::kWin] = put_v(S.WIN.v);
+    pl.table_off[PlanLevel::kL1Ptr] = put_v(S.l1_ptr);
+    pl.table_off[PlanLevel::kL1Pairs] = put_v(S.l1_pairs);
+    pl.table_off[PlanLevel::kOut] = put_v(S.Sp.v);
+    pl.table_off[PlanLevel::kL2Ptr] = put_v(S.l2_ptr);
+    pl.table_off[PlanLevel::kL2Pairs] = put_v(S.l2_pairs);
+    pl.table_off[PlanLevel::kT1Ptr] = put_v(S.t1_ptr);
+    pl.table_off[PlanLevel::kT1] = put_v(S.t1);
+    pl.table_off[PlanLevel::kT2] = put_v(S.t2);
+    pl.table_off[PlanLevel::kOffNext] = put_v(pl.O_next.v);
+    pl.table_off[PlanLevel::kMapNext] = put_v(pl.map_next);
   }
   return plan;
 }
@@ -942,12 +980,13 @@ void setup_local(gamblet_ctx* h) {
   for (const int2& o : h->lv[q].off_h) Oq.add(o.x, o.y);
   std::shared_ptr<const Plan> plan = cached_plan(q, h->opts.rho, h->opts.nbr_rule, Oq, h->N);
   h->plan = plan;
+  const char* dplan = P.upload(plan->packed, s);  // every plan table in one copy
   for (int k = q; k >= 2; --k) {
     LevelDev& L = h->lv[k];
     const PlanLevel& pl = plan->lv[k];
     const SymLevel& S = pl.S;
     const int Lpar = 1 << (k - 1);
-    L.pair_idx = P.upload(S.pair_idx, s);
+    L.pair_idx = plan_table<int>(dplan, pl, PlanLevel::kPairIdx);
     // patch solves -> Rhat^(k-1,k)
     T* Rhat = P.alloc<T>((int64_t)NB * 4 * L.npar);
     const double sz = (double)sizeof(T);
@@ -959,8 +998,10 @@ void setup_local(gamblet_ctx* h) {
       h->prof.end(tok, s);
     } else {
       PatchPcgGeom gp{NB, h->jc, h->nbr, L.pair_idx, Lpar, L.npar, (int)pl.half.size(),
-                      P.upload(pl.half, s), (int)pl.adj.size(), P.upload(pl.adj_ptr, s),
-                      P.upload(pl.adj, s), P.upload(pl.diag_h, s), pl.spp, 0, L.npar, 2};
+                      plan_table<int4>(dplan, pl, PlanLevel::kHalf), (int)pl.adj.size(),
+                      plan_table<int>(dplan, pl, PlanLevel::kAdjPtr),
+                      plan_table<int4>(dplan, pl, PlanLevel::kAdj),
+                      plan_table<int>(dplan, pl, PlanLevel::kDiagH), pl.spp, 0, L.npar, 2};
       if (patch_pcg_smem_bytes<T>(gp) > 227 * 1024)
         fail(GAMBLET_ERR_UNSUPPORTED, "patch blocks exceed shared memory; lower rho");
       tune_patch_shape<T>(h, k, gp, Rhat);
@@ -984,23 +1025,23 @@ void setup_local(gamblet_ctx* h) {
     gg.NB = NB;
     gg.nbr = h->nbr;
     gg.nwin = S.WIN.size();
-    gg.win = P.upload(S.WIN.v, s);
-    gg.l1_ptr = P.upload(S.l1_ptr, s);
-    gg.l1_pairs = P.upload(S.l1_pairs, s);
+    gg.win = plan_table<int2>(dplan, pl, PlanLevel::kWin);
+    gg.l1_ptr = plan_table<int>(dplan, pl, PlanLevel::kL1Ptr);
+    gg.l1_pairs = plan_table<int2>(dplan, pl, PlanLevel::kL1Pairs);
     gg.nout = S.Sp.size();
-    gg.out = P.upload(S.Sp.v, s);
-    gg.l2_ptr = P.upload(S.l2_ptr, s);
-    gg.l2_pairs = P.upload(S.l2_pairs, s);
+    gg.out = plan_table<int2>(dplan, pl, PlanLevel::kOut);
+    gg.l2_ptr = plan_table<int>(dplan, pl, PlanLevel::kL2Ptr);
+    gg.l2_pairs = plan_table<int2>(dplan, pl, PlanLevel::kL2Pairs);
     gg.Lpar = Lpar;
     gg.nrow = L.npar;
     gg.i_begin = 0;
     gg.i_end = L.npar;
     gg.tile_wmin = S.tile_wmin;
     gg.tile_W = S.tile_W;
-    gg.t1_ptr = P.upload(S.t1_ptr, s);
-    gg.t1 = P.upload(S.t1, s);
+    gg.t1_ptr = plan_table<int>(dplan, pl, PlanLevel::kT1Ptr);
+    gg.t1 = plan_table<int2>(dplan, pl, PlanLevel::kT1);
     gg.nt2 = (int)S.t2.size();
-    gg.t2 = P.upload(S.t2, s);
+    gg.t2 = plan_table<int4>(dplan, pl, PlanLevel::kT2);
     // 2 x 2 row tiles while their window boxes stay small enough for
     // several CTAs per SM, else the warp-cooperative kernel; the autotuner
     // decides on large levels
@@ -1029,8 +1070,8 @@ void setup_local(gamblet_ctx* h) {
       LevelDev& Ln = h->lv[k - 1];
       Ln.off_h = pl.O_next.v;
       Ln.noff = pl.O_next.size();
-      Ln.off = P.upload(Ln.off_h, s);
-      int* dmap = P.upload(pl.map_next, s);
+      Ln.off = plan_table<int2>(dplan, pl, PlanLevel::kOffNext);
+      const int* dmap = plan_table<int>(dplan, pl, PlanLevel::kMapNext);
       T* blk = P.alloc<T>((int64_t)Ln.noff * Ln.npar * 16);
       tok = h->prof.begin("cells_to_blocks",
                           sz * ((double)gg.nout * L.npar + (double)Ln.noff * Ln.npar * 16), 0.0, s);
@@ -1040,7 +1081,7 @@ void setup_local(gamblet_ctx* h) {
       CK(cudaGetLastError());
       Ln.Ahat = blk;
     } else {
-      h->l1map = P.upload(pl.map_next, s);
+      h->l1map = plan_table<int>(dplan, pl, PlanLevel::kMapNext);
       h->A1L = P.alloc<double>(16);
       launch_level1_factor<T>(Acell, (int)L.npar, h->l1map, h->A1L, h->status, s);
       CK(cudaGetLastError());
@@ -2759,6 +2800,12 @@ std::vector<int32_t> canon_map(gamblet_ctx* h, int k) {
   const LevelDev& L = h->lv[k];
   std::vector<int32_t> cm(L.ncell, -1);
   if (k == h->q) {
+    if ((int64_t)h->morton_of_h.size() != h->n) {  // fetched on first use
+      h->morton_of_h.resize(h->n);
+      CK(cudaMemcpyAsync(h->morton_of_h.data(), h->morton_of, sizeof(int32_t) * h->n,
+                         cudaMemcpyDeviceToHost, h->s));
+      CK(cudaStreamSynchronize(h->s));
+    }
     for (int i = 0; i < h->n; ++i) cm[h->morton_of_h[i]] = i;
     return cm;
   }
