@@ -44,8 +44,8 @@ def parse():
     ap.add_argument("--size", type=int, default=1024, help="cells per side (power of two)")
     ap.add_argument("--contrast", type=float, default=1e4)
     ap.add_argument("--rho", type=float, default=3.0)
-    ap.add_argument("--level-tol", type=float, default=0.1)
-    ap.add_argument("--refine-tol", type=float, default=1e-10)
+    ap.add_argument("--level-tol", type=float, default=0.05)
+    ap.add_argument("--refine-tol", type=float, default=1e-9)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain float64 arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
