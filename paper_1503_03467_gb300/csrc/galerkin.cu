@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256) k_galerkin_rows(const T* __restrict__ Aha
 // which c - r is an output offset (host list t2).  Compared with a row per
 // CTA this reads each block and each Rhat row up to four times less often.
 size_t galerkin_tile_smem_bytes(const GalerkinGeom& g, size_t elem) {
-  return elem * (16 * (size_t)g.NB + 16 * (size_t)g.tile_W * g.tile_W) + sizeof(int2) * g.NB;
+  return elem * (16 * (size_t)g.NB + 16 * (size_t)g.tile_W * g.tile_W);
 }
 
 template <typename T>
@@ -147,11 +147,9 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
   const int NB = g.NB, W = g.tile_W, WW = W * W, wmin = g.tile_wmin;
   T* rr = reinterpret_cast<T*>(smem_raw);  // [4][NB][4]
   T* tt = rr + 16 * NB;                    // [4][WW][4]
-  int2* snbr = reinterpret_cast<int2*>(tt + 16 * WW);  // N_j
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int64_t nrow = g.nrow;
   const int64_t t0 = g.i_begin >> 2, t1 = (g.i_end + 3) >> 2;
-  for (int j = threadIdx.x; j < NB; j += blockDim.x) snbr[j] = g.nbr[j];
   for (int64_t tile = t0 + blockIdx.x; tile < t1; tile += gridDim.x) {
     const int64_t i0 = tile << 2;
     int x0, y0;
@@ -202,8 +200,9 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
     }
     __syncthreads();
     // phase 2: outputs A_{i0+r, c} for every target cell c.  Eight lanes per
-    // target (four targets per warp) stride over the neighbours j, so the
-    // partial sums combine in three shuffle steps.
+    // target (four targets per warp) stride over the target's list of pairs
+    // (j, u) whose window position holds a nonzero t, so the partial sums
+    // combine in three shuffle steps.
     {
       const int sub = lane & 7, grp = lane >> 3;
       for (int e0 = 4 * warp; e0 < g.nt2; e0 += 4 * nwarp) {
@@ -217,12 +216,10 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
         T acc[4] = {T(0), T(0), T(0), T(0)};
         if (have) {
           const T* rc = Rhat + (int64_t)ip * 4 * NB;
-          const int bx = tg.x - wmin, by = tg.y - wmin;
-          for (int j = sub; j < NB; j += 8) {
-            const int2 nb = snbr[j];
-            const int ux = bx + nb.x, uy = by + nb.y;
-            if ((unsigned)ux >= (unsigned)W || (unsigned)uy >= (unsigned)W) continue;
-            const int u = uy * W + ux;
+          const int q1 = g.t2p_ptr[e + 1];
+          for (int q = g.t2p_ptr[e] + sub; q < q1; q += 8) {
+            const int pu = __ldg(g.t2p + q);
+            const int j = pu & 0xff, u = pu >> 8;
             T rv[4];
             load_vec4(rc + 4 * j, rv);
 #pragma unroll

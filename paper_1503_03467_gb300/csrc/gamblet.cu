@@ -186,6 +186,11 @@ struct SymLevel {
   std::vector<int> t1_ptr;
   std::vector<int2> t1;           // (o, j of rows 0..3 packed in bytes)
   std::vector<int4> t2;           // (c.x, c.y, d0 | d1 << 16, d2 | d3 << 16)
+  // per target e, the pairs (j, u) whose window position u = c + N_j lies in
+  // the window of some row of the tile (packed j | u << 8, ranges t2p_ptr);
+  // targets are sorted by decreasing pair count so that the targets that a
+  // warp handles together have about the same work
+  std::vector<int> t2p_ptr, t2p;
 };
 
 // ---------------------------------------------------------------- handle
@@ -470,6 +475,15 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
   std::set<std::pair<int, int>> targets;
   for (int r = 0; r < 4; ++r)
     for (const int2& d : S.Sp.v) targets.insert({d.y + (r >> 1), d.x + (r & 1)});
+  // window positions holding a nonzero t_r(u) for some row r of the tile
+  std::set<std::pair<int, int>> win4;
+  for (int r = 0; r < 4; ++r)
+    for (const int2& w : S.WIN.v) win4.insert({w.y + (r >> 1), w.x + (r & 1)});
+  struct Target {
+    int4 t;
+    std::vector<int> pairs;
+  };
+  std::vector<Target> tl;
   for (const auto& c : targets) {
     const int cx = c.second, cy = c.first;
     int dr[4];
@@ -478,7 +492,26 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
     auto pack = [](int lo, int hi) {
       return (int)(((uint32_t)lo & 0xffffu) | ((uint32_t)hi << 16));
     };
-    S.t2.push_back(make_int4(cx, cy, pack(dr[0], dr[1]), pack(dr[2], dr[3])));
+    Target t;
+    t.t = make_int4(cx, cy, pack(dr[0], dr[1]), pack(dr[2], dr[3]));
+    for (int j = 0; j < NB; ++j) {
+      const int wx = cx + N.v[j].x, wy = cy + N.v[j].y;
+      if (!win4.count({wy, wx})) continue;
+      const int u = (wy - wmin) * W + (wx - wmin);  // inside the box: win4 lies in it
+      if (u < 0 || u >= W * W || (u >> 23) != 0)
+        fail(GAMBLET_ERR_UNSUPPORTED, "window too large for tiled Galerkin");
+      t.pairs.push_back(j | (u << 8));
+    }
+    tl.push_back(std::move(t));
+  }
+  std::stable_sort(tl.begin(), tl.end(), [](const Target& a, const Target& b) {
+    return a.pairs.size() > b.pairs.size();
+  });
+  S.t2p_ptr.assign(1, 0);
+  for (const Target& t : tl) {
+    S.t2.push_back(t.t);
+    S.t2p.insert(S.t2p.end(), t.pairs.begin(), t.pairs.end());
+    S.t2p_ptr.push_back((int)S.t2p.size());
   }
   return S;
 }
@@ -624,7 +657,7 @@ struct PlanLevel {
   OffSet O_next;
   // byte offsets of this level's tables in Plan::packed
   enum { kPairIdx, kHalf, kAdjPtr, kAdj, kDiagH, kWin, kL1Ptr, kL1Pairs, kOut, kL2Ptr, kL2Pairs,
-         kT1Ptr, kT1, kT2, kOffNext, kMapNext, kNumTables };
+         kT1Ptr, kT1, kT2, kT2pPtr, kT2p, kOffNext, kMapNext, kNumTables };
   size_t table_off[kNumTables] = {};
 };
 struct Plan {
@@ -784,6 +817,8 @@ std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
     pl.table_off[PlanLevel::kT1Ptr] = put_v(S.t1_ptr);
     pl.table_off[PlanLevel::kT1] = put_v(S.t1);
     pl.table_off[PlanLevel::kT2] = put_v(S.t2);
+    pl.table_off[PlanLevel::kT2pPtr] = put_v(S.t2p_ptr);
+    pl.table_off[PlanLevel::kT2p] = put_v(S.t2p);
     pl.table_off[PlanLevel::kOffNext] = put_v(pl.O_next.v);
     pl.table_off[PlanLevel::kMapNext] = put_v(pl.map_next);
   }
@@ -1042,6 +1077,8 @@ void setup_local(gamblet_ctx* h) {
     gg.t1 = plan_table<int2>(dplan, pl, PlanLevel::kT1);
     gg.nt2 = (int)S.t2.size();
     gg.t2 = plan_table<int4>(dplan, pl, PlanLevel::kT2);
+    gg.t2p_ptr = plan_table<int>(dplan, pl, PlanLevel::kT2pPtr);
+    gg.t2p = plan_table<int>(dplan, pl, PlanLevel::kT2p);
     // 2 x 2 row tiles while their window boxes stay small enough for
     // several CTAs per SM, else the warp-cooperative kernel; the autotuner
     // decides on large levels

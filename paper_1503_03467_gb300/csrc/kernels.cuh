@@ -199,6 +199,8 @@ struct GalerkinGeom {
   const int2* t1;        // (o, j per row packed in bytes, 0xff = none)
   int nt2;
   const int4* t2;        // (c.x, c.y, d0 | d1 << 16, d2 | d3 << 16), d = -1: none
+  const int* t2p_ptr;    // nt2 + 1
+  const int* t2p;        // per target: (j | u << 8) with c + N_j = WIN position u
 };
 // Shared memory of k_galerkin_tile: four Rhat rows and four window boxes.
 size_t galerkin_tile_smem_bytes(const GalerkinGeom& g, size_t elem);
