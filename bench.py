@@ -141,15 +141,18 @@ def load_peaks():
         return {}
 
 
-def ncu_traffic(kernel: str):
+def ncu_traffic(kernel: str, mixed: bool = True):
     """Per-launch DRAM traffic of `kernel` from the committed ncu summary, or
-    None when absent or taken on a different version of the kernel source."""
+    None when absent, taken on a different version of the kernel source, or
+    taken in the other working precision (float vs double instantiation)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(path)).get(kernel)
     except (OSError, ValueError):
         return None
     if not rec:
+        return None
+    if ("<float" in rec.get("kernel", "")) != mixed:
         return None
     src = os.path.join(ROOT, rec["source"])
     try:
@@ -594,7 +597,7 @@ def roofline(stats, peaks, clocks, mixed):
     per_launch_flops = st["flops"] / launches
     total_ms = sum(s["ms"] for s in stats.values())
     common = {"kernel": name, "launches": st["launches"], "avg_launch_ms": avg_ms,
-              "share_of_device_time": st["ms"] / total_ms, "traffic": ncu_traffic(name)}
+              "share_of_device_time": st["ms"] / total_ms, "traffic": ncu_traffic(name, mixed)}
     if family in ("patch_pcg", "patch_cholesky"):
         # SIMT arithmetic: 152 SMs x 128 lanes (fp32) or the nominal float64
         # rate, at the maximum SM clock
@@ -605,9 +608,15 @@ def roofline(stats, peaks, clocks, mixed):
             peak = 1.25
             src = "nominal GB300 float64 rate"
         achieved = per_launch_flops / (avg_ms * 1e-3) / 1e12
-        return {**common, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "peak_source": src,
-                "algorithmic": f"{per_launch_flops:.4g} flop per launch"}
+        out = {**common, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+               "frac": achieved / peak, "peak_source": src,
+               "algorithmic": f"{per_launch_flops:.4g} flop per launch"}
+        if mixed:
+            # the lanes are not what binds this kernel: its shared-memory
+            # block products are (ncu summary in profiles/)
+            out["binding_unit"] = ("shared-memory load pipe, L1/TEX 81-85% of peak (ncu, "
+                                   "profiles/patch_galerkin_512x512_mixed.md)")
+        return out
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
     return {**common, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
