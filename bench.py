@@ -507,8 +507,10 @@ def mass_init_timing(nv, torch, dev, a, stream):
 
 
 def level_conditions(nv, a, dev_in, steps=60):
-    """cond(B^(k)) estimates (Lanczos, float64 level operators) per level:
-    the paper bounds them uniformly in k (Theorem thmodhehiudhehd)."""
+    """cond(B^(k)) estimates (Lanczos, float64 level operators) per level, for
+    W of Construction const2 (the stored basis) and const1: the paper bounds
+    them uniformly in k (Theorem thmodhehiudhehd) and finds const2 the better
+    conditioned."""
     q = int(np.log2(a.size))
     o = opts_for(nv, a, nv.FP64, None, 0)
     o.refine_max_iter = 0
@@ -516,8 +518,9 @@ def level_conditions(nv, a, dev_in, steps=60):
     try:
         out = {}
         for k in range(2, q + 1):
-            lo, hi = nv.gamblet_level_condition(h, k, steps)
-            out[str(k)] = {"lmin": lo, "lmax": hi, "cond": hi / lo}
+            lo, hi = nv.gamblet_level_condition(h, k, steps, 2)
+            lo1, hi1 = nv.gamblet_level_condition(h, k, steps, 1)
+            out[str(k)] = {"lmin": lo, "lmax": hi, "cond": hi / lo, "cond_const1": hi1 / lo1}
         return out
     finally:
         nv.gamblet_destroy(h)

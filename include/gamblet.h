@@ -260,8 +260,15 @@ GAMBLET_API gamblet_status gamblet_solve_truncated(gamblet_handle h, int32_t k, 
  * blocks, steps iterations (capped at |J^(k)|) from a fixed pseudo-random
  * start, extremes of the Lanczos matrix by Sturm bisection.  Localized
  * transform only.  cond(B^(k)) ~ lmax / lmin.
+ *   construction  2: W of Construction const2 (orthonormal rows, the basis
+ *                 the library stores); 1: Construction const1 (row t of a
+ *                 parent = child t minus child t + 1), for which
+ *                 W1 A W1^T = M B M^T with the per-parent change of basis M
+ *                 (Sec. 4.6; the paper compares the two constructions'
+ *                 condition numbers).  Anything else: INVALID_ARG.
  */
-GAMBLET_API gamblet_status gamblet_level_condition(gamblet_handle h, int32_t k, int32_t steps,
+GAMBLET_API gamblet_status gamblet_level_condition(gamblet_handle h, int32_t k,
+                                                   int32_t construction, int32_t steps,
                                                    double* lmin, double* lmax);
 
 /*

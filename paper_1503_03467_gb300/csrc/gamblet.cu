@@ -2502,7 +2502,8 @@ int tridiag_count_below(const std::vector<double>& d, const std::vector<double>&
 // a fixed pseudo-random start on the detail slots), then bisection on the
 // Sturm counts of the Lanczos tridiagonal matrix.
 template <typename T>
-void level_condition_impl(gamblet_ctx* h, int k, int steps, double* lmin, double* lmax) {
+void level_condition_impl(gamblet_ctx* h, int k, int construction, int steps, double* lmin,
+                          double* lmax) {
   cudaStream_t s = h->s;
   LevelDev& L = h->lv[k];
   Pool tmp;
@@ -2512,7 +2513,18 @@ void level_condition_impl(gamblet_ctx* h, int k, int steps, double* lmin, double
   double* vp = tmp.zeros<double>(n, s);
   double* w = tmp.zeros<double>(n, s);
   double* d = tmp.zeros<double>(8, s);
+  double* t1 = construction == 1 ? tmp.zeros<double>(n, s) : nullptr;
   const int Lpar = 1 << (k - 1);
+  // the operator: B^(k) in the stored basis, or M B^(k) M^T for const1
+  auto apply = [&](const double* x, double* y) {
+    if (construction == 1) {
+      launch_detail_basis(L.npar, L.pmask, x, t1, 1, s);
+      launch_detail_spmv<T>((const T*)L.Bd, L.off, L.noff, Lpar, L.npar, t1, y, s);
+      launch_detail_basis(L.npar, L.pmask, y, y, 0, s);
+    } else {
+      launch_detail_spmv<T>((const T*)L.Bd, L.off, L.noff, Lpar, L.npar, x, y, s);
+    }
+  };
   auto dot = [&](const double* a, const double* b) {
     CK(cudaMemsetAsync(d, 0, sizeof(double) * 8, s));
     launch_dots(n, a, b, nullptr, nullptr, nullptr, nullptr, d, s);
@@ -2529,7 +2541,7 @@ void level_condition_impl(gamblet_ctx* h, int k, int steps, double* lmin, double
   double beta = 0;
   const int m = std::max(1, std::min<int>(steps, L.nJ));
   for (int j = 0; j < m; ++j) {
-    launch_detail_spmv<T>((const T*)L.Bd, L.off, L.noff, Lpar, L.npar, v, w, s);
+    apply(v, w);
     const double alpha = dot(w, v);
     // w <- w - alpha v - beta v_prev
     launch_lanczos_step(n, 1.0, w, v, -alpha, vp, -beta, w, s);
@@ -2681,14 +2693,16 @@ gamblet_status gamblet_solve_truncated(gamblet_handle h, int32_t k, const double
   }
 }
 
-gamblet_status gamblet_level_condition(gamblet_handle h, int32_t k, int32_t steps,
-                                       double* lmin, double* lmax) {
+gamblet_status gamblet_level_condition(gamblet_handle h, int32_t k, int32_t construction,
+                                       int32_t steps, double* lmin, double* lmax) {
   try {
     if (!h || !lmin || !lmax || k < 2 || k > h->q || steps < 1)
       fail(GAMBLET_ERR_INVALID_ARG, "bad handle, level, steps or output");
+    if (construction != 1 && construction != 2)
+      fail(GAMBLET_ERR_INVALID_ARG, "construction must be 1 or 2");
     if (h->exact) fail(GAMBLET_ERR_UNSUPPORTED, "diagnostics run on the localized transform");
-    if (h->mixed) level_condition_impl<float>(h, k, steps, lmin, lmax);
-    else level_condition_impl<double>(h, k, steps, lmin, lmax);
+    if (h->mixed) level_condition_impl<float>(h, k, construction, steps, lmin, lmax);
+    else level_condition_impl<double>(h, k, construction, steps, lmin, lmax);
     return GAMBLET_OK;
   } catch (const GbError& e) {
     return set_error(e);

@@ -24,6 +24,10 @@ void launch_detail_spmv(const T* Bd, const int2* off, int noff, int Lpar, int64_
                         const double* x, double* y, cudaStream_t s);
 // deterministic pseudo-random start vector on the active detail slots
 void launch_detail_start(int64_t npar, const uint32_t* pmask, double* v, cudaStream_t s);
+// detail vectors from the stored Helmert basis to Construction const1:
+// out = M in (transpose 0) or M^T in (1), per parent; W1 A W1^T = M B M^T
+void launch_detail_basis(int64_t npar, const uint32_t* pmask, const double* in, double* out,
+                         int transpose, cudaStream_t s);
 // out = a x + b y + c z (y, z may be NULL)
 void launch_lanczos_step(int64_t n, double a, const double* x, const double* y, double b,
                          const double* z, double c, double* out, cudaStream_t s);

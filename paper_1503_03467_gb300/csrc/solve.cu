@@ -545,6 +545,46 @@ void launch_lanczos_step(int64_t n, double a, const double* x, const double* y, 
   if (n > 0) { count_launch(); k_lanczos_step<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, x, y, b, z, c, out); }
 }
 
+// Change of detail basis on transformed level vectors, per parent with
+// cnt active children: out = M in (transpose = 0) or M^T in (1), with
+// M = W1 W2^T the matrix taking the orthonormal Helmert rows W2 (the stored
+// basis) to the consecutive differences W1 of Construction const1 (row t:
+// child t minus child t + 1, in the order of the active children).  Then
+// W1 A W1^T = M B M^T.  Slot 3 and inactive slots are zero on output.
+// in and out may be the same array: a thread reads its parent's slots
+// before it writes them, and parents do not overlap.
+__global__ void k_detail_basis(int64_t npar, const uint32_t* __restrict__ pmask,
+                               const double* in, double* out, int transpose) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= npar) return;
+  const int m = (int)pmask[p] & 15;
+  const int cnt = __popc(m);
+  int cidx[4] = {0, 0, 0, 0};  // slot of the j-th active child
+  for (int c = 0, j = 0; c < 4; ++c)
+    if ((m >> c) & 1) cidx[j++] = c;
+  double M[3][3];
+  for (int t = 0; t < 3; ++t)
+    for (int a = 0; a < 3; ++a) {
+      M[t][a] = 0.0;
+      if (t < cnt - 1 && a < cnt - 1)
+        M[t][a] = qv<double>(m, a, cidx[t]) - qv<double>(m, a, cidx[t + 1]);
+    }
+  const double x0 = in[4 * p], x1 = in[4 * p + 1], x2 = in[4 * p + 2];
+  for (int t = 0; t < 3; ++t) {
+    const double v = transpose ? M[0][t] * x0 + M[1][t] * x1 + M[2][t] * x2
+                               : M[t][0] * x0 + M[t][1] * x1 + M[t][2] * x2;
+    out[4 * p + t] = t < cnt - 1 ? v : 0.0;
+  }
+  out[4 * p + 3] = 0.0;
+}
+void launch_detail_basis(int64_t npar, const uint32_t* pmask, const double* in, double* out,
+                         int transpose, cudaStream_t s) {
+  if (npar > 0) {
+    count_launch();
+    k_detail_basis<<<(unsigned)((npar + 255) / 256), 256, 0, s>>>(npar, pmask, in, out, transpose);
+  }
+}
+
 // ---------------------------------------------------------------- several right-hand sides
 // Restriction of nrhs vectors: the row of Rhat is read once per lane and
 // applied to the neighbours' slots of every right-hand side.

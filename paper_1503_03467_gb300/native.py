@@ -87,7 +87,7 @@ SIGNATURES = {
     "gamblet_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.POINTER(Info)]),
     "gamblet_level_condition": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
-                                               ctypes.POINTER(ctypes.c_double),
+                                               ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                                ctypes.POINTER(ctypes.c_double)]),
     "gamblet_compress": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
@@ -240,11 +240,12 @@ def gamblet_solve(h: int, g, u, components=None, info: Info | None = None) -> in
     return _check(st)
 
 
-def gamblet_level_condition(h: int, k: int, steps: int = 60):
-    """(lmin, lmax) estimates of B^(k)'s extreme eigenvalues (Lanczos)."""
+def gamblet_level_condition(h: int, k: int, steps: int = 60, construction: int = 2):
+    """(lmin, lmax) estimates of the extreme eigenvalues of B^(k) = W A W^T
+    (Lanczos) for W of Construction const2 (2) or const1 (1)."""
     lo, hi = ctypes.c_double(), ctypes.c_double()
-    _check(_lib.gamblet_level_condition(ctypes.c_void_p(h), int(k), int(steps), ctypes.byref(lo),
-                                        ctypes.byref(hi)))
+    _check(_lib.gamblet_level_condition(ctypes.c_void_p(h), int(k), int(construction), int(steps),
+                                        ctypes.byref(lo), ctypes.byref(hi)))
     return lo.value, hi.value
 
 

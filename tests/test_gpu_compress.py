@@ -43,19 +43,22 @@ def test_compression_matches_oracle(which):
         nv.gamblet_destroy(h)
 
 
-def test_level_condition_matches_dense_eigenvalues():
-    """Lanczos extremes of B^(k) against the dense eigenvalues of the
-    oracle's B^(k) (exact when the Lanczos runs |J^(k)| steps)."""
+@pytest.mark.parametrize("construction", [2, 1])
+def test_level_condition_matches_dense_eigenvalues(construction):
+    """Lanczos extremes of B^(k) = W A W^T against the dense eigenvalues of
+    the oracle's B^(k) for the same construction of W (exact when the
+    Lanczos runs |J^(k)| steps)."""
     from paper_1503_03467_gb300 import native as nv
     p = make_problem(32, 1e3, 6)
-    ref = gamblet_local_setup(p.A, p.cells, p.q, 3.0)
+    ref = gamblet_local_setup(p.A, p.cells, p.q, 3.0,
+                              construction="const1" if construction == 1 else "const2")
     h = _setup(p)
     try:
         for k in range(2, p.q + 1):
             ev = np.linalg.eigvalsh(ref["B"][k].toarray())
             nJ = len(ev)
             steps = nJ if nJ <= 200 else 200
-            lo, hi = nv.gamblet_level_condition(h, k, steps)
+            lo, hi = nv.gamblet_level_condition(h, k, steps, construction)
             tol = 1e-8 if steps == nJ else 1e-3
             assert abs(hi - ev[-1]) <= tol * ev[-1], (k, hi, ev[-1])
             assert abs(lo - ev[0]) <= tol * ev[-1] + tol * ev[0], (k, lo, ev[0])
