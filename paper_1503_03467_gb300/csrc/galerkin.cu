@@ -32,7 +32,7 @@ __device__ __forceinline__ void load_vec4(const double* p, double* b) {
   b[3] = v1.y;
 }
 
-// 4-element shared-memory rows as single 16-byte (float) or two 16-byte
+// 4-element rows (shared or global memory) as single 16-byte (float) or two 16-byte
 // (double) accesses: lanes that touch consecutive rows then hit distinct
 // banks, where four scalar accesses at a 16-byte stride collide four ways.
 __device__ __forceinline__ void sld4(const float* p, float* v) {
@@ -466,16 +466,19 @@ __global__ void k_cells_to_blocks(const T* __restrict__ Acell, int64_t ncell,
       for (int c = 0; c < 4; ++c) acc += Qr[a * 4 + c] * M[c * 4 + cc];
       Tm[a * 4 + cc] = acc;
     }
-  T* out = blk + t * 16;
+  T* out = blk + t * 16;  // 16-byte aligned: one vector store per output row
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 4; ++a) {
+    T row[4];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       T acc = 0;
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) acc += Tm[a * 4 + cc] * Qc[b * 4 + cc];
-      out[a * 4 + b] = acc;
+      row[b] = acc;
     }
+    sst4(out + 4 * a, row);
+  }
 }
 
 template <typename T>

@@ -349,6 +349,23 @@ template void launch_cg_rest<double>(const CgLevel*, int, int, CgScalars*, doubl
 
 // ---------------------------------------------------------------- set-up helpers
 // Bd[o][3a+b][p] = Ahat[o][p][4a+b] (detail block, coalesced copy).
+// One 4-entry row of a 4x4 block (16-byte aligned) as vector loads.
+__device__ __forceinline__ void ldrow4(const float* p, float* r) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  r[0] = v.x;
+  r[1] = v.y;
+  r[2] = v.z;
+  r[3] = v.w;
+}
+__device__ __forceinline__ void ldrow4(const double* p, double* r) {
+  const double2 v0 = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 v1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  r[0] = v0.x;
+  r[1] = v0.y;
+  r[2] = v1.x;
+  r[3] = v1.y;
+}
+
 template <typename T>
 __global__ void k_extract_detail(const T* __restrict__ Ahat, int noff, int64_t npar, T* Bd) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -357,13 +374,18 @@ __global__ void k_extract_detail(const T* __restrict__ Ahat, int noff, int64_t n
   const int64_t p = t - (int64_t)o * npar;
   const T* A = Ahat + t * 16;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < 3; ++a) {
+    T row[4];
+    ldrow4(A + 4 * a, row);  // one 16-byte load per block row
 #pragma unroll
-    for (int b = 0; b < 3; ++b) Bd[((int64_t)o * 9 + 3 * a + b) * npar + p] = A[4 * a + b];
+    for (int b = 0; b < 3; ++b) Bd[((int64_t)o * 9 + 3 * a + b) * npar + p] = row[b];
+  }
 }
 
 // Dinv[e][p] = inverse of the active leading block of the diagonal detail
-// block (zeros outside it), computed in float64.
+// block (zeros outside it), in the working precision (a 3x3 SPD block; the
+// float64 pipe would make this kernel wait in the mixed path).  Fixed trip
+// counts with predicates keep every array in registers.
 template <typename T>
 __global__ void k_detail_dinv(const T* __restrict__ Ahat, int o0, int64_t npar,
                               const uint32_t* __restrict__ pmask, T* Dinv) {
@@ -371,34 +393,44 @@ __global__ void k_detail_dinv(const T* __restrict__ Ahat, int o0, int64_t npar,
   if (p >= npar) return;
   const int m = __popc(pmask[p] & 15u);
   const int na = m > 0 ? m - 1 : 0;
-  double M[9], Inv[9];
-  for (int e = 0; e < 9; ++e) Inv[e] = 0.0;
+  T M[9], Inv[9];
   const T* A = Ahat + ((int64_t)o0 * npar + p) * 16;
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) M[3 * a + b] = (a < na && b < na) ? (double)A[4 * a + b] : 0.0;
-  // Gauss-Jordan on the na x na SPD block (no pivoting needed)
-  for (int a = 0; a < na; ++a) Inv[3 * a + a] = 1.0;
-  bool ok = true;
-  for (int c = 0; c < na; ++c) {
-    const double d = M[3 * c + c];
-    if (!(d > 0)) {
-      ok = false;
-      break;
-    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T row[4];
+    ldrow4(A + 4 * a, row);
+#pragma unroll
     for (int b = 0; b < 3; ++b) {
-      M[3 * c + b] /= d;
-      Inv[3 * c + b] /= d;
+      M[3 * a + b] = (a < na && b < na) ? row[b] : T(0);
+      Inv[3 * a + b] = (a == b && a < na) ? T(1) : T(0);
     }
-    for (int a = 0; a < na; ++a) {
-      if (a == c) continue;
-      const double f = M[3 * a + c];
+  }
+  // Gauss-Jordan on the na x na SPD block (no pivoting needed)
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (c >= na) continue;
+    const T d = M[4 * c];
+    ok = ok && d > T(0);
+    const T id = d > T(0) ? T(1) / d : T(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      M[3 * c + b] *= id;
+      Inv[3 * c + b] *= id;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a == c || a >= na) continue;
+      const T f = M[3 * a + c];
+#pragma unroll
       for (int b = 0; b < 3; ++b) {
         M[3 * a + b] -= f * M[3 * c + b];
         Inv[3 * a + b] -= f * Inv[3 * c + b];
       }
     }
   }
-  for (int e = 0; e < 9; ++e) Dinv[(int64_t)e * npar + p] = ok ? (T)Inv[e] : T(0);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) Dinv[(int64_t)e * npar + p] = ok ? Inv[e] : T(0);
 }
 
 template <typename T>

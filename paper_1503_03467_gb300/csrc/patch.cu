@@ -399,7 +399,7 @@ __device__ __forceinline__ void block_sum2(T& a, T& b, T* red) {
 }
 
 template <typename T, int kGather>
-__global__ void __launch_bounds__(256) k_patch_pcg(const T* __restrict__ Ahat,
+__global__ void __launch_bounds__(256, 3) k_patch_pcg(const T* __restrict__ Ahat,
                                                    const uint32_t* __restrict__ pmask,
                                                    PatchPcgGeom g, T* __restrict__ Rhat,
                                                    double tol2, int max_iter, int* iter_stats) {

@@ -26,6 +26,14 @@ __device__ __forceinline__ void ld4(const double* p, double* b) {
   b[3] = v1.y;
 }
 
+__device__ __forceinline__ void st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double* v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
 // ---------------------------------------------------------------- restriction
 // One warp per coarse row i (lanes over the neighbours j, so the row of R-hat
 // is read with unit stride); the four warps of a CTA hold the four children
@@ -106,10 +114,11 @@ __global__ void k_transpose_rhat(const T* __restrict__ Rhat, int NB, const int2*
   int x, y;
   demorton((uint32_t)p, x, y);
   const int i = shift_cell(x, y, -nbr[j].x, -nbr[j].y, Lpar, npar);
-  T* dst = RT + t * 4;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) dst[a] = i >= 0 ? Rhat[(int64_t)i * 4 * NB + 4 * j + a] : T(0);
-  dst[3] = T(0);
+  // one 16-byte load and store per entry (slot 3 of RT is zero)
+  T v[4] = {T(0), T(0), T(0), T(0)};
+  if (i >= 0) ld4(Rhat + (int64_t)i * 4 * NB + 4 * j, v);
+  v[3] = T(0);
+  st4(RT + t * 4, v);
 }
 
 template <typename T>
