@@ -361,7 +361,12 @@ struct gamblet_ctx {
   // per level and CG iteration: algorithmic traffic and flops of the SpMV and
   // of the vector kernels
   std::vector<double> cg_bytes_spmv, cg_flops_spmv, cg_bytes_vec, cg_flops_vec;
-  // outer
+  // outer: the fine operator as a Morton node stencil (float64), its cell
+  // offsets, and a scratch vector for the untransformed SpMV input
+  double* qst = nullptr;
+  const int2* qoff = nullptr;
+  int qns = 0;
+  double* xplain = nullptr;
   double* u64 = nullptr;
   double* r64 = nullptr;
   double* z64 = nullptr;
@@ -636,9 +641,42 @@ void import_fine(gamblet_ctx* h, const gamblet_csr* A) {
   L.off = P.upload(L.off_h, s);
   double* blk = P.zeros<double>((int64_t)L.noff * L.npar * 16, s);
   launch_csr_to_blocks(n, rowptr, colind, val, h->morton_of, rx, ry, L.npar, blk, s);
-  launch_transform_blocks(blk, L.off, L.noff, L.npar, Lpar, L.pmask, s);
+  if (h->mixed) {
+    // the working copy is transformed in float32 straight from the float64
+    // blocks; the outer float64 iteration applies the node stencil instead
+    float* a32 = P.alloc<float>((int64_t)L.noff * L.npar * 16);
+    launch_transform_blocks_f32(blk, a32, L.off, L.noff, L.npar, Lpar, L.pmask, s);
+    L.Ahat = a32;
+    L.Ahat64 = nullptr;
+  } else {
+    launch_transform_blocks(blk, L.off, L.noff, L.npar, Lpar, L.pmask, s);
+    L.Ahat64 = blk;
+  }
   CK(cudaGetLastError());
-  L.Ahat64 = blk;
+  // node stencil of A^(q) in Morton order for the outer float64 SpMV
+  int* next = P.zeros<int>(4, s);
+  launch_csr_node_extent(n, rowptr, colind, h->morton_of, next, next + 2, s);
+  int next_h[4];
+  CK(cudaMemcpyAsync(next_h, next, sizeof(next_h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int nrx = next_h[0], nry = next_h[1];
+  std::vector<int2> qoff;
+  for (int dy = -nry; dy <= nry; ++dy)
+    for (int dx = -nrx; dx <= nrx; ++dx) qoff.push_back(make_int2(dx, dy));
+  h->qns = (int)qoff.size();
+  h->qoff = P.upload(qoff, s);
+  h->qst = P.zeros<double>((int64_t)h->qns * L.ncell, s);
+  launch_csr_to_mstencil(n, rowptr, colind, val, h->morton_of, nrx, nry, L.ncell, h->qst, s);
+  CK(cudaGetLastError());
+}
+
+// yhat = Ahat^(q) xhat = Q A Q^T xhat in float64 on transformed level-q
+// vectors: untransform, node-stencil SpMV, transform (the last two fused).
+void outer_spmv(gamblet_ctx* h, const double* xhat, double* yhat) {
+  LevelDev& Lq = h->lv[h->q];
+  launch_transform_vec<double>(xhat, h->xplain, Lq.npar, Lq.pmask, -1, h->s);
+  launch_stencil_spmv_q(h->qst, h->qoff, h->qns, 1 << h->q, Lq.ncell, Lq.npar, Lq.pmask,
+                        h->xplain, yhat, h->s);
 }
 
 // ------------------------------------------------------------ symbolic plan
@@ -1004,9 +1042,11 @@ void setup_local(gamblet_ctx* h) {
     LevelDev& L = h->lv[q];
     const int64_t nv = (int64_t)L.noff * L.npar * 16;
     if (is_f32<T>()) {
-      float* a32 = P.alloc<float>(nv);
-      launch_convert_f64_f32(L.Ahat64, a32, nv, s);
-      L.Ahat = a32;
+      if (!L.Ahat) {  // transformed in float32 by the import already
+        float* a32 = P.alloc<float>(nv);
+        launch_convert_f64_f32(L.Ahat64, a32, nv, s);
+        L.Ahat = a32;
+      }
     } else {
       L.Ahat = L.Ahat64;
     }
@@ -1270,6 +1310,7 @@ void alloc_solve(gamblet_ctx* h) {
   h->U1 = P.zeros<T>(4, s);
   const int64_t nq = h->lv[q].ncell;
   h->u64 = P.zeros<double>(nq, s);
+  h->xplain = P.zeros<double>(nq, s);
   h->r64 = P.zeros<double>(nq, s);
   h->z64 = P.zeros<double>(nq, s);
   h->p64 = P.zeros<double>(nq, s);
@@ -1665,10 +1706,9 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
   const int maxit = h->opts.refine_max_iter;
   if (maxit > 0 && gnorm > 0) {
     // flexible CG (one-term orthogonalisation) on Ahat^(q) u = ghat
-    const int Lpar = 1 << (q - 1);
     double* d = h->dots;
     // r = g - A u
-    launch_block_spmv64(Lq.Ahat64, Lq.off, Lq.noff, Lpar, Lq.npar, h->u64, h->q64, s);
+    outer_spmv(h, h->u64, h->q64);
     CK(cudaMemcpyAsync(h->r64, h->g64, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(d, 0, sizeof(double) * 8, s));
     // d[7] = 1 used as unit denominator: r += (-1) * (1/1) q
@@ -1685,9 +1725,10 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
       if (is_f32<T>()) launch_convert_f32_f64((const float*)zT, h->z64, nq, s);
       CK(cudaMemcpyAsync(h->p64, h->z64, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
       for (outer = 1; outer <= maxit; ++outer) {
-        int tok = h->prof.begin("outer_spmv64", 8.0 * ((double)Lq.noff * Lq.npar * 16 + 8.0 * Lq.npar),
-                                2.0 * 16.0 * Lq.noff * Lq.npar, s);
-        launch_block_spmv64(Lq.Ahat64, Lq.off, Lq.noff, Lpar, Lq.npar, h->p64, h->q64, s);
+        // stencil read once, xhat read, x written and read, yhat written
+        int tok = h->prof.begin("outer_spmv64", 8.0 * ((double)h->qns * Lq.ncell + 4.0 * Lq.ncell),
+                                2.0 * h->qns * Lq.ncell + 2.0 * 32.0 * Lq.npar, s);
+        outer_spmv(h, h->p64, h->q64);
         h->prof.end(tok, s);
         CK(cudaMemsetAsync(d, 0, sizeof(double) * 4, s));
         // d0 = p.q, d1 = p.r
@@ -1714,7 +1755,7 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
       }
     }
     // true residual
-    launch_block_spmv64(Lq.Ahat64, Lq.off, Lq.noff, Lpar, Lq.npar, h->u64, h->q64, s);
+    outer_spmv(h, h->u64, h->q64);
     CK(cudaMemcpyAsync(h->r64, h->g64, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(d + 7, &one, sizeof(double), cudaMemcpyHostToDevice, s));
     launch_axpy(nq, d + 7, d + 7, -1.0, h->q64, h->r64, s);
@@ -2125,13 +2166,12 @@ void solve_group(gamblet_ctx* h, int nb, const double* G_user, double* U_user, d
   precondition(g64, z64);
   CK(cudaMemcpyAsync(u64, z64, sizeof(double) * nq * nb, cudaMemcpyDeviceToDevice, s));
   const int maxit = h->opts.refine_max_iter;
-  const int Lpar = 1 << (q - 1);
   std::vector<double> rel(nb, 0.0);
   std::vector<int> active(nb, 0), outer(nb, 0);
   double one = 1.0;
   double* onep = tmp.upload(std::vector<double>(nb, 1.0), s);
   auto residual = [&]() {  // r = g - A u, rel = |r| / |g|
-    launch_block_spmv64_m(Lq.Ahat64, Lq.off, Lq.noff, Lpar, Lq.npar, u64, q64, nq, nb, s);
+    for (int r = 0; r < nb; ++r) outer_spmv(h, u64 + r * nq, q64 + r * nq);
     CK(cudaMemcpyAsync(r64, g64, sizeof(double) * nq * nb, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(d, 0, sizeof(double) * 8 * nb, s));
     for (int r = 0; r < nb; ++r) {
@@ -2152,7 +2192,8 @@ void solve_group(gamblet_ctx* h, int nb, const double* G_user, double* U_user, d
       CK(cudaMemcpyAsync(p64, z64, sizeof(double) * nq * nb, cudaMemcpyDeviceToDevice, s));
       for (int it = 1; it <= maxit && nact; ++it) {
         int tok = h->prof.begin("outer_spmv64", 0.0, 0.0, s);
-        launch_block_spmv64_m(Lq.Ahat64, Lq.off, Lq.noff, Lpar, Lq.npar, p64, q64, nq, nb, s);
+        for (int r = 0; r < nb; ++r)
+          if (active[r]) outer_spmv(h, p64 + r * nq, q64 + r * nq);
         h->prof.end(tok, s);
         CK(cudaMemsetAsync(d, 0, sizeof(double) * 8 * nb, s));
         for (int r = 0; r < nb; ++r) {

@@ -246,6 +246,98 @@ void launch_transform_blocks(double* blk, const int2* off, int noff, int64_t npa
                                                                 pmask); }
 }
 
+// Fine CSR -> node stencil in Morton order: St[s][c] = A_{i, j} with c the
+// level-q cell of unknown i and c + S_s that of j (S: the (2 rx + 1) x
+// (2 ry + 1) box, row-major in (dy, dx)); cells without an unknown stay 0.
+// St must be zeroed; each (s, c) is written by the thread of its row only.
+__global__ void k_csr_to_mstencil(int n, const int32_t* __restrict__ rowptr,
+                                  const int32_t* __restrict__ colind,
+                                  const double* __restrict__ val,
+                                  const int32_t* __restrict__ morton_of, int rx, int ry,
+                                  int64_t ncell, double* St) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int ci = morton_of[i];
+  int xi, yi;
+  demorton((uint32_t)ci, xi, yi);
+  for (int t = rowptr[i]; t < rowptr[i + 1]; ++t) {
+    const int j = colind[t];
+    if ((unsigned)j >= (unsigned)n) continue;
+    int xj, yj;
+    demorton((uint32_t)morton_of[j], xj, yj);
+    const int dx = xj - xi, dy = yj - yi;
+    if (dx < -rx || dx > rx || dy < -ry || dy > ry) continue;
+    St[(int64_t)((dy + ry) * (2 * rx + 1) + dx + rx) * ncell + ci] += val[t];
+  }
+}
+void launch_csr_to_mstencil(int n, const int32_t* rowptr, const int32_t* colind,
+                            const double* val, const int32_t* morton_of, int rx, int ry,
+                            int64_t ncell, double* St, cudaStream_t s) {
+  if (n > 0) {
+    count_launch();
+    k_csr_to_mstencil<<<(n + 127) / 128, 128, 0, s>>>(n, rowptr, colind, val, morton_of, rx, ry,
+                                                      ncell, St);
+  }
+}
+
+// out(o, p) = Q_{mask p} blk(o, p) Q_{mask p+off_o}^T in float32 arithmetic
+// from an untransformed float64 block stencil: the level-q operator of the
+// mixed path without a float64 transform (the float64 pipe is the slow one).
+__global__ void k_transform_blocks_f32(const double* __restrict__ blk, float* out,
+                                       const int2* __restrict__ off, int noff, int64_t npar,
+                                       int Lpar, const uint32_t* __restrict__ pmask) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)noff * npar) return;
+  const int o = (int)(t / npar);
+  const int64_t p = t - (int64_t)o * npar;
+  int x, y;
+  demorton((uint32_t)p, x, y);
+  const int pp = shift_cell(x, y, off[o].x, off[o].y, Lpar, npar);
+  const int mr = (int)pmask[p] & 15;
+  const int mc = pp >= 0 ? (int)pmask[pp] & 15 : 0;
+  float M[16], Tm[16], Qr[16], Qc[16];
+  qmat<float>(mr, Qr);
+  qmat<float>(mc, Qc);
+  const double2* B2 = reinterpret_cast<const double2*>(blk + t * 16);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const double2 v = B2[e];
+    M[2 * e] = (float)v.x;
+    M[2 * e + 1] = (float)v.y;
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float acc = 0.f;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc += Qr[a * 4 + r] * M[r * 4 + c];
+      Tm[a * 4 + c] = acc;
+    }
+  float4* O4 = reinterpret_cast<float4*>(out + t * 16);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    float v[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      float acc = 0.f;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc += Tm[a * 4 + c] * Qc[b * 4 + c];
+      v[b] = acc;
+    }
+    O4[a] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+void launch_transform_blocks_f32(const double* blk, float* out, const int2* off, int noff,
+                                 int64_t npar, int Lpar, const uint32_t* pmask, cudaStream_t s) {
+  const int64_t n = (int64_t)noff * npar;
+  if (n > 0) {
+    count_launch();
+    k_transform_blocks_f32<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blk, out, off, noff, npar,
+                                                                        Lpar, pmask);
+  }
+}
+
 __global__ void k_f64_to_f32(const double* __restrict__ in, float* out, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];

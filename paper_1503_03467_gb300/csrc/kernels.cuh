@@ -117,6 +117,20 @@ void launch_csr_to_blocks(int n, const int32_t* rowptr, const int32_t* colind,
                           const double* val, const int32_t* morton_of, int rx, int ry,
                           int64_t npar, double* blk, cudaStream_t s);
 
+// Fine CSR -> node stencil in Morton order, St[s][c] (s over the box
+// (2 rx + 1) x (2 ry + 1), row-major in (dy, dx)); St must be zeroed.
+void launch_csr_to_mstencil(int n, const int32_t* rowptr, const int32_t* colind,
+                            const double* val, const int32_t* morton_of, int rx, int ry,
+                            int64_t ncell, double* St, cudaStream_t s);
+// yhat = Q (A x): node-stencil SpMV on the untransformed level-q vector x,
+// transformed output (one thread per parent).
+void launch_stencil_spmv_q(const double* St, const int2* off, int ns, int L, int64_t ncell,
+                           int64_t npar, const uint32_t* pmask, const double* x, double* yhat,
+                           cudaStream_t s);
+// out(o, p) = Q blk(o, p) Q'^T in float32 from an untransformed float64 stencil.
+void launch_transform_blocks_f32(const double* blk, float* out, const int2* off, int noff,
+                                 int64_t npar, int Lpar, const uint32_t* pmask, cudaStream_t s);
+
 // ---------------------------------------------------------------- transforms
 // In place: blk(o, p) <- Q_{mask p} blk(o, p) Q_{mask p+off_o}^T.
 void launch_transform_blocks(double* blk, const int2* off, int noff, int64_t npar,
@@ -307,8 +321,6 @@ void launch_cg_level_setup(const T* Ahat, int noff, int o0, int64_t npar, const 
                            T* Bd, T* Dinv, cudaStream_t s);
 
 // Outer float64 operations on transformed level-q vectors.
-void launch_block_spmv64(const double* Ahat, const int2* off, int noff, int Lpar, int64_t npar,
-                         const double* x, double* y, cudaStream_t s);
 // dots[i] += a_i . b_i for up to 3 pairs (nullptr pairs skipped).
 void launch_dots(int64_t n, const double* a0, const double* b0, const double* a1,
                  const double* b1, const double* a2, const double* b2, double* dots,
@@ -368,8 +380,6 @@ void launch_prolong_m(const T* RT, int NB, const int2* nbr, int Lpar, int64_t np
                       const T* v_km1, int64_t vstride, const T* w_k, int64_t wstride,
                       const uint32_t* pmask_k, int inverse, T* out, int64_t ostride, int nrhs,
                       cudaStream_t s);
-void launch_block_spmv64_m(const double* Ahat, const int2* off, int noff, int Lpar, int64_t npar,
-                           const double* x, double* y, int64_t stride, int nrhs, cudaStream_t s);
 // The batched level CG over (level, right-hand side): scalars sc[l * nrhs + r],
 // vectors of right-hand side r at CgLevel pointer + r * rstride.
 template <typename T>

@@ -305,42 +305,54 @@ template void launch_level1_solve<float>(const double*, const float*, float*, cu
 template void launch_level1_solve<double>(const double*, const double*, double*, cudaStream_t);
 
 // ---------------------------------------------------------------- outer float64
-// y = Ahat x on the float64 block stencil.  Four lanes per parent, lane a
-// owning block row a: for each offset the 8 parents of a warp read 8
-// consecutive 128-byte blocks (one coalesced 1 KB stream), the neighbour's
-// four x values are a broadcast, and row a is written by its own lane.
-__global__ void __launch_bounds__(256) k_block_spmv64(const double* __restrict__ A,
-                                                      const int2* __restrict__ off, int noff,
-                                                      int Lpar, int64_t npar,
-                                                      const double* __restrict__ xv, double* yv) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t p = t >> 2;
-  const int a = (int)(t & 3);
-  if (p >= npar) return;
-  int x, y;
-  demorton((uint32_t)p, x, y);
-  double acc = 0;
-  const double2 zero = make_double2(0.0, 0.0);
-#pragma unroll 3
-  for (int o = 0; o < noff; ++o) {
-    // predicated rather than branched, so unrolled iterations keep their
-    // loads in flight together
-    const int q = shift_cell(x, y, off[o].x, off[o].y, Lpar, npar);
-    const bool ok = q >= 0;
-    const double2* row = reinterpret_cast<const double2*>(A + ((int64_t)o * npar + p) * 16 + 4 * a);
-    const double2* xq = reinterpret_cast<const double2*>(xv + 4 * (int64_t)(ok ? q : 0));
-    const double2 r0 = ok ? __ldg(row) : zero, r1 = ok ? __ldg(row + 1) : zero;
-    const double2 x0 = ok ? __ldg(xq) : zero, x1 = ok ? __ldg(xq + 1) : zero;
-    acc += r0.x * x0.x + r0.y * x0.y + r1.x * x1.x + r1.y * x1.y;
+// yhat = Q (A x) on the float64 level-q vectors: x untransformed (Morton
+// order), A the node stencil St[s][c] over the cell offsets off[s].  One
+// thread per parent: per offset its four cells' stencil values are 32
+// contiguous bytes (one coalesced stream across the warp), then the
+// parent's Q (rows unrolled, so its constants fold) transforms the result.
+// With yhat = Q A Q^T xhat this is the transformed operator at 9 stored
+// values per node instead of 36 per node in 4 x 4 transformed blocks.
+__global__ void __launch_bounds__(256) k_stencil_spmv_q(const double* __restrict__ St,
+                                                        const int2* __restrict__ off, int ns,
+                                                        int L, int64_t ncell, int64_t npar,
+                                                        const uint32_t* __restrict__ pmask,
+                                                        const double* __restrict__ x,
+                                                        double* yhat) {
+  const int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (P >= npar) return;
+  int xc[4], yc[4];
+  bool in[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    in[a] = 4 * P + a < ncell;
+    demorton((uint32_t)(4 * P + a), xc[a], yc[a]);
   }
-  yv[4 * p + a] = acc;
+  double y[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int t = 0; t < ns; ++t) {
+    const int2 o = off[t];
+    const double2* s2 = reinterpret_cast<const double2*>(St + (int64_t)t * ncell + 4 * P);
+    const double2 s01 = __ldg(s2), s23 = __ldg(s2 + 1);
+    const double sv[4] = {s01.x, s01.y, s23.x, s23.y};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int nb = in[a] ? shift_cell(xc[a], yc[a], o.x, o.y, L, ncell) : -1;
+      if (nb >= 0) y[a] += sv[a] * x[nb];
+    }
+  }
+  const int m = (int)pmask[P] & 15;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+    yhat[4 * P + a] = qv<double>(m, a, 0) * y[0] + qv<double>(m, a, 1) * y[1] +
+                      qv<double>(m, a, 2) * y[2] + qv<double>(m, a, 3) * y[3];
 }
 
-void launch_block_spmv64(const double* Ahat, const int2* off, int noff, int Lpar, int64_t npar,
-                         const double* x, double* y, cudaStream_t s) {
+void launch_stencil_spmv_q(const double* St, const int2* off, int ns, int L, int64_t ncell,
+                           int64_t npar, const uint32_t* pmask, const double* x, double* yhat,
+                           cudaStream_t s) {
   if (npar <= 0) return;
-  const int64_t n = 4 * npar;
-  { count_launch(); k_block_spmv64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ahat, off, noff, Lpar, npar, x, y); }
+  count_launch();
+  k_stencil_spmv_q<<<(unsigned)((npar + 255) / 256), 256, 0, s>>>(St, off, ns, L, ncell, npar,
+                                                                  pmask, x, yhat);
 }
 
 __global__ void k_dots(int64_t n, const double* __restrict__ a0, const double* __restrict__ b0,
@@ -759,43 +771,5 @@ template void launch_prolong_m<double>(const double*, int, const int2*, int, int
                                        const double*, int64_t, const double*, int64_t,
                                        const uint32_t*, int, double*, int64_t, int, cudaStream_t);
 
-// y_r = Ahat x_r for nrhs vectors, each 128-byte block row read once.
-__global__ void __launch_bounds__(256) k_block_spmv64_m(const double* __restrict__ A,
-                                                        const int2* __restrict__ off, int noff,
-                                                        int Lpar, int64_t npar,
-                                                        const double* __restrict__ xv, double* yv,
-                                                        int64_t stride, int nrhs) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t p = t >> 2;
-  const int a = (int)(t & 3);
-  if (p >= npar) return;
-  int x, y;
-  demorton((uint32_t)p, x, y);
-  double acc[kMaxRhs] = {0, 0, 0, 0};
-  for (int o = 0; o < noff; ++o) {
-    const int q = shift_cell(x, y, off[o].x, off[o].y, Lpar, npar);
-    if (q < 0) continue;
-    const double2* row = reinterpret_cast<const double2*>(A + ((int64_t)o * npar + p) * 16 + 4 * a);
-    const double2 r0 = __ldg(row), r1 = __ldg(row + 1);
-#pragma unroll
-    for (int r = 0; r < kMaxRhs; ++r) {
-      if (r < nrhs) {
-        const double2* xq = reinterpret_cast<const double2*>(xv + r * stride + 4 * (int64_t)q);
-        const double2 x0 = __ldg(xq), x1 = __ldg(xq + 1);
-        acc[r] += r0.x * x0.x + r0.y * x0.y + r1.x * x1.x + r1.y * x1.y;
-      }
-    }
-  }
-  for (int r = 0; r < nrhs; ++r) yv[r * stride + 4 * p + a] = acc[r];
-}
-
-void launch_block_spmv64_m(const double* Ahat, const int2* off, int noff, int Lpar, int64_t npar,
-                           const double* x, double* y, int64_t stride, int nrhs, cudaStream_t s) {
-  if (npar <= 0) return;
-  const int64_t n = 4 * npar;
-  count_launch();
-  k_block_spmv64_m<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ahat, off, noff, Lpar, npar, x, y,
-                                                                stride, nrhs);
-}
 
 }  // namespace gb
