@@ -327,3 +327,47 @@ def test_several_right_hand_sides(precision):
                 assert info.rel_residual < 1e-12
         finally:
             nv.gamblet_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_convergence_status_and_iteration_counts(precision):
+    """The status and counters a caller relies on: a one-pass solve whose
+    level CGs are stopped after a few iterations reports NOT_CONVERGED with
+    those iteration counts; an outer iteration stopped short of its
+    tolerance reports NOT_CONVERGED with its count; a normal solve reports OK
+    and at least one level-CG iteration on every level.  (The counts are
+    accumulated on the device and read once per solve.)"""
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(32, 1e3, 3)
+    rp, ci, va = csr_arrays(p.A)
+
+    def run(level_tol, level_max_iter, refine_tol, refine_max_iter):
+        o = nv.gamblet_default_opts()
+        o.precision = precision
+        o.level_tol = level_tol
+        o.level_max_iter = level_max_iter
+        o.refine_tol = refine_tol
+        o.refine_max_iter = refine_max_iter
+        h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
+        try:
+            u = np.zeros(p.ndof)
+            info = nv.Info()
+            st = nv.gamblet_solve(h, p.g, u, None, info)
+            return st, info, u
+        finally:
+            nv.gamblet_destroy(h)
+
+    # one pass, level CGs capped at two iterations and far from 1e-14
+    st, info, u = run(1e-14, 2, 1e-10, 0)
+    assert st == nv.ERR_NOT_CONVERGED and info.status == nv.ERR_NOT_CONVERGED
+    assert np.all(np.isfinite(u)) and np.linalg.norm(u) > 0
+    for k in range(2, p.q + 1):
+        assert 1 <= info.level_iters[k] <= 2, (k, info.level_iters[k])
+    # outer iteration capped at one step, tolerance out of reach
+    st, info, u = run(0.1, 1000, 1e-15, 1)
+    assert st == nv.ERR_NOT_CONVERGED and info.outer_iters == 1
+    # normal solve
+    st, info, u = run(0.1, 1000, 1e-10, 100)
+    assert st == nv.OK and info.rel_residual <= 1e-10
+    assert all(info.level_iters[k] >= 1 for k in range(2, p.q + 1))
+    assert rel(u, direct.solve(p.A, p.g)[0]) < 1e-8
