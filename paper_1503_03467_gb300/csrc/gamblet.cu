@@ -38,6 +38,11 @@ void launch_dense_transform(const double* in, int64_t npar, const uint32_t* pmas
                             cudaStream_t s);
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// Kernels launched by replays of a captured graph are counted per replay;
+// the counts taken while capturing are removed again.
+long long launches_now() { return g_launches.load(std::memory_order_relaxed); }
+void uncount_launches(long long n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace gb
 
 using namespace gb;
@@ -357,7 +362,8 @@ struct gamblet_ctx {
   cudaGraphExec_t cg_exec = nullptr;
   bool cg_while = false;           // cg_exec is a device-side while loop
   int* cg_loop_count = nullptr;    // passes of that loop
-  int* cg_stats = nullptr;         // device: level-CG iterations per level, [32] not converged
+  int* cg_stats = nullptr;         // device: level-CG iterations per level, [32] not converged,
+                                   // [33] passes of the device-side loop
   // per level and CG iteration: algorithmic traffic and flops of the SpMV and
   // of the vector kernels
   std::vector<double> cg_bytes_spmv, cg_flops_spmv, cg_bytes_vec, cg_flops_vec;
@@ -1366,7 +1372,7 @@ void alloc_solve(gamblet_ctx* h) {
     h->cg_sc = P.zeros<CgScalars>(std::max(h->cg_nlev, 1), s);
     h->any_active = P.zeros<int>(1, s);
     h->cg_loop_count = P.zeros<int>(1, s);
-    h->cg_stats = P.zeros<int>(33, s);
+    h->cg_stats = P.zeros<int>(34, s);
   }
 }
 
@@ -1398,6 +1404,7 @@ void build_cg_graph(gamblet_ctx* h, int chunk, double tol2, int maxit) {
   cudaGetLastError();
   if (while_ok) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const long long c0 = launches_now();
     CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
                                      cudaStreamCaptureModeThreadLocal));
     launch_cg_spmv<T>(h->cg_lv, h->cg_nlev, h->cg_spmv_blocks, h->cg_sc, h->cg_max_ts, cs);
@@ -1405,6 +1412,7 @@ void build_cg_graph(gamblet_ctx* h, int chunk, double tol2, int maxit) {
                       cond, 1, h->cg_loop_count, maxit + 2);
     cudaGraph_t captured;
     CK(cudaStreamEndCapture(cs, &captured));
+    uncount_launches(launches_now() - c0);  // counted per pass when the loop runs
     h->cg_while = true;
   } else {
     CK(cudaGraphDestroy(g));
@@ -1423,12 +1431,19 @@ void build_cg_graph(gamblet_ctx* h, int chunk, double tol2, int maxit) {
 }
 
 template <typename T>
+void cg_work_per_iteration(gamblet_ctx* h);
+
+// level-CG iterations per captured chunk when the driver offers no
+// conditional nodes (the while-loop graph is used otherwise)
+constexpr int kCgChunk = 8;
+
+template <typename T>
 void run_level_cg(gamblet_ctx* h) {
   cudaStream_t s = h->s;
   if (h->cg_nlev == 0) return;
   const double tol2 = h->opts.level_tol * h->opts.level_tol;
   const int maxit = std::max(h->opts.level_max_iter, 1);
-  const int chunk = 8;
+  const int chunk = kCgChunk;
   CK(cudaMemsetAsync(h->cg_sc, 0, sizeof(CgScalars) * h->cg_nlev, s));
   CK(cudaMemsetAsync(h->cg_loop_count, 0, sizeof(int), s));
   launch_cg_init<T>(h->cg_lv, h->cg_nlev, h->cg_blocks, h->cg_sc, s);
@@ -1467,31 +1482,17 @@ void run_level_cg(gamblet_ctx* h) {
   }
   // iteration counts and convergence stay on the device until the solve ends
   // (levels above a truncation are not solved and cannot fail to converge)
-  launch_cg_collect(h->cg_sc, h->cg_nlev, h->kmax, tol2, h->cg_stats, s);
+  launch_cg_collect(h->cg_sc, h->cg_nlev, h->kmax, tol2, h->cg_while ? h->cg_loop_count : nullptr,
+                    h->cg_stats, s);
   CK(cudaGetLastError());
-  if (h->cg_bytes_spmv.empty()) {
-    h->cg_bytes_spmv.assign(h->cg_nlev, 0.0);
-    h->cg_flops_spmv.assign(h->cg_nlev, 0.0);
-    h->cg_bytes_vec.assign(h->cg_nlev, 0.0);
-    h->cg_flops_vec.assign(h->cg_nlev, 0.0);
-    for (int l = 0; l < h->cg_nlev; ++l) {
-      // algorithmic traffic: the 3x3 detail blocks of B^(k) once per iteration,
-      // p read, Ap written (3 active slots); vector kernels: x, r, z, p, Ap, Dinv
-      const LevelDev& L = h->lv[l + 2];
-      const double sz = (double)sizeof(T);
-      h->cg_bytes_spmv[l] = sz * ((double)L.noff * L.npar * 9 + 6.0 * L.npar);
-      h->cg_flops_spmv[l] = 2.0 * 9.0 * L.noff * L.npar;
-      h->cg_bytes_vec[l] = sz * 3.0 * L.npar * 12;
-      h->cg_flops_vec[l] = 3.0 * L.npar * 12;
-    }
-  }
+  cg_work_per_iteration<T>(h);
 }
 
 // Level-CG counts accumulated on the device since the last call: added to
 // the handle's totals and to the kernel profile (synchronises the stream).
 void flush_level_stats(gamblet_ctx* h) {
   if (!h->cg_stats || h->cg_nlev == 0) return;
-  int st[33];
+  int st[34];
   CK(cudaMemcpyAsync(st, h->cg_stats, sizeof(st), cudaMemcpyDeviceToHost, h->s));
   CK(cudaMemsetAsync(h->cg_stats, 0, sizeof(st), h->s));
   CK(cudaStreamSynchronize(h->s));
@@ -1509,6 +1510,7 @@ void flush_level_stats(gamblet_ctx* h) {
     }
   }
   if (st[32]) h->level_not_conv = true;
+  count_launches(4LL * st[33]);  // spmv, update, scalars, direction per pass
 }
 
 // in: transformed level-q vector (T); out: transformed (inverse_last = 0) or
@@ -1591,6 +1593,26 @@ void apply_G_up(gamblet_ctx* h, T* out, int inverse_last) {
     }
   }
   CK(cudaGetLastError());
+}
+
+// Level-CG traffic and flops per iteration and level (kernel profile).
+template <typename T>
+void cg_work_per_iteration(gamblet_ctx* h) {
+  if (!h->cg_bytes_spmv.empty()) return;
+  h->cg_bytes_spmv.assign(h->cg_nlev, 0.0);
+  h->cg_flops_spmv.assign(h->cg_nlev, 0.0);
+  h->cg_bytes_vec.assign(h->cg_nlev, 0.0);
+  h->cg_flops_vec.assign(h->cg_nlev, 0.0);
+  for (int l = 0; l < h->cg_nlev; ++l) {
+    // the 3x3 detail blocks of B^(k) once per iteration, p read, Ap written
+    // (3 active slots); vector kernels: x, r, z, p, Ap, Dinv
+    const LevelDev& L = h->lv[l + 2];
+    const double sz = (double)sizeof(T);
+    h->cg_bytes_spmv[l] = sz * ((double)L.noff * L.npar * 9 + 6.0 * L.npar);
+    h->cg_flops_spmv[l] = 2.0 * 9.0 * L.noff * L.npar;
+    h->cg_bytes_vec[l] = sz * 3.0 * L.npar * 12;
+    h->cg_flops_vec[l] = 3.0 * L.npar * 12;
+  }
 }
 
 template <typename T>
@@ -1884,6 +1906,14 @@ gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
       alloc_solve<double>(h);
     }
     CK(cudaEventRecord(e1, h->s));
+    // the level-CG graph is captured while the device still runs the setup
+    // (a capture launches nothing), not inside the first solve
+    if (!h->exact && h->opts.use_graph && h->cg_nlev > 0 && !h->cg_exec) {
+      const double tol2 = h->opts.level_tol * h->opts.level_tol;
+      const int maxit = std::max(h->opts.level_max_iter, 1);
+      if (h->mixed) build_cg_graph<float>(h, kCgChunk, tol2, maxit);
+      else build_cg_graph<double>(h, kCgChunk, tol2, maxit);
+    }
     CK(cudaStreamSynchronize(h->s));
     CK(cudaGetLastError());
     float ms = 0;

@@ -298,10 +298,11 @@ void launch_cg_init(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc
 // Activates the levels l < nlev_on whose right-hand side is nonzero.
 void launch_cg_start(CgScalars* sc, int nlev, int nlev_on, double tol2, int* any_active,
                      cudaStream_t s);
-// Accumulate per-level iteration counts into stats[2..31] and a
-// not-converged flag into stats[32] on the device (nlev <= 30).
-void launch_cg_collect(const CgScalars* sc, int nlev, int kmax, double tol2, int* stats,
-                       cudaStream_t s);
+// Accumulate per-level iteration counts into stats[2..31], a not-converged
+// flag into stats[32] and the device-side loop's passes (loop_count, or
+// NULL) into stats[33] on the device (nlev <= 30).
+void launch_cg_collect(const CgScalars* sc, int nlev, int kmax, double tol2,
+                       const int* loop_count, int* stats, cudaStream_t s);
 // One CG iteration = launch_cg_spmv (Ap = B p, p.Ap) then launch_cg_rest
 // (x, r, z update with r.z and r.r; scalars and convergence; p = z + beta p).
 template <typename T>

@@ -296,19 +296,22 @@ void launch_cg_start(CgScalars* sc, int nlev, int nlev_on, double tol2, int* any
 // Iteration counts of one level-CG call added to stats[k] (level k = l + 2)
 // and stats[32] set when a solved level (k <= kmax) missed the tolerance, so
 // that the host reads them once per solve instead of after every call.
+// stats[33] accumulates the passes of the device-side loop (loop_count, may
+// be NULL), each of which launched the four kernels of one CG iteration.
 __global__ void k_cg_collect(const CgScalars* __restrict__ sc, int nlev, int kmax, double tol2,
-                             int* stats) {
+                             const int* loop_count, int* stats) {
   const int l = threadIdx.x;
+  if (l == 0 && loop_count) stats[33] += *loop_count;
   if (l >= nlev || l + 2 > 31) return;
   stats[l + 2] += sc[l].iters;
   if (l + 2 <= kmax && sc[l].rr > tol2 * sc[l].rr0) stats[32] = 1;
 }
 
-void launch_cg_collect(const CgScalars* sc, int nlev, int kmax, double tol2, int* stats,
-                       cudaStream_t s) {
+void launch_cg_collect(const CgScalars* sc, int nlev, int kmax, double tol2,
+                       const int* loop_count, int* stats, cudaStream_t s) {
   if (nlev <= 0) return;
   count_launch();
-  k_cg_collect<<<1, 32, 0, s>>>(sc, nlev, kmax, tol2, stats);
+  k_cg_collect<<<1, 32, 0, s>>>(sc, nlev, kmax, tol2, loop_count, stats);
 }
 
 template <typename T>
