@@ -2,7 +2,12 @@
 
 Forward: the library assembles the fine operator's values from exp(log a)
 (gamblet_assemble_cells), builds the hierarchy (gamblet_setup) and solves
-A u = g (gamblet_solve).  Backward: for an upstream gradient G = dL/du the
+A u = g (gamblet_solve).  The hierarchy either stays alive for the backward
+pass (keep_hierarchy=True) or is released after the forward solve and
+recomputed level by level in the backward pass from the saved operator
+values (keep_hierarchy=False: between the two passes only the fine values,
+8 bytes per stored entry, are held instead of every level's operators and
+interpolation rows).  Backward: for an upstream gradient G = dL/du the
 adjoint system A lambda = G is solved with the same hierarchy and the
 per-cell contraction dL/dlog a_c = -a_c lambda_c^T K_ref u_c runs in the
 library's adjoint kernel (gamblet_grad with u_obs = u - G, so that its
@@ -48,7 +53,7 @@ class Q1Mesh:
 
 class GambletSolve(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, log_a, g, mesh: Q1Mesh, opts):
+    def forward(ctx, log_a, g, mesh: Q1Mesh, opts, keep_hierarchy=True):
         stream = torch.cuda.current_stream(log_a.device).cuda_stream
         log_a = log_a.detach().contiguous()
         val = torch.empty(mesh.colind.numel(), dtype=torch.float64, device=log_a.device)
@@ -61,8 +66,15 @@ class GambletSolve(torch.autograd.Function):
         g = g.detach().contiguous()
         u = torch.empty_like(g)
         nv.gamblet_solve(handle.h, g, u)
-        ctx.handle = handle
         ctx.mesh = mesh
+        ctx.opts = o
+        if keep_hierarchy:
+            ctx.handle = handle
+        else:  # released now, recomputed in backward
+            nv.gamblet_destroy(handle.h)
+            handle.h = 0
+            ctx.handle = None
+            ctx.val = val
         ctx.save_for_backward(a, u)
         return u
 
@@ -70,12 +82,21 @@ class GambletSolve(torch.autograd.Function):
     def backward(ctx, grad_u):
         a, u = ctx.saved_tensors
         mesh = ctx.mesh
+        handle = ctx.handle
+        if handle is None:
+            o = ctx.opts
+            o.stream = torch.cuda.current_stream(grad_u.device).cuda_stream
+            handle = _Handle(nv.gamblet_setup(mesh.rowptr, mesh.colind, ctx.val, mesh.q,
+                                              mesh.cells, o))
         u_obs = (u - grad_u.contiguous()).contiguous()
         dlog_a = torch.empty_like(a)
-        nv.gamblet_grad(ctx.handle.h, mesh.cell_nodes, a, mesh.K_ref, u, u_obs, dlog_a)
-        return dlog_a, None, None, None
+        nv.gamblet_grad(handle.h, mesh.cell_nodes, a, mesh.K_ref, u, u_obs, dlog_a)
+        return dlog_a, None, None, None, None
 
 
-def gamblet_solve(log_a: torch.Tensor, g: torch.Tensor, mesh: Q1Mesh, opts=None) -> torch.Tensor:
-    """u(log a) for the mesh, differentiable with respect to log_a."""
-    return GambletSolve.apply(log_a, g, mesh, opts)
+def gamblet_solve(log_a: torch.Tensor, g: torch.Tensor, mesh: Q1Mesh, opts=None,
+                  keep_hierarchy: bool = True) -> torch.Tensor:
+    """u(log a) for the mesh, differentiable with respect to log_a.  With
+    keep_hierarchy=False the hierarchy is released after the forward solve
+    and recomputed in the backward pass."""
+    return GambletSolve.apply(log_a, g, mesh, opts, keep_hierarchy)

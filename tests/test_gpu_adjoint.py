@@ -106,3 +106,25 @@ def test_assemble_cells_matches_host_assembly():
     _, _, va = csr_arrays(p.A)
     assert np.abs(val.cpu().numpy() - va).max() <= 1e-13 * np.abs(va).max()
     assert np.allclose(a.cpu().numpy(), np.exp(p.log_a.ravel()), rtol=1e-15)
+
+
+def test_recomputed_hierarchy_gives_the_same_gradient():
+    """keep_hierarchy=False releases the hierarchy after the forward solve
+    and recomputes it in the backward pass: the gradient is the one of the
+    kept hierarchy (the setup is deterministic)."""
+    import torch
+    from paper_1503_03467_gb300.solver import gamblet_solve
+    n = 32
+    p = make_problem(n, 1e3, 2)
+    obs = make_problem(n, 1e3, 7)
+    u_obs = torch.tensor(direct.solve(obs.A, p.g)[0], device="cuda:0")
+    g = torch.tensor(p.g, device="cuda:0")
+    mesh = _mesh(p)
+    grads = []
+    for keep in (True, False):
+        log_a = torch.tensor(p.log_a.ravel(), dtype=torch.float64, device="cuda:0",
+                             requires_grad=True)
+        u = gamblet_solve(log_a, g, mesh, _opts(1), keep_hierarchy=keep)
+        (0.5 * ((u - u_obs) ** 2).sum()).backward()
+        grads.append(log_a.grad.cpu().numpy())
+    assert np.linalg.norm(grads[1] - grads[0]) <= 1e-12 * np.linalg.norm(grads[0])
