@@ -348,7 +348,7 @@ size_t patch_pcg_smem_bytes(const PatchPcgGeom& pg) {
   b += sizeof(T) * 3 * (size_t)pg.NB;                     // shared direction vector
   b += sizeof(int) * ((size_t)nadj + pg.NB + 1);          // adjacency (packed) + row pointers
   b += sizeof(int) * 2 * (size_t)pg.NB;                   // parent index, active unknowns
-  b += sizeof(double) * 2 * 32 + 16;                      // reductions
+  b += sizeof(double) * 24 + 16;                          // reduction slots
   return (b + 15) & ~(size_t)15;
 }
 template size_t patch_pcg_smem_bytes<float>(const PatchPcgGeom&);
@@ -378,24 +378,68 @@ __device__ __forceinline__ T warp_sum_t(T v) {
   return v;
 }
 
-// sum over the block of a and b (every thread gets both)
-template <typename T>
-__device__ __forceinline__ void block_sum2(T& a, T& b, T* red) {
-  a = warp_sum_t(a);
-  b = warp_sum_t(b);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (lane == 0) {
-    red[2 * warp] = a;
-    red[2 * warp + 1] = b;
+// Block sums for at most eight warps.  Each warp's lane 0 writes its partial
+// into a slot array that is zero past the warp count, and every thread then
+// reads the whole array as 16-byte broadcasts (two to eight loads instead of
+// one per warp and value).  Consecutive reductions alternate between two slot
+// arrays, so one barrier per reduction suffices: a thread writes a slot array
+// again only after the barrier of the reduction in between, which every
+// thread reaches after reading it.
+__device__ __forceinline__ float sum8(const float* r) {
+  const float4 u = *reinterpret_cast<const float4*>(r);
+  const float4 v = *reinterpret_cast<const float4*>(r + 4);
+  return ((u.x + u.y) + (u.z + u.w)) + ((v.x + v.y) + (v.z + v.w));
+}
+__device__ __forceinline__ double sum8(const double* r) {
+  double t = 0;
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const double2 u = reinterpret_cast<const double2*>(r)[w];
+    t += u.x + u.y;
   }
-  __syncthreads();
+  return t;
+}
+// slots (a_w, b_w) interleaved, 16 entries
+__device__ __forceinline__ void sum8x2(const float* r, float& a, float& b) {
   a = 0;
   b = 0;
-  for (int w = 0; w < nw; ++w) {
-    a += red[2 * w];
-    b += red[2 * w + 1];
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const float4 u = reinterpret_cast<const float4*>(r)[w];
+    a += u.x + u.z;
+    b += u.y + u.w;
+  }
+}
+__device__ __forceinline__ void sum8x2(const double* r, double& a, double& b) {
+  a = 0;
+  b = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    const double2 u = reinterpret_cast<const double2*>(r)[w];
+    a += u.x;
+    b += u.y;
+  }
+}
+
+// sum over the block of a (every thread gets it); red1: 8 slots
+template <typename T>
+__device__ __forceinline__ T block_sum1(T a, T* red1) {
+  a = warp_sum_t(a);
+  if ((threadIdx.x & 31) == 0) red1[threadIdx.x >> 5] = a;
+  __syncthreads();
+  return sum8(red1);
+}
+// sum over the block of a and b (every thread gets both); red2: 16 slots
+template <typename T>
+__device__ __forceinline__ void block_sum2(T& a, T& b, T* red2) {
+  a = warp_sum_t(a);
+  b = warp_sum_t(b);
+  if ((threadIdx.x & 31) == 0) {
+    red2[2 * (threadIdx.x >> 5)] = a;
+    red2[2 * (threadIdx.x >> 5) + 1] = b;
   }
   __syncthreads();
+  sum8x2(red2, a, b);
 }
 
 template <typename T, int kGather>
@@ -413,7 +457,10 @@ __global__ void __launch_bounds__(256, 3) k_patch_pcg(const T* __restrict__ Ahat
   int* pj = sptr + NB + 1;
   int* mj = pj + NB;
   T* red = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(mj + NB) + 15) & ~(uintptr_t)15);
+  T* red1 = red;       // 8 slots: p.q
+  T* red2 = red + 8;   // 16 slots: (r.z, r.r)
   const int tid = threadIdx.x;
+  if (tid < 24) red[tid] = T(0);  // slots of absent warps stay zero
   const int64_t np = g.npatch;
   const int S = g.spp;  // threads per neighbour parent (lanes of one warp)
   // patch structure, identical for every patch of the level
@@ -563,7 +610,7 @@ __global__ void __launch_bounds__(256, 3) k_patch_pcg(const T* __restrict__ Ahat
     for (int a = 0; a < 3; ++a) zv[a] = Di[3 * a] * rv[0] + Di[3 * a + 1] * rv[1] + Di[3 * a + 2] * rv[2];
     T rz = lead ? rv[0] * zv[0] + rv[1] * zv[1] + rv[2] * zv[2] : T(0);
     T rr0 = lead ? rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2] : T(0);
-    block_sum2<T>(rz, rr0, red);
+    block_sum2<T>(rz, rr0, red2);
 #pragma unroll
     for (int a = 0; a < 3; ++a) pv[a] = zv[a];
     int it = 0;
@@ -596,8 +643,7 @@ __global__ void __launch_bounds__(256, 3) k_patch_pcg(const T* __restrict__ Ahat
           q1 += __shfl_xor_sync(0xffffffffu, q1, o);
           q2 += __shfl_xor_sync(0xffffffffu, q2, o);
         }
-        T pq = lead ? pv[0] * q0 + pv[1] * q1 + pv[2] * q2 : T(0), unused = 0;
-        block_sum2<T>(pq, unused, red);
+        const T pq = block_sum1<T>(lead ? pv[0] * q0 + pv[1] * q1 + pv[2] * q2 : T(0), red1);
         const T alpha = pq > T(0) ? rz / pq : T(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a) xv[a] += alpha * pv[a];
@@ -609,7 +655,7 @@ __global__ void __launch_bounds__(256, 3) k_patch_pcg(const T* __restrict__ Ahat
           zv[a] = Di[3 * a] * rv[0] + Di[3 * a + 1] * rv[1] + Di[3 * a + 2] * rv[2];
         T rz_new = lead ? rv[0] * zv[0] + rv[1] * zv[1] + rv[2] * zv[2] : T(0);
         T rr = lead ? rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2] : T(0);
-        block_sum2<T>(rz_new, rr, red);
+        block_sum2<T>(rz_new, rr, red2);
         if ((double)rr <= tol2 * (double)rr0 || !(rz_new > T(0))) break;
         const T beta = rz_new / rz;
         rz = rz_new;
