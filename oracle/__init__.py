@@ -19,6 +19,8 @@ be checked against the paper by eye:
   without the level recursion (Sec. 4.2 Theorem thmgugyug0), tiny grids.
 * ``adjoint``   - gradient of J = 1/2 |u - u_obs|^2 with respect to the
   cell log-coefficients through a direct adjoint solve.
+* ``local_adjoint`` - gradient of J through the one-pass localized map
+  (reverse mode through Algorithm 2's solve and localized setup).
 * ``massinit``  - the level-q initialisation by the mass matrix
   (Algorithm 1 lines 1-5, Algorithm 2 lines 2a-5 with Definition
   deflocinvm).
