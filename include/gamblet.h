@@ -306,6 +306,40 @@ GAMBLET_API gamblet_status gamblet_grad(gamblet_handle h, int32_t ncell, const i
                             const double* u_obs, double* dJ, double* J, gamblet_info* info);
 
 /*
+ * Gradient of J = 1/2 |u_loc - u_obs|^2 through the ONE-PASS localized
+ * transform: u_loc = G_loc g is the output of Algorithm 2 (lines 15-18: the
+ * restriction with the localized R^(k-1,k), the level solves, the
+ * prolongation and sum) with the handle's patch and level solves and no
+ * outer refinement, and the derivative follows its dependence on the
+ * coefficient through the localized setup (lines 7-13: the patch solves of
+ * Definition defb, R^(k-1,k) and the Galerkin products).  The paper has no
+ * such derivative; this is reverse-mode differentiation of those steps:
+ *   dJ/dtheta_c = a_c sum_{p,r} sym(Abar^(q))_{cell_nodes[4c+p], cell_nodes[4c+r]} K_ref[4p+r],
+ * theta_c = log a_c, Abar^(q) the adjoint of A^(q) after the reverse pass.
+ * It is exact for the map that the handle computes when the patch and level
+ * solves are exact; with tolerances it carries their error (tight
+ * tolerances, e.g. patch_tol 1e-13 and level_tol 1e-13, give the derivative
+ * of Algorithm 2 with exact solves).
+ *   ncell, cell_nodes, cell_a, K_ref  as for gamblet_grad.
+ *   g, u_obs    n float64: right-hand side and observation.
+ *   u           NULL or n float64: receives u_loc.
+ *   dJ          ncell float64 output.
+ *   dJ_dg       NULL or n float64: receives dJ/dg = G_loc (u_loc - u_obs).
+ *   J           NULL or receives J.
+ * Host or device buffers.  Needs a localized float64 (precision 0) handle of
+ * one problem, set up with gamblet_setup and patch_tol >= 0; anything else
+ * returns UNSUPPORTED.  NOT_CONVERGED if a level solve hit its cap (all
+ * outputs still written).  Device work memory: about
+ * 8 (|S_k| + 4 |S_k + N|) n_(k-1) bytes at the finest level k = q (a few
+ * hundred MB at 256 x 256 cells, rho = 3), released before return.
+ */
+GAMBLET_API gamblet_status gamblet_grad_onepass(gamblet_handle h, int32_t ncell,
+                                                const int32_t* cell_nodes, const double* cell_a,
+                                                const double* K_ref, const double* g,
+                                                const double* u_obs, double* u, double* dJ,
+                                                double* dJ_dg, double* J, gamblet_info* info);
+
+/*
  * J = 1/2 |u - u_obs|^2, the objective that gamblet_grad also returns, for
  * callers that cannot allocate device memory when they need it: code inside
  * CUDA stream capture in global mode (cudaMalloc is not permitted there) and

@@ -393,6 +393,7 @@ struct gamblet_ctx {
   std::vector<double> patch_flops_iter_k;  // per level: flops of one iteration of one patch
   int level_iters_acc[32];
   bool level_not_conv = false;
+  const char* dplan = nullptr;  // device copy of the plan tables (localized setup)
 };
 
 namespace {
@@ -1062,6 +1063,7 @@ void setup_local(gamblet_ctx* h) {
   std::shared_ptr<const Plan> plan = cached_plan(q, h->opts.rho, h->opts.nbr_rule, Oq, h->N);
   h->plan = plan;
   const char* dplan = P.upload(plan->packed, s);  // every plan table in one copy
+  h->dplan = dplan;
   for (int k = q; k >= 2; --k) {
     LevelDev& L = h->lv[k];
     const PlanLevel& pl = plan->lv[k];
@@ -1818,6 +1820,277 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
     info->outer_iters = outer;
     for (int k = 0; k < 32; ++k) info->level_iters[k] = h->level_iters_acc[k];
     info->rel_residual = relres;
+    info->setup_ms = h->setup_ms;
+    info->solve_ms = ms;
+    info->patch_iters_max = h->patch_iters_max;
+    info->patch_iters_mean = h->patch_iters_mean;
+  }
+  return st;
+}
+
+// ------------------------------------------------- one-pass gradient (reverse)
+// Symbolic tables of the reverse pass at level k (all offsets in level-(k-1)
+// cell units unless stated):
+//  S   plain offsets of A^(k-1): 2 O_(k-1) + (c' - c) over the child slots
+//      (the 3 x 3 box when k - 1 = 1);
+//  TW  window S + N of T = X Rhat, with the pairs (d, j), S_d + N_j = TW_w;
+//  rg  [NB][noff_k] window index of N_j - O_o;
+//  yg  [noff_k][NB] (window index of N_j + O_o, index j' of N_j + O_o in N).
+struct RevLevel {
+  int nS = 0, nTW = 0;
+  const int2* S = nullptr;
+  const int* tw_ptr = nullptr;
+  const int2* tw_pairs = nullptr;
+  const int* rg = nullptr;
+  const int2* yg = nullptr;
+};
+
+// Box lookup (2 obox + 1)^2 -> index in a block-offset list, -1 elsewhere.
+std::vector<int> offset_box(const std::vector<int2>& off, int& obox) {
+  obox = 0;
+  for (const int2& o : off) obox = std::max(obox, std::max(std::abs(o.x), std::abs(o.y)));
+  const int side = 2 * obox + 1;
+  std::vector<int> box((size_t)side * side, -1);
+  for (size_t e = 0; e < off.size(); ++e)
+    box[(size_t)(off[e].y + obox) * side + (off[e].x + obox)] = (int)e;
+  return box;
+}
+
+RevLevel reverse_tables(gamblet_ctx* h, int k, Pool& tmp) {
+  cudaStream_t s = h->s;
+  RevLevel R;
+  OffSet S;
+  if (k - 1 == 1) {
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) S.add(dx, dy);
+  } else {
+    for (const int2& o : h->lv[k - 1].off_h)
+      for (int c = 0; c < 4; ++c)
+        for (int cp = 0; cp < 4; ++cp)
+          S.add(2 * o.x + (cp & 1) - (c & 1), 2 * o.y + (cp >> 1) - (c >> 1));
+  }
+  const OffSet& N = h->N;
+  OffSet TW;
+  for (const int2& d : S.v)
+    for (const int2& n : N.v) TW.add(d.x + n.x, d.y + n.y);
+  std::vector<std::vector<int2>> lists(TW.size());
+  for (int d = 0; d < S.size(); ++d)
+    for (int j = 0; j < N.size(); ++j)
+      lists[TW.find(S.v[d].x + N.v[j].x, S.v[d].y + N.v[j].y)].push_back(make_int2(d, j));
+  std::vector<int> ptr(1, 0);
+  std::vector<int2> pairs;
+  for (const auto& l : lists) {
+    pairs.insert(pairs.end(), l.begin(), l.end());
+    ptr.push_back((int)pairs.size());
+  }
+  const std::vector<int2>& Ok = h->lv[k].off_h;
+  const int NB = N.size(), no = (int)Ok.size();
+  std::vector<int> rg((size_t)NB * no);
+  std::vector<int2> yg((size_t)no * NB);
+  for (int j = 0; j < NB; ++j)
+    for (int o = 0; o < no; ++o) {
+      rg[(size_t)j * no + o] = TW.find(N.v[j].x - Ok[o].x, N.v[j].y - Ok[o].y);
+      const int wx = N.v[j].x + Ok[o].x, wy = N.v[j].y + Ok[o].y;
+      yg[(size_t)o * NB + j] = make_int2(TW.find(wx, wy), N.find(wx, wy));
+    }
+  R.nS = S.size();
+  R.nTW = TW.size();
+  int2* dS = nullptr;
+  int* dptr = nullptr;
+  int2* dpairs = nullptr;
+  int* drg = nullptr;
+  int2* dyg = nullptr;
+  to_device(tmp, dS, S.v.data(), (int64_t)S.v.size(), s);
+  to_device(tmp, dptr, ptr.data(), (int64_t)ptr.size(), s);
+  to_device(tmp, dpairs, pairs.data(), (int64_t)pairs.size(), s);
+  to_device(tmp, drg, rg.data(), (int64_t)rg.size(), s);
+  to_device(tmp, dyg, yg.data(), (int64_t)yg.size(), s);
+  R.S = dS;
+  R.tw_ptr = dptr;
+  R.tw_pairs = dpairs;
+  R.rg = drg;
+  R.yg = dyg;
+  return R;
+}
+
+// The patch-CG geometry of level k as the setup launched it.
+PatchPcgGeom patch_geometry(gamblet_ctx* h, int k) {
+  const PlanLevel& pl = h->plan->lv[k];
+  LevelDev& L = h->lv[k];
+  const char* dplan = h->dplan;
+  PatchPcgGeom gp{h->N.size(), h->jc, h->nbr, L.pair_idx, 1 << (k - 1), L.npar,
+                  (int)pl.half.size(), plan_table<int4>(dplan, pl, PlanLevel::kHalf),
+                  (int)pl.adj.size(), plan_table<int>(dplan, pl, PlanLevel::kAdjPtr),
+                  plan_table<int4>(dplan, pl, PlanLevel::kAdj),
+                  plan_table<int>(dplan, pl, PlanLevel::kDiagH), L.shape[0], 0, L.npar,
+                  L.shape[1]};
+  return gp;
+}
+
+// Gradient of J = 1/2 |u_loc - u_obs|^2 for the one-pass localized solution
+// u_loc = G_loc g (Algorithm 2 with the handle's patch and level solves).
+// Forward: the one-pass transform of g and of the misfit (G_loc is
+// symmetric, so the second pass is the adjoint of the solve chain and gives
+// dJ/dg); reverse: the setup levels from the coarsest to the finest.
+gamblet_status grad_onepass_impl(gamblet_ctx* h, int ncell, const int32_t* cell_nodes,
+                                 const double* cell_a, const double* K_ref, const double* g_user,
+                                 const double* uobs_user, double* u_user, double* dJ_user,
+                                 double* dJdg_user, double* J, gamblet_info* info) {
+  cudaStream_t s = h->s;
+  const int q = h->q;
+  const int NB = h->N.size();
+  LevelDev& Lq = h->lv[q];
+  const int64_t nq = Lq.ncell;
+  Pool tmp;
+  tmp.s = s;
+  flush_level_stats(h);
+  for (int k = 0; k < 32; ++k) h->level_iters_acc[k] = 0;
+  h->level_not_conv = false;
+  const int kmax_saved = h->kmax;
+  h->kmax = q;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, s));
+  double* g_dev = nullptr;
+  double* uo_dev = nullptr;
+  to_device(tmp, g_dev, g_user, h->n, s);
+  to_device(tmp, uo_dev, uobs_user, h->n, s);
+  // ---- forward: u_hat = G ghat, keeping the intermediates of every level
+  launch_gather_morton(g_dev, h->unknown_of, nq, h->g64, s);
+  launch_transform_vec<double>(h->g64, h->g64, Lq.npar, Lq.pmask, +1, s);
+  apply_G<double>(h, h->g64, h->z64, 0);
+  std::vector<double*> gh(q + 1, nullptr), wg(q + 1, nullptr), vg(q + 1, nullptr);
+  for (int k = 2; k <= q; ++k) {
+    LevelDev& L = h->lv[k];
+    gh[k] = tmp.alloc<double>(L.ncell);
+    wg[k] = tmp.alloc<double>(L.ncell);
+    CK(cudaMemcpyAsync(gh[k], L.ghat, sizeof(double) * L.ncell, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(wg[k], L.w, sizeof(double) * L.ncell, cudaMemcpyDeviceToDevice, s));
+    if (k < q) {
+      vg[k] = tmp.alloc<double>(L.ncell);
+      CK(cudaMemcpyAsync(vg[k], L.v, sizeof(double) * L.ncell, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  double* U1g = tmp.alloc<double>(4);
+  CK(cudaMemcpyAsync(U1g, h->U1, sizeof(double) * 4, cudaMemcpyDeviceToDevice, s));
+  // ---- misfit (transformed) and J
+  launch_gather_morton(uo_dev, h->unknown_of, nq, h->r64, s);
+  launch_transform_vec<double>(h->r64, h->r64, Lq.npar, Lq.pmask, +1, s);
+  CK(cudaMemcpyAsync(h->p64, h->z64, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
+  double* d = h->dots;
+  CK(cudaMemsetAsync(d, 0, sizeof(double) * 8, s));
+  const double one = 1.0;
+  CK(cudaMemcpyAsync(d + 7, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+  launch_axpy(nq, d + 7, d + 7, -1.0, h->r64, h->p64, s);
+  launch_dots(nq, h->p64, h->p64, nullptr, nullptr, nullptr, nullptr, d, s);
+  // ---- the misfit through the same chain: lambda^(k), dJ/dg
+  apply_G<double>(h, h->p64, h->q64, 0);
+  // ---- reverse of the setup
+  std::vector<double*> Y(q + 1, nullptr);
+  int64_t max_rows = 0;
+  for (int k = 2; k <= q; ++k) {
+    LevelDev& L = h->lv[k];
+    Y[k] = tmp.zeros<double>((int64_t)L.noff * L.npar * 16, s);
+    launch_ybar_level(Y[k], L.noff, L.off, 1 << (k - 1), L.npar, (const double*)L.w, wg[k], s);
+    max_rows = std::max(max_rows, L.npar);
+  }
+  double* A1bar = tmp.alloc<double>(16);
+  launch_abar1(A1bar, (const double*)h->U1, U1g, s);
+  double* Rbar = tmp.alloc<double>(max_rows * NB * 4);
+  double* M = tmp.alloc<double>(max_rows * NB * 4);
+  int* pstats = tmp.zeros<int>(4, s);
+  for (int k = 2; k <= q; ++k) {
+    LevelDev& L = h->lv[k];
+    const int Lpar = 1 << (k - 1);
+    RevLevel R = reverse_tables(h, k, tmp);
+    int obox = 0;
+    const int* oidx = nullptr;
+    if (k - 1 >= 2) {
+      std::vector<int> box = offset_box(h->lv[k - 1].off_h, obox);
+      int* db = nullptr;
+      to_device(tmp, db, box.data(), (int64_t)box.size(), s);
+      oidx = db;
+    }
+    double* X = tmp.alloc<double>((int64_t)R.nS * L.npar);
+    double* T = tmp.alloc<double>(L.npar * R.nTW * 4);
+    const double* vprev = k == 2 ? U1g : vg[k - 1];
+    const double* gbprev = (const double*)(k == 2 ? h->U1 : h->lv[k - 1].v);
+    int tok = h->prof.begin("grad_rbar_outer", 0.0, 0.0, s);
+    launch_rbar_outer(Rbar, h->nbr, NB, Lpar, L.npar, vprev, gbprev, (const double*)L.ghat, gh[k],
+                      s);
+    h->prof.end(tok, s);
+    tok = h->prof.begin("grad_xbar", 0.0, 0.0, s);
+    launch_xbar_cells(X, R.nS, R.S, Lpar, L.npar, k - 1 == 1 ? A1bar : nullptr,
+                      k - 1 >= 2 ? Y[k - 1] : nullptr, k - 1 >= 2 ? h->lv[k - 1].npar : 0, oidx,
+                      obox, k - 1 >= 2 ? h->lv[k - 1].pmask : nullptr, s);
+    h->prof.end(tok, s);
+    tok = h->prof.begin("grad_window_product", 0.0, 0.0, s);
+    launch_window_product(T, R.nTW, R.tw_ptr, R.tw_pairs, X, R.S, (const double*)L.Rhat, NB, Lpar,
+                          L.npar, s);
+    h->prof.end(tok, s);
+    tok = h->prof.begin("grad_rbar_galerkin", 0.0, 0.0, s);
+    launch_rbar_galerkin(Rbar, T, R.nTW, R.rg, (const double*)L.Ahat, L.noff, L.off, h->nbr, NB,
+                         Lpar, L.npar, s);
+    h->prof.end(tok, s);
+    tok = h->prof.begin("grad_patch_adjoint", 0.0, 0.0, s);
+    launch_patch_pcg_adjoint((const double*)L.Ahat, L.pmask, patch_geometry(h, k), Rbar, M,
+                             h->patch_tol, 200, pstats, h->num_sms, s);
+    h->prof.end(tok, s);
+    tok = h->prof.begin("grad_ybar_galerkin", 0.0, 0.0, s);
+    launch_ybar_galerkin(Y[k], L.noff, L.off, R.yg, T, R.nTW, (const double*)L.Rhat, M, h->nbr, NB,
+                         Lpar, L.npar, s);
+    h->prof.end(tok, s);
+    CK(cudaGetLastError());
+  }
+  // ---- dJ/dlog a from the finest level's adjoint
+  int oboxq = 0;
+  std::vector<int> boxq = offset_box(Lq.off_h, oboxq);
+  int* oidxq = nullptr;
+  to_device(tmp, oidxq, boxq.data(), (int64_t)boxq.size(), s);
+  int32_t* cn = nullptr;
+  double* ca = nullptr;
+  double* kr = nullptr;
+  to_device(tmp, cn, cell_nodes, 4 * (int64_t)ncell, s);
+  to_device(tmp, ca, cell_a, ncell, s);
+  to_device(tmp, kr, K_ref, 16, s);
+  const bool dev_dJ = is_device_ptr(dJ_user);
+  double* dJ = dev_dJ ? dJ_user : tmp.alloc<double>(ncell);
+  int tok = h->prof.begin("grad_cells", 0.0, 0.0, s);
+  launch_grad_cells(dJ, ncell, cn, ca, kr, h->morton_of, Y[q], Lq.npar, oidxq, oboxq, Lq.pmask, s);
+  h->prof.end(tok, s);
+  if (!dev_dJ) CK(cudaMemcpyAsync(dJ_user, dJ, sizeof(double) * ncell, cudaMemcpyDeviceToHost, s));
+  // ---- u_loc and dJ/dg back to unknown order
+  auto to_user = [&](double* hat, double* user) {
+    if (!user) return;
+    launch_transform_vec<double>(hat, hat, Lq.npar, Lq.pmask, -1, s);
+    double* o = is_device_ptr(user) ? user : tmp.alloc<double>(h->n);
+    launch_scatter_unknown(hat, h->morton_of, h->n, o, s);
+    if (o != user) CK(cudaMemcpyAsync(user, o, sizeof(double) * h->n, cudaMemcpyDeviceToHost, s));
+  };
+  to_user(h->z64, u_user);
+  to_user(h->q64, dJdg_user);
+  double jh = 0;
+  CK(cudaMemcpyAsync(&jh, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(e1, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->kmax = kmax_saved;
+  if (J) *J = 0.5 * jh;
+  flush_level_stats(h);
+  h->prof.resolve();
+  check_status(h, "one-pass gradient");
+  const gamblet_status st = h->level_not_conv ? GAMBLET_ERR_NOT_CONVERGED : GAMBLET_OK;
+  if (info) {
+    info->status = st;
+    info->q = q;
+    info->outer_iters = 0;
+    for (int k = 0; k < 32; ++k) info->level_iters[k] = h->level_iters_acc[k];
+    info->rel_residual = 0;
     info->setup_ms = h->setup_ms;
     info->solve_ms = ms;
     info->patch_iters_max = h->patch_iters_max;
@@ -2855,6 +3128,25 @@ gamblet_status gamblet_grad(gamblet_handle h, int32_t ncell, const int32_t* cell
       CK(cudaMemcpyAsync(dJ, out, sizeof(double) * ncell, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return st;
+  } catch (const GbError& e) {
+    if (info) info->status = e.st;
+    return set_error(e);
+  }
+}
+
+gamblet_status gamblet_grad_onepass(gamblet_handle h, int32_t ncell, const int32_t* cell_nodes,
+                                    const double* cell_a, const double* K_ref, const double* g,
+                                    const double* u_obs, double* u, double* dJ, double* dJ_dg,
+                                    double* J, gamblet_info* info) {
+  try {
+    if (!h || !cell_nodes || !cell_a || !K_ref || !g || !u_obs || !dJ)
+      fail(GAMBLET_ERR_INVALID_ARG, "NULL argument");
+    if (ncell < 1) fail(GAMBLET_ERR_INVALID_ARG, "ncell must be positive");
+    if (h->exact || h->mixed || h->mass || h->nprob != 1 || h->patch_tol < 0 || !h->plan)
+      fail(GAMBLET_ERR_UNSUPPORTED,
+           "the one-pass gradient needs a localized float64 setup of one problem with "
+           "A^(q) = A and iterative patch solves (patch_tol >= 0)");
+    return grad_onepass_impl(h, ncell, cell_nodes, cell_a, K_ref, g, u_obs, u, dJ, dJ_dg, J, info);
   } catch (const GbError& e) {
     if (info) info->status = e.st;
     return set_error(e);

@@ -442,11 +442,15 @@ __device__ __forceinline__ void block_sum2(T& a, T& b, T* red2) {
   sum8x2(red2, a, b);
 }
 
-template <typename T, int kGather>
+// kAdj: the same patch systems with the right-hand side b_i read from
+// adj_rhs ([i][NB][4], detail slots) and the solution written to Rhat's
+// layout with a zero average slot (the adjoint solves of the reverse pass).
+template <typename T, int kGather, bool kAdj>
 __global__ void __launch_bounds__(256, 3) k_patch_pcg(const T* __restrict__ Ahat,
                                                    const uint32_t* __restrict__ pmask,
                                                    PatchPcgGeom g, T* __restrict__ Rhat,
-                                                   double tol2, int max_iter, int* iter_stats) {
+                                                   double tol2, int max_iter, int* iter_stats,
+                                                   const T* __restrict__ adj_rhs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = g.NB;
   const int nadj = g.nadj;
@@ -565,7 +569,13 @@ __global__ void __launch_bounds__(256, 3) k_patch_pcg(const T* __restrict__ Ahat
     }
     // ---- right-hand side of neighbour j
     T rv[3] = {T(0), T(0), T(0)};
-    if (own && na > 0) {
+    if (kAdj) {
+      if (own && na > 0) {
+        const T* b = adj_rhs + i * 4 * NB + 4 * j;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) rv[t] = t < na ? b[t] : T(0);
+      }
+    } else if (own && na > 0) {
       const int o = g.pair_idx[j * NB + g.jc];
       if (o >= 0) {
         const T* bl = Ahat + ((int64_t)o * np + pjj) * 16;
@@ -672,7 +682,7 @@ __global__ void __launch_bounds__(256, 3) k_patch_pcg(const T* __restrict__ Ahat
       T* row = Rhat + i * 4 * NB + 4 * j;
 #pragma unroll
       for (int t = 0; t < 3; ++t) row[t] = t < na ? xv[t] : T(0);
-      row[3] = (j == g.jc) ? inv_sqrt_mi : T(0);
+      row[3] = (!kAdj && j == g.jc) ? inv_sqrt_mi : T(0);
     }
     __syncthreads();
   }
@@ -689,7 +699,8 @@ void launch_patch_pcg(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g, T*
   const int64_t nsolve = g.i_end - g.i_begin;
   if (nsolve <= 0) return;
   const size_t smem = patch_pcg_smem_bytes<T>(g);
-  auto kern = g.gather == 2 ? k_patch_pcg<T, 2> : (g.gather == 1 ? k_patch_pcg<T, 1> : k_patch_pcg<T, 0>);
+  auto kern = g.gather == 2 ? k_patch_pcg<T, 2, false>
+                            : (g.gather == 1 ? k_patch_pcg<T, 1, false> : k_patch_pcg<T, 0, false>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int threads = ((g.NB * g.spp + 31) / 32) * 32;
   int per_sm = 1;
@@ -700,8 +711,29 @@ void launch_patch_pcg(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g, T*
   {
     count_launch();
     kern<<<(unsigned)grid, threads, smem, s>>>(Ahat, pmask_k, g, Rhat, tol * tol, max_iter,
-                                               iter_stats);
+                                               iter_stats, nullptr);
   }
+}
+
+void launch_patch_pcg_adjoint(const double* Ahat, const uint32_t* pmask_k, PatchPcgGeom g,
+                              const double* rhs, double* out, double tol, int max_iter,
+                              int* iter_stats, int num_sms, cudaStream_t s) {
+  const int64_t nsolve = g.i_end - g.i_begin;
+  if (nsolve <= 0) return;
+  const size_t smem = patch_pcg_smem_bytes<double>(g);
+  auto kern = g.gather == 2 ? k_patch_pcg<double, 2, true>
+                            : (g.gather == 1 ? k_patch_pcg<double, 1, true>
+                                             : k_patch_pcg<double, 0, true>);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int threads = ((g.NB * g.spp + 31) / 32) * 32;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)num_sms * per_sm;
+  if (grid > nsolve) grid = nsolve;
+  count_launch();
+  kern<<<(unsigned)grid, threads, smem, s>>>(Ahat, pmask_k, g, out, tol * tol, max_iter,
+                                             iter_stats, rhs);
 }
 template void launch_patch_pcg<float>(const float*, const uint32_t*, PatchPcgGeom, float*, double,
                                       int, int*, int, cudaStream_t);

@@ -100,6 +100,11 @@ SIGNATURES = {
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Info)]),
+    "gamblet_grad_onepass": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(Info)]),
     "gamblet_assemble_cells": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -283,6 +288,22 @@ def gamblet_grad(h: int, cell_nodes, cell_a, K_ref, u, u_obs, dJ,
                            _ptr(cell_a, np.float64), _ptr(K_ref, np.float64),
                            _ptr(u, np.float64), _ptr(u_obs, np.float64), _ptr(dJ, np.float64),
                            ctypes.byref(J), ctypes.byref(info))
+    _check(st)
+    return J.value
+
+
+def gamblet_grad_onepass(h: int, cell_nodes, cell_a, K_ref, g, u_obs, dJ, u=None, dJ_dg=None,
+                         info: Info | None = None) -> float:
+    """Gradient of J = 1/2 |u_loc - u_obs|^2 through the one-pass localized
+    transform (setup included); returns J, writes dJ (and u_loc, dJ/dg)."""
+    info = info if info is not None else Info()
+    J = ctypes.c_double()
+    ncell = int(cell_a.shape[0])
+    st = _lib.gamblet_grad_onepass(ctypes.c_void_p(h), ncell, _ptr(cell_nodes, np.int32),
+                                   _ptr(cell_a, np.float64), _ptr(K_ref, np.float64),
+                                   _ptr(g, np.float64), _ptr(u_obs, np.float64),
+                                   _ptr(u, np.float64), _ptr(dJ, np.float64),
+                                   _ptr(dJ_dg, np.float64), ctypes.byref(J), ctypes.byref(info))
     _check(st)
     return J.value
 

@@ -1,0 +1,102 @@
+"""Gradient of J = 1/2 |u_loc - u_obs|^2 through the one-pass localized
+transform (gamblet_grad_onepass, float64, patch solves to 1e-13 and level
+solves to 1e-12) against the CPU oracle's reverse pass (oracle/local_adjoint.py), and at
+256 x 256 cells against central differences of the GPU's own one-pass map."""
+import numpy as np
+import pytest
+
+from oracle import direct, local_adjoint
+from workloads import assemble_q1, cell_corner_dofs, make_problem
+from workloads.rough import K_REF
+
+from gpu_util import csr_arrays
+
+pytestmark = pytest.mark.gpu
+
+
+def _opts(rho, precision=0):
+    from paper_1503_03467_gb300 import native as nv
+    o = nv.gamblet_default_opts()
+    o.precision = precision
+    o.rho = rho
+    o.patch_tol = 1e-13
+    o.level_tol = 1e-12
+    o.level_max_iter = 5000
+    return o
+
+
+def _gpu_grad(A, p, u_obs, rho, log_a=None):
+    from paper_1503_03467_gb300 import native as nv
+    log_a = p.log_a.ravel() if log_a is None else log_a
+    rp, ci, va = csr_arrays(A)
+    h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, _opts(rho))
+    try:
+        ncell = p.n * p.n
+        dJ = np.zeros(ncell)
+        u = np.zeros(p.ndof)
+        dg = np.zeros(p.ndof)
+        info = nv.Info()
+        J = nv.gamblet_grad_onepass(h, cell_corner_dofs(p.n), np.exp(log_a), K_REF.ravel().copy(),
+                                    p.g, u_obs, dJ, u=u, dJ_dg=dg, info=info)
+        assert info.status == 0
+    finally:
+        nv.gamblet_destroy(h)
+    return J, dJ, u, dg
+
+
+@pytest.mark.parametrize("n,rho", [(16, 1.0), (16, 2.0), (16, 3.0), (32, 3.0), (32, 1.5)])
+def test_onepass_gradient_matches_oracle(n, rho):
+    p = make_problem(n, 1e4, 0)
+    obs = make_problem(n, 1e4, 7)
+    u_obs, _ = direct.solve(obs.A, p.g)
+    J, dJ, u, dg = _gpu_grad(p.A, p, u_obs, rho)
+    r = local_adjoint.gradient_one_pass(p.A, p.g, u_obs, n, np.exp(p.log_a), K_REF, p.cells,
+                                        p.q, rho)
+    assert np.linalg.norm(u - r["u"]) <= 1e-10 * np.linalg.norm(r["u"])
+    assert abs(J - r["J"]) <= 1e-10 * r["J"]
+    assert np.linalg.norm(dg - r["dJ_dg"]) <= 1e-9 * np.linalg.norm(r["dJ_dg"])
+    assert np.abs(dJ - r["grad"]).max() <= 1e-8 * np.abs(r["grad"]).max()
+
+
+def test_onepass_gradient_of_uniform_coefficient_misfit_zero():
+    """u_obs = u_loc: J = 0 and every derivative vanishes."""
+    p = make_problem(16, 10.0, 2)
+    _, _, u, _ = _gpu_grad(p.A, p, np.zeros(p.ndof), 2.0)
+    J, dJ, _, dg = _gpu_grad(p.A, p, u, 2.0)
+    assert J <= 1e-26 * float(u @ u)
+    assert np.abs(dJ).max() <= 1e-12 and np.abs(dg).max() <= 1e-12
+
+
+def test_onepass_gradient_at_256_matches_central_differences():
+    """The derivative along a random direction of log a against central
+    differences of J through the GPU's one-pass map (3 setups of 65,025
+    unknowns, rho = 3)."""
+    n = 256
+    p = make_problem(n, 1e3, 0)
+    obs = make_problem(n, 1e3, 7)
+    u_obs = direct.solve(obs.A, p.g)[0]
+    J0, dJ, _, _ = _gpu_grad(p.A, p, u_obs, 3.0)
+    d = np.random.default_rng(5).standard_normal(n * n)
+    h = 1e-5
+    Js = []
+    for sgn in (1.0, -1.0):
+        la = p.log_a.ravel() + sgn * h * d
+        A = assemble_q1(np.exp(la).reshape(n, n))
+        Js.append(_gpu_grad(A, p, u_obs, 3.0, log_a=la)[0])
+    fd = (Js[0] - Js[1]) / (2 * h)
+    assert abs(fd - dJ @ d) <= 1e-6 * abs(fd)
+
+
+def test_onepass_gradient_needs_float64_handle():
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(16, 10.0, 0)
+    rp, ci, va = csr_arrays(p.A)
+    h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, _opts(2.0, precision=1))
+    try:
+        with pytest.raises(nv.GambletError) as e:
+            nv.gamblet_grad_onepass(h, cell_corner_dofs(16), np.exp(p.log_a.ravel()),
+                                    K_REF.ravel().copy(), p.g, np.zeros(p.ndof),
+                                    np.zeros(256))
+        assert e.value.status == nv.ERR_UNSUPPORTED
+    finally:
+        nv.gamblet_destroy(h)
