@@ -315,6 +315,85 @@ def adjoint_timing(nv, torch, dev, steps=3):
             "grad_over_forward_kept": bk / fk, "rel_err_vs_oracle_adjoint_kept": errk}
 
 
+def onepass_grad_timing(nv, torch, dev, steps=3):
+    """Gradient through the one-pass localized transform (gamblet_one_pass
+    autograd wrapper -> gamblet_grad_onepass) on the 256 x 256 problem of the
+    adjoint entry, float64 with patch and level solves to 1e-10: forward
+    (assembly + setup + one-pass solve) and backward (the misfit's pass and
+    the reverse pass over the setup), CUDA events; checked against central
+    differences of J through the same one-pass map along a random direction;
+    per-kernel times of one profiled reverse pass."""
+    from oracle import direct
+    from paper_1503_03467_gb300.solver import Q1Mesh, gamblet_one_pass
+    from workloads import assemble_q1, cell_corner_dofs, make_problem
+    from workloads.rough import K_REF
+    n = 256
+    p = make_problem(n, 1e3, 0)
+    obs = make_problem(n, 1e3, 7)
+    u_obs_np, _ = direct.solve(obs.A, p.g)
+    A = p.A.tocsr()
+    mesh = Q1Mesh(A.indptr, A.indices, p.cells, cell_corner_dofs(n), K_REF, p.q, dev)
+
+    def opts(profile=0):
+        o = nv.gamblet_default_opts()
+        o.precision = 0
+        o.patch_tol = 1e-10
+        o.level_tol = 1e-10
+        o.level_max_iter = 5000
+        o.profile = profile
+        return o
+
+    g = torch.tensor(p.g, device=dev)
+    u_obs = torch.tensor(u_obs_np, device=dev)
+    fwd, bwd = [], []
+    for it in range(steps + 1):
+        log_a = torch.tensor(p.log_a.ravel(), dtype=torch.float64, device=dev, requires_grad=True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record()
+        u = gamblet_one_pass(log_a, g, mesh, opts())
+        J = 0.5 * ((u - u_obs) ** 2).sum()
+        e1.record()
+        J.backward()
+        e2.record()
+        e2.synchronize()
+        if it > 0:
+            fwd.append(e0.elapsed_time(e1))
+            bwd.append(e1.elapsed_time(e2))
+    grad = log_a.grad.cpu().numpy()
+    # central differences of J(log a) through the same map
+    d = np.random.default_rng(5).standard_normal(n * n)
+    hstep = 1e-5
+    Js = []
+    for sgn in (1.0, -1.0):
+        la = torch.tensor(p.log_a.ravel() + sgn * hstep * d, dtype=torch.float64, device=dev)
+        with torch.no_grad():
+            us = gamblet_one_pass(la, g, mesh, opts())
+        Js.append(0.5 * float(((us - u_obs) ** 2).sum()))
+    fd = (Js[0] - Js[1]) / (2 * hstep)
+    # per-kernel times of one reverse pass
+    cn = torch.tensor(cell_corner_dofs(n), device=dev)
+    a_dev = torch.tensor(np.exp(p.log_a.ravel()), device=dev)
+    kr = torch.tensor(K_REF.ravel(), device=dev)
+    h = nv.gamblet_setup(A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data, p.q,
+                         p.cells, opts(1))
+    try:
+        nv.gamblet_reset_kernel_stats(h)
+        dJ = torch.empty(n * n, dtype=torch.float64, device=dev)
+        nv.gamblet_grad_onepass(h, cn, a_dev, kr, g, u_obs, dJ)
+        ks = {s_["name"]: round(s_["ms"], 4) for s_ in nv.gamblet_kernel_stats(h)
+              if s_["name"].startswith("grad_") or s_["name"] in ("level_cg", "restrict",
+                                                                   "prolong")}
+    finally:
+        nv.gamblet_destroy(h)
+    f, b = statistics.mean(fwd), statistics.mean(bwd)
+    return {"workload": "256x256 Q1, q=8, contrast 1e3, 65,536 cells, rho 3, float64, patch and "
+                        "level solves to 1e-10",
+            "forward_ms": f, "grad_ms": b, "grad_over_forward": b / f,
+            "fd_directional_rel_err": abs(fd - float(grad @ d)) / abs(fd),
+            "reverse_kernels_ms": ks}
+
+
 def rank_share(items, ws, rank):
     """The items of one rank: round-robin, so sizes mix evenly; every item
     belongs to exactly one rank."""
@@ -772,6 +851,7 @@ def main():
         line["speedup_mixed_vs_plain"] = line["plain_fp64"]["ms_per_step"] / ms
     if not a.no_adjoint:
         line["adjoint"] = adjoint_timing(nv, torch, dev)
+        line["adjoint_one_pass"] = onepass_grad_timing(nv, torch, dev)
     if not a.no_batched:
         line["batched"] = batched_timing(nv, torch, dev, a, stream, flush, ws, rank)
     if not a.no_localization:

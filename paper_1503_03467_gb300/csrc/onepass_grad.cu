@@ -12,7 +12,8 @@
 //    symmetrisation (only its symmetric part enters: A^(k) is symmetric).
 //  * X: the symmetric part of the adjoint of A^(k-1) in plain level-(k-1)
 //    coordinates, as a cell stencil X[d][i] = Xbar(i, i + S_d).
-//  * T = X Rhat (row i over the window i + TW_w, four children each).
+//  * T = X Rhat (row i over the window i + TW_w, four children each),
+//    stored [w][i][4].
 // With those, for k = 2..q (the reverse of Alg. 2 lines 13, 12, 11, 7):
 //   Rbar += 2 T Ahat_k (on the pattern of Rhat),  M_i = B_i^-1 Rbar_i (patch
 //   solves with the adjoint right-hand side), Y_k += Rhat^T (T - M) on the
@@ -23,12 +24,21 @@
 
 namespace gb {
 
+// The per-parent transforms of the 16 child masks, Qs[m * 16 + 4 a + c] =
+// Q_m[a][c], staged in shared memory by the first 256 threads of a block.
+__device__ void stage_q(double* Qs) {
+  for (int t = threadIdx.x; t < 256; t += blockDim.x)
+    Qs[t] = qv<double>(t >> 4, (t >> 2) & 3, t & 3);
+  __syncthreads();
+}
+
 // Plain entry (i, i') of a level operator whose transformed blocks are Y
 // ([o][P][4][4]; P = i >> 2, slot a = i & 3), zero off the block pattern:
 // sum_{alpha, beta} Q_P[alpha][a] Y[o][P][alpha][beta] Q_P'[beta][b].
 __device__ double plain_entry(const double* __restrict__ Y, int64_t npar,
                               const int* __restrict__ oidx, int obox,
-                              const uint32_t* __restrict__ pmask, int64_t i, int64_t ip) {
+                              const uint32_t* __restrict__ pmask, const double* Qs, int64_t i,
+                              int64_t ip) {
   const int64_t P = i >> 2, Pp = ip >> 2;
   const int a = (int)(i & 3), b = (int)(ip & 3);
   int x, y, xp, yp;
@@ -38,16 +48,17 @@ __device__ double plain_entry(const double* __restrict__ Y, int64_t npar,
   if (dx < -obox || dx > obox || dy < -obox || dy > obox) return 0.0;
   const int o = oidx[(dy + obox) * (2 * obox + 1) + (dx + obox)];
   if (o < 0) return 0.0;
-  const int m = (int)pmask[P] & 15, mp = (int)pmask[Pp] & 15;
+  const double* Qr = Qs + 16 * ((int)pmask[P] & 15);
+  const double* Qc = Qs + 16 * ((int)pmask[Pp] & 15);
   const double* B = Y + ((int64_t)o * npar + P) * 16;
   double s = 0.0;
 #pragma unroll
   for (int al = 0; al < 4; ++al) {
-    const double qa = qv<double>(m, al, a);
+    const double qa = Qr[4 * al + a];
     if (qa == 0.0) continue;
     double t = 0.0;
 #pragma unroll
-    for (int be = 0; be < 4; ++be) t += B[4 * al + be] * qv<double>(mp, be, b);
+    for (int be = 0; be < 4; ++be) t += B[4 * al + be] * Qc[4 * be + b];
     s += qa * t;
   }
   return s;
@@ -104,6 +115,8 @@ __global__ void k_xbar_cells(double* __restrict__ X, int nS, const int2* __restr
                              const double* __restrict__ Y, int64_t npar_prev,
                              const int* __restrict__ oidx, int obox,
                              const uint32_t* __restrict__ pmask_prev) {
+  __shared__ double Qs[256];
+  stage_q(Qs);
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)nS * ncell) return;
   const int d = (int)(t / ncell);
@@ -116,22 +129,24 @@ __global__ void k_xbar_cells(double* __restrict__ X, int nS, const int2* __restr
     if (A1bar) {
       v = 0.5 * (A1bar[4 * i + ip] + A1bar[4 * ip + i]);
     } else {
-      v = 0.5 * (plain_entry(Y, npar_prev, oidx, obox, pmask_prev, i, ip) +
-                 plain_entry(Y, npar_prev, oidx, obox, pmask_prev, ip, i));
+      v = 0.5 * (plain_entry(Y, npar_prev, oidx, obox, pmask_prev, Qs, i, ip) +
+                 plain_entry(Y, npar_prev, oidx, obox, pmask_prev, Qs, ip, i));
     }
   }
   X[t] = v;
 }
 
-// T[i][w][c] = sum over (d, j) with S_d + N_j = TW_w of X[d][i] Rhat[i + S_d][j][c].
+// T[w][i][c] = sum over (d, j) with S_d + N_j = TW_w of X[d][i] Rhat[i + S_d][j][c]
+// (window position outermost, so consecutive threads take consecutive rows:
+// the X reads and T writes coalesce).
 __global__ void k_window_product(double* __restrict__ T, int nTW, const int* __restrict__ tw_ptr,
                                  const int2* __restrict__ tw_pairs, const double* __restrict__ X,
                                  const int2* __restrict__ S, const double* __restrict__ Rhat,
                                  int NB, int L, int64_t nrow) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nrow * nTW) return;
-  const int64_t i = t / nTW;
-  const int w = (int)(t - i * nTW);
+  const int w = (int)(t / nrow);
+  const int64_t i = t - (int64_t)w * nrow;
   int x, y;
   demorton((uint32_t)i, x, y);
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -173,7 +188,7 @@ __global__ void k_rbar_galerkin(double* __restrict__ Rbar, const double* __restr
     const int Pp = shift_cell(px, py, -off[o].x, -off[o].y, L, nrow);
     if (Pp < 0) continue;
     const double* B = Ahat + ((int64_t)o * nrow + Pp) * 16;
-    const double* tv = T + ((int64_t)i * nTW + w) * 4;
+    const double* tv = T + ((int64_t)w * nrow + i) * 4;
 #pragma unroll
     for (int cp = 0; cp < 4; ++cp)
 #pragma unroll
@@ -209,7 +224,7 @@ __global__ void k_ybar_galerkin(double* __restrict__ Y, int noff, const int2* __
     const double* r = Rhat + ((int64_t)i * NB + j) * 4;
     double z[4] = {0.0, 0.0, 0.0, 0.0};
     if (wj.x >= 0) {
-      const double* tv = T + ((int64_t)i * nTW + wj.x) * 4;
+      const double* tv = T + ((int64_t)wj.x * npar + i) * 4;
 #pragma unroll
       for (int c = 0; c < 4; ++c) z[c] = tv[c];
     }
@@ -236,6 +251,8 @@ __global__ void k_grad_cells(double* __restrict__ out, int ncell,
                              const int32_t* __restrict__ morton_of, const double* __restrict__ Y,
                              int64_t npar, const int* __restrict__ oidx, int obox,
                              const uint32_t* __restrict__ pmask) {
+  __shared__ double Qs[256];
+  stage_q(Qs);
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
   int64_t m[4];
@@ -249,8 +266,8 @@ __global__ void k_grad_cells(double* __restrict__ out, int ncell,
     if (m[p] < 0) continue;
     for (int r = 0; r < 4; ++r) {
       if (m[r] < 0) continue;
-      const double xv = 0.5 * (plain_entry(Y, npar, oidx, obox, pmask, m[p], m[r]) +
-                               plain_entry(Y, npar, oidx, obox, pmask, m[r], m[p]));
+      const double xv = 0.5 * (plain_entry(Y, npar, oidx, obox, pmask, Qs, m[p], m[r]) +
+                               plain_entry(Y, npar, oidx, obox, pmask, Qs, m[r], m[p]));
       s += xv * Kref[4 * p + r];
     }
   }

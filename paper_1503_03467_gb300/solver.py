@@ -13,6 +13,10 @@ per-cell contraction dL/dlog a_c = -a_c lambda_c^T K_ref u_c runs in the
 library's adjoint kernel (gamblet_grad with u_obs = u - G, so that its
 right-hand side u - u_obs is G).  The paper has no adjoint; this is the
 discrete adjoint of the system of Sec. 5.1.
+
+gamblet_one_pass differentiates the one-pass localized map itself
+(Algorithm 2 without refinement) through its setup, with respect to log a
+and g.
 """
 from __future__ import annotations
 
@@ -92,6 +96,53 @@ class GambletSolve(torch.autograd.Function):
         dlog_a = torch.empty_like(a)
         nv.gamblet_grad(handle.h, mesh.cell_nodes, a, mesh.K_ref, u, u_obs, dlog_a)
         return dlog_a, None, None, None, None
+
+
+class GambletOnePass(torch.autograd.Function):
+    """u_loc(log a, g): the one-pass localized transform (Algorithm 2 with the
+    handle's patch and level solves, no outer refinement), differentiable
+    through the localized setup.  Backward: gamblet_grad_onepass with
+    u_obs = u_loc - G, so that its misfit is the upstream gradient G; it
+    returns dL/dlog a and dL/dg = G_loc G."""
+
+    @staticmethod
+    def forward(ctx, log_a, g, mesh: Q1Mesh, opts):
+        stream = torch.cuda.current_stream(log_a.device).cuda_stream
+        log_a = log_a.detach().contiguous()
+        val = torch.empty(mesh.colind.numel(), dtype=torch.float64, device=log_a.device)
+        a = torch.empty_like(log_a)
+        nv.gamblet_assemble_cells(mesh.rowptr, mesh.colind, mesh.cell_nodes, log_a, mesh.K_ref,
+                                  val, a, stream)
+        o = opts if opts is not None else nv.gamblet_default_opts()
+        o.stream = stream
+        o.refine_max_iter = 0  # the one-pass output
+        handle = _Handle(nv.gamblet_setup(mesh.rowptr, mesh.colind, val, mesh.q, mesh.cells, o))
+        g = g.detach().contiguous()
+        u = torch.empty_like(g)
+        nv.gamblet_solve(handle.h, g, u)
+        ctx.mesh = mesh
+        ctx.handle = handle
+        ctx.save_for_backward(a, g, u)
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        a, g, u = ctx.saved_tensors
+        mesh = ctx.mesh
+        u_obs = (u - grad_u.contiguous()).contiguous()
+        dlog_a = torch.empty_like(a)
+        dg = torch.empty_like(g)
+        nv.gamblet_grad_onepass(ctx.handle.h, mesh.cell_nodes, a, mesh.K_ref, g, u_obs, dlog_a,
+                                dJ_dg=dg)
+        return dlog_a, dg, None, None
+
+
+def gamblet_one_pass(log_a: torch.Tensor, g: torch.Tensor, mesh: Q1Mesh,
+                     opts=None) -> torch.Tensor:
+    """u_loc(log a, g) of the one-pass localized transform, differentiable
+    with respect to log_a and g (float64 handle: opts.precision = 0, and
+    patch_tol >= 0)."""
+    return GambletOnePass.apply(log_a, g, mesh, opts)
 
 
 def gamblet_solve(log_a: torch.Tensor, g: torch.Tensor, mesh: Q1Mesh, opts=None,

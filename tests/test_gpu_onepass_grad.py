@@ -100,3 +100,28 @@ def test_onepass_gradient_needs_float64_handle():
         assert e.value.status == nv.ERR_UNSUPPORTED
     finally:
         nv.gamblet_destroy(h)
+
+
+def test_autograd_one_pass_gradients_match_oracle():
+    """The autograd wrapper: dL/dlog a and dL/dg of L = 1/2 |u_loc - u_obs|^2."""
+    import torch
+    from paper_1503_03467_gb300.solver import Q1Mesh, gamblet_one_pass
+    n, rho = 32, 2.0
+    p = make_problem(n, 1e4, 1)
+    obs = make_problem(n, 1e4, 7)
+    u_obs_np, _ = direct.solve(obs.A, p.g)
+    dev = torch.device("cuda:0")
+    rp, ci, _ = csr_arrays(p.A)
+    mesh = Q1Mesh(rp, ci, p.cells, cell_corner_dofs(n), K_REF, p.q, dev)
+    log_a = torch.tensor(p.log_a.ravel(), dtype=torch.float64, device=dev, requires_grad=True)
+    g = torch.tensor(p.g, device=dev, requires_grad=True)
+    u = gamblet_one_pass(log_a, g, mesh, _opts(rho))
+    L = 0.5 * ((u - torch.tensor(u_obs_np, device=dev)) ** 2).sum()
+    L.backward()
+    r = local_adjoint.gradient_one_pass(p.A, p.g, u_obs_np, n, np.exp(p.log_a), K_REF, p.cells,
+                                        p.q, rho)
+    assert np.linalg.norm(u.detach().cpu().numpy() - r["u"]) <= 1e-10 * np.linalg.norm(r["u"])
+    ga = log_a.grad.cpu().numpy()
+    assert np.abs(ga - r["grad"]).max() <= 1e-8 * np.abs(r["grad"]).max()
+    gg = g.grad.cpu().numpy()
+    assert np.linalg.norm(gg - r["dJ_dg"]) <= 1e-9 * np.linalg.norm(r["dJ_dg"])
