@@ -69,11 +69,13 @@ def one_pass(A, g, cells, q, rho, rule="euclid", construction="const2"):
     return S, {"g": gk, "w": w, "U1": U1, "v": v, "u": v[q]}
 
 
-def cell_gradient(n, a, Abar_q, K_ref):
+def cell_gradient(n, a, Abar_q, K_ref, cell_nodes=None):
     """dJ/dlog a_c = a_c sum_{p,r} Abar_sym[p, r] K_ref[p, r] over the
-    interior corners of each cell (cells row-major, as log_a.ravel())."""
+    unknown corners of each cell (cells row-major, as log_a.ravel();
+    cell_nodes[c, p] = unknown of corner p or -1, default: every interior
+    node of the n x n grid)."""
     X = 0.5 * (Abar_q + Abar_q.T)
-    cd = cell_corner_dofs(n)
+    cd = cell_corner_dofs(n) if cell_nodes is None else np.asarray(cell_nodes)
     av = np.asarray(a, dtype=np.float64).ravel()
     out = np.zeros(n * n)
     for c in range(n * n):
@@ -90,7 +92,7 @@ def cell_gradient(n, a, Abar_q, K_ref):
 
 
 def gradient_one_pass(A, g, u_obs, n, a, K_ref, cells, q, rho, rule="euclid",
-                      construction="const2"):
+                      construction="const2", cell_nodes=None):
     """Returns dict with J, grad (dJ/dlog a per cell), u (the one-pass
     solution), dJ_dg, and the per-level adjoints Abar (dense) and Rbar."""
     S, f = one_pass(A, g, cells, q, rho, rule, construction)
@@ -148,6 +150,6 @@ def gradient_one_pass(A, g, u_obs, n, a, K_ref, cells, q, rho, rule="euclid",
             Bbar[np.ix_(chi, chi)] -= np.outer(mu, y)
         Abar[k] += Wk.T @ Bbar @ Wk - Wk.T @ rhsbar @ pibar
 
-    grad = cell_gradient(n, a, Abar[q], K_ref)
+    grad = cell_gradient(n, a, Abar[q], K_ref, cell_nodes)
     return {"J": J, "grad": grad, "u": f["u"], "dJ_dg": gbar[q],
             "Abar": Abar, "Rbar": Rbar, "setup": S}

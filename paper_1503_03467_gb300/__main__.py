@@ -6,6 +6,7 @@ timing and profiling runs:
                                    [--repeat 1] [--profile] [--capture-last]
                                    [--no-autotune] [--galerkin-variant -1|0|1|2]
                                    [--patch-gather -1|0|1|2]
+                                   [--grad-one-pass]
 
 Prints, for the last of `repeat` setup + solve passes, the setup and solve
 device times, the outer iterations and the final relative residual
@@ -13,7 +14,10 @@ reported by the library; --profile adds the per-kernel CUDA-event times
 (gamblet_kernel_stats).  --capture-last brackets the last pass with
 cudaProfilerStart/Stop, so a profiler started with profiling off
 (ncu --profile-from-start off) sees only that pass: the earlier passes
-fill the process-wide plan and autotuning caches.
+fill the process-wide plan and autotuning caches.  --grad-one-pass replaces
+the solve by the gradient through the one-pass transform
+(gamblet_grad_onepass, float64 only; J = 1/2 |u_loc - u_obs|^2 with u_obs
+the problem of seed + 7 solved by the same handle's one-pass transform).
 """
 import argparse
 import json
@@ -38,6 +42,7 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--galerkin-variant", type=int, default=-1)
     ap.add_argument("--patch-gather", type=int, default=-1)
+    ap.add_argument("--grad-one-pass", action="store_true")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from workloads import make_problem
@@ -71,7 +76,16 @@ def main(argv=None):
         try:
             u = np.zeros(p.ndof)
             info = nv.Info()
-            nv.gamblet_solve(h, p.g, u, None, info)
+            if a.grad_one_pass:
+                from workloads import cell_corner_dofs
+                from workloads.rough import K_REF
+                u_obs = np.zeros(p.ndof)
+                nv.gamblet_solve(h, make_problem(a.size, a.contrast, a.seed + 7).g, u_obs)
+                dJ = np.zeros(a.size * a.size)
+                nv.gamblet_grad_onepass(h, cell_corner_dofs(a.size), np.exp(p.log_a.ravel()),
+                                        K_REF.ravel().copy(), p.g, u_obs, dJ, u=u, info=info)
+            else:
+                nv.gamblet_solve(h, p.g, u, None, info)
             if last:
                 if a.capture_last:
                     torch.cuda.profiler.stop()

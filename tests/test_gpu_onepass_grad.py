@@ -14,30 +14,34 @@ from gpu_util import csr_arrays
 pytestmark = pytest.mark.gpu
 
 
-def _opts(rho, precision=0):
+def _opts(rho, precision=0, rule=0):
     from paper_1503_03467_gb300 import native as nv
     o = nv.gamblet_default_opts()
     o.precision = precision
     o.rho = rho
+    o.nbr_rule = rule
     o.patch_tol = 1e-13
     o.level_tol = 1e-12
     o.level_max_iter = 5000
     return o
 
 
-def _gpu_grad(A, p, u_obs, rho, log_a=None):
+def _gpu_grad(A, p, u_obs, rho, log_a=None, g=None, cells=None, cell_nodes=None, rule=0):
     from paper_1503_03467_gb300 import native as nv
     log_a = p.log_a.ravel() if log_a is None else log_a
+    g = p.g if g is None else g
+    cells = p.cells if cells is None else cells
+    cell_nodes = cell_corner_dofs(p.n) if cell_nodes is None else cell_nodes
     rp, ci, va = csr_arrays(A)
-    h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, _opts(rho))
+    h = nv.gamblet_setup(rp, ci, va, p.q, cells, _opts(rho, rule=rule))
     try:
         ncell = p.n * p.n
         dJ = np.zeros(ncell)
-        u = np.zeros(p.ndof)
-        dg = np.zeros(p.ndof)
+        u = np.zeros(A.shape[0])
+        dg = np.zeros(A.shape[0])
         info = nv.Info()
-        J = nv.gamblet_grad_onepass(h, cell_corner_dofs(p.n), np.exp(log_a), K_REF.ravel().copy(),
-                                    p.g, u_obs, dJ, u=u, dJ_dg=dg, info=info)
+        J = nv.gamblet_grad_onepass(h, cell_nodes, np.exp(log_a), K_REF.ravel().copy(),
+                                    g, u_obs, dJ, u=u, dJ_dg=dg, info=info)
         assert info.status == 0
     finally:
         nv.gamblet_destroy(h)
@@ -56,6 +60,47 @@ def test_onepass_gradient_matches_oracle(n, rho):
     assert abs(J - r["J"]) <= 1e-10 * r["J"]
     assert np.linalg.norm(dg - r["dJ_dg"]) <= 1e-9 * np.linalg.norm(r["dJ_dg"])
     assert np.abs(dJ - r["grad"]).max() <= 1e-8 * np.abs(r["grad"]).max()
+
+
+def _close(J, dJ, u, dg, r):
+    assert np.linalg.norm(u - r["u"]) <= 1e-10 * np.linalg.norm(r["u"])
+    assert abs(J - r["J"]) <= 1e-10 * r["J"]
+    assert np.linalg.norm(dg - r["dJ_dg"]) <= 1e-9 * np.linalg.norm(r["dJ_dg"])
+    assert np.abs(dJ - r["grad"]).max() <= 1e-8 * np.abs(r["grad"]).max()
+
+
+def test_onepass_gradient_on_domains_with_holes():
+    """Removed nodes (Dirichlet there) leave parents with one to three
+    children and cells with none: the child masks of every reverse kernel."""
+    n = 32
+    p = make_problem(n, 1e3, 8)
+    x, y = p.cells[:, 0], p.cells[:, 1]
+    masks = [~((x >= 10) & (x <= 17) & (y >= 12) & (y <= 14)) & ~((x == 3) & (y == 29)),
+             ~((x >= 16) & (y >= 16)) & ~((x >= 9) & (x <= 11) & (y <= 4))]
+    for keep in masks:
+        idx = np.nonzero(keep)[0]
+        new = -np.ones(p.ndof, dtype=np.int64)
+        new[idx] = np.arange(len(idx))
+        cd = cell_corner_dofs(n)
+        cn = np.ascontiguousarray(np.where(cd >= 0, new[np.maximum(cd, 0)], -1), dtype=np.int32)
+        A = p.A[idx][:, idx]
+        g = np.ascontiguousarray(p.g[idx])
+        cells = np.ascontiguousarray(p.cells[idx])
+        u_obs = np.random.default_rng(11).standard_normal(len(idx))
+        J, dJ, u, dg = _gpu_grad(A, p, u_obs, 3.0, g=g, cells=cells, cell_nodes=cn)
+        r = local_adjoint.gradient_one_pass(A, g, u_obs, n, np.exp(p.log_a), K_REF, cells, p.q,
+                                            3.0, cell_nodes=cn)
+        _close(J, dJ, u, dg, r)
+
+
+def test_onepass_gradient_chebyshev_patches():
+    n = 16
+    p = make_problem(n, 1e4, 4)
+    u_obs = np.random.default_rng(12).standard_normal(p.ndof)
+    J, dJ, u, dg = _gpu_grad(p.A, p, u_obs, 2.0, rule=1)
+    r = local_adjoint.gradient_one_pass(p.A, p.g, u_obs, n, np.exp(p.log_a), K_REF, p.cells,
+                                        p.q, 2.0, rule="cheb")
+    _close(J, dJ, u, dg, r)
 
 
 def test_onepass_gradient_of_uniform_coefficient_misfit_zero():

@@ -13,7 +13,7 @@ import pytest
 import oracle.local_adjoint as la
 from oracle import adjoint, direct
 from oracle.local import gamblet_local_setup, gamblet_local_solve
-from workloads import assemble_q1, make_problem
+from workloads import assemble_q1, cell_corner_dofs, make_problem
 from workloads.rough import K_REF
 
 N, CONTRAST, RHO = 16, 1e4, 1.0
@@ -80,6 +80,41 @@ def test_rhs_gradient_is_the_one_pass_solve_of_the_misfit():
     r = la.gradient_one_pass(p.A, p.g, u_obs, N, np.exp(p.log_a), K_REF, p.cells, p.q, RHO)
     ref = gamblet_local_solve(r["setup"], r["u"] - u_obs)["u"]
     assert np.abs(r["dJ_dg"] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def _holed(p):
+    """Nodes of a rectangle and a single node removed (Dirichlet there): some
+    parents have fewer than four children and some cells none."""
+    x, y = p.cells[:, 0], p.cells[:, 1]
+    keep = ~((x >= 5) & (x <= 8) & (y >= 6) & (y <= 7)) & ~((x == 2) & (y == 13))
+    idx = np.nonzero(keep)[0]
+    new = -np.ones(p.ndof, dtype=np.int64)
+    new[idx] = np.arange(len(idx))
+    cd = cell_corner_dofs(N)
+    cn = np.where(cd >= 0, new[np.maximum(cd, 0)], -1)
+    return idx, cn
+
+
+def test_one_pass_gradient_on_a_domain_with_holes():
+    p, _ = _case()
+    idx, cn = _holed(p)
+    u_obs = np.random.default_rng(11).standard_normal(len(idx))
+    g = p.g[idx]
+
+    def J(log_a):
+        A = assemble_q1(np.exp(log_a).reshape(N, N))[idx][:, idx]
+        S = gamblet_local_setup(A, p.cells[idx], p.q, 2.0)
+        u = gamblet_local_solve(S, g)["u"]
+        return 0.5 * float((u - u_obs) @ (u - u_obs))
+
+    A = p.A[idx][:, idx]
+    r = la.gradient_one_pass(A, g, u_obs, N, np.exp(p.log_a), K_REF, p.cells[idx], p.q, 2.0,
+                             cell_nodes=cn)
+    d = np.random.default_rng(3).standard_normal(N * N)
+    h = 1e-5
+    la0 = p.log_a.ravel()
+    fd = (J(la0 + h * d) - J(la0 - h * d)) / (2 * h)
+    assert abs(fd - r["grad"] @ d) <= 1e-8 * abs(fd)
 
 
 MUTATIONS = {
