@@ -334,33 +334,39 @@ def onepass_grad_timing(nv, torch, dev, steps=3):
     A = p.A.tocsr()
     mesh = Q1Mesh(A.indptr, A.indices, p.cells, cell_corner_dofs(n), K_REF, p.q, dev)
 
-    def opts(profile=0):
+    def opts(profile=0, precision=0):
         o = nv.gamblet_default_opts()
-        o.precision = 0
-        o.patch_tol = 1e-10
-        o.level_tol = 1e-10
+        o.precision = precision
+        o.patch_tol = 1e-10 if precision == 0 else 1e-6
+        o.level_tol = 1e-10 if precision == 0 else 1e-6
         o.level_max_iter = 5000
         o.profile = profile
         return o
 
     g = torch.tensor(p.g, device=dev)
     u_obs = torch.tensor(u_obs_np, device=dev)
-    fwd, bwd = [], []
-    for it in range(steps + 1):
-        log_a = torch.tensor(p.log_a.ravel(), dtype=torch.float64, device=dev, requires_grad=True)
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        torch.cuda.synchronize()
-        e0.record()
-        u = gamblet_one_pass(log_a, g, mesh, opts())
-        J = 0.5 * ((u - u_obs) ** 2).sum()
-        e1.record()
-        J.backward()
-        e2.record()
-        e2.synchronize()
-        if it > 0:
-            fwd.append(e0.elapsed_time(e1))
-            bwd.append(e1.elapsed_time(e2))
-    grad = log_a.grad.cpu().numpy()
+
+    def run(precision):
+        fwd, bwd = [], []
+        for it in range(steps + 1):
+            log_a = torch.tensor(p.log_a.ravel(), dtype=torch.float64, device=dev,
+                                 requires_grad=True)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            torch.cuda.synchronize()
+            e0.record()
+            u = gamblet_one_pass(log_a, g, mesh, opts(precision=precision))
+            J = 0.5 * ((u - u_obs) ** 2).sum()
+            e1.record()
+            J.backward()
+            e2.record()
+            e2.synchronize()
+            if it > 0:
+                fwd.append(e0.elapsed_time(e1))
+                bwd.append(e1.elapsed_time(e2))
+        return statistics.mean(fwd), statistics.mean(bwd), log_a.grad.cpu().numpy()
+
+    f, b, grad = run(0)
+    fm, bm, gradm = run(nv.MIXED)
     # central differences of J(log a) through the same map
     d = np.random.default_rng(5).standard_normal(n * n)
     hstep = 1e-5
@@ -386,12 +392,16 @@ def onepass_grad_timing(nv, torch, dev, steps=3):
                                                                    "prolong")}
     finally:
         nv.gamblet_destroy(h)
-    f, b = statistics.mean(fwd), statistics.mean(bwd)
     return {"workload": "256x256 Q1, q=8, contrast 1e3, 65,536 cells, rho 3, float64, patch and "
                         "level solves to 1e-10",
             "forward_ms": f, "grad_ms": b, "grad_over_forward": b / f,
             "fd_directional_rel_err": abs(fd - float(grad @ d)) / abs(fd),
-            "reverse_kernels_ms": ks}
+            "reverse_kernels_ms": ks,
+            "mixed": {"precision": "float32 hierarchy and reverse pass, patch and level solves "
+                                   "to 1e-6",
+                      "forward_ms": fm, "grad_ms": bm, "grad_over_forward": bm / fm,
+                      "rel_diff_vs_float64_grad": float(np.linalg.norm(gradm - grad)
+                                                        / np.linalg.norm(grad))}}
 
 
 def rank_share(items, ws, rank):

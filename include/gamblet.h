@@ -326,12 +326,17 @@ GAMBLET_API gamblet_status gamblet_grad(gamblet_handle h, int32_t ncell, const i
  *   dJ          ncell float64 output.
  *   dJ_dg       NULL or n float64: receives dJ/dg = G_loc (u_loc - u_obs).
  *   J           NULL or receives J.
- * Host or device buffers.  Needs a localized float64 (precision 0) handle of
- * one problem, set up with gamblet_setup and patch_tol >= 0; anything else
- * returns UNSUPPORTED.  NOT_CONVERGED if a level solve hit its cap (all
+ * Host or device buffers.  Needs a localized handle of one problem, set up
+ * with gamblet_setup and patch_tol >= 0; anything else returns UNSUPPORTED.
+ * The reverse pass runs in the handle's working precision: float64 for
+ * precision 0; float32 on the mixed path's float32 hierarchy (J, the misfit
+ * and the outputs in float64), which gives the derivative of the float32
+ * one-pass map to float32 accuracy (about 1e-4 relative with patch and level
+ * tolerances of 1e-6).  NOT_CONVERGED if a level solve hit its cap (all
  * outputs still written).  Device work memory: about
- * 8 (|S_k| + 4 |S_k + N|) n_(k-1) bytes at the finest level k = q (a few
- * hundred MB at 256 x 256 cells, rho = 3), released before return.
+ * e (|S_k| + 4 |S_k + N|) n_(k-1) bytes at the finest level k = q, e the
+ * element size (a few hundred MB at 256 x 256 cells, rho = 3, float64),
+ * released before return.
  */
 GAMBLET_API gamblet_status gamblet_grad_onepass(gamblet_handle h, int32_t ncell,
                                                 const int32_t* cell_nodes, const double* cell_a,

@@ -6,7 +6,7 @@ timing and profiling runs:
                                    [--repeat 1] [--profile] [--capture-last]
                                    [--no-autotune] [--galerkin-variant -1|0|1|2]
                                    [--patch-gather -1|0|1|2]
-                                   [--grad-one-pass]
+                                   [--grad-one-pass] [--patch-tol 0]
 
 Prints, for the last of `repeat` setup + solve passes, the setup and solve
 device times, the outer iterations and the final relative residual
@@ -16,7 +16,7 @@ cudaProfilerStart/Stop, so a profiler started with profiling off
 (ncu --profile-from-start off) sees only that pass: the earlier passes
 fill the process-wide plan and autotuning caches.  --grad-one-pass replaces
 the solve by the gradient through the one-pass transform
-(gamblet_grad_onepass, float64 only; J = 1/2 |u_loc - u_obs|^2 with u_obs
+(gamblet_grad_onepass; J = 1/2 |u_loc - u_obs|^2 with u_obs
 the problem of seed + 7 solved by the same handle's one-pass transform).
 """
 import argparse
@@ -36,6 +36,7 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--level-tol", type=float, default=0.1)
     ap.add_argument("--refine-tol", type=float, default=1e-10)
+    ap.add_argument("--patch-tol", type=float, default=0.0)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--profile", action="store_true")
     ap.add_argument("--capture-last", action="store_true")
@@ -58,6 +59,7 @@ def main(argv=None):
     o.level_tol = a.level_tol
     o.refine_tol = a.refine_tol
     o.refine_max_iter = 100
+    o.patch_tol = a.patch_tol
     o.profile = 1 if a.profile else 0
     o.autotune = 0 if a.no_autotune else 1
     o.galerkin_variant = a.galerkin_variant

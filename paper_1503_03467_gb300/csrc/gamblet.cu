@@ -1931,7 +1931,10 @@ PatchPcgGeom patch_geometry(gamblet_ctx* h, int k) {
 // u_loc = G_loc g (Algorithm 2 with the handle's patch and level solves).
 // Forward: the one-pass transform of g and of the misfit (G_loc is
 // symmetric, so the second pass is the adjoint of the solve chain and gives
-// dJ/dg); reverse: the setup levels from the coarsest to the finest.
+// dJ/dg); reverse: the setup levels from the coarsest to the finest.  T is the
+// working precision of the hierarchy (float on the mixed path); J, the
+// misfit and the outputs are float64.
+template <typename T>
 gamblet_status grad_onepass_impl(gamblet_ctx* h, int ncell, const int32_t* cell_nodes,
                                  const double* cell_a, const double* K_ref, const double* g_user,
                                  const double* uobs_user, double* u_user, double* dJ_user,
@@ -1959,21 +1962,24 @@ gamblet_status grad_onepass_impl(gamblet_ctx* h, int ncell, const int32_t* cell_
   // ---- forward: u_hat = G ghat, keeping the intermediates of every level
   launch_gather_morton(g_dev, h->unknown_of, nq, h->g64, s);
   launch_transform_vec<double>(h->g64, h->g64, Lq.npar, Lq.pmask, +1, s);
-  apply_G<double>(h, h->g64, h->z64, 0);
-  std::vector<double*> gh(q + 1, nullptr), wg(q + 1, nullptr), vg(q + 1, nullptr);
+  T* gT = as_T<T>(h, h->g64, h->rT, nq, true);
+  T* zT = as_T<T>(h, h->z64, h->zT, nq, false);
+  apply_G<T>(h, gT, zT, 0);
+  if (is_f32<T>()) launch_convert_f32_f64((const float*)zT, h->z64, nq, s);
+  std::vector<T*> gh(q + 1, nullptr), wg(q + 1, nullptr), vg(q + 1, nullptr);
   for (int k = 2; k <= q; ++k) {
     LevelDev& L = h->lv[k];
-    gh[k] = tmp.alloc<double>(L.ncell);
-    wg[k] = tmp.alloc<double>(L.ncell);
-    CK(cudaMemcpyAsync(gh[k], L.ghat, sizeof(double) * L.ncell, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(wg[k], L.w, sizeof(double) * L.ncell, cudaMemcpyDeviceToDevice, s));
+    gh[k] = tmp.alloc<T>(L.ncell);
+    wg[k] = tmp.alloc<T>(L.ncell);
+    CK(cudaMemcpyAsync(gh[k], L.ghat, sizeof(T) * L.ncell, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(wg[k], L.w, sizeof(T) * L.ncell, cudaMemcpyDeviceToDevice, s));
     if (k < q) {
-      vg[k] = tmp.alloc<double>(L.ncell);
-      CK(cudaMemcpyAsync(vg[k], L.v, sizeof(double) * L.ncell, cudaMemcpyDeviceToDevice, s));
+      vg[k] = tmp.alloc<T>(L.ncell);
+      CK(cudaMemcpyAsync(vg[k], L.v, sizeof(T) * L.ncell, cudaMemcpyDeviceToDevice, s));
     }
   }
-  double* U1g = tmp.alloc<double>(4);
-  CK(cudaMemcpyAsync(U1g, h->U1, sizeof(double) * 4, cudaMemcpyDeviceToDevice, s));
+  T* U1g = tmp.alloc<T>(4);
+  CK(cudaMemcpyAsync(U1g, h->U1, sizeof(T) * 4, cudaMemcpyDeviceToDevice, s));
   // ---- misfit (transformed) and J
   launch_gather_morton(uo_dev, h->unknown_of, nq, h->r64, s);
   launch_transform_vec<double>(h->r64, h->r64, Lq.npar, Lq.pmask, +1, s);
@@ -1985,20 +1991,23 @@ gamblet_status grad_onepass_impl(gamblet_ctx* h, int ncell, const int32_t* cell_
   launch_axpy(nq, d + 7, d + 7, -1.0, h->r64, h->p64, s);
   launch_dots(nq, h->p64, h->p64, nullptr, nullptr, nullptr, nullptr, d, s);
   // ---- the misfit through the same chain: lambda^(k), dJ/dg
-  apply_G<double>(h, h->p64, h->q64, 0);
+  T* mT = as_T<T>(h, h->p64, h->rT, nq, true);
+  T* dgT = is_f32<T>() ? (T*)h->zT : (T*)h->q64;
+  apply_G<T>(h, mT, dgT, 0);
+  if (is_f32<T>()) launch_convert_f32_f64((const float*)dgT, h->q64, nq, s);
   // ---- reverse of the setup
-  std::vector<double*> Y(q + 1, nullptr);
+  std::vector<T*> Y(q + 1, nullptr);
   int64_t max_rows = 0;
   for (int k = 2; k <= q; ++k) {
     LevelDev& L = h->lv[k];
-    Y[k] = tmp.zeros<double>((int64_t)L.noff * L.npar * 16, s);
-    launch_ybar_level(Y[k], L.noff, L.off, 1 << (k - 1), L.npar, (const double*)L.w, wg[k], s);
+    Y[k] = tmp.zeros<T>((int64_t)L.noff * L.npar * 16, s);
+    launch_ybar_level<T>(Y[k], L.noff, L.off, 1 << (k - 1), L.npar, (const T*)L.w, wg[k], s);
     max_rows = std::max(max_rows, L.npar);
   }
-  double* A1bar = tmp.alloc<double>(16);
-  launch_abar1(A1bar, (const double*)h->U1, U1g, s);
-  double* Rbar = tmp.alloc<double>(max_rows * NB * 4);
-  double* M = tmp.alloc<double>(max_rows * NB * 4);
+  T* A1bar = tmp.alloc<T>(16);
+  launch_abar1<T>(A1bar, (const T*)h->U1, U1g, s);
+  T* Rbar = tmp.alloc<T>(max_rows * NB * 4);
+  T* M = tmp.alloc<T>(max_rows * NB * 4);
   int* pstats = tmp.zeros<int>(4, s);
   for (int k = 2; k <= q; ++k) {
     LevelDev& L = h->lv[k];
@@ -2012,34 +2021,34 @@ gamblet_status grad_onepass_impl(gamblet_ctx* h, int ncell, const int32_t* cell_
       to_device(tmp, db, box.data(), (int64_t)box.size(), s);
       oidx = db;
     }
-    double* X = tmp.alloc<double>((int64_t)R.nS * L.npar);
-    double* T = tmp.alloc<double>(L.npar * R.nTW * 4);
-    const double* vprev = k == 2 ? U1g : vg[k - 1];
-    const double* gbprev = (const double*)(k == 2 ? h->U1 : h->lv[k - 1].v);
+    T* X = tmp.alloc<T>((int64_t)R.nS * L.npar);
+    T* Tw = tmp.alloc<T>(L.npar * R.nTW * 4);
+    const T* vprev = k == 2 ? U1g : vg[k - 1];
+    const T* gbprev = (const T*)(k == 2 ? h->U1 : h->lv[k - 1].v);
     int tok = h->prof.begin("grad_rbar_outer", 0.0, 0.0, s);
-    launch_rbar_outer(Rbar, h->nbr, NB, Lpar, L.npar, vprev, gbprev, (const double*)L.ghat, gh[k],
-                      s);
+    launch_rbar_outer<T>(Rbar, h->nbr, NB, Lpar, L.npar, vprev, gbprev, (const T*)L.ghat, gh[k],
+                         s);
     h->prof.end(tok, s);
     tok = h->prof.begin("grad_xbar", 0.0, 0.0, s);
-    launch_xbar_cells(X, R.nS, R.S, Lpar, L.npar, k - 1 == 1 ? A1bar : nullptr,
+    launch_xbar_cells<T>(X, R.nS, R.S, Lpar, L.npar, k - 1 == 1 ? A1bar : nullptr,
                       k - 1 >= 2 ? Y[k - 1] : nullptr, k - 1 >= 2 ? h->lv[k - 1].npar : 0, oidx,
                       obox, k - 1 >= 2 ? h->lv[k - 1].pmask : nullptr, s);
     h->prof.end(tok, s);
     tok = h->prof.begin("grad_window_product", 0.0, 0.0, s);
-    launch_window_product(T, R.nTW, R.tw_ptr, R.tw_pairs, X, R.S, (const double*)L.Rhat, NB, Lpar,
-                          L.npar, s);
+    launch_window_product<T>(Tw, R.nTW, R.tw_ptr, R.tw_pairs, X, R.S, (const T*)L.Rhat, NB, Lpar,
+                             L.npar, s);
     h->prof.end(tok, s);
     tok = h->prof.begin("grad_rbar_galerkin", 0.0, 0.0, s);
-    launch_rbar_galerkin(Rbar, T, R.nTW, R.rg, (const double*)L.Ahat, L.noff, L.off, h->nbr, NB,
-                         Lpar, L.npar, s);
+    launch_rbar_galerkin<T>(Rbar, Tw, R.nTW, R.rg, (const T*)L.Ahat, L.noff, L.off, h->nbr, NB,
+                            Lpar, L.npar, s);
     h->prof.end(tok, s);
     tok = h->prof.begin("grad_patch_adjoint", 0.0, 0.0, s);
-    launch_patch_pcg_adjoint((const double*)L.Ahat, L.pmask, patch_geometry(h, k), Rbar, M,
-                             h->patch_tol, 200, pstats, h->num_sms, s);
+    launch_patch_pcg_adjoint<T>((const T*)L.Ahat, L.pmask, patch_geometry(h, k), Rbar, M,
+                                h->patch_tol, 200, pstats, h->num_sms, s);
     h->prof.end(tok, s);
     tok = h->prof.begin("grad_ybar_galerkin", 0.0, 0.0, s);
-    launch_ybar_galerkin(Y[k], L.noff, L.off, R.yg, T, R.nTW, (const double*)L.Rhat, M, h->nbr, NB,
-                         Lpar, L.npar, s);
+    launch_ybar_galerkin<T>(Y[k], L.noff, L.off, R.yg, Tw, R.nTW, (const T*)L.Rhat, M, h->nbr, NB,
+                            Lpar, L.npar, s);
     h->prof.end(tok, s);
     CK(cudaGetLastError());
   }
@@ -2057,7 +2066,8 @@ gamblet_status grad_onepass_impl(gamblet_ctx* h, int ncell, const int32_t* cell_
   const bool dev_dJ = is_device_ptr(dJ_user);
   double* dJ = dev_dJ ? dJ_user : tmp.alloc<double>(ncell);
   int tok = h->prof.begin("grad_cells", 0.0, 0.0, s);
-  launch_grad_cells(dJ, ncell, cn, ca, kr, h->morton_of, Y[q], Lq.npar, oidxq, oboxq, Lq.pmask, s);
+  launch_grad_cells<T>(dJ, ncell, cn, ca, kr, h->morton_of, Y[q], Lq.npar, oidxq, oboxq, Lq.pmask,
+                       s);
   h->prof.end(tok, s);
   if (!dev_dJ) CK(cudaMemcpyAsync(dJ_user, dJ, sizeof(double) * ncell, cudaMemcpyDeviceToHost, s));
   // ---- u_loc and dJ/dg back to unknown order
@@ -3142,11 +3152,15 @@ gamblet_status gamblet_grad_onepass(gamblet_handle h, int32_t ncell, const int32
     if (!h || !cell_nodes || !cell_a || !K_ref || !g || !u_obs || !dJ)
       fail(GAMBLET_ERR_INVALID_ARG, "NULL argument");
     if (ncell < 1) fail(GAMBLET_ERR_INVALID_ARG, "ncell must be positive");
-    if (h->exact || h->mixed || h->mass || h->nprob != 1 || h->patch_tol < 0 || !h->plan)
+    if (h->exact || h->mass || h->nprob != 1 || h->patch_tol < 0 || !h->plan)
       fail(GAMBLET_ERR_UNSUPPORTED,
-           "the one-pass gradient needs a localized float64 setup of one problem with "
-           "A^(q) = A and iterative patch solves (patch_tol >= 0)");
-    return grad_onepass_impl(h, ncell, cell_nodes, cell_a, K_ref, g, u_obs, u, dJ, dJ_dg, J, info);
+           "the one-pass gradient needs a localized setup of one problem with A^(q) = A and "
+           "iterative patch solves (patch_tol >= 0)");
+    if (h->mixed)
+      return grad_onepass_impl<float>(h, ncell, cell_nodes, cell_a, K_ref, g, u_obs, u, dJ, dJ_dg,
+                                      J, info);
+    return grad_onepass_impl<double>(h, ncell, cell_nodes, cell_a, K_ref, g, u_obs, u, dJ, dJ_dg,
+                                     J, info);
   } catch (const GbError& e) {
     if (info) info->status = e.st;
     return set_error(e);

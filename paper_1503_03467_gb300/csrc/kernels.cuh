@@ -197,9 +197,10 @@ size_t patch_pcg_smem_bytes(const PatchPcgGeom& g);
 // The same patch systems with right-hand sides rhs ([i][NB][4], detail
 // slots; the adjoint solves of the reverse pass), solutions written to out
 // in Rhat's layout with a zero average slot.
-void launch_patch_pcg_adjoint(const double* Ahat, const uint32_t* pmask_k, PatchPcgGeom g,
-                              const double* rhs, double* out, double tol, int max_iter,
-                              int* iter_stats, int num_sms, cudaStream_t s);
+template <typename T>
+void launch_patch_pcg_adjoint(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g,
+                              const T* rhs, T* out, double tol, int max_iter, int* iter_stats,
+                              int num_sms, cudaStream_t s);
 
 // ---------------------------------------------------------------- Galerkin
 struct GalerkinGeom {
@@ -400,30 +401,37 @@ void launch_cgm_iteration(const CgLevel* lv, int nlev, int spmv_blocks, int tota
 size_t cgm_spmv_smem_bytes(int max_ts, size_t elem, int nrhs);
 
 // ---------------------------------------------------------------- one-pass gradient
-// Reverse pass through the localized setup and one-pass solve (float64;
-// onepass_grad.cu).  Y arrays: adjoints of the transformed level operators
-// ([o][P][16]); oidx: box lookup (2 obox + 1)^2 of block offsets -> index.
-void launch_rbar_outer(double* Rbar, const int2* nbr, int NB, int L, int64_t nrow, const double* v,
-                       const double* gbar, const double* ubar, const double* ghat,
-                       cudaStream_t s);
-void launch_ybar_level(double* Y, int noff, const int2* off, int L, int64_t npar,
-                       const double* lam, const double* w, cudaStream_t s);
-void launch_abar1(double* A1bar, const double* lam1, const double* U1, cudaStream_t s);
-void launch_xbar_cells(double* X, int nS, const int2* S, int L, int64_t ncell,
-                       const double* A1bar, const double* Y, int64_t npar_prev, const int* oidx,
-                       int obox, const uint32_t* pmask_prev, cudaStream_t s);
-void launch_window_product(double* T, int nTW, const int* tw_ptr, const int2* tw_pairs,
-                           const double* X, const int2* S, const double* Rhat, int NB, int L,
-                           int64_t nrow, cudaStream_t s);
-void launch_rbar_galerkin(double* Rbar, const double* T, int nTW, const int* rg,
-                          const double* Ahat, int noff, const int2* off, const int2* nbr, int NB,
-                          int L, int64_t nrow, cudaStream_t s);
-void launch_ybar_galerkin(double* Y, int noff, const int2* off, const int2* yg, const double* T,
-                          int nTW, const double* Rhat, const double* M, const int2* nbr, int NB,
-                          int L, int64_t npar, cudaStream_t s);
+// Reverse pass through the localized setup and one-pass solve (onepass_grad.cu;
+// E = float or double, the working precision of the hierarchy).  Y arrays:
+// adjoints of the transformed level operators ([o][P][16]); oidx: box lookup
+// (2 obox + 1)^2 of block offsets -> index.
+template <typename E>
+void launch_rbar_outer(E* Rbar, const int2* nbr, int NB, int L, int64_t nrow, const E* v,
+                       const E* gbar, const E* ubar, const E* ghat, cudaStream_t s);
+template <typename E>
+void launch_ybar_level(E* Y, int noff, const int2* off, int L, int64_t npar, const E* lam,
+                       const E* w, cudaStream_t s);
+template <typename E>
+void launch_abar1(E* A1bar, const E* lam1, const E* U1, cudaStream_t s);
+template <typename E>
+void launch_xbar_cells(E* X, int nS, const int2* S, int L, int64_t ncell, const E* A1bar,
+                       const E* Y, int64_t npar_prev, const int* oidx, int obox,
+                       const uint32_t* pmask_prev, cudaStream_t s);
+template <typename E>
+void launch_window_product(E* T, int nTW, const int* tw_ptr, const int2* tw_pairs, const E* X,
+                           const int2* S, const E* Rhat, int NB, int L, int64_t nrow,
+                           cudaStream_t s);
+template <typename E>
+void launch_rbar_galerkin(E* Rbar, const E* T, int nTW, const int* rg, const E* Ahat, int noff,
+                          const int2* off, const int2* nbr, int NB, int L, int64_t nrow,
+                          cudaStream_t s);
+template <typename E>
+void launch_ybar_galerkin(E* Y, int noff, const int2* off, const int2* yg, const E* T, int nTW,
+                          const E* Rhat, const E* M, const int2* nbr, int NB, int L, int64_t npar,
+                          cudaStream_t s);
+template <typename E>
 void launch_grad_cells(double* out, int ncell, const int32_t* cell_nodes, const double* cell_a,
-                       const double* Kref, const int32_t* morton_of, const double* Y,
-                       int64_t npar, const int* oidx, int obox, const uint32_t* pmask,
-                       cudaStream_t s);
+                       const double* Kref, const int32_t* morton_of, const E* Y, int64_t npar,
+                       const int* oidx, int obox, const uint32_t* pmask, cudaStream_t s);
 
 }  // namespace gb

@@ -715,15 +715,15 @@ void launch_patch_pcg(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g, T*
   }
 }
 
-void launch_patch_pcg_adjoint(const double* Ahat, const uint32_t* pmask_k, PatchPcgGeom g,
-                              const double* rhs, double* out, double tol, int max_iter,
-                              int* iter_stats, int num_sms, cudaStream_t s) {
+template <typename T>
+void launch_patch_pcg_adjoint(const T* Ahat, const uint32_t* pmask_k, PatchPcgGeom g,
+                              const T* rhs, T* out, double tol, int max_iter, int* iter_stats,
+                              int num_sms, cudaStream_t s) {
   const int64_t nsolve = g.i_end - g.i_begin;
   if (nsolve <= 0) return;
-  const size_t smem = patch_pcg_smem_bytes<double>(g);
-  auto kern = g.gather == 2 ? k_patch_pcg<double, 2, true>
-                            : (g.gather == 1 ? k_patch_pcg<double, 1, true>
-                                             : k_patch_pcg<double, 0, true>);
+  const size_t smem = patch_pcg_smem_bytes<T>(g);
+  auto kern = g.gather == 2 ? k_patch_pcg<T, 2, true>
+                            : (g.gather == 1 ? k_patch_pcg<T, 1, true> : k_patch_pcg<T, 0, true>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int threads = ((g.NB * g.spp + 31) / 32) * 32;
   int per_sm = 1;
@@ -735,6 +735,12 @@ void launch_patch_pcg_adjoint(const double* Ahat, const uint32_t* pmask_k, Patch
   kern<<<(unsigned)grid, threads, smem, s>>>(Ahat, pmask_k, g, out, tol * tol, max_iter,
                                              iter_stats, rhs);
 }
+template void launch_patch_pcg_adjoint<float>(const float*, const uint32_t*, PatchPcgGeom,
+                                              const float*, float*, double, int, int*, int,
+                                              cudaStream_t);
+template void launch_patch_pcg_adjoint<double>(const double*, const uint32_t*, PatchPcgGeom,
+                                               const double*, double*, double, int, int*, int,
+                                               cudaStream_t);
 template void launch_patch_pcg<float>(const float*, const uint32_t*, PatchPcgGeom, float*, double,
                                       int, int*, int, cudaStream_t);
 template void launch_patch_pcg<double>(const double*, const uint32_t*, PatchPcgGeom, double*,

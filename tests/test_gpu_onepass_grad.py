@@ -132,11 +132,42 @@ def test_onepass_gradient_at_256_matches_central_differences():
     assert abs(fd - dJ @ d) <= 1e-6 * abs(fd)
 
 
-def test_onepass_gradient_needs_float64_handle():
+def test_onepass_gradient_mixed_precision():
+    """The mixed path's float32 hierarchy: the reverse pass in float32 (patch
+    and level solves to 1e-6) against the oracle's float64 gradient."""
+    from paper_1503_03467_gb300 import native as nv
+    n = 32
+    p = make_problem(n, 1e4, 0)
+    obs = make_problem(n, 1e4, 7)
+    u_obs, _ = direct.solve(obs.A, p.g)
+    rp, ci, va = csr_arrays(p.A)
+    o = _opts(3.0, precision=nv.MIXED)
+    o.patch_tol = 1e-6
+    o.level_tol = 1e-6
+    h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
+    try:
+        dJ = np.zeros(n * n)
+        u = np.zeros(p.ndof)
+        dg = np.zeros(p.ndof)
+        J = nv.gamblet_grad_onepass(h, cell_corner_dofs(n), np.exp(p.log_a.ravel()),
+                                    K_REF.ravel().copy(), p.g, u_obs, dJ, u=u, dJ_dg=dg)
+    finally:
+        nv.gamblet_destroy(h)
+    r = local_adjoint.gradient_one_pass(p.A, p.g, u_obs, n, np.exp(p.log_a), K_REF, p.cells,
+                                        p.q, 3.0)
+    assert np.linalg.norm(u - r["u"]) <= 1e-4 * np.linalg.norm(r["u"])
+    assert abs(J - r["J"]) <= 1e-4 * r["J"]
+    assert np.linalg.norm(dg - r["dJ_dg"]) <= 1e-4 * np.linalg.norm(r["dJ_dg"])
+    assert np.linalg.norm(dJ - r["grad"]) <= 1e-3 * np.linalg.norm(r["grad"])
+
+
+def test_onepass_gradient_needs_iterative_patch_solves():
     from paper_1503_03467_gb300 import native as nv
     p = make_problem(16, 10.0, 0)
     rp, ci, va = csr_arrays(p.A)
-    h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, _opts(2.0, precision=1))
+    o = _opts(2.0)
+    o.patch_tol = -1.0  # dense Cholesky patch solves
+    h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
     try:
         with pytest.raises(nv.GambletError) as e:
             nv.gamblet_grad_onepass(h, cell_corner_dofs(16), np.exp(p.log_a.ravel()),
