@@ -64,7 +64,7 @@ class GambletSolve(torch.autograd.Function):
         a = torch.empty_like(log_a)
         nv.gamblet_assemble_cells(mesh.rowptr, mesh.colind, mesh.cell_nodes, log_a, mesh.K_ref,
                                   val, a, stream)
-        o = opts if opts is not None else nv.gamblet_default_opts()
+        o = nv.Opts.from_buffer_copy(opts) if opts is not None else nv.gamblet_default_opts()
         o.stream = stream
         handle = _Handle(nv.gamblet_setup(mesh.rowptr, mesh.colind, val, mesh.q, mesh.cells, o))
         g = g.detach().contiguous()
@@ -113,7 +113,8 @@ class GambletOnePass(torch.autograd.Function):
         a = torch.empty_like(log_a)
         nv.gamblet_assemble_cells(mesh.rowptr, mesh.colind, mesh.cell_nodes, log_a, mesh.K_ref,
                                   val, a, stream)
-        o = opts if opts is not None else nv.gamblet_default_opts()
+        # a copy: the caller's options keep their refinement settings
+        o = nv.Opts.from_buffer_copy(opts) if opts is not None else nv.gamblet_default_opts()
         o.stream = stream
         o.refine_max_iter = 0  # the one-pass output
         handle = _Handle(nv.gamblet_setup(mesh.rowptr, mesh.colind, val, mesh.q, mesh.cells, o))

@@ -48,7 +48,8 @@ def _gpu_grad(A, p, u_obs, rho, log_a=None, g=None, cells=None, cell_nodes=None,
     return J, dJ, u, dg
 
 
-@pytest.mark.parametrize("n,rho", [(16, 1.0), (16, 2.0), (16, 3.0), (32, 3.0), (32, 1.5)])
+@pytest.mark.parametrize("n,rho", [(4, 1.0), (8, 2.0), (16, 1.0), (16, 2.0), (16, 3.0),
+                                   (32, 3.0), (32, 1.5)])
 def test_onepass_gradient_matches_oracle(n, rho):
     p = make_problem(n, 1e4, 0)
     obs = make_problem(n, 1e4, 7)
@@ -191,7 +192,9 @@ def test_autograd_one_pass_gradients_match_oracle():
     mesh = Q1Mesh(rp, ci, p.cells, cell_corner_dofs(n), K_REF, p.q, dev)
     log_a = torch.tensor(p.log_a.ravel(), dtype=torch.float64, device=dev, requires_grad=True)
     g = torch.tensor(p.g, device=dev, requires_grad=True)
-    u = gamblet_one_pass(log_a, g, mesh, _opts(rho))
+    o = _opts(rho)
+    u = gamblet_one_pass(log_a, g, mesh, o)
+    assert o.refine_max_iter == _opts(rho).refine_max_iter  # the caller's options are untouched
     L = 0.5 * ((u - torch.tensor(u_obs_np, device=dev)) ** 2).sum()
     L.backward()
     r = local_adjoint.gradient_one_pass(p.A, p.g, u_obs_np, n, np.exp(p.log_a), K_REF, p.cells,
