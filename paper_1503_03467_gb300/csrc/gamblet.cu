@@ -1856,61 +1856,89 @@ std::vector<int> offset_box(const std::vector<int2>& off, int& obox) {
   return box;
 }
 
-RevLevel reverse_tables(gamblet_ctx* h, int k, Pool& tmp) {
-  cudaStream_t s = h->s;
-  RevLevel R;
-  OffSet S;
-  if (k - 1 == 1) {
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) S.add(dx, dy);
-  } else {
-    for (const int2& o : h->lv[k - 1].off_h)
-      for (int c = 0; c < 4; ++c)
-        for (int cp = 0; cp < 4; ++cp)
-          S.add(2 * o.x + (cp & 1) - (c & 1), 2 * o.y + (cp >> 1) - (c >> 1));
+// Every level's reverse tables and the block-offset boxes, packed into one
+// buffer (16-byte aligned pieces) and cached process-wide per plan: they
+// depend only on the geometry, and one upload per call replaces a
+// synchronising copy per table.
+struct RevPack {
+  std::vector<char> bytes;
+  struct Level {
+    int nS = 0, nTW = 0, obox = 0;
+    size_t S = 0, tw_ptr = 0, tw_pairs = 0, rg = 0, yg = 0, oidx = 0;
+  };
+  std::vector<Level> lv;  // index k; lv[1] holds only the box of O_1 (unused)
+  int oboxq = 0;
+  size_t oidxq = 0;
+};
+
+template <typename V>
+size_t pack_append(std::vector<char>& buf, const std::vector<V>& v) {
+  size_t off = (buf.size() + 15) & ~(size_t)15;
+  buf.resize(off + sizeof(V) * v.size());
+  if (!v.empty()) std::memcpy(buf.data() + off, v.data(), sizeof(V) * v.size());
+  return off;
+}
+
+std::shared_ptr<const RevPack> reverse_pack(gamblet_ctx* h) {
+  static std::mutex mu;
+  static std::map<std::string, std::shared_ptr<const RevPack>> cache;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(h->plan->key);
+    if (it != cache.end()) return it->second;
   }
+  auto P = std::make_shared<RevPack>();
+  const int q = h->q;
   const OffSet& N = h->N;
-  OffSet TW;
-  for (const int2& d : S.v)
-    for (const int2& n : N.v) TW.add(d.x + n.x, d.y + n.y);
-  std::vector<std::vector<int2>> lists(TW.size());
-  for (int d = 0; d < S.size(); ++d)
-    for (int j = 0; j < N.size(); ++j)
-      lists[TW.find(S.v[d].x + N.v[j].x, S.v[d].y + N.v[j].y)].push_back(make_int2(d, j));
-  std::vector<int> ptr(1, 0);
-  std::vector<int2> pairs;
-  for (const auto& l : lists) {
-    pairs.insert(pairs.end(), l.begin(), l.end());
-    ptr.push_back((int)pairs.size());
-  }
-  const std::vector<int2>& Ok = h->lv[k].off_h;
-  const int NB = N.size(), no = (int)Ok.size();
-  std::vector<int> rg((size_t)NB * no);
-  std::vector<int2> yg((size_t)no * NB);
-  for (int j = 0; j < NB; ++j)
-    for (int o = 0; o < no; ++o) {
-      rg[(size_t)j * no + o] = TW.find(N.v[j].x - Ok[o].x, N.v[j].y - Ok[o].y);
-      const int wx = N.v[j].x + Ok[o].x, wy = N.v[j].y + Ok[o].y;
-      yg[(size_t)o * NB + j] = make_int2(TW.find(wx, wy), N.find(wx, wy));
+  P->lv.resize(q + 1);
+  for (int k = 2; k <= q; ++k) {
+    RevPack::Level& R = P->lv[k];
+    OffSet S;
+    if (k - 1 == 1) {
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) S.add(dx, dy);
+    } else {
+      for (const int2& o : h->lv[k - 1].off_h)
+        for (int c = 0; c < 4; ++c)
+          for (int cp = 0; cp < 4; ++cp)
+            S.add(2 * o.x + (cp & 1) - (c & 1), 2 * o.y + (cp >> 1) - (c >> 1));
     }
-  R.nS = S.size();
-  R.nTW = TW.size();
-  int2* dS = nullptr;
-  int* dptr = nullptr;
-  int2* dpairs = nullptr;
-  int* drg = nullptr;
-  int2* dyg = nullptr;
-  to_device(tmp, dS, S.v.data(), (int64_t)S.v.size(), s);
-  to_device(tmp, dptr, ptr.data(), (int64_t)ptr.size(), s);
-  to_device(tmp, dpairs, pairs.data(), (int64_t)pairs.size(), s);
-  to_device(tmp, drg, rg.data(), (int64_t)rg.size(), s);
-  to_device(tmp, dyg, yg.data(), (int64_t)yg.size(), s);
-  R.S = dS;
-  R.tw_ptr = dptr;
-  R.tw_pairs = dpairs;
-  R.rg = drg;
-  R.yg = dyg;
-  return R;
+    OffSet TW;
+    for (const int2& d : S.v)
+      for (const int2& n : N.v) TW.add(d.x + n.x, d.y + n.y);
+    std::vector<std::vector<int2>> lists(TW.size());
+    for (int d = 0; d < S.size(); ++d)
+      for (int j = 0; j < N.size(); ++j)
+        lists[TW.find(S.v[d].x + N.v[j].x, S.v[d].y + N.v[j].y)].push_back(make_int2(d, j));
+    std::vector<int> ptr(1, 0);
+    std::vector<int2> pairs;
+    for (const auto& l : lists) {
+      pairs.insert(pairs.end(), l.begin(), l.end());
+      ptr.push_back((int)pairs.size());
+    }
+    const std::vector<int2>& Ok = h->lv[k].off_h;
+    const int NB = N.size(), no = (int)Ok.size();
+    std::vector<int> rg((size_t)NB * no);
+    std::vector<int2> yg((size_t)no * NB);
+    for (int j = 0; j < NB; ++j)
+      for (int o = 0; o < no; ++o) {
+        rg[(size_t)j * no + o] = TW.find(N.v[j].x - Ok[o].x, N.v[j].y - Ok[o].y);
+        const int wx = N.v[j].x + Ok[o].x, wy = N.v[j].y + Ok[o].y;
+        yg[(size_t)o * NB + j] = make_int2(TW.find(wx, wy), N.find(wx, wy));
+      }
+    R.nS = S.size();
+    R.nTW = TW.size();
+    R.S = pack_append(P->bytes, S.v);
+    R.tw_ptr = pack_append(P->bytes, ptr);
+    R.tw_pairs = pack_append(P->bytes, pairs);
+    R.rg = pack_append(P->bytes, rg);
+    R.yg = pack_append(P->bytes, yg);
+    if (k - 1 >= 2) R.oidx = pack_append(P->bytes, offset_box(h->lv[k - 1].off_h, R.obox));
+  }
+  P->oidxq = pack_append(P->bytes, offset_box(h->lv[q].off_h, P->oboxq));
+  std::lock_guard<std::mutex> lock(mu);
+  cache[h->plan->key] = P;
+  return P;
 }
 
 // The patch-CG geometry of level k as the setup launched it.
@@ -1955,10 +1983,25 @@ gamblet_status grad_onepass_impl(gamblet_ctx* h, int ncell, const int32_t* cell_
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaEventRecord(e0, s));
+  // every table of the reverse pass in one copy, and the caller's arrays,
+  // before any kernel is queued (copies from pageable host memory wait for
+  // the stream)
+  std::shared_ptr<const RevPack> pack = reverse_pack(h);
+  const char* dpack = tmp.upload(pack->bytes, s);
   double* g_dev = nullptr;
   double* uo_dev = nullptr;
   to_device(tmp, g_dev, g_user, h->n, s);
   to_device(tmp, uo_dev, uobs_user, h->n, s);
+  int32_t* cn = nullptr;
+  double* ca = nullptr;
+  double* kr = nullptr;
+  to_device(tmp, cn, cell_nodes, 4 * (int64_t)ncell, s);
+  to_device(tmp, ca, cell_a, ncell, s);
+  to_device(tmp, kr, K_ref, 16, s);
+  double* d = h->dots;
+  CK(cudaMemsetAsync(d, 0, sizeof(double) * 8, s));
+  const double one = 1.0;
+  CK(cudaMemcpyAsync(d + 7, &one, sizeof(double), cudaMemcpyHostToDevice, s));
   // ---- forward: u_hat = G ghat, keeping the intermediates of every level
   launch_gather_morton(g_dev, h->unknown_of, nq, h->g64, s);
   launch_transform_vec<double>(h->g64, h->g64, Lq.npar, Lq.pmask, +1, s);
@@ -1984,10 +2027,6 @@ gamblet_status grad_onepass_impl(gamblet_ctx* h, int ncell, const int32_t* cell_
   launch_gather_morton(uo_dev, h->unknown_of, nq, h->r64, s);
   launch_transform_vec<double>(h->r64, h->r64, Lq.npar, Lq.pmask, +1, s);
   CK(cudaMemcpyAsync(h->p64, h->z64, sizeof(double) * nq, cudaMemcpyDeviceToDevice, s));
-  double* d = h->dots;
-  CK(cudaMemsetAsync(d, 0, sizeof(double) * 8, s));
-  const double one = 1.0;
-  CK(cudaMemcpyAsync(d + 7, &one, sizeof(double), cudaMemcpyHostToDevice, s));
   launch_axpy(nq, d + 7, d + 7, -1.0, h->r64, h->p64, s);
   launch_dots(nq, h->p64, h->p64, nullptr, nullptr, nullptr, nullptr, d, s);
   // ---- the misfit through the same chain: lambda^(k), dJ/dg
@@ -2012,15 +2051,17 @@ gamblet_status grad_onepass_impl(gamblet_ctx* h, int ncell, const int32_t* cell_
   for (int k = 2; k <= q; ++k) {
     LevelDev& L = h->lv[k];
     const int Lpar = 1 << (k - 1);
-    RevLevel R = reverse_tables(h, k, tmp);
-    int obox = 0;
-    const int* oidx = nullptr;
-    if (k - 1 >= 2) {
-      std::vector<int> box = offset_box(h->lv[k - 1].off_h, obox);
-      int* db = nullptr;
-      to_device(tmp, db, box.data(), (int64_t)box.size(), s);
-      oidx = db;
-    }
+    const RevPack::Level& pk = pack->lv[k];
+    RevLevel R;
+    R.nS = pk.nS;
+    R.nTW = pk.nTW;
+    R.S = reinterpret_cast<const int2*>(dpack + pk.S);
+    R.tw_ptr = reinterpret_cast<const int*>(dpack + pk.tw_ptr);
+    R.tw_pairs = reinterpret_cast<const int2*>(dpack + pk.tw_pairs);
+    R.rg = reinterpret_cast<const int*>(dpack + pk.rg);
+    R.yg = reinterpret_cast<const int2*>(dpack + pk.yg);
+    const int obox = pk.obox;
+    const int* oidx = k - 1 >= 2 ? reinterpret_cast<const int*>(dpack + pk.oidx) : nullptr;
     T* X = tmp.alloc<T>((int64_t)R.nS * L.npar);
     T* Tw = tmp.alloc<T>(L.npar * R.nTW * 4);
     const T* vprev = k == 2 ? U1g : vg[k - 1];
@@ -2053,16 +2094,8 @@ gamblet_status grad_onepass_impl(gamblet_ctx* h, int ncell, const int32_t* cell_
     CK(cudaGetLastError());
   }
   // ---- dJ/dlog a from the finest level's adjoint
-  int oboxq = 0;
-  std::vector<int> boxq = offset_box(Lq.off_h, oboxq);
-  int* oidxq = nullptr;
-  to_device(tmp, oidxq, boxq.data(), (int64_t)boxq.size(), s);
-  int32_t* cn = nullptr;
-  double* ca = nullptr;
-  double* kr = nullptr;
-  to_device(tmp, cn, cell_nodes, 4 * (int64_t)ncell, s);
-  to_device(tmp, ca, cell_a, ncell, s);
-  to_device(tmp, kr, K_ref, 16, s);
+  const int oboxq = pack->oboxq;
+  const int* oidxq = reinterpret_cast<const int*>(dpack + pack->oidxq);
   const bool dev_dJ = is_device_ptr(dJ_user);
   double* dJ = dev_dJ ? dJ_user : tmp.alloc<double>(ncell);
   int tok = h->prof.begin("grad_cells", 0.0, 0.0, s);
