@@ -352,6 +352,7 @@ struct gamblet_ctx {
   const int* l1map = nullptr;
   // CG batch
   CgLevel* cg_lv = nullptr;
+  CgLevel* cg_lv_h = nullptr;  // pinned staging copy (the upload does not wait for the setup)
   CgScalars* cg_sc = nullptr;
   int* any_active = nullptr;
   int* any_active_h = nullptr;  // pinned
@@ -1370,7 +1371,15 @@ void alloc_solve(gamblet_ctx* h) {
     prepare_cg_spmv<T>(max_ts);
     h->cg_nlev = (int)cl.size();
     h->cg_blocks = blocks;
-    h->cg_lv = P.upload(cl, s);
+    // from pinned memory: a copy from pageable memory would wait here for
+    // every setup kernel queued so far
+    h->cg_lv = P.alloc<CgLevel>((int64_t)cl.size());
+    if (!cl.empty()) {
+      if ((int)cl.size() > h->q) fail(GAMBLET_ERR_INVALID_ARG, "level count exceeds q");
+      std::memcpy(h->cg_lv_h, cl.data(), sizeof(CgLevel) * cl.size());
+      CK(cudaMemcpyAsync(h->cg_lv, h->cg_lv_h, sizeof(CgLevel) * cl.size(),
+                         cudaMemcpyHostToDevice, s));
+    }
     h->cg_sc = P.zeros<CgScalars>(std::max(h->cg_nlev, 1), s);
     h->any_active = P.zeros<int>(1, s);
     h->cg_loop_count = P.zeros<int>(1, s);
@@ -2199,6 +2208,7 @@ gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
     CK(cudaMallocHost(&h->any_active_h, sizeof(int)));
     CK(cudaMallocHost(&h->dots_h, sizeof(double) * 8));
     CK(cudaMallocHost(&h->status_h, sizeof(int)));
+    CK(cudaMallocHost(&h->cg_lv_h, sizeof(CgLevel) * (size_t)std::max(q, 1)));
     h->status = h->pool.zeros<int>(1, h->s);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -3516,6 +3526,7 @@ void gamblet_destroy(gamblet_handle h) {
   if (h->any_active_h) cudaFreeHost(h->any_active_h);
   if (h->dots_h) cudaFreeHost(h->dots_h);
   if (h->status_h) cudaFreeHost(h->status_h);
+  if (h->cg_lv_h) cudaFreeHost(h->cg_lv_h);
   delete h;
 }
 
