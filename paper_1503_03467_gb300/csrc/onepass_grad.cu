@@ -34,6 +34,23 @@ __device__ void stage_q(E* Qs) {
   __syncthreads();
 }
 
+// One 4-element entry (16-byte aligned) as vector loads.
+__device__ __forceinline__ void ld4v(const float* p, float* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+__device__ __forceinline__ void ld4v(const double* p, double* v) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+
 // Plain entry (i, i') of a level operator whose transformed blocks are Y
 // ([o][P][4][4]; P = i >> 2, slot a = i & 3), zero off the block pattern:
 // sum_{alpha, beta} Q_P[alpha][a] Y[o][P][alpha][beta] Q_P'[beta][b].
@@ -157,15 +174,42 @@ __global__ void k_window_product(E* __restrict__ T, int nTW, const int* __restri
   int x, y;
   demorton((uint32_t)i, x, y);
   E acc[4] = {E(0), E(0), E(0), E(0)};
-  for (int e = tw_ptr[w]; e < tw_ptr[w + 1]; ++e) {
-    const int2 dj = tw_pairs[e];
-    const E xv = X[(int64_t)dj.x * nrow + i];
-    if (xv == E(0)) continue;
-    const int ip = shift_cell(x, y, S[dj.x].x, S[dj.x].y, L, nrow);
-    if (ip < 0) continue;
-    const E* r = Rhat + ((int64_t)ip * NB + dj.y) * 4;
+  // four pairs per step in float32, their loads issued before any is used:
+  // the chain pair -> X -> Rhat row is otherwise a dependent latency per
+  // pair (in float64 the extra registers cost more occupancy than the
+  // overlap gains: one pair per step measured fastest)
+  constexpr int U = sizeof(E) == 4 ? 4 : 1;
+  const int e1 = tw_ptr[w + 1];
+  for (int e = tw_ptr[w]; e < e1; e += U) {
+    int2 dj[U];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[c] += xv * r[c];
+    for (int u = 0; u < U; ++u) dj[u] = e + u < e1 ? tw_pairs[e + u] : make_int2(-1, 0);
+    E xv[U];
+    int ip[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      xv[u] = E(0);
+      ip[u] = -1;
+      if (dj[u].x >= 0) {
+        xv[u] = X[(int64_t)dj[u].x * nrow + i];
+        const int2 sd = S[dj[u].x];
+        ip[u] = shift_cell(x, y, sd.x, sd.y, L, nrow);
+      }
+    }
+    E r[U][4];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (ip[u] >= 0 && xv[u] != E(0)) {
+        ld4v(Rhat + ((int64_t)ip[u] * NB + dj[u].y) * 4, r[u]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) r[u][c] = E(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[c] += xv[u] * r[u][c];
   }
   E* out = T + t * 4;
 #pragma unroll
@@ -196,11 +240,14 @@ __global__ void k_rbar_galerkin(E* __restrict__ Rbar, const E* __restrict__ T, i
     const int Pp = shift_cell(px, py, -off[o].x, -off[o].y, L, nrow);
     if (Pp < 0) continue;
     const E* B = Ahat + ((int64_t)o * nrow + Pp) * 16;
-    const E* tv = T + ((int64_t)w * nrow + i) * 4;
+    E tv[4], b[16];
+    ld4v(T + ((int64_t)w * nrow + i) * 4, tv);
+#pragma unroll
+    for (int cp = 0; cp < 4; ++cp) ld4v(B + 4 * cp, b + 4 * cp);
 #pragma unroll
     for (int cp = 0; cp < 4; ++cp)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[c] += tv[cp] * B[4 * cp + c];
+      for (int c = 0; c < 4; ++c) acc[c] += tv[cp] * b[4 * cp + c];
   }
   E* out = Rbar + t * 4;
 #pragma unroll
@@ -230,18 +277,12 @@ __global__ void k_ybar_galerkin(E* __restrict__ Y, int noff, const int2* __restr
     const int i = shift_cell(x, y, -nbr[j].x, -nbr[j].y, L, npar);
     if (i < 0) continue;
     const int2 wj = yg[o * NB + j];
-    const E* r = Rhat + ((int64_t)i * NB + j) * 4;
-    E z[4] = {E(0), E(0), E(0), E(0)};
-    if (wj.x >= 0) {
-      const E* tv = T + ((int64_t)wj.x * npar + i) * 4;
+    E r[4], z[4] = {E(0), E(0), E(0), E(0)}, m[4] = {E(0), E(0), E(0), E(0)};
+    ld4v(Rhat + ((int64_t)i * NB + j) * 4, r);
+    if (wj.x >= 0) ld4v(T + ((int64_t)wj.x * npar + i) * 4, z);
+    if (wj.y >= 0) ld4v(M + ((int64_t)i * NB + wj.y) * 4, m);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) z[c] = tv[c];
-    }
-    if (wj.y >= 0) {
-      const E* mv = M + ((int64_t)i * NB + wj.y) * 4;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) z[c] -= mv[c];
-    }
+    for (int c = 0; c < 4; ++c) z[c] -= m[c];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
