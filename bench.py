@@ -674,10 +674,11 @@ def cpu_oracle(p):
 
 
 def cpu_oracle_other():
-    """The other two CPU baselines: the oracle's exact (non-localized)
-    decomposition at 32 x 32 cells (q = 5, C = 100) and its localized setup +
-    one-pass solve at 128 x 128 (q = 7, C = 1e4, rho = 3), in fine DOFs/s.
-    Both run numpy/scipy, whose BLAS uses the host's cores."""
+    """The other CPU baselines: the oracle's exact (non-localized)
+    decomposition at 32 x 32 cells (q = 5, C = 100), its localized setup +
+    one-pass solve at 128 x 128 (q = 7, C = 1e4, rho = 3), and its gradient
+    through the one-pass transform at 32 x 32 (rho = 3), in fine DOFs/s.
+    All run numpy/scipy, whose BLAS uses the host's cores."""
     from workloads import make_problem
     from oracle.exact import gamblet_exact
     from oracle.local import gamblet_local_setup, gamblet_local_solve
@@ -699,6 +700,19 @@ def cpu_oracle_other():
                                 "setup_s": t1 - t0, "solve_s": t2 - t1,
                                 "sample": "localized setup (dense patch solves, rho = 3) and "
                                           "one-pass solve, 16,129 unknowns"}
+    # the gradient through the one-pass transform (dense reverse pass)
+    from oracle import direct
+    from oracle.local_adjoint import gradient_one_pass
+    from workloads.rough import K_REF
+    p = make_problem(32, 1e4, 0)
+    u_obs, _ = direct.solve(make_problem(32, 1e4, 7).A, p.g)
+    t0 = time.perf_counter()
+    gradient_one_pass(p.A, p.g, u_obs, 32, np.exp(p.log_a), K_REF, p.cells, p.q, 3.0)
+    t = time.perf_counter() - t0
+    out["one_pass_gradient_32x32"] = {"value": p.ndof / t, "unit": UNIT, "seconds": t,
+                                      "sample": "localized setup, one-pass solve and the reverse "
+                                                "pass through both (dense), rho = 3, 961 "
+                                                "unknowns"}
     out["cores"] = os.cpu_count()
     out["kind"] = "oracle"
     return out
