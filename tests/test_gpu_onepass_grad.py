@@ -204,3 +204,36 @@ def test_autograd_one_pass_gradients_match_oracle():
     assert np.abs(ga - r["grad"]).max() <= 1e-8 * np.abs(r["grad"]).max()
     gg = g.grad.cpu().numpy()
     assert np.linalg.norm(gg - r["dJ_dg"]) <= 1e-9 * np.linalg.norm(r["dJ_dg"])
+
+
+def test_onepass_outputs_at_512_equal_one_pass_solves():
+    """At 512 x 512 (mixed, bench level tolerance): u_loc and dJ/dg of
+    gamblet_grad_onepass equal gamblet_solve's one-pass output (no outer
+    refinement) for g and for the misfit u_loc - u_obs, through the same
+    handle (G_loc is symmetric)."""
+    from paper_1503_03467_gb300 import native as nv
+    n = 512
+    p = make_problem(n, 1e4, 0)
+    rp, ci, va = csr_arrays(p.A)
+    o = _opts(3.0, precision=nv.MIXED)
+    o.patch_tol = 0.0  # the mixed default
+    o.level_tol = 0.05
+    o.refine_max_iter = 0
+    h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
+    try:
+        u_obs = np.random.default_rng(21).standard_normal(p.ndof)
+        dJ = np.zeros(n * n)
+        u = np.zeros(p.ndof)
+        dg = np.zeros(p.ndof)
+        J = nv.gamblet_grad_onepass(h, cell_corner_dofs(n), np.exp(p.log_a.ravel()),
+                                    K_REF.ravel().copy(), p.g, u_obs, dJ, u=u, dJ_dg=dg)
+        u1 = np.zeros(p.ndof)
+        nv.gamblet_solve(h, p.g, u1)
+        dg1 = np.zeros(p.ndof)
+        nv.gamblet_solve(h, u1 - u_obs, dg1)
+    finally:
+        nv.gamblet_destroy(h)
+    assert np.linalg.norm(u - u1) <= 1e-6 * np.linalg.norm(u1)
+    assert abs(J - 0.5 * float((u1 - u_obs) @ (u1 - u_obs))) <= 1e-6 * J
+    assert np.linalg.norm(dg - dg1) <= 1e-5 * np.linalg.norm(dg1)
+    assert np.all(np.isfinite(dJ)) and np.abs(dJ).max() > 0
