@@ -84,14 +84,30 @@ __host__ __device__ __forceinline__ int shift_cell(int x, int y, int dx, int dy,
 // active slots below c), row 3 is 1/sqrt(cnt) and row t < cnt - 1 is the
 // normalised Helmert row t + 1 of Lemma const0:
 //   U^(n)_{t+1, .} = (1, ..., 1 [t+1 times], -(t+1), 0, ...) / sqrt((t+1)(t+2)).
+// 1 / sqrt(n) for the six n that occur (cnt = 1..4 and (t + 1)(t + 2) =
+// 2, 6, 12) as literal constants: float64 square roots and divisions per
+// element are slow on this part's float64 pipe.
+template <typename T>
+__host__ __device__ __forceinline__ T inv_sqrt_q(int n) {
+  switch (n) {
+    case 1: return T(1);
+    case 2: return T(0.70710678118654752440);   // 1/sqrt(2)
+    case 3: return T(0.57735026918962576451);   // 1/sqrt(3)
+    case 4: return T(0.5);
+    case 6: return T(0.40824829046386301637);   // 1/sqrt(6)
+    case 12: return T(0.28867513459481288225);  // 1/sqrt(12)
+    default: return T(1) / sqrt(T(n));
+  }
+}
+
 template <typename T>
 __host__ __device__ __forceinline__ T qv(int m, int a, int c) {
   if (!((m >> c) & 1)) return T(0);
   const int cnt = __popc_portable(m & 15);
   const int j = __popc_portable(m & ((1 << c) - 1));
-  if (a == 3) return T(1) / sqrt(T(cnt));
+  if (a == 3) return inv_sqrt_q<T>(cnt);
   if (a >= cnt - 1) return T(0);
-  const T nrm = T(1) / sqrt(T((a + 1) * (a + 2)));
+  const T nrm = inv_sqrt_q<T>((a + 1) * (a + 2));
   if (j <= a) return nrm;
   if (j == a + 1) return -T(a + 1) * nrm;
   return T(0);

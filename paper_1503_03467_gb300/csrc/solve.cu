@@ -375,19 +375,33 @@ void launch_dots(int64_t n, const double* a0, const double* b0, const double* a1
                  const double* b1, const double* a2, const double* b2, double* dots,
                  cudaStream_t s) {
   if (n <= 0) return;
+  // at most four blocks per SM: every block adds its partial sums to the
+  // same three words, and those atomics serialise
+  static thread_local int dev_cached = -1, sms = 152;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != dev_cached) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    dev_cached = dev;
+  }
   int64_t blocks = (n + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
+  if (blocks > 4 * (int64_t)sms) blocks = 4 * (int64_t)sms;
   { count_launch(); k_dots<<<(unsigned)blocks, 256, 0, s>>>(n, a0, b0, a1, b1, a2, b2, dots); }
 }
 
 // y += sign * (num / den) * x
+// (the scalar is formed once per block: a float64 division per element
+// would hold this memory-bound kernel on the float64 pipe)
 __global__ void k_axpy(int64_t n, const double* __restrict__ num, const double* __restrict__ den,
                        double sign, const double* __restrict__ x, double* y) {
+  __shared__ double sa;
+  if (threadIdx.x == 0) {
+    const double d = *den;
+    sa = d != 0.0 ? sign * (*num) / d : 0.0;
+  }
+  __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double d = *den;
-  const double a = d != 0.0 ? sign * (*num) / d : 0.0;
-  y[i] += a * x[i];
+  if (i < n) y[i] += sa * x[i];
 }
 void launch_axpy(int64_t n, const double* alpha_num, const double* alpha_den, double sign,
                  const double* x, double* y, cudaStream_t s) {
@@ -397,11 +411,14 @@ void launch_axpy(int64_t n, const double* alpha_num, const double* alpha_den, do
 // p = x + sign * (num / den) * p
 __global__ void k_xpby(int64_t n, const double* __restrict__ x, const double* __restrict__ num,
                        const double* __restrict__ den, double sign, double* p) {
+  __shared__ double sb;  // once per block, as in k_axpy
+  if (threadIdx.x == 0) {
+    const double d = *den;
+    sb = d != 0.0 ? sign * (*num) / d : 0.0;
+  }
+  __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double d = *den;
-  const double b = d != 0.0 ? sign * (*num) / d : 0.0;
-  p[i] = x[i] + b * p[i];
+  if (i < n) p[i] = x[i] + sb * p[i];
 }
 void launch_xpby(int64_t n, const double* x, const double* beta_num, const double* beta_den,
                  double sign, double* p, cudaStream_t s) {

@@ -115,7 +115,7 @@ def test_onepass_gradient_of_uniform_coefficient_misfit_zero():
 
 def test_onepass_gradient_at_256_matches_central_differences():
     """The derivative along a random direction of log a against central
-    differences of J through the GPU's one-pass map (3 setups of 65,025
+    differences of J through the GPU's one-pass map (5 setups of 65,025
     unknowns, rho = 3)."""
     n = 256
     p = make_problem(n, 1e3, 0)
@@ -123,13 +123,16 @@ def test_onepass_gradient_at_256_matches_central_differences():
     u_obs = direct.solve(obs.A, p.g)[0]
     J0, dJ, _, _ = _gpu_grad(p.A, p, u_obs, 3.0)
     d = np.random.default_rng(5).standard_normal(n * n)
-    h = 1e-5
-    Js = []
-    for sgn in (1.0, -1.0):
-        la = p.log_a.ravel() + sgn * h * d
+    # fourth-order central differences: a step large enough that the noise
+    # of the iterative solves (1e-12) stays far below the tolerance, with a
+    # truncation error of order h^4
+    h = 1e-4
+    Js = {}
+    for m in (2, 1, -1, -2):
+        la = p.log_a.ravel() + m * h * d
         A = assemble_q1(np.exp(la).reshape(n, n))
-        Js.append(_gpu_grad(A, p, u_obs, 3.0, log_a=la)[0])
-    fd = (Js[0] - Js[1]) / (2 * h)
+        Js[m] = _gpu_grad(A, p, u_obs, 3.0, log_a=la)[0]
+    fd = (8 * (Js[1] - Js[-1]) - (Js[2] - Js[-2])) / (12 * h)
     assert abs(fd - dJ @ d) <= 1e-6 * abs(fd)
 
 
