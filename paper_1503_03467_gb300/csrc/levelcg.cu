@@ -200,14 +200,21 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_cg_update(const CgLevel* __restrict__ lv, int nlev,
                                                    CgScalars* sc) {
   __shared__ double red[8];
+  __shared__ T salpha;
   const int l = find_level(lv, nlev, blockIdx.x);
   if (!sc[l].active) return;
   const CgLevel L = lv[l];
+  // alpha once per block: a float64 division per element would hold this
+  // memory-bound kernel on the float64 pipe
+  if (threadIdx.x == 0) {
+    const double pAp = sc[l].pAp;
+    salpha = pAp > 0 ? (T)(sc[l].rz / pAp) : T(0);
+  }
+  __syncthreads();
   const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
   double rz = 0, rr = 0;
   if (p < L.npar) {
-    const double pAp = sc[l].pAp;
-    const T alpha = pAp > 0 ? (T)(sc[l].rz / pAp) : T(0);
+    const T alpha = salpha;
     T* x = (T*)L.x;
     T* r = (T*)L.r;
     T* z = (T*)L.z;
@@ -669,11 +676,16 @@ __global__ void __launch_bounds__(256) k_cgm_update(const CgLevel* __restrict__ 
   if (!S->active) return;
   const CgLevel L = lv[l];
   const int64_t off = rh * L.rstride;
+  __shared__ T salpha;  // once per block, as in k_cg_update
+  if (threadIdx.x == 0) {
+    const double pAp = S->pAp;
+    salpha = pAp > 0 ? (T)(S->rz / pAp) : T(0);
+  }
+  __syncthreads();
   const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
   double rz = 0, rr = 0;
   if (p < L.npar) {
-    const double pAp = S->pAp;
-    const T alpha = pAp > 0 ? (T)(S->rz / pAp) : T(0);
+    const T alpha = salpha;
     T* x = (T*)L.x + off;
     T* r = (T*)L.r + off;
     T* z = (T*)L.z + off;

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ RT, int N
   if (lane != 0) return;
   T h3 = 0;
   if (m) {
-    h3 = v[p] * (T(1) / sqrt(T(__popc(m))));
+    h3 = v[p] * inv_sqrt_q<T>(__popc(m));
     if (w) {
       h0 += w[4 * p];
       h1 += w[4 * p + 1];
