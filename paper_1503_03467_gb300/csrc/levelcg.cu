@@ -40,6 +40,54 @@ __device__ __forceinline__ void block_sum_add(double v, double* dst, double* red
   __syncthreads();
 }
 
+// The same for per-thread partials in the working precision T: the warp
+// reduces in T (float shuffles and adds on the mixed path, so the float64
+// pipe sees only the per-warp values), the warps and the blocks in float64.
+// Two sums (a -> *da, b -> *db) share one pair of barriers; red needs 16.
+template <typename T>
+__device__ __forceinline__ T warp_sum_w(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ void block_sum2_add(T a, T b, double* da, double* db, double* red) {
+  a = warp_sum_w(a);
+  b = warp_sum_w(b);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[warp] = (double)a;
+    red[8 + warp] = (double)b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    double va = lane < nw ? red[lane] : 0.0;
+    double vb = lane < nw ? red[8 + lane] : 0.0;
+    va = warp_sum(va);
+    vb = warp_sum(vb);
+    if (lane == 0) {
+      if (va != 0.0) atomicAdd(da, va);
+      if (vb != 0.0) atomicAdd(db, vb);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void block_sum1_add(T a, double* da, double* red) {
+  a = warp_sum_w(a);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = (double)a;
+  __syncthreads();
+  if (warp == 0) {
+    double va = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    va = warp_sum(va);
+    if (lane == 0 && va != 0.0) atomicAdd(da, va);
+  }
+  __syncthreads();
+}
+
 // z = Dinv r for one parent (3 active slots at most)
 template <typename T>
 __device__ __forceinline__ void apply_dinv(const T* __restrict__ Dinv, int64_t npar, int64_t p,
@@ -182,24 +230,23 @@ __global__ void __launch_bounds__(256) k_cg_spmv(const CgLevel* __restrict__ lv,
     y1v += __shfl_xor_sync(0xffffffffu, y1v, o);
     y2v += __shfl_xor_sync(0xffffffffu, y2v, o);
   }
-  double part = 0;
+  T part = 0;
   if (own && sub == 0) {
     T* Ap = (T*)L.Ap;
     Ap[4 * p] = y0v;
     Ap[4 * p + 1] = y1v;
     Ap[4 * p + 2] = y2v;
     const int c0 = ly * TS + lx;
-    part = (double)xs[c0] * y0v + (double)xs[TS * TS + c0] * y1v +
-           (double)xs[2 * TS * TS + c0] * y2v;
+    part = xs[c0] * y0v + xs[TS * TS + c0] * y1v + xs[2 * TS * TS + c0] * y2v;
   }
-  block_sum_add(part, &sc[l].pAp, red);
+  block_sum1_add<T>(part, &sc[l].pAp, red);
 }
 
 // x += alpha p, r -= alpha Ap, z = Dinv r; rz_new += r.z, rr_new += r.r
 template <typename T>
 __global__ void __launch_bounds__(256) k_cg_update(const CgLevel* __restrict__ lv, int nlev,
                                                    CgScalars* sc) {
-  __shared__ double red[8];
+  __shared__ double red[16];
   __shared__ T salpha;
   const int l = find_level(lv, nlev, blockIdx.x);
   if (!sc[l].active) return;
@@ -212,7 +259,7 @@ __global__ void __launch_bounds__(256) k_cg_update(const CgLevel* __restrict__ l
   }
   __syncthreads();
   const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
-  double rz = 0, rr = 0;
+  T rz = 0, rr = 0;
   if (p < L.npar) {
     const T alpha = salpha;
     T* x = (T*)L.x;
@@ -231,12 +278,11 @@ __global__ void __launch_bounds__(256) k_cg_update(const CgLevel* __restrict__ l
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       z[4 * p + a] = zv[a];
-      rz += (double)rv[a] * (double)zv[a];
-      rr += (double)rv[a] * (double)rv[a];
+      rz += rv[a] * zv[a];
+      rr += rv[a] * rv[a];
     }
   }
-  block_sum_add(rz, &sc[l].rz_new, red);
-  block_sum_add(rr, &sc[l].rr_new, red);
+  block_sum2_add<T>(rz, rr, &sc[l].rz_new, &sc[l].rr_new, red);
 }
 
 // beta, convergence on |r|_2, counters; one thread so any_active is exact
