@@ -697,25 +697,24 @@ __global__ void __launch_bounds__(256) k_cgm_spmv(const CgLevel* __restrict__ lv
 #pragma unroll
   for (int r = 0; r < kMaxRhs; ++r) {
     if (r >= nrhs) break;
-    double part = 0;
+    T part = 0;
     if (own && sub == 0 && ((act >> r) & 1)) {
       T* Ap = (T*)L.Ap + r * L.rstride;
       Ap[4 * p] = yv[r][0];
       Ap[4 * p + 1] = yv[r][1];
       Ap[4 * p + 2] = yv[r][2];
       const int c0 = ly * TS + lx;
-      part = (double)xs[(r * 3) * plane + c0] * yv[r][0] +
-             (double)xs[(r * 3 + 1) * plane + c0] * yv[r][1] +
-             (double)xs[(r * 3 + 2) * plane + c0] * yv[r][2];
+      part = xs[(r * 3) * plane + c0] * yv[r][0] + xs[(r * 3 + 1) * plane + c0] * yv[r][1] +
+             xs[(r * 3 + 2) * plane + c0] * yv[r][2];
     }
-    block_sum_add(part, &sc[l * nrhs + r].pAp, red);
+    block_sum1_add<T>(part, &sc[l * nrhs + r].pAp, red);
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_cgm_update(const CgLevel* __restrict__ lv, int nlev,
                                                     CgScalars* sc, int nrhs) {
-  __shared__ double red[8];
+  __shared__ double red[16];
   const int l = find_level(lv, nlev, blockIdx.x);
   const int rh = blockIdx.y;
   CgScalars* S = &sc[l * nrhs + rh];
@@ -729,7 +728,7 @@ __global__ void __launch_bounds__(256) k_cgm_update(const CgLevel* __restrict__ 
   }
   __syncthreads();
   const int64_t p = (int64_t)(blockIdx.x - L.block_begin) * blockDim.x + threadIdx.x;
-  double rz = 0, rr = 0;
+  T rz = 0, rr = 0;
   if (p < L.npar) {
     const T alpha = salpha;
     T* x = (T*)L.x + off;
@@ -748,12 +747,11 @@ __global__ void __launch_bounds__(256) k_cgm_update(const CgLevel* __restrict__ 
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       z[4 * p + a] = zv[a];
-      rz += (double)rv[a] * (double)zv[a];
-      rr += (double)rv[a] * (double)rv[a];
+      rz += rv[a] * zv[a];
+      rr += rv[a] * rv[a];
     }
   }
-  block_sum_add(rz, &S->rz_new, red);
-  block_sum_add(rr, &S->rr_new, red);
+  block_sum2_add<T>(rz, rr, &S->rz_new, &S->rr_new, red);
 }
 
 __global__ void k_cgm_scalars(CgScalars* sc, int n, double tol2, int max_iter, int* any_active) {
