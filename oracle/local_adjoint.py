@@ -30,8 +30,9 @@ Fine operator (Sec. 5.1): A^(q) = sum_c a_c K_c, so
   dJ/dtheta_c = a_c sum_{p,r corners of c} Abar^(q)_sym[p, r] K_ref[p, r].
 
 Pins (tests/test_oracle_local_adjoint.py): central differences of the
-one-pass map itself, the exact-solution adjoint when the patches cover the
-domain, and dJ/dg = G_loc (u_loc - u_obs) (G_loc is symmetric).
+one-pass map itself (also on a domain with holes), the exact-solution
+adjoint when the patches cover the domain, dJ/dg = G_loc (u_loc - u_obs)
+(G_loc is symmetric), and planted mistakes that the differences catch.
 """
 from __future__ import annotations
 
