@@ -102,9 +102,10 @@ typedef struct {
                                timing candidates on a sample of each large
                                level, once per geometry and precision in a
                                process; 0: fixed rules                     */
-  int32_t galerkin_variant; /* -1: automatic; 0..3: use that Galerkin
-                               kernel on every level (see
-                               gamblet_launch_shapes)                      */
+  int32_t galerkin_variant; /* -1: automatic; 0..5: use that Galerkin
+                               kernel on every level (3, 4, 5: the tile
+                               kernel with 8, 4, 16 lanes per output;
+                               see gamblet_launch_shapes)                  */
   int32_t patch_gather;     /* -1: automatic; 0, 1, 2: use that patch-CG
                                block gather on every level                 */
   void* stream;             /* cudaStream_t                                */
@@ -394,7 +395,8 @@ GAMBLET_API gamblet_status gamblet_assemble_cells(int32_t n, const int32_t* rowp
  *   shapes[1]  patch-CG block gather (0 thread per block, 1 half-warp per block,
  *              2 four lanes per block)
  *   shapes[2]  Galerkin kernel (0 thread per position, 1 warp-cooperative,
- *              2 warp per row, 3 2 x 2 row tiles)
+ *              2 warp per row, 3, 4, 5 2 x 2 row tiles with 8, 4, 16 lanes
+ *              per output target)
  *   shapes[3]  level-CG SpMV threads per parent (1: 16 x 16 tiles, 4: 8 x 8,
  *              16: 4 x 4) */
 GAMBLET_API gamblet_status gamblet_launch_shapes(gamblet_handle h, int32_t k, int32_t* shapes);

@@ -138,7 +138,7 @@ size_t galerkin_tile_smem_bytes(const GalerkinGeom& g, size_t elem) {
   return elem * (16 * (size_t)g.NB + 16 * (size_t)g.tile_W * g.tile_W);
 }
 
-template <typename T>
+template <typename T, int LPT>
 __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Ahat,
                                                        const T* __restrict__ Rhat,
                                                        const uint32_t* __restrict__ pmask,
@@ -199,13 +199,16 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
       for (int r = 0; r < 4; ++r) sst4(tt + ((size_t)r * WW + u) * 4, acc[r]);
     }
     __syncthreads();
-    // phase 2: outputs A_{i0+r, c} for every target cell c.  Eight lanes per
-    // target (four targets per warp) stride over the target's list of pairs
-    // (j, u) whose window position holds a nonzero t, so the partial sums
-    // combine in three shuffle steps.
+    // phase 2: outputs A_{i0+r, c} for every target cell c.  LPT lanes per
+    // target (32 / LPT targets per warp; 4, 8 or 16, chosen per level by the
+    // launch-shape tuner: short pair lists on the finest level, long ones on
+    // dense levels) stride over the target's list of pairs (j, u) whose
+    // window position holds a nonzero t; the partial sums combine in
+    // log2(LPT) shuffle steps.
     {
-      const int sub = lane & 7, grp = lane >> 3;
-      for (int e0 = 4 * warp; e0 < g.nt2; e0 += 4 * nwarp) {
+      constexpr int TPW = 32 / LPT;
+      const int sub = lane & (LPT - 1), grp = lane / LPT;
+      for (int e0 = TPW * warp; e0 < g.nt2; e0 += TPW * nwarp) {
         const int e = e0 + grp;
         const bool ok = e < g.nt2;
         const int4 tg = ok ? g.t2[e] : make_int4(0, 0, -1, -1);
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
         if (have) {
           const T* rc = Rhat + (int64_t)ip * 4 * NB;
           const int q1 = g.t2p_ptr[e + 1];
-          for (int q = g.t2p_ptr[e] + sub; q < q1; q += 8) {
+          for (int q = g.t2p_ptr[e] + sub; q < q1; q += LPT) {
             const int pu = __ldg(g.t2p + q);
             const int j = pu & 0xff, u = pu >> 8;
             T rv[4];
@@ -234,9 +237,8 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           T v = acc[r];
-          v += __shfl_xor_sync(0xffffffffu, v, 4);
-          v += __shfl_xor_sync(0xffffffffu, v, 2);
-          v += __shfl_xor_sync(0xffffffffu, v, 1);
+#pragma unroll
+          for (int o = LPT / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
           if (sub == 0 && ok && d[r] >= 0 && i0 + r >= g.i_begin && i0 + r < g.i_end)
             Aout[(int64_t)d[r] * nrow + i0 + r] = live[r] ? v : T(0);
         }
@@ -397,12 +399,15 @@ void launch_galerkin(const T* Ahat, const T* Rhat, const uint32_t* pmask_k, Gale
   size_t smem = sizeof(T) * 4 * ((size_t)g.NB + (size_t)g.nwin);
   int64_t grid = nrows < 65535 * 16 ? nrows : 65535 * 16;
   count_launch();
-  if (g.variant == 3) {
+  if (g.variant >= 3) {
+    // 3, 4, 5: the tile kernel with 8, 4 or 16 lanes per output target
     const size_t st = galerkin_tile_smem_bytes(g, sizeof(T));
-    cudaFuncSetAttribute(k_galerkin_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st);
+    auto kern = g.variant == 4 ? k_galerkin_tile<T, 4>
+                               : (g.variant == 5 ? k_galerkin_tile<T, 16> : k_galerkin_tile<T, 8>);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st);
     const int64_t nt = ((g.i_end + 3) >> 2) - (g.i_begin >> 2);
-    k_galerkin_tile<T><<<(unsigned)(nt < 65535 * 16 ? nt : 65535 * 16), 256, st, s>>>(
-        Ahat, Rhat, pmask_k, g, Aout);
+    kern<<<(unsigned)(nt < 65535 * 16 ? nt : 65535 * 16), 256, st, s>>>(Ahat, Rhat, pmask_k, g,
+                                                                       Aout);
   } else if (g.variant == 2) {
     const size_t smem8 = 8 * smem;  // eight warps, one row each
     cudaFuncSetAttribute(k_galerkin_warprow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

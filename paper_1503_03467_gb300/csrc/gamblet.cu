@@ -1015,9 +1015,9 @@ void tune_galerkin_variant(gamblet_ctx* h, int k, GalerkinGeom& gg, const T* Aha
     gt.i_begin = (gg.nrow / 2 / kTuneSampleRows) * kTuneSampleRows;
     gt.i_end = std::min(gt.i_begin + kTuneSampleRows, gg.nrow);
     float best = 1e30f;
-    for (int cand : {0, 1, 2, 3}) {
+    for (int cand : {0, 1, 2, 3, 4, 5}) {
       if (cand == 2 && 8 * sizeof(T) * 4 * ((size_t)gg.NB + gg.nwin) > 227 * 1024) continue;
-      if (cand == 3 && galerkin_tile_smem_bytes(gg, sizeof(T)) > 227 * 1024) continue;
+      if (cand >= 3 && galerkin_tile_smem_bytes(gg, sizeof(T)) > 227 * 1024) continue;
       gt.variant = cand;
       const float ms = time_on_stream(s, [&] {
         launch_galerkin<T>(Ahat, Rhat, h->lv[k].pmask, gt, Acell, s);
@@ -1135,11 +1135,11 @@ void setup_local(gamblet_ctx* h) {
     if (sizeof(T) * 4 * ((size_t)NB + (size_t)gg.nwin) > 227 * 1024)
       fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin window exceeds shared memory");
     T* Acell = P.alloc<T>((int64_t)gg.nout * L.npar);
-    if (h->opts.galerkin_variant >= 0 && h->opts.galerkin_variant <= 3) {
+    if (h->opts.galerkin_variant >= 0 && h->opts.galerkin_variant <= 5) {
       gg.variant = h->opts.galerkin_variant;
       if (gg.variant == 2 && 8 * sizeof(T) * 4 * ((size_t)NB + gg.nwin) > 227 * 1024)
         fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin warp-per-row window exceeds shared memory");
-      if (gg.variant == 3 && galerkin_tile_smem_bytes(gg, sizeof(T)) > 227 * 1024)
+      if (gg.variant >= 3 && galerkin_tile_smem_bytes(gg, sizeof(T)) > 227 * 1024)
         fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin tile window exceeds shared memory");
     } else {
       tune_galerkin_variant<T>(h, k, gg, (const T*)L.Ahat, Rhat, Acell);
@@ -2188,8 +2188,8 @@ gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
       fail(GAMBLET_ERR_INVALID_ARG, "unknown precision");
     if (h->opts.nbr_rule != 0 && h->opts.nbr_rule != 1)
       fail(GAMBLET_ERR_INVALID_ARG, "nbr_rule must be 0 or 1");
-    if (h->opts.galerkin_variant < -1 || h->opts.galerkin_variant > 3)
-      fail(GAMBLET_ERR_INVALID_ARG, "galerkin_variant must be -1, 0, 1, 2 or 3");
+    if (h->opts.galerkin_variant < -1 || h->opts.galerkin_variant > 5)
+      fail(GAMBLET_ERR_INVALID_ARG, "galerkin_variant must be -1 or 0..5");
     if (h->opts.patch_gather < -1 || h->opts.patch_gather > 2)
       fail(GAMBLET_ERR_INVALID_ARG, "patch_gather must be -1, 0, 1 or 2");
     if (h->exact && q > 7)

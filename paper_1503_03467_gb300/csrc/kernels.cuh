@@ -218,7 +218,8 @@ struct GalerkinGeom {
   int64_t nrow;          // stored level-(k-1) cells (4^(k-1) for a full square)
   int64_t i_begin, i_end;  // rows computed: [i_begin, i_end) (all: 0, nrow)
   int variant;           // 0: thread per window position / output, 1: warp-cooperative,
-                         // 2: warp per row, 3: 2 x 2 row tiles
+                         // 2: warp per row, 3, 4, 5: 2 x 2 row tiles with 8, 4 or 16
+                         // lanes per output target
   int tile_wmin, tile_W; // tiles: window box [wmin, wmin + W)^2 from the tile origin
   const int* t1_ptr;     // W * W + 1
   const int2* t1;        // (o, j per row packed in bytes, 0xff = none)
