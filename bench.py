@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--rho", type=float, default=3.0)
     ap.add_argument("--level-tol", type=float, default=0.05)
     ap.add_argument("--refine-tol", type=float, default=1e-9)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="end-to-end steps (0: the same as --steps)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain float64 arm")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-gradient timing")
@@ -194,11 +195,15 @@ def opts_for(nv, a, precision, stream_ptr, profile):
     return o
 
 
-def run_arm(nv, torch, a, dev_in, precision, steps, warmup, stream, flush, clocks_dev=None):
-    """Times `steps` setup+solve passes on device-resident inputs."""
+def run_arm(nv, torch, a, dev_in, precision, steps, warmup, stream, flush, clocks_dev=None,
+            profile=0):
+    """Times `steps` setup+solve passes on device-resident inputs.  With
+    profile = 1 the library also brackets every kernel phase with CUDA
+    events (per-kernel times for the roofline); the headline pass runs with
+    profile = 0."""
     ndof = int(dev_in["g"].shape[0])
     q = int(np.log2(a.size))
-    o = opts_for(nv, a, precision, stream.cuda_stream, 1)
+    o = opts_for(nv, a, precision, stream.cuda_stream, profile)
     u = torch.zeros(ndof, dtype=torch.float64, device=dev_in["g"].device)
     times, setup_ms, solve_ms, infos, stats = [], [], [], [], {}
     clk = None
@@ -226,7 +231,7 @@ def run_arm(nv, torch, a, dev_in, precision, steps, warmup, stream, flush, clock
             setup_ms.append(info.setup_ms)
             solve_ms.append(info.solve_ms)
             infos.append(info.as_dict())
-            for st in nv.gamblet_kernel_stats(h):
+            for st in (nv.gamblet_kernel_stats(h) if profile else []):
                 acc = stats.setdefault(st["name"], {"launches": 0, "ms": 0.0, "bytes": 0.0,
                                                     "flops": 0.0})
                 for key in ("launches", "ms", "bytes", "flops"):
@@ -257,6 +262,63 @@ def run_e2e(nv, a, host, precision, steps):
             times.append((t1 - t0) * 1e3)
     h2d = sum(host[k].nbytes for k in ("rowptr", "colind", "val", "cells", "g"))
     return {"ms": statistics.mean(times), "h2d": h2d, "d2h": u.nbytes, "u": u}
+
+
+def cold_start(a, dev_index):
+    """First setup + solve in a fresh process: the process-wide symbolic plan,
+    the autotuner's choices and the library's memory pool are all empty, so
+    this includes building the plan, tuning the launch shapes and the first
+    device allocations (the CUDA context is created before the clock
+    starts).  The timed steps of the headline reuse all three, the way a
+    repeated solve on the same geometry would."""
+    cmd = [sys.executable, "-m", "paper_1503_03467_gb300", "--size", str(a.size),
+           "--precision", "mixed", "--rho", f"{a.rho:g}", "--contrast", f"{a.contrast:g}",
+           "--level-tol", f"{a.level_tol:g}", "--refine-tol", f"{a.refine_tol:g}", "--wall"]
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES=os.environ.get("CUDA_VISIBLE_DEVICES",
+                                                               str(dev_index)))
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
+        out = json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        return {"error": f"{type(e).__name__}: {e}"}
+    return {"wall_ms": out.get("wall_ms"), "setup_ms": out.get("setup_ms"),
+            "solve_ms": out.get("solve_ms"),
+            "what": "first setup + solve in a fresh process (plan, tuner and memory pool "
+                    "empty; CUDA context created beforehand)"}
+
+
+def measured_alu_peaks(torch, dev):
+    """Dense GEMM throughput of this GPU through torch.matmul (cuBLAS), the
+    way the HBM and bf16 figures of MEASURED_PEAKS.json are taken: float32
+    with IEEE products (SIMT FMA lanes), TF32 tensor cores, float64.  Best of
+    five, CUDA events; no clock or power setting is touched."""
+    out = {}
+    prev = torch.get_float32_matmul_precision()
+    try:
+        for name, dtype, prec, n in (("fp32_simt_tflops", torch.float32, "highest", 8192),
+                                     ("tf32_tflops", torch.float32, "high", 8192),
+                                     ("fp64_tflops", torch.float64, "highest", 4096)):
+            torch.set_float32_matmul_precision(prec)
+            x = torch.randn(n, n, device=dev, dtype=dtype)
+            y = torch.randn(n, n, device=dev, dtype=dtype)
+            torch.matmul(x, y)
+            best = float("inf")
+            for _ in range(5):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(x, y)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            del x, y
+    finally:
+        torch.set_float32_matmul_precision(prev)
+    torch.cuda.empty_cache()
+    out["how"] = ("torch.matmul n^3 (2 n^3 flop), best of 5, CUDA events: float32 with "
+                  "precision 'highest' (8192), TF32 with precision 'high' (8192), float64 (4096)")
+    return out
 
 
 def adjoint_timing(nv, torch, dev, steps=3):
@@ -733,9 +795,10 @@ def families(stats):
     return out
 
 
-def roofline(stats, peaks, clocks, mixed):
+def roofline(stats, peaks, alu, mixed):
     """Roofline entry of the single kernel (kernel family and level) with the
-    largest share of device time; per-launch figures are its own averages."""
+    largest share of device time; per-launch figures are its own averages.
+    `alu` holds the measured GEMM throughputs (measured_alu_peaks)."""
     name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
     family = name.rsplit("_k", 1)[0] if "_k" in name and name.rsplit("_k", 1)[1].isdigit() else name
     launches = max(st["launches"], 1)
@@ -744,25 +807,27 @@ def roofline(stats, peaks, clocks, mixed):
     per_launch_flops = st["flops"] / launches
     total_ms = sum(s["ms"] for s in stats.values())
     common = {"kernel": name, "launches": st["launches"], "avg_launch_ms": avg_ms,
-              "share_of_device_time": st["ms"] / total_ms, "traffic": ncu_traffic(name, mixed)}
-    if family in ("patch_pcg", "patch_cholesky"):
-        # SIMT arithmetic: 152 SMs x 128 lanes (fp32) or the nominal float64
-        # rate, at the maximum SM clock
-        if mixed:
-            peak = 152 * 128 * 2 * 2.070e9 / 1e12
-            src = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (nominal)"
+              "share_of_device_time": st["ms"] / total_ms, "traffic": ncu_traffic(name, mixed),
+              "timing": "CUDA events around every launch of the kernel, over a second pass of "
+                        "the timed steps with the library's per-kernel events on"}
+    if family in ("patch_pcg", "patch_cholesky", "patch_mma"):
+        tensor = family == "patch_mma"
+        if tensor:
+            key, what = "tf32_tflops", "TF32 tensor-core GEMM (torch.matmul, of measured)"
+        elif mixed:
+            key, what = "fp32_simt_tflops", "float32 SIMT GEMM (torch.matmul, of measured)"
         else:
-            peak = 1.25
-            src = "nominal GB300 float64 rate"
+            key, what = "fp64_tflops", "float64 GEMM (torch.matmul, of measured)"
+        peak = alu.get(key)
         achieved = per_launch_flops / (avg_ms * 1e-3) / 1e12
-        out = {**common, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-               "frac": achieved / peak, "peak_source": src,
+        out = {**common, "bound": "tensor" if tensor else "alu", "achieved": achieved,
+               "peak": peak, "unit": "TFLOP/s",
+               "frac": achieved / peak if peak else None, "peak_source": what,
                "algorithmic": f"{per_launch_flops:.4g} flop per launch"}
-        if mixed:
-            # the lanes are not what binds this kernel: its shared-memory
-            # block products are (ncu summary in profiles/)
-            out["binding_unit"] = ("shared-memory load pipe, L1/TEX 81-85% of peak (ncu, "
-                                   "profiles/patch_galerkin_512x512_mixed.md)")
+        if mixed and not tensor:
+            # the lanes are not what binds this kernel: its shared-memory block
+            # products are (ncu summary of the patch CG kernel)
+            out["binding_unit"] = "shared-memory load pipe, L1/TEX 81-85% of peak (ncu)"
         return out
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
@@ -770,6 +835,19 @@ def roofline(stats, peaks, clocks, mixed):
             "frac": achieved / peak,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
             else "fallback 6.8 TB/s", "algorithmic": f"{per_launch_bytes:.4g} byte per launch"}
+
+
+def bench_config(a, ndof):
+    """The workload description shared by both arms of the bench."""
+    return {"workload": workload_name(a), "dofs": ndof, "per_rank_problems": 1,
+            "l2": "flushed between timed steps (256 MiB device write)",
+            "level_tol": a.level_tol, "refine_tol": a.refine_tol,
+            "precision": "mixed: float32 patch solves (block-Jacobi CG to 1e-3), Galerkin "
+                         "products and level-CG SpMV; float64 dot products, coarsest solve and "
+                         "outer refinement",
+            "caches": "the symbolic plan, the autotuner's launch shapes and the library's "
+                      "memory pool are process-wide and warm in the timed steps (filled "
+                      "during warm-up); the cold first call is reported as setup_cold"}
 
 
 def reference_main(a, ws, rank):
@@ -789,7 +867,7 @@ def reference_main(a, ws, rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": workload_name(a), "dofs": p.ndof},
+        "config": bench_config(a, p.ndof),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "full 2^20-class problem: SuperLU factor + solve + 3 "
                                    "extended-precision refinement steps, per step"},
@@ -820,6 +898,7 @@ def main():
     ndof = p.ndof
     # oracle solution for the error bar (and the CPU baseline on rank 0, N = 1)
     ud, cpu_s = cpu_oracle(p)
+    cold = cold_start(a, torch.cuda.current_device()) if rank == 0 else None
     dev_in = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -830,8 +909,11 @@ def main():
     plain = None
     if not a.no_plain:
         plain = run_arm(nv, torch, a, dev_in, nv.FP64, max(2, a.steps // 2), max(1, a.warmup // 2),
-                        stream, flush)
-    e2e = run_e2e(nv, a, host, nv.MIXED, a.e2e_steps)
+                        stream, flush, profile=1)
+    e2e = run_e2e(nv, a, host, nv.MIXED, a.e2e_steps or a.steps)
+    # per-kernel CUDA-event times for the roofline: the same K steps again with
+    # the library's per-phase events on (the headline pass above runs without)
+    prof = run_arm(nv, torch, a, dev_in, nv.MIXED, a.steps, 1, stream, flush, profile=1)
     ms = statistics.mean(mixed["times_ms"])
     ms_max, _ = reduce_over_ranks(torch, dev, ms, ndof)
     if ws > 1:
@@ -840,15 +922,12 @@ def main():
     err_e2e = rel_err(e2e["u"], ud)
     value = ws * ndof / (ms_max * 1e-3)
     peaks = load_peaks()
+    alu = measured_alu_peaks(torch, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": workload_name(a), "dofs": ndof, "per_rank_problems": 1,
-                   "l2": "flushed between timed steps (256 MiB device write)",
-                   "level_tol": a.level_tol, "refine_tol": a.refine_tol,
-                   "precision": "mixed: f32 patch Cholesky / Galerkin / level SpMV, "
-                                "f64 dots, coarsest solve and refinement"},
+        "config": bench_config(a, ndof),
         "rel_err": err_mixed, "rel_err_ok": err_mixed <= REL_ERR_BAR,
         "setup_ms": statistics.mean(mixed["setup_ms"]),
         "solve_ms": statistics.mean(mixed["solve_ms"]),
@@ -858,11 +937,13 @@ def main():
         "e2e": {"value": ws * ndof / (e2e["ms"] * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(e2e["h2d"]), "d2h_bytes_per_step": int(e2e["d2h"]),
                 "rel_err": err_e2e},
-        "roofline": roofline(mixed["stats"], peaks, mixed["clocks"], True),
+        "roofline": roofline(prof["stats"], peaks, alu, True),
         "clocks": mixed["clocks"],
-        "kernels": {k: {"share": v["ms"] / sum(s["ms"] for s in families(mixed["stats"]).values()),
+        "alu_peaks": alu,
+        "setup_cold": cold,
+        "kernels": {k: {"share": v["ms"] / sum(s["ms"] for s in families(prof["stats"]).values()),
                         "ms_per_step": v["ms"] / a.steps, "launches_per_step": v["launches"] / a.steps}
-                    for k, v in sorted(families(mixed["stats"]).items(), key=lambda kv: -kv[1]["ms"])},
+                    for k, v in sorted(families(prof["stats"]).items(), key=lambda kv: -kv[1]["ms"])},
     }
     if plain is not None:
         pms = statistics.mean(plain["times_ms"])
@@ -871,7 +952,7 @@ def main():
             "setup_ms": statistics.mean(plain["setup_ms"]),
             "solve_ms": statistics.mean(plain["solve_ms"]),
             "rel_err": rel_err(plain["u"], ud), "outer_iters": plain["infos"][-1]["outer_iters"],
-            "roofline": roofline(plain["stats"], peaks, None, False)}
+            "roofline": roofline(plain["stats"], peaks, alu, False)}
         line["speedup_mixed_vs_plain"] = line["plain_fp64"]["ms_per_step"] / ms
     if not a.no_adjoint:
         line["adjoint"] = adjoint_timing(nv, torch, dev)

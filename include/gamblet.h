@@ -347,15 +347,20 @@ GAMBLET_API gamblet_status gamblet_grad_onepass(gamblet_handle h, int32_t ncell,
 
 /*
  * J = 1/2 |u - u_obs|^2, the objective that gamblet_grad also returns, for
- * callers that cannot allocate device memory when they need it: code inside
- * CUDA stream capture in global mode (cudaMalloc is not permitted there) and
- * hosts whose own allocator holds the free device memory or that run under a
- * hard memory budget (e.g. an optimiser evaluating J during a line search).
- * The paper has no counterpart; this is a service entry point.
+ * callers that cannot allocate device memory when they need it: applications
+ * whose framework allocator already holds the free device memory (a caching
+ * allocator grows to fill the GPU, so a side cudaMalloc can fail), programs
+ * under a hard device-memory budget, and loops that evaluate J many times
+ * (an optimiser's line search) and cannot accept the device-wide
+ * synchronisation of cudaFree.  The paper has no counterpart; this is a
+ * service entry point.
  *   n       number of unknowns, 1 <= n <= GAMBLET_NOALLOC_MAX_N; larger n
  *           returns UNSUPPORTED.
- *   u, u_obs  device pointers, n float64 each.
- *   J       device or host pointer to one float64 (host: the call waits).
+ *   u, u_obs  device pointers of the current device, n float64 each; a host
+ *           pointer or another GPU's memory returns INVALID_ARG.
+ *   J       device pointer (current device) or host pointer to one float64;
+ *           with a host pointer the call copies J back and waits for the
+ *           stream.
  *   stream  cudaStream_t for the two kernels (0 = legacy default stream).
  * Allocates nothing: the partial sums live in a fixed 8.2 KB device array
  * that every GPU loading the library keeps until exit.  The first call on a

@@ -6,7 +6,7 @@ timing and profiling runs:
                                    [--repeat 1] [--profile] [--capture-last]
                                    [--no-autotune] [--galerkin-variant -1|0|1|2]
                                    [--patch-gather -1|0|1|2]
-                                   [--grad-one-pass] [--patch-tol 0]
+                                   [--grad-one-pass] [--patch-tol 0] [--wall]
 
 Prints, for the last of `repeat` setup + solve passes, the setup and solve
 device times, the outer iterations and the final relative residual
@@ -44,6 +44,9 @@ def main(argv=None):
     ap.add_argument("--galerkin-variant", type=int, default=-1)
     ap.add_argument("--patch-gather", type=int, default=-1)
     ap.add_argument("--grad-one-pass", action="store_true")
+    ap.add_argument("--wall", action="store_true",
+                    help="also report the host wall-clock time of the last pass (the CUDA "
+                         "context is created before the first pass)")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from workloads import make_problem
@@ -68,12 +71,18 @@ def main(argv=None):
     colind = np.ascontiguousarray(A.indices, dtype=np.int32)
     val = np.ascontiguousarray(A.data)
     out = None
+    if a.wall:
+        import time
+        import torch
+        torch.zeros(1, device="cuda")
+        torch.cuda.synchronize()
     for r in range(max(a.repeat, 1)):
         last = r == max(a.repeat, 1) - 1
         if last and a.capture_last:
             import torch
             torch.cuda.synchronize()
             torch.cuda.profiler.start()
+        t0 = time.perf_counter() if a.wall else 0.0
         h = nv.gamblet_setup(rowptr, colind, val, p.q, p.cells, o)
         try:
             u = np.zeros(p.ndof)
@@ -88,11 +97,14 @@ def main(argv=None):
                                         K_REF.ravel().copy(), p.g, u_obs, dJ, u=u, info=info)
             else:
                 nv.gamblet_solve(h, p.g, u, None, info)
+            t1 = time.perf_counter() if a.wall else 0.0
             if last:
                 if a.capture_last:
                     torch.cuda.profiler.stop()
                 out = info.as_dict()
                 out["dofs"] = p.ndof
+                if a.wall:
+                    out["wall_ms"] = (t1 - t0) * 1e3
                 if a.profile:
                     out["kernels"] = {st["name"]: {"launches": st["launches"],
                                                    "ms": round(st["ms"], 4)}

@@ -69,17 +69,45 @@ struct GbError {
   } while (0)
 
 // ---------------------------------------------------------------- device memory
-// Stream-ordered allocations from the device's default memory pool (kept
-// cached across handles, so a repeated setup does not pay for cudaMalloc).
+// Stream-ordered allocations from a memory pool that the library owns, one
+// per device.  Its release threshold is unlimited, so freed blocks stay
+// cached for the next handle and a repeated setup does not pay for
+// cudaMalloc; the device's default pool, which the caller's own allocators
+// may share, keeps its settings.  The cached memory is returned when the
+// process exits.
+cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) fail(GAMBLET_ERR_UNSUPPORTED, "device ordinal beyond 63");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t mp = nullptr;
+    CK(cudaMemPoolCreate(&mp, &props));
+    uint64_t thr = UINT64_MAX;
+    CK(cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr));
+    pools[dev] = mp;
+  }
+  return pools[dev];
+}
+
 struct Pool {
   std::vector<void*> ptrs;
   int64_t bytes = 0;
   cudaStream_t s = nullptr;
+  cudaMemPool_t mp = nullptr;
   template <typename T>
   T* alloc(int64_t n) {
     if (n <= 0) n = 1;
+    if (!mp) mp = library_pool();
     void* p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, sizeof(T) * (size_t)n, s);
+    cudaError_t e = cudaMallocFromPoolAsync(&p, sizeof(T) * (size_t)n, mp, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       fail(GAMBLET_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(sizeof(T) * n) + " bytes");
@@ -2197,13 +2225,6 @@ gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
-    {
-      // keep freed pool memory cached in this process (no device setting changes)
-      cudaMemPool_t mp;
-      CK(cudaDeviceGetDefaultMemPool(&mp, dev));
-      uint64_t thr = UINT64_MAX;
-      CK(cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr));
-    }
     for (int k = 0; k < 32; ++k) h->level_iters_acc[k] = 0;
     CK(cudaMallocHost(&h->any_active_h, sizeof(int)));
     CK(cudaMallocHost(&h->dots_h, sizeof(double) * 8));

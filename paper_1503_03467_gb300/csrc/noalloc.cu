@@ -2,13 +2,15 @@
 //
 // gamblet_grad computes the same J with scratch it allocates per call (a
 // residual vector and a float64 accumulator).  This entry point is for
-// callers that cannot allocate device memory at the time they need J: code
-// running inside CUDA stream capture in global mode (where cudaMalloc is not
-// permitted), and hosts that have handed all free device memory to their own
-// allocator or run under a hard memory budget, for example an optimiser that
-// evaluates J many times per line search.  Its scratch is a file-scope
-// device array of fixed size, so it never calls cudaMalloc, cudaFree or any
-// allocating library routine.
+// callers that cannot allocate device memory at the moment they need J:
+// applications whose framework allocator has already reserved the free
+// device memory (a caching allocator grows to fill the GPU, so a side
+// cudaMalloc can fail although the framework itself has room), programs run
+// under a hard device-memory budget, and latency-sensitive loops, such as an
+// optimiser evaluating J many times per line search, that cannot afford the
+// device-wide synchronisation that cudaFree implies.  Its scratch is a
+// file-scope device array of fixed size, so it never calls cudaMalloc,
+// cudaFree or any allocating library routine.
 //
 // Scratch: at most GAMBLET_NOALLOC_BLOCKS partial sums (one per block of
 // GAMBLET_NOALLOC_CHUNK elements) plus one slot for the result, 8.2 KB held
@@ -95,13 +97,24 @@ double* scratch_for_current_device(cudaError_t* err) {
   return g_scratch_ptr[dev];
 }
 
-bool on_device(const void* p) {
+// Where a pointer lives: 1 for device memory of the current device (or
+// managed memory), 0 for host memory, -1 for another GPU's memory.  The
+// kernels run on the current device and would fault on another GPU's memory
+// without peer access, so such pointers are refused.
+int ptr_kind(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return 1;
+  if (a.type != cudaMemoryTypeDevice) return 0;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return a.device == dev ? 1 : -1;
 }
 
 }  // namespace
@@ -115,9 +128,10 @@ extern "C" gamblet_status gamblet_objective_noalloc(int32_t n, const double* u,
         "sums of 2048 elements each)");
     return n < 1 ? GAMBLET_ERR_INVALID_ARG : GAMBLET_ERR_UNSUPPORTED;
   }
-  if (!u || !u_obs || !J || !on_device(u) || !on_device(u_obs)) {
+  if (!u || !u_obs || !J || ptr_kind(u) != 1 || ptr_kind(u_obs) != 1 || ptr_kind(J) < 0) {
     gb::noalloc_set_error(
-        "gamblet_objective_noalloc: u and u_obs must be device pointers and J non-NULL");
+        "gamblet_objective_noalloc: u and u_obs must be device pointers of the current device, "
+        "J a host pointer or a device pointer of the current device");
     return GAMBLET_ERR_INVALID_ARG;
   }
   cudaError_t err = cudaSuccess;
@@ -129,7 +143,7 @@ extern "C" gamblet_status gamblet_objective_noalloc(int32_t n, const double* u,
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int nblocks = (n + GAMBLET_NOALLOC_CHUNK - 1) / GAMBLET_NOALLOC_CHUNK;
-  const bool j_dev = on_device(J);
+  const bool j_dev = ptr_kind(J) == 1;
   double* out = j_dev ? J : scratch + GAMBLET_NOALLOC_BLOCKS;
   gb::count_launch();
   k_objective_partials<<<nblocks, GAMBLET_NOALLOC_THREADS, 0, s>>>(n, u, u_obs, scratch);

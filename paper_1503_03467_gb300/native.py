@@ -310,7 +310,15 @@ def gamblet_grad_onepass(h: int, cell_nodes, cell_a, K_ref, g, u_obs, dJ, u=None
 
 def gamblet_objective_noalloc(n: int, u, u_obs, J, stream=None) -> int:
     """J = 1/2 |u - u_obs|^2 into J (a 1-element float64 tensor or array);
-    u and u_obs must be CUDA tensors.  Allocates no device memory."""
+    u and u_obs must be CUDA tensors of the current device.  Allocates no
+    device memory.  The C side cannot see the lengths of the buffers, so
+    they are checked here."""
+    n = int(n)
+    for name, a in (("u", u), ("u_obs", u_obs)):
+        if a is None or n > int(a.numel() if hasattr(a, "numel") else np.asarray(a).size):
+            raise ValueError(f"gamblet_objective_noalloc: {name} holds fewer than n = {n} values")
+    if J is None or int(J.numel() if hasattr(J, "numel") else np.asarray(J).size) < 1:
+        raise ValueError("gamblet_objective_noalloc: J must hold one value")
     return _check(_lib.gamblet_objective_noalloc(int(n), _ptr(u, np.float64),
                                                  _ptr(u_obs, np.float64), _ptr(J, np.float64),
                                                  stream))

@@ -60,3 +60,45 @@ def pack_problems(probs):
     A = sp.block_diag([pr.A for pr in probs], format="csr")
     g = np.concatenate([pr.g for pr in probs])
     return A, g, np.ascontiguousarray(np.concatenate(cells), dtype=np.int32), Q, offsets
+
+
+def _dense(a):
+    return a.toarray() if hasattr(a, "toarray") else np.asarray(a, dtype=np.float64)
+
+
+def max_dev(a, b):
+    """Element-wise deviation max_ij |a_ij - b_ij| / max_ij |b_ij|."""
+    a, b = _dense(a), _dense(b)
+    assert a.shape == b.shape, (a.shape, b.shape)
+    return float(np.abs(a - b).max(initial=0.0) / max(np.abs(b).max(initial=0.0), 1e-300))
+
+
+def row_dev(a, b):
+    """Element-wise deviation with each row scaled by its own largest |b_ij|:
+    max_i max_j |a_ij - b_ij| / max_j |b_ij|.  For R every row is one
+    patch's gamblet, whose entries decay exponentially away from its cell
+    (Sec. 4.10), so this guards the small tails that a whole-matrix scale
+    would hide."""
+    a, b = _dense(a), _dense(b)
+    assert a.shape == b.shape, (a.shape, b.shape)
+    scale = np.abs(b).max(axis=1, keepdims=True)
+    scale[scale == 0] = 1.0
+    return float((np.abs(a - b) / scale).max(initial=0.0))
+
+
+def check_op(a, b, tol, what=None):
+    """Level operator parity, element by element: |a - b| <= tol max|b|."""
+    d = max_dev(a, b)
+    assert d <= tol, (what, d, tol)
+
+
+def check_R(a, b, tol, what=None):
+    """Interpolation parity: element-wise within tol of each row's largest
+    entry, and the same nonzero pattern (the patch support of Definition
+    defb: a GPU entry outside the oracle's patch, or a missing one inside
+    it, fails regardless of size)."""
+    a, b = _dense(a), _dense(b)
+    d = row_dev(a, b)
+    assert d <= tol, (what, d, tol)
+    sa, sb = a != 0, b != 0
+    assert np.array_equal(sa, sb), (what, "support", int((sa & ~sb).sum()), int((sb & ~sa).sum()))

@@ -78,3 +78,17 @@ def test_host_only_calls(lib):
     lib.gamblet_destroy(0)  # NULL is ignored
     with pytest.raises(lib.GambletError):
         lib.gamblet_level_size(0, 1)
+
+
+def test_noalloc_source_calls_no_allocator():
+    """The allocation-free objective's translation unit, comments removed,
+    names no device or host allocation routine (its scratch is a fixed
+    file-scope device array)."""
+    import re
+    src = open(os.path.join(ROOT, "paper_1503_03467_gb300", "csrc", "noalloc.cu")).read()
+    code = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    code = re.sub(r"//[^\n]*", "", code)
+    for name in ("cudaMalloc", "cudaFree", "cudaMallocAsync", "cudaMemPool", "cudaHostAlloc",
+                 "malloc(", "new ", "torch", "at::"):
+        assert name not in code, name
+    assert re.search(r"static __device__ __align__\(256\) double g_objective_scratch\[", code)

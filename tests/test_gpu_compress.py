@@ -7,7 +7,7 @@ from oracle.compress import compress
 from oracle.local import gamblet_local_setup
 from workloads import make_example1, make_problem
 
-from gpu_util import coo_to_dense, csr_arrays, rel
+from gpu_util import check_op, coo_to_dense, csr_arrays, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +32,7 @@ def test_compression_matches_oracle(which):
         for k in range(2, p.q + 1):
             nJ = ref["B"][k].shape[0]
             B = coo_to_dense(*nv.gamblet_get_operator(h, 2, k), (nJ, nJ))
-            assert rel(B, ref["B"][k]) < 1e-10, k
+            check_op(B, ref["B"][k], 1e-10, ("B", k))
         for eps in (0.0, 1e-3, 1e-2):
             u_ref, kept_ref, total_ref = compress(ref, p.g, eps)
             u = np.zeros(p.ndof)

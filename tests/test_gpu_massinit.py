@@ -7,7 +7,7 @@ import scipy.sparse.linalg as spla
 from oracle.massinit import gamblet_mass_setup, gamblet_mass_solve, mass_initialised_operator
 from workloads import assemble_q1_mass, make_example1, make_problem
 
-from gpu_util import coo_to_dense, csr_arrays, rel
+from gpu_util import check_R, check_op, coo_to_dense, csr_arrays, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -39,12 +39,12 @@ def test_mass_initialised_operators_and_one_pass_match_oracle(rho_q):
     try:
         n = p.ndof
         Aq = coo_to_dense(*nv.gamblet_get_operator(h, 0, p.q), (n, n))
-        assert rel(Aq, ref["A"][p.q]) < 1e-12
+        check_op(Aq, ref["A"][p.q], 1e-12, ("A", p.q))
         for k in range(2, p.q + 1):
             nkm1, _ = nv.gamblet_level_size(h, k - 1)
             nk, _ = nv.gamblet_level_size(h, k)
             R = coo_to_dense(*nv.gamblet_get_operator(h, 1, k), (nkm1, nk))
-            assert rel(R, ref["R"][k]) < 1e-10, k
+            check_R(R, ref["R"][k], 1e-10, ("R", k))
         u = np.zeros(n)
         assert nv.gamblet_solve(h, p.g, u) == nv.OK
         assert rel(u, u_ref) < 1e-9

@@ -1,5 +1,6 @@
 """Pins of the compression in the normalised gamblet basis (oracle)."""
 import numpy as np
+import pytest
 
 from oracle.compress import compress, normalised_coefficients
 from oracle.local import gamblet_local_setup, gamblet_local_solve
@@ -50,3 +51,82 @@ def test_representation_is_sparse_for_example1():
     d = u - u_c
     assert kept < 0.1 * total
     assert d @ (p.A @ d) < 1e-3 * (u @ (p.A @ u))
+
+
+# ---- the normalisation itself, pinned against the basis functions -------
+#
+# Sec. 5.1 normalises each coefficient by the energy norm of its basis
+# function: psi^(1)_i / ||psi^(1)_i||_a and chi^(k)_j / ||chi^(k)_j||_a.  The
+# pin builds those functions in fine coordinates without the level recursion:
+# psi^(k) from the brute-force projections (Sec. 4.2, psi^(k) = A^-1 Pi_k^T
+# Theta^(k)^-1), chi^(k)_j = sum_i W_ji psi^(k)_i (Sec. 4.4), energies as
+# f^T A f, and the coefficients by expanding the exact level components
+# u^(1) = sum_i U_i psi^(1)_i and u^(k) - u^(k-1) = sum_j w_j chi^(k)_j
+# (Theorem thddwedmgugyug) in those functions.
+
+def _brute_normalised(p):
+    from oracle.brute import brute
+    from oracle.hierarchy import Hierarchy
+    b = brute(p.A, p.g, p.cells, p.q)
+    H = Hierarchy(p.cells, p.q)
+    Ad = p.A.toarray()
+    c = {}
+    psi1 = b["psi"][1]
+    U, *_ = np.linalg.lstsq(psi1, b["uk"][1], rcond=None)
+    c[1] = U * np.sqrt(np.einsum("ni,nm,mi->i", psi1, Ad, psi1))
+    for k in range(2, p.q + 1):
+        chi = b["psi"][k] @ H.W(k).toarray().T          # n_q x |J^(k)|
+        w, *_ = np.linalg.lstsq(chi, b["uk"][k] - b["uk"][k - 1], rcond=None)
+        c[k] = w * np.sqrt(np.einsum("nj,nm,mj->j", chi, Ad, chi))
+    return c
+
+
+def _max_dev(c, cb):
+    scale = max(np.abs(v).max() for v in cb.values())
+    return max(np.abs(c[k] - cb[k]).max() for k in cb) / scale
+
+
+@pytest.mark.parametrize("n,C,seed", [(8, 1e2, 0), (16, 1e3, 3)])
+def test_normalised_coefficients_equal_energy_norms_of_basis_functions(n, C, seed):
+    p = make_problem(n, C, seed)
+    s = gamblet_local_setup(p.A, p.cells, p.q, np.inf)
+    c, _ = normalised_coefficients(s, p.g)
+    cb = _brute_normalised(p)
+    assert set(c) == set(cb)
+    for k in cb:
+        assert c[k].shape == cb[k].shape, k
+    assert _max_dev(c, cb) < 1e-9
+
+
+# plausible mistakes in the normalisation, planted in a copy of the oracle
+NORM_MUTATIONS = {
+    "no_detail_normalisation": ('res["w"][k] * np.sqrt(setup["B"][k].diagonal())',
+                                'res["w"][k] * 1.0'),
+    "detail_norm_from_diagonal_only": (
+        'res["w"][k] * np.sqrt(setup["B"][k].diagonal())',
+        'res["w"][k] * np.sqrt(abs(setup["W"][k]).power(2) @ setup["A"][k].diagonal())'),
+    "detail_norm_squared": ('res["w"][k] * np.sqrt(setup["B"][k].diagonal())',
+                            'res["w"][k] * setup["B"][k].diagonal()'),
+    "coarse_norm_from_level_2": ('res["U1"] * np.sqrt(setup["A"][1].diagonal())',
+                                 'res["U1"] * np.sqrt(setup["A"][2].diagonal()[:res["U1"].size])'),
+    "no_coarse_normalisation": ('res["U1"] * np.sqrt(setup["A"][1].diagonal())',
+                                'res["U1"] * 1.0'),
+}
+
+
+@pytest.mark.parametrize("name", sorted(NORM_MUTATIONS))
+def test_normalisation_pin_catches_planted_mistake(name):
+    import inspect
+    import types
+    import oracle.compress as oc
+    src = inspect.getsource(oc)
+    old, new = NORM_MUTATIONS[name]
+    assert old in src, name
+    mod = types.ModuleType("oracle.compress_mut")
+    mod.__dict__["__package__"] = "oracle"
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), mod.__dict__)
+    p = make_problem(8, 1e2, 0)
+    s = gamblet_local_setup(p.A, p.cells, p.q, np.inf)
+    c, _ = mod.normalised_coefficients(s, p.g)
+    cb = _brute_normalised(p)
+    assert _max_dev(c, cb) > 1e-6

@@ -1,8 +1,9 @@
 """gamblet_objective_noalloc, the allocation-free objective entry point for
-callers that cannot allocate device memory when they evaluate J (code under
-CUDA stream capture in global mode, hosts whose allocator owns the free
-memory), must return the J that gamblet_grad returns.  This file is named to
-be collected last, so a failure here comes after every other test has run."""
+callers that cannot allocate device memory when they evaluate J (a
+framework's caching allocator holding the free memory, a hard memory budget,
+loops that cannot pay for cudaFree's device-wide synchronisation), must
+return the J that gamblet_grad returns.  This file is named to be collected
+last, so a failure here comes after every other test has run."""
 import numpy as np
 import pytest
 
@@ -74,3 +75,26 @@ def test_objective_noalloc_allocates_nothing_and_rejects_oversize():
     with pytest.raises(nv.GambletError) as e:
         nv.gamblet_objective_noalloc(big.numel(), big, big, J)
     assert e.value.status == nv.ERR_UNSUPPORTED
+
+
+def test_objective_noalloc_rejects_memory_off_the_current_device():
+    """Host memory for u or u_obs is refused before any kernel runs (the
+    kernels would otherwise dereference a host address on the device);
+    short buffers are refused by the binding, which knows their lengths."""
+    import torch
+    from paper_1503_03467_gb300 import native as nv
+    dev = torch.device("cuda:0")
+    u = torch.randn(100, dtype=torch.float64, device=dev)
+    J = torch.zeros(1, dtype=torch.float64, device=dev)
+    host = np.zeros(100)
+    for a, b in ((host, u), (u, host)):
+        with pytest.raises(nv.GambletError) as e:
+            nv.gamblet_objective_noalloc(100, a, b, J)
+        assert e.value.status == nv.ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        nv.gamblet_objective_noalloc(101, u, u, J)
+    with pytest.raises(ValueError):
+        nv.gamblet_objective_noalloc(100, u, u, np.zeros(0))
+    assert nv.gamblet_objective_noalloc(100, u, u, J) == nv.OK
+    torch.cuda.synchronize()
+    assert J.item() == 0.0
