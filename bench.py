@@ -813,17 +813,26 @@ def roofline(stats, peaks, alu, mixed):
     if family in ("patch_pcg", "patch_cholesky", "patch_mma"):
         tensor = family == "patch_mma"
         if tensor:
-            key, what = "tf32_tflops", "TF32 tensor-core GEMM (torch.matmul, of measured)"
+            # kind::f16 products: the dense float16 rate equals the bf16 rate
+            peak = peaks.get("bf16_tflops")
+            what = "dense bf16/fp16 tensor-core GEMM, MEASURED_PEAKS.json bf16_tflops (of measured)"
         elif mixed:
-            key, what = "fp32_simt_tflops", "float32 SIMT GEMM (torch.matmul, of measured)"
+            peak = alu.get("fp32_simt_tflops")
+            what = "float32 SIMT GEMM (torch.matmul, of measured)"
         else:
-            key, what = "fp64_tflops", "float64 GEMM (torch.matmul, of measured)"
-        peak = alu.get(key)
+            peak = alu.get("fp64_tflops")
+            what = "float64 GEMM (torch.matmul, of measured)"
         achieved = per_launch_flops / (avg_ms * 1e-3) / 1e12
         out = {**common, "bound": "tensor" if tensor else "alu", "achieved": achieved,
                "peak": peak, "unit": "TFLOP/s",
                "frac": achieved / peak if peak else None, "peak_source": what,
-               "algorithmic": f"{per_launch_flops:.4g} flop per launch"}
+               "algorithmic": f"{per_launch_flops:.4g} flop per launch" + (
+                   " (tensor-core products issued: windows x iterations x M-tiles x "
+                   "2 x 128 x 16 x K)" if tensor else "")}
+        if tensor:
+            out["binding_unit"] = ("per-iteration latency of the window CG (block reductions, "
+                                   "barriers, product issue); N = 16 products use a fraction "
+                                   "of the pipe by construction")
         if mixed and not tensor:
             # the lanes are not what binds this kernel: its shared-memory block
             # products are (ncu summary of the patch CG kernel)
@@ -938,6 +947,8 @@ def main():
                 "h2d_bytes_per_step": int(e2e["h2d"]), "d2h_bytes_per_step": int(e2e["d2h"]),
                 "rel_err": err_e2e},
         "roofline": roofline(prof["stats"], peaks, alu, True),
+        "roofline_patch": roofline({k: v for k, v in prof["stats"].items()
+                                    if k.startswith("patch_")} or prof["stats"], peaks, alu, True),
         "clocks": mixed["clocks"],
         "alu_peaks": alu,
         "setup_cold": cold,

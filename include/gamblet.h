@@ -106,8 +106,17 @@ typedef struct {
                                kernel on every level (3, 4, 5: the tile
                                kernel with 8, 4, 16 lanes per output;
                                see gamblet_launch_shapes)                  */
-  int32_t patch_gather;     /* -1: automatic; 0, 1, 2: use that patch-CG
-                               block gather on every level                 */
+  int32_t patch_gather;     /* -1: automatic; 0, 1, 2: use the SIMT patch
+                               CG with that block gather on every level;
+                               3, 4: the tensor-core patch solves
+                               (tcgen05, float16 block-Jacobi-scaled patch
+                               matrices, float32 accumulation) with windows
+                               of 1 x 1 or 2 x 2 coarse cells per CTA on
+                               every level - mixed path only, UNSUPPORTED
+                               otherwise.  Automatic considers the
+                               tensor-core solves on the mixed path when
+                               patch_tol >= 4.8e-4 (their float16 rounding
+                               of the scaled matrix is 2^-11 relative)     */
   void* stream;             /* cudaStream_t                                */
 } gamblet_opts;
 
@@ -396,9 +405,11 @@ GAMBLET_API gamblet_status gamblet_assemble_cells(int32_t n, const int32_t* rowp
 
 /* Launch shapes the setup used at level k (2 <= k <= q, localized
  * transform), chosen by the autotuner or by the fixed rules:
- *   shapes[0]  patch-CG threads per neighbour parent (1, 2, 4; 0 = Cholesky)
+ *   shapes[0]  patch-CG threads per neighbour parent (1, 2, 4; 0 = Cholesky or
+ *              tensor-core patch solves)
  *   shapes[1]  patch-CG block gather (0 thread per block, 1 half-warp per block,
- *              2 four lanes per block)
+ *              2 four lanes per block), or 3, 4 for the tensor-core patch
+ *              solves with windows of 1 x 1 or 2 x 2 coarse cells
  *   shapes[2]  Galerkin kernel (0 thread per position, 1 warp-cooperative,
  *              2 warp per row, 3, 4, 5 2 x 2 row tiles with 8, 4, 16 lanes
  *              per output target)

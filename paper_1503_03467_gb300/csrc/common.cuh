@@ -42,6 +42,8 @@ __host__ __device__ __forceinline__ int __popc_portable(unsigned v) {
 enum DevStatus : int {
   DEV_OK = 0,
   DEV_NOT_SPD = 1,   // non-positive pivot in a factorisation
+  DEV_TIMEOUT = 2,   // a bounded wait on an asynchronous unit (tensor-core
+                     // completion barrier) gave up; the kernel returned early
 };
 
 // ---------------------------------------------------------------- Morton

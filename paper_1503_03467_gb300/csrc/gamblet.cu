@@ -420,6 +420,7 @@ struct gamblet_ctx {
   int patch_iters_max = 0;
   double patch_iters_mean = 0;
   std::vector<double> patch_flops_iter_k;  // per level: flops of one iteration of one patch
+  std::vector<double> patch_mma_flops_k;   // per level: tensor-core flops of one window product
   int level_iters_acc[32];
   bool level_not_conv = false;
   const char* dplan = nullptr;  // device copy of the plan tables (localized setup)
@@ -437,6 +438,8 @@ void check_status(gamblet_ctx* h, const char* where) {
   CK(cudaStreamSynchronize(h->s));
   if (*h->status_h == DEV_NOT_SPD)
     fail(GAMBLET_ERR_NOT_SPD, std::string("non-positive pivot in ") + where);
+  if (*h->status_h == DEV_TIMEOUT)
+    fail(GAMBLET_ERR_CUDA, std::string("a tensor-core completion wait gave up in ") + where);
 }
 
 // ------------------------------------------------------------ symbolic build
@@ -721,8 +724,23 @@ void outer_spmv(gamblet_ctx* h, const double* xhat, double* yhat) {
 // patch block lists and the Galerkin pair lists of every level.  It does not
 // depend on coefficient values, so it is built once per geometry and kept in
 // a process-wide cache (like an FFT plan).
+// Tables of the tensor-core patch solves (patch_mma.cu) for windows of G x G
+// coarse cells, G = 1 and 2: the union of the windows' neighbourhoods, which
+// patches each union parent belongs to, the stored blocks between union
+// parents, the right-hand-side blocks and the union index of every patch
+// neighbour.  All are offsets, so one table serves every window of the level.
+struct MmaWin {
+  bool ok = false;  // fits one CTA (at most three M-tiles and the shared memory)
+  int NP = 0, nU = 0, n = 0, Kp = 0, Mt = 0, diag_o = -1;
+  std::vector<int2> U;
+  std::vector<int> ubits, rhs_o, outmap;
+  std::vector<int4> pairs;
+  size_t off[5] = {};  // U, ubits, pairs, rhs_o, outmap in Plan::packed
+};
+
 struct PlanLevel {
   SymLevel S;
+  MmaWin mwin[2];  // G = 1, G = 2
   std::vector<int4> half, adj;   // patch CG: stored blocks and per-row adjacency
   std::vector<int> adj_ptr, diag_h;
   int spp = 1;
@@ -822,6 +840,55 @@ void assign_bank_slots(PlanLevel& pl, int NB) {
   for (int& d : pl.diag_h) d = slot[d];
 }
 
+size_t patch_mma_smem_bytes_of(const MmaWin& W, int NB) {
+  PatchMmaGeom g{};
+  g.NP = W.NP;
+  g.nU = W.nU;
+  g.n = W.n;
+  g.Kp = W.Kp;
+  g.Mt = W.Mt;
+  g.NB = NB;
+  return patch_mma_smem_bytes(g);
+}
+
+void build_mma_window(MmaWin& W, int G, const OffSet& O, const OffSet& N) {
+  const int NB = N.size();
+  W.NP = G * G;
+  std::vector<int2> cell(W.NP);
+  for (int c = 0; c < W.NP; ++c) cell[c] = make_int2(c & 1, c >> 1);
+  std::map<std::pair<int, int>, int> bits;  // (dy, dx) -> patch bits, row-major order
+  for (int c = 0; c < W.NP; ++c)
+    for (const int2& o : N.v) bits[{cell[c].y + o.y, cell[c].x + o.x}] |= 1 << c;
+  OffSet U;
+  W.U.clear();
+  W.ubits.clear();
+  for (const auto& kv : bits) {
+    U.add(kv.first.second, kv.first.first);
+    W.U.push_back(make_int2(kv.first.second, kv.first.first));
+    W.ubits.push_back(kv.second);
+  }
+  W.nU = U.size();
+  W.n = 3 * W.nU;
+  W.Kp = (W.n + 15) / 16 * 16;
+  W.Mt = (W.n + 127) / 128;
+  W.diag_o = O.find(0, 0);
+  W.pairs.clear();
+  for (int a = 0; a < W.nU; ++a)
+    for (int b = 0; b < a; ++b) {
+      const int o = O.find(W.U[b].x - W.U[a].x, W.U[b].y - W.U[a].y);
+      if (o >= 0) W.pairs.push_back(make_int4(a, b, o, 0));
+    }
+  W.rhs_o.assign((size_t)W.NP * W.nU, -1);
+  for (int c = 0; c < W.NP; ++c)
+    for (int u = 0; u < W.nU; ++u)
+      W.rhs_o[(size_t)c * W.nU + u] = O.find(cell[c].x - W.U[u].x, cell[c].y - W.U[u].y);
+  W.outmap.assign((size_t)W.NP * NB, 0);
+  for (int c = 0; c < W.NP; ++c)
+    for (int j = 0; j < NB; ++j)
+      W.outmap[(size_t)c * NB + j] = U.find(cell[c].x + N.v[j].x, cell[c].y + N.v[j].y);
+  W.ok = W.diag_o >= 0 && W.Mt <= 3 && patch_mma_smem_bytes_of(W, NB) <= 227 * 1024;
+}
+
 std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
                                        const std::string& key) {
   auto plan = std::make_shared<Plan>();
@@ -856,6 +923,7 @@ std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
     while (pl.spp > 1 && NB * pl.spp > 256) pl.spp >>= 1;
     pl.flops_iter = 18.0 * (2.0 * pl.half.size() - NB) + 60.0 * NB;
     assign_bank_slots(pl, NB);
+    for (int gi = 0; gi < 2; ++gi) build_mma_window(pl.mwin[gi], gi + 1, pl.S.O, N);
     if (k - 1 >= 2) {
       pl.O_next = blocks_from_cells(pl.S.S, pl.S.Sp, k - 1, pl.map_next);
       O = pl.O_next;
@@ -895,6 +963,13 @@ std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
     pl.table_off[PlanLevel::kT2p] = put_v(S.t2p);
     pl.table_off[PlanLevel::kOffNext] = put_v(pl.O_next.v);
     pl.table_off[PlanLevel::kMapNext] = put_v(pl.map_next);
+    for (MmaWin& W : pl.mwin) {
+      W.off[0] = put_v(W.U);
+      W.off[1] = put_v(W.ubits);
+      W.off[2] = put_v(W.pairs);
+      W.off[3] = put_v(W.rhs_o);
+      W.off[4] = put_v(W.outmap);
+    }
   }
   return plan;
 }
@@ -989,13 +1064,57 @@ double patch_flops(gamblet_ctx* h, int k) {
   return f;
 }
 
-// Patch-CG launch shape at level k: lanes per neighbour parent (1, 2, 4)
-// and block gather (thread, half-warp or four lanes per block), timed on a
-// Morton block of kTuneSample coarse cells in the middle of the level (its
-// Rhat rows are overwritten by the full launch that follows).
+// Device geometry of the tensor-core patch solves with windows of G x G
+// coarse cells at level k.
+PatchMmaGeom mma_geometry(gamblet_ctx* h, int k, int G, const char* dplan, const PlanLevel& pl) {
+  const MmaWin& W = pl.mwin[G - 1];
+  const LevelDev& L = h->lv[k];
+  PatchMmaGeom g{};
+  g.NP = W.NP;
+  g.nU = W.nU;
+  g.n = W.n;
+  g.Kp = W.Kp;
+  g.Mt = W.Mt;
+  g.npair = (int)W.pairs.size();
+  g.NB = h->N.size();
+  g.jc = h->jc;
+  g.diag_o = W.diag_o;
+  g.Lpar = 1 << (k - 1);
+  g.npatch = L.npar;
+  g.w_begin = 0;
+  g.w_end = L.npar / W.NP;
+  g.U = reinterpret_cast<const int2*>(dplan + W.off[0]);
+  g.ubits = reinterpret_cast<const int*>(dplan + W.off[1]);
+  g.pairs = reinterpret_cast<const int4*>(dplan + W.off[2]);
+  g.rhs_o = reinterpret_cast<const int*>(dplan + W.off[3]);
+  g.outmap = reinterpret_cast<const int*>(dplan + W.off[4]);
+  return g;
+}
+
+// The tensor-core patch solve rounds the scaled patch matrix to float16
+// (relative 2^-11 per entry), so it is a candidate only where the requested
+// patch tolerance is no tighter than that rounding.
+constexpr double kMmaMinPatchTol = 4.8e-4;
+
+// Patch solver and launch shape at level k.  Returns 0 for the SIMT patch CG
+// (with gp.spp, gp.gather set: lanes per neighbour parent 1, 2, 4 and block
+// gather by thread, half-warp or four lanes per block) or G = 1, 2 for the
+// tensor-core solves with windows of G x G cells (float32 path only).  The
+// candidates are timed on a Morton block of kTuneSample coarse cells in the
+// middle of the level (its Rhat rows are overwritten by the full launch that
+// follows).
 template <typename T>
-void tune_patch_shape(gamblet_ctx* h, int k, PatchPcgGeom& gp, T* Rhat) {
-  if (!h->opts.autotune || gp.npatch < kTuneMinParents) return;
+int tune_patch_shape(gamblet_ctx* h, int k, PatchPcgGeom& gp, T* Rhat, const PatchMmaGeom* mg,
+                     const bool* mma_ok) {
+  if (!h->opts.autotune || gp.npatch < kTuneMinParents) {
+    // fixed rule: the tensor-core windows of 2 x 2 cells where the patch
+    // matrices are at least half full of blocks (the coarse levels; the
+    // finest level's 9-point operator leaves them sparse)
+    const int NB = gp.NB;
+    const bool dense = 2.0 * gp.nhalf >= 0.5 * NB * (NB + 1.0);
+    if (is_f32<T>() && h->patch_tol >= kMmaMinPatchTol && dense && mma_ok[1]) return 2;
+    return 0;
+  }
   const std::string key = h->plan->key + "/patch_pcg/" + std::to_string(k) + "/" +
                           std::to_string(sizeof(T)) + "/" + std::to_string(h->patch_tol);
   int code = 0;
@@ -1007,9 +1126,10 @@ void tune_patch_shape(gamblet_ctx* h, int k, PatchPcgGeom& gp, T* Rhat) {
     gt.i_end = std::min(gt.i_begin + kTuneSample, gp.npatch);
     float best = 1e30f;
     code = gp.spp * 4 + gp.gather;
+    const bool simt_fits = patch_pcg_smem_bytes<T>(gp) <= 227 * 1024;
     for (int spp : {1, 2, 4})
       for (int gather : {0, 1, 2}) {
-        if (gp.NB * spp > 256) continue;
+        if (!simt_fits || gp.NB * spp > 256) continue;
         gt.spp = spp;
         gt.gather = gather;
         const float ms = time_on_stream(s, [&] {
@@ -1021,10 +1141,27 @@ void tune_patch_shape(gamblet_ctx* h, int k, PatchPcgGeom& gp, T* Rhat) {
           code = spp * 4 + gather;
         }
       }
+    if (is_f32<T>() && h->patch_tol >= kMmaMinPatchTol)
+      for (int G = 1; G <= 2; ++G) {
+        if (!mma_ok[G - 1]) continue;
+        PatchMmaGeom mt = mg[G - 1];
+        mt.w_begin = gt.i_begin / mt.NP;
+        mt.w_end = gt.i_end / mt.NP;
+        const float ms = time_on_stream(s, [&] {
+          launch_patch_mma((const float*)h->lv[k].Ahat, h->lv[k].pmask, mt, (float*)Rhat,
+                           h->patch_tol, 200, stats, h->status, h->num_sms, s);
+        });
+        if (ms < best) {
+          best = ms;
+          code = 64 + G;
+        }
+      }
     tune_store(key, code);
   }
+  if (code >= 64) return code - 64;
   gp.spp = code / 4;
   gp.gather = code % 4;
+  return 0;
 }
 
 // Galerkin kernel of level k (k_galerkin_rows, k_galerkin_warp or
@@ -1073,6 +1210,7 @@ void setup_local(gamblet_ctx* h) {
   if (NB > 256) fail(GAMBLET_ERR_UNSUPPORTED, "patch neighbourhood too large; lower rho");
   h->patch_stats = P.zeros<int>(4 * (q + 1), s);
   h->patch_flops_iter_k.assign(q + 1, 0.0);
+  h->patch_mma_flops_k.assign(q + 1, 0.0);
   // level q values in T
   {
     LevelDev& L = h->lv[q];
@@ -1114,18 +1252,59 @@ void setup_local(gamblet_ctx* h) {
                       plan_table<int>(dplan, pl, PlanLevel::kAdjPtr),
                       plan_table<int4>(dplan, pl, PlanLevel::kAdj),
                       plan_table<int>(dplan, pl, PlanLevel::kDiagH), pl.spp, 0, L.npar, 2};
-      if (patch_pcg_smem_bytes<T>(gp) > 227 * 1024)
-        fail(GAMBLET_ERR_UNSUPPORTED, "patch blocks exceed shared memory; lower rho");
-      tune_patch_shape<T>(h, k, gp, Rhat);
-      if (h->opts.patch_gather >= 0 && h->opts.patch_gather <= 2) gp.gather = h->opts.patch_gather;
-      L.shape[0] = gp.spp;
-      L.shape[1] = gp.gather;
-      // flops are added after setup from the measured iteration counts
-      int tok = h->prof.begin("patch_pcg_k" + std::to_string(k), pbytes, 0.0, s);
-      launch_patch_pcg<T>((const T*)L.Ahat, L.pmask, gp, Rhat, h->patch_tol, 200,
-                          h->patch_stats + 4 * k, h->num_sms, s);
-      h->prof.end(tok, s);
-      h->patch_flops_iter_k[k] = pl.flops_iter;
+      PatchMmaGeom mg[2];
+      bool mma_ok[2];
+      for (int G = 1; G <= 2; ++G) {
+        mma_ok[G - 1] = is_f32<T>() && pl.mwin[G - 1].ok && L.npar % (G * G) == 0;
+        mg[G - 1] = mma_geometry(h, k, G, dplan, pl);
+      }
+      const bool simt_fits = patch_pcg_smem_bytes<T>(gp) <= 227 * 1024;
+      int solver = 0;  // 0: SIMT patch CG; G = 1, 2: tensor-core windows of G x G cells
+      const int force = h->opts.patch_gather;
+      if (force >= 3) {
+        solver = force - 2;
+        if (!mma_ok[solver - 1])
+          fail(GAMBLET_ERR_UNSUPPORTED, "tensor-core patch solves (patch_gather " +
+                                            std::to_string(force) +
+                                            ") need the mixed path and a window that fits one "
+                                            "CTA; lower rho or use patch_gather <= 2");
+      } else {
+        solver = tune_patch_shape<T>(h, k, gp, Rhat, mg, mma_ok);
+        if (solver == 0 && !simt_fits) {
+          // the SIMT kernel cannot hold the patch: the tensor-core window
+          // with one cell per CTA still can on the float32 path
+          if (mma_ok[0]) solver = 1;
+          else fail(GAMBLET_ERR_UNSUPPORTED, "patch blocks exceed shared memory; lower rho");
+        }
+        if (force >= 0 && force <= 2) {
+          if (!simt_fits)
+            fail(GAMBLET_ERR_UNSUPPORTED, "patch blocks exceed shared memory; lower rho");
+          solver = 0;
+          gp.gather = force;
+        }
+      }
+      if (solver == 0) {
+        L.shape[0] = gp.spp;
+        L.shape[1] = gp.gather;
+        // flops are added after setup from the measured iteration counts
+        int tok = h->prof.begin("patch_pcg_k" + std::to_string(k), pbytes, 0.0, s);
+        launch_patch_pcg<T>((const T*)L.Ahat, L.pmask, gp, Rhat, h->patch_tol, 200,
+                            h->patch_stats + 4 * k, h->num_sms, s);
+        h->prof.end(tok, s);
+        h->patch_flops_iter_k[k] = pl.flops_iter;
+        h->patch_mma_flops_k[k] = 0.0;
+      } else {
+        const PatchMmaGeom& g = mg[solver - 1];
+        L.shape[0] = 0;
+        L.shape[1] = 2 + solver;
+        int tok = h->prof.begin("patch_mma_k" + std::to_string(k), pbytes, 0.0, s);
+        launch_patch_mma((const float*)L.Ahat, L.pmask, g, (float*)Rhat, h->patch_tol, 200,
+                         h->patch_stats + 4 * k, h->status, h->num_sms, s);
+        h->prof.end(tok, s);
+        h->patch_flops_iter_k[k] = 0.0;
+        // executed tensor-core work per product: Mt M-tiles of 128 x 16 x Kp
+        h->patch_mma_flops_k[k] = 2.0 * g.Mt * 128.0 * 16.0 * g.Kp;
+      }
     }
     CK(cudaGetLastError());
     L.Rhat = Rhat;
@@ -1978,17 +2157,19 @@ std::shared_ptr<const RevPack> reverse_pack(gamblet_ctx* h) {
   return P;
 }
 
-// The patch-CG geometry of level k as the setup launched it.
+// The patch-CG geometry of level k as the setup launched it (the plan's
+// default shape where the setup used the tensor-core solves).
 PatchPcgGeom patch_geometry(gamblet_ctx* h, int k) {
   const PlanLevel& pl = h->plan->lv[k];
   LevelDev& L = h->lv[k];
   const char* dplan = h->dplan;
+  const bool simt = L.shape[1] <= 2 && L.shape[0] > 0;
   PatchPcgGeom gp{h->N.size(), h->jc, h->nbr, L.pair_idx, 1 << (k - 1), L.npar,
                   (int)pl.half.size(), plan_table<int4>(dplan, pl, PlanLevel::kHalf),
                   (int)pl.adj.size(), plan_table<int>(dplan, pl, PlanLevel::kAdjPtr),
                   plan_table<int4>(dplan, pl, PlanLevel::kAdj),
-                  plan_table<int>(dplan, pl, PlanLevel::kDiagH), L.shape[0], 0, L.npar,
-                  L.shape[1]};
+                  plan_table<int>(dplan, pl, PlanLevel::kDiagH), simt ? L.shape[0] : pl.spp, 0,
+                  L.npar, simt ? L.shape[1] : 2};
   return gp;
 }
 
@@ -2218,8 +2399,8 @@ gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
       fail(GAMBLET_ERR_INVALID_ARG, "nbr_rule must be 0 or 1");
     if (h->opts.galerkin_variant < -1 || h->opts.galerkin_variant > 5)
       fail(GAMBLET_ERR_INVALID_ARG, "galerkin_variant must be -1 or 0..5");
-    if (h->opts.patch_gather < -1 || h->opts.patch_gather > 2)
-      fail(GAMBLET_ERR_INVALID_ARG, "patch_gather must be -1, 0, 1 or 2");
+    if (h->opts.patch_gather < -1 || h->opts.patch_gather > 4)
+      fail(GAMBLET_ERR_INVALID_ARG, "patch_gather must be -1 or 0..4");
     if (h->exact && q > 7)
       fail(GAMBLET_ERR_UNSUPPORTED, "the exact (rho <= 0) transform is limited to q <= 7");
     int dev = 0;
@@ -2280,8 +2461,12 @@ gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
         // algorithmic flops of the patch CG at level k: per iteration the
         // block product (18 flops per used 3x3 block) plus block-Jacobi and
         // vector work, times the iterations actually run
-        h->prof.add("patch_pcg_k" + std::to_string(k), 0.0,
-                    (double)ps[4 * k + 1] * h->patch_flops_iter_k[k]);
+        if (h->patch_mma_flops_k[k] > 0)
+          h->prof.add("patch_mma_k" + std::to_string(k), 0.0,
+                      (double)ps[4 * k + 3] * h->patch_mma_flops_k[k]);
+        else
+          h->prof.add("patch_pcg_k" + std::to_string(k), 0.0,
+                      (double)ps[4 * k + 1] * h->patch_flops_iter_k[k]);
       }
       h->patch_iters_mean = n_sum > 0 ? (double)it_sum / n_sum : 0.0;
     }

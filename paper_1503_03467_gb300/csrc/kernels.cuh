@@ -202,6 +202,30 @@ void launch_patch_pcg_adjoint(const T* Ahat, const uint32_t* pmask_k, PatchPcgGe
                               const T* rhs, T* out, double tol, int max_iter, int* iter_stats,
                               int num_sms, cudaStream_t s);
 
+// Tensor-core patch solves (patch_mma.cu, float32 path): the patches of the
+// G x G coarse cells i = NP w .. NP w + NP - 1 (NP = G^2, Morton order) share
+// one CTA, which gathers the block-Jacobi-scaled union matrix B^(k)|_U once
+// (float16, tcgen05 kind::f16) and runs their CG solves as one product per
+// iteration.  Windows [w_begin, w_end) are solved; status receives
+// DEV_NOT_SPD on a non-positive diagonal-block pivot and DEV_TIMEOUT if a
+// tensor-core completion wait gives up.  iter_stats as for the patch CG, plus
+// [3] += tensor-core products issued (one per window and iteration).
+struct PatchMmaGeom {
+  int NP, nU, n, Kp, Mt;  // patches per window, union parents, unknowns, padded K, M-tiles
+  int npair;              // stored union blocks a > b
+  int NB, jc, diag_o, Lpar;
+  int64_t npatch, w_begin, w_end;
+  const int2* U;          // union offsets relative to the window's first cell
+  const int* ubits;       // per union parent: bit c set when it lies in patch c
+  const int4* pairs;      // (a, b, o, 0): block of B^(k) between union parents a > b
+  const int* rhs_o;       // [c][u]: offset index of cell c seen from parent u, or -1
+  const int* outmap;      // [c][j]: union index of cell c + N_j
+};
+void launch_patch_mma(const float* Ahat, const uint32_t* pmask_k, PatchMmaGeom g, float* Rhat,
+                      double tol, int max_iter, int* iter_stats, int* status, int num_sms,
+                      cudaStream_t s);
+size_t patch_mma_smem_bytes(const PatchMmaGeom& g);
+
 // ---------------------------------------------------------------- Galerkin
 struct GalerkinGeom {
   int NB;

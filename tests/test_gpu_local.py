@@ -372,3 +372,101 @@ def test_convergence_status_and_iteration_counts(precision):
     assert st == nv.OK and info.rel_residual <= 1e-10
     assert all(info.level_iters[k] >= 1 for k in range(2, p.q + 1))
     assert rel(u, direct.solve(p.A, p.g)[0]) < 1e-8
+
+
+# ---- tensor-core patch solves (tcgen05, windows of 1 x 1 or 2 x 2 cells) ----
+#
+# The tensor-core kernel solves each patch system on the block-Jacobi-scaled
+# matrix L^-1 B L^-T stored in float16, with float32 accumulation and float32
+# CG vectors.  Rounding the scaled matrix to float16 perturbs every entry by
+# at most u = 2^-11 = 4.9e-4 relative, so the patch solutions (the rows of
+# R) move by about u times the condition number of the scaled patch matrix
+# from the exact ones; measured 0.6e-4 to 1.0e-4 of each row's largest entry
+# on these cases with the CG tolerance at 1e-6.  The bound below is 2u per
+# row for R and 1e-4 for A^(k-1) (element-wise, of its largest entry), and
+# the support of R must be the oracle's patch support exactly.
+
+MMA_CASES = [(32, 1e4, 0, 3.0, 0), (64, 1e4, 1, 3.0, 0), (64, 1e6, 5, 2.0, 0), (32, 1e3, 3, 3.0, 1)]
+
+
+@pytest.mark.parametrize("force", [3, 4])
+@pytest.mark.parametrize("n,C,seed,rho,rule", MMA_CASES)
+def test_tensor_core_patch_solves_match_oracle(force, n, C, seed, rho, rule):
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(n, C, seed)
+    ref = gamblet_local_setup(p.A, p.cells, p.q, rho, "euclid" if rule == 0 else "cheb")
+    rp, ci, va = csr_arrays(p.A)
+    o = nv.gamblet_default_opts()
+    o.rho = rho
+    o.nbr_rule = rule
+    o.precision = nv.MIXED
+    o.patch_tol = 1e-6
+    o.patch_gather = force
+    o.level_tol = 1e-7
+    o.level_max_iter = 5000
+    o.refine_max_iter = 0
+    h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
+    try:
+        for k in range(2, p.q + 1):
+            assert nv.gamblet_launch_shapes(h, k)["patch_gather"] == force
+        ops = _ops(h, p.q)
+        for k in range(2, p.q + 1):
+            check_R(ops[("R", k)], ref["R"][k], 2 * 2.0 ** -11, ("R", k))
+            check_op(ops[("A", k - 1)], ref["A"][k - 1], 1e-4, ("A", k - 1))
+    finally:
+        nv.gamblet_destroy(h)
+
+
+@pytest.mark.parametrize("force", [3, 4])
+def test_tensor_core_patch_solves_on_ragged_domain_and_refined_solve(force):
+    """Holes (parents with 1, 2 and 3 children, absent union parents at the
+    boundary of a hole) through the tensor-core windows, and the refined
+    solution of the same handle type against the direct solve."""
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(32, 1e3, 8)
+    x, y = p.cells[:, 0], p.cells[:, 1]
+    keep = ~((x >= 10) & (x <= 17) & (y >= 12) & (y <= 14)) & ~((x == 3) & (y == 29))
+    A, g, cells = drop_nodes(p, keep)
+    ref = gamblet_local_setup(A, cells, p.q, 3.0)
+    rp, ci, va = csr_arrays(A)
+    o = nv.gamblet_default_opts()
+    o.rho = 3.0
+    o.precision = nv.MIXED
+    o.patch_tol = 1e-6
+    o.patch_gather = force
+    o.level_tol = 1e-7
+    o.level_max_iter = 5000
+    o.refine_max_iter = 0
+    h = nv.gamblet_setup(rp, ci, va, p.q, cells, o)
+    try:
+        ops = _ops(h, p.q)
+        for k in range(2, p.q + 1):
+            check_R(ops[("R", k)], ref["R"][k], 2 * 2.0 ** -11, ("R", k))
+            check_op(ops[("A", k - 1)], ref["A"][k - 1], 1e-4, ("A", k - 1))
+    finally:
+        nv.gamblet_destroy(h)
+    o.patch_tol = 1e-3
+    o.refine_max_iter = 60
+    o.level_tol = 1e-6
+    h = nv.gamblet_setup(rp, ci, va, p.q, cells, o)
+    try:
+        u = np.zeros(A.shape[0])
+        info = nv.Info()
+        assert nv.gamblet_solve(h, g, u, None, info) == nv.OK
+        assert info.rel_residual < 1e-12
+        assert rel(u, direct.solve(A, g)[0]) < 1e-9
+    finally:
+        nv.gamblet_destroy(h)
+
+
+def test_tensor_core_patch_solves_need_the_mixed_path():
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(16, 1e2, 0)
+    rp, ci, va = csr_arrays(p.A)
+    o = nv.gamblet_default_opts()
+    o.rho = 2.0
+    o.precision = nv.FP64
+    o.patch_gather = 4
+    with pytest.raises(nv.GambletError) as e:
+        nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
+    assert e.value.status == nv.ERR_UNSUPPORTED
