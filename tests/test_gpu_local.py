@@ -177,8 +177,10 @@ def test_truncated_solve_sums_leading_components(precision, tol):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_autotuned_shapes_are_valid_and_change_nothing_but_rounding(precision):
     """The autotuner picks among launch shapes that compute the same rows
-    (only the summation order differs); 256 x 256 has levels large enough
-    to be tuned."""
+    (only the summation order differs, and on the mixed path the
+    tensor-core patch solves round the scaled patch matrix to float16, which
+    the refined solve absorbs); 256 x 256 has levels large enough to be
+    tuned."""
     from paper_1503_03467_gb300 import native as nv
     p = make_problem(256, 1e4, 13)
     rp, ci, va = csr_arrays(p.A)
@@ -194,7 +196,9 @@ def test_autotuned_shapes_are_valid_and_change_nothing_but_rounding(precision):
         try:
             for k in range(2, p.q + 1):
                 sh = nv.gamblet_launch_shapes(h, k)
-                assert sh["patch_spp"] in (1, 2, 4) and sh["patch_gather"] in (0, 1, 2)
+                simt = sh["patch_spp"] in (1, 2, 4) and sh["patch_gather"] in (0, 1, 2)
+                mma = precision == 1 and sh["patch_spp"] == 0 and sh["patch_gather"] in (3, 4)
+                assert simt or mma, sh
                 assert sh["galerkin_variant"] in (0, 1, 2, 3, 4, 5) and sh["cg_spp"] in (1, 4, 16)
             u = np.zeros(p.ndof)
             info = nv.Info()
