@@ -586,12 +586,14 @@ def batched_timing(nv, torch, dev, a, stream, flush, ws=1, rank=0):
     }
 
 
-def localization_errors(nv, a, dev_in, ud, radii=(1.0, 2.0, 3.0)):
+def localization_errors(nv, a, dev_in, ud, radii=(1.0, 2.0, 3.0, 4.0, 5.0, 6.0)):
     """One-pass (no outer iteration) relative error against the direct
     solution for each patch radius rho: the localization error of the
     transform of Definition defb.  Float64 with patch and level solves to
     1e-12, so that localization, not rounding, is measured (in float32 the
-    one-pass result carries rounding errors near 1e-3 at contrast 1e4)."""
+    one-pass result carries rounding errors near 1e-3 at contrast 1e4).  From
+    rho = 4 on, the float64 patch blocks exceed one CTA's shared memory and
+    the patch CG runs over thread-block clusters."""
     import torch
     q = int(np.log2(a.size))
     out = {}

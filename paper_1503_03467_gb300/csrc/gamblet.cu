@@ -421,6 +421,7 @@ struct gamblet_ctx {
   double patch_iters_mean = 0;
   std::vector<double> patch_flops_iter_k;  // per level: flops of one iteration of one patch
   std::vector<double> patch_mma_flops_k;   // per level: tensor-core flops of one window product
+  std::vector<bool> patch_cluster_k;        // per level: patch CG over a thread-block cluster
   int level_iters_acc[32];
   bool level_not_conv = false;
   const char* dplan = nullptr;  // device copy of the plan tables (localized setup)
@@ -1064,6 +1065,58 @@ double patch_flops(gamblet_ctx* h, int k) {
   return f;
 }
 
+// Cluster split of the patch CG of level k for patches beyond one CTA's
+// shared memory: the smallest cluster (2, 4, 8, 16 CTAs) whose CTAs each hold
+// at most 32 block rows and fit their blocks into shared memory, the rows cut
+// into contiguous ranges of at most B blocks for the smallest feasible B.
+template <typename T>
+bool cluster_geometry(const PatchPcgGeom& gp, const PlanLevel& pl, PatchClusterGeom& c) {
+  const int NB = gp.NB;
+  const std::vector<int>& ap = pl.adj_ptr;
+  for (int cs : {2, 4, 8, 16}) {
+    auto ranges = [&](int B, std::vector<int>& cut) {
+      cut.assign(1, 0);
+      int rows = 0, blocks = 0;
+      for (int j = 0; j < NB; ++j) {
+        const int bj = ap[j + 1] - ap[j];
+        if (bj > B) return false;
+        if (rows == 32 || blocks + bj > B) {
+          cut.push_back(j);
+          rows = 0;
+          blocks = 0;
+        }
+        ++rows;
+        blocks += bj;
+      }
+      cut.push_back(NB);
+      return (int)cut.size() - 1 <= cs;
+    };
+    int lo = 1, hi = ap[NB];
+    std::vector<int> cut;
+    if (!ranges(hi, cut)) continue;  // more than 32 rows per CTA even with all blocks
+    while (lo < hi) {
+      const int mid = (lo + hi) / 2;
+      if (ranges(mid, cut)) hi = mid;
+      else lo = mid + 1;
+    }
+    ranges(hi, cut);
+    c = PatchClusterGeom{};
+    c.pg = gp;
+    c.cs = cs;
+    c.max_rows = 0;
+    c.max_blocks = 0;
+    const int nr = (int)cut.size() - 1;
+    for (int r = 0; r <= cs; ++r) c.jsplit[r] = r <= nr ? cut[r] : NB;
+    for (int r = 0; r < cs; ++r) {
+      c.max_rows = std::max(c.max_rows, c.jsplit[r + 1] - c.jsplit[r]);
+      c.max_blocks = std::max(c.max_blocks, ap[c.jsplit[r + 1]] - ap[c.jsplit[r]]);
+    }
+    if (c.max_rows < 1) c.max_rows = 1;
+    if (patch_cluster_smem_bytes<T>(c) <= 227 * 1024) return true;
+  }
+  return false;
+}
+
 // Device geometry of the tensor-core patch solves with windows of G x G
 // coarse cells at level k.
 PatchMmaGeom mma_geometry(gamblet_ctx* h, int k, int G, const char* dplan, const PlanLevel& pl) {
@@ -1211,6 +1264,7 @@ void setup_local(gamblet_ctx* h) {
   h->patch_stats = P.zeros<int>(4 * (q + 1), s);
   h->patch_flops_iter_k.assign(q + 1, 0.0);
   h->patch_mma_flops_k.assign(q + 1, 0.0);
+  h->patch_cluster_k.assign(q + 1, false);
   // level q values in T
   {
     LevelDev& L = h->lv[q];
@@ -1259,8 +1313,11 @@ void setup_local(gamblet_ctx* h) {
         mg[G - 1] = mma_geometry(h, k, G, dplan, pl);
       }
       const bool simt_fits = patch_pcg_smem_bytes<T>(gp) <= 227 * 1024;
-      int solver = 0;  // 0: SIMT patch CG; G = 1, 2: tensor-core windows of G x G cells
+      // 0: SIMT patch CG; G = 1, 2: tensor-core windows of G x G cells;
+      // 3: SIMT patch CG over a thread-block cluster (patches beyond one CTA)
+      int solver = 0;
       const int force = h->opts.patch_gather;
+      const bool mma_tol = h->patch_tol >= kMmaMinPatchTol;
       if (force >= 3) {
         solver = force - 2;
         if (!mma_ok[solver - 1])
@@ -1268,22 +1325,33 @@ void setup_local(gamblet_ctx* h) {
                                             std::to_string(force) +
                                             ") need the mixed path and a window that fits one "
                                             "CTA; lower rho or use patch_gather <= 2");
+      } else if (!simt_fits) {
+        // the single-CTA kernel cannot hold the patch: the tensor-core window
+        // of one cell where its float16 rounding is within the patch
+        // tolerance, else the cluster-distributed CG
+        solver = (force < 0 && mma_ok[0] && mma_tol) ? 1 : 3;
       } else {
         solver = tune_patch_shape<T>(h, k, gp, Rhat, mg, mma_ok);
-        if (solver == 0 && !simt_fits) {
-          // the SIMT kernel cannot hold the patch: the tensor-core window
-          // with one cell per CTA still can on the float32 path
-          if (mma_ok[0]) solver = 1;
-          else fail(GAMBLET_ERR_UNSUPPORTED, "patch blocks exceed shared memory; lower rho");
-        }
         if (force >= 0 && force <= 2) {
-          if (!simt_fits)
-            fail(GAMBLET_ERR_UNSUPPORTED, "patch blocks exceed shared memory; lower rho");
           solver = 0;
           gp.gather = force;
         }
       }
-      if (solver == 0) {
+      PatchClusterGeom gcl{};
+      if (solver == 3 && !cluster_geometry<T>(gp, pl, gcl))
+        fail(GAMBLET_ERR_UNSUPPORTED,
+             "patch of " + std::to_string(3 * NB) + " unknowns exceeds a 16-CTA cluster; lower rho");
+      if (solver == 3) {
+        L.shape[0] = gcl.cs;
+        L.shape[1] = 5;
+        int tok = h->prof.begin("patch_cluster_k" + std::to_string(k), pbytes, 0.0, s);
+        CK(launch_patch_pcg_cluster<T>((const T*)L.Ahat, L.pmask, gcl, Rhat, h->patch_tol, 200,
+                                       h->patch_stats + 4 * k, s));
+        h->prof.end(tok, s);
+        h->patch_flops_iter_k[k] = pl.flops_iter;
+        h->patch_mma_flops_k[k] = 0.0;
+        h->patch_cluster_k[k] = true;
+      } else if (solver == 0) {
         L.shape[0] = gp.spp;
         L.shape[1] = gp.gather;
         // flops are added after setup from the measured iteration counts
@@ -2464,6 +2532,9 @@ gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
         if (h->patch_mma_flops_k[k] > 0)
           h->prof.add("patch_mma_k" + std::to_string(k), 0.0,
                       (double)ps[4 * k + 3] * h->patch_mma_flops_k[k]);
+        else if (h->patch_cluster_k[k])
+          h->prof.add("patch_cluster_k" + std::to_string(k), 0.0,
+                      (double)ps[4 * k + 1] * h->patch_flops_iter_k[k]);
         else
           h->prof.add("patch_pcg_k" + std::to_string(k), 0.0,
                       (double)ps[4 * k + 1] * h->patch_flops_iter_k[k]);
@@ -3405,6 +3476,11 @@ gamblet_status gamblet_grad_onepass(gamblet_handle h, int32_t ncell, const int32
       fail(GAMBLET_ERR_UNSUPPORTED,
            "the one-pass gradient needs a localized setup of one problem with A^(q) = A and "
            "iterative patch solves (patch_tol >= 0)");
+    for (int k = 2; k <= h->q; ++k)
+      if (k < (int)h->patch_cluster_k.size() && h->patch_cluster_k[k])
+        fail(GAMBLET_ERR_UNSUPPORTED,
+             "the one-pass gradient needs patches that fit one CTA's shared memory (its "
+             "adjoint patch solves have no cluster form); lower rho");
     if (h->mixed)
       return grad_onepass_impl<float>(h, ncell, cell_nodes, cell_a, K_ref, g, u_obs, u, dJ, dJ_dg,
                                       J, info);

@@ -202,6 +202,27 @@ void launch_patch_pcg_adjoint(const T* Ahat, const uint32_t* pmask_k, PatchPcgGe
                               const T* rhs, T* out, double tol, int max_iter, int* iter_stats,
                               int num_sms, cudaStream_t s);
 
+// Patch CG over a thread-block cluster (patch_cluster.cu) for patches whose
+// blocks exceed one CTA's shared memory: CTA c of each cluster of cs keeps
+// the block rows jsplit[c] <= j < jsplit[c + 1] (one warp per row, at most
+// max_rows rows and max_blocks blocks per CTA); the direction vector and the
+// inner products are exchanged through distributed shared memory.  Same
+// iteration, stopping rule and iter_stats as launch_patch_pcg.  Returns the
+// launch status (the cluster shape is checked by the runtime).
+struct PatchClusterGeom {
+  PatchPcgGeom pg;
+  int cs;           // CTAs per cluster: 2, 4, 8 or 16
+  int max_rows;     // rows of the largest range (32 threads each)
+  int max_blocks;   // stored blocks of the largest range
+  int jsplit[17];   // row ranges of the cs CTAs
+};
+template <typename T>
+cudaError_t launch_patch_pcg_cluster(const T* Ahat, const uint32_t* pmask_k,
+                                     const PatchClusterGeom& c, T* Rhat, double tol,
+                                     int max_iter, int* iter_stats, cudaStream_t s);
+template <typename T>
+size_t patch_cluster_smem_bytes(const PatchClusterGeom& c);
+
 // Tensor-core patch solves (patch_mma.cu, float32 path): the patches of the
 // G x G coarse cells i = NP w .. NP w + NP - 1 (NP = G^2, Morton order) share
 // one CTA, which gathers the block-Jacobi-scaled union matrix B^(k)|_U once

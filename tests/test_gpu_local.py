@@ -269,13 +269,15 @@ def test_galerkin_kernels_on_ragged_and_prefix_domains(variant):
 
 @pytest.mark.parametrize("variant", [-1, 1, 3])
 def test_rho4_operators_match_oracle(variant):
-    """rho = 4 (89 neighbour parents, wider windows and stencils) in the
-    mixed path, with the automatic and the forced Galerkin kernels; float32
-    operators against the float64 oracle.  The float64 path stages the
-    patch blocks of rho = 4 beyond shared memory and refuses cleanly."""
+    """rho = 4 (89 neighbour parents, wider windows and stencils) with the
+    automatic and the forced Galerkin kernels: float32 operators of the mixed
+    path against the float64 oracle, and the float64 path, whose patch blocks
+    exceed one CTA's shared memory and are solved by the cluster-distributed
+    patch CG, element by element at 1e-10."""
     from paper_1503_03467_gb300 import native as nv
     p = make_problem(64, 1e3, 16)
     ref = gamblet_local_setup(p.A, p.cells, p.q, 4.0)
+    one = gamblet_local_solve(ref, p.g)
     rp, ci, va = csr_arrays(p.A)
     o = nv.gamblet_default_opts()
     o.rho = 4.0
@@ -294,9 +296,57 @@ def test_rho4_operators_match_oracle(variant):
     finally:
         nv.gamblet_destroy(h)
     o.precision = nv.FP64
-    with pytest.raises(nv.GambletError) as e:
-        nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
-    assert e.value.status == nv.ERR_UNSUPPORTED
+    o.patch_tol = 0.0
+    o.level_tol = 1e-14
+    h = nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
+    try:
+        assert any(nv.gamblet_launch_shapes(h, k)["patch_gather"] == 5 for k in range(2, p.q + 1))
+        ops = _ops(h, p.q)
+        for k in range(2, p.q + 1):
+            check_R(ops[("R", k)], ref["R"][k], 1e-10, ("R", k))
+            check_op(ops[("A", k - 1)], ref["A"][k - 1], 1e-10, ("A", k - 1))
+        u = np.zeros(p.ndof)
+        assert nv.gamblet_solve(h, p.g, u) == nv.OK
+        assert rel(u, one["u"]) < 1e-9
+    finally:
+        nv.gamblet_destroy(h)
+
+
+@pytest.mark.parametrize("rho", [5.0, 6.0])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_large_patches_over_thread_block_clusters(rho, precision):
+    """rho = 5 and 6 (129 and 169 neighbour parents, up to 507 patch unknowns):
+    every level's patch blocks exceed one CTA's shared memory and the patch
+    CG runs over a cluster of CTAs on one GPU.  Operators against the oracle
+    element by element (float64 at 1e-10; float32 with the CG to 1e-7 at
+    1e-4), the one-pass solution, and the refined solution."""
+    from paper_1503_03467_gb300 import native as nv
+    p = make_problem(32, 1e4, 17)
+    ref = gamblet_local_setup(p.A, p.cells, p.q, rho)
+    one = gamblet_local_solve(ref, p.g)
+    tol = 1e-10 if precision == 0 else 1e-4
+    h = _setup(p.A, p.cells, p.q, rho, precision=precision,
+               patch_tol=0.0 if precision == 0 else 1e-7)
+    try:
+        shapes = [nv.gamblet_launch_shapes(h, k) for k in range(2, p.q + 1)]
+        assert any(sh["patch_gather"] == 5 and sh["patch_spp"] in (2, 4, 8, 16) for sh in shapes)
+        ops = _ops(h, p.q)
+        for k in range(2, p.q + 1):
+            check_R(ops[("R", k)], ref["R"][k], tol, ("R", k))
+            check_op(ops[("A", k - 1)], ref["A"][k - 1], tol, ("A", k - 1))
+        u = np.zeros(p.ndof)
+        assert nv.gamblet_solve(h, p.g, u) == nv.OK
+        assert rel(u, one["u"]) < (1e-9 if precision == 0 else 1e-3)
+    finally:
+        nv.gamblet_destroy(h)
+    h = _setup(p.A, p.cells, p.q, rho, precision=precision, refine=60, level_tol=1e-6)
+    try:
+        u = np.zeros(p.ndof)
+        info = nv.Info()
+        assert nv.gamblet_solve(h, p.g, u, None, info) == nv.OK
+        assert rel(u, direct.solve(p.A, p.g)[0]) < 1e-9
+    finally:
+        nv.gamblet_destroy(h)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -474,3 +524,22 @@ def test_tensor_core_patch_solves_need_the_mixed_path():
     with pytest.raises(nv.GambletError) as e:
         nv.gamblet_setup(rp, ci, va, p.q, p.cells, o)
     assert e.value.status == nv.ERR_UNSUPPORTED
+
+
+def test_one_pass_gradient_refuses_cluster_patches():
+    """The reverse pass has no cluster form of its adjoint patch solves, so a
+    handle whose patches needed a thread-block cluster is refused."""
+    from paper_1503_03467_gb300 import native as nv
+    from workloads import cell_corner_dofs
+    from workloads.rough import K_REF
+    p = make_problem(64, 1e2, 2)
+    h = _setup(p.A, p.cells, p.q, 4.0, precision=0, patch_tol=1e-10)
+    try:
+        assert any(nv.gamblet_launch_shapes(h, k)["patch_gather"] == 5 for k in range(2, p.q + 1))
+        dJ = np.zeros(p.n * p.n)
+        with pytest.raises(nv.GambletError) as e:
+            nv.gamblet_grad_onepass(h, cell_corner_dofs(p.n), np.exp(p.log_a.ravel()),
+                                    K_REF.ravel().copy(), p.g, np.zeros(p.ndof), dJ)
+        assert e.value.status == nv.ERR_UNSUPPORTED
+    finally:
+        nv.gamblet_destroy(h)
