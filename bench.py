@@ -616,6 +616,27 @@ def localization_errors(nv, a, dev_in, ud, radii=(1.0, 2.0, 3.0, 4.0, 5.0, 6.0))
     return out
 
 
+def mixed_by_rho(nv, torch, a, dev_in, stream, flush, ud, radii=(3.0, 4.0), steps=3):
+    """The headline mixed arm (setup + refined solve, the same tolerances) at
+    patch radii 3 and 4: device time per step, DOF/s, outer iterations and
+    the error against the direct solution.  A larger radius makes the
+    one-pass transform more accurate (fewer outer iterations) and the setup
+    heavier."""
+    import copy
+    out = {}
+    for rho in radii:
+        b = copy.copy(a)
+        b.rho = rho
+        r = run_arm(nv, torch, b, dev_in, nv.MIXED, steps, 2, stream, flush)
+        ms = statistics.mean(r["times_ms"])
+        out[str(int(rho))] = {"ms_per_step": ms, "value": int(dev_in["g"].shape[0]) / (ms * 1e-3),
+                              "unit": UNIT, "setup_ms": statistics.mean(r["setup_ms"]),
+                              "solve_ms": statistics.mean(r["solve_ms"]),
+                              "outer_iters": r["infos"][-1]["outer_iters"],
+                              "rel_err": rel_err(r["u"], ud)}
+    return out
+
+
 def mass_init_timing(nv, torch, dev, a, stream):
     """Setup with the mass-matrix initialisation (Algorithm 2 lines 2a-5,
     rho_q = 2) and refined solve: the paper's Example 1 (q = 6, float64,
@@ -974,6 +995,7 @@ def main():
         line["batched"] = batched_timing(nv, torch, dev, a, stream, flush, ws, rank)
     if not a.no_localization:
         line["localization_error_one_pass"] = localization_errors(nv, a, dev_in, ud)
+        line["mixed_by_rho"] = mixed_by_rho(nv, torch, a, dev_in, stream, flush, ud)
     if not a.no_mass:
         line["mass_init"] = mass_init_timing(nv, torch, dev, a, stream)
     if not a.no_localization:
