@@ -153,7 +153,10 @@ def ncu_traffic(kernel: str, mixed: bool = True):
         return None
     if not rec:
         return None
-    if ("<float" in rec.get("kernel", "")) != mixed:
+    prec = rec.get("precision")
+    if prec is None:
+        prec = "f32" if "<float" in rec.get("kernel", "") else "f64"
+    if (prec == "f32") != mixed:
         return None
     src = os.path.join(ROOT, rec["source"])
     try:
@@ -818,11 +821,20 @@ def families(stats):
     return out
 
 
-def roofline(stats, peaks, alu, mixed):
-    """Roofline entry of the single kernel (kernel family and level) with the
-    largest share of device time; per-launch figures are its own averages.
-    `alu` holds the measured GEMM throughputs (measured_alu_peaks)."""
-    name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
+# CUDA graphs of several kernels (the level CG's device-side loop) are timed
+# as one entry; the contract's roofline is for a single kernel
+COMPOSITE = ("level_cg",)
+
+
+def roofline(stats, peaks, alu, mixed, name=None):
+    """Roofline entry of one kernel (kernel family and level): by default the
+    single kernel with the largest share of device time; per-launch figures
+    are its own averages.  `alu` holds the measured GEMM throughputs
+    (measured_alu_peaks)."""
+    if name is None:
+        single = {k: v for k, v in stats.items() if k not in COMPOSITE} or stats
+        name = max(single.items(), key=lambda kv: kv[1]["ms"])[0]
+    st = stats[name]
     family = name.rsplit("_k", 1)[0] if "_k" in name and name.rsplit("_k", 1)[1].isdigit() else name
     launches = max(st["launches"], 1)
     avg_ms = st["ms"] / launches
@@ -833,7 +845,7 @@ def roofline(stats, peaks, alu, mixed):
               "share_of_device_time": st["ms"] / total_ms, "traffic": ncu_traffic(name, mixed),
               "timing": "CUDA events around every launch of the kernel, over a second pass of "
                         "the timed steps with the library's per-kernel events on"}
-    if family in ("patch_pcg", "patch_cholesky", "patch_mma"):
+    if family in ("patch_pcg", "patch_cholesky", "patch_mma", "patch_cluster"):
         tensor = family == "patch_mma"
         if tensor:
             # kind::f16 products: the dense float16 rate equals the bf16 rate
@@ -855,7 +867,7 @@ def roofline(stats, peaks, alu, mixed):
         if tensor:
             out["binding_unit"] = ("per-iteration latency of the window CG (block reductions, "
                                    "barriers, product issue); N = 16 products use a fraction "
-                                   "of the pipe by construction")
+                                   "of the pipe by construction (ncu: tensor pipe 3 % active)")
         if mixed and not tensor:
             # the lanes are not what binds this kernel: its shared-memory block
             # products are (ncu summary of the patch CG kernel)
@@ -863,10 +875,21 @@ def roofline(stats, peaks, alu, mixed):
         return out
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
-    return {**common, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
-            else "fallback 6.8 TB/s", "algorithmic": f"{per_launch_bytes:.4g} byte per launch"}
+    out = {**common, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks
+           else "fallback 6.8 TB/s", "algorithmic": f"{per_launch_bytes:.4g} byte per launch"}
+    if per_launch_flops > 0:
+        fp = alu.get("fp32_simt_tflops" if mixed else "fp64_tflops")
+        tf = per_launch_flops / (avg_ms * 1e-3) / 1e12
+        out["alu"] = {"achieved": tf, "peak": fp, "unit": "TFLOP/s",
+                      "frac": tf / fp if fp else None,
+                      "algorithmic": f"{per_launch_flops:.4g} flop per launch"}
+    if name in COMPOSITE:
+        out["composite"] = ("one CUDA graph per launch: SpMV, update, scalar and direction "
+                            "kernels repeated by a device-side while loop; ncu lists none of "
+                            "them, so traffic is not measured")
+    return out
 
 
 def bench_config(a, ndof):
@@ -970,8 +993,10 @@ def main():
                 "h2d_bytes_per_step": int(e2e["h2d"]), "d2h_bytes_per_step": int(e2e["d2h"]),
                 "rel_err": err_e2e},
         "roofline": roofline(prof["stats"], peaks, alu, True),
-        "roofline_patch": roofline({k: v for k, v in prof["stats"].items()
-                                    if k.startswith("patch_")} or prof["stats"], peaks, alu, True),
+        "roofline_others": {n: roofline(prof["stats"], peaks, alu, True, name=n)
+                            for n in ("level_cg", "patch_mma_k9", "galerkin_k9", "galerkin_k10",
+                                      "patch_pcg_k10", "restrict", "prolong")
+                            if n in prof["stats"]},
         "clocks": mixed["clocks"],
         "alu_peaks": alu,
         "setup_cold": cold,
