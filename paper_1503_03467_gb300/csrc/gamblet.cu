@@ -263,6 +263,8 @@ struct LevelDev {
   double* wc = nullptr;  // compact detail vector (exact path)
   // level CG operator (localized path)
   void* Bd = nullptr;    // [noff][9][npar]
+  void* Bq = nullptr;    // 32-byte float16 block records of the level CG (mixed path), or NULL
+  float* bq_scale = nullptr;  // device: inverse scale of Bq
   void* Dinv = nullptr;  // [9][npar]
   int R = 0;             // halo radius
   int o0 = -1;           // index of the zero offset in O_k (diagonal blocks)
@@ -1148,6 +1150,10 @@ PatchMmaGeom mma_geometry(gamblet_ctx* h, int k, int G, const char* dplan, const
 // (relative 2^-11 per entry), so it is a candidate only where the requested
 // patch tolerance is no tighter than that rounding.
 constexpr double kMmaMinPatchTol = 4.8e-4;
+// The level CG reads float16 block records on the mixed path when the
+// requested level tolerance is this loose (the bench's is 0.05); tighter
+// tolerances keep the float32 blocks.
+constexpr double kHalfLevelTol = 1e-3;
 
 // Patch solver and launch shape at level k.  Returns 0 for the SIMT patch CG
 // (with gp.spp, gp.gather set: lanes per neighbour parent 1, 2, 4 and block
@@ -1468,6 +1474,17 @@ void setup_local(gamblet_ctx* h) {
     launch_cg_level_setup<T>((const T*)L.Ahat, L.noff, o0, L.npar, L.pmask, Bd, Dinv, s);
     L.Bd = Bd;
     L.Dinv = Dinv;
+    L.Bq = nullptr;
+    L.bq_scale = nullptr;
+    if (is_f32<T>() && h->opts.level_tol >= kHalfLevelTol) {
+      // the level CG's product reads each block as one 32-byte float16 record
+      // (two 16-byte loads instead of nine scalar ones), with a rounding of
+      // 2^-11 relative per entry, far below the level tolerance
+      L.Bq = P.alloc<uint4>((int64_t)L.noff * L.npar * 2);
+      L.bq_scale = P.alloc<float>(1);
+      launch_cg_block_records((const float*)L.Ahat, (const float*)Bd, L.noff, L.npar, L.Bq,
+                              L.bq_scale, P.alloc<unsigned>(1), s);
+    }
   }
   CK(cudaGetLastError());
 }
@@ -1613,6 +1630,8 @@ void alloc_solve(gamblet_ctx* h) {
       LevelDev& L = h->lv[k];
       CgLevel c;
       c.Bd = L.Bd;
+      c.Bq = L.Bq;
+      c.bq_inv_scale = L.bq_scale;
       c.Dinv = L.Dinv;
       c.off = L.off;
       c.noff = L.noff;
@@ -1894,7 +1913,7 @@ void cg_work_per_iteration(gamblet_ctx* h) {
     // (3 active slots); vector kernels: x, r, z, p, Ap, Dinv
     const LevelDev& L = h->lv[l + 2];
     const double sz = (double)sizeof(T);
-    h->cg_bytes_spmv[l] = sz * ((double)L.noff * L.npar * 9 + 6.0 * L.npar);
+    h->cg_bytes_spmv[l] = (L.Bq ? 32.0 : 9.0 * sz) * ((double)L.noff * L.npar) + sz * 6.0 * L.npar;
     h->cg_flops_spmv[l] = 2.0 * 9.0 * L.noff * L.npar;
     h->cg_bytes_vec[l] = sz * 3.0 * L.npar * 12;
     h->cg_flops_vec[l] = 3.0 * L.npar * 12;

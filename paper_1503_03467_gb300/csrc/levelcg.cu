@@ -11,6 +11,8 @@
 // offsets reads the matrix with unit stride and the vector from shared
 // memory.  The CG is preconditioned by the inverse of each parent's 3x3
 // diagonal detail block (block Jacobi).  Dots accumulate in float64.
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -154,6 +156,20 @@ __global__ void k_cg_start(CgScalars* sc, int nlev, int nlev_on, double tol2, in
   *any_active = act;
 }
 
+// Entries 0..8 of a 32-byte float16 block record (two 16-byte words).
+template <typename T>
+__device__ __forceinline__ void unpack9(const uint4& u0, const uint4& u1, T* b) {
+  const __half2* h0 = reinterpret_cast<const __half2*>(&u0);
+  const __half2* h1 = reinterpret_cast<const __half2*>(&u1);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __half22float2(h0[i]);
+    b[2 * i] = (T)f.x;
+    b[2 * i + 1] = (T)f.y;
+  }
+  b[8] = (T)__low2float(h1[0]);
+}
+
 // Ap = B p over the 3x3 detail blocks; pAp += p.Ap.  One CTA = one tile of
 // T x T parents (T = 16, or 8 with four threads per parent splitting the
 // offsets when the stencil is wide; or the whole lattice when smaller).
@@ -201,28 +217,60 @@ __global__ void __launch_bounds__(256) k_cg_spmv(const CgLevel* __restrict__ lv,
     demorton((uint32_t)p, px, py);
     lx = px - x0 + R;
     ly = py - y0 + R;
-    const T* Bd = (const T*)L.Bd;
     const int64_t np = L.npar;
-    // two offsets per pass: their 18 matrix loads are in flight together
-    for (int o = sub; o < L.noff; o += 2 * spp) {
-      const int o2 = o + spp;
-      const bool two = o2 < L.noff;
-      const int2 d = L.off[o];
-      const int2 d2 = L.off[two ? o2 : o];
-      const T* B = Bd + (int64_t)o * 9 * np + p;
-      const T* B2 = Bd + (int64_t)(two ? o2 : o) * 9 * np + p;
-      T b[9], b2[9];
+    if (L.Bq) {
+      // 32-byte float16 records: two 16-byte loads per block
+      const uint4* Bq = reinterpret_cast<const uint4*>(L.Bq);
+      for (int o = sub; o < L.noff; o += 2 * spp) {
+        const int o2 = o + spp;
+        const bool two = o2 < L.noff;
+        const int2 d = L.off[o];
+        const int2 d2 = L.off[two ? o2 : o];
+        const uint4 u0 = __ldg(Bq + ((int64_t)o * np + p) * 2);
+        const uint4 u1 = __ldg(Bq + ((int64_t)o * np + p) * 2 + 1);
+        uint4 w0 = make_uint4(0, 0, 0, 0), w1 = make_uint4(0, 0, 0, 0);
+        if (two) {
+          w0 = __ldg(Bq + ((int64_t)o2 * np + p) * 2);
+          w1 = __ldg(Bq + ((int64_t)o2 * np + p) * 2 + 1);
+        }
+        T b[9], b2[9];
+        unpack9<T>(u0, u1, b);
+        unpack9<T>(w0, w1, b2);
+        const int c = (ly + d.y) * TS + lx + d.x;
+        const int c2 = (ly + d2.y) * TS + lx + d2.x;
+        const T a0 = xs[c], a1 = xs[TS * TS + c], a2 = xs[2 * TS * TS + c];
+        const T e0 = xs[c2], e1 = xs[TS * TS + c2], e2 = xs[2 * TS * TS + c2];
+        y0v += b[0] * a0 + b[1] * a1 + b[2] * a2 + b2[0] * e0 + b2[1] * e1 + b2[2] * e2;
+        y1v += b[3] * a0 + b[4] * a1 + b[5] * a2 + b2[3] * e0 + b2[4] * e1 + b2[5] * e2;
+        y2v += b[6] * a0 + b[7] * a1 + b[8] * a2 + b2[6] * e0 + b2[7] * e1 + b2[8] * e2;
+      }
+      const T si = (T)*L.bq_inv_scale;  // a power of two: exact
+      y0v *= si;
+      y1v *= si;
+      y2v *= si;
+    } else {
+      const T* Bd = (const T*)L.Bd;
+      // two offsets per pass: their 18 matrix loads are in flight together
+      for (int o = sub; o < L.noff; o += 2 * spp) {
+        const int o2 = o + spp;
+        const bool two = o2 < L.noff;
+        const int2 d = L.off[o];
+        const int2 d2 = L.off[two ? o2 : o];
+        const T* B = Bd + (int64_t)o * 9 * np + p;
+        const T* B2 = Bd + (int64_t)(two ? o2 : o) * 9 * np + p;
+        T b[9], b2[9];
 #pragma unroll
-      for (int e = 0; e < 9; ++e) b[e] = B[e * np];
+        for (int e = 0; e < 9; ++e) b[e] = B[e * np];
 #pragma unroll
-      for (int e = 0; e < 9; ++e) b2[e] = two ? B2[e * np] : T(0);
-      const int c = (ly + d.y) * TS + lx + d.x;
-      const int c2 = (ly + d2.y) * TS + lx + d2.x;
-      const T a0 = xs[c], a1 = xs[TS * TS + c], a2 = xs[2 * TS * TS + c];
-      const T e0 = xs[c2], e1 = xs[TS * TS + c2], e2 = xs[2 * TS * TS + c2];
-      y0v += b[0] * a0 + b[1] * a1 + b[2] * a2 + b2[0] * e0 + b2[1] * e1 + b2[2] * e2;
-      y1v += b[3] * a0 + b[4] * a1 + b[5] * a2 + b2[3] * e0 + b2[4] * e1 + b2[5] * e2;
-      y2v += b[6] * a0 + b[7] * a1 + b[8] * a2 + b2[6] * e0 + b2[7] * e1 + b2[8] * e2;
+        for (int e = 0; e < 9; ++e) b2[e] = two ? B2[e * np] : T(0);
+        const int c = (ly + d.y) * TS + lx + d.x;
+        const int c2 = (ly + d2.y) * TS + lx + d2.x;
+        const T a0 = xs[c], a1 = xs[TS * TS + c], a2 = xs[2 * TS * TS + c];
+        const T e0 = xs[c2], e1 = xs[TS * TS + c2], e2 = xs[2 * TS * TS + c2];
+        y0v += b[0] * a0 + b[1] * a1 + b[2] * a2 + b2[0] * e0 + b2[1] * e1 + b2[2] * e2;
+        y1v += b[3] * a0 + b[4] * a1 + b[5] * a2 + b2[3] * e0 + b2[4] * e1 + b2[5] * e2;
+        y2v += b[6] * a0 + b[7] * a1 + b[8] * a2 + b2[6] * e0 + b2[7] * e1 + b2[8] * e2;
+      }
     }
   }
   for (int o = 1; o < spp; o <<= 1) {
@@ -504,6 +552,62 @@ void launch_cg_level_setup(const T* Ahat, int noff, int o0, int64_t npar, const 
 }
 template void launch_cg_level_setup<float>(const float*, int, int, int64_t, const uint32_t*,
                                            float*, float*, cudaStream_t);
+
+// Largest |x| of a float array (non-negative floats order like their bits).
+__global__ void k_absmax(const float* __restrict__ x, int64_t n, unsigned* amax) {
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(x[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(amax, __float_as_uint(m));
+}
+
+// One thread per block (o, p): its 3x3 detail block as one 32-byte record.
+__global__ void k_block_records(const float* __restrict__ Ahat, int noff, int64_t npar,
+                                const unsigned* __restrict__ amax, uint4* Bq, float* inv_scale) {
+  const float m = __uint_as_float(*amax);
+  // 2^e <= m < 2^(e+1); the scale 2^(14 - e) puts the largest entry in [2^14, 2^15)
+  const int e = m > 0.f ? ((__float_as_int(m) >> 23) & 255) - 127 : 0;
+  const int a = max(min(14 - e, 100), -100);
+  const float sc = ldexpf(1.f, a);
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t == 0) *inv_scale = ldexpf(1.f, -a);
+  if (t >= (int64_t)noff * npar) return;
+  const float* A = Ahat + t * 16;
+  float v[16];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float4 row = __ldg(reinterpret_cast<const float4*>(A + 4 * r));
+    v[3 * r] = row.x * sc;
+    v[3 * r + 1] = row.y * sc;
+    v[3 * r + 2] = row.z * sc;
+  }
+#pragma unroll
+  for (int i = 9; i < 16; ++i) v[i] = 0.f;
+  uint4 w[2];
+  __half2* h = reinterpret_cast<__half2*>(w);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) h[i] = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+  Bq[2 * t] = w[0];
+  Bq[2 * t + 1] = w[1];
+}
+
+void launch_cg_block_records(const float* Ahat, const float* Bd, int noff, int64_t npar,
+                             void* Bq, float* inv_scale, unsigned* amax, cudaStream_t s) {
+  const int64_t n = (int64_t)noff * npar;
+  if (n <= 0) return;
+  cudaMemsetAsync(amax, 0, sizeof(unsigned), s);
+  const int64_t nv = 9 * n;
+  const int64_t want = (nv + 255) / 256;
+  count_launch();
+  k_absmax<<<(unsigned)(want < 4096 ? want : 4096), 256, 0, s>>>(Bd, nv, amax);
+  count_launch();
+  k_block_records<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ahat, noff, npar, amax,
+                                                              reinterpret_cast<uint4*>(Bq),
+                                                              inv_scale);
+}
 template void launch_cg_level_setup<double>(const double*, int, int, int64_t, const uint32_t*,
                                             double*, double*, cudaStream_t);
 
@@ -669,14 +773,21 @@ __global__ void __launch_bounds__(256) k_cgm_spmv(const CgLevel* __restrict__ lv
     lx = px - x0 + R;
     ly = py - y0 + R;
     const T* Bd = (const T*)L.Bd;
+    const uint4* Bq = reinterpret_cast<const uint4*>(L.Bq);
     const int64_t np = L.npar;
     for (int o = sub; o < L.noff; o += spp) {
       const int2 d = L.off[o];
       const int c = (ly + d.y) * TS + lx + d.x;
-      const T* B = Bd + (int64_t)o * 9 * np + p;
       T b[9];
+      if (Bq) {  // the block records of the single-right-hand-side CG
+        const uint4 u0 = __ldg(Bq + ((int64_t)o * np + p) * 2);
+        const uint4 u1 = __ldg(Bq + ((int64_t)o * np + p) * 2 + 1);
+        unpack9<T>(u0, u1, b);
+      } else {
+        const T* B = Bd + (int64_t)o * 9 * np + p;
 #pragma unroll
-      for (int e = 0; e < 9; ++e) b[e] = B[e * np];
+        for (int e = 0; e < 9; ++e) b[e] = B[e * np];
+      }
 #pragma unroll
       for (int r = 0; r < kMaxRhs; ++r) {
         if (r < nrhs) {
@@ -688,6 +799,13 @@ __global__ void __launch_bounds__(256) k_cgm_spmv(const CgLevel* __restrict__ lv
         }
       }
     }
+  }
+  if (own && L.Bq) {
+    const T si = (T)*L.bq_inv_scale;  // a power of two: exact
+#pragma unroll
+    for (int r = 0; r < kMaxRhs; ++r)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) yv[r][a] *= si;
   }
 #pragma unroll
   for (int r = 0; r < kMaxRhs; ++r)
