@@ -1,0 +1,524 @@
+// host.cuh - types and helpers shared by the host translation units of the
+// library (gamblet.cu: setup, solve, gradients and the C ABI; plan.cu: the
+// symbolic plan of a geometry; tune.cu: the launch-shape autotuner).  None
+// of it is exported: the library is built with hidden visibility and only
+// the functions of include/gamblet.h are public.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/gamblet.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace gb {
+// launch counters (gamblet.cu)
+long long launches_now();
+void uncount_launches(long long n);
+void count_launches(long long n);
+
+namespace hs {
+
+
+struct GbError {
+  gamblet_status st;
+  std::string msg;
+};
+
+[[noreturn]] inline void fail(gamblet_status st, const std::string& msg) {
+  throw GbError{st, msg};
+}
+
+#define CK(x)                                                                           \
+  do {                                                                                  \
+    cudaError_t e_ = (x);                                                               \
+    if (e_ != cudaSuccess) {                                                            \
+      if (e_ == cudaErrorMemoryAllocation)                                              \
+        fail(GAMBLET_ERR_OUT_OF_MEMORY, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+      fail(GAMBLET_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_));          \
+    }                                                                                   \
+  } while (0)
+
+// ---------------------------------------------------------------- device memory
+// Stream-ordered allocations from a memory pool that the library owns, one
+// per device.  Its release threshold is unlimited, so freed blocks stay
+// cached for the next handle and a repeated setup does not pay for
+// cudaMalloc; the device's default pool, which the caller's own allocators
+// may share, keeps its settings.  The cached memory is returned when the
+// process exits.
+inline cudaMemPool_t library_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) fail(GAMBLET_ERR_UNSUPPORTED, "device ordinal beyond 63");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t mp = nullptr;
+    CK(cudaMemPoolCreate(&mp, &props));
+    uint64_t thr = UINT64_MAX;
+    CK(cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr));
+    pools[dev] = mp;
+  }
+  return pools[dev];
+}
+
+struct Pool {
+  std::vector<void*> ptrs;
+  int64_t bytes = 0;
+  cudaStream_t s = nullptr;
+  cudaMemPool_t mp = nullptr;
+  template <typename T>
+  T* alloc(int64_t n) {
+    if (n <= 0) n = 1;
+    if (!mp) mp = library_pool();
+    void* p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, sizeof(T) * (size_t)n, mp, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(GAMBLET_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(sizeof(T) * n) + " bytes");
+    }
+    ptrs.push_back(p);
+    bytes += (int64_t)sizeof(T) * n;
+    return static_cast<T*>(p);
+  }
+  template <typename T>
+  T* zeros(int64_t n, cudaStream_t s) {
+    T* p = alloc<T>(n);
+    CK(cudaMemsetAsync(p, 0, sizeof(T) * (size_t)std::max<int64_t>(n, 1), s));
+    return p;
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v, cudaStream_t s) {
+    T* p = alloc<T>((int64_t)v.size());
+    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
+    return p;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+    ptrs.clear();
+    bytes = 0;
+  }
+  ~Pool() { release(); }
+};
+
+inline bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copy n elements from caller memory (host or device) into a device buffer.
+template <typename T>
+void to_device(Pool& pool, T*& dst, const T* src, int64_t n, cudaStream_t s) {
+  if (!dst) dst = pool.alloc<T>(n);
+  if (n > 0) CK(cudaMemcpyAsync(dst, src, sizeof(T) * (size_t)n, cudaMemcpyDefault, s));
+}
+
+// Caller memory as a device pointer: device memory is read in place (the
+// calls that use this finish with a stream synchronisation), host memory is
+// copied into a pool buffer.
+template <typename T>
+const T* as_device(Pool& pool, const T* src, int64_t n, cudaStream_t s) {
+  if (is_device_ptr(src)) return src;
+  T* dst = nullptr;
+  to_device(pool, dst, src, n, s);
+  return dst;
+}
+
+// ---------------------------------------------------------------- offset sets
+using Off = std::pair<int, int>;  // (dx, dy)
+
+struct OffSet {
+  std::vector<int2> v;
+  std::map<Off, int> idx;
+  void add(int dx, int dy) {
+    Off k{dx, dy};
+    if (idx.count(k)) return;
+    idx[k] = (int)v.size();
+    v.push_back(make_int2(dx, dy));
+  }
+  int find(int dx, int dy) const {
+    auto it = idx.find(Off{dx, dy});
+    return it == idx.end() ? -1 : it->second;
+  }
+  int size() const { return (int)v.size(); }
+};
+
+// i^rho offsets of Sec. 4.10 in cell units, row-major (dy, dx).
+OffSet neighbour_offsets(double rho, int rule);
+
+// Symbolic data of one localized level k (patch, Galerkin, conversion).
+struct SymLevel {
+  OffSet O;                       // block offsets of Ahat^(k) (level k-1 cell units)
+  std::vector<int> pair_idx;      // NB x NB
+  OffSet WIN, S;                  // window and output cell offsets
+  OffSet Sp;                      // the half-plane of S that is computed
+  std::vector<int> l1_ptr, l2_ptr;
+  std::vector<int2> l1_pairs, l2_pairs;
+  std::vector<int> map_next;      // conversion map to level k-1 blocks (or level-1 map)
+  // 2 x 2 row tiles (k_galerkin_tile): window positions u of the tile as a
+  // box [wmin, wmin + W)^2 relative to the tile origin; per u the offsets o
+  // with, for each of the four rows, the neighbour index j (0xff = none);
+  // output targets c with the index d in Sp of c - row, per row (-1 = none)
+  int tile_wmin = 0, tile_W = 0;
+  std::vector<int> t1_ptr;
+  std::vector<int2> t1;           // (o, j of rows 0..3 packed in bytes)
+  std::vector<int4> t2;           // (c.x, c.y, d0 | d1 << 16, d2 | d3 << 16)
+  // per target e, the pairs (j, u) whose window position u = c + N_j lies in
+  // the window of some row of the tile (packed j | u << 8, ranges t2p_ptr);
+  // targets are sorted by decreasing pair count so that the targets that a
+  // warp handles together have about the same work
+  std::vector<int> t2p_ptr, t2p;
+};
+
+// ---------------------------------------------------------------- handle
+struct LevelDev {
+  int k = 0;
+  int L = 0;          // 2^k
+  int64_t ncell = 0;  // stored cells, 4 npar (4^k for a full square)
+  int64_t npar = 0;   // stored level-(k-1) cells (4^(k-1) for a full square)
+  std::vector<uint32_t> pmask_h;
+  uint32_t* pmask = nullptr;
+  int n_active = 0, nJ = 0;
+  // localized
+  const int2* off = nullptr;
+  int noff = 0;
+  std::vector<int2> off_h;
+  void* Ahat = nullptr;      // T
+  double* Ahat64 = nullptr;  // level q float64 copy (mixed) or alias
+  void* Rhat = nullptr;      // T, npar rows
+  void* RT = nullptr;        // T, Rhat regrouped by parent (prolongation)
+  const int* pair_idx = nullptr;
+  int shape[4] = {0, 0, 0, 0};  // launch shapes used: patch spp, patch gather, Galerkin variant, CG spp
+  // exact (dense)
+  double* D = nullptr;       // transformed dense Ahat^(k)
+  double* Bc = nullptr;      // Cholesky factor of B^(k)
+  double* Rh = nullptr;      // dense Rhat (npar x ncell)
+  int32_t* det = nullptr;
+  int32_t* par = nullptr;
+  std::vector<int32_t> det_h, par_h;
+  // solve buffers (T)
+  void* ghat = nullptr;  // ncell
+  void* v = nullptr;     // ncell
+  void* w = nullptr;     // ncell
+  void* cr = nullptr;
+  void* cz = nullptr;
+  void* cp = nullptr;
+  void* cAp = nullptr;
+  double* wc = nullptr;  // compact detail vector (exact path)
+  // level CG operator (localized path)
+  void* Bd = nullptr;    // [noff][9][npar]
+  void* Bq = nullptr;    // 32-byte float16 block records of the level CG (mixed path), or NULL
+  float* bq_scale = nullptr;  // device: inverse scale of Bq
+  void* Dinv = nullptr;  // [9][npar]
+  int R = 0;             // halo radius
+  int o0 = -1;           // index of the zero offset in O_k (diagonal blocks)
+};
+
+// Per-kernel CUDA-event timing on the library's stream (opts.profile).
+struct Prof {
+  struct Stat {
+    std::string name;
+    long long launches = 0;
+    double ms = 0, bytes = 0, flops = 0;
+  };
+  struct Pend {
+    int id;
+    cudaEvent_t a, b;
+    double bytes, flops;
+  };
+  bool on = false;
+  std::vector<Stat> stats;
+  std::vector<Pend> pend;
+  std::vector<cudaEvent_t> pool;
+  int id(const std::string& name) {
+    for (size_t i = 0; i < stats.size(); ++i)
+      if (stats[i].name == name) return (int)i;
+    stats.push_back(Stat{name});
+    return (int)stats.size() - 1;
+  }
+  cudaEvent_t ev() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    return e;
+  }
+  // returns a token for end(); -1 when profiling is off
+  int begin(const std::string& name, double bytes, double flops, cudaStream_t s) {
+    if (!on) return -1;
+    Pend p{id(name), ev(), ev(), bytes, flops};
+    CK(cudaEventRecord(p.a, s));
+    pend.push_back(p);
+    return (int)pend.size() - 1;
+  }
+  void end(int tok, cudaStream_t s) {
+    if (tok < 0) return;
+    CK(cudaEventRecord(pend[tok].b, s));
+  }
+  // call after the stream has been synchronised
+  void resolve() {
+    for (Pend& p : pend) {
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, p.a, p.b));
+      Stat& st = stats[p.id];
+      st.launches += 1;
+      st.ms += ms;
+      st.bytes += p.bytes;
+      st.flops += p.flops;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pend.clear();
+  }
+  void add(const std::string& name, double bytes, double flops) {
+    if (!on) return;
+    Stat& st = stats[id(name)];
+    st.bytes += bytes;
+    st.flops += flops;
+  }
+  ~Prof() {
+    for (Pend& p : pend) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+struct Plan;  // symbolic plan of a geometry (defined with the setup code)
+
+}  // namespace hs
+}  // namespace gb
+
+using namespace gb;
+using namespace gb::hs;
+
+struct gamblet_ctx {
+  Prof prof;
+  std::shared_ptr<const Plan> plan;
+  gamblet_opts opts;
+  cudaStream_t s = nullptr;
+  int q = 0;
+  int n = 0;           // fine unknowns
+  int nprob = 1;       // independent problems packed in the hierarchy
+  int kmax = 0;        // finest level whose detail component a solve adds (q = all)
+  // level-q initialisation by the mass matrix: nodal coefficients are
+  // u_phi = M^-1,loc U (Minv[i][j] on the patch offsets nbrq)
+  bool mass = false;
+  double* Minv = nullptr;
+  int2* nbrq = nullptr;
+  int NBq = 0;
+  bool exact = false;
+  bool mixed = false;
+  int num_sms = 1;
+  Pool pool;
+  int32_t* morton_of = nullptr;   // n
+  int32_t* unknown_of = nullptr;  // 4^q
+  std::vector<int32_t> morton_of_h;
+  std::vector<LevelDev> lv;       // index k (0 unused)
+  OffSet N;                       // neighbour offsets
+  int jc = 0;
+  int2* nbr = nullptr;
+  // level 1
+  double* A1 = nullptr;      // plain 4 x 4 (copy, for getters)
+  double* A1L = nullptr;     // Cholesky factor
+  void* g1 = nullptr;        // T, 4
+  void* U1 = nullptr;        // T, 4
+  const int* l1map = nullptr;
+  // CG batch
+  CgLevel* cg_lv = nullptr;
+  CgLevel* cg_lv_h = nullptr;  // pinned staging copy (the upload does not wait for the setup)
+  CgScalars* cg_sc = nullptr;
+  int* any_active = nullptr;
+  int* any_active_h = nullptr;  // pinned
+  int cg_blocks = 0;
+  int cg_spmv_blocks = 0;
+  int cg_nlev = 0;
+  int cg_max_ts = 1;
+  cudaGraphExec_t cg_exec = nullptr;
+  bool cg_while = false;           // cg_exec is a device-side while loop
+  int* cg_loop_count = nullptr;    // passes of that loop
+  int* cg_stats = nullptr;         // device: level-CG iterations per level, [32] not converged,
+                                   // [33] passes of the device-side loop
+  // per level and CG iteration: algorithmic traffic and flops of the SpMV and
+  // of the vector kernels
+  std::vector<double> cg_bytes_spmv, cg_flops_spmv, cg_bytes_vec, cg_flops_vec;
+  // outer: the fine operator as a Morton node stencil (float64), its cell
+  // offsets, and a scratch vector for the untransformed SpMV input
+  double* qst = nullptr;
+  const int2* qoff = nullptr;
+  int qns = 0;
+  double* xplain = nullptr;
+  double* u64 = nullptr;
+  double* r64 = nullptr;
+  double* z64 = nullptr;
+  double* p64 = nullptr;
+  double* q64 = nullptr;
+  double* g64 = nullptr;
+  void* rT = nullptr;
+  void* zT = nullptr;
+  double* dots = nullptr;
+  double* dots_h = nullptr;  // pinned
+  int* status = nullptr;
+  int* status_h = nullptr;   // pinned
+  double setup_ms = 0;
+  double patch_tol = 0;         // resolved patch tolerance (< 0: Cholesky)
+  int* patch_stats = nullptr;   // device: max, sum, count over all levels
+  int patch_iters_max = 0;
+  double patch_iters_mean = 0;
+  std::vector<double> patch_flops_iter_k;  // per level: flops of one iteration of one patch
+  std::vector<double> patch_mma_flops_k;   // per level: tensor-core flops of one window product
+  std::vector<bool> patch_cluster_k;        // per level: patch CG over a thread-block cluster
+  int level_iters_acc[32];
+  bool level_not_conv = false;
+  const char* dplan = nullptr;  // device copy of the plan tables (localized setup)
+};
+
+namespace gb {
+namespace hs {
+
+template <typename T>
+constexpr bool is_f32() {
+  return sizeof(T) == 4;
+}
+
+inline void check_status(gamblet_ctx* h, const char* where) {
+  CK(cudaMemcpyAsync(h->status_h, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (*h->status_h == DEV_NOT_SPD)
+    fail(GAMBLET_ERR_NOT_SPD, std::string("non-positive pivot in ") + where);
+  if (*h->status_h == DEV_TIMEOUT)
+    fail(GAMBLET_ERR_CUDA, std::string("a tensor-core completion wait gave up in ") + where);
+}
+
+// ------------------------------------------------------------ symbolic plan
+// Everything the localized setup derives from the geometry alone (q, rho,
+// neighbour rule and the fine operator's block offsets): offset sets, the
+// patch block lists and the Galerkin pair lists of every level.  It does not
+// depend on coefficient values, so it is built once per geometry and kept in
+// a process-wide cache (like an FFT plan).
+// Tables of the tensor-core patch solves (patch_mma.cu) for windows of G x G
+// coarse cells, G = 1 and 2: the union of the windows' neighbourhoods, which
+// patches each union parent belongs to, the stored blocks between union
+// parents, the right-hand-side blocks and the union index of every patch
+// neighbour.  All are offsets, so one table serves every window of the level.
+struct MmaWin {
+  bool ok = false;  // fits one CTA (at most three M-tiles and the shared memory)
+  int NP = 0, nU = 0, n = 0, Kp = 0, Mt = 0, diag_o = -1;
+  std::vector<int2> U;
+  std::vector<int> ubits, rhs_o, outmap;
+  std::vector<int4> pairs;
+  size_t off[5] = {};  // U, ubits, pairs, rhs_o, outmap in Plan::packed
+};
+
+struct PlanLevel {
+  SymLevel S;
+  MmaWin mwin[2];  // G = 1, G = 2
+  std::vector<int4> half, adj;   // patch CG: stored blocks and per-row adjacency
+  std::vector<int> adj_ptr, diag_h;
+  int spp = 1;
+  double flops_iter = 0;
+  std::vector<int> map_next;          // block conversion map (or the level-1 map)
+  OffSet O_next;
+  // byte offsets of this level's tables in Plan::packed
+  enum { kPairIdx, kHalf, kAdjPtr, kAdj, kDiagH, kWin, kL1Ptr, kL1Pairs, kOut, kL2Ptr, kL2Pairs,
+         kT1Ptr, kT1, kT2, kT2pPtr, kT2p, kOffNext, kMapNext, kNumTables };
+  size_t table_off[kNumTables] = {};
+};
+struct Plan {
+  std::vector<PlanLevel> lv;  // index k
+  std::string key;            // geometry key of the process-wide cache
+  // every table of every level in one 16-byte aligned buffer, so that a setup
+  // moves the whole plan to the device with one copy
+  std::vector<char> packed;
+};
+
+// Device address of table t of level k in a device copy of Plan::packed.
+template <typename E>
+inline const E* plan_table(const char* dev, const PlanLevel& pl, int t) {
+  return reinterpret_cast<const E*>(dev + pl.table_off[t]);
+}
+
+int half_code(const OffSet& Sp, int dx, int dy);
+OffSet blocks_from_cells(const OffSet& S, const OffSet& Sp, int km1, std::vector<int>& map);
+
+// ---- plan.cu
+SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k);
+std::shared_ptr<const Plan> cached_plan(int q, double rho, int rule, const OffSet& Oq,
+                                        const OffSet& N);
+
+// ---- tune.cu
+// Levels smaller than kTuneMinParents keep the fixed launch rules.
+constexpr int64_t kTuneMinParents = 16384;
+// The tensor-core patch solve rounds the scaled patch matrix to float16
+// (relative 2^-11 per entry), so it is a candidate only where the requested
+// patch tolerance is no tighter than that rounding.
+constexpr double kMmaMinPatchTol = 4.8e-4;
+// The level CG reads float16 block records on the mixed path when the
+// requested level tolerance is this loose (the bench's is 0.05); tighter
+// tolerances keep the float32 blocks.
+constexpr double kHalfLevelTol = 1e-3;
+
+bool tune_lookup(const std::string& key, int* v);
+void tune_store(const std::string& key, int v);
+double patch_flops(gamblet_ctx* h, int k);
+template <typename T>
+bool cluster_geometry(const PatchPcgGeom& gp, const PlanLevel& pl, PatchClusterGeom& c);
+PatchMmaGeom mma_geometry(gamblet_ctx* h, int k, int G, const char* dplan, const PlanLevel& pl);
+template <typename T>
+int tune_patch_shape(gamblet_ctx* h, int k, PatchPcgGeom& gp, T* Rhat, const PatchMmaGeom* mg,
+                     const bool* mma_ok);
+template <typename T>
+void tune_galerkin_variant(gamblet_ctx* h, int k, GalerkinGeom& gg, const T* Ahat, const T* Rhat,
+                           T* Acell);
+template <typename T>
+int tuned_cg_spp(gamblet_ctx* h, int k, const CgLevel& c);
+
+// ---- gamblet.cu
+gamblet_status set_error(const GbError& e);
+// yhat = Ahat^(q) xhat in float64 (the outer iteration's operator)
+void outer_spmv(gamblet_ctx* h, const double* xhat, double* yhat);
+// ---- solve_host.cu
+// level-CG iterations per captured chunk when the driver offers no
+// conditional nodes (the while-loop graph is used otherwise)
+constexpr int kCgChunk = 8;
+// The level-CG iteration of every level as one CUDA graph (device-side loop).
+template <typename T>
+void build_cg_graph(gamblet_ctx* h, int chunk, double tol2, int maxit);
+void flush_level_stats(gamblet_ctx* h);
+template <typename T>
+T* as_T(gamblet_ctx* h, double* v64, void* vT, int64_t n, bool to);
+template <typename T>
+void apply_G(gamblet_ctx* h, const T* in, T* out, int inverse_last);
+
+}  // namespace hs
+}  // namespace gb

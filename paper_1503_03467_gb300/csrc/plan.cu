@@ -1,0 +1,403 @@
+// plan.cu - the symbolic plan of a geometry: everything the localized setup
+// (Algorithm 2 with Definition defb) derives from the geometry alone - the
+// patch neighbourhoods i^rho (Sec. 4.10), the block offset sets of every
+// level A^(k) (exact Minkowski sums of the interpolation and operator
+// supports), the patch block lists, the Galerkin pair lists (Eq. eqhuhiuv)
+// and the tables of the tensor-core patch windows - built once per geometry
+// and cached process-wide.
+#include "host.cuh"
+
+namespace gb {
+namespace hs {
+
+// i^rho offsets of Sec. 4.10 in cell units, row-major (dy, dx).
+OffSet neighbour_offsets(double rho, int rule) {
+  OffSet N;
+  const int R = (int)std::floor(rho) + 1;
+  for (int dy = -R; dy <= R; ++dy)
+    for (int dx = -R; dx <= R; ++dx) {
+      bool ok;
+      if (rule == 0) {
+        const double ex = std::max(std::abs(dx) - 1, 0), ey = std::max(std::abs(dy) - 1, 0);
+        ok = ex * ex + ey * ey <= rho * rho * (1 + 1e-12);
+      } else {
+        ok = std::max(std::abs(dx), std::abs(dy)) <= rho + 1e-12;
+      }
+      if (ok) N.add(dx, dy);
+    }
+  return N;
+}
+
+// ------------------------------------------------------------ symbolic build
+SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
+  SymLevel S;
+  S.O = O_k;
+  const int NB = N.size();
+  const int Lpar = 1 << (k - 1);  // level k-1 lattice side
+  S.pair_idx.assign((size_t)NB * NB, -1);
+  for (int a = 0; a < NB; ++a)
+    for (int b = 0; b < NB; ++b)
+      S.pair_idx[(size_t)a * NB + b] = O_k.find(N.v[b].x - N.v[a].x, N.v[b].y - N.v[a].y);
+  // window: positions p' = i + WIN_w reachable from the patch through O_k
+  for (int j = 0; j < NB; ++j)
+    for (const int2& o : O_k.v) {
+      const int wx = N.v[j].x - o.x, wy = N.v[j].y - o.y;  // row parent p' with p - p' = o
+      if (std::abs(wx) <= Lpar - 1 && std::abs(wy) <= Lpar - 1) S.WIN.add(wx, wy);
+    }
+  S.l1_ptr.assign(S.WIN.size() + 1, 0);
+  std::vector<std::vector<int2>> l1(S.WIN.size());
+  for (int j = 0; j < NB; ++j)
+    for (int o = 0; o < O_k.size(); ++o) {
+      const int w = S.WIN.find(N.v[j].x - O_k.v[o].x, N.v[j].y - O_k.v[o].y);
+      if (w >= 0) l1[w].push_back(make_int2(j, o));
+    }
+  for (int w = 0; w < S.WIN.size(); ++w) {
+    S.l1_ptr[w + 1] = S.l1_ptr[w] + (int)l1[w].size();
+    S.l1_pairs.insert(S.l1_pairs.end(), l1[w].begin(), l1[w].end());
+  }
+  // outputs d with WIN_w = d + N_j
+  for (int w = 0; w < S.WIN.size(); ++w)
+    for (int j = 0; j < NB; ++j) {
+      const int dx = S.WIN.v[w].x - N.v[j].x, dy = S.WIN.v[w].y - N.v[j].y;
+      if (std::abs(dx) <= Lpar - 1 && std::abs(dy) <= Lpar - 1) S.S.add(dx, dy);
+    }
+  for (const int2& d : S.S.v)
+    if (d.y > 0 || (d.y == 0 && d.x >= 0)) S.Sp.add(d.x, d.y);
+  std::vector<std::vector<int2>> l2(S.Sp.size());
+  for (int d = 0; d < S.Sp.size(); ++d)
+    for (int j = 0; j < NB; ++j) {
+      const int w = S.WIN.find(S.Sp.v[d].x + N.v[j].x, S.Sp.v[d].y + N.v[j].y);
+      if (w >= 0) l2[d].push_back(make_int2(j, w));
+    }
+  S.l2_ptr.assign(S.Sp.size() + 1, 0);
+  for (int d = 0; d < S.Sp.size(); ++d) {
+    S.l2_ptr[d + 1] = S.l2_ptr[d] + (int)l2[d].size();
+    S.l2_pairs.insert(S.l2_pairs.end(), l2[d].begin(), l2[d].end());
+  }
+  // 2 x 2 tiles: row r sits at (r & 1, r >> 1) from the tile origin
+  int wmin = 0, wmax = 0;
+  for (const int2& w : S.WIN.v) {
+    wmin = std::min(wmin, std::min(w.x, w.y));
+    wmax = std::max(wmax, std::max(w.x, w.y));
+  }
+  const int W = wmax - wmin + 2;
+  S.tile_wmin = wmin;
+  S.tile_W = W;
+  S.t1_ptr.assign((size_t)W * W + 1, 0);
+  for (int uy = 0; uy < W; ++uy)
+    for (int ux = 0; ux < W; ++ux) {
+      const int u = uy * W + ux;
+      for (int o = 0; o < O_k.size(); ++o) {
+        uint32_t packed = 0;
+        bool any = false;
+        for (int r = 0; r < 4; ++r) {
+          // t_i(w) gathers A_hat[o][i + w] R_hat_i[j] with N_j = w + O_o
+          const int wx = ux + wmin - (r & 1), wy = uy + wmin - (r >> 1);
+          int j = S.WIN.find(wx, wy) >= 0 ? N.find(wx + O_k.v[o].x, wy + O_k.v[o].y) : -1;
+          if (j > 254) fail(GAMBLET_ERR_UNSUPPORTED, "neighbourhood too large for tiled Galerkin");
+          if (j >= 0) any = true;
+          packed |= (uint32_t)(j >= 0 ? j : 0xff) << (8 * r);
+        }
+        if (any) S.t1.push_back(make_int2(o, (int)packed));
+      }
+      S.t1_ptr[u + 1] = (int)S.t1.size();
+    }
+  std::set<std::pair<int, int>> targets;
+  for (int r = 0; r < 4; ++r)
+    for (const int2& d : S.Sp.v) targets.insert({d.y + (r >> 1), d.x + (r & 1)});
+  // window positions holding a nonzero t_r(u) for some row r of the tile
+  std::set<std::pair<int, int>> win4;
+  for (int r = 0; r < 4; ++r)
+    for (const int2& w : S.WIN.v) win4.insert({w.y + (r >> 1), w.x + (r & 1)});
+  struct Target {
+    int4 t;
+    std::vector<int> pairs;
+  };
+  std::vector<Target> tl;
+  for (const auto& c : targets) {
+    const int cx = c.second, cy = c.first;
+    int dr[4];
+    for (int r = 0; r < 4; ++r) dr[r] = S.Sp.find(cx - (r & 1), cy - (r >> 1));
+    if (S.Sp.size() > 32767) fail(GAMBLET_ERR_UNSUPPORTED, "output stencil too large for tiled Galerkin");
+    auto pack = [](int lo, int hi) {
+      return (int)(((uint32_t)lo & 0xffffu) | ((uint32_t)hi << 16));
+    };
+    Target t;
+    t.t = make_int4(cx, cy, pack(dr[0], dr[1]), pack(dr[2], dr[3]));
+    for (int j = 0; j < NB; ++j) {
+      const int wx = cx + N.v[j].x, wy = cy + N.v[j].y;
+      if (!win4.count({wy, wx})) continue;
+      const int u = (wy - wmin) * W + (wx - wmin);  // inside the box: win4 lies in it
+      if (u < 0 || u >= W * W || (u >> 23) != 0)
+        fail(GAMBLET_ERR_UNSUPPORTED, "window too large for tiled Galerkin");
+      t.pairs.push_back(j | (u << 8));
+    }
+    tl.push_back(std::move(t));
+  }
+  std::stable_sort(tl.begin(), tl.end(), [](const Target& a, const Target& b) {
+    return a.pairs.size() > b.pairs.size();
+  });
+  S.t2p_ptr.assign(1, 0);
+  for (const Target& t : tl) {
+    S.t2.push_back(t.t);
+    S.t2p.insert(S.t2p.end(), t.pairs.begin(), t.pairs.end());
+    S.t2p_ptr.push_back((int)S.t2p.size());
+  }
+  return S;
+}
+
+// Where A_{i, i+d} lives in the half-plane output: index of d in Sp, or
+// -2 - (index of -d) for the mirrored half, or -1 when d is outside S.
+int half_code(const OffSet& Sp, int dx, int dy) {
+  const int a = Sp.find(dx, dy);
+  if (a >= 0) return a;
+  const int b = Sp.find(-dx, -dy);
+  return b >= 0 ? -2 - b : -1;
+}
+
+// Block offsets of level k-1 (level k-2 cell units) from the level k-1 cell
+// offsets S, and the conversion map [o][c*4+c'] (half_code of the offset).
+OffSet blocks_from_cells(const OffSet& S, const OffSet& Sp, int km1, std::vector<int>& map) {
+  OffSet O;
+  const int Lp = 1 << (km1 - 1);
+  for (const int2& d : S.v)
+    for (int c = 0; c < 4; ++c)
+      for (int cc = 0; cc < 4; ++cc) {
+        const int ex = d.x - ((cc & 1) - (c & 1)), ey = d.y - ((cc >> 1) - (c >> 1));
+        if ((ex & 1) || (ey & 1)) continue;
+        const int Dx = ex / 2, Dy = ey / 2;
+        if (std::abs(Dx) <= Lp - 1 && std::abs(Dy) <= Lp - 1) O.add(Dx, Dy);
+      }
+  map.assign((size_t)O.size() * 16, -1);
+  for (int o = 0; o < O.size(); ++o)
+    for (int c = 0; c < 4; ++c)
+      for (int cc = 0; cc < 4; ++cc)
+        map[(size_t)o * 16 + c * 4 + cc] =
+            half_code(Sp, 2 * O.v[o].x + (cc & 1) - (c & 1), 2 * O.v[o].y + (cc >> 1) - (c >> 1));
+  return O;
+}
+
+// Shared-memory slots of the stored patch blocks, chosen so that the lanes
+// of a warp that read blocks in the same CG step hit distinct banks.  Thread
+// (j, sub) of the patch CG walks entries sub, sub + S, ... of row j's
+// adjacency list (S = pl.spp lanes per neighbour parent), so the blocks read
+// together are those of one (warp, step) group.  A block's words sit at
+// 9 * slot + q, and 9 is invertible modulo 32, so blocks whose slots differ
+// modulo 32 never share a bank.  Each block is greedily given a residue
+// (colour) unused in its two groups (the row of ja and, transposed, of jb);
+// when all 32 are taken the least used one is reused.  Slots are colour +
+// 32 * rank; unused slots are padding (ja = -1).  Only the layout changes,
+// not the arithmetic.
+void assign_bank_slots(PlanLevel& pl, int NB) {
+  const int nb = (int)pl.half.size();
+  const int S = pl.spp;
+  std::vector<std::vector<int>> groups_of(nb);
+  std::map<std::pair<int, int>, int> gid;
+  for (int j = 0; j < NB; ++j)
+    for (int e = pl.adj_ptr[j]; e < pl.adj_ptr[j + 1]; ++e) {
+      const int kpos = e - pl.adj_ptr[j];
+      const int thread = j * S + kpos % S;
+      const std::pair<int, int> key{thread / 32, kpos / S};
+      auto it = gid.find(key);
+      const int g = it == gid.end() ? (gid[key] = (int)gid.size()) : it->second;
+      groups_of[pl.adj[e].x].push_back(g);
+    }
+  std::vector<uint32_t> used(gid.size(), 0u);           // colours taken per group
+  std::vector<std::array<int, 32>> use_count(gid.size());
+  for (auto& a : use_count) a.fill(0);
+  std::vector<int> colour(nb, 0), count(32, 0);
+  for (int b = 0; b < nb; ++b) {
+    uint32_t taken = 0;
+    for (int g : groups_of[b]) taken |= used[g];
+    int c = -1;
+    for (int t = 0; t < 32; ++t) {
+      const int cand = (b + t) & 31;  // rotate the start to balance the classes
+      if (!((taken >> cand) & 1u)) {
+        c = cand;
+        break;
+      }
+    }
+    if (c < 0) {  // every residue taken: the least used in these groups
+      int best = 1 << 30;
+      for (int cand = 0; cand < 32; ++cand) {
+        int u = 0;
+        for (int g : groups_of[b]) u += use_count[g][cand];
+        if (u < best) {
+          best = u;
+          c = cand;
+        }
+      }
+    }
+    colour[b] = c;
+    for (int g : groups_of[b]) {
+      used[g] |= 1u << c;
+      ++use_count[g][c];
+    }
+  }
+  std::vector<int> rank(nb);
+  for (int b = 0; b < nb; ++b) rank[b] = count[colour[b]]++;
+  const int per = *std::max_element(count.begin(), count.end());
+  std::vector<int> slot(nb);
+  std::vector<int4> half(32 * (size_t)per, make_int4(-1, -1, 0, 0));
+  for (int b = 0; b < nb; ++b) {
+    slot[b] = colour[b] + 32 * rank[b];
+    half[slot[b]] = pl.half[b];
+  }
+  pl.half.swap(half);
+  for (int4& a : pl.adj) a.x = slot[a.x];
+  for (int& d : pl.diag_h) d = slot[d];
+}
+
+size_t patch_mma_smem_bytes_of(const MmaWin& W, int NB) {
+  PatchMmaGeom g{};
+  g.NP = W.NP;
+  g.nU = W.nU;
+  g.n = W.n;
+  g.Kp = W.Kp;
+  g.Mt = W.Mt;
+  g.NB = NB;
+  return patch_mma_smem_bytes(g);
+}
+
+void build_mma_window(MmaWin& W, int G, const OffSet& O, const OffSet& N) {
+  const int NB = N.size();
+  W.NP = G * G;
+  std::vector<int2> cell(W.NP);
+  for (int c = 0; c < W.NP; ++c) cell[c] = make_int2(c & 1, c >> 1);
+  std::map<std::pair<int, int>, int> bits;  // (dy, dx) -> patch bits, row-major order
+  for (int c = 0; c < W.NP; ++c)
+    for (const int2& o : N.v) bits[{cell[c].y + o.y, cell[c].x + o.x}] |= 1 << c;
+  OffSet U;
+  W.U.clear();
+  W.ubits.clear();
+  for (const auto& kv : bits) {
+    U.add(kv.first.second, kv.first.first);
+    W.U.push_back(make_int2(kv.first.second, kv.first.first));
+    W.ubits.push_back(kv.second);
+  }
+  W.nU = U.size();
+  W.n = 3 * W.nU;
+  W.Kp = (W.n + 15) / 16 * 16;
+  W.Mt = (W.n + 127) / 128;
+  W.diag_o = O.find(0, 0);
+  W.pairs.clear();
+  for (int a = 0; a < W.nU; ++a)
+    for (int b = 0; b < a; ++b) {
+      const int o = O.find(W.U[b].x - W.U[a].x, W.U[b].y - W.U[a].y);
+      if (o >= 0) W.pairs.push_back(make_int4(a, b, o, 0));
+    }
+  W.rhs_o.assign((size_t)W.NP * W.nU, -1);
+  for (int c = 0; c < W.NP; ++c)
+    for (int u = 0; u < W.nU; ++u)
+      W.rhs_o[(size_t)c * W.nU + u] = O.find(cell[c].x - W.U[u].x, cell[c].y - W.U[u].y);
+  W.outmap.assign((size_t)W.NP * NB, 0);
+  for (int c = 0; c < W.NP; ++c)
+    for (int j = 0; j < NB; ++j)
+      W.outmap[(size_t)c * NB + j] = U.find(cell[c].x + N.v[j].x, cell[c].y + N.v[j].y);
+  W.ok = W.diag_o >= 0 && W.Mt <= 3 && patch_mma_smem_bytes_of(W, NB) <= 227 * 1024;
+}
+
+std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
+                                       const std::string& key) {
+  auto plan = std::make_shared<Plan>();
+  plan->key = key;
+  plan->lv.resize(q + 1);
+  const int NB = N.size();
+  OffSet O = Oq;
+  for (int k = q; k >= 2; --k) {
+    PlanLevel& pl = plan->lv[k];
+    pl.S = build_sym(O, N, k);
+    // patch blocks: pairs (ja >= jb) coupled through O_k
+    std::vector<std::vector<int4>> rows(NB);
+    pl.adj_ptr.assign(NB + 1, 0);
+    pl.diag_h.assign(NB, -1);
+    for (int ja = 0; ja < NB; ++ja)
+      for (int jb = 0; jb <= ja; ++jb) {
+        const int o = pl.S.pair_idx[(size_t)ja * NB + jb];
+        if (o < 0) continue;
+        const int hidx = (int)pl.half.size();
+        pl.half.push_back(make_int4(ja, jb, o, 0));
+        rows[ja].push_back(make_int4(hidx, jb, 0, 0));
+        if (jb != ja) rows[jb].push_back(make_int4(hidx, ja, 1, 0));
+        else pl.diag_h[ja] = hidx;
+      }
+    for (int j = 0; j < NB; ++j) {
+      if (pl.diag_h[j] < 0) fail(GAMBLET_ERR_INVALID_ARG, "patch block without diagonal");
+      pl.adj_ptr[j + 1] = pl.adj_ptr[j] + (int)rows[j].size();
+      pl.adj.insert(pl.adj.end(), rows[j].begin(), rows[j].end());
+    }
+    const double row_len = (double)pl.adj.size() / NB;
+    pl.spp = row_len > 24 ? 4 : (row_len > 12 ? 2 : 1);
+    while (pl.spp > 1 && NB * pl.spp > 256) pl.spp >>= 1;
+    pl.flops_iter = 18.0 * (2.0 * pl.half.size() - NB) + 60.0 * NB;
+    assign_bank_slots(pl, NB);
+    for (int gi = 0; gi < 2; ++gi) build_mma_window(pl.mwin[gi], gi + 1, pl.S.O, N);
+    if (k - 1 >= 2) {
+      pl.O_next = blocks_from_cells(pl.S.S, pl.S.Sp, k - 1, pl.map_next);
+      O = pl.O_next;
+    } else {
+      pl.map_next.assign(16, -1);
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j)
+          pl.map_next[i * 4 + j] = half_code(pl.S.Sp, (j & 1) - (i & 1), (j >> 1) - (i >> 1));
+    }
+  }
+  std::vector<char>& buf = plan->packed;
+  auto put = [&buf](const void* src, size_t bytes) {
+    const size_t off = buf.size();
+    buf.resize(off + std::max<size_t>((bytes + 15) & ~(size_t)15, 16), 0);
+    if (bytes) std::memcpy(buf.data() + off, src, bytes);
+    return off;
+  };
+  auto put_v = [&put](const auto& v) { return put(v.data(), v.size() * sizeof(v[0])); };
+  for (int k = q; k >= 2; --k) {
+    PlanLevel& pl = plan->lv[k];
+    const SymLevel& S = pl.S;
+    pl.table_off[PlanLevel::kPairIdx] = put_v(S.pair_idx);
+    pl.table_off[PlanLevel::kHalf] = put_v(pl.half);
+    pl.table_off[PlanLevel::kAdjPtr] = put_v(pl.adj_ptr);
+    pl.table_off[PlanLevel::kAdj] = put_v(pl.adj);
+    pl.table_off[PlanLevel::kDiagH] = put_v(pl.diag_h);
+    pl.table_off[PlanLevel::kWin] = put_v(S.WIN.v);
+    pl.table_off[PlanLevel::kL1Ptr] = put_v(S.l1_ptr);
+    pl.table_off[PlanLevel::kL1Pairs] = put_v(S.l1_pairs);
+    pl.table_off[PlanLevel::kOut] = put_v(S.Sp.v);
+    pl.table_off[PlanLevel::kL2Ptr] = put_v(S.l2_ptr);
+    pl.table_off[PlanLevel::kL2Pairs] = put_v(S.l2_pairs);
+    pl.table_off[PlanLevel::kT1Ptr] = put_v(S.t1_ptr);
+    pl.table_off[PlanLevel::kT1] = put_v(S.t1);
+    pl.table_off[PlanLevel::kT2] = put_v(S.t2);
+    pl.table_off[PlanLevel::kT2pPtr] = put_v(S.t2p_ptr);
+    pl.table_off[PlanLevel::kT2p] = put_v(S.t2p);
+    pl.table_off[PlanLevel::kOffNext] = put_v(pl.O_next.v);
+    pl.table_off[PlanLevel::kMapNext] = put_v(pl.map_next);
+    for (MmaWin& W : pl.mwin) {
+      W.off[0] = put_v(W.U);
+      W.off[1] = put_v(W.ubits);
+      W.off[2] = put_v(W.pairs);
+      W.off[3] = put_v(W.rhs_o);
+      W.off[4] = put_v(W.outmap);
+    }
+  }
+  return plan;
+}
+
+std::shared_ptr<const Plan> cached_plan(int q, double rho, int rule, const OffSet& Oq,
+                                        const OffSet& N) {
+  static std::mutex mu;
+  static std::map<std::string, std::shared_ptr<const Plan>> cache;
+  std::string key = std::to_string(q) + "/" + std::to_string(rho) + "/" + std::to_string(rule);
+  for (const int2& o : Oq.v) key += "/" + std::to_string(o.x) + "," + std::to_string(o.y);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  auto plan = build_plan(q, Oq, N, key);
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = plan;
+  return plan;
+}
+
+}  // namespace hs
+}  // namespace gb
