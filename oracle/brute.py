@@ -16,9 +16,12 @@ import numpy as np
 
 def level_cells(cells, q, k):
     """Sorted distinct level-k cells and the map fine node -> level-k index
-    (row-major (y, x) order, matching the oracle hierarchy)."""
+    (row-major (y, x) order in 2-D, (z, y, x) in 3-D, matching the oracle
+    hierarchy)."""
     c = np.asarray(cells, dtype=np.int64) >> (q - k)
-    key = c[:, 1] * (1 << k) + c[:, 0]
+    key = np.zeros(len(c), dtype=np.int64)
+    for a in range(c.shape[1] - 1, -1, -1):
+        key = key * (1 << k) + c[:, a]
     ukey, inv = np.unique(key, return_inverse=True)
     return ukey, inv
 

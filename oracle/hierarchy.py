@@ -9,11 +9,18 @@ a basis of Ker(pi^(k-1,k)) with one block per parent (Sec. 4.6, Lemma lemwk),
 built by Construction const1 (consecutive differences) or Construction
 const2 (normalised rows 1..m-1 of U^(m) from Lemma const0).
 
+The construction is the same in every dimension d (the paper's setting
+is a domain of R^d; the cells are squares for d = 2 and cubes for d = 3, so
+a parent has up to 2^d children).
+
 Ordering conventions (the CUDA path uses the same ones so that
 W-dependent quantities can be compared entry by entry):
 * level q: the fine dof order given by the caller;
-* level k < q: distinct cells sorted row-major by (y, x);
-* the children of a parent are ordered row-major by (y & 1, x & 1);
+* level k < q: distinct cells sorted row-major by (y, x) in 2-D and by
+  (z, y, x) in 3-D (x varies fastest);
+* the children of a parent are ordered by the child slot
+  sum_a (c_a & 1) 2^a: row-major by (y & 1, x & 1) in 2-D and by
+  (z & 1, y & 1, x & 1) in 3-D;
 * rows of W^(k) are ordered by parent, then by t = 1..m_s - 1.
 
 Parity pins: tests/test_oracle_pins.py (pi pibar^T = I, W W^T = I for
@@ -47,38 +54,53 @@ def helmert_ubar(n: int) -> np.ndarray:
     return U / np.linalg.norm(U, axis=1, keepdims=True)
 
 
+def cell_key(c: np.ndarray, k: int) -> np.ndarray:
+    """Row-major key of level-k lattice cells c (n x d, x first): x varies
+    fastest, then y, then z."""
+    c = np.asarray(c, dtype=np.int64)
+    key = np.zeros(len(c), dtype=np.int64)
+    for a in range(c.shape[1] - 1, -1, -1):
+        key = key * (1 << k) + c[:, a]
+    return key
+
+
+def key_cells(key: np.ndarray, k: int, d: int) -> np.ndarray:
+    """Inverse of cell_key: n x d cells of the keys."""
+    key = np.asarray(key, dtype=np.int64)
+    return np.stack([(key >> (k * a)) & ((1 << k) - 1) for a in range(d)], axis=1)
+
+
 @dataclasses.dataclass
 class Level:
-    cells: np.ndarray          # n_k x 2 (x, y) lattice cells at level k
+    cells: np.ndarray          # n_k x d lattice cells (x, y[, z]) at level k
     parent: np.ndarray | None  # n_k -> index in level k-1 (None for k = 1)
 
 
 class Hierarchy:
-    """Levels 1..q built from the fine nodes' level-q cells."""
+    """Levels 1..q built from the fine nodes' level-q cells (n x d,
+    d = 2 or 3)."""
 
     def __init__(self, cells_q: np.ndarray, q: int):
         cells_q = np.asarray(cells_q, dtype=np.int64)
         self.q = q
+        self.d = cells_q.shape[1]
         self.levels: dict[int, Level] = {}
         self.levels[q] = Level(cells=cells_q, parent=None)
         for k in range(q - 1, 0, -1):
             child = self.levels[k + 1].cells
-            pc = child >> 1
-            key = pc[:, 1] * (1 << k) + pc[:, 0]
-            ukey, inv = np.unique(key, return_inverse=True)
-            cells = np.stack([ukey % (1 << k), ukey // (1 << k)], axis=1)
-            self.levels[k] = Level(cells=cells, parent=None)
+            ukey, inv = np.unique(cell_key(child >> 1, k), return_inverse=True)
+            self.levels[k] = Level(cells=key_cells(ukey, k, self.d), parent=None)
             self.levels[k + 1].parent = inv.astype(np.int64)
 
     def n(self, k: int) -> int:
         return len(self.levels[k].cells)
 
     def children(self, k: int) -> list[np.ndarray]:
-        """Children (level-k indices) of each level-(k-1) node, ordered
-        row-major by (y & 1, x & 1)."""
+        """Children (level-k indices) of each level-(k-1) node, ordered by
+        the child slot sum_a (c_a & 1) 2^a."""
         par = self.levels[k].parent
         cells = self.levels[k].cells
-        slot = (cells[:, 1] & 1) * 2 + (cells[:, 0] & 1)
+        slot = sum((cells[:, a] & 1) << a for a in range(self.d))
         order = np.lexsort((slot, par))
         counts = np.bincount(par, minlength=self.n(k - 1))
         splits = np.cumsum(counts)[:-1]
@@ -132,20 +154,18 @@ class Hierarchy:
     def neighbours(self, k: int, rho: float, rule: str = "euclid") -> list[np.ndarray]:
         """i^rho at level k (Sec. 4.10, first paragraph): level-k nodes whose subdomain
         lies within distance H_k * rho of tau_i.  In lattice units the
-        distance between closed squares with offsets (dx, dy) is
-        sqrt(max(|dx|-1,0)^2 + max(|dy|-1,0)^2).  rule="cheb" uses the
-        box max(|dx|,|dy|) <= rho instead."""
+        distance between closed squares (cubes) whose offsets are
+        (d_1, .., d_d) is sqrt(sum_a max(|d_a| - 1, 0)^2).  rule="cheb" uses
+        the box max_a |d_a| <= rho instead."""
         c = self.levels[k].cells
         out = []
         for i in range(len(c)):
-            dx = np.abs(c[:, 0] - c[i, 0])
-            dy = np.abs(c[:, 1] - c[i, 1])
+            dist = np.abs(c - c[i])
             if rule == "euclid":
-                ex = np.maximum(dx - 1, 0)
-                ey = np.maximum(dy - 1, 0)
-                ok = ex * ex + ey * ey <= rho * rho
+                e = np.maximum(dist - 1, 0)
+                ok = (e * e).sum(axis=1) <= rho * rho
             elif rule == "cheb":
-                ok = np.maximum(dx, dy) <= rho
+                ok = dist.max(axis=1) <= rho
             else:
                 raise ValueError(rule)
             out.append(np.nonzero(ok)[0])

@@ -24,3 +24,10 @@ from .rough import (  # noqa: F401
     rough_log_coefficient,
     interior_cells,
 )
+from .rough3d import (  # noqa: F401
+    K_REF3,
+    assemble_q1_3d,
+    interior_cells3,
+    make_problem3,
+    rough_log_coefficient3,
+)
