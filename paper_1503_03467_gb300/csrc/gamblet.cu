@@ -198,7 +198,7 @@ void setup_local(gamblet_ctx* h) {
   for (const int2& o : h->lv[q].off_h) Oq.add(o.x, o.y);
   std::shared_ptr<const Plan> plan = cached_plan(q, h->opts.rho, h->opts.nbr_rule, Oq, h->N);
   h->plan = plan;
-  const char* dplan = P.upload(plan->packed, s);  // every plan table in one copy
+  const char* dplan = P.upload_owned(plan, plan->packed, s);  // every plan table in one copy
   h->dplan = dplan;
   for (int k = q; k >= 2; --k) {
     LevelDev& L = h->lv[k];

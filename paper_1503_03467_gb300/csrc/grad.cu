@@ -168,7 +168,7 @@ gamblet_status grad_onepass_impl(gamblet_ctx* h, int ncell, const int32_t* cell_
   // before any kernel is queued (copies from pageable host memory wait for
   // the stream)
   std::shared_ptr<const RevPack> pack = reverse_pack(h);
-  const char* dpack = tmp.upload(pack->bytes, s);
+  const char* dpack = tmp.upload_owned(pack, pack->bytes, s);
   double* g_dev = nullptr;
   double* uo_dev = nullptr;
   to_device(tmp, g_dev, g_user, h->n, s);

@@ -87,6 +87,12 @@ struct Pool {
   int64_t bytes = 0;
   cudaStream_t s = nullptr;
   cudaMemPool_t mp = nullptr;
+  // Host sources of the uploads, kept until release(): an asynchronous copy
+  // from pageable host memory may still be reading its source after
+  // cudaMemcpyAsync has returned (a GPU that reaches host memory directly,
+  // as on Grace systems, runs it in stream order), so a source must outlive
+  // the copy.  Each entry remembers the stream its copy was issued on.
+  std::vector<std::pair<cudaStream_t, std::shared_ptr<const void>>> host_keep;
   template <typename T>
   T* alloc(int64_t n) {
     if (n <= 0) n = 1;
@@ -107,13 +113,33 @@ struct Pool {
     CK(cudaMemsetAsync(p, 0, sizeof(T) * (size_t)std::max<int64_t>(n, 1), s));
     return p;
   }
+  // Copy of v on the device; the pool keeps its own host copy of v until the
+  // stream has passed the copy (see host_keep).
   template <typename T>
   T* upload(const std::vector<T>& v, cudaStream_t s) {
+    auto keep = std::make_shared<const std::vector<T>>(v);
+    return upload_owned(keep, *keep, s);
+  }
+  // Same, for a source owned by `owner` (a cached plan): the pool holds a
+  // reference to the owner instead of copying the data.
+  template <typename T>
+  T* upload_owned(std::shared_ptr<const void> owner, const std::vector<T>& v, cudaStream_t s) {
     T* p = alloc<T>((int64_t)v.size());
-    if (!v.empty()) CK(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
+    if (!v.empty()) {
+      CK(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
+      host_keep.emplace_back(s, std::move(owner));
+    }
     return p;
   }
   void release() {
+    if (!host_keep.empty()) {
+      std::vector<cudaStream_t> streams;
+      for (auto& e : host_keep)
+        if (std::find(streams.begin(), streams.end(), e.first) == streams.end())
+          streams.push_back(e.first);
+      for (cudaStream_t st : streams) cudaStreamSynchronize(st);
+      host_keep.clear();
+    }
     for (void* p : ptrs) cudaFreeAsync(p, s);
     ptrs.clear();
     bytes = 0;

@@ -126,6 +126,21 @@ SIGNATURES = {
                                                  ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p]),
     "gamblet_destroy": (None, [ctypes.c_void_p]),
+    # three-dimensional path (include/gamblet3d.h)
+    "gamblet3d_setup": (ctypes.c_int, [ctypes.POINTER(Csr), ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "gamblet3d_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.POINTER(Info)]),
+    "gamblet3d_level_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    "gamblet3d_get_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gamblet3d_level_geometry": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_int32)]),
+    "gamblet3d_device_bytes": (ctypes.c_int64, [ctypes.c_void_p]),
+    "gamblet3d_destroy": (None, [ctypes.c_void_p]),
     "gamblet_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "gamblet_last_error": (ctypes.c_char_p, []),
 }
@@ -384,3 +399,59 @@ def gamblet_status_string(st: int) -> str:
 
 def gamblet_last_error() -> str:
     return _lib.gamblet_last_error().decode()
+
+
+# ---------------------------------------------------------------- three dimensions
+def gamblet3d_setup(rowptr, colind, val, q: int, cells, opts: Opts | None = None) -> int:
+    """cells: n x 3 int32 level-q lattice cells (x, y, z)."""
+    n = int(rowptr.shape[0]) - 1
+    csr = Csr(n, int(colind.shape[0]), _ptr(rowptr, np.int32), _ptr(colind, np.int32),
+              _ptr(val, np.float64))
+    h = ctypes.c_void_p()
+    st = _lib.gamblet3d_setup(ctypes.byref(csr), int(q), _ptr(cells, np.int32),
+                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    if st not in (OK, ERR_NOT_CONVERGED) and h.value:
+        _lib.gamblet3d_destroy(h)
+    _check(st)
+    return h.value
+
+
+def gamblet3d_solve(h: int, g, u, components=None, info: Info | None = None) -> int:
+    return _check(_lib.gamblet3d_solve(ctypes.c_void_p(h), _ptr(g, np.float64),
+                                       _ptr(u, np.float64), _ptr(components, np.float64),
+                                       ctypes.byref(info) if info is not None else None))
+
+
+def gamblet3d_level_size(h: int, k: int) -> tuple[int, int]:
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.gamblet3d_level_size(ctypes.c_void_p(h), int(k), ctypes.byref(a),
+                                     ctypes.byref(b)))
+    return a.value, b.value
+
+
+def gamblet3d_get_operator(h: int, which: int, k: int):
+    """COO triplets (rows, cols, vals) of A^(k) (0), R^(k-1,k) (1), B^(k) (2)."""
+    nnz = ctypes.c_int64()
+    _check(_lib.gamblet3d_get_operator(ctypes.c_void_p(h), int(which), int(k), 0,
+                                       ctypes.byref(nnz), None, None, None))
+    r = np.zeros(nnz.value, dtype=np.int32)
+    c = np.zeros(nnz.value, dtype=np.int32)
+    v = np.zeros(nnz.value, dtype=np.float64)
+    _check(_lib.gamblet3d_get_operator(ctypes.c_void_p(h), int(which), int(k), nnz.value,
+                                       ctypes.byref(nnz), _ptr(r), _ptr(c), _ptr(v)))
+    return r, c, v
+
+
+def gamblet3d_level_geometry(h: int, k: int) -> dict:
+    g = (ctypes.c_int32 * 4)()
+    _check(_lib.gamblet3d_level_geometry(ctypes.c_void_p(h), int(k), g))
+    return {"neighbours": g[0], "block_offsets": g[1], "patch_iters_max": g[2],
+            "dilated_offsets": g[3]}
+
+
+def gamblet3d_device_bytes(h: int) -> int:
+    return int(_lib.gamblet3d_device_bytes(ctypes.c_void_p(h)))
+
+
+def gamblet3d_destroy(h: int) -> None:
+    _lib.gamblet3d_destroy(ctypes.c_void_p(h))

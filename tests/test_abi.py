@@ -1,5 +1,6 @@
 """The C ABI library loads without a GPU, exports every function that
-include/gamblet.h declares, and the ctypes structures match the C layout."""
+include/gamblet.h and include/gamblet3d.h declare, and the ctypes structures
+match the C layout."""
 import ctypes
 import os
 import re
@@ -10,6 +11,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "gamblet.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in ("gamblet.h", "gamblet3d.h")]
 
 
 @pytest.fixture(scope="module")
@@ -21,20 +23,21 @@ def lib():
 
 
 def declared_functions():
-    src = open(HEADER).read()
-    return sorted(set(re.findall(r"GAMBLET_API\s+[\w\s\*]+?\b(gamblet_\w+)\s*\(", src)))
+    src = "".join(open(h).read() for h in HEADERS)
+    return sorted(set(re.findall(r"GAMBLET_API\s+[\w\s\*]+?\b(gamblet\w*?_\w+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for required in ("gamblet_setup", "gamblet_solve", "gamblet_grad", "gamblet_destroy"):
+    for required in ("gamblet_setup", "gamblet_solve", "gamblet_grad", "gamblet_destroy",
+                     "gamblet3d_setup", "gamblet3d_solve", "gamblet3d_get_operator"):
         assert required in names
 
 
 def test_every_declared_symbol_is_exported(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True,
                          text=True, check=True).stdout
-    exported = set(re.findall(r"\bT\s+(gamblet_\w+)", out))
+    exported = set(re.findall(r"\bT\s+(gamblet\w*?_\w+)", out))
     missing = [n for n in declared_functions() if n not in exported]
     assert not missing, missing
     # and the binding knows each of them
