@@ -59,6 +59,8 @@ def parse():
                     help="skip the one-pass localization error per patch radius")
     ap.add_argument("--no-mass", action="store_true",
                     help="skip the mass-matrix initialisation timings")
+    ap.add_argument("--no-3d", action="store_true",
+                    help="skip the three-dimensional (64^3) timing")
     return ap.parse_args()
 
 
@@ -693,6 +695,93 @@ def mass_init_timing(nv, torch, dev, a, stream):
     return out
 
 
+def three_d_timing(nv, torch, dev, peaks, alu, steps=3):
+    """The three-dimensional path (include/gamblet3d.h, float64 throughout):
+    setup + refined solve to a relative residual of 1e-9 on the 64^3
+    trilinear rough-coefficient problem (250,047 unknowns, contrast 1e4,
+    seed 0) with patch radius 1 under both neighbourhood rules, inputs
+    resident on the device; the error against the oracle's direct solve on
+    the 32^3 problem (29,791 unknowns); per-kernel device times and the
+    roofline of the three largest kernels from a separate profiled pass."""
+    from oracle import direct
+    from workloads import make_problem3
+
+    def dev_csr(p):
+        A = p.A.tocsr()
+        A.sort_indices()
+        return [torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in
+                (A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float64))]
+
+    def opts(rho, rule, profile):
+        o = nv.gamblet_default_opts()
+        o.rho, o.nbr_rule, o.profile = rho, rule, profile
+        o.level_tol, o.patch_tol = 0.05, 1e-3
+        o.refine_tol, o.refine_max_iter = 1e-9, 200
+        return o
+
+    out = {"workload": "64^3 Q1 trilinear rough coefficient, q=6, contrast 10000, g~N(0,1), "
+                       "float64", "l2": "inputs and operators (about 1 GB) exceed L2"}
+    p = make_problem3(64, 1e4, 0)
+    rp, ci, va = dev_csr(p)
+    cells = torch.from_numpy(np.ascontiguousarray(p.cells)).to(dev)
+    g = torch.from_numpy(p.g).to(dev)
+    u = torch.zeros_like(g)
+    for rule, rname in ((1, "cheb"), (0, "euclid")):
+        o = opts(1.0, rule, 0)
+        times, infos = [], []
+        for rep in range(steps + 1):
+            torch.cuda.synchronize()
+            h = nv.gamblet3d_setup(rp, ci, va, p.q, cells, o)
+            info = nv.Info()
+            nv.gamblet3d_solve(h, g, u, None, info)
+            nv.gamblet3d_destroy(h)
+            if rep:
+                times.append(info.setup_ms + info.solve_ms)
+                infos.append(info.as_dict())
+        ms = statistics.mean(times)
+        row = {"rho": 1, "rule": rname, "dofs": p.ndof, "ms_per_step": ms,
+               "value": p.ndof / (ms * 1e-3), "unit": UNIT,
+               "setup_ms": statistics.mean(i["setup_ms"] for i in infos),
+               "solve_ms": statistics.mean(i["solve_ms"] for i in infos),
+               "outer_iters": infos[-1]["outer_iters"], "rel_residual": infos[-1]["rel_residual"],
+               "patch_iters_mean": infos[-1]["patch_iters_mean"]}
+        # profiled pass: per-kernel times and the roofline of the largest kernels
+        h = nv.gamblet3d_setup(rp, ci, va, p.q, cells, opts(1.0, rule, 1))
+        nv.gamblet3d_solve(h, g, u, None, nv.Info())
+        st = nv.gamblet3d_kernel_stats(h)
+        nv.gamblet3d_destroy(h)
+        tot = sum(x["ms"] for x in st)
+        top = sorted(st, key=lambda x: -x["ms"])[:3]
+        rl = {}
+        for x in top:
+            e = {"ms": x["ms"], "share": x["ms"] / tot, "launches": x["launches"]}
+            if x["ms"] > 0 and x["bytes"] > 0:
+                gbs = x["bytes"] / (x["ms"] * 1e-3) / 1e9
+                e["hbm"] = {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": gbs / peaks["hbm_gbs"]}
+            if x["ms"] > 0 and x["flops"] > 0 and alu.get("fp64_tflops"):
+                tf = x["flops"] / (x["ms"] * 1e-3) / 1e12
+                e["fp64"] = {"achieved": tf, "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
+                             "frac": tf / alu["fp64_tflops"]}
+            rl[x["name"]] = e
+        row["kernels_top"] = rl
+        out[rname] = row
+    # error against the oracle's direct solve (32^3)
+    p = make_problem3(32, 1e4, 0)
+    rp, ci, va = dev_csr(p)
+    cells = torch.from_numpy(np.ascontiguousarray(p.cells)).to(dev)
+    g = torch.from_numpy(p.g).to(dev)
+    u = torch.zeros_like(g)
+    h = nv.gamblet3d_setup(rp, ci, va, p.q, cells, opts(1.0, 1, 0))
+    info = nv.Info()
+    nv.gamblet3d_solve(h, g, u, None, info)
+    nv.gamblet3d_destroy(h)
+    ud, _ = direct.solve(p.A, p.g)
+    out["rel_err_vs_oracle_32x32x32"] = rel_err(u.cpu().numpy(), ud)
+    out["peaks"] = "HBM: MEASURED_PEAKS.json hbm_gbs; float64: torch.matmul float64 (alu_peaks)"
+    return out
+
+
 def level_conditions(nv, a, dev_in, steps=60):
     """cond(B^(k)) estimates (Lanczos, float64 level operators) per level, for
     W of Construction const2 (the stored basis) and const1: the paper bounds
@@ -1025,6 +1114,8 @@ def main():
         line["mass_init"] = mass_init_timing(nv, torch, dev, a, stream)
     if not a.no_localization:
         line["level_condition"] = level_conditions(nv, a, dev_in)
+    if not a.no_3d:
+        line["three_d"] = three_d_timing(nv, torch, dev, peaks, alu)
     if not a.no_mass:
         line["multi_rhs"] = multi_rhs_timing(nv, torch, a, dev_in, stream)
     if rank == 0 and ws == 1 and not a.no_cpu:

@@ -40,7 +40,8 @@ typedef struct gamblet3d_ctx* gamblet3d_handle;
  *          between closed cubes, 1 Chebyshev box), level_tol,
  *          level_max_iter, refine_tol, refine_max_iter, patch_tol (> 0: the
  *          relative residual of the block-Jacobi CG of each patch system;
- *          0: 1e-12), profile (per-phase device times in info) and stream.
+ *          0: 1e-12), profile (per-kernel device times,
+ *          gamblet3d_kernel_stats) and stream.
  *          precision must be GAMBLET_FP64 (MIXED returns UNSUPPORTED).
  *   out    receives the handle.
  * Returns INVALID_ARG for malformed input (a cell outside the lattice or
@@ -92,6 +93,14 @@ GAMBLET_API gamblet_status gamblet3d_get_operator(gamblet3d_handle h, int32_t wh
  * geom[1] = block offsets |O_k| of A^(k), geom[2] = patch CG iterations
  * (largest), geom[3] = dilated offsets of the Galerkin rows. */
 GAMBLET_API gamblet_status gamblet3d_level_geometry(gamblet3d_handle h, int32_t k, int32_t* geom);
+
+/* Per-kernel statistics of the handle's setup and solves when opts.profile
+ * = 1 (CUDA-event time on the library's stream, launches, and algorithmic
+ * bytes and flops), as for gamblet_kernel_stats; returns the number of
+ * entries available (capacity 0 queries it). */
+GAMBLET_API int32_t gamblet3d_kernel_stats(gamblet3d_handle h, gamblet_kernel_stat* out,
+                                           int32_t capacity);
+GAMBLET_API void gamblet3d_reset_kernel_stats(gamblet3d_handle h);
 
 /* Device bytes held by the handle. */
 GAMBLET_API int64_t gamblet3d_device_bytes(gamblet3d_handle h);

@@ -129,6 +129,7 @@ struct Lev3 {
   double* Rhat = nullptr;
   int patch_it_max = 0;
   double patch_it_mean = 0;
+  int patch_pairs = 0;     // coupled (a, b) pairs of a patch system
   int nD = 0;
   // solve vectors (8^k entries, Morton order)
   double* gnode = nullptr;
@@ -169,6 +170,7 @@ struct TempBuf {
 }  // namespace
 
 struct gamblet3d_ctx {
+  Prof prof;
   gamblet_opts opts;
   cudaStream_t s = nullptr;
   int q = 0, n = 0;
@@ -329,6 +331,8 @@ gamblet3d_ctx* setup3(const gamblet_csr* A, int q, const int32_t* cells, const g
     fail(GAMBLET_ERR_INVALID_ARG, "bad tolerance or iteration cap");
   h->s = (cudaStream_t)h->opts.stream;
   h->pool.s = h->s;
+  h->prof.on = h->opts.profile != 0;
+  Prof& prof = h->prof;
   cudaStream_t s = h->s;
   Pool& P = h->pool;
   h->q = q;
@@ -396,9 +400,12 @@ gamblet3d_ctx* setup3(const gamblet_csr* A, int q, const int32_t* cells, const g
     upload_offsets(h.get(), L);
     L.Ahat = P.zeros<double>((int64_t)L.O.size() * L.npar * 64, s);
     OffLookup lk{L.lk, L.lkR};
+    const double blk_bytes = (double)L.O.size() * L.npar * 64 * sizeof(double);
+    const int tk = prof.begin("import3", (double)h->nnz * 16 + blk_bytes * 2, 0.0, s);
     launch_csr_to_blocks3(n, h->rowptr, h->colind, h->val, h->morton_of, lk, q, L.npar, L.Ahat, s);
     launch_transform_blocks3(L.Ahat, L.Ahat, L.off, L.mirror, L.O.size(), L.npar, L.Lpar, L.pmask,
                              0, h->qtab, s);
+    prof.end(tk, s);
   }
   const double ptol = h->opts.patch_tol > 0 ? h->opts.patch_tol : 1e-12;
   int* it_stats = P.zeros<int>(3 * (q + 1), s);
@@ -406,7 +413,9 @@ gamblet3d_ctx* setup3(const gamblet_csr* A, int q, const int32_t* cells, const g
     Lev3& L = h->lv[k];
     if (L.o0 < 0) fail(GAMBLET_ERR_INVALID_ARG, "the diagonal block offset is missing");
     L.Dinv = P.alloc<double>(L.npar * 64);
+    const int td = prof.begin("dinv3", (double)L.npar * 128 * sizeof(double), 0.0, s);
     launch_detail_inverse3(L.Ahat, L.o0, L.npar, L.pmask, L.Dinv, h->status, s);
+    prof.end(td, s);
     // patches
     L.N = neighbours3(h->opts.rho, h->opts.nbr_rule, L.Lpar - 1);
     L.NB = L.N.size();
@@ -424,8 +433,13 @@ gamblet3d_ctx* setup3(const gamblet_csr* A, int q, const int32_t* cells, const g
     L.nbr = P.upload(L.N.v, s);
     L.pair = P.upload(pair, s);
     L.Rhat = P.alloc<double>(L.npar * L.NB * 8);
+    int npairs = 0;
+    for (int v : pair) npairs += v >= 0;
+    L.patch_pairs = npairs;
+    const int tp = prof.begin("patch_cg3_k" + std::to_string(k), 0.0, 0.0, s);
     launch_patch_cg3(L.Ahat, L.Dinv, L.pmask, L.geom(), ptol, kPatchMaxIter, L.Rhat,
                      it_stats + 3 * k, s);
+    prof.end(tp, s);
     CK(cudaGetLastError());
     // Galerkin product into level k-1
     GalPlan g = galerkin_plan(L);
@@ -455,10 +469,22 @@ gamblet3d_ctx* setup3(const gamblet_csr* A, int q, const int32_t* cells, const g
     gg.noff = L.O.size();
     gg.noff_out = C.O.size();
     gg.npar_out = C.npar;
-    launch_galerkin3(L.Ahat, L.Rhat, L.pmask, gg, raw.as<double>(), s);
+    {
+      // per active coarse row: phase 1 reads 64 block entries per (j, o) pair,
+      // phase 2 an 8-vector per (j', d) pair
+      const double rows = (double)C.n_active;
+      const double fl = rows * (128.0 * g.l1.size() + 16.0 * g.l2.size());
+      const double by = (double)L.O.size() * L.npar * 512 + (double)L.npar * L.NB * 64 +
+                        (double)nblk * sizeof(double);
+      const int tg = prof.begin("galerkin3_k" + std::to_string(k), by, fl, s);
+      launch_galerkin3(L.Ahat, L.Rhat, L.pmask, gg, raw.as<double>(), s);
+      prof.end(tg, s);
+    }
     C.Ahat = P.alloc<double>(nblk);
+    const int tt = prof.begin("transform3", (double)nblk * 3 * sizeof(double), 0.0, s);
     launch_transform_blocks3(raw.as<double>(), C.Ahat, C.off, C.mirror, C.O.size(), C.npar,
                              C.Lpar, C.pmask, 1, h->qtab, s);
+    prof.end(tt, s);
     CK(cudaGetLastError());
   }
   // solve buffers
@@ -514,6 +540,7 @@ gamblet3d_ctx* setup3(const gamblet_csr* A, int q, const int32_t* cells, const g
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
   h->setup_ms = ms_between(ev.a, ev.b);
+  prof.resolve();
   if (const int gv = guard_take())
     fail(GAMBLET_ERR_CUDA, "internal index guard " + std::to_string(gv) + " failed in the setup");
   int st = 0;
@@ -524,6 +551,13 @@ gamblet3d_ctx* setup3(const gamblet_csr* A, int q, const int32_t* cells, const g
   int64_t sum = 0, cnt = 0;
   for (int k = 2; k <= q; ++k) {
     Lev3& L = h->lv[k];
+    // CG work of the patch systems: per iteration the product with the
+    // patch's detail blocks (49 multiply-adds per coupled pair), the
+    // block-Jacobi step (49 per parent) and about ten vector operations per
+    // unknown; the blocks are read from memory on every iteration
+    const double per_it_fl = 2.0 * 49 * L.patch_pairs + 2.0 * 49 * L.NB + 10.0 * 7 * L.NB;
+    const double per_it_by = (double)L.patch_pairs * 7 * 56 + (double)L.NB * 7 * 64;
+    prof.add("patch_cg3_k" + std::to_string(k), per_it_by * its[3 * k + 1], per_it_fl * its[3 * k + 1]);
     L.patch_it_max = its[3 * k];
     L.patch_it_mean = its[3 * k + 2] ? (double)its[3 * k + 1] / its[3 * k + 2] : 0.0;
     h->patch_it_max = std::max(h->patch_it_max, L.patch_it_max);
@@ -550,6 +584,7 @@ void dots(gamblet3d_ctx* h, int64_t n, const double* x, const double* y, const d
 bool level_cg(gamblet3d_ctx* h, int* iters) {
   cudaStream_t s = h->s;
   if (h->cg_nlev == 0) return true;
+  Prof& prof = h->prof;
   const double tol = h->opts.level_tol;
   const int maxit = h->opts.level_max_iter;
   launch_lcg3_start(h->cg_lv, h->cg_nlev, h->cg_nblk, h->cb, h->cx, h->cr, h->cz, h->cp,
@@ -562,6 +597,7 @@ bool level_cg(gamblet3d_ctx* h, int* iters) {
     bool any = false;
     for (auto& c : h->sc_h) any |= c.active == 1;
     if (!any) break;
+    const int tc = prof.begin("level_cg3", 0.0, 0.0, s);
     for (int it = 0; it < kCgChunk3; ++it) {
       launch_lcg3_spmv(h->cg_lv, h->cg_nlev, h->cg_nblk, h->cg_sc, h->cp, h->cAp, h->cg_part, s);
       launch_lcg3_alpha(h->cg_lv, h->cg_nlev, h->cg_part, h->cg_sc, s);
@@ -570,6 +606,7 @@ bool level_cg(gamblet3d_ctx* h, int* iters) {
       launch_lcg3_beta(h->cg_lv, h->cg_nlev, h->cg_part, h->cg_sc, tol, maxit, s);
       launch_lcg3_direction(h->cg_lv, h->cg_nlev, h->cg_nblk, h->cg_sc, h->cz, h->cp, s);
     }
+    prof.end(tc, s);
     CK(cudaGetLastError());
   }
   CK(cudaMemcpyAsync(h->sc_h.data(), h->cg_sc, sizeof(Lcg3Scalars) * h->cg_nlev,
@@ -580,6 +617,13 @@ bool level_cg(gamblet3d_ctx* h, int* iters) {
     const int k = l + 2;
     if (iters && k < 32) iters[k] += h->sc_h[l].iters;
     if (h->sc_h[l].active != 0) ok = false;
+    // the iterations this level ran: its detail blocks (49 values of 8
+    // bytes each) once per iteration, and about twelve passes over the
+    // level's vectors (8 doubles per parent)
+    const Lev3& L = h->lv[k];
+    const double it = h->sc_h[l].iters;
+    prof.add("level_cg3", it * ((double)L.O.size() * L.npar * 392 + 12.0 * 64 * L.npar),
+             it * (2.0 * 49 * L.O.size() * L.npar + 2.0 * 49 * L.npar + 12.0 * 8 * L.npar));
   }
   return ok;
 }
@@ -589,6 +633,14 @@ bool level_cg(gamblet3d_ctx* h, int* iters) {
 bool apply_G3(gamblet3d_ctx* h, const double* in, double* out, double* comps, int* iters) {
   cudaStream_t s = h->s;
   const int q = h->q;
+  Prof& prof = h->prof;
+  double rb = 0, rf = 0;
+  for (int k = 2; k <= q; ++k) {
+    const Lev3& L = h->lv[k];
+    rb += (double)L.npar * L.NB * 64 + (double)L.npar * 8 * 8 * 3;
+    rf += 2.0 * L.npar * L.NB * 8 + 2.0 * 64 * L.npar;
+  }
+  const int tr = prof.begin("restrict3", rb, rf, s);
   launch_gather3(in, h->unknown_of, h->lv[q].ncell, h->lv[q].gnode, s);
   for (int k = q; k >= 2; --k) {
     Lev3& L = h->lv[k];
@@ -596,16 +648,19 @@ bool apply_G3(gamblet3d_ctx* h, const double* in, double* out, double* comps, in
     launch_transform_vec3(L.gnode, ghat, L.npar, L.pmask, +1, h->qtab, s);
     launch_restrict3(L.Rhat, ghat, L.pmask, L.geom(), h->lv[k - 1].gnode, s);
   }
+  prof.end(tr, s);
   const bool ok = level_cg(h, iters);
   launch_coarsest3(h->lv[1].Ahat, h->lv[1].pmask_h[0], h->lv[1].gnode, h->qtab, h->U1, h->status,
                    s);
   const double* vprev = h->U1;
+  const int tq = prof.begin("prolong3", rb, rf, s);
   for (int k = 2; k <= q; ++k) {
     Lev3& L = h->lv[k];
     launch_prolong3(L.Rhat, vprev, h->cx + L.v0, L.pmask, L.geom(), h->qtab, L.v, s);
     vprev = L.v;
   }
   launch_scatter_unknown3(h->lv[q].v, h->morton_of, h->n, out, s);
+  prof.end(tq, s);
   if (comps) {
     for (int k0 = 1; k0 <= q; ++k0) {
       const double* vp = k0 == 1 ? h->U1 : nullptr;
@@ -655,7 +710,10 @@ gamblet_status solve3(gamblet3d_ctx* h, const double* g, double* u, double* comp
     const double stop = h->opts.refine_tol * gnorm;
     bool conv = gnorm == 0.0;
     while (!conv && outer < h->opts.refine_max_iter) {
+      const int to = h->prof.begin("outer_spmv3", (double)h->nnz * 12 + (double)n * 24,
+                                   2.0 * h->nnz, s);
       launch_csr_spmv3(n, h->rowptr, h->colind, h->val, h->p, h->qv, s);
+      h->prof.end(to, s);
       double pq = 0;
       dots(h, n, h->p, h->qv, nullptr, &pq);
       if (!(pq > 0)) break;
@@ -689,6 +747,7 @@ gamblet_status solve3(gamblet3d_ctx* h, const double* g, double* u, double* comp
     CK(cudaMemcpyAsync(comps, cd, sizeof(double) * (size_t)q * n, cudaMemcpyDeviceToHost, s));
   CK(cudaEventRecord(ev.b, s));
   CK(cudaStreamSynchronize(s));
+  h->prof.resolve();
   int st = 0;
   CK(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st == DEV_NOT_SPD) fail(GAMBLET_ERR_NOT_SPD, "non-positive pivot in the level-1 Cholesky");
@@ -907,6 +966,25 @@ gamblet_status gamblet3d_level_geometry(gamblet3d_handle h, int32_t k, int32_t* 
   geom[2] = L.patch_it_max;
   geom[3] = L.nD;
   return GAMBLET_OK;
+}
+
+int32_t gamblet3d_kernel_stats(gamblet3d_handle h, gamblet_kernel_stat* out, int32_t capacity) {
+  if (!h) return 0;
+  const int32_t n = (int32_t)h->prof.stats.size();
+  for (int32_t i = 0; i < n && i < capacity && out; ++i) {
+    const Prof::Stat& st = h->prof.stats[i];
+    std::memset(out[i].name, 0, sizeof(out[i].name));
+    std::strncpy(out[i].name, st.name.c_str(), sizeof(out[i].name) - 1);
+    out[i].launches = st.launches;
+    out[i].ms = st.ms;
+    out[i].bytes = st.bytes;
+    out[i].flops = st.flops;
+  }
+  return n;
+}
+
+void gamblet3d_reset_kernel_stats(gamblet3d_handle h) {
+  if (h) h->prof.stats.clear();
 }
 
 int64_t gamblet3d_device_bytes(gamblet3d_handle h) { return h ? h->pool.bytes : 0; }

@@ -139,6 +139,9 @@ SIGNATURES = {
                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gamblet3d_level_geometry": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32,
                                                 ctypes.POINTER(ctypes.c_int32)]),
+    "gamblet3d_kernel_stats": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(KernelStat),
+                                                ctypes.c_int32]),
+    "gamblet3d_reset_kernel_stats": (None, [ctypes.c_void_p]),
     "gamblet3d_device_bytes": (ctypes.c_int64, [ctypes.c_void_p]),
     "gamblet3d_destroy": (None, [ctypes.c_void_p]),
     "gamblet_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
@@ -447,6 +450,18 @@ def gamblet3d_level_geometry(h: int, k: int) -> dict:
     _check(_lib.gamblet3d_level_geometry(ctypes.c_void_p(h), int(k), g))
     return {"neighbours": g[0], "block_offsets": g[1], "patch_iters_max": g[2],
             "dilated_offsets": g[3]}
+
+
+def gamblet3d_kernel_stats(h: int) -> list[dict]:
+    n = _lib.gamblet3d_kernel_stats(ctypes.c_void_p(h), None, 0)
+    arr = (KernelStat * max(n, 1))()
+    n = _lib.gamblet3d_kernel_stats(ctypes.c_void_p(h), arr, n)
+    return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "ms": arr[i].ms,
+             "bytes": arr[i].bytes, "flops": arr[i].flops} for i in range(n)]
+
+
+def gamblet3d_reset_kernel_stats(h: int) -> None:
+    _lib.gamblet3d_reset_kernel_stats(ctypes.c_void_p(h))
 
 
 def gamblet3d_device_bytes(h: int) -> int:
