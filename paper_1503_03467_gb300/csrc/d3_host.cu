@@ -344,8 +344,7 @@ gamblet3d_ctx* setup3(const gamblet_csr* A, int q, const int32_t* cells, const g
 
   // fine CSR and cells on the device
   std::vector<int32_t> rp((size_t)n + 1);
-  CK(cudaMemcpyAsync(rp.data(), A->rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDefault, s));
-  CK(cudaStreamSynchronize(s));
+  to_host(rp.data(), A->rowptr, (int64_t)n + 1);
   if (rp[0] != 0 || rp[n] != A->nnz) fail(GAMBLET_ERR_INVALID_ARG, "rowptr[0] != 0 or rowptr[n] != nnz");
   for (int i = 0; i < n; ++i)
     if (rp[i + 1] < rp[i]) fail(GAMBLET_ERR_INVALID_ARG, "rowptr is not non-decreasing");

@@ -739,8 +739,8 @@ gamblet_ctx* setup_batched_impl(int32_t nprob, const gamblet_csr* A, const int32
   for (int p = 0; p < nprob; ++p) {
     const BatchSeg& b = seg[p];
     CK(cudaMemcpyAsync(R + b.row0, A[p].rowptr, sizeof(int32_t) * b.n, cudaMemcpyDefault, s));
-    CK(cudaMemcpyAsync(&ends[2 * p], A[p].rowptr, sizeof(int32_t), cudaMemcpyDefault, s));
-    CK(cudaMemcpyAsync(&ends[2 * p + 1], A[p].rowptr + b.n, sizeof(int32_t), cudaMemcpyDefault, s));
+    to_host(&ends[2 * p], A[p].rowptr, 1);
+    to_host(&ends[2 * p + 1], A[p].rowptr + b.n, 1);
     CK(cudaMemcpyAsync(C + b.nnz0, A[p].colind, sizeof(int32_t) * A[p].nnz, cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(V + b.nnz0, A[p].val, sizeof(double) * A[p].nnz, cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(X + 2 * b.row0, cells[p], sizeof(int32_t) * 2 * b.n, cudaMemcpyDefault, s));
@@ -1050,7 +1050,7 @@ gamblet_status gamblet_grad(gamblet_handle h, int32_t ncell, const int32_t* cell
     to_device(tmp, cn, cell_nodes, 4 * (int64_t)ncell, s);
     to_device(tmp, ca, cell_a, ncell, s);
     double kh[16];
-    CK(cudaMemcpy(kh, K_ref, sizeof(kh), cudaMemcpyDefault));
+    to_host(kh, K_ref, 16);
     launch_set_kref(kh);
     double* out = nullptr;
     const bool dev_out = is_device_ptr(dJ);
@@ -1081,7 +1081,7 @@ gamblet_status gamblet_assemble_cells(int32_t n, const int32_t* rowptr, const in
       fail(GAMBLET_ERR_INVALID_ARG, "pattern, cells, log_a and val must be device pointers");
     cudaStream_t s = (cudaStream_t)stream;
     double kh[16];
-    CK(cudaMemcpy(kh, K_ref, sizeof(kh), cudaMemcpyDefault));
+    to_host(kh, K_ref, 16);
     launch_set_kref(kh);
     Pool tmp;
     tmp.s = s;

@@ -165,6 +165,16 @@ void to_device(Pool& pool, T*& dst, const T* src, int64_t n, cudaStream_t s) {
   if (n > 0) CK(cudaMemcpyAsync(dst, src, sizeof(T) * (size_t)n, cudaMemcpyDefault, s));
 }
 
+// Copy n elements of caller memory (host or device) into a host buffer: a
+// plain memcpy for host memory, a device-to-host copy otherwise (no copy
+// engine ever moves host memory to host memory).
+template <typename T>
+void to_host(T* dst, const T* src, int64_t n) {
+  if (n <= 0) return;
+  if (is_device_ptr(src)) CK(cudaMemcpy(dst, src, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost));
+  else std::memcpy(dst, src, sizeof(T) * (size_t)n);
+}
+
 // Caller memory as a device pointer: device memory is read in place (the
 // calls that use this finish with a stream synchronisation), host memory is
 // copied into a pool buffer.
