@@ -2,6 +2,7 @@
 timing and profiling runs:
 
   python -m paper_1503_03467_gb300 [--size 512] [--precision mixed|fp64]
+                                   [--dim 2|3] [--rule euclid|cheb]
                                    [--rho 3] [--contrast 1e4] [--seed 0]
                                    [--repeat 1] [--profile] [--capture-last]
                                    [--no-autotune] [--galerkin-variant -1|0|1|2]
@@ -18,6 +19,8 @@ fill the process-wide plan and autotuning caches.  --grad-one-pass replaces
 the solve by the gradient through the one-pass transform
 (gamblet_grad_onepass; J = 1/2 |u_loc - u_obs|^2 with u_obs
 the problem of seed + 7 solved by the same handle's one-pass transform).
+--dim 3 runs the three-dimensional path instead (size^3 trilinear cells,
+float64; include/gamblet3d.h).
 """
 import argparse
 import json
@@ -31,6 +34,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_1503_03467_gb300")
     ap.add_argument("--size", type=int, default=512)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--dim", type=int, choices=[2, 3], default=2)
+    ap.add_argument("--rule", choices=["euclid", "cheb"], default="euclid")
     ap.add_argument("--rho", type=float, default=3.0)
     ap.add_argument("--contrast", type=float, default=1e4)
     ap.add_argument("--seed", type=int, default=0)
@@ -49,15 +54,18 @@ def main(argv=None):
                          "context is created before the first pass)")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
-    from workloads import make_problem
+    from workloads import make_problem, make_problem3
     from . import build
     build.build()
     from . import native as nv
+    if a.dim == 3:
+        return main3(a, nv, make_problem3(a.size, a.contrast, a.seed))
     p = make_problem(a.size, a.contrast, a.seed)
     A = p.A.tocsr()
     A.sort_indices()
     o = nv.gamblet_default_opts()
     o.rho = a.rho
+    o.nbr_rule = 1 if a.rule == "cheb" else 0
     o.precision = nv.MIXED if a.precision == "mixed" else nv.FP64
     o.level_tol = a.level_tol
     o.refine_tol = a.refine_tol
@@ -112,6 +120,48 @@ def main(argv=None):
                     out["shapes"] = {k: nv.gamblet_launch_shapes(h, k) for k in range(2, p.q + 1)}
         finally:
             nv.gamblet_destroy(h)
+    print(json.dumps(out))
+    return 0
+
+
+def main3(a, nv, p):
+    """The three-dimensional path (float64): setup + refined solve."""
+    A = p.A.tocsr()
+    A.sort_indices()
+    o = nv.gamblet_default_opts()
+    o.rho = a.rho
+    o.nbr_rule = 1 if a.rule == "cheb" else 0
+    o.level_tol = a.level_tol
+    o.refine_tol = a.refine_tol
+    o.refine_max_iter = 200
+    o.patch_tol = a.patch_tol if a.patch_tol > 0 else 1e-3
+    o.profile = 1 if a.profile else 0
+    rowptr = np.ascontiguousarray(A.indptr, dtype=np.int32)
+    colind = np.ascontiguousarray(A.indices, dtype=np.int32)
+    val = np.ascontiguousarray(A.data)
+    out = None
+    for r in range(max(a.repeat, 1)):
+        last = r == max(a.repeat, 1) - 1
+        if last and a.capture_last:
+            import torch
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+        h = nv.gamblet3d_setup(rowptr, colind, val, p.q, p.cells, o)
+        try:
+            u = np.zeros(p.ndof)
+            info = nv.Info()
+            nv.gamblet3d_solve(h, p.g, u, None, info)
+            if last:
+                if a.capture_last:
+                    torch.cuda.profiler.stop()
+                out = info.as_dict()
+                out["dofs"] = p.ndof
+                if a.profile:
+                    out["kernels"] = {st["name"]: {"launches": st["launches"],
+                                                   "ms": round(st["ms"], 4)}
+                                      for st in nv.gamblet3d_kernel_stats(h)}
+        finally:
+            nv.gamblet3d_destroy(h)
     print(json.dumps(out))
     return 0
 
