@@ -31,7 +31,7 @@ using namespace gb::d3;
 namespace {
 
 constexpr int kMaxQ3 = 8;
-constexpr size_t kSmemLimit = 227 * 1024;
+constexpr size_t kSmemLimit = 222 * 1024;  // 227 KB per CTA less the kernels' static reduction buffer
 constexpr int kPatchMaxIter = 1000;
 constexpr int kCgChunk3 = 8;
 

@@ -52,38 +52,49 @@ __device__ __forceinline__ double group8_sum(double v) {
   return v;
 }
 
-// Sum of v over the CTA (every thread receives it); red holds one double
-// per warp.  All threads of the CTA must call it.
+// Sum of v over the CTA (every thread receives it).  The partial values go
+// through shared memory and one warp adds them (eight per lane, then a
+// butterfly), so the float64 pipe, the scarce unit of this part, sees 13
+// warp instructions per sum instead of 13 for every warp.  red holds
+// kRed doubles; all threads of the CTA must call it.
+constexpr int kRed = 2 * kThreads + 2;
 __device__ __forceinline__ double cta_sum(double v, double* red) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt = blockDim.x;
+  __syncthreads();  // earlier readers of red are done
+  red[threadIdx.x] = v;
   __syncthreads();
-  if (lane == 0) red[w] = v;
+  if (threadIdx.x < 32) {
+    double s = 0;
+    for (int i = threadIdx.x; i < nt; i += 32) s += red[i];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) red[2 * nt] = s;
+  }
   __syncthreads();
-  double s = 0;
-  const int nw = blockDim.x >> 5;
-  for (int i = 0; i < nw; ++i) s += red[i];
-  return s;
+  return red[2 * nt];
 }
 
 __device__ __forceinline__ void cta_sum2(double& a, double& b, double* red) {
-  a = warp_sum(a);
-  b = warp_sum(b);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nw = blockDim.x >> 5;
+  const int nt = blockDim.x;
   __syncthreads();
-  if (lane == 0) {
-    red[w] = a;
-    red[nw + w] = b;
+  red[threadIdx.x] = a;
+  red[nt + threadIdx.x] = b;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double sa = 0, sb = 0;
+    for (int i = threadIdx.x; i < nt; i += 32) {
+      sa += red[i];
+      sb += red[nt + i];
+    }
+    sa = warp_sum(sa);
+    sb = warp_sum(sb);
+    if (threadIdx.x == 0) {
+      red[2 * nt] = sa;
+      red[2 * nt + 1] = sb;
+    }
   }
   __syncthreads();
-  double sa = 0, sb = 0;
-  for (int i = 0; i < nw; ++i) {
-    sa += red[i];
-    sb += red[nw + i];
-  }
-  a = sa;
-  b = sb;
+  a = red[2 * nt];
+  b = red[2 * nt + 1];
 }
 
 }  // namespace
@@ -351,7 +362,7 @@ __global__ void __launch_bounds__(kThreads)
                 const uint32_t* __restrict__ pmask_k, Patch3Geom g, double tol, int max_iter,
                 double* Rhat, int* iter_stats) {
   extern __shared__ double sm[];
-  __shared__ double red[2 * (kThreads / 32)];
+  __shared__ double red[kRed];
   const int NB = g.NB;
   const int NV = NB * 8;
   double* x = sm;
@@ -494,7 +505,7 @@ void launch_patch_cg3(const double* Ahat, const double* Dinv, const uint32_t* pm
 // P_i + D_d, T[d][c] = sum over (j, o) with N_j + O_o = D_d of
 // sum_a Rhat_i[j][a] Ahat(o, P_i + N_j)[a][c].  Phase 2: for each output
 // offset e with i' = i + E_e active, A^(k-1)_(i, i') = sum over (j', d) with
-// E_e + N_j' = D_d of T[d] . Rhat_i'[j'] (one warp per output).
+// E_e + N_j' = D_d of T[d] . Rhat_i'[j'] (eight lanes per output).
 size_t galerkin3_smem(int NB, int nD) {
   return (size_t)NB * 8 * sizeof(double) + (size_t)nD * 8 * sizeof(double) +
          (size_t)NB * sizeof(int);
@@ -538,26 +549,34 @@ __global__ void __launch_bounds__(kThreads)
     T[e] = acc;
   }
   __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
-  const int sub = lane >> 3, c = lane & 7;
+  // one group of eight lanes per output (lane c = slot c of the dot
+  // products), so the final sum over the slots is three shuffle steps
+  const int grp = tid >> 3, c = tid & 7, ngrp = blockDim.x >> 3;
   // level k-1 node i and its parent (a level k-2 cell)
   const int Lout = g.Lpar >> 1;
   int px, py, pz;
   demorton3((uint32_t)(i >> 3), px, py, pz);
-  for (int e = warp; e < g.nE; e += nwarps) {
-    const int4 E = g.E[e];
-    int ip = shift3(cx, cy, cz, E.x, E.y, E.z, g.Lpar);
-    if (ip >= 0 && !inb(9, ip, npar)) ip = -1;
-    if (ip < 0 || pmask_k[ip] == 0) continue;
-    double acc = 0.0;
-    const double* Rp = Rhat + (int64_t)ip * NB * 8 + c;
-    for (int l = g.l2_ptr[e] + sub; l < g.l2_ptr[e + 1]; l += 4) {
-      const int2 jd = g.l2[l];
-      if (!inb(10, jd.y, g.nD) || !inb(11, jd.x, NB)) continue;
-      acc += T[jd.y * 8 + c] * Rp[jd.x * 8];
+  const int nrounds = (g.nE + ngrp - 1) / ngrp;  // every lane runs the same rounds
+  for (int rnd = 0; rnd < nrounds; ++rnd) {
+    const int e = rnd * ngrp + grp;
+    int ip = -1;
+    if (e < g.nE) {
+      const int4 E = g.E[e];
+      ip = shift3(cx, cy, cz, E.x, E.y, E.z, g.Lpar);
+      if (ip >= 0 && !inb(9, ip, npar)) ip = -1;
+      if (ip >= 0 && pmask_k[ip] == 0) ip = -1;
     }
-    acc = warp_sum(acc);
-    if (lane == 0) {
+    double acc = 0.0;
+    if (ip >= 0) {
+      const double* Rp = Rhat + (int64_t)ip * NB * 8 + c;
+      for (int l = g.l2_ptr[e]; l < g.l2_ptr[e + 1]; ++l) {
+        const int2 jd = g.l2[l];
+        if (!inb(10, jd.y, g.nD) || !inb(11, jd.x, NB)) continue;
+        acc += T[jd.y * 8 + c] * Rp[jd.x * 8];
+      }
+    }
+    acc = group8_sum(acc);
+    if (ip >= 0 && c == 0) {
       int qx, qy, qz;
       demorton3((uint32_t)ip >> 3, qx, qy, qz);
       const int o = g.out_lk.find(qx - px, qy - py, qz - pz);
@@ -703,7 +722,7 @@ __device__ __forceinline__ double precond8(const double* __restrict__ Dinv, int6
 __global__ void k_lcg3_start(const Lcg3Level* __restrict__ lv, int nlev,
                              const double* __restrict__ b, double* x, double* r, double* z,
                              double* p, double* part) {
-  __shared__ double red[2 * (kThreads / 32)];
+  __shared__ double red[kRed];
   const int l = find_level(lv, nlev, blockIdx.x);
   const Lcg3Level L = lv[max(l, 0)];
   const int64_t P = (int64_t)(blockIdx.x - L.blk0) * (kThreads / 8) + (threadIdx.x >> 3);
@@ -736,7 +755,7 @@ __device__ __forceinline__ double level_sum(const Lcg3Level& L, const double* pa
 
 __global__ void k_lcg3_init_scalars(const Lcg3Level* __restrict__ lv, const double* part,
                                     Lcg3Scalars* sc, double tol) {
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[kRed];
   const Lcg3Level L = lv[blockIdx.x];
   const double rz = level_sum(L, part, 0, red);
   const double bb = level_sum(L, part, 1, red);
@@ -754,7 +773,7 @@ __global__ void k_lcg3_init_scalars(const Lcg3Level* __restrict__ lv, const doub
 __global__ void k_lcg3_spmv(const Lcg3Level* __restrict__ lv, int nlev,
                             const Lcg3Scalars* __restrict__ sc, const double* __restrict__ p,
                             double* Ap, double* part) {
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[kRed];
   const int l = find_level(lv, nlev, blockIdx.x);
   if (l < 0 || sc[l].active != 1) return;
   const Lcg3Level L = lv[l];
@@ -785,7 +804,7 @@ __global__ void k_lcg3_spmv(const Lcg3Level* __restrict__ lv, int nlev,
 
 __global__ void k_lcg3_alpha(const Lcg3Level* __restrict__ lv, const double* part,
                              Lcg3Scalars* sc) {
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[kRed];
   const Lcg3Level L = lv[blockIdx.x];
   if (sc[blockIdx.x].active != 1) return;
   const double pq = level_sum(L, part, 0, red);
@@ -804,7 +823,7 @@ __global__ void k_lcg3_update(const Lcg3Level* __restrict__ lv, int nlev,
                               const Lcg3Scalars* __restrict__ sc, const double* __restrict__ p,
                               const double* __restrict__ Ap, double* x, double* r, double* z,
                               double* part) {
-  __shared__ double red[2 * (kThreads / 32)];
+  __shared__ double red[kRed];
   const int l = find_level(lv, nlev, blockIdx.x);
   if (l < 0 || sc[l].active != 1) return;
   const Lcg3Level L = lv[l];
@@ -831,7 +850,7 @@ __global__ void k_lcg3_update(const Lcg3Level* __restrict__ lv, int nlev,
 
 __global__ void k_lcg3_beta(const Lcg3Level* __restrict__ lv, const double* part,
                             Lcg3Scalars* sc, double tol, int max_iter) {
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[kRed];
   const Lcg3Level L = lv[blockIdx.x];
   if (sc[blockIdx.x].active != 1) return;
   const double rz = level_sum(L, part, 1, red);
@@ -1015,7 +1034,7 @@ int dot3_blocks(int64_t n) {
 }
 __global__ void k_dot3(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
                        const double* __restrict__ w, double* part) {
-  __shared__ double red[2 * (kThreads / 32)];
+  __shared__ double red[kRed];
   double a = 0.0, b = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1029,7 +1048,7 @@ __global__ void k_dot3(int64_t n, const double* __restrict__ x, const double* __
   }
 }
 __global__ void k_dot3_finish(const double* __restrict__ part, int nb, int nout, double* out) {
-  __shared__ double red[kThreads / 32];
+  __shared__ double red[kRed];
   for (int o = 0; o < nout; ++o) {
     double s = 0.0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[o * nb + b];
