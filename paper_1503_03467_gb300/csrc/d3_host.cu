@@ -267,11 +267,21 @@ GalPlan galerkin_plan(const Lev3& L) {
     g.l1.insert(g.l1.end(), v.begin(), v.end());
     g.l1_ptr.push_back((int)g.l1.size());
   }
+  // outputs in order of decreasing pair count: the eight-lane groups of a
+  // warp then take outputs of about the same work
+  std::vector<int> order(l2.size());
+  for (size_t e = 0; e < order.size(); ++e) order[e] = (int)e;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return l2[a].size() > l2[b].size(); });
+  OffSet3 Esorted;
   g.l2_ptr.push_back(0);
-  for (auto& v : l2) {
-    g.l2.insert(g.l2.end(), v.begin(), v.end());
+  for (int e : order) {
+    const int4 o = g.E.v[e];
+    Esorted.add(o.x, o.y, o.z);
+    g.l2.insert(g.l2.end(), l2[e].begin(), l2[e].end());
     g.l2_ptr.push_back((int)g.l2.size());
   }
+  g.E = Esorted;
   // parent offsets of level k-1 (level k-2 cell units) reached by the
   // outputs: floor((x + e) / 2) over the child slot bits x
   const int capn = std::max(L.Lpar / 2 - 1, 0);
