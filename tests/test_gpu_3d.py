@@ -72,9 +72,10 @@ def test_exact_transform_3d(n, seed):
             check_op(ops[("B", k)], ex["B"][k], TOL, ("B", k))
 
 
-@pytest.mark.parametrize("n,rho,rule", [(16, 1, "cheb"), (8, 1, "euclid"), (16, 2, "cheb")])
-def test_localized_operators_3d(n, rho, rule):
-    p = make_problem3(n, 1e3, 2)
+@pytest.mark.parametrize("n,rho,rule,contrast", [(16, 1, "cheb", 1e3), (8, 1, "euclid", 1e3),
+                                                  (16, 2, "cheb", 1e3), (16, 1, "cheb", 1e6)])
+def test_localized_operators_3d(n, rho, rule, contrast):
+    p = make_problem3(n, contrast, 2)
     s = gamblet_local_setup(p.A, p.cells, p.q, rho=rho, rule=rule)
     loc = gamblet_local_solve(s, p.g, return_components=True)
     u, comps, ops, info = _run(p.A, p.g, p.cells, p.q,
