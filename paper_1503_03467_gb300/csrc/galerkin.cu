@@ -32,6 +32,38 @@ __device__ __forceinline__ void load_vec4(const double* p, double* b) {
   b[3] = v1.y;
 }
 
+// A whole 4x4 block (64 bytes float, 128 bytes double) as 32-byte loads: two
+// (float) or four (double) instead of four or eight 16-byte loads, so each
+// 32-byte sector of a block is looked up once by the L1 instead of twice.
+// Blocks start at multiples of 16 elements from the base; load_block takes
+// this path when the base is 32-byte aligned (the library's allocations are)
+// and the 16-byte one otherwise.
+__device__ __forceinline__ void load_blk16(const float* p, float* b) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(b[8 * h]), "=f"(b[8 * h + 1]), "=f"(b[8 * h + 2]), "=f"(b[8 * h + 3]),
+                   "=f"(b[8 * h + 4]), "=f"(b[8 * h + 5]), "=f"(b[8 * h + 6]), "=f"(b[8 * h + 7])
+                 : "l"(p + 8 * h));
+}
+__device__ __forceinline__ void load_blk16(const double* p, double* b) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h)
+    asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+                 : "=d"(b[4 * h]), "=d"(b[4 * h + 1]), "=d"(b[4 * h + 2]), "=d"(b[4 * h + 3])
+                 : "l"(p + 4 * h));
+}
+
+template <typename T>
+__device__ __forceinline__ void load_block(const T* p, T* b, bool wide) {
+  if (wide) {
+    load_blk16(p, b);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) load_vec4(p + 4 * q, b + 4 * q);
+  }
+}
+
 // 4-element rows (shared or global memory) as single 16-byte (float) or two 16-byte
 // (double) accesses: lanes that touch consecutive rows then hit distinct
 // banks, where four scalar accesses at a 16-byte stride collide four ways.
@@ -72,6 +104,7 @@ __global__ void __launch_bounds__(256) k_galerkin_rows(const T* __restrict__ Aha
   T* rrow = reinterpret_cast<T*>(smem_raw);
   T* t = rrow + 4 * g.NB;
   const int64_t nrow = g.nrow;
+  const bool wide = (reinterpret_cast<uintptr_t>(Ahat) & 31) == 0;
   for (int64_t i = g.i_begin + blockIdx.x; i < g.i_end; i += gridDim.x) {
     if ((pmask[i] & 15u) == 0) {
       for (int d = threadIdx.x; d < g.nout; d += blockDim.x) Aout[(int64_t)d * nrow + i] = T(0);
@@ -90,8 +123,7 @@ __global__ void __launch_bounds__(256) k_galerkin_rows(const T* __restrict__ Aha
           const int2 jo = g.l1_pairs[e];
           const T* blk = Ahat + ((int64_t)jo.y * nrow + p) * 16;
           T b[16];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) load_vec4(blk + 4 * r, b + 4 * r);
+          load_block(blk, b, wide);
           const T r0 = rrow[4 * jo.x], r1 = rrow[4 * jo.x + 1];
           const T r2 = rrow[4 * jo.x + 2], r3 = rrow[4 * jo.x + 3];
           acc0 += b[0] * r0 + b[1] * r1 + b[2] * r2 + b[3] * r3;
@@ -139,16 +171,18 @@ size_t galerkin_tile_smem_bytes(const GalerkinGeom& g, size_t elem) {
 }
 
 template <typename T, int LPT>
-__global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Ahat,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_galerkin_tile(const T* __restrict__ Ahat,
                                                        const T* __restrict__ Rhat,
                                                        const uint32_t* __restrict__ pmask,
                                                        GalerkinGeom g, T* __restrict__ Aout) {
+  static_assert(LPT >= 4 && LPT <= 32 && (LPT & (LPT - 1)) == 0, "lanes per target");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NB = g.NB, W = g.tile_W, WW = W * W, wmin = g.tile_wmin;
   T* rr = reinterpret_cast<T*>(smem_raw);  // [4][NB][4]
   T* tt = rr + 16 * NB;                    // [4][WW][4]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int64_t nrow = g.nrow;
+  const bool wide = (reinterpret_cast<uintptr_t>(Ahat) & 31) == 0;
   const int64_t t0 = g.i_begin >> 2, t1 = (g.i_end + 3) >> 2;
   for (int64_t tile = t0 + blockIdx.x; tile < t1; tile += gridDim.x) {
     const int64_t i0 = tile << 2;
@@ -180,8 +214,7 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
           const int2 ent = g.t1[e];
           const T* blk = Ahat + ((int64_t)ent.x * nrow + p) * 16;
           T b[16];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) load_vec4(blk + 4 * q, b + 4 * q);
+          load_block(blk, b, wide);
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
             const int j = ((unsigned)ent.y >> (8 * r)) & 0xffu;
@@ -234,14 +267,23 @@ __global__ void __launch_bounds__(256) k_galerkin_tile(const T* __restrict__ Aha
             }
           }
         }
+        // Reduce-scatter of the four row sums over the LPT lanes: the lanes
+        // that differ in bit 0 trade two of the four partial sums, those that
+        // differ in bit 1 trade one, and the remaining bits add whole values,
+        // so lane `sub` < 4 ends with row r = 2 (sub & 1) + (sub >> 1 & 1):
+        // 3 + log2(LPT / 4) shuffles instead of 4 log2(LPT).
+        const bool b0 = (sub & 1) != 0, b1 = (sub & 2) != 0;
+        T k0 = b0 ? acc[2] : acc[0], k1 = b0 ? acc[3] : acc[1];
+        k0 += __shfl_xor_sync(0xffffffffu, b0 ? acc[0] : acc[2], 1);
+        k1 += __shfl_xor_sync(0xffffffffu, b0 ? acc[1] : acc[3], 1);
+        T v = (b1 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, b1 ? k0 : k1, 2);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          T v = acc[r];
-#pragma unroll
-          for (int o = LPT / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (sub == 0 && ok && d[r] >= 0 && i0 + r >= g.i_begin && i0 + r < g.i_end)
-            Aout[(int64_t)d[r] * nrow + i0 + r] = live[r] ? v : T(0);
-        }
+        for (int o = 4; o < LPT; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int r = 2 * (int)b0 + (int)b1;
+        const int dr = r == 0 ? d[0] : (r == 1 ? d[1] : (r == 2 ? d[2] : d[3]));
+        const bool lr = r == 0 ? live[0] : (r == 1 ? live[1] : (r == 2 ? live[2] : live[3]));
+        if (sub < 4 && ok && dr >= 0 && i0 + r >= g.i_begin && i0 + r < g.i_end)
+          Aout[(int64_t)dr * nrow + i0 + r] = lr ? v : T(0);
       }
     }
     __syncthreads();
@@ -264,6 +306,7 @@ __global__ void __launch_bounds__(256) k_galerkin_warprow(const T* __restrict__ 
   T* rrow = reinterpret_cast<T*>(smem_raw) + (size_t)warp * per;
   T* t = rrow + 4 * g.NB;
   const int64_t nrow = g.nrow;
+  const bool wide = (reinterpret_cast<uintptr_t>(Ahat) & 31) == 0;
   for (int64_t i = g.i_begin + (int64_t)blockIdx.x * nwarp + warp; i < g.i_end;
        i += (int64_t)gridDim.x * nwarp) {
     if ((pmask[i] & 15u) == 0) {
@@ -287,8 +330,7 @@ __global__ void __launch_bounds__(256) k_galerkin_warprow(const T* __restrict__ 
           const int2 jo = g.l1_pairs[e];
           const T* blk = Ahat + ((int64_t)jo.y * nrow + p) * 16;
           T b[16];
-#pragma unroll
-          for (int r = 0; r < 4; ++r) load_vec4(blk + 4 * r, b + 4 * r);
+          load_block(blk, b, wide);
           const T r0 = rrow[4 * jo.x], r1 = rrow[4 * jo.x + 1];
           const T r2 = rrow[4 * jo.x + 2], r3 = rrow[4 * jo.x + 3];
           acc0 += b[0] * r0 + b[1] * r1 + b[2] * r2 + b[3] * r3;
