@@ -159,9 +159,10 @@ __global__ void __launch_bounds__(256) k_galerkin_rows(const T* __restrict__ Aha
 
 // Four coarse rows per CTA: the 2 x 2 cells i0..i0+3 of one level-(k-2)
 // parent (row r at (r & 1, r >> 1) from the tile origin).  Phase 1: a thread
-// per position u of the tile's window box loads each block Ahat[o][origin+u]
-// once and applies it to every row whose patch reaches it (host list t1:
-// the neighbour index j of each row), accumulating t_r(u) for the four rows.
+// per position u of the tile's window box that phase 2 reads (host list
+// t1_order) loads each block Ahat[o][origin+u] once and applies it to every
+// row whose patch reaches it (host list t1: the neighbour index j of each
+// row), accumulating t_r(u) for the four rows.
 // Phase 2: a warp per output target cell c loads the row Rhat_c once (lanes
 // over j) and forms the dot products with t_r(c + N_j) of every row r for
 // which c - r is an output offset (host list t2).  Compared with a row per
@@ -199,8 +200,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_galerkin_tile(c
       sst4(rr + (r * NB + j) * 4, v);
     }
     __syncthreads();
-    // phase 1: t_r(u) = sum over stored blocks of the window
-    for (int u = threadIdx.x; u < WW; u += blockDim.x) {
+    // phase 1: t_r(u) = sum over stored blocks of the window, for the
+    // positions that phase 2 reads (longest block lists first)
+    for (int iu = threadIdx.x; iu < g.nt1u; iu += blockDim.x) {
+      const int u = __ldg(g.t1_order + iu);
       const int uy = u / W, ux = u - uy * W;
       const int p = shift_cell(x0, y0, ux + wmin, uy + wmin, g.Lpar, nrow);
       T acc[4][4];

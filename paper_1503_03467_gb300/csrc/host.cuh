@@ -224,6 +224,7 @@ struct SymLevel {
   int tile_wmin = 0, tile_W = 0;
   std::vector<int> t1_ptr;
   std::vector<int2> t1;           // (o, j of rows 0..3 packed in bytes)
+  std::vector<int> t1_order;      // the window positions phase 2 reads, by decreasing list length
   std::vector<int4> t2;           // (c.x, c.y, d0 | d1 << 16, d2 | d3 << 16)
   // per target e, the pairs (j, u) whose window position u = c + N_j lies in
   // the window of some row of the tile (packed j | u << 8, ranges t2p_ptr);
@@ -487,7 +488,7 @@ struct PlanLevel {
   OffSet O_next;
   // byte offsets of this level's tables in Plan::packed
   enum { kPairIdx, kHalf, kAdjPtr, kAdj, kDiagH, kWin, kL1Ptr, kL1Pairs, kOut, kL2Ptr, kL2Pairs,
-         kT1Ptr, kT1, kT2, kT2pPtr, kT2p, kOffNext, kMapNext, kNumTables };
+         kT1Ptr, kT1, kT2, kT2pPtr, kT2p, kT1Order, kOffNext, kMapNext, kNumTables };
   size_t table_off[kNumTables] = {};
 };
 struct Plan {

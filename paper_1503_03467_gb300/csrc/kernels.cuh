@@ -268,6 +268,8 @@ struct GalerkinGeom {
   int tile_wmin, tile_W; // tiles: window box [wmin, wmin + W)^2 from the tile origin
   const int* t1_ptr;     // W * W + 1
   const int2* t1;        // (o, j per row packed in bytes, 0xff = none)
+  int nt1u;              // window positions read by phase 2 ...
+  const int* t1_order;   // ... in order of decreasing list length
   int nt2;
   const int4* t2;        // (c.x, c.y, d0 | d1 << 16, d2 | d3 << 16), d = -1: none
   const int* t2p_ptr;    // nt2 + 1

@@ -83,25 +83,8 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
   const int W = wmax - wmin + 2;
   S.tile_wmin = wmin;
   S.tile_W = W;
-  S.t1_ptr.assign((size_t)W * W + 1, 0);
-  for (int uy = 0; uy < W; ++uy)
-    for (int ux = 0; ux < W; ++ux) {
-      const int u = uy * W + ux;
-      for (int o = 0; o < O_k.size(); ++o) {
-        uint32_t packed = 0;
-        bool any = false;
-        for (int r = 0; r < 4; ++r) {
-          // t_i(w) gathers A_hat[o][i + w] R_hat_i[j] with N_j = w + O_o
-          const int wx = ux + wmin - (r & 1), wy = uy + wmin - (r >> 1);
-          int j = S.WIN.find(wx, wy) >= 0 ? N.find(wx + O_k.v[o].x, wy + O_k.v[o].y) : -1;
-          if (j > 254) fail(GAMBLET_ERR_UNSUPPORTED, "neighbourhood too large for tiled Galerkin");
-          if (j >= 0) any = true;
-          packed |= (uint32_t)(j >= 0 ? j : 0xff) << (8 * r);
-        }
-        if (any) S.t1.push_back(make_int2(o, (int)packed));
-      }
-      S.t1_ptr[u + 1] = (int)S.t1.size();
-    }
+  // phase 2: the output targets of the tile and, per target, the window
+  // positions its patch reaches
   std::set<std::pair<int, int>> targets;
   for (int r = 0; r < 4; ++r)
     for (const int2& d : S.Sp.v) targets.insert({d.y + (r >> 1), d.x + (r & 1)});
@@ -114,6 +97,7 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
     std::vector<int> pairs;
   };
   std::vector<Target> tl;
+  std::vector<char> read(W * W, 0);  // window positions phase 2 reads
   for (const auto& c : targets) {
     const int cx = c.second, cy = c.first;
     int dr[4];
@@ -131,6 +115,7 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
       if (u < 0 || u >= W * W || (u >> 23) != 0)
         fail(GAMBLET_ERR_UNSUPPORTED, "window too large for tiled Galerkin");
       t.pairs.push_back(j | (u << 8));
+      read[u] = 1;
     }
     tl.push_back(std::move(t));
   }
@@ -143,6 +128,36 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
     S.t2p.insert(S.t2p.end(), t.pairs.begin(), t.pairs.end());
     S.t2p_ptr.push_back((int)S.t2p.size());
   }
+  // phase 1: the block list of every window position that phase 2 reads (the
+  // others - the part of the window below the half-plane targets' patches -
+  // are left out: their products would never be used)
+  S.t1_ptr.assign((size_t)W * W + 1, 0);
+  for (int uy = 0; uy < W; ++uy)
+    for (int ux = 0; ux < W; ++ux) {
+      const int u = uy * W + ux;
+      for (int o = 0; o < O_k.size() && read[u]; ++o) {
+        uint32_t packed = 0;
+        bool any = false;
+        for (int r = 0; r < 4; ++r) {
+          // t_i(w) gathers A_hat[o][i + w] R_hat_i[j] with N_j = w + O_o
+          const int wx = ux + wmin - (r & 1), wy = uy + wmin - (r >> 1);
+          int j = S.WIN.find(wx, wy) >= 0 ? N.find(wx + O_k.v[o].x, wy + O_k.v[o].y) : -1;
+          if (j > 254) fail(GAMBLET_ERR_UNSUPPORTED, "neighbourhood too large for tiled Galerkin");
+          if (j >= 0) any = true;
+          packed |= (uint32_t)(j >= 0 ? j : 0xff) << (8 * r);
+        }
+        if (any) S.t1.push_back(make_int2(o, (int)packed));
+      }
+      S.t1_ptr[u + 1] = (int)S.t1.size();
+    }
+  // the positions phase 2 reads, by decreasing block count: the threads of a
+  // CTA take them round-robin, so the lanes of a warp walk lists of about
+  // the same length and the threads' totals differ by at most one list
+  for (int u = 0; u < W * W; ++u)
+    if (read[u]) S.t1_order.push_back(u);
+  std::stable_sort(S.t1_order.begin(), S.t1_order.end(), [&S](int a, int b) {
+    return S.t1_ptr[a + 1] - S.t1_ptr[a] > S.t1_ptr[b + 1] - S.t1_ptr[b];
+  });
   return S;
 }
 
@@ -369,6 +384,7 @@ std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
     pl.table_off[PlanLevel::kT2] = put_v(S.t2);
     pl.table_off[PlanLevel::kT2pPtr] = put_v(S.t2p_ptr);
     pl.table_off[PlanLevel::kT2p] = put_v(S.t2p);
+    pl.table_off[PlanLevel::kT1Order] = put_v(S.t1_order);
     pl.table_off[PlanLevel::kOffNext] = put_v(pl.O_next.v);
     pl.table_off[PlanLevel::kMapNext] = put_v(pl.map_next);
     for (MmaWin& W : pl.mwin) {
