@@ -102,9 +102,11 @@ typedef struct {
                                timing candidates on a sample of each large
                                level, once per geometry and precision in a
                                process; 0: fixed rules                     */
-  int32_t galerkin_variant; /* -1: automatic; 0..5: use that Galerkin
+  int32_t galerkin_variant; /* -1: automatic; 0..8: use that Galerkin
                                kernel on every level (3, 4, 5: the tile
                                kernel with 8, 4, 16 lanes per output;
+                               6, 7, 8: the tile kernel with 4, 8, 16
+                               lanes per horizontal pair of outputs;
                                see gamblet_launch_shapes)                  */
   int32_t patch_gather;     /* -1: automatic; 0, 1, 2: use the SIMT patch
                                CG with that block gather on every level;

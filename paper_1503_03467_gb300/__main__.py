@@ -5,7 +5,7 @@ timing and profiling runs:
                                    [--dim 2|3] [--rule euclid|cheb]
                                    [--rho 3] [--contrast 1e4] [--seed 0]
                                    [--repeat 1] [--profile] [--capture-last]
-                                   [--no-autotune] [--galerkin-variant -1|0|1|2]
+                                   [--no-autotune] [--galerkin-variant -1|0..8]
                                    [--patch-gather -1|0|1|2]
                                    [--grad-one-pass] [--patch-tol 0] [--wall]
 

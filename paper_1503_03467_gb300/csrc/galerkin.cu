@@ -171,7 +171,94 @@ size_t galerkin_tile_smem_bytes(const GalerkinGeom& g, size_t elem) {
   return elem * (16 * (size_t)g.NB + 16 * (size_t)g.tile_W * g.tile_W);
 }
 
+// Phase 2 of the tile kernel over horizontal pairs of targets (c, c + (1, 0)):
+// one list of window positions u per pair (the union of the two targets'
+// lists), so each t_r(u) read from shared memory serves both targets and the
+// list bookkeeping is shared; a target without partner has d = -1 in its
+// second record and ja / jb = 0xff where its patch does not reach u.  The
+// eight sums (two targets x four rows) are reduce-scattered over the LPT
+// lanes: lanes that differ in bit 0 trade four of them, in bit 1 two, in bit
+// 2 one, and higher bits add whole values.
 template <typename T, int LPT>
+__device__ __forceinline__ void galerkin_tile_pairs(const GalerkinGeom& g, const T* __restrict__ Rhat,
+                                                    const uint32_t* __restrict__ pmask,
+                                                    const T* tt, int WW, int x0, int y0, int64_t i0,
+                                                    const bool (&live)[4], T* __restrict__ Aout) {
+  constexpr int TPW = 32 / LPT;
+  constexpr int H = LPT >= 8 ? 1 : 2;  // values a lane holds after the reduce-scatter
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int sub = lane & (LPT - 1), grp = lane / LPT;
+  const int NB = g.NB;
+  const int64_t nrow = g.nrow;
+  for (int e0 = TPW * warp; e0 < g.nt3; e0 += TPW * nwarp) {
+    const int e = e0 + grp;
+    const bool ok = e < g.nt3;
+    const int4 ta = ok ? g.t3[2 * e] : make_int4(0, 0, -1, -1);
+    const int4 tb = ok ? g.t3[2 * e + 1] : make_int4(0, 0, -1, -1);
+    int d[8] = {(int)(short)(ta.z & 0xffff), ta.z >> 16, (int)(short)(ta.w & 0xffff), ta.w >> 16,
+                (int)(short)(tb.z & 0xffff), tb.z >> 16, (int)(short)(tb.w & 0xffff), tb.w >> 16};
+    const bool any_b = d[4] >= 0 || d[5] >= 0 || d[6] >= 0 || d[7] >= 0;
+    const int ipa = ok ? shift_cell(x0, y0, ta.x, ta.y, g.Lpar, nrow) : -1;
+    const int ipb = ok && any_b ? shift_cell(x0, y0, tb.x, tb.y, g.Lpar, nrow) : -1;
+    const bool ha = ipa >= 0 && (pmask[ipa] & 15u);
+    const bool hb = ipb >= 0 && (pmask[ipb] & 15u);
+    bool need[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) need[r] = d[r] >= 0 || d[4 + r] >= 0;
+    T v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = T(0);
+    if (ha || hb) {
+      const T* ra = Rhat + (int64_t)(ha ? ipa : 0) * 4 * NB;
+      const T* rb = Rhat + (int64_t)(hb ? ipb : 0) * 4 * NB;
+      const int q1 = g.t3p_ptr[e + 1];
+      for (int q = g.t3p_ptr[e] + sub; q < q1; q += LPT) {
+        const uint32_t pu = __ldg(g.t3p + q);
+        const int u = (int)(pu & 0xffffu), ja = (int)((pu >> 16) & 0xffu), jb = (int)(pu >> 24);
+        T va[4] = {T(0), T(0), T(0), T(0)}, vb[4] = {T(0), T(0), T(0), T(0)};
+        if (ha && ja != 0xff) load_vec4(ra + 4 * ja, va);
+        if (hb && jb != 0xff) load_vec4(rb + 4 * jb, vb);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if (!need[r]) continue;
+          T tv[4];
+          sld4(tt + ((size_t)r * WW + u) * 4, tv);
+          v[r] += va[0] * tv[0] + va[1] * tv[1] + va[2] * tv[2] + va[3] * tv[3];
+          v[4 + r] += vb[0] * tv[0] + vb[1] * tv[1] + vb[2] * tv[2] + vb[3] * tv[3];
+        }
+      }
+    }
+    int base = 0;
+#pragma unroll
+    for (int h = 4, bit = 1; h >= H && bit < LPT; h >>= 1, bit <<= 1) {
+      const bool upper = (sub & bit) != 0;
+#pragma unroll
+      for (int i = 0; i < h; ++i) {
+        const T send = upper ? v[i] : v[i + h];
+        const T keep = upper ? v[i + h] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+      }
+      if (upper) base += h;
+    }
+#pragma unroll
+    for (int bit = 8; bit < LPT; bit <<= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], bit);
+    if (sub < 8 / H && ok) {
+#pragma unroll
+      for (int t = 0; t < H; ++t) {
+        const int idx = base + t, r = idx & 3;
+        int dv = -1;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c == idx) dv = d[c];
+        const bool lr = r == 0 ? live[0] : (r == 1 ? live[1] : (r == 2 ? live[2] : live[3]));
+        if (dv >= 0 && i0 + r >= g.i_begin && i0 + r < g.i_end)
+          Aout[(int64_t)dv * nrow + i0 + r] = lr ? v[t] : T(0);
+      }
+    }
+  }
+}
+
+template <typename T, int LPT, bool PAIRS>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_galerkin_tile(const T* __restrict__ Ahat,
                                                        const T* __restrict__ Rhat,
                                                        const uint32_t* __restrict__ pmask,
@@ -241,7 +328,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_galerkin_tile(c
     // dense levels) stride over the target's list of pairs (j, u) whose
     // window position holds a nonzero t; the partial sums combine in
     // log2(LPT) shuffle steps.
-    {
+    if constexpr (PAIRS) {
+      galerkin_tile_pairs<T, LPT>(g, Rhat, pmask, tt, WW, x0, y0, i0, live, Aout);
+    } else {
       constexpr int TPW = 32 / LPT;
       const int sub = lane & (LPT - 1), grp = lane / LPT;
       for (int e0 = TPW * warp; e0 < g.nt2; e0 += TPW * nwarp) {
@@ -445,10 +534,16 @@ void launch_galerkin(const T* Ahat, const T* Rhat, const uint32_t* pmask_k, Gale
   int64_t grid = nrows < 65535 * 16 ? nrows : 65535 * 16;
   count_launch();
   if (g.variant >= 3) {
-    // 3, 4, 5: the tile kernel with 8, 4 or 16 lanes per output target
+    // 3, 4, 5: the tile kernel with 8, 4 or 16 lanes per output target;
+    // 6, 7, 8: the same with 4, 8 or 16 lanes per horizontal pair of targets
     const size_t st = galerkin_tile_smem_bytes(g, sizeof(T));
-    auto kern = g.variant == 4 ? k_galerkin_tile<T, 4>
-                               : (g.variant == 5 ? k_galerkin_tile<T, 16> : k_galerkin_tile<T, 8>);
+    void (*kern)(const T*, const T*, const uint32_t*, GalerkinGeom, T*) =
+        g.variant == 4   ? k_galerkin_tile<T, 4, false>
+        : g.variant == 5 ? k_galerkin_tile<T, 16, false>
+        : g.variant == 6 ? k_galerkin_tile<T, 4, true>
+        : g.variant == 7 ? k_galerkin_tile<T, 8, true>
+        : g.variant == 8 ? k_galerkin_tile<T, 16, true>
+                         : k_galerkin_tile<T, 8, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st);
     const int64_t nt = ((g.i_end + 3) >> 2) - (g.i_begin >> 2);
     kern<<<(unsigned)(nt < 65535 * 16 ? nt : 65535 * 16), 256, st, s>>>(Ahat, Rhat, pmask_k, g,

@@ -320,6 +320,10 @@ void setup_local(gamblet_ctx* h) {
     gg.t2 = plan_table<int4>(dplan, pl, PlanLevel::kT2);
     gg.t2p_ptr = plan_table<int>(dplan, pl, PlanLevel::kT2pPtr);
     gg.t2p = plan_table<int>(dplan, pl, PlanLevel::kT2p);
+    gg.nt3 = (int)S.t3p_ptr.size() - 1;
+    gg.t3 = plan_table<int4>(dplan, pl, PlanLevel::kT3);
+    gg.t3p_ptr = plan_table<int>(dplan, pl, PlanLevel::kT3pPtr);
+    gg.t3p = plan_table<uint32_t>(dplan, pl, PlanLevel::kT3p);
     // 2 x 2 row tiles while their window boxes stay small enough for
     // several CTAs per SM, else the warp-cooperative kernel; the autotuner
     // decides on large levels
@@ -327,7 +331,7 @@ void setup_local(gamblet_ctx* h) {
     if (sizeof(T) * 4 * ((size_t)NB + (size_t)gg.nwin) > 227 * 1024)
       fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin window exceeds shared memory");
     T* Acell = P.alloc<T>((int64_t)gg.nout * L.npar);
-    if (h->opts.galerkin_variant >= 0 && h->opts.galerkin_variant <= 5) {
+    if (h->opts.galerkin_variant >= 0 && h->opts.galerkin_variant <= 8) {
       gg.variant = h->opts.galerkin_variant;
       if (gg.variant == 2 && 8 * sizeof(T) * 4 * ((size_t)NB + gg.nwin) > 227 * 1024)
         fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin warp-per-row window exceeds shared memory");
@@ -596,8 +600,8 @@ gamblet_ctx* setup_impl(const gamblet_csr* A, int32_t q, const int32_t* cells,
       fail(GAMBLET_ERR_INVALID_ARG, "unknown precision");
     if (h->opts.nbr_rule != 0 && h->opts.nbr_rule != 1)
       fail(GAMBLET_ERR_INVALID_ARG, "nbr_rule must be 0 or 1");
-    if (h->opts.galerkin_variant < -1 || h->opts.galerkin_variant > 5)
-      fail(GAMBLET_ERR_INVALID_ARG, "galerkin_variant must be -1 or 0..5");
+    if (h->opts.galerkin_variant < -1 || h->opts.galerkin_variant > 8)
+      fail(GAMBLET_ERR_INVALID_ARG, "galerkin_variant must be -1 or 0..8");
     if (h->opts.patch_gather < -1 || h->opts.patch_gather > 4)
       fail(GAMBLET_ERR_INVALID_ARG, "patch_gather must be -1 or 0..4");
     if (h->exact && q > 7)

@@ -231,6 +231,13 @@ struct SymLevel {
   // targets are sorted by decreasing pair count so that the targets that a
   // warp handles together have about the same work
   std::vector<int> t2p_ptr, t2p;
+  // the targets in horizontal pairs (c, c + (1, 0)) where both exist, else
+  // alone (second record with d = -1): two t2-style records per pair, and
+  // per pair the union of the two targets' window positions u with the j of
+  // each (packed u | ja << 16 | jb << 24, 0xff = none), by decreasing length
+  std::vector<int4> t3;
+  std::vector<int> t3p_ptr;
+  std::vector<uint32_t> t3p;
 };
 
 // ---------------------------------------------------------------- handle
@@ -488,7 +495,8 @@ struct PlanLevel {
   OffSet O_next;
   // byte offsets of this level's tables in Plan::packed
   enum { kPairIdx, kHalf, kAdjPtr, kAdj, kDiagH, kWin, kL1Ptr, kL1Pairs, kOut, kL2Ptr, kL2Pairs,
-         kT1Ptr, kT1, kT2, kT2pPtr, kT2p, kT1Order, kOffNext, kMapNext, kNumTables };
+         kT1Ptr, kT1, kT2, kT2pPtr, kT2p, kT1Order, kT3, kT3pPtr, kT3p, kOffNext, kMapNext,
+         kNumTables };
   size_t table_off[kNumTables] = {};
 };
 struct Plan {

@@ -119,6 +119,49 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
     }
     tl.push_back(std::move(t));
   }
+  // the same targets in horizontal pairs (c, c + (1, 0)) where both exist
+  // (tl is in (y, x) order here): one list of window positions u per pair,
+  // the union of the two targets' lists, with both targets' j at u
+  {
+    struct Group {
+      int4 a, b;
+      std::vector<uint32_t> ent;
+    };
+    std::vector<Group> gl;
+    const int4 none = make_int4(0, 0, -1, -1);
+    for (size_t e = 0; e < tl.size(); ++e) {
+      Group gr;
+      gr.a = tl[e].t;
+      gr.b = none;
+      std::map<int, std::pair<int, int>> at;  // u -> (j of a, j of b)
+      for (int pu : tl[e].pairs) at[pu >> 8] = {pu & 0xff, 0xff};
+      if (e + 1 < tl.size() && tl[e + 1].t.y == tl[e].t.y && tl[e + 1].t.x == tl[e].t.x + 1) {
+        gr.b = tl[e + 1].t;
+        for (int pu : tl[e + 1].pairs) {
+          auto it = at.find(pu >> 8);
+          if (it == at.end()) at[pu >> 8] = {0xff, pu & 0xff};
+          else it->second.second = pu & 0xff;
+        }
+        ++e;
+      }
+      for (const auto& kv : at) {
+        if (kv.first > 0xffff) fail(GAMBLET_ERR_UNSUPPORTED, "window too large for tiled Galerkin");
+        gr.ent.push_back((uint32_t)kv.first | ((uint32_t)kv.second.first << 16) |
+                         ((uint32_t)kv.second.second << 24));
+      }
+      gl.push_back(std::move(gr));
+    }
+    std::stable_sort(gl.begin(), gl.end(), [](const Group& a, const Group& b) {
+      return a.ent.size() > b.ent.size();
+    });
+    S.t3p_ptr.assign(1, 0);
+    for (const Group& gr : gl) {
+      S.t3.push_back(gr.a);
+      S.t3.push_back(gr.b);
+      S.t3p.insert(S.t3p.end(), gr.ent.begin(), gr.ent.end());
+      S.t3p_ptr.push_back((int)S.t3p.size());
+    }
+  }
   std::stable_sort(tl.begin(), tl.end(), [](const Target& a, const Target& b) {
     return a.pairs.size() > b.pairs.size();
   });
@@ -385,6 +428,9 @@ std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
     pl.table_off[PlanLevel::kT2pPtr] = put_v(S.t2p_ptr);
     pl.table_off[PlanLevel::kT2p] = put_v(S.t2p);
     pl.table_off[PlanLevel::kT1Order] = put_v(S.t1_order);
+    pl.table_off[PlanLevel::kT3] = put_v(S.t3);
+    pl.table_off[PlanLevel::kT3pPtr] = put_v(S.t3p_ptr);
+    pl.table_off[PlanLevel::kT3p] = put_v(S.t3p);
     pl.table_off[PlanLevel::kOffNext] = put_v(pl.O_next.v);
     pl.table_off[PlanLevel::kMapNext] = put_v(pl.map_next);
     for (MmaWin& W : pl.mwin) {

@@ -246,7 +246,7 @@ void tune_galerkin_variant(gamblet_ctx* h, int k, GalerkinGeom& gg, const T* Aha
     gt.i_begin = (gg.nrow / 2 / kTuneSampleRows) * kTuneSampleRows;
     gt.i_end = std::min(gt.i_begin + kTuneSampleRows, gg.nrow);
     float best = 1e30f;
-    for (int cand : {0, 1, 2, 3, 4, 5}) {
+    for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 8}) {
       if (cand == 2 && 8 * sizeof(T) * 4 * ((size_t)gg.NB + gg.nwin) > 227 * 1024) continue;
       if (cand >= 3 && galerkin_tile_smem_bytes(gg, sizeof(T)) > 227 * 1024) continue;
       gt.variant = cand;
