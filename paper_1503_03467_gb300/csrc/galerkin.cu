@@ -546,8 +546,9 @@ void launch_galerkin(const T* Ahat, const T* Rhat, const uint32_t* pmask_k, Gale
                          : k_galerkin_tile<T, 8, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st);
     const int64_t nt = ((g.i_end + 3) >> 2) - (g.i_begin >> 2);
-    kern<<<(unsigned)(nt < 65535 * 16 ? nt : 65535 * 16), 256, st, s>>>(Ahat, Rhat, pmask_k, g,
-                                                                       Aout);
+    const int threads = g.tile_threads == 128 ? 128 : 256;
+    kern<<<(unsigned)(nt < 65535 * 16 ? nt : 65535 * 16), threads, st, s>>>(Ahat, Rhat, pmask_k,
+                                                                           g, Aout);
   } else if (g.variant == 2) {
     const size_t smem8 = 8 * smem;  // eight warps, one row each
     cudaFuncSetAttribute(k_galerkin_warprow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

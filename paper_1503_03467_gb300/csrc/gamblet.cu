@@ -312,6 +312,7 @@ void setup_local(gamblet_ctx* h) {
     gg.i_end = L.npar;
     gg.tile_wmin = S.tile_wmin;
     gg.tile_W = S.tile_W;
+    gg.tile_threads = 256;
     gg.t1_ptr = plan_table<int>(dplan, pl, PlanLevel::kT1Ptr);
     gg.t1 = plan_table<int2>(dplan, pl, PlanLevel::kT1);
     gg.nt1u = (int)S.t1_order.size();

@@ -266,6 +266,7 @@ struct GalerkinGeom {
                          // 2: warp per row, 3, 4, 5: 2 x 2 row tiles with 8, 4 or 16
                          // lanes per output target
   int tile_wmin, tile_W; // tiles: window box [wmin, wmin + W)^2 from the tile origin
+  int tile_threads;      // tiles: threads per CTA (256, or 128 for more CTAs per SM)
   const int* t1_ptr;     // W * W + 1
   const int2* t1;        // (o, j per row packed in bytes, 0xff = none)
   int nt1u;              // window positions read by phase 2 ...

@@ -17,7 +17,11 @@ namespace hs {
 // every later setup of that geometry (the results depend on the shape only
 // through summation order).  Levels smaller than kTuneMinParents keep the
 // fixed rule: their kernels are too short for the choice to matter.
-constexpr int64_t kTuneSample = 4096;  // a 64 x 64 Morton block of coarse cells
+// Patch solves: a 256 x 128 Morton block of coarse cells, about fifteen
+// patches per CTA of the persistent SIMT kernels, so that the timing sees
+// their steady state (with two per CTA the launch and the tail dominated,
+// and the tuner's choice on the finest level changed from run to run)
+constexpr int64_t kTuneSample = 32768;
 // Galerkin rows are cheap and one variant packs eight rows per CTA: a larger
 // sample keeps every candidate's grid larger than the GPU
 constexpr int64_t kTuneSampleRows = 16384;
@@ -239,6 +243,7 @@ void tune_galerkin_variant(gamblet_ctx* h, int k, GalerkinGeom& gg, const T* Aha
   if (!h->opts.autotune || gg.nrow < kTuneMinParents) return;
   const std::string key = h->plan->key + "/galerkin/" + std::to_string(k) + "/" +
                           std::to_string(sizeof(T));
+  // code: variant + 16 * (tile kernels launched with 128 threads per CTA)
   int v = gg.variant;
   if (!tune_lookup(key, &v)) {
     cudaStream_t s = h->s;
@@ -246,21 +251,25 @@ void tune_galerkin_variant(gamblet_ctx* h, int k, GalerkinGeom& gg, const T* Aha
     gt.i_begin = (gg.nrow / 2 / kTuneSampleRows) * kTuneSampleRows;
     gt.i_end = std::min(gt.i_begin + kTuneSampleRows, gg.nrow);
     float best = 1e30f;
-    for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 8}) {
-      if (cand == 2 && 8 * sizeof(T) * 4 * ((size_t)gg.NB + gg.nwin) > 227 * 1024) continue;
-      if (cand >= 3 && galerkin_tile_smem_bytes(gg, sizeof(T)) > 227 * 1024) continue;
-      gt.variant = cand;
-      const float ms = time_on_stream(s, [&] {
-        launch_galerkin<T>(Ahat, Rhat, h->lv[k].pmask, gt, Acell, s);
-      });
-      if (ms < best) {
-        best = ms;
-        v = cand;
+    for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 8})
+      for (int half : {0, 1}) {
+        if (cand == 2 && 8 * sizeof(T) * 4 * ((size_t)gg.NB + gg.nwin) > 227 * 1024) continue;
+        if (cand >= 3 && galerkin_tile_smem_bytes(gg, sizeof(T)) > 227 * 1024) continue;
+        if (half && cand < 3) continue;
+        gt.variant = cand;
+        gt.tile_threads = half ? 128 : 256;
+        const float ms = time_on_stream(s, [&] {
+          launch_galerkin<T>(Ahat, Rhat, h->lv[k].pmask, gt, Acell, s);
+        });
+        if (ms < best) {
+          best = ms;
+          v = cand + 16 * half;
+        }
       }
-    }
     tune_store(key, v);
   }
-  gg.variant = v;
+  gg.variant = v % 16;
+  gg.tile_threads = v >= 16 ? 128 : 256;
 }
 
 template <typename T>
