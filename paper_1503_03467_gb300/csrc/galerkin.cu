@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256) k_galerkin_rows(const T* __restrict__ Aha
 // which c - r is an output offset (host list t2).  Compared with a row per
 // CTA this reads each block and each Rhat row up to four times less often.
 size_t galerkin_tile_smem_bytes(const GalerkinGeom& g, size_t elem) {
-  return elem * (16 * (size_t)g.NB + 16 * (size_t)g.tile_W * g.tile_W);
+  return elem * (16 * (size_t)g.NB + 16 * (size_t)g.nt1u);
 }
 
 // Phase 2 of the tile kernel over horizontal pairs of targets (c, c + (1, 0)):
@@ -182,7 +182,7 @@ size_t galerkin_tile_smem_bytes(const GalerkinGeom& g, size_t elem) {
 template <typename T, int LPT>
 __device__ __forceinline__ void galerkin_tile_pairs(const GalerkinGeom& g, const T* __restrict__ Rhat,
                                                     const uint32_t* __restrict__ pmask,
-                                                    const T* tt, int WW, int x0, int y0, int64_t i0,
+                                                    const T* tt, int NT, int x0, int y0, int64_t i0,
                                                     const bool (&live)[4], T* __restrict__ Aout) {
   constexpr int TPW = 32 / LPT;
   constexpr int H = LPT >= 8 ? 1 : 2;  // values a lane holds after the reduce-scatter
@@ -214,7 +214,7 @@ __device__ __forceinline__ void galerkin_tile_pairs(const GalerkinGeom& g, const
       const int q1 = g.t3p_ptr[e + 1];
       for (int q = g.t3p_ptr[e] + sub; q < q1; q += LPT) {
         const uint32_t pu = __ldg(g.t3p + q);
-        const int u = (int)(pu & 0xffffu), ja = (int)((pu >> 16) & 0xffu), jb = (int)(pu >> 24);
+        const int cu = (int)(pu & 0xffffu), ja = (int)((pu >> 16) & 0xffu), jb = (int)(pu >> 24);
         T va[4] = {T(0), T(0), T(0), T(0)}, vb[4] = {T(0), T(0), T(0), T(0)};
         if (ha && ja != 0xff) load_vec4(ra + 4 * ja, va);
         if (hb && jb != 0xff) load_vec4(rb + 4 * jb, vb);
@@ -222,7 +222,7 @@ __device__ __forceinline__ void galerkin_tile_pairs(const GalerkinGeom& g, const
         for (int r = 0; r < 4; ++r) {
           if (!need[r]) continue;
           T tv[4];
-          sld4(tt + ((size_t)r * WW + u) * 4, tv);
+          sld4(tt + ((size_t)r * NT + cu) * 4, tv);
           v[r] += va[0] * tv[0] + va[1] * tv[1] + va[2] * tv[2] + va[3] * tv[3];
           v[4 + r] += vb[0] * tv[0] + vb[1] * tv[1] + vb[2] * tv[2] + vb[3] * tv[3];
         }
@@ -265,9 +265,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_galerkin_tile(c
                                                        GalerkinGeom g, T* __restrict__ Aout) {
   static_assert(LPT >= 4 && LPT <= 32 && (LPT & (LPT - 1)) == 0, "lanes per target");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int NB = g.NB, W = g.tile_W, WW = W * W, wmin = g.tile_wmin;
+  const int NB = g.NB, W = g.tile_W, NT = g.nt1u, wmin = g.tile_wmin;
   T* rr = reinterpret_cast<T*>(smem_raw);  // [4][NB][4]
-  T* tt = rr + 16 * NB;                    // [4][WW][4]
+  T* tt = rr + 16 * NB;                    // [4][NT][4]: t_r at the positions phase 2 reads
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int64_t nrow = g.nrow;
   const bool wide = (reinterpret_cast<uintptr_t>(Ahat) & 31) == 0;
@@ -290,7 +290,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_galerkin_tile(c
     // phase 1: t_r(u) = sum over stored blocks of the window, for the
     // positions that phase 2 reads (longest block lists first)
     for (int iu = threadIdx.x; iu < g.nt1u; iu += blockDim.x) {
-      const int u = __ldg(g.t1_order + iu);
+      const int ucid = __ldg(g.t1_order + iu);
+      const int u = ucid & 0xffff, cu = ucid >> 16;
       const int uy = u / W, ux = u - uy * W;
       const int p = shift_cell(x0, y0, ux + wmin, uy + wmin, g.Lpar, nrow);
       T acc[4][4];
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_galerkin_tile(c
         }
       }
 #pragma unroll
-      for (int r = 0; r < 4; ++r) sst4(tt + ((size_t)r * WW + u) * 4, acc[r]);
+      for (int r = 0; r < 4; ++r) sst4(tt + ((size_t)r * NT + cu) * 4, acc[r]);
     }
     __syncthreads();
     // phase 2: outputs A_{i0+r, c} for every target cell c.  LPT lanes per
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_galerkin_tile(c
     // window position holds a nonzero t; the partial sums combine in
     // log2(LPT) shuffle steps.
     if constexpr (PAIRS) {
-      galerkin_tile_pairs<T, LPT>(g, Rhat, pmask, tt, WW, x0, y0, i0, live, Aout);
+      galerkin_tile_pairs<T, LPT>(g, Rhat, pmask, tt, NT, x0, y0, i0, live, Aout);
     } else {
       constexpr int TPW = 32 / LPT;
       const int sub = lane & (LPT - 1), grp = lane / LPT;
@@ -347,14 +348,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_galerkin_tile(c
           const int q1 = g.t2p_ptr[e + 1];
           for (int q = g.t2p_ptr[e] + sub; q < q1; q += LPT) {
             const int pu = __ldg(g.t2p + q);
-            const int j = pu & 0xff, u = pu >> 8;
+            const int j = pu & 0xff, cu = pu >> 8;
             T rv[4];
             load_vec4(rc + 4 * j, rv);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
               if (d[r] < 0) continue;
               T tv[4];
-              sld4(tt + ((size_t)r * WW + u) * 4, tv);
+              sld4(tt + ((size_t)r * NT + cu) * 4, tv);
               acc[r] += rv[0] * tv[0] + rv[1] * tv[1] + rv[2] * tv[2] + rv[3] * tv[3];
             }
           }

@@ -312,7 +312,6 @@ void setup_local(gamblet_ctx* h) {
     gg.i_end = L.npar;
     gg.tile_wmin = S.tile_wmin;
     gg.tile_W = S.tile_W;
-    gg.tile_threads = 256;
     gg.t1_ptr = plan_table<int>(dplan, pl, PlanLevel::kT1Ptr);
     gg.t1 = plan_table<int2>(dplan, pl, PlanLevel::kT1);
     gg.nt1u = (int)S.t1_order.size();
@@ -328,12 +327,14 @@ void setup_local(gamblet_ctx* h) {
     // 2 x 2 row tiles while their window boxes stay small enough for
     // several CTAs per SM, else the warp-cooperative kernel; the autotuner
     // decides on large levels
-    gg.variant = galerkin_tile_smem_bytes(gg, sizeof(T)) <= 100 * 1024 ? 3 : 1;
+    gg.variant = galerkin_tile_smem_bytes(gg, sizeof(T)) <= 100 * 1024 ? 7 : 1;
+    gg.tile_threads = gg.variant == 7 ? 128 : 256;  // small levels: more CTAs to fill the GPU
     if (sizeof(T) * 4 * ((size_t)NB + (size_t)gg.nwin) > 227 * 1024)
       fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin window exceeds shared memory");
     T* Acell = P.alloc<T>((int64_t)gg.nout * L.npar);
     if (h->opts.galerkin_variant >= 0 && h->opts.galerkin_variant <= 8) {
       gg.variant = h->opts.galerkin_variant;
+      gg.tile_threads = 256;
       if (gg.variant == 2 && 8 * sizeof(T) * 4 * ((size_t)NB + gg.nwin) > 227 * 1024)
         fail(GAMBLET_ERR_UNSUPPORTED, "Galerkin warp-per-row window exceeds shared memory");
       if (gg.variant >= 3 && galerkin_tile_smem_bytes(gg, sizeof(T)) > 227 * 1024)

@@ -224,17 +224,18 @@ struct SymLevel {
   int tile_wmin = 0, tile_W = 0;
   std::vector<int> t1_ptr;
   std::vector<int2> t1;           // (o, j of rows 0..3 packed in bytes)
-  std::vector<int> t1_order;      // the window positions phase 2 reads, by decreasing list length
+  std::vector<int> t1_order;      // the window positions phase 2 reads, by decreasing list
+                                  // length: u | cid << 16 (cid: index among them in box order)
   std::vector<int4> t2;           // (c.x, c.y, d0 | d1 << 16, d2 | d3 << 16)
   // per target e, the pairs (j, u) whose window position u = c + N_j lies in
-  // the window of some row of the tile (packed j | u << 8, ranges t2p_ptr);
+  // the window of some row of the tile (packed j | cid(u) << 8, ranges t2p_ptr);
   // targets are sorted by decreasing pair count so that the targets that a
   // warp handles together have about the same work
   std::vector<int> t2p_ptr, t2p;
   // the targets in horizontal pairs (c, c + (1, 0)) where both exist, else
   // alone (second record with d = -1): two t2-style records per pair, and
   // per pair the union of the two targets' window positions u with the j of
-  // each (packed u | ja << 16 | jb << 24, 0xff = none), by decreasing length
+  // each (packed cid(u) | ja << 16 | jb << 24, 0xff = none), by decreasing length
   std::vector<int4> t3;
   std::vector<int> t3p_ptr;
   std::vector<uint32_t> t3p;

@@ -270,15 +270,15 @@ struct GalerkinGeom {
   const int* t1_ptr;     // W * W + 1
   const int2* t1;        // (o, j per row packed in bytes, 0xff = none)
   int nt1u;              // window positions read by phase 2 ...
-  const int* t1_order;   // ... in order of decreasing list length
+  const int* t1_order;   // ... in order of decreasing list length (u | cid << 16)
   int nt2;
   const int4* t2;        // (c.x, c.y, d0 | d1 << 16, d2 | d3 << 16), d = -1: none
   const int* t2p_ptr;    // nt2 + 1
-  const int* t2p;        // per target: (j | u << 8) with c + N_j = WIN position u
+  const int* t2p;        // per target: (j | cid << 8) with c + N_j = window position cid
   int nt3;               // target pairs (c, c + (1, 0)), variants 6-8:
   const int4* t3;        // two t2-style records per pair (second: d = -1 if alone)
   const int* t3p_ptr;    // nt3 + 1
-  const uint32_t* t3p;   // per pair: u | ja << 16 | jb << 24 (0xff = none)
+  const uint32_t* t3p;   // per pair: cid | ja << 16 | jb << 24 (0xff = none)
 };
 // Shared memory of k_galerkin_tile: four Rhat rows and four window boxes.
 size_t galerkin_tile_smem_bytes(const GalerkinGeom& g, size_t elem);

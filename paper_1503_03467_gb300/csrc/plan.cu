@@ -119,6 +119,14 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
     }
     tl.push_back(std::move(t));
   }
+  // the window products t_r(u) are kept only at the positions phase 2 reads,
+  // numbered in box order (cid), so that a tile's shared memory holds
+  // |read| instead of W^2 positions; the pair lists below carry cid
+  std::vector<int> cid(W * W, -1);
+  int ncid = 0;
+  for (int u = 0; u < W * W; ++u)
+    if (read[u]) cid[u] = ncid++;
+  if (W * W > 65536) fail(GAMBLET_ERR_UNSUPPORTED, "window too large for tiled Galerkin");
   // the same targets in horizontal pairs (c, c + (1, 0)) where both exist
   // (tl is in (y, x) order here): one list of window positions u per pair,
   // the union of the two targets' lists, with both targets' j at u
@@ -146,7 +154,7 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
       }
       for (const auto& kv : at) {
         if (kv.first > 0xffff) fail(GAMBLET_ERR_UNSUPPORTED, "window too large for tiled Galerkin");
-        gr.ent.push_back((uint32_t)kv.first | ((uint32_t)kv.second.first << 16) |
+        gr.ent.push_back((uint32_t)cid[kv.first] | ((uint32_t)kv.second.first << 16) |
                          ((uint32_t)kv.second.second << 24));
       }
       gl.push_back(std::move(gr));
@@ -168,7 +176,7 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
   S.t2p_ptr.assign(1, 0);
   for (const Target& t : tl) {
     S.t2.push_back(t.t);
-    S.t2p.insert(S.t2p.end(), t.pairs.begin(), t.pairs.end());
+    for (int pu : t.pairs) S.t2p.push_back((pu & 0xff) | (cid[pu >> 8] << 8));
     S.t2p_ptr.push_back((int)S.t2p.size());
   }
   // phase 1: the block list of every window position that phase 2 reads (the
@@ -201,6 +209,7 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
   std::stable_sort(S.t1_order.begin(), S.t1_order.end(), [&S](int a, int b) {
     return S.t1_ptr[a + 1] - S.t1_ptr[a] > S.t1_ptr[b + 1] - S.t1_ptr[b];
   });
+  for (int& u : S.t1_order) u |= cid[u] << 16;  // (u, cid) packed
   return S;
 }
 

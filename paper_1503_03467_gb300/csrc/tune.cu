@@ -25,6 +25,9 @@ constexpr int64_t kTuneSample = 32768;
 // Galerkin rows are cheap and one variant packs eight rows per CTA: a larger
 // sample keeps every candidate's grid larger than the GPU
 constexpr int64_t kTuneSampleRows = 16384;
+// Galerkin levels from 4096 rows are tuned (a whole level up to the sample
+// size): below that the fixed rule (pairs of targets, 128 threads) holds
+constexpr int64_t kTuneMinRows = 4096;
 
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
@@ -240,7 +243,7 @@ int tune_patch_shape(gamblet_ctx* h, int k, PatchPcgGeom& gp, T* Rhat, const Pat
 template <typename T>
 void tune_galerkin_variant(gamblet_ctx* h, int k, GalerkinGeom& gg, const T* Ahat,
                            const T* Rhat, T* Acell) {
-  if (!h->opts.autotune || gg.nrow < kTuneMinParents) return;
+  if (!h->opts.autotune || gg.nrow < kTuneMinRows) return;
   const std::string key = h->plan->key + "/galerkin/" + std::to_string(k) + "/" +
                           std::to_string(sizeof(T));
   // code: variant + 16 * (tile kernels launched with 128 threads per CTA)
