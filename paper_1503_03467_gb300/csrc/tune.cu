@@ -200,8 +200,11 @@ int tune_patch_shape(gamblet_ctx* h, int k, PatchPcgGeom& gp, T* Rhat, const Pat
     float best = 1e30f;
     code = gp.spp * 4 + gp.gather;
     const bool simt_fits = patch_pcg_smem_bytes<T>(gp) <= 227 * 1024;
+    // lanes per neighbour parent; the block gather by four lanes per block
+    // row (gathers 0 and 1 lose to it at every level size measured, and each
+    // candidate costs cold-start time; both stay available as forced shapes)
     for (int spp : {1, 2, 4})
-      for (int gather : {0, 1, 2}) {
+      for (int gather : {2}) {
         if (!simt_fits || gp.NB * spp > 256) continue;
         gt.spp = spp;
         gt.gather = gather;
@@ -237,7 +240,9 @@ int tune_patch_shape(gamblet_ctx* h, int k, PatchPcgGeom& gp, T* Rhat, const Pat
   return 0;
 }
 
-// Galerkin kernel of level k (k_galerkin_rows, k_galerkin_warp or
+// Galerkin kernel of level k (the tile kernel over pairs of targets with 4, 8
+// or 16 lanes per pair at 256 or 128 threads per CTA, or, where a tile's
+// window does not fit shared memory, k_galerkin_rows, k_galerkin_warp or
 // k_galerkin_warprow), timed on kTuneSampleRows rows in the middle of the
 // level (rewritten by the full launch).
 template <typename T>
@@ -254,10 +259,14 @@ void tune_galerkin_variant(gamblet_ctx* h, int k, GalerkinGeom& gg, const T* Aha
     gt.i_begin = (gg.nrow / 2 / kTuneSampleRows) * kTuneSampleRows;
     gt.i_end = std::min(gt.i_begin + kTuneSampleRows, gg.nrow);
     float best = 1e30f;
-    for (int cand : {0, 1, 2, 3, 4, 5, 6, 7, 8})
+    // where the tile fits: the pair-of-targets tile kernels (6, 7, 8), which
+    // beat the single-target ones (3, 4, 5) and the row kernels (0, 1, 2) on
+    // every level measured, at 256 and 128 threads; else the row kernels
+    const bool tile = galerkin_tile_smem_bytes(gg, sizeof(T)) <= 227 * 1024;
+    for (int cand : {0, 1, 2, 6, 7, 8})
       for (int half : {0, 1}) {
+        if (tile != (cand >= 3)) continue;
         if (cand == 2 && 8 * sizeof(T) * 4 * ((size_t)gg.NB + gg.nwin) > 227 * 1024) continue;
-        if (cand >= 3 && galerkin_tile_smem_bytes(gg, sizeof(T)) > 227 * 1024) continue;
         if (half && cand < 3) continue;
         gt.variant = cand;
         gt.tile_threads = half ? 128 : 256;
