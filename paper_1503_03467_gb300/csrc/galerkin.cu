@@ -158,11 +158,12 @@ __global__ void __launch_bounds__(256) k_galerkin_rows(const T* __restrict__ Aha
 }
 
 // Four coarse rows per CTA: the 2 x 2 cells i0..i0+3 of one level-(k-2)
-// parent (row r at (r & 1, r >> 1) from the tile origin).  Phase 1: a thread
-// per position u of the tile's window box that phase 2 reads (host list
-// t1_order) loads each block Ahat[o][origin+u] once and applies it to every
-// row whose patch reaches it (host list t1: the neighbour index j of each
-// row), accumulating t_r(u) for the four rows.
+// parent (row r at (r & 1, r >> 1) from the tile origin).  Phase 1: for each
+// position u of the tile's window box that phase 2 reads, a thread walks u's
+// block list (host list t1; positions in t1_items): each block
+// Ahat[o][origin+u] is loaded once and applied to every row whose patch
+// reaches it (the neighbour index j of each row), accumulating t_r(u) for
+// the four rows.
 // Phase 2: a warp per output target cell c loads the row Rhat_c once (lanes
 // over j) and forms the dot products with t_r(c + N_j) of every row r for
 // which c - r is an output offset (host list t2).  Compared with a row per
@@ -190,8 +191,12 @@ __device__ __forceinline__ void galerkin_tile_pairs(const GalerkinGeom& g, const
   const int sub = lane & (LPT - 1), grp = lane / LPT;
   const int NB = g.NB;
   const int64_t nrow = g.nrow;
-  for (int e0 = TPW * warp; e0 < g.nt3; e0 += TPW * nwarp) {
-    const int e = e0 + grp;
+  // pairs by decreasing length, dealt to the warps in alternating direction
+  // so that no warp takes the longest lists of every round
+  const int per_round = TPW * nwarp;
+  for (int round = 0; round * per_round < g.nt3; ++round) {
+    const int slot = TPW * warp + grp;
+    const int e = round * per_round + ((round & 1) ? per_round - 1 - slot : slot);
     const bool ok = e < g.nt3;
     const int4 ta = ok ? g.t3[2 * e] : make_int4(0, 0, -1, -1);
     const int4 tb = ok ? g.t3[2 * e + 1] : make_int4(0, 0, -1, -1);
@@ -288,10 +293,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_galerkin_tile(c
     }
     __syncthreads();
     // phase 1: t_r(u) = sum over stored blocks of the window, for the
-    // positions that phase 2 reads (longest block lists first)
-    for (int iu = threadIdx.x; iu < g.nt1u; iu += blockDim.x) {
-      const int ucid = __ldg(g.t1_order + iu);
-      const int u = ucid & 0xffff, cu = ucid >> 16;
+    // positions that phase 2 reads (longest lists first, dealt in
+    // alternating direction so that the threads' totals even out)
+    const int nthr = blockDim.x;
+    for (int round = 0; round * nthr < g.nitems; ++round) {
+      const int iw = round * nthr + ((round & 1) ? nthr - 1 - (int)threadIdx.x : (int)threadIdx.x);
+      if (iw >= g.nitems) continue;
+      const int4 item = __ldg(g.t1_items + iw);
+      const int u = item.x & 0xffff, cu = item.x >> 16;
       const int uy = u / W, ux = u - uy * W;
       const int p = shift_cell(x0, y0, ux + wmin, uy + wmin, g.Lpar, nrow);
       T acc[4][4];
@@ -300,8 +309,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_galerkin_tile(c
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = T(0);
       if (p >= 0) {
-        const int e1 = g.t1_ptr[u + 1];
-        for (int e = g.t1_ptr[u]; e < e1; ++e) {
+        for (int e = item.y; e < item.z; ++e) {
           const int2 ent = g.t1[e];
           const T* blk = Ahat + ((int64_t)ent.x * nrow + p) * 16;
           T b[16];

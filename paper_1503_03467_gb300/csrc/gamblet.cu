@@ -314,8 +314,9 @@ void setup_local(gamblet_ctx* h) {
     gg.tile_W = S.tile_W;
     gg.t1_ptr = plan_table<int>(dplan, pl, PlanLevel::kT1Ptr);
     gg.t1 = plan_table<int2>(dplan, pl, PlanLevel::kT1);
-    gg.nt1u = (int)S.t1_order.size();
-    gg.t1_order = plan_table<int>(dplan, pl, PlanLevel::kT1Order);
+    gg.nt1u = S.n_read;
+    gg.nitems = (int)S.t1_items.size();
+    gg.t1_items = plan_table<int4>(dplan, pl, PlanLevel::kT1Order);
     gg.nt2 = (int)S.t2.size();
     gg.t2 = plan_table<int4>(dplan, pl, PlanLevel::kT2);
     gg.t2p_ptr = plan_table<int>(dplan, pl, PlanLevel::kT2pPtr);

@@ -224,8 +224,9 @@ struct SymLevel {
   int tile_wmin = 0, tile_W = 0;
   std::vector<int> t1_ptr;
   std::vector<int2> t1;           // (o, j of rows 0..3 packed in bytes)
-  std::vector<int> t1_order;      // the window positions phase 2 reads, by decreasing list
-                                  // length: u | cid << 16 (cid: index among them in box order)
+  int n_read = 0;                 // window positions phase 2 reads (cid: their index in box order)
+  std::vector<int4> t1_items;     // phase-1 work items (u | cid << 16, list begin, end, 0), by
+                                  // decreasing length
   std::vector<int4> t2;           // (c.x, c.y, d0 | d1 << 16, d2 | d3 << 16)
   // per target e, the pairs (j, u) whose window position u = c + N_j lies in
   // the window of some row of the tile (packed j | cid(u) << 8, ranges t2p_ptr);

@@ -269,8 +269,9 @@ struct GalerkinGeom {
   int tile_threads;      // tiles: threads per CTA (256, or 128 for more CTAs per SM)
   const int* t1_ptr;     // W * W + 1
   const int2* t1;        // (o, j per row packed in bytes, 0xff = none)
-  int nt1u;              // window positions read by phase 2 ...
-  const int* t1_order;   // ... in order of decreasing list length (u | cid << 16)
+  int nt1u;              // window positions read by phase 2 (cid < nt1u)
+  int nitems;            // phase-1 work items: (u | cid << 16, t1 begin, t1 end, 0), one
+  const int4* t1_items;  // per read position, by decreasing length
   int nt2;
   const int4* t2;        // (c.x, c.y, d0 | d1 << 16, d2 | d3 << 16), d = -1: none
   const int* t2p_ptr;    // nt2 + 1

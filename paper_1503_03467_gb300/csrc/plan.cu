@@ -204,12 +204,16 @@ SymLevel build_sym(const OffSet& O_k, const OffSet& N, int k) {
   // the positions phase 2 reads, by decreasing block count: the threads of a
   // CTA take them round-robin, so the lanes of a warp walk lists of about
   // the same length and the threads' totals differ by at most one list
+  // phase-1 work items: the read positions with their block lists, sorted by
+  // decreasing length; the kernel deals them to its threads in alternating
+  // direction, so that the threads' totals even out
   for (int u = 0; u < W * W; ++u)
-    if (read[u]) S.t1_order.push_back(u);
-  std::stable_sort(S.t1_order.begin(), S.t1_order.end(), [&S](int a, int b) {
-    return S.t1_ptr[a + 1] - S.t1_ptr[a] > S.t1_ptr[b + 1] - S.t1_ptr[b];
+    if (read[u])
+      S.t1_items.push_back(make_int4(u | (cid[u] << 16), S.t1_ptr[u], S.t1_ptr[u + 1], 0));
+  std::stable_sort(S.t1_items.begin(), S.t1_items.end(), [](const int4& a, const int4& b) {
+    return a.z - a.y > b.z - b.y;
   });
-  for (int& u : S.t1_order) u |= cid[u] << 16;  // (u, cid) packed
+  S.n_read = ncid;
   return S;
 }
 
@@ -436,7 +440,7 @@ std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
     pl.table_off[PlanLevel::kT2] = put_v(S.t2);
     pl.table_off[PlanLevel::kT2pPtr] = put_v(S.t2p_ptr);
     pl.table_off[PlanLevel::kT2p] = put_v(S.t2p);
-    pl.table_off[PlanLevel::kT1Order] = put_v(S.t1_order);
+    pl.table_off[PlanLevel::kT1Order] = put_v(S.t1_items);
     pl.table_off[PlanLevel::kT3] = put_v(S.t3);
     pl.table_off[PlanLevel::kT3pPtr] = put_v(S.t3p_ptr);
     pl.table_off[PlanLevel::kT3p] = put_v(S.t3p);
