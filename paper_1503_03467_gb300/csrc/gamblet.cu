@@ -394,14 +394,21 @@ void setup_local(gamblet_ctx* h) {
     L.Dinv = Dinv;
     L.Bq = nullptr;
     L.bq_scale = nullptr;
-    if (is_f32<T>() && h->opts.level_tol >= kHalfLevelTol) {
+    L.nhoff = 0;
+    L.hoff = nullptr;
+    const PlanLevel& pl = h->plan->lv[k];
+    if (is_f32<T>() && h->opts.level_tol >= kHalfLevelTol && !pl.hidx.empty()) {
       // the level CG's product reads each block as one 32-byte float16 record
       // (two 16-byte loads instead of nine scalar ones), with a rounding of
-      // 2^-11 relative per entry, far below the level tolerance
-      L.Bq = P.alloc<uint4>((int64_t)L.noff * L.npar * 2);
+      // 2^-11 relative per entry, far below the level tolerance; B^(k) is
+      // symmetric, so only the blocks of the half-plane offsets are stored
+      L.nhoff = (int)pl.hidx.size();
+      L.hoff = plan_table<int2>(h->dplan, pl, PlanLevel::kHOff);
+      L.Bq = P.alloc<uint4>((int64_t)L.nhoff * L.npar * 2);
       L.bq_scale = P.alloc<float>(1);
-      launch_cg_block_records((const float*)L.Ahat, (const float*)Bd, L.noff, L.npar, L.Bq,
-                              L.bq_scale, P.alloc<unsigned>(1), s);
+      launch_cg_block_records((const float*)L.Ahat, (const float*)Bd, L.noff,
+                              plan_table<int>(h->dplan, pl, PlanLevel::kHIdx), L.nhoff, L.npar,
+                              L.Bq, L.bq_scale, P.alloc<unsigned>(1), s);
     }
   }
   CK(cudaGetLastError());
@@ -518,6 +525,8 @@ void alloc_solve(gamblet_ctx* h) {
       c.Dinv = L.Dinv;
       c.off = L.off;
       c.noff = L.noff;
+      c.hoff = L.hoff;
+      c.nhoff = L.nhoff;
       c.R = L.R;
       c.Lpar = 1 << (k - 1);
       c.npar = L.npar;

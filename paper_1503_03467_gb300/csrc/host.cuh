@@ -279,8 +279,11 @@ struct LevelDev {
   double* wc = nullptr;  // compact detail vector (exact path)
   // level CG operator (localized path)
   void* Bd = nullptr;    // [noff][9][npar]
-  void* Bq = nullptr;    // 32-byte float16 block records of the level CG (mixed path), or NULL
+  void* Bq = nullptr;    // 32-byte float16 block records of the level CG (mixed path), or NULL:
+                         // one per offset d of the half-plane H of O_k and parent p
   float* bq_scale = nullptr;  // device: inverse scale of Bq
+  int nhoff = 0;         // |H|
+  const int2* hoff = nullptr;  // device: the offsets of H
   void* Dinv = nullptr;  // [9][npar]
   int R = 0;             // halo radius
   int o0 = -1;           // index of the zero offset in O_k (diagonal blocks)
@@ -495,10 +498,14 @@ struct PlanLevel {
   double flops_iter = 0;
   std::vector<int> map_next;          // block conversion map (or the level-1 map)
   OffSet O_next;
+  // the half-plane H of O_k (d.y > 0, or d.y = 0 and d.x >= 0): indices into
+  // O_k and the offsets (empty if O_k is not symmetric)
+  std::vector<int> hidx;
+  std::vector<int2> hoff;
   // byte offsets of this level's tables in Plan::packed
   enum { kPairIdx, kHalf, kAdjPtr, kAdj, kDiagH, kWin, kL1Ptr, kL1Pairs, kOut, kL2Ptr, kL2Pairs,
          kT1Ptr, kT1, kT2, kT2pPtr, kT2p, kT1Order, kT3, kT3pPtr, kT3p, kOffNext, kMapNext,
-         kNumTables };
+         kHIdx, kHOff, kNumTables };
   size_t table_off[kNumTables] = {};
 };
 struct Plan {

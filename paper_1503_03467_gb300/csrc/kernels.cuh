@@ -325,13 +325,18 @@ void launch_prolong(const T* RT, int NB, const int2* nbr, int Lpar, int64_t npar
 // (levelcg.cu).
 struct CgLevel {
   const void* Bd;     // detail blocks, SoA [noff][9][npar] (T)
-  const void* Bq;     // or NULL: the same blocks as 32-byte float16 records
-                      // [noff][npar][16] (entries 0..8, the rest zero), scaled
-                      // by a power of two
+  const void* Bq;     // or NULL: the blocks of the offsets d of the half-plane
+                      // H of O_k (d.y > 0, or d.y = 0 and d.x >= 0) as 32-byte
+                      // float16 records [nhoff][npar][16] (entries 0..8, the
+                      // rest zero), scaled by a power of two; B^(k) is
+                      // symmetric, so the block of -d at p is the transpose
+                      // of the block of d at p - d
   const float* bq_inv_scale;  // device: the inverse of that scale (with Bq)
   const void* Dinv;   // inverse diagonal detail blocks [9][npar] (T)
   const int2* off;
   int noff;
+  const int2* hoff;   // with Bq: the offsets of H
+  int nhoff;
   int R;              // largest |offset component| (halo radius)
   int Lpar;
   int64_t npar;
@@ -351,12 +356,14 @@ struct CgScalars {
   int active, iters;
 };
 size_t cg_spmv_smem_bytes(int max_ts, size_t elem);
-// Bq[o][p][0..8] = float16(Ahat[o][p] detail block * 2^s), entries 9..15
-// zero, with 2^s chosen from the largest |entry| of the level's detail blocks
-// (Bd, noff * 9 * npar values) so that it lies in [2^14, 2^15);
-// *inv_scale = 2^-s.  amax: one device word of scratch.
-void launch_cg_block_records(const float* Ahat, const float* Bd, int noff, int64_t npar,
-                             void* Bq, float* inv_scale, unsigned* amax, cudaStream_t s);
+// Bq[h][p][0..8] = float16(Ahat[hidx[h]][p] detail block * 2^s), entries
+// 9..15 zero, for the nh offsets hidx of the half-plane; 2^s is chosen from
+// the largest |entry| of the level's detail blocks (Bd, noff * 9 * npar
+// values) so that it lies in [2^14, 2^15); *inv_scale = 2^-s.  amax: one
+// device word of scratch.
+void launch_cg_block_records(const float* Ahat, const float* Bd, int noff, const int* hidx,
+                             int nh, int64_t npar, void* Bq, float* inv_scale, unsigned* amax,
+                             cudaStream_t s);
 // Side of the square parent tile of one level-CG SpMV CTA (256 threads):
 // 16 with one thread per parent, 8 with four, 4 with sixteen (wide stencils:
 // more CTAs per level and more lanes splitting the offsets).

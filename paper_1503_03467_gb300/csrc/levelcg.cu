@@ -174,7 +174,7 @@ __device__ __forceinline__ void unpack9(const uint4& u0, const uint4& u1, T* b) 
 // T x T parents (T = 16, or 8 with four threads per parent splitting the
 // offsets when the stencil is wide; or the whole lattice when smaller).
 template <typename T>
-__global__ void __launch_bounds__(256) k_cg_spmv(const CgLevel* __restrict__ lv, int nlev,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 0) k_cg_spmv(const CgLevel* __restrict__ lv, int nlev,
                                                  CgScalars* sc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[8];
@@ -219,30 +219,31 @@ __global__ void __launch_bounds__(256) k_cg_spmv(const CgLevel* __restrict__ lv,
     ly = py - y0 + R;
     const int64_t np = L.npar;
     if (L.Bq) {
-      // 32-byte float16 records: two 16-byte loads per block
+      // 32-byte float16 records of the half-plane offsets (two 16-byte loads
+      // per block): the record of d at p gives B(p, p + d), the record of d
+      // at p - d gives B(p, p - d) as its transpose, so each stored block is
+      // read from DRAM once per product and serves both of its rows
       const uint4* Bq = reinterpret_cast<const uint4*>(L.Bq);
-      for (int o = sub; o < L.noff; o += 2 * spp) {
-        const int o2 = o + spp;
-        const bool two = o2 < L.noff;
-        const int2 d = L.off[o];
-        const int2 d2 = L.off[two ? o2 : o];
-        const uint4 u0 = __ldg(Bq + ((int64_t)o * np + p) * 2);
-        const uint4 u1 = __ldg(Bq + ((int64_t)o * np + p) * 2 + 1);
+      for (int hh = sub; hh < L.nhoff; hh += spp) {
+        const int2 d = L.hoff[hh];
+        const int qn = (d.x | d.y) ? shift_cell(px, py, -d.x, -d.y, L.Lpar, np) : -1;
+        const uint4 u0 = __ldg(Bq + ((int64_t)hh * np + p) * 2);
+        const uint4 u1 = __ldg(Bq + ((int64_t)hh * np + p) * 2 + 1);
         uint4 w0 = make_uint4(0, 0, 0, 0), w1 = make_uint4(0, 0, 0, 0);
-        if (two) {
-          w0 = __ldg(Bq + ((int64_t)o2 * np + p) * 2);
-          w1 = __ldg(Bq + ((int64_t)o2 * np + p) * 2 + 1);
+        if (qn >= 0) {
+          w0 = __ldg(Bq + ((int64_t)hh * np + qn) * 2);
+          w1 = __ldg(Bq + ((int64_t)hh * np + qn) * 2 + 1);
         }
         T b[9], b2[9];
         unpack9<T>(u0, u1, b);
         unpack9<T>(w0, w1, b2);
         const int c = (ly + d.y) * TS + lx + d.x;
-        const int c2 = (ly + d2.y) * TS + lx + d2.x;
+        const int c2 = (ly - d.y) * TS + lx - d.x;
         const T a0 = xs[c], a1 = xs[TS * TS + c], a2 = xs[2 * TS * TS + c];
         const T e0 = xs[c2], e1 = xs[TS * TS + c2], e2 = xs[2 * TS * TS + c2];
-        y0v += b[0] * a0 + b[1] * a1 + b[2] * a2 + b2[0] * e0 + b2[1] * e1 + b2[2] * e2;
-        y1v += b[3] * a0 + b[4] * a1 + b[5] * a2 + b2[3] * e0 + b2[4] * e1 + b2[5] * e2;
-        y2v += b[6] * a0 + b[7] * a1 + b[8] * a2 + b2[6] * e0 + b2[7] * e1 + b2[8] * e2;
+        y0v += b[0] * a0 + b[1] * a1 + b[2] * a2 + b2[0] * e0 + b2[3] * e1 + b2[6] * e2;
+        y1v += b[3] * a0 + b[4] * a1 + b[5] * a2 + b2[1] * e0 + b2[4] * e1 + b2[7] * e2;
+        y2v += b[6] * a0 + b[7] * a1 + b[8] * a2 + b2[2] * e0 + b2[5] * e1 + b2[8] * e2;
       }
       const T si = (T)*L.bq_inv_scale;  // a power of two: exact
       y0v *= si;
@@ -564,9 +565,11 @@ __global__ void k_absmax(const float* __restrict__ x, int64_t n, unsigned* amax)
   if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(amax, __float_as_uint(m));
 }
 
-// One thread per block (o, p): its 3x3 detail block as one 32-byte record.
-__global__ void k_block_records(const float* __restrict__ Ahat, int noff, int64_t npar,
-                                const unsigned* __restrict__ amax, uint4* Bq, float* inv_scale) {
+// One thread per block (h, p): the 3x3 detail block of offset hidx[h] at
+// parent p as one 32-byte record.
+__global__ void k_block_records(const float* __restrict__ Ahat, const int* __restrict__ hidx,
+                                int nh, int64_t npar, const unsigned* __restrict__ amax, uint4* Bq,
+                                float* inv_scale) {
   const float m = __uint_as_float(*amax);
   // 2^e <= m < 2^(e+1); the scale 2^(14 - e) puts the largest entry in [2^14, 2^15)
   const int e = m > 0.f ? ((__float_as_int(m) >> 23) & 255) - 127 : 0;
@@ -574,8 +577,9 @@ __global__ void k_block_records(const float* __restrict__ Ahat, int noff, int64_
   const float sc = ldexpf(1.f, a);
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t == 0) *inv_scale = ldexpf(1.f, -a);
-  if (t >= (int64_t)noff * npar) return;
-  const float* A = Ahat + t * 16;
+  if (t >= (int64_t)nh * npar) return;
+  const int64_t hh = t / npar;
+  const float* A = Ahat + ((int64_t)hidx[hh] * npar + (t - hh * npar)) * 16;
   float v[16];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
@@ -594,19 +598,21 @@ __global__ void k_block_records(const float* __restrict__ Ahat, int noff, int64_
   Bq[2 * t + 1] = w[1];
 }
 
-void launch_cg_block_records(const float* Ahat, const float* Bd, int noff, int64_t npar,
-                             void* Bq, float* inv_scale, unsigned* amax, cudaStream_t s) {
+void launch_cg_block_records(const float* Ahat, const float* Bd, int noff, const int* hidx,
+                             int nh, int64_t npar, void* Bq, float* inv_scale, unsigned* amax,
+                             cudaStream_t s) {
   const int64_t n = (int64_t)noff * npar;
-  if (n <= 0) return;
+  if (n <= 0 || nh <= 0) return;
   cudaMemsetAsync(amax, 0, sizeof(unsigned), s);
   const int64_t nv = 9 * n;
   const int64_t want = (nv + 255) / 256;
   count_launch();
   k_absmax<<<(unsigned)(want < 4096 ? want : 4096), 256, 0, s>>>(Bd, nv, amax);
+  const int64_t nr = (int64_t)nh * npar;
   count_launch();
-  k_block_records<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ahat, noff, npar, amax,
-                                                              reinterpret_cast<uint4*>(Bq),
-                                                              inv_scale);
+  k_block_records<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(Ahat, hidx, nh, npar, amax,
+                                                               reinterpret_cast<uint4*>(Bq),
+                                                               inv_scale);
 }
 template void launch_cg_level_setup<double>(const double*, int, int, int64_t, const uint32_t*,
                                             double*, double*, cudaStream_t);
@@ -775,27 +781,54 @@ __global__ void __launch_bounds__(256) k_cgm_spmv(const CgLevel* __restrict__ lv
     const T* Bd = (const T*)L.Bd;
     const uint4* Bq = reinterpret_cast<const uint4*>(L.Bq);
     const int64_t np = L.npar;
-    for (int o = sub; o < L.noff; o += spp) {
-      const int2 d = L.off[o];
-      const int c = (ly + d.y) * TS + lx + d.x;
-      T b[9];
-      if (Bq) {  // the block records of the single-right-hand-side CG
-        const uint4 u0 = __ldg(Bq + ((int64_t)o * np + p) * 2);
-        const uint4 u1 = __ldg(Bq + ((int64_t)o * np + p) * 2 + 1);
-        unpack9<T>(u0, u1, b);
-      } else {
+    if (Bq) {
+      // the half-plane block records of the single-right-hand-side CG: the
+      // record of d at p and, transposed, the record of d at p - d
+      for (int hh = sub; hh < L.nhoff; hh += spp) {
+        const int2 d = L.hoff[hh];
+        const int qn = (d.x | d.y) ? shift_cell(px, py, -d.x, -d.y, L.Lpar, np) : -1;
+        const int c = (ly + d.y) * TS + lx + d.x;
+        const int c2 = (ly - d.y) * TS + lx - d.x;
+        T b[9], bt[9];
+        unpack9<T>(__ldg(Bq + ((int64_t)hh * np + p) * 2),
+                   __ldg(Bq + ((int64_t)hh * np + p) * 2 + 1), b);
+        if (qn >= 0) {
+          unpack9<T>(__ldg(Bq + ((int64_t)hh * np + qn) * 2),
+                     __ldg(Bq + ((int64_t)hh * np + qn) * 2 + 1), bt);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 9; ++e) bt[e] = T(0);
+        }
+#pragma unroll
+        for (int r = 0; r < kMaxRhs; ++r) {
+          if (r < nrhs) {
+            const T a0 = xs[(r * 3) * plane + c], a1 = xs[(r * 3 + 1) * plane + c],
+                    a2 = xs[(r * 3 + 2) * plane + c];
+            const T e0 = xs[(r * 3) * plane + c2], e1 = xs[(r * 3 + 1) * plane + c2],
+                    e2 = xs[(r * 3 + 2) * plane + c2];
+            yv[r][0] += b[0] * a0 + b[1] * a1 + b[2] * a2 + bt[0] * e0 + bt[3] * e1 + bt[6] * e2;
+            yv[r][1] += b[3] * a0 + b[4] * a1 + b[5] * a2 + bt[1] * e0 + bt[4] * e1 + bt[7] * e2;
+            yv[r][2] += b[6] * a0 + b[7] * a1 + b[8] * a2 + bt[2] * e0 + bt[5] * e1 + bt[8] * e2;
+          }
+        }
+      }
+    } else {
+      for (int o = sub; o < L.noff; o += spp) {
+        const int2 d = L.off[o];
+        const int c = (ly + d.y) * TS + lx + d.x;
+        T b[9];
         const T* B = Bd + (int64_t)o * 9 * np + p;
 #pragma unroll
         for (int e = 0; e < 9; ++e) b[e] = B[e * np];
-      }
 #pragma unroll
-      for (int r = 0; r < kMaxRhs; ++r) {
-        if (r < nrhs) {
-          const T a0 = xs[(r * 3) * plane + c], a1 = xs[(r * 3 + 1) * plane + c],
-                  a2 = xs[(r * 3 + 2) * plane + c];
-          yv[r][0] += b[0] * a0 + b[1] * a1 + b[2] * a2;
-          yv[r][1] += b[3] * a0 + b[4] * a1 + b[5] * a2;
-          yv[r][2] += b[6] * a0 + b[7] * a1 + b[8] * a2;
+        for (int r = 0; r < kMaxRhs; ++r) {
+          if (r < nrhs) {
+            const T a0 = xs[(r * 3) * plane + c], a1 = xs[(r * 3 + 1) * plane + c],
+                    a2 = xs[(r * 3 + 2) * plane + c];
+            yv[r][0] += b[0] * a0 + b[1] * a1 + b[2] * a2;
+            yv[r][1] += b[3] * a0 + b[4] * a1 + b[5] * a2;
+            yv[r][2] += b[6] * a0 + b[7] * a1 + b[8] * a2;
+          }
         }
       }
     }

@@ -398,6 +398,17 @@ std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
       pl.adj.insert(pl.adj.end(), rows[j].begin(), rows[j].end());
     }
     const double row_len = (double)pl.adj.size() / NB;
+    // half-plane of the symmetric block stencil (the level CG stores one
+    // block per pair of opposite offsets)
+    bool sym = true;
+    for (const int2& d : pl.S.O.v) sym = sym && pl.S.O.find(-d.x, -d.y) >= 0;
+    for (int o = 0; o < pl.S.O.size() && sym; ++o) {
+      const int2 d = pl.S.O.v[o];
+      if (d.y > 0 || (d.y == 0 && d.x >= 0)) {
+        pl.hidx.push_back(o);
+        pl.hoff.push_back(d);
+      }
+    }
     pl.spp = row_len > 24 ? 4 : (row_len > 12 ? 2 : 1);
     while (pl.spp > 1 && NB * pl.spp > 256) pl.spp >>= 1;
     pl.flops_iter = 18.0 * (2.0 * pl.half.size() - NB) + 60.0 * NB;
@@ -446,6 +457,8 @@ std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
     pl.table_off[PlanLevel::kT3p] = put_v(S.t3p);
     pl.table_off[PlanLevel::kOffNext] = put_v(pl.O_next.v);
     pl.table_off[PlanLevel::kMapNext] = put_v(pl.map_next);
+    pl.table_off[PlanLevel::kHIdx] = put_v(pl.hidx);
+    pl.table_off[PlanLevel::kHOff] = put_v(pl.hoff);
     for (MmaWin& W : pl.mwin) {
       W.off[0] = put_v(W.U);
       W.off[1] = put_v(W.ubits);

@@ -239,7 +239,8 @@ void cg_work_per_iteration(gamblet_ctx* h) {
     // (3 active slots); vector kernels: x, r, z, p, Ap, Dinv
     const LevelDev& L = h->lv[l + 2];
     const double sz = (double)sizeof(T);
-    h->cg_bytes_spmv[l] = (L.Bq ? 32.0 : 9.0 * sz) * ((double)L.noff * L.npar) + sz * 6.0 * L.npar;
+    h->cg_bytes_spmv[l] = (L.Bq ? 32.0 * L.nhoff : 9.0 * sz * L.noff) * (double)L.npar +
+                          sz * 6.0 * L.npar;
     h->cg_flops_spmv[l] = 2.0 * 9.0 * L.noff * L.npar;
     h->cg_bytes_vec[l] = sz * 3.0 * L.npar * 12;
     h->cg_flops_vec[l] = 3.0 * L.npar * 12;
