@@ -389,15 +389,17 @@ void setup_local(gamblet_ctx* h) {
     L.R = R;
     T* Bd = P.alloc<T>((int64_t)L.noff * 9 * L.npar);
     T* Dinv = P.alloc<T>(9 * L.npar);
-    launch_cg_level_setup<T>((const T*)L.Ahat, L.noff, o0, L.npar, L.pmask, Bd, Dinv, s);
+    const PlanLevel& pl = h->plan->lv[k];
+    const bool records = is_f32<T>() && h->opts.level_tol >= kHalfLevelTol && !pl.hidx.empty();
+    unsigned* amax = records ? P.alloc<unsigned>(1) : nullptr;
+    launch_cg_level_setup<T>((const T*)L.Ahat, L.noff, o0, L.npar, L.pmask, Bd, Dinv, amax, s);
     L.Bd = Bd;
     L.Dinv = Dinv;
     L.Bq = nullptr;
     L.bq_scale = nullptr;
     L.nhoff = 0;
     L.hoff = nullptr;
-    const PlanLevel& pl = h->plan->lv[k];
-    if (is_f32<T>() && h->opts.level_tol >= kHalfLevelTol && !pl.hidx.empty()) {
+    if (records) {
       // the level CG's product reads each block as one 32-byte float16 record
       // (two 16-byte loads instead of nine scalar ones), with a rounding of
       // 2^-11 relative per entry, far below the level tolerance; B^(k) is
@@ -406,9 +408,8 @@ void setup_local(gamblet_ctx* h) {
       L.hoff = plan_table<int2>(h->dplan, pl, PlanLevel::kHOff);
       L.Bq = P.alloc<uint4>((int64_t)L.nhoff * L.npar * 2);
       L.bq_scale = P.alloc<float>(1);
-      launch_cg_block_records((const float*)L.Ahat, (const float*)Bd, L.noff,
-                              plan_table<int>(h->dplan, pl, PlanLevel::kHIdx), L.nhoff, L.npar,
-                              L.Bq, L.bq_scale, P.alloc<unsigned>(1), s);
+      launch_cg_block_records((const float*)L.Ahat, plan_table<int>(h->dplan, pl, PlanLevel::kHIdx),
+                              L.nhoff, L.npar, amax, L.Bq, L.bq_scale, s);
     }
   }
   CK(cudaGetLastError());

@@ -357,13 +357,12 @@ struct CgScalars {
 };
 size_t cg_spmv_smem_bytes(int max_ts, size_t elem);
 // Bq[h][p][0..8] = float16(Ahat[hidx[h]][p] detail block * 2^s), entries
-// 9..15 zero, for the nh offsets hidx of the half-plane; 2^s is chosen from
-// the largest |entry| of the level's detail blocks (Bd, noff * 9 * npar
-// values) so that it lies in [2^14, 2^15); *inv_scale = 2^-s.  amax: one
-// device word of scratch.
-void launch_cg_block_records(const float* Ahat, const float* Bd, int noff, const int* hidx,
-                             int nh, int64_t npar, void* Bq, float* inv_scale, unsigned* amax,
-                             cudaStream_t s);
+// 9..15 zero, for the nh offsets hidx of the half-plane; 2^s puts the
+// largest |entry| of the level's detail blocks, *amax (the bits of the
+// largest diagonal entry, from launch_cg_level_setup), in [2^14, 2^15);
+// *inv_scale = 2^-s.
+void launch_cg_block_records(const float* Ahat, const int* hidx, int nh, int64_t npar,
+                             const unsigned* amax, void* Bq, float* inv_scale, cudaStream_t s);
 // Side of the square parent tile of one level-CG SpMV CTA (256 threads):
 // 16 with one thread per parent, 8 with four, 4 with sixteen (wide stencils:
 // more CTAs per level and more lanes splitting the offsets).
@@ -394,10 +393,12 @@ void launch_cg_rest(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc
                     int max_iter, int* any_active, cudaStream_t s,
                     cudaGraphConditionalHandle cond = 0, int use_cond = 0,
                     int* loop_count = nullptr, int loop_limit = 0);
-// Coalesced detail-block copy and block-Jacobi inverses of one level.
+// Coalesced detail-block copy and block-Jacobi inverses of one level; with
+// amax (one device word, or NULL) also the bits of the level's largest
+// active diagonal entry, which bounds every entry of the SPD operator.
 template <typename T>
 void launch_cg_level_setup(const T* Ahat, int noff, int o0, int64_t npar, const uint32_t* pmask,
-                           T* Bd, T* Dinv, cudaStream_t s);
+                           T* Bd, T* Dinv, unsigned* amax, cudaStream_t s);
 
 // Outer float64 operations on transformed level-q vectors.
 // dots[i] += a_i . b_i for up to 3 pairs (nullptr pairs skipped).

@@ -491,10 +491,25 @@ __global__ void k_extract_detail(const T* __restrict__ Ahat, int noff, int64_t n
 // block (zeros outside it), in the working precision (a 3x3 SPD block; the
 // float64 pipe would make this kernel wait in the mixed path).  Fixed trip
 // counts with predicates keep every array in registers.
+// With amax, also the largest active diagonal entry of the level (atomicMax on
+// its bits): B^(k) is symmetric positive definite, so |B_ij| <=
+// sqrt(B_ii B_jj) and that entry bounds every entry of every block.
 template <typename T>
 __global__ void k_detail_dinv(const T* __restrict__ Ahat, int o0, int64_t npar,
-                              const uint32_t* __restrict__ pmask, T* Dinv) {
+                              const uint32_t* __restrict__ pmask, T* Dinv, unsigned* amax) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (amax) {  // warp-uniform: every lane reaches the shuffles
+    float dm = 0.f;
+    if (p < npar) {
+      const int mm = __popc(pmask[p] & 15u);
+      const int nn = mm > 0 ? mm - 1 : 0;
+      const T* A = Ahat + ((int64_t)o0 * npar + p) * 16;
+      for (int a = 0; a < nn; ++a) dm = fmaxf(dm, fabsf((float)A[5 * a]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    if ((threadIdx.x & 31) == 0 && dm > 0.f) atomicMax(amax, __float_as_uint(dm));
+  }
   if (p >= npar) return;
   const int m = __popc(pmask[p] & 15u);
   const int na = m > 0 ? m - 1 : 0;
@@ -540,30 +555,21 @@ __global__ void k_detail_dinv(const T* __restrict__ Ahat, int o0, int64_t npar,
 
 template <typename T>
 void launch_cg_level_setup(const T* Ahat, int noff, int o0, int64_t npar, const uint32_t* pmask,
-                           T* Bd, T* Dinv, cudaStream_t s) {
+                           T* Bd, T* Dinv, unsigned* amax, cudaStream_t s) {
   const int64_t n = (int64_t)noff * npar;
   if (n > 0) {
     count_launch();
     k_extract_detail<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ahat, noff, npar, Bd);
   }
+  if (amax) cudaMemsetAsync(amax, 0, sizeof(unsigned), s);
   if (npar > 0) {
     count_launch();
-    k_detail_dinv<T><<<(unsigned)((npar + 255) / 256), 256, 0, s>>>(Ahat, o0, npar, pmask, Dinv);
+    k_detail_dinv<T><<<(unsigned)((npar + 255) / 256), 256, 0, s>>>(Ahat, o0, npar, pmask, Dinv,
+                                                                   amax);
   }
 }
 template void launch_cg_level_setup<float>(const float*, int, int, int64_t, const uint32_t*,
-                                           float*, float*, cudaStream_t);
-
-// Largest |x| of a float array (non-negative floats order like their bits).
-__global__ void k_absmax(const float* __restrict__ x, int64_t n, unsigned* amax) {
-  float m = 0.f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    m = fmaxf(m, fabsf(x[i]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(amax, __float_as_uint(m));
-}
+                                           float*, float*, unsigned*, cudaStream_t);
 
 // One thread per block (h, p): the 3x3 detail block of offset hidx[h] at
 // parent p as one 32-byte record.
@@ -598,16 +604,9 @@ __global__ void k_block_records(const float* __restrict__ Ahat, const int* __res
   Bq[2 * t + 1] = w[1];
 }
 
-void launch_cg_block_records(const float* Ahat, const float* Bd, int noff, const int* hidx,
-                             int nh, int64_t npar, void* Bq, float* inv_scale, unsigned* amax,
-                             cudaStream_t s) {
-  const int64_t n = (int64_t)noff * npar;
-  if (n <= 0 || nh <= 0) return;
-  cudaMemsetAsync(amax, 0, sizeof(unsigned), s);
-  const int64_t nv = 9 * n;
-  const int64_t want = (nv + 255) / 256;
-  count_launch();
-  k_absmax<<<(unsigned)(want < 4096 ? want : 4096), 256, 0, s>>>(Bd, nv, amax);
+void launch_cg_block_records(const float* Ahat, const int* hidx, int nh, int64_t npar,
+                             const unsigned* amax, void* Bq, float* inv_scale, cudaStream_t s) {
+  if (nh <= 0 || npar <= 0) return;
   const int64_t nr = (int64_t)nh * npar;
   count_launch();
   k_block_records<<<(unsigned)((nr + 255) / 256), 256, 0, s>>>(Ahat, hidx, nh, npar, amax,
@@ -615,7 +614,7 @@ void launch_cg_block_records(const float* Ahat, const float* Bd, int noff, const
                                                                inv_scale);
 }
 template void launch_cg_level_setup<double>(const double*, int, int, int64_t, const uint32_t*,
-                                            double*, double*, cudaStream_t);
+                                            double*, double*, unsigned*, cudaStream_t);
 
 // ---------------------------------------------------------------- diagnostics
 // y = B^(k) x on the detail slots (thread per parent, float64 vectors): the
