@@ -387,10 +387,13 @@ void setup_local(gamblet_ctx* h) {
     if (o0 < 0) fail(GAMBLET_ERR_INVALID_ARG, "level operator has no diagonal blocks");
     L.o0 = o0;
     L.R = R;
-    T* Bd = P.alloc<T>((int64_t)L.noff * 9 * L.npar);
     T* Dinv = P.alloc<T>(9 * L.npar);
     const PlanLevel& pl = h->plan->lv[k];
     const bool records = is_f32<T>() && h->opts.level_tol >= kHalfLevelTol && !pl.hidx.empty();
+    // with the records the CG never reads the coalesced copy Bd; the
+    // diagnostics that do (compression, condition estimates) build it on
+    // first use (level_detail_blocks)
+    T* Bd = records ? nullptr : P.alloc<T>((int64_t)L.noff * 9 * L.npar);
     unsigned* amax = records ? P.alloc<unsigned>(1) : nullptr;
     launch_cg_level_setup<T>((const T*)L.Ahat, L.noff, o0, L.npar, L.pmask, Bd, Dinv, amax, s);
     L.Bd = Bd;

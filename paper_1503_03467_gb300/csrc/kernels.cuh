@@ -393,12 +393,16 @@ void launch_cg_rest(const CgLevel* lv, int nlev, int total_blocks, CgScalars* sc
                     int max_iter, int* any_active, cudaStream_t s,
                     cudaGraphConditionalHandle cond = 0, int use_cond = 0,
                     int* loop_count = nullptr, int loop_limit = 0);
-// Coalesced detail-block copy and block-Jacobi inverses of one level; with
-// amax (one device word, or NULL) also the bits of the level's largest
-// active diagonal entry, which bounds every entry of the SPD operator.
+// Coalesced detail-block copy (Bd, or NULL to skip it) and block-Jacobi
+// inverses of one level; with amax (one device word, or NULL) also the bits
+// of the level's largest active diagonal entry, which bounds every entry of
+// the SPD operator.
 template <typename T>
 void launch_cg_level_setup(const T* Ahat, int noff, int o0, int64_t npar, const uint32_t* pmask,
                            T* Bd, T* Dinv, unsigned* amax, cudaStream_t s);
+// Bd[o][3a+b][p] = detail block (a, b) of Ahat[o][p]: the coalesced copy alone.
+template <typename T>
+void launch_extract_detail(const T* Ahat, int noff, int64_t npar, T* Bd, cudaStream_t s);
 
 // Outer float64 operations on transformed level-q vectors.
 // dots[i] += a_i . b_i for up to 3 pairs (nullptr pairs skipped).

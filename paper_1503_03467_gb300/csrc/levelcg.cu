@@ -554,13 +554,20 @@ __global__ void k_detail_dinv(const T* __restrict__ Ahat, int o0, int64_t npar,
 }
 
 template <typename T>
-void launch_cg_level_setup(const T* Ahat, int noff, int o0, int64_t npar, const uint32_t* pmask,
-                           T* Bd, T* Dinv, unsigned* amax, cudaStream_t s) {
+void launch_extract_detail(const T* Ahat, int noff, int64_t npar, T* Bd, cudaStream_t s) {
   const int64_t n = (int64_t)noff * npar;
   if (n > 0) {
     count_launch();
     k_extract_detail<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Ahat, noff, npar, Bd);
   }
+}
+template void launch_extract_detail<float>(const float*, int, int64_t, float*, cudaStream_t);
+template void launch_extract_detail<double>(const double*, int, int64_t, double*, cudaStream_t);
+
+template <typename T>
+void launch_cg_level_setup(const T* Ahat, int noff, int o0, int64_t npar, const uint32_t* pmask,
+                           T* Bd, T* Dinv, unsigned* amax, cudaStream_t s) {
+  if (Bd) launch_extract_detail<T>(Ahat, noff, npar, Bd, s);
   if (amax) cudaMemsetAsync(amax, 0, sizeof(unsigned), s);
   if (npar > 0) {
     count_launch();

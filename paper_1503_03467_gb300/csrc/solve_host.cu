@@ -741,6 +741,20 @@ gamblet_status solve_many_impl(gamblet_ctx* h, int nrhs, const double* G, double
   return st;
 }
 
+// The coalesced detail blocks Bd of level k, built on first use where the
+// setup skipped them (the level CG of the mixed path reads its block records
+// instead); they live in the handle's pool until gamblet_destroy.
+template <typename T>
+const T* level_detail_blocks(gamblet_ctx* h, int k) {
+  LevelDev& L = h->lv[k];
+  if (!L.Bd) {
+    T* Bd = h->pool.alloc<T>((int64_t)L.noff * 9 * L.npar);
+    launch_extract_detail<T>((const T*)L.Ahat, L.noff, L.npar, Bd, h->s);
+    L.Bd = Bd;
+  }
+  return (const T*)L.Bd;
+}
+
 // Level-q initialisation by the mass matrix (Algorithm 2, lines 2a-5 with
 // Definition deflocinvm): M^-1,loc on patches of radius rho_q around every
 // node, A^(q),loc = (M^-1,loc)^T A M^-1,loc as a CSR, then the ordinary
@@ -770,7 +784,7 @@ void compress_impl(gamblet_ctx* h, const double* g_user, double eps, double* u_u
   unsigned long long* dv = tmp.zeros<unsigned long long>(2, s);  // max bits, kept
   for (int k = 2; k <= q; ++k) {
     LevelDev& L = h->lv[k];
-    launch_coef_max<T>((const T*)L.w, (const T*)L.Bd, L.o0, L.npar, L.pmask, dv, s);
+    launch_coef_max<T>((const T*)L.w, level_detail_blocks<T>(h, k), L.o0, L.npar, L.pmask, dv, s);
   }
   unsigned long long dh[2];
   CK(cudaMemcpyAsync(dh, dv, sizeof(dh), cudaMemcpyDeviceToHost, s));
@@ -798,7 +812,8 @@ void compress_impl(gamblet_ctx* h, const double* g_user, double eps, double* u_u
   CK(cudaMemcpyAsync(h->U1, U1, sizeof(T) * 4, cudaMemcpyHostToDevice, s));
   for (int k = 2; k <= q; ++k) {
     LevelDev& L = h->lv[k];
-    launch_coef_threshold<T>((T*)L.w, (const T*)L.Bd, L.o0, L.npar, L.pmask, thr, dv + 1, s);
+    launch_coef_threshold<T>((T*)L.w, level_detail_blocks<T>(h, k), L.o0, L.npar, L.pmask, thr,
+                             dv + 1, s);
   }
   T* zT = as_T<T>(h, h->z64, h->zT, nq, false);
   apply_G_up<T>(h, zT, 1);
@@ -856,13 +871,14 @@ void level_condition_impl(gamblet_ctx* h, int k, int construction, int steps, do
   double* t1 = construction == 1 ? tmp.zeros<double>(n, s) : nullptr;
   const int Lpar = 1 << (k - 1);
   // the operator: B^(k) in the stored basis, or M B^(k) M^T for const1
+  const T* Bd = level_detail_blocks<T>(h, k);
   auto apply = [&](const double* x, double* y) {
     if (construction == 1) {
       launch_detail_basis(L.npar, L.pmask, x, t1, 1, s);
-      launch_detail_spmv<T>((const T*)L.Bd, L.off, L.noff, Lpar, L.npar, t1, y, s);
+      launch_detail_spmv<T>(Bd, L.off, L.noff, Lpar, L.npar, t1, y, s);
       launch_detail_basis(L.npar, L.pmask, y, y, 0, s);
     } else {
-      launch_detail_spmv<T>((const T*)L.Bd, L.off, L.noff, Lpar, L.npar, x, y, s);
+      launch_detail_spmv<T>(Bd, L.off, L.noff, Lpar, L.npar, x, y, s);
     }
   };
   auto dot = [&](const double* a, const double* b) {
