@@ -35,58 +35,64 @@ __device__ __forceinline__ void st4(double* p, const double* v) {
 }
 
 // ---------------------------------------------------------------- restriction
-// One warp per coarse row i (lanes over the neighbours j, so the row of R-hat
-// is read with unit stride); the four warps of a CTA hold the four children
-// of one level-(k-2) parent, whose transform Q^(k-1) is applied through
-// shared memory before the write.
+// Sixteen lanes per coarse row i (lanes over the neighbours j, so the row of
+// R-hat is read with unit stride; four neighbours per lane, their loads
+// issued before use), two rows per warp; the eight rows of a CTA are the
+// children of two level-(k-2) parents, whose transforms Q^(k-1) are applied
+// through shared memory before the write.
 template <typename T>
 __global__ void __launch_bounds__(128) k_restrict(const T* __restrict__ Rhat, int NB,
                                                   const int2* __restrict__ nbr, int Lpar,
                                                   int64_t nrow, const T* __restrict__ ghat, T* out,
                                                   const uint32_t* __restrict__ pmask_km1) {
-  __shared__ T vals[4];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t i = (int64_t)blockIdx.x * 4 + w;
+  __shared__ T vals[8];
+  const int l16 = threadIdx.x & 15, hr = threadIdx.x >> 4;
+  const int64_t base = (int64_t)blockIdx.x * 8;
+  const int64_t i = base + hr;
   T acc = 0;
   if (i < nrow) {
     int x, y;
     demorton((uint32_t)i, x, y);
     const T* row = Rhat + i * 4 * NB;
-    // two neighbours per lane per pass, loads issued before use
-    for (int j0 = lane; j0 < NB; j0 += 64) {
-      const int j1 = j0 + 32;
-      const int p0 = shift_cell(x, y, nbr[j0].x, nbr[j0].y, Lpar, nrow);
-      const int p1 = j1 < NB ? shift_cell(x, y, nbr[j1].x, nbr[j1].y, Lpar, nrow) : -1;
-      T r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0}, g0[4] = {0, 0, 0, 0}, g1[4] = {0, 0, 0, 0};
-      if (p0 >= 0) {
-        ld4(row + 4 * j0, r0);
-        ld4(ghat + 4 * (int64_t)p0, g0);
-      }
-      if (p1 >= 0) {
-        ld4(row + 4 * j1, r1);
-        ld4(ghat + 4 * (int64_t)p1, g1);
+    for (int j0 = l16; j0 < NB; j0 += 64) {
+      T r[4][4], gv[4][4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int j = j0 + 16 * v;
+        const int p = j < NB ? shift_cell(x, y, nbr[j].x, nbr[j].y, Lpar, nrow) : -1;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) r[v][c] = gv[v][c] = T(0);
+        if (p >= 0) {
+          ld4(row + 4 * j, r[v]);
+          ld4(ghat + 4 * (int64_t)p, gv[v]);
+        }
       }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc += r0[c] * g0[c] + r1[c] * g1[c];
+      for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc += r[v][c] * gv[v][c];
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (pmask_km1 == nullptr) {
-    if (lane == 0 && i < nrow) out[i] = acc;
+    if (l16 == 0 && i < nrow) out[i] = acc;
     return;
   }
-  if (lane == 0) vals[w] = acc;
+  if (l16 == 0) vals[hr] = acc;
   __syncthreads();
-  if (threadIdx.x < 4) {
-    // all four slots of the parent are written: in the last parent of a
-    // prefix the rows >= nrow are absent children (zero), but the slots of
-    // the transformed vector are not
-    const int64_t base = (int64_t)blockIdx.x * 4;
-    const int m = (int)pmask_km1[base >> 2] & 15;
-    const int a = threadIdx.x;
-    out[base + a] = qv<T>(m, a, 0) * vals[0] + qv<T>(m, a, 1) * vals[1] +
-                    qv<T>(m, a, 2) * vals[2] + qv<T>(m, a, 3) * vals[3];
+  if (threadIdx.x < 8) {
+    // all four slots of a parent are written: in the last parent of a prefix
+    // the rows >= nrow are absent children (zero), but the slots of the
+    // transformed vector are not
+    const int q = threadIdx.x >> 2, a = threadIdx.x & 3;
+    const int64_t pb = base + 4 * q;
+    if (pb < nrow) {
+      const int m = (int)pmask_km1[pb >> 2] & 15;
+      const T* v = vals + 4 * q;
+      out[pb + a] = qv<T>(m, a, 0) * v[0] + qv<T>(m, a, 1) * v[1] + qv<T>(m, a, 2) * v[2] +
+                    qv<T>(m, a, 3) * v[3];
+    }
   }
 }
 
@@ -94,7 +100,7 @@ template <typename T>
 void launch_restrict(const T* Rhat, int NB, const int2* nbr, int Lpar, int64_t nrow,
                      const T* ghat_k, T* g_km1, const uint32_t* pmask_km1, cudaStream_t s) {
   if (nrow <= 0) return;
-  { count_launch(); k_restrict<T><<<(unsigned)((nrow + 3) / 4), 128, 0, s>>>(Rhat, NB, nbr, Lpar, nrow, ghat_k, g_km1, pmask_km1); }
+  { count_launch(); k_restrict<T><<<(unsigned)((nrow + 7) / 8), 128, 0, s>>>(Rhat, NB, nbr, Lpar, nrow, ghat_k, g_km1, pmask_km1); }
 }
 template void launch_restrict<float>(const float*, int, const int2*, int, int64_t, const float*,
                                      float*, const uint32_t*, cudaStream_t);
