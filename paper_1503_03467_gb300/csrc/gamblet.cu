@@ -312,11 +312,10 @@ void setup_local(gamblet_ctx* h) {
     gg.i_end = L.npar;
     gg.tile_wmin = S.tile_wmin;
     gg.tile_W = S.tile_W;
-    gg.t1_ptr = plan_table<int>(dplan, pl, PlanLevel::kT1Ptr);
     gg.t1 = plan_table<int2>(dplan, pl, PlanLevel::kT1);
     gg.nt1u = S.n_read;
     gg.nitems = (int)S.t1_items.size();
-    gg.t1_items = plan_table<int4>(dplan, pl, PlanLevel::kT1Order);
+    gg.t1_items = plan_table<int4>(dplan, pl, PlanLevel::kT1Items);
     gg.nt2 = (int)S.t2.size();
     gg.t2 = plan_table<int4>(dplan, pl, PlanLevel::kT2);
     gg.t2p_ptr = plan_table<int>(dplan, pl, PlanLevel::kT2pPtr);
@@ -799,6 +798,10 @@ gamblet_ctx* setup_batched_impl(int32_t nprob, const gamblet_csr* A, const int32
   return h;
 }
 
+// Level-q initialisation by the mass matrix (Algorithm 2, lines 2a-5 with
+// Definition deflocinvm): M^-1,loc on patches of radius rho_q around every
+// node, A^(q),loc = (M^-1,loc)^T A M^-1,loc as a CSR, then the ordinary
+// setup on it.  The handle keeps M^-1,loc for the solve's output map.
 gamblet_ctx* setup_mass_impl(const gamblet_csr* A, const gamblet_csr* M, int32_t q,
                              const int32_t* cells, double rho_q, const gamblet_opts* opts) {
   if (!A || !M || !cells) fail(GAMBLET_ERR_INVALID_ARG, "A, M and cells must be non-NULL");

@@ -504,7 +504,7 @@ struct PlanLevel {
   std::vector<int2> hoff;
   // byte offsets of this level's tables in Plan::packed
   enum { kPairIdx, kHalf, kAdjPtr, kAdj, kDiagH, kWin, kL1Ptr, kL1Pairs, kOut, kL2Ptr, kL2Pairs,
-         kT1Ptr, kT1, kT2, kT2pPtr, kT2p, kT1Order, kT3, kT3pPtr, kT3p, kOffNext, kMapNext,
+         kT1, kT2, kT2pPtr, kT2p, kT1Items, kT3, kT3pPtr, kT3p, kOffNext, kMapNext,
          kHIdx, kHOff, kNumTables };
   size_t table_off[kNumTables] = {};
 };

@@ -267,7 +267,6 @@ struct GalerkinGeom {
                          // lanes per output target
   int tile_wmin, tile_W; // tiles: window box [wmin, wmin + W)^2 from the tile origin
   int tile_threads;      // tiles: threads per CTA (256, or 128 for more CTAs per SM)
-  const int* t1_ptr;     // W * W + 1
   const int2* t1;        // (o, j per row packed in bytes, 0xff = none)
   int nt1u;              // window positions read by phase 2 (cid < nt1u)
   int nitems;            // phase-1 work items: (u | cid << 16, t1 begin, t1 end, 0), one

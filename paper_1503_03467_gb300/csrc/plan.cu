@@ -446,12 +446,11 @@ std::shared_ptr<const Plan> build_plan(int q, const OffSet& Oq, const OffSet& N,
     pl.table_off[PlanLevel::kOut] = put_v(S.Sp.v);
     pl.table_off[PlanLevel::kL2Ptr] = put_v(S.l2_ptr);
     pl.table_off[PlanLevel::kL2Pairs] = put_v(S.l2_pairs);
-    pl.table_off[PlanLevel::kT1Ptr] = put_v(S.t1_ptr);
     pl.table_off[PlanLevel::kT1] = put_v(S.t1);
     pl.table_off[PlanLevel::kT2] = put_v(S.t2);
     pl.table_off[PlanLevel::kT2pPtr] = put_v(S.t2p_ptr);
     pl.table_off[PlanLevel::kT2p] = put_v(S.t2p);
-    pl.table_off[PlanLevel::kT1Order] = put_v(S.t1_items);
+    pl.table_off[PlanLevel::kT1Items] = put_v(S.t1_items);
     pl.table_off[PlanLevel::kT3] = put_v(S.t3);
     pl.table_off[PlanLevel::kT3pPtr] = put_v(S.t3p_ptr);
     pl.table_off[PlanLevel::kT3p] = put_v(S.t3p);

@@ -755,10 +755,6 @@ const T* level_detail_blocks(gamblet_ctx* h, int k) {
   return (const T*)L.Bd;
 }
 
-// Level-q initialisation by the mass matrix (Algorithm 2, lines 2a-5 with
-// Definition deflocinvm): M^-1,loc on patches of radius rho_q around every
-// node, A^(q),loc = (M^-1,loc)^T A M^-1,loc as a CSR, then the ordinary
-// setup on it.  The handle keeps M^-1,loc for the solve's output map.
 // Compression in the normalised basis psi^(1)/||psi^(1)||_a, chi^(k)/||chi^(k)||_a
 // (Sec. 5.1): one-pass transform of g, threshold eps * max |c|, rebuild.
 template <typename T>
