@@ -138,7 +138,8 @@ template void launch_transpose_rhat<float>(const float*, int, const int2*, int, 
 template void launch_transpose_rhat<double>(const double*, int, const int2*, int, int64_t,
                                             double*, cudaStream_t);
 
-// One warp per parent p: vhat = [w; v_p / sqrt(m)] + sum_j RT[p][j] v[p - N_j],
+// Sixteen lanes per parent p (two parents per warp, four neighbours' loads
+// in flight per lane): vhat = [w; v_p / sqrt(m)] + sum_j RT[p][j] v[p - N_j],
 // then (inverse) v = Q^T vhat.
 template <typename T>
 __global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ RT, int NB,
@@ -147,42 +148,44 @@ __global__ void __launch_bounds__(128) k_prolong(const T* __restrict__ RT, int N
                                                  const T* __restrict__ w,
                                                  const uint32_t* __restrict__ pmask, int inverse,
                                                  T* out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (p >= npar) return;
-  const int m = (int)pmask[p] & 15;
+  const int l16 = threadIdx.x & 15;
+  const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const bool valid = p < npar;  // no early exit: every lane takes part in the shuffles
+  const int m = valid ? (int)pmask[p] & 15 : 0;
   T h0 = 0, h1 = 0, h2 = 0;
   if (m) {
     int x, y;
     demorton((uint32_t)p, x, y);
     const T* row = RT + p * 4 * NB;
-    // two neighbours per lane per pass, loads issued before use
-    for (int j0 = lane; j0 < NB; j0 += 64) {
-      const int j1 = j0 + 32;
-      const int i0 = shift_cell(x, y, -nbr[j0].x, -nbr[j0].y, Lpar, npar);
-      const int i1 = j1 < NB ? shift_cell(x, y, -nbr[j1].x, -nbr[j1].y, Lpar, npar) : -1;
-      T r0[4] = {0, 0, 0, 0}, r1[4] = {0, 0, 0, 0};
-      T v0 = 0, v1 = 0;
-      if (i0 >= 0) {
-        ld4(row + 4 * j0, r0);
-        v0 = v[i0];
+    for (int j0 = l16; j0 < NB; j0 += 64) {
+      T r[4][4], vv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int j = j0 + 16 * t;
+        const int i = j < NB ? shift_cell(x, y, -nbr[j].x, -nbr[j].y, Lpar, npar) : -1;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) r[t][c] = T(0);
+        vv[t] = T(0);
+        if (i >= 0) {
+          ld4(row + 4 * j, r[t]);
+          vv[t] = v[i];
+        }
       }
-      if (i1 >= 0) {
-        ld4(row + 4 * j1, r1);
-        v1 = v[i1];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        h0 += r[t][0] * vv[t];
+        h1 += r[t][1] * vv[t];
+        h2 += r[t][2] * vv[t];
       }
-      h0 += r0[0] * v0 + r1[0] * v1;
-      h1 += r0[1] * v0 + r1[1] * v1;
-      h2 += r0[2] * v0 + r1[2] * v1;
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = 8; o > 0; o >>= 1) {
     h0 += __shfl_xor_sync(0xffffffffu, h0, o);
     h1 += __shfl_xor_sync(0xffffffffu, h1, o);
     h2 += __shfl_xor_sync(0xffffffffu, h2, o);
   }
-  if (lane != 0) return;
+  if (l16 != 0 || !valid) return;
   T h3 = 0;
   if (m) {
     h3 = v[p] * inv_sqrt_q<T>(__popc(m));
@@ -211,7 +214,7 @@ void launch_prolong(const T* RT, int NB, const int2* nbr, int Lpar, int64_t npar
                     const T* v_km1, const T* w_k, const uint32_t* pmask_k, int inverse, T* out,
                     cudaStream_t s) {
   if (npar <= 0) return;
-  { count_launch(); k_prolong<T><<<(unsigned)((npar * 32 + 127) / 128), 128, 0, s>>>(RT, NB, nbr, Lpar, npar, v_km1, w_k, pmask_k, inverse, out); }
+  { count_launch(); k_prolong<T><<<(unsigned)((npar * 16 + 127) / 128), 128, 0, s>>>(RT, NB, nbr, Lpar, npar, v_km1, w_k, pmask_k, inverse, out); }
 }
 template void launch_prolong<float>(const float*, int, const int2*, int, int64_t, const float*,
                                     const float*, const uint32_t*, int, float*, cudaStream_t);
