@@ -412,6 +412,12 @@ void launch_axpy(int64_t n, const double* alpha_num, const double* alpha_den, do
                  const double* x, double* y, cudaStream_t s);
 void launch_xpby(int64_t n, const double* x, const double* beta_num, const double* beta_den,
                  double sign, double* p, cudaStream_t s);
+// u += (num / den) p, r -= (num / den) q and *rr += r.r (updated r), one pass.
+void launch_update_ur(int64_t n, const double* num, const double* den, const double* p,
+                      const double* q, double* u, double* r, double* rr, cudaStream_t s);
+// z = (double) zf and *zq += z.q, one pass.
+void launch_widen_dot(int64_t n, const float* zf, double* z, const double* q, double* zq,
+                      cudaStream_t s);
 
 // Adjoint contraction: dJ_c = -a_c sum_{p,r} lam[n_p] K[p][r] u[n_r].
 void launch_adjoint_contract(int ncell, const int32_t* cell_nodes, const double* cell_a,

@@ -398,6 +398,68 @@ void launch_dots(int64_t n, const double* a0, const double* b0, const double* a1
   { count_launch(); k_dots<<<(unsigned)blocks, 256, 0, s>>>(n, a0, b0, a1, b1, a2, b2, dots); }
 }
 
+// Grid of a reduction kernel: at most four blocks per SM (every block adds
+// its partial sums to the same words, and those atomics serialise).
+static int64_t reduction_blocks(int64_t n) {
+  static thread_local int dev_cached = -1, sms = 152;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != dev_cached) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    dev_cached = dev;
+  }
+  const int64_t blocks = (n + 255) / 256;
+  return blocks > 4 * (int64_t)sms ? 4 * (int64_t)sms : blocks;
+}
+
+// One step of the outer flexible CG in one pass: u += (num / den) p,
+// r -= (num / den) q, and *rr += r.r of the updated r.
+__global__ void k_update_ur(int64_t n, const double* __restrict__ num,
+                            const double* __restrict__ den, const double* __restrict__ p,
+                            const double* __restrict__ q, double* u, double* r, double* rr) {
+  __shared__ double sa;  // once per block, as in k_axpy
+  if (threadIdx.x == 0) {
+    const double d = *den;
+    sa = d != 0.0 ? (*num) / d : 0.0;
+  }
+  __syncthreads();
+  const double a = sa;
+  double s0 = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    u[i] += a * p[i];
+    const double ri = r[i] - a * q[i];
+    r[i] = ri;
+    s0 += ri * ri;
+  }
+  block_atomic_add(s0, rr);
+}
+void launch_update_ur(int64_t n, const double* num, const double* den, const double* p,
+                      const double* q, double* u, double* r, double* rr, cudaStream_t s) {
+  if (n <= 0) return;
+  count_launch();
+  k_update_ur<<<(unsigned)reduction_blocks(n), 256, 0, s>>>(n, num, den, p, q, u, r, rr);
+}
+
+// z = (double) zf and *zq += z.q in one pass.
+__global__ void k_widen_dot(int64_t n, const float* __restrict__ zf, double* z,
+                            const double* __restrict__ q, double* zq) {
+  double s0 = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = (double)zf[i];
+    z[i] = zi;
+    s0 += zi * q[i];
+  }
+  block_atomic_add(s0, zq);
+}
+void launch_widen_dot(int64_t n, const float* zf, double* z, const double* q, double* zq,
+                      cudaStream_t s) {
+  if (n <= 0) return;
+  count_launch();
+  k_widen_dot<<<(unsigned)reduction_blocks(n), 256, 0, s>>>(n, zf, z, q, zq);
+}
+
 // y += sign * (num / den) * x
 // (the scalar is formed once per block: a float64 division per element
 // would hold this memory-bound kernel on the float64 pipe)

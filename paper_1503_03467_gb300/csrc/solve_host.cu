@@ -392,9 +392,8 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
         CK(cudaMemsetAsync(d, 0, sizeof(double) * 4, s));
         // d0 = p.q, d1 = p.r
         launch_dots(nq, h->p64, h->q64, h->p64, h->r64, nullptr, nullptr, d, s);
-        launch_axpy(nq, d + 1, d + 0, +1.0, h->p64, h->u64, s);
-        launch_axpy(nq, d + 1, d + 0, -1.0, h->q64, h->r64, s);
-        launch_dots(nq, nullptr, nullptr, nullptr, nullptr, h->r64, h->r64, d, s);  // d2 = r.r
+        // u += (d1 / d0) p, r -= (d1 / d0) q, d2 = r.r
+        launch_update_ur(nq, d + 1, d + 0, h->p64, h->q64, h->u64, h->r64, d + 2, s);
         CK(cudaMemcpyAsync(h->dots_h, d, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         relres = std::sqrt(h->dots_h[2]) / gnorm;
@@ -402,9 +401,11 @@ gamblet_status solve_impl(gamblet_ctx* h, const double* g_user, double* u_user, 
         if (relres <= h->opts.refine_tol) break;
         rT = as_T<T>(h, h->r64, h->rT, nq, true);
         apply_G<T>(h, rT, zT, 0);
-        if (is_f32<T>()) launch_convert_f32_f64((const float*)zT, h->z64, nq, s);
         // d3 = z.q ; p = z - (d3 / d0) p
-        launch_dots(nq, h->z64, h->q64, nullptr, nullptr, nullptr, nullptr, d + 3, s);
+        if (is_f32<T>())
+          launch_widen_dot(nq, (const float*)zT, h->z64, h->q64, d + 3, s);
+        else
+          launch_dots(nq, h->z64, h->q64, nullptr, nullptr, nullptr, nullptr, d + 3, s);
         launch_xpby(nq, h->z64, d + 3, d + 0, -1.0, h->p64, s);
         CK(cudaGetLastError());
       }
