@@ -164,10 +164,12 @@ __global__ void __launch_bounds__(256) k_galerkin_rows(const T* __restrict__ Aha
 // Ahat[o][origin+u] is loaded once and applied to every row whose patch
 // reaches it (the neighbour index j of each row), accumulating t_r(u) for
 // the four rows.
-// Phase 2: a warp per output target cell c loads the row Rhat_c once (lanes
-// over j) and forms the dot products with t_r(c + N_j) of every row r for
-// which c - r is an output offset (host list t2).  Compared with a row per
-// CTA this reads each block and each Rhat row up to four times less often.
+// Phase 2: LPT lanes per output target cell c (host list t2), or per
+// horizontal pair of targets (host list t3, variants 6-8), walk the list of
+// window positions u = c + N_j, reading Rhat_c(j) from global memory and
+// t_r(u) from shared memory, and form the dot products of every row r for
+// which c - r is an output offset.  Compared with a row per CTA this reads
+// each block and each Rhat row up to four times less often.
 size_t galerkin_tile_smem_bytes(const GalerkinGeom& g, size_t elem) {
   return elem * (16 * (size_t)g.NB + 16 * (size_t)g.nt1u);
 }
@@ -332,11 +334,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_galerkin_tile(c
     }
     __syncthreads();
     // phase 2: outputs A_{i0+r, c} for every target cell c.  LPT lanes per
-    // target (32 / LPT targets per warp; 4, 8 or 16, chosen per level by the
-    // launch-shape tuner: short pair lists on the finest level, long ones on
-    // dense levels) stride over the target's list of pairs (j, u) whose
-    // window position holds a nonzero t; the partial sums combine in
-    // log2(LPT) shuffle steps.
+    // target or pair of targets (4, 8 or 16, chosen per level by the
+    // launch-shape tuner) stride over its list of window positions; the
+    // partial sums are reduce-scattered over the lanes.
     if constexpr (PAIRS) {
       galerkin_tile_pairs<T, LPT>(g, Rhat, pmask, tt, NT, x0, y0, i0, live, Aout);
     } else {
