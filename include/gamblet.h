@@ -97,11 +97,12 @@ typedef struct {
   int32_t use_graph;        /* capture repeated launch sequences in CUDA graphs */
   int32_t profile;          /* 1: time every kernel phase with CUDA events on
                                the library's stream (gamblet_kernel_stats)  */
-  int32_t autotune;         /* 1: pick launch shapes (patch-CG lanes per
-                               neighbour parent, level-CG SpMV tile) by
-                               timing candidates on a sample of each large
-                               level, once per geometry and precision in a
-                               process; 0: fixed rules                     */
+  int32_t autotune;         /* 1: pick launch shapes (patch solver and its
+                               lanes per neighbour parent, Galerkin kernel,
+                               lanes and threads per CTA, level-CG SpMV
+                               tile) by timing candidates on a sample of
+                               each large level, once per geometry and
+                               precision in a process; 0: fixed rules      */
   int32_t galerkin_variant; /* -1: automatic; 0..8: use that Galerkin
                                kernel on every level (3, 4, 5: the tile
                                kernel with 8, 4, 16 lanes per output;
