@@ -453,6 +453,24 @@ GAMBLET_API int32_t gamblet_kernel_stats(gamblet_handle h, gamblet_kernel_stat* 
                                          int32_t capacity);
 GAMBLET_API void gamblet_reset_kernel_stats(gamblet_handle h);
 
+/*
+ * Host-only consistency check of the symbolic plan (needs no GPU): builds the
+ * plan of a full 2^q x 2^q square (Q1 block stencil, patches i^rho of
+ * Sec. 4.10 with rule nbr_rule) and verifies its tables against their
+ * definitions derived independently - the half-plane of every symmetric
+ * block stencil (one block per pair of opposite offsets), the phase-1 lists
+ * of the tiled Galerkin product (every contribution Ahat[o][u] Rhat_r(j) with
+ * u = r + N_j - O_o at a position the outputs read, exactly once) and its
+ * phase-2 lists, single and paired (every incidence of an output target c
+ * with a window position c + N_j, Eq. eqhuhiuv).
+ *   q         2..12; rho in (0, 8]; nbr_rule 0 (Euclidean) or 1 (box).
+ *   counts    NULL or 5 int64: levels, phase-1 entries, phase-1 items,
+ *             phase-2 incidences, half-plane offsets (summed over levels).
+ * Returns INVALID_ARG with the first violated property in gamblet_last_error.
+ */
+GAMBLET_API gamblet_status gamblet_plan_check(int32_t q, double rho, int32_t nbr_rule,
+                                              int64_t* counts);
+
 /* Total CUDA kernel launches issued by this library in this process. */
 GAMBLET_API int64_t gamblet_kernel_launches(void);
 

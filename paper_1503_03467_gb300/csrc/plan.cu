@@ -488,3 +488,182 @@ std::shared_ptr<const Plan> cached_plan(int q, double rho, int rule, const OffSe
 
 }  // namespace hs
 }  // namespace gb
+
+namespace gb {
+namespace hs {
+
+// Consistency of a plan's tables with their definitions, derived a second way
+// (from the contributions each table must carry rather than the way the
+// builder enumerates them).  counts: levels, t1 entries, phase-1 items,
+// phase-2 target incidences, half-plane offsets.
+void check_plan(const Plan& P, int q, const OffSet& N, int64_t* counts) {
+  auto need = [](bool ok, int k, const std::string& what) {
+    if (!ok) fail(GAMBLET_ERR_INVALID_ARG, "plan level " + std::to_string(k) + ": " + what);
+  };
+  const int NB = N.size();
+  int64_t n_t1 = 0, n_items = 0, n_inc = 0, n_half = 0;
+  for (int k = q; k >= 2; --k) {
+    const PlanLevel& pl = P.lv[k];
+    const SymLevel& S = pl.S;
+    const int Lpar = 1 << (k - 1);
+    // half-plane of the level stencil: one of d, -d for every d != 0, and 0
+    std::vector<int> want_h;
+    for (int o = 0; o < S.O.size(); ++o) {
+      const int2 d = S.O.v[o];
+      need(S.O.find(-d.x, -d.y) >= 0, k, "block stencil not symmetric");
+      if (d.y > 0 || (d.y == 0 && d.x >= 0)) want_h.push_back(o);
+    }
+    need(pl.hidx == want_h && pl.hoff.size() == want_h.size(), k, "half-plane offsets");
+    for (size_t h = 0; h < want_h.size(); ++h)
+      need(pl.hoff[h].x == S.O.v[want_h[h]].x && pl.hoff[h].y == S.O.v[want_h[h]].y, k,
+           "half-plane offset values");
+    n_half += (int64_t)want_h.size();
+    // tile geometry: row r of the 2 x 2 tile sits at rv[r] from the origin
+    const int W = S.tile_W, wmin = S.tile_wmin;
+    const int2 rv[4] = {make_int2(0, 0), make_int2(1, 0), make_int2(0, 1), make_int2(1, 1)};
+    auto box = [&](int x, int y) {
+      const int ux = x - wmin, uy = y - wmin;
+      return (ux >= 0 && ux < W && uy >= 0 && uy < W) ? uy * W + ux : -1;
+    };
+    // positions read by phase 2: c + N_j for every output target c of a row,
+    // where some row's window holds it
+    std::set<int> win4;
+    for (int r = 0; r < 4; ++r)
+      for (const int2& w : S.WIN.v) {
+        const int u = box(rv[r].x + w.x, rv[r].y + w.y);
+        need(u >= 0, k, "window outside the tile box");
+        win4.insert(u);
+      }
+    std::set<int> read;
+    std::map<std::pair<int, int>, std::set<std::pair<int, int>>> inc;  // target -> (j, u)
+    for (int r = 0; r < 4; ++r)
+      for (const int2& d : S.Sp.v) {
+        const int cx = rv[r].x + d.x, cy = rv[r].y + d.y;
+        for (int j = 0; j < NB; ++j) {
+          const int u = box(cx + N.v[j].x, cy + N.v[j].y);
+          if (u >= 0 && win4.count(u)) {
+            inc[{cx, cy}].insert({j, u});
+            read.insert(u);
+          }
+        }
+        inc[{cx, cy}];  // targets without positions still carry outputs
+      }
+    // phase-1 items: the read positions, once each, with their box-order index
+    std::vector<int> cid_of(W * W, -1);
+    {
+      int c = 0;
+      for (int u : read) cid_of[u] = c++;
+    }
+    need((int)S.t1_items.size() == (int)read.size() && S.n_read == (int)read.size(), k,
+         "phase-1 items do not match the read positions");
+    std::set<int> seen;
+    for (size_t e = 0; e < S.t1_items.size(); ++e) {
+      const int4 it = S.t1_items[e];
+      const int u = it.x & 0xffff, c = it.x >> 16;
+      need(read.count(u) && !seen.count(u), k, "phase-1 item position");
+      seen.insert(u);
+      need(c == cid_of[u], k, "phase-1 item index");
+      need(it.y == S.t1_ptr[u] && it.z == S.t1_ptr[u + 1], k, "phase-1 item range");
+      if (e > 0) need(it.z - it.y <= S.t1_items[e - 1].z - S.t1_items[e - 1].y, k, "item order");
+    }
+    n_items += (int64_t)S.t1_items.size();
+    // phase 1: every contribution A_hat[o][u] R_hat_r(j) with u = r + N_j - O_o
+    // at a read position, exactly once, and nothing else
+    std::set<std::tuple<int, int, int, int>> want1, have1;  // (u, o, r, j)
+    for (int r = 0; r < 4; ++r)
+      for (int j = 0; j < NB; ++j)
+        for (int o = 0; o < S.O.size(); ++o) {
+          const int wx = N.v[j].x - S.O.v[o].x, wy = N.v[j].y - S.O.v[o].y;
+          if (std::abs(wx) > Lpar - 1 || std::abs(wy) > Lpar - 1) continue;
+          const int u = box(rv[r].x + wx, rv[r].y + wy);
+          if (u >= 0 && read.count(u)) want1.insert({u, o, r, j});
+        }
+    for (int u = 0; u < W * W; ++u)
+      for (int e = S.t1_ptr[u]; e < S.t1_ptr[u + 1]; ++e) {
+        for (int r = 0; r < 4; ++r) {
+          const int j = ((unsigned)S.t1[e].y >> (8 * r)) & 0xffu;
+          if (j != 0xff) {
+            need(read.count(u) > 0, k, "phase-1 entry at an unread position");
+            const bool fresh = have1.insert({u, S.t1[e].x, r, j}).second;
+            need(fresh, k, "phase-1 contribution listed twice");
+          }
+        }
+        ++n_t1;
+      }
+    need(have1 == want1, k, "phase-1 contributions");
+    // phase 2, single targets: row offsets and the pair lists
+    std::map<std::pair<int, int>, std::set<std::pair<int, int>>> got2, got3;
+    for (size_t e = 0; e < S.t2.size(); ++e) {
+      const int4 t = S.t2[e];
+      const int d[4] = {(int)(short)(t.z & 0xffff), t.z >> 16, (int)(short)(t.w & 0xffff),
+                        t.w >> 16};
+      for (int r = 0; r < 4; ++r)
+        need(d[r] == S.Sp.find(t.x - rv[r].x, t.y - rv[r].y), k, "phase-2 output offsets");
+      auto& g = got2[{t.x, t.y}];
+      for (int q2 = S.t2p_ptr[e]; q2 < S.t2p_ptr[e + 1]; ++q2) {
+        const int j = S.t2p[q2] & 0xff, c = S.t2p[q2] >> 8;
+        need(c >= 0 && c < (int)read.size(), k, "phase-2 position index");
+        g.insert({j, c});
+      }
+    }
+    // phase 2, pairs of targets (c, c + (1, 0))
+    need((int)S.t3.size() == 2 * ((int)S.t3p_ptr.size() - 1), k, "pair records");
+    for (size_t e = 0; 2 * e < S.t3.size(); ++e) {
+      const int4 a = S.t3[2 * e], b = S.t3[2 * e + 1];
+      const bool has_b = (b.z != -1 || b.w != -1);
+      if (has_b) need(b.x == a.x + 1 && b.y == a.y, k, "pair partner");
+      auto& ga = got3[{a.x, a.y}];
+      for (int q3 = S.t3p_ptr[e]; q3 < S.t3p_ptr[e + 1]; ++q3) {
+        const uint32_t pu = S.t3p[q3];
+        const int c = (int)(pu & 0xffffu), ja = (int)((pu >> 16) & 0xffu), jb = (int)(pu >> 24);
+        need(c < (int)read.size() && (ja != 0xff || jb != 0xff), k, "pair entry");
+        if (ja != 0xff) ga.insert({ja, c});
+        if (jb != 0xff) {
+          need(has_b, k, "pair entry for a missing partner");
+          got3[{b.x, b.y}].insert({jb, c});
+        }
+      }
+      if (has_b) got3[{b.x, b.y}];
+    }
+    // both lists carry exactly the incidences of the definition
+    std::map<std::pair<int, int>, std::set<std::pair<int, int>>> want2;
+    for (const auto& kv : inc) {
+      auto& w = want2[kv.first];
+      for (const auto& ju : kv.second) w.insert({ju.first, cid_of[ju.second]});
+      n_inc += (int64_t)kv.second.size();
+    }
+    need(got2 == want2, k, "phase-2 pair lists (single targets)");
+    need(got3 == want2, k, "phase-2 pair lists (pairs of targets)");
+  }
+  if (counts) {
+    counts[0] = q - 1;
+    counts[1] = n_t1;
+    counts[2] = n_items;
+    counts[3] = n_inc;
+    counts[4] = n_half;
+  }
+}
+
+}  // namespace hs
+}  // namespace gb
+
+extern "C" gamblet_status gamblet_plan_check(int32_t q, double rho, int32_t nbr_rule,
+                                             int64_t* counts) {
+  using namespace gb::hs;
+  try {
+    if (q < 2 || q > 12) fail(GAMBLET_ERR_INVALID_ARG, "q must be in [2, 12]");
+    if (!(rho > 0) || rho > 8) fail(GAMBLET_ERR_INVALID_ARG, "rho must be in (0, 8]");
+    if (nbr_rule != 0 && nbr_rule != 1) fail(GAMBLET_ERR_INVALID_ARG, "nbr_rule must be 0 or 1");
+    OffSet Oq;  // the Q1 operator's 3 x 3 block stencil on a full square
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) Oq.add(dx, dy);
+    const OffSet N = neighbour_offsets(rho, nbr_rule);
+    const auto plan = build_plan(q, Oq, N, "check");
+    check_plan(*plan, q, N, counts);
+    return GAMBLET_OK;
+  } catch (const GbError& e) {
+    return set_error(e);
+  } catch (const std::exception& e) {
+    return set_error(GbError{GAMBLET_ERR_INVALID_ARG, e.what()});
+  }
+}

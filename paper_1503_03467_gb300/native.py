@@ -122,6 +122,8 @@ SIGNATURES = {
                                               ctypes.c_int32]),
     "gamblet_reset_kernel_stats": (None, [ctypes.c_void_p]),
     "gamblet_kernel_launches": (ctypes.c_int64, []),
+    "gamblet_plan_check": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                          ctypes.c_void_p]),
     "gamblet_objective_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p]),
@@ -386,6 +388,16 @@ def gamblet_reset_kernel_stats(h: int) -> None:
 
 def gamblet_kernel_launches() -> int:
     return int(_lib.gamblet_kernel_launches())
+
+
+def gamblet_plan_check(q: int, rho: float, nbr_rule: int = 0) -> dict:
+    """Host-only consistency check of the symbolic plan of a 2^q square (no
+    GPU needed); raises GambletError on the first violated property."""
+    counts = (ctypes.c_int64 * 5)()
+    _check(_lib.gamblet_plan_check(int(q), float(rho), int(nbr_rule),
+                                   ctypes.cast(counts, ctypes.c_void_p)))
+    return {"levels": counts[0], "phase1_entries": counts[1], "phase1_items": counts[2],
+            "phase2_incidences": counts[3], "half_offsets": counts[4]}
 
 
 def gamblet_device_bytes(h: int) -> int:
