@@ -458,11 +458,14 @@ GAMBLET_API void gamblet_reset_kernel_stats(gamblet_handle h);
  * plan of a full 2^q x 2^q square (Q1 block stencil, patches i^rho of
  * Sec. 4.10 with rule nbr_rule) and verifies its tables against their
  * definitions derived independently - the half-plane of every symmetric
- * block stencil (one block per pair of opposite offsets), the phase-1 lists
- * of the tiled Galerkin product (every contribution Ahat[o][u] Rhat_r(j) with
- * u = r + N_j - O_o at a position the outputs read, exactly once) and its
- * phase-2 lists, single and paired (every incidence of an output target c
- * with a window position c + N_j, Eq. eqhuhiuv).
+ * block stencil (one block per pair of opposite offsets), the patch block
+ * lists and per-row adjacency (Definition defb), the tensor-core windows
+ * (union of the patches, membership bits, blocks, right-hand-side offsets,
+ * output map), the phase-1 lists of the tiled Galerkin product (every
+ * contribution Ahat[o][u] Rhat_r(j) with u = r + N_j - O_o at a position the
+ * outputs read, exactly once) and its phase-2 lists, single and paired
+ * (every incidence of an output target c with a window position c + N_j,
+ * Eq. eqhuhiuv).
  *   q         2..12; rho in (0, 8]; nbr_rule 0 (Euclidean) or 1 (box).
  *   counts    NULL or 5 int64: levels, phase-1 entries, phase-1 items,
  *             phase-2 incidences, half-plane offsets (summed over levels).

@@ -634,6 +634,75 @@ void check_plan(const Plan& P, int q, const OffSet& N, int64_t* counts) {
     }
     need(got2 == want2, k, "phase-2 pair lists (single targets)");
     need(got3 == want2, k, "phase-2 pair lists (pairs of targets)");
+    // patch matrices (Definition defb): one stored block per neighbour pair
+    // ja >= jb coupled through O_k, in bank-coloured slots; each row's
+    // adjacency walks every block touching it (the other side transposed)
+    std::set<std::tuple<int, int, int>> wantb, haveb;  // (ja, jb, o)
+    for (int a = 0; a < NB; ++a)
+      for (int b = 0; b < NB; ++b) {
+        const int o = S.O.find(N.v[b].x - N.v[a].x, N.v[b].y - N.v[a].y);
+        need(S.pair_idx[(size_t)a * NB + b] == o, k, "patch pair index");
+        if (a >= b && o >= 0) wantb.insert({a, b, o});
+      }
+    for (const int4& hb : pl.half)
+      if (hb.x >= 0) need(haveb.insert({hb.x, hb.y, hb.z}).second, k, "patch block stored twice");
+    need(haveb == wantb, k, "patch blocks");
+    for (int j = 0; j < NB; ++j) {
+      std::set<std::pair<int, int>> wanta, havea;  // (other, transposed) of each touching block
+      for (const auto& t : wantb) {
+        if (std::get<0>(t) == j) wanta.insert({std::get<1>(t), 0});
+        else if (std::get<1>(t) == j) wanta.insert({std::get<0>(t), 1});
+      }
+      for (int e = pl.adj_ptr[j]; e < pl.adj_ptr[j + 1]; ++e) {
+        const int4 ad = pl.adj[e];
+        const int4 hb = pl.half[ad.x];
+        need(ad.z == 0 ? (hb.x == j && hb.y == ad.y) : (hb.y == j && hb.x == ad.y), k,
+             "patch adjacency entry");
+        havea.insert({ad.y, ad.z});
+      }
+      need(havea == wanta && pl.adj_ptr[j + 1] - pl.adj_ptr[j] == (int)wanta.size(), k,
+           "patch adjacency of a row");
+      need(pl.half[pl.diag_h[j]].x == j && pl.half[pl.diag_h[j]].y == j, k, "patch diagonal");
+    }
+    // tensor-core windows of G x G cells: the union of the patches, the
+    // membership bits, the union's blocks, right-hand-side offsets and the
+    // output map
+    for (int G = 1; G <= 2; ++G) {
+      const MmaWin& Wn = pl.mwin[G - 1];
+      std::set<std::pair<int, int>> U;
+      for (int c = 0; c < G * G; ++c)
+        for (const int2& o : N.v) U.insert({(c & 1) + o.x, (c >> 1) + o.y});
+      need((int)Wn.U.size() == (int)U.size() && Wn.nU == (int)U.size() && Wn.NP == G * G, k,
+           "window union size");
+      std::map<std::pair<int, int>, int> uidx;
+      for (int u = 0; u < Wn.nU; ++u) {
+        need(U.count({Wn.U[u].x, Wn.U[u].y}) && !uidx.count({Wn.U[u].x, Wn.U[u].y}), k,
+             "window union member");
+        uidx[{Wn.U[u].x, Wn.U[u].y}] = u;
+        int bits = 0;
+        for (int c = 0; c < G * G; ++c)
+          if (N.find(Wn.U[u].x - (c & 1), Wn.U[u].y - (c >> 1)) >= 0) bits |= 1 << c;
+        need(Wn.ubits[u] == bits, k, "window membership bits");
+        for (int c = 0; c < G * G; ++c)
+          need(Wn.rhs_o[(size_t)c * Wn.nU + u] ==
+                   S.O.find((c & 1) - Wn.U[u].x, (c >> 1) - Wn.U[u].y),
+               k, "window right-hand-side offset");
+      }
+      std::set<std::tuple<int, int, int>> wantw, havew;
+      for (int a = 0; a < Wn.nU; ++a)
+        for (int b = 0; b < a; ++b) {
+          const int o = S.O.find(Wn.U[b].x - Wn.U[a].x, Wn.U[b].y - Wn.U[a].y);
+          if (o >= 0) wantw.insert({a, b, o});
+        }
+      for (const int4& pr : Wn.pairs) havew.insert({pr.x, pr.y, pr.z});
+      need(havew == wantw && Wn.pairs.size() == wantw.size(), k, "window blocks");
+      for (int c = 0; c < G * G; ++c)
+        for (int j = 0; j < NB; ++j)
+          need(Wn.outmap[(size_t)c * NB + j] ==
+                   uidx.at({(c & 1) + N.v[j].x, (c >> 1) + N.v[j].y}),
+               k, "window output map");
+      need(Wn.diag_o == S.O.find(0, 0), k, "window diagonal offset");
+    }
   }
   if (counts) {
     counts[0] = q - 1;

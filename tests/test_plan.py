@@ -1,7 +1,8 @@
 """Host logic of the symbolic plan (no GPU): gamblet_plan_check rebuilds the
 tables of a 2^q square and verifies them against their definitions derived a
 second way - the half-plane of each symmetric level stencil (the level CG
-stores one block per pair of opposite offsets), the phase-1 contributions of
+stores one block per pair of opposite offsets), the patch block lists and
+adjacency (Definition defb), the tensor-core windows, the phase-1 contributions of
 the tiled Galerkin product (Eq. eqhuhiuv; every Ahat[o][u] Rhat_r(j) with
 u = r + N_j - O_o at a position the outputs read, exactly once) and its
 phase-2 incidences, for single targets and for horizontal pairs of targets."""
