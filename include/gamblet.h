@@ -463,9 +463,10 @@ GAMBLET_API void gamblet_reset_kernel_stats(gamblet_handle h);
  * (union of the patches, membership bits, blocks, right-hand-side offsets,
  * output map), the phase-1 lists of the tiled Galerkin product (every
  * contribution Ahat[o][u] Rhat_r(j) with u = r + N_j - O_o at a position the
- * outputs read, exactly once) and its phase-2 lists, single and paired
- * (every incidence of an output target c with a window position c + N_j,
- * Eq. eqhuhiuv).
+ * outputs read, exactly once), its phase-2 lists, single and paired (every
+ * incidence of an output target c with a window position c + N_j,
+ * Eq. eqhuhiuv), and the next level's block stencil and conversion map
+ * (every coupling of the coarse cell stencil in exactly one block).
  *   q         2..12; rho in (0, 8]; nbr_rule 0 (Euclidean) or 1 (box).
  *   counts    NULL or 5 int64: levels, phase-1 entries, phase-1 items,
  *             phase-2 incidences, half-plane offsets (summed over levels).

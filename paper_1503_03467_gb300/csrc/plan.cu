@@ -703,6 +703,31 @@ void check_plan(const Plan& P, int q, const OffSet& N, int64_t* counts) {
                k, "window output map");
       need(Wn.diag_o == S.O.find(0, 0), k, "window diagonal offset");
     }
+    // the level-(k-1) block stencil: every coupling d of the cell stencil S
+    // between child c of a parent and some child of another lies in O_(k-1),
+    // and the conversion map points at d in the computed half-plane (or at
+    // -d, read transposed)
+    if (k - 1 >= 2) {
+      const OffSet& On = pl.O_next;
+      const int Lp = 1 << (k - 2);
+      auto decodes_to = [&](int m, int dx, int dy) {
+        if (m >= 0) return S.Sp.v[m].x == dx && S.Sp.v[m].y == dy;
+        if (m <= -2) return S.Sp.v[-m - 2].x == -dx && S.Sp.v[-m - 2].y == -dy;
+        return false;
+      };
+      for (const int2& d : S.S.v)
+        for (int c = 0; c < 4; ++c)
+          for (int cc = 0; cc < 4; ++cc) {
+            const int ex = d.x - ((cc & 1) - (c & 1)), ey = d.y - ((cc >> 1) - (c >> 1));
+            if ((ex & 1) || (ey & 1)) continue;
+            const int Dx = ex / 2, Dy = ey / 2;
+            if (std::abs(Dx) > Lp - 1 || std::abs(Dy) > Lp - 1) continue;
+            const int o = On.find(Dx, Dy);
+            need(o >= 0, k, "cell coupling missing from the next block stencil");
+            need(decodes_to(pl.map_next[(size_t)o * 16 + c * 4 + cc], d.x, d.y), k,
+                 "block conversion map");
+          }
+    }
   }
   if (counts) {
     counts[0] = q - 1;
