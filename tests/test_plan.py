@@ -19,7 +19,8 @@ def nv():
 
 
 @pytest.mark.parametrize("q,rho,rule", [(4, 1.0, 0), (5, 2.0, 0), (6, 3.0, 0), (8, 3.0, 0),
-                                        (6, 2.0, 1), (5, 4.0, 0), (7, 1.5, 1), (6, 6.0, 0)])
+                                        (6, 2.0, 1), (5, 4.0, 0), (7, 1.5, 1), (6, 6.0, 0),
+                                        (10, 3.0, 0), (11, 3.0, 0), (9, 4.0, 0)])
 def test_plan_tables_match_their_definitions(nv, q, rho, rule):
     c = nv.gamblet_plan_check(q, rho, rule)
     assert c["levels"] == q - 1
