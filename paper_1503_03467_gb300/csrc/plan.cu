@@ -4,7 +4,14 @@
 // level A^(k) (exact Minkowski sums of the interpolation and operator
 // supports), the patch block lists, the Galerkin pair lists (Eq. eqhuhiuv)
 // and the tables of the tensor-core patch windows - built once per geometry
-// and cached process-wide.
+// and cached process-wide; and a host-only check of those tables against
+// their definitions (gamblet_plan_check).
+#include <map>
+#include <set>
+#include <string>
+#include <tuple>
+#include <vector>
+
 #include "host.cuh"
 
 namespace gb {
